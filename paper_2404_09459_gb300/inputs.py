@@ -1,0 +1,155 @@
+"""Seeded synthetic matrix pairs (input generation only; no GSV arithmetic).
+
+A pair is built with planted generalized singular values, the construction the
+paper uses for its synthetic experiments (Section 4.1: G1 = U Sigma1 R,
+G2 = V Sigma2 R with orthonormalised Gaussian U, V, sorted uniform alpha,
+beta = sqrt(1 - alpha^2)), made real-valued and numerically low-rank:
+
+    G1 = U_r diag(alpha) D O_r + sigma N1,    G2 = V_r diag(beta) D O_r + sigma N2
+
+U_r (m x r), V_r (p x r) Haar column-orthonormal, O_r (r x n) orthonormal rows,
+D = diag(d_1..d_r) the singular scale of the shared factor R = D O_r, N1, N2
+i.i.d. N(0, 1).  Without noise the r non-trivial GSV pairs are exactly
+(alpha_i, beta_i) and the singular values of the stack [G1; G2] are d_i.
+
+Used by the tests (the oracle and the GPU see the same arrays) and by the
+benchmark.  The `torch` backend builds the same recipe on a CUDA device with
+torch's generator (different random stream) for pairs too large for the host.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class PairSpec:
+    """Shape and spectrum of one synthetic pair plus the solver parameters."""
+    m: int
+    p: int
+    n: int
+    r: int
+    alpha: str = "uniform"      # "linspace" (0.99 .. 0.01) or "uniform" (U(0,1) sorted desc)
+    decay: str = "exp10"        # "logspace02" (1..100), "exp10" exp(-i/10), "pow15" i^-1.5
+    sigma: float = 1e-6
+    k: int = 0                  # target rank (0: use r)
+    oversample: int = 10
+    q: int = 1
+    seed: int = 0
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def kk(self) -> int:
+        return self.k if self.k else self.r
+
+    @property
+    def l(self) -> int:
+        return self.kk + self.oversample
+
+
+# Workloads.  `PAIR_FP64_SMALL` is the plain FP64 pair, `PAIR_TF32_LARGE` the single
+# large mixed-precision pair, `PAIR_BF16_STRESS` the slow-decay precision stress pair.
+PAIR_FP64_SMALL = PairSpec(m=2000, p=2000, n=200, r=20, alpha="linspace", decay="logspace02",
+                           sigma=1e-8, k=20, oversample=10, q=1, seed=0)
+PAIR_TF32_LARGE = PairSpec(m=20000, p=15000, n=1000, r=50, alpha="uniform", decay="exp10",
+                           sigma=1e-6, k=50, oversample=10, q=2, seed=0)
+PAIR_BF16_STRESS = PairSpec(m=120000, p=80000, n=4000, r=200, alpha="uniform", decay="pow15",
+                            sigma=1e-4, k=200, oversample=20, q=3, seed=0)
+
+
+def planted_alpha(spec: PairSpec, rng: np.random.Generator) -> np.ndarray:
+    if spec.alpha == "linspace":
+        a = np.linspace(0.99, 0.01, spec.r)
+    elif spec.alpha == "uniform":
+        a = np.sort(rng.uniform(0.0, 1.0, spec.r))[::-1].copy()
+    else:
+        raise ValueError(spec.alpha)
+    return a
+
+
+def planted_scale(spec: PairSpec) -> np.ndarray:
+    i = np.arange(1, spec.r + 1, dtype=np.float64)
+    if spec.decay == "logspace02":
+        return np.logspace(0.0, 2.0, spec.r)
+    if spec.decay == "exp10":
+        return np.exp(-i / 10.0)
+    if spec.decay == "pow15":
+        return i ** -1.5
+    raise ValueError(spec.decay)
+
+
+def _haar_columns(rng: np.random.Generator, rows: int, cols: int) -> np.ndarray:
+    a = rng.standard_normal((rows, cols))
+    q, r = np.linalg.qr(a)
+    return q * np.sign(np.diag(r))[None, :]
+
+
+def planted_pair(spec: PairSpec, dtype=np.float64):
+    """Numpy pair (G1, G2, alpha_true, beta_true) for `spec` (host memory)."""
+    rng = np.random.default_rng(np.random.SeedSequence([spec.seed, spec.m, spec.p, spec.n, spec.r]))
+    alpha = planted_alpha(spec, rng)
+    beta = np.sqrt((1.0 - alpha) * (1.0 + alpha))
+    d = planted_scale(spec)
+    U = _haar_columns(rng, spec.m, spec.r)
+    V = _haar_columns(rng, spec.p, spec.r)
+    O = _haar_columns(rng, spec.n, spec.r).T
+    G1 = (U * (alpha * d)[None, :]) @ O
+    G2 = (V * (beta * d)[None, :]) @ O
+    if spec.sigma:
+        G1 += spec.sigma * rng.standard_normal(G1.shape)
+        G2 += spec.sigma * rng.standard_normal(G2.shape)
+    return G1.astype(dtype), G2.astype(dtype), alpha, beta
+
+
+def planted_pair_torch(spec: PairSpec, device="cuda", dtype=None):
+    """The same recipe built with torch on `device` (for pairs too large for numpy)."""
+    import torch
+    dtype = dtype or torch.float32
+    g = torch.Generator(device=device)
+    g.manual_seed(int(spec.seed) * 1000003 + spec.m * 7 + spec.p * 11 + spec.n * 13 + spec.r)
+    rng = np.random.default_rng(np.random.SeedSequence([spec.seed, spec.m, spec.p, spec.n, spec.r]))
+    alpha = planted_alpha(spec, rng)
+    beta = np.sqrt((1.0 - alpha) * (1.0 + alpha))
+    d = planted_scale(spec)
+
+    def haar(rows, cols):
+        a = torch.randn(rows, cols, generator=g, device=device, dtype=torch.float64)
+        q, r = torch.linalg.qr(a)
+        return q * torch.sign(torch.diagonal(r))[None, :]
+
+    U = haar(spec.m, spec.r)
+    V = haar(spec.p, spec.r)
+    O = haar(spec.n, spec.r).T
+    ad = torch.tensor(alpha * d, device=device)
+    bd = torch.tensor(beta * d, device=device)
+    out = []
+    for basis, w, rows in ((U, ad, spec.m), (V, bd, spec.p)):
+        G = torch.empty(rows, spec.n, device=device, dtype=dtype)
+        step = 8192
+        for r0 in range(0, rows, step):
+            r1 = min(rows, r0 + step)
+            blk = (basis[r0:r1] * w[None, :]) @ O
+            if spec.sigma:
+                blk += spec.sigma * torch.randn(r1 - r0, spec.n, generator=g, device=device,
+                                                dtype=torch.float64)
+            G[r0:r1] = blk.to(dtype)
+        out.append(G)
+    return out[0], out[1], alpha, beta
+
+
+def uneven_batch(npairs: int = 256, seed: int = 0, m_range=(2000, 30000), n_range=(100, 1000),
+                 r_range=(10, 100), oversample: int = 10, q: int = 1, sigma: float = 1e-6):
+    """Specs of a batch of uneven pairs: m, p ~ U[m_range], n ~ U[n_range],
+    r ~ U[r_range] (clipped so that k + oversample <= min(m, p, n)), seed per pair."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, npairs, 4242]))
+    specs = []
+    for i in range(npairs):
+        m = int(rng.integers(m_range[0], m_range[1] + 1))
+        p = int(rng.integers(m_range[0], m_range[1] + 1))
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        r = int(rng.integers(r_range[0], r_range[1] + 1))
+        r = min(r, min(m, p, n) - oversample)
+        specs.append(PairSpec(m=m, p=p, n=n, r=r, alpha="uniform", decay="exp10", sigma=sigma,
+                              k=r, oversample=oversample, q=q, seed=seed * 100003 + i))
+    return specs
