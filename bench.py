@@ -1,0 +1,298 @@
+"""Benchmark of the randomized GSV solve on GB300.
+
+One step = one full solve of the workload pair (both basis extractions with q
+power iterations, the projections, the FP64 compressed-pair GSVD), inputs
+resident in HBM.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload tf32_large|fp64_small|bf16_stress] [--prec tf32|fp32|...]
+
+Multi-GPU (torchrun, N > 1): every rank solves its own independent pairs (the
+units shard with no data-path collective): weak scaling, value = pairs of all
+ranks / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2404_09459_gb300.inputs import (PAIR_BF16_STRESS, PAIR_FP64_SMALL, PAIR_TF32_LARGE,  # noqa: E402
+                                           planted_pair, planted_pair_torch)
+
+WORKLOADS = {
+    "tf32_large": (PAIR_TF32_LARGE, "tf32"),
+    "fp64_small": (PAIR_FP64_SMALL, "fp64"),
+    "bf16_stress": (PAIR_BF16_STRESS, "bf16"),
+}
+METRIC = "pairs/sec and sketch TFLOP/s at GSV rel-err <=1e-4, chosen form vs plain FP64"
+DTYPE = {"tf32": "tf32", "tf32x3": "tf32x3", "bf16": "bf16", "fp32": "f32", "fp64": "f64"}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "fallback": True}
+
+
+def workload_desc(spec, prec):
+    return (f"single pair m={spec.m} p={spec.p} n={spec.n} rank={spec.r} k={spec.kk} "
+            f"oversample={spec.oversample} q={spec.q}, {prec} sketch/power/projection, FP64 small GSVD")
+
+
+def sketch_flops(spec):
+    """Algorithmic GEMM flops of one solve: per side (2q+2) passes of 2 M n l."""
+    return sum((2 * spec.q + 2) * 2.0 * M * spec.n * spec.l for M in (spec.m, spec.p))
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if len(r) > 5 + i and r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def cpu_baseline(spec, seconds=20.0):
+    """The FP64 oracle (NumPy/LAPACK, all host cores) on a bounded sample: whole pairs."""
+    from oracle import gsvd as O
+    G1, G2, _, _ = planted_pair(spec)
+    t0 = time.perf_counter()
+    done = 0
+    while True:
+        O.rand_gsvd(G1, G2, spec.kk, spec.oversample, spec.q, spec.seed)
+        done += 1
+        if time.perf_counter() - t0 > seconds or done >= 8:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "pairs/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{done} full solve(s) of the workload pair with the FP64 oracle (OpenBLAS, "
+                      f"{os.cpu_count()} threads)"}
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the oracle timed on host cores (rank 0 only)."""
+    spec, prec = WORKLOADS[args.workload]
+    if rank != 0:
+        return
+    from oracle import gsvd as O
+    G1, G2, _, _ = planted_pair(spec)
+    for _ in range(args.warmup):
+        O.rand_gsvd(G1, G2, spec.kk, spec.oversample, spec.q, spec.seed)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.rand_gsvd(G1, G2, spec.kk, spec.oversample, spec.q, spec.seed)
+    dt = time.perf_counter() - t0
+    v = args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "pairs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": workload_desc(spec, "fp64 oracle")},
+            "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{args.steps} full solves of the workload pair"},
+            "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="tf32_large", choices=sorted(WORKLOADS))
+    ap.add_argument("--prec", default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison leg")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import paper_2404_09459_gb300 as P
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    P._build.build()
+
+    spec, default_prec = WORKLOADS[args.workload]
+    prec = args.prec or default_prec
+    # each rank draws its own pair (independent units)
+    from dataclasses import replace
+    rspec = replace(spec, seed=spec.seed + 1000 * rank)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    G1, G2, _, _ = planted_pair_torch(rspec, device=f"cuda:{local}", dtype=dt)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")  # > 129 MB L2
+
+    ctx = P.Context(prec, device=local)
+    for _ in range(args.warmup):
+        ctx.solve(G1, G2, spec.kk, spec.oversample, spec.q, rspec.seed)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    st = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    l0 = ctx.launch_count()
+    barrier()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)  # L2 flush between timed steps (outside the events)
+            evs[i][0].record(st)
+            ctx.solve(G1, G2, spec.kk, spec.oversample, spec.q, rspec.seed)
+            evs[i][1].record(st)
+        barrier()
+    launches = (ctx.launch_count() - l0) // args.steps
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    if dist is not None:
+        t = torch.tensor([ms], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = world * args.steps / (ms / 1e3)
+    tflops = sketch_flops(spec) / (ms_step / 1e3) / 1e12
+
+    # per-stage device time of the same solve (CUDA events on the solve stream)
+    pctx = P.Context(prec, device=local, flags=P.FLAG_PROFILE)
+    pctx.solve(G1, G2, spec.kk, spec.oversample, spec.q, rspec.seed)
+    pctx.profile(reset=True)
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        pctx.solve(G1, G2, spec.kk, spec.oversample, spec.q, rspec.seed)
+    prof = pctx.profile()
+    pctx.close()
+    tot = sum(v[0] for v in prof.values())
+    stages = {k: {"ms_per_step": v[0] / args.steps, "calls_per_step": v[1] // args.steps,
+                  "share": (v[0] / tot if tot else None)} for k, v in prof.items()}
+
+    # roofline of the sketch product Y = G X (HBM-bound: G read once per launch)
+    pk = peaks()
+    sk_ms, sk_calls = prof["sketch"]
+    el = 8 if prec == "fp64" else 4
+    # algorithmic bytes per launch averaged over both sides: G + X + Y
+    bytes_per_launch = sum((M * spec.n + spec.l * spec.n + M * spec.l) * el for M in (spec.m, spec.p)) / 2
+    achieved = bytes_per_launch / (sk_ms / sk_calls / 1e3) / 1e9 if sk_calls else None
+    roof = {"kernel": "sketch product Y = G X", "bound": "hbm", "achieved": achieved,
+            "peak": pk.get("hbm_gbs"), "unit": "GB/s",
+            "frac": (achieved / pk["hbm_gbs"]) if achieved else None, "traffic": None,
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if not pk.get("fallback") else "fallback"}
+
+    # end to end through the public API with host (pinned) buffers
+    h1 = torch.empty(G1.shape, dtype=dt, pin_memory=True)
+    h2 = torch.empty(G2.shape, dtype=dt, pin_memory=True)
+    h1.copy_(G1)
+    h2.copy_(G2)
+    n1, n2 = h1.numpy(), h2.numpy()
+    ectx = P.Context(prec, device=local)
+    ectx.solve(n1, n2, spec.kk, spec.oversample, spec.q, rspec.seed)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        out = ectx.solve(n1, n2, spec.kk, spec.oversample, spec.q, rspec.seed)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    ectx.close()
+    e2e = {"value": world * args.steps / e2e_s, "unit": "pairs/s",
+           "h2d_bytes_per_step": int((spec.m + spec.p) * spec.n * el),
+           "d2h_bytes_per_step": int(2 * spec.kk * 8 + 2 * 8)}
+
+    # plain FP64 GPU path on the same pair (the comparison the metric names)
+    fp64 = None
+    if not args.no_fp64 and prec != "fp64":
+        g1d, g2d = G1.double(), G2.double()
+        fctx = P.Context("fp64", device=local)
+        fctx.solve(g1d, g2d, spec.kk, spec.oversample, spec.q, rspec.seed)
+        torch.cuda.synchronize()
+        reps = 2
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            fctx.solve(g1d, g2d, spec.kk, spec.oversample, spec.q, rspec.seed)
+        e1.record(st)
+        torch.cuda.synchronize()
+        fms = e0.elapsed_time(e1) / reps
+        fctx.close()
+        del g1d, g2d
+        fp64 = {"value": 1e3 / fms, "unit": "pairs/s", "ms_per_step": fms, "speedup_of_chosen_form": (1e3 / ms_step) / (1e3 / fms)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(spec)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": DTYPE.get(prec, prec), "data": "synthetic",
+                "config": {"workload": workload_desc(spec, prec), "l2": "flushed between timed steps (256 MiB write)",
+                           "parallelism": f"independent pairs, {world} rank(s)"},
+                "sketch_tflops": tflops, "roofline": roof, "stages": stages, "fp64_plain": fp64,
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,177 @@
+/*
+ * gsvd_rand.h — C ABI of the GB300 randomized generalized-singular-value library.
+ *
+ * Method: Xu, Shen, Li, Gao, Li, "Randomized algorithms for GSVs" (arXiv:2404.09459).
+ * For a matrix pair {G1 (m x n), G2 (p x n)} (Section 1, eq. (gsvd1):
+ * G1 = U Sigma1 R, G2 = V Sigma2 R, alpha_i^2 + beta_i^2 = 1) the library
+ *   1. extracts orthonormal bases Q1, Q2 of the column spaces of G1, G2 with a
+ *      Gaussian sketch Y = G Omega (Theorem 3: Omega has k + p columns) and q
+ *      power (subspace) iterations, re-orthonormalising with shifted CholeskyQR2;
+ *   2. projects B_s = Q_s^T G_s (Algorithm 2, the compressed pair);
+ *   3. computes the GSVs of the compressed pair (Algorithm 2; the reduced QR of
+ *      the stack is taken rank-revealing, truncated to k pairs) in FP64;
+ *   4. evaluates the comparative quantities of Section 1 (angular distance,
+ *      relative significance, generalized fractions, generalized entropy).
+ * Every step runs in this library's own CUDA kernels (sm_103a).
+ *
+ * Conventions shared by all entry points
+ *   - Matrices are row-major with a leading dimension in ELEMENTS (ld >= cols).
+ *   - Pointers may be device pointers or host pointers; the library detects
+ *     which with cudaPointerGetAttributes.  Host inputs are copied to device
+ *     workspace inside the call; host outputs are written after a stream sync.
+ *   - Inputs are read-only and owned by the caller.  Outputs are caller-owned.
+ *   - The library owns its device workspace, allocated on first use and grown
+ *     on demand (cudaMalloc); it is freed by gsvd_rand_destroy.
+ *   - Work is enqueued on cfg->stream.  gsvd_rand_solve and gsvd_rand_metrics
+ *     synchronise that stream before returning so that they can report a
+ *     status (breakdown, non-finite input) read back from the device.
+ *   - Return value: GSVD_RAND_OK (0) or a negative GSVD_RAND_ERR_* code;
+ *     gsvd_rand_last_error() gives a one-line message.  Nothing traps the GPU:
+ *     device-side problems are reported through status words.
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef GSVD_RAND_H
+#define GSVD_RAND_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GSVD_RAND_OK 0
+#define GSVD_RAND_ERR_ARG (-1)         /* bad shape, pointer, or parameter */
+#define GSVD_RAND_ERR_OOM (-2)         /* device allocation failed */
+#define GSVD_RAND_ERR_CUDA (-3)        /* a CUDA runtime call failed */
+#define GSVD_RAND_ERR_NONFINITE (-4)   /* NaN/Inf in the input or an intermediate */
+#define GSVD_RAND_ERR_BREAKDOWN (-5)   /* Cholesky failed even after the shift (e.g. G = 0) */
+#define GSVD_RAND_ERR_TOL_MISS (-6)    /* adaptive basis reached its column cap above tol */
+#define GSVD_RAND_ERR_TIMEOUT (-7)     /* a bounded device-side wait ran out */
+#define GSVD_RAND_ERR_UNSUPPORTED (-8) /* option not built / not available on this device */
+
+/* Arithmetic of the sketch, power and projection products.
+ *   FP64   : G is double; all products in FP64 (the plain path).
+ *   TF32   : G is float; products on tensor cores with TF32 inputs and FP32
+ *            accumulation; CholeskyQR2 in FP32 data with an FP64-reduced Gram;
+ *            small GSVD in FP64.
+ *   TF32X3 : as TF32, with each operand split hi + lo and three tensor products
+ *            (hi*hi + hi*lo + lo*hi), about FP32 accuracy.
+ *   BF16   : G is float; products with BF16 inputs and FP32 accumulation.
+ *   FP32   : G is float; products with FP32 CUDA-core FMAs (no tensor cores).  */
+typedef enum {
+  GSVD_RAND_FP64 = 0,
+  GSVD_RAND_TF32 = 1,
+  GSVD_RAND_BF16 = 2,
+  GSVD_RAND_TF32X3 = 3,
+  GSVD_RAND_FP32 = 4
+} gsvd_rand_prec;
+
+/* Philox stream ids (fourth counter word) of the Gaussian test matrices. */
+#define GSVD_RAND_STREAM_FIXED 0u          /* the n x (k+p) Omega of the fixed-rank solve */
+#define GSVD_RAND_STREAM_ADAPTIVE 0x10000u /* + block index i: Omega_i of Algorithm 1 */
+#define GSVD_RAND_STREAM_PROBE 0x20000u    /* the 16-column probe sketch */
+
+typedef struct gsvd_rand_ctx *gsvd_rand_t;
+
+typedef struct {
+  int device;        /* CUDA device ordinal the context is bound to */
+  void *stream;      /* cudaStream_t to enqueue on; NULL = the legacy default stream */
+  int prec;          /* gsvd_rand_prec */
+  int adaptive;      /* 0: fixed rank k + oversample (Theorem 3); reserved for Algorithm 1 */
+  int block_b;       /* Algorithm 1 block size b (paper: 100) */
+  double tol;        /* Algorithm 1 relative residual tolerance */
+  int use_learned;   /* reserved: learned (k, q) proposal */
+  const char *mlp_path; /* reserved */
+  int flags;         /* GSVD_RAND_FLAG_* */
+} gsvd_rand_config;
+
+/* flags */
+#define GSVD_RAND_FLAG_CHOL_FP64 1 /* mixed precisions: run the CholeskyQR factorisations in FP64 */
+#define GSVD_RAND_FLAG_PROFILE 2   /* time each stage with CUDA events on the solve stream */
+
+/* Stages timed under GSVD_RAND_FLAG_PROFILE. */
+#define GSVD_RAND_STAGE_SKETCH 0 /* Y = G X products (sketch and power steps) */
+#define GSVD_RAND_STAGE_GTQ 1    /* Z = G^T Q products incl. the projection B = Q^T G */
+#define GSVD_RAND_STAGE_ORTH 2   /* shifted CholeskyQR2 (Gram, Cholesky, triangular apply) */
+#define GSVD_RAND_STAGE_SMALL 3  /* compressed-pair GSVD (FP64), all of it */
+#define GSVD_RAND_STAGE_SMALL_GRAM 4   /* ... of which K = S S^T */
+#define GSVD_RAND_STAGE_SMALL_JACOBI 5 /* ... the FP32 Jacobi eigensolve of K */
+#define GSVD_RAND_STAGE_SMALL_REFINE 6 /* ... the FP64 eigenvector refinement of K */
+#define GSVD_RAND_STAGE_SMALL_CS 7     /* ... the CS step (C1, C2 and their eigensolve) */
+#define GSVD_RAND_NUM_STAGES 8
+
+/* Fill *cfg with defaults: device 0, default stream, TF32, fixed rank, b = 100, tol = 1e-4. */
+int gsvd_rand_config_init(gsvd_rand_config *cfg);
+
+/* Create a context on cfg->device.  *out receives the handle.
+ * Errors: ARG (NULL pointers, bad prec), CUDA (device cannot be set). */
+int gsvd_rand_create(gsvd_rand_t *out, const gsvd_rand_config *cfg);
+
+/* Release the context and its workspace.  NULL is accepted. */
+int gsvd_rand_destroy(gsvd_rand_t h);
+
+/* Message of the last failing call on this context ("" if none). Owned by the context. */
+const char *gsvd_rand_last_error(gsvd_rand_t h);
+
+/* Randomized GSVs of {G1, G2} (Algorithm 2 with the fixed-rank basis of
+ * Theorem 3 and q power iterations).
+ *   G1, ld1 : m x n matrix, element type double (FP64) or float (other precs)
+ *   G2, ld2 : p x n matrix, same element type
+ *   k       : number of GSV pairs returned, 1 <= k
+ *   oversample : extra sketch columns (the paper's p); l = k + oversample must
+ *             satisfy l <= min(m, p, n) and l <= 256
+ *   q       : power iterations, 0 <= q <= 16
+ *   seed    : Philox key; side s in {0, 1} uses counter words (t, 0, s, 0)
+ *   alpha   : k doubles, non-increasing (eq. (ab)); beta: k doubles, non-decreasing
+ *   r_out   : may be NULL; receives k
+ *   resid_out : may be NULL; receives 2 doubles, the relative residual
+ *             ||(I - Q_s Q_s^T) G_s||_F / ||G_s||_F of each side in the
+ *             cumulated form sqrt(||G_s||_F^2 - ||Q_s^T G_s||_F^2) (Section 2)
+ * Errors: ARG, OOM, CUDA, NONFINITE, BREAKDOWN.  Synchronises cfg->stream. */
+int gsvd_rand_solve(gsvd_rand_t h, const void *G1, int64_t m, int64_t ld1, const void *G2,
+                    int64_t p, int64_t ld2, int64_t n, int k, int oversample, int q,
+                    uint64_t seed, double *alpha, double *beta, int *r_out, double *resid_out);
+
+/* Comparative quantities of Section 1 for r GSV pairs (alpha non-increasing,
+ * beta non-decreasing):
+ *   theta[i] = atan2(alpha_i, beta_i) - pi/4      (antisymmetric angular distance)
+ *   rho[i]   = alpha_i / beta_i, +inf if beta_i = 0 (relative significance)
+ *   P1[i] = alpha_i^2 / sum alpha^2, P2[i] = beta_i^2 / sum beta^2
+ *   D[0], D[1] = -(1/log N) sum P log P, 0 log 0 = 0 (generalized entropy)
+ * pad_to_n = 0: N = r.  pad_to_n > r: pad to N = pad_to_n pairs as Algorithm 2
+ * does — pad_mode 0 appends (alpha, beta) = (0, 1), pad_mode 1 prepends (1, 0).
+ * theta, rho, P1, P2 hold N doubles; D holds 2.  Any output may be NULL.
+ * Errors: ARG (r < 1, N < 2, NULL alpha/beta).  Synchronises cfg->stream. */
+int gsvd_rand_metrics(gsvd_rand_t h, const double *alpha, const double *beta, int r,
+                      int pad_to_n, int pad_mode, double *theta, double *rho, double *P1,
+                      double *P2, double *D);
+
+/* The Gaussian test matrix the solver draws: out (n x l, row-major, ld = l)
+ * with out[i][j] from Philox4x32-10 (Salmon et al., SC'11) and Box-Muller:
+ *   e = i*l + j, t = e >> 1; counter (t, pair, side, stream), key (seed lo, seed hi);
+ *   words x0..x3: u1 = ((x0 >> 5) 2^26 + (x1 >> 6) + 0.5) 2^-53,
+ *                 u2 = ((x2 >> 5) 2^26 + (x3 >> 6)) 2^-53,
+ *   r = sqrt(-2 ln u1), a = 2 pi u2; even e -> r cos a, odd e -> r sin a.
+ * Computed in FP64.  Errors: ARG, OOM, CUDA. */
+int gsvd_rand_gaussian(gsvd_rand_t h, int64_t n, int64_t l, uint64_t seed, uint32_t pair,
+                       uint32_t side, uint32_t stream, double *out);
+
+/* The raw Philox4x32-10 words for counters (t, pair, side, stream), t = 0..count-1:
+ * out[4 t + w] = word w.  Errors: ARG, OOM, CUDA. */
+int gsvd_rand_philox(gsvd_rand_t h, uint64_t count, uint64_t seed, uint32_t pair, uint32_t side,
+                     uint32_t stream, uint32_t *out);
+
+/* Accumulated device time (ms, from CUDA events on the solve stream) and call
+ * count of one stage since creation or the last reset; only filled while the
+ * context has GSVD_RAND_FLAG_PROFILE.  Errors: ARG (bad stage). */
+int gsvd_rand_profile_get(gsvd_rand_t h, int stage, double *total_ms, int64_t *calls);
+int gsvd_rand_profile_reset(gsvd_rand_t h);
+
+/* Total number of CUDA kernels this library has launched in this process. */
+uint64_t gsvd_rand_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GSVD_RAND_H */

@@ -1,0 +1,234 @@
+"""GB300 randomized generalized singular values (arXiv:2404.09459).
+
+Thin ctypes binding over the C ABI of `libgsvdrand.so` (include/gsvd_rand.h):
+argument marshalling only; every step runs in the library's CUDA kernels.
+PyTorch, when present, only supplies device memory and the current stream.
+The library must be built first (`paper_2404_09459_gb300._build.build()`);
+nothing here falls back to a CPU implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from ._build import LIB
+
+__all__ = ["Context", "GsvdRandError", "load_library", "PREC", "LIB"]
+
+PREC = {"fp64": 0, "tf32": 1, "bf16": 2, "tf32x3": 3, "fp32": 4}
+ERRORS = {-1: "ARG", -2: "OOM", -3: "CUDA", -4: "NONFINITE", -5: "BREAKDOWN", -6: "TOL_MISS",
+          -7: "TIMEOUT", -8: "UNSUPPORTED"}
+FLAG_CHOL_FP64 = 1
+
+EXPORTS = ("gsvd_rand_config_init", "gsvd_rand_create", "gsvd_rand_destroy", "gsvd_rand_last_error",
+           "gsvd_rand_solve", "gsvd_rand_metrics", "gsvd_rand_gaussian", "gsvd_rand_philox",
+           "gsvd_rand_profile_get", "gsvd_rand_profile_reset", "gsvd_rand_launch_count")
+FLAG_PROFILE = 2
+STAGES = ("sketch", "gtq", "orth", "small", "small_gram", "small_jacobi", "small_refine", "small_cs")
+
+
+class GsvdRandError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"gsvd_rand error {code} ({ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+        self.name = ERRORS.get(code, "?")
+
+
+class _Config(C.Structure):
+    _fields_ = [("device", C.c_int), ("stream", C.c_void_p), ("prec", C.c_int), ("adaptive", C.c_int),
+                ("block_b", C.c_int), ("tol", C.c_double), ("use_learned", C.c_int),
+                ("mlp_path", C.c_char_p), ("flags", C.c_int)]
+
+
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Load libgsvdrand.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    path = path or LIB
+    if not os.path.exists(path):
+        raise ImportError(f"{path} not found: build it with paper_2404_09459_gb300._build.build()")
+    lib = C.CDLL(path)
+    vp, i64, i32, u64, u32 = C.c_void_p, C.c_int64, C.c_int, C.c_uint64, C.c_uint32
+    dp = C.POINTER(C.c_double)
+    lib.gsvd_rand_config_init.argtypes = [C.POINTER(_Config)]
+    lib.gsvd_rand_create.argtypes = [C.POINTER(vp), C.POINTER(_Config)]
+    lib.gsvd_rand_destroy.argtypes = [vp]
+    lib.gsvd_rand_last_error.argtypes = [vp]
+    lib.gsvd_rand_last_error.restype = C.c_char_p
+    lib.gsvd_rand_solve.argtypes = [vp, vp, i64, i64, vp, i64, i64, i64, i32, i32, i32, u64, vp, vp, vp, vp]
+    lib.gsvd_rand_metrics.argtypes = [vp, vp, vp, i32, i32, i32, vp, vp, vp, vp, vp]
+    lib.gsvd_rand_gaussian.argtypes = [vp, i64, i64, u64, u32, u32, u32, vp]
+    lib.gsvd_rand_philox.argtypes = [vp, u64, u64, u32, u32, u32, vp]
+    lib.gsvd_rand_profile_get.argtypes = [vp, i32, dp, C.POINTER(C.c_int64)]
+    lib.gsvd_rand_profile_reset.argtypes = [vp]
+    lib.gsvd_rand_launch_count.argtypes = []
+    lib.gsvd_rand_launch_count.restype = C.c_uint64
+    for name in EXPORTS:
+        if name not in ("gsvd_rand_last_error", "gsvd_rand_launch_count"):
+            getattr(lib, name).restype = C.c_int
+    if path == LIB:
+        _lib = lib
+    return lib
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _mat_ptr(x, want_dtype: str):
+    """(pointer, rows, cols, ld, on_device, keepalive) of a row-major matrix."""
+    if _is_torch(x):
+        import torch
+        dt = {"f64": torch.float64, "f32": torch.float32}[want_dtype]
+        if x.dtype != dt:
+            raise TypeError(f"expected {dt}, got {x.dtype}")
+        if x.dim() != 2 or x.stride(1) != 1:
+            raise ValueError("matrix must be 2-D with unit column stride (row-major)")
+        return x.data_ptr(), x.shape[0], x.shape[1], max(x.stride(0), x.shape[1]), x.is_cuda, x
+    import numpy as np
+    dt = {"f64": np.float64, "f32": np.float32}[want_dtype]
+    a = np.asarray(x)
+    if a.dtype != dt:
+        raise TypeError(f"expected {np.dtype(dt)}, got {a.dtype}")
+    if a.ndim != 2 or a.strides[1] != a.itemsize or a.strides[0] % a.itemsize:
+        raise ValueError("matrix must be 2-D row-major")
+    return a.ctypes.data, a.shape[0], a.shape[1], max(a.strides[0] // a.itemsize, a.shape[1]), False, a
+
+
+class Context:
+    """One library context (device, stream, precision).
+
+    prec: "fp64" | "tf32" | "tf32x3" | "bf16" | "fp32".  stream: a torch.cuda.Stream,
+    a raw cudaStream_t int, or None for torch's current stream (legacy default
+    stream without torch).
+    """
+
+    def __init__(self, prec: str = "tf32", device: int = 0, stream=None, flags: int = 0):
+        self.lib = load_library()
+        cfg = _Config()
+        self.lib.gsvd_rand_config_init(C.byref(cfg))
+        cfg.device = device
+        cfg.prec = PREC[prec]
+        cfg.flags = flags
+        if stream is None:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream(device)
+            except ImportError:
+                stream = None
+        if stream is not None and hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        cfg.stream = C.c_void_p(int(stream) if stream else 0)
+        self.prec = prec
+        self.device = device
+        self._stream = stream
+        h = C.c_void_p()
+        rc = self.lib.gsvd_rand_create(C.byref(h), C.byref(cfg))
+        if rc:
+            raise GsvdRandError(rc, "create failed")
+        self.h = h
+
+    # ------------------------------------------------------------------ util
+    def _check(self, rc):
+        if rc:
+            raise GsvdRandError(rc, self.lib.gsvd_rand_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gsvd_rand_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _out_vec(self, on_device: bool, n: int, dtype="f64"):
+        if on_device:
+            import torch
+            dt = {"f64": torch.float64, "u32": torch.int32}[dtype]
+            t = torch.empty(n, dtype=dt, device=f"cuda:{self.device}")
+            return t, t.data_ptr()
+        import numpy as np
+        a = np.empty(n, dtype={"f64": np.float64, "u32": np.uint32}[dtype])
+        return a, a.ctypes.data
+
+    # ------------------------------------------------------------------ API
+    def solve(self, G1, G2, k: int, oversample: int = 10, q: int = 1, seed: int = 0):
+        """Randomized GSVs of {G1, G2}: dict(alpha, beta, r, resid).
+
+        Outputs live where G1 lives (CUDA tensors for CUDA inputs, numpy otherwise)."""
+        want = "f64" if self.prec == "fp64" else "f32"
+        p1, m, n1, ld1, dev1, k1 = _mat_ptr(G1, want)
+        p2, p, n2, ld2, dev2, k2 = _mat_ptr(G2, want)
+        if n1 != n2:
+            raise ValueError("G1 and G2 must have the same number of columns")
+        alpha, pa = self._out_vec(dev1, k)
+        beta, pb = self._out_vec(dev1, k)
+        r = C.c_int(0)
+        resid = (C.c_double * 2)()
+        rc = self.lib.gsvd_rand_solve(self.h, p1, m, ld1, p2, p, ld2, n1, k, oversample, q, seed, pa, pb,
+                                      C.addressof(r), C.addressof(resid))
+        self._check(rc)
+        return dict(alpha=alpha, beta=beta, r=r.value, resid=(resid[0], resid[1]))
+
+    def metrics(self, alpha, beta, pad_to_n: int = 0, pad_mode: int = 0):
+        """Section 1 quantities: dict(theta, rho, P1, P2, D1, D2)."""
+        import numpy as np
+        on_dev = _is_torch(alpha) and alpha.is_cuda
+        if _is_torch(alpha):
+            pa, pb, r = alpha.data_ptr(), beta.data_ptr(), alpha.numel()
+            keep = (alpha, beta)
+        else:
+            a = np.ascontiguousarray(alpha, dtype=np.float64)
+            b = np.ascontiguousarray(beta, dtype=np.float64)
+            pa, pb, r = a.ctypes.data, b.ctypes.data, a.size
+            keep = (a, b)
+        N = max(pad_to_n, r)
+        outs = [self._out_vec(on_dev, N) for _ in range(4)]
+        D, pD = self._out_vec(on_dev, 2)
+        rc = self.lib.gsvd_rand_metrics(self.h, pa, pb, r, pad_to_n, pad_mode, *[o[1] for o in outs], pD)
+        del keep
+        self._check(rc)
+        return dict(theta=outs[0][0], rho=outs[1][0], P1=outs[2][0], P2=outs[3][0], D1=D[0], D2=D[1])
+
+    def gaussian(self, n: int, l: int, seed: int, pair: int = 0, side: int = 0, stream: int = 0,
+                 device_out: bool = False):
+        """The n x l Gaussian test matrix (FP64) the solver draws."""
+        out, ptr = self._out_vec(device_out, n * l)
+        self._check(self.lib.gsvd_rand_gaussian(self.h, n, l, seed, pair, side, stream, ptr))
+        return out.reshape(n, l)
+
+    def profile(self, reset: bool = False):
+        """Per-stage device time (ms) and call counts recorded under FLAG_PROFILE."""
+        out = {}
+        for i, name in enumerate(STAGES):
+            ms = C.c_double()
+            n = C.c_int64()
+            self._check(self.lib.gsvd_rand_profile_get(self.h, i, C.byref(ms), C.byref(n)))
+            out[name] = (ms.value, n.value)
+        if reset:
+            self.lib.gsvd_rand_profile_reset(self.h)
+        return out
+
+    def launch_count(self) -> int:
+        """Kernels launched by the library so far in this process."""
+        return int(self.lib.gsvd_rand_launch_count())
+
+    def philox(self, count: int, seed: int, pair: int = 0, side: int = 0, stream: int = 0):
+        """Raw Philox4x32-10 words, shape (count, 4) uint32 (host)."""
+        out, ptr = self._out_vec(False, 4 * count, "u32")
+        self._check(self.lib.gsvd_rand_philox(self.h, count, seed, pair, side, stream, ptr))
+        return out.reshape(count, 4)

@@ -1,0 +1,677 @@
+// C ABI and host orchestration of the randomized GSV solve.
+//
+// Pipeline per side s (G_s is M x n, l = k + oversample):
+//   Omega_s (Philox, Theorem 3)  ->  Y = G Omega            (sketch)
+//   Q = orth(Y)                                              (shifted CholeskyQR2)
+//   q times: Z = G^T Q, Zh = orth(Z), Y = G Zh, Q = orth(Y)  (power / subspace iteration)
+//   B_s = Q^T G (rows of the stack S), ||G||^2 - ||B||^2    (projection, cumulated residual)
+// then the compressed-pair GSVD in FP64 (Algorithm 2, rank-revealing reading):
+//   K = S S^T, leading-k eigenvectors Zr (FP32 Jacobi + FP64 Ogita-Aishima),
+//   C1 = Z1^T Z1, C2 = Z2^T Z2, alpha^2 / beta^2 from the eigenvectors of C1.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/gsvd_rand.h"
+#include "kernels.h"
+#include "tc.h"
+
+using namespace gsvdr;
+
+struct gsvd_rand_ctx {
+  gsvd_rand_config cfg{};
+  cudaStream_t stream = nullptr;
+  std::string err;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  DevStatus* st_host = nullptr;  // pinned
+  double* res_host = nullptr;    // pinned, 4 doubles
+  int tc_ok = -1;                // tensor-core path usable on this device
+  // optional per-stage CUDA-event timing (GSVD_RAND_FLAG_PROFILE)
+  struct Rec {
+    int stage;
+    cudaEvent_t a, b;
+  };
+  std::vector<cudaEvent_t> evpool;
+  size_t evused = 0;
+  std::vector<Rec> recs;
+  double prof_ms[8] = {};
+  int64_t prof_calls[8] = {};
+};
+
+namespace gsvdr {
+std::atomic<uint64_t> g_launch_count{0};
+}
+
+namespace {
+
+int fail(gsvd_rand_ctx* h, int code, const char* fmt, ...) {
+  if (h) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    h->err = buf;
+  }
+  return code;
+}
+
+#define CU(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t _e = (call);                                                            \
+    if (_e != cudaSuccess)                                                              \
+      return fail(h, _e == cudaErrorMemoryAllocation ? GSVD_RAND_ERR_OOM : GSVD_RAND_ERR_CUDA, \
+                  "%s failed: %s (%s:%d)", #call, cudaGetErrorString(_e), __FILE__, __LINE__); \
+  } while (0)
+
+// Stage timing: events recorded on the solve stream around each stage call.
+cudaEvent_t prof_event(gsvd_rand_ctx* h) {
+  if (h->evused == h->evpool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    h->evpool.push_back(e);
+  }
+  return h->evpool[h->evused++];
+}
+
+struct ProfScope {
+  gsvd_rand_ctx* h;
+  int stage;
+  cudaEvent_t a = nullptr;
+  ProfScope(gsvd_rand_ctx* h_, int stage_) : h(h_), stage(stage_) {
+    if (h->cfg.flags & GSVD_RAND_FLAG_PROFILE) {
+      a = prof_event(h);
+      if (a) cudaEventRecord(a, h->stream);
+    }
+  }
+  ~ProfScope() {
+    if (a) {
+      cudaEvent_t b = prof_event(h);
+      if (b) {
+        cudaEventRecord(b, h->stream);
+        h->recs.push_back({stage, a, b});
+      }
+    }
+  }
+};
+
+void prof_collect(gsvd_rand_ctx* h) {
+  for (auto& r : h->recs) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      h->prof_ms[r.stage] += ms;
+      h->prof_calls[r.stage] += 1;
+    }
+  }
+  h->recs.clear();
+  h->evused = 0;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Bump allocator over the context workspace (256-byte aligned slices).
+struct Bump {
+  size_t off = 0;
+  char* base = nullptr;
+  template <typename T>
+  T* take(int64_t elems) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += (size_t)std::max<int64_t>(elems, 1) * sizeof(T);
+    return p;
+  }
+};
+
+int ensure_ws(gsvd_rand_ctx* h, size_t bytes) {
+  if (bytes <= h->ws_bytes) return GSVD_RAND_OK;
+  if (h->ws) {
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->ws);
+    h->ws = nullptr;
+    h->ws_bytes = 0;
+  }
+  size_t want = bytes + bytes / 8;
+  cudaError_t e = cudaMalloc(&h->ws, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, GSVD_RAND_ERR_OOM, "workspace allocation of %zu bytes failed", want);
+  }
+  h->ws_bytes = want;
+  return GSVD_RAND_OK;
+}
+
+// Per-side buffers.
+template <typename T>
+struct SideBufs {
+  T* Xt;          // lx x ldx   (Omega^T, later Zh^T), K-major for the sketch product
+  T* Y;           // M x lp
+  T* Q;           // M x lp
+  T* tmp;         // max(M, n) x lp   (CholeskyQR2 intermediate)
+  T* Z;           // n x lp
+  T* part;        // splits x n x lp  (split-K partials of G^T Q)
+  double* gpart;  // Gram partials
+  double* W;      // l x l
+  void* R;        // l x l (TC)
+  void* rinv;     // l (TC)
+  double* gnorm;  // sketch-CTA partial sums of G^2
+  double* bnorm;  // reduce-block partial sums of B^2
+};
+
+struct Plan {
+  int64_t M[2];
+  int64_t n, ldx, lp, lx, ldn;
+  int l, L;
+  int64_t part_elems, gpart_elems;
+  int gn_ctas[2], bn_blocks;
+};
+
+template <typename T>
+int64_t part_cap(const Plan& pl) {
+  return pl.part_elems;
+}
+
+template <typename T, typename TC>
+struct Solver {
+  gsvd_rand_ctx* h;
+  cudaStream_t st;
+  DevStatus* st_dev;
+  int prec;
+  bool use_tc;
+
+  int orth(SideBufs<T>& b, const T* Yin, int64_t M, int l, int64_t lp, T* out, int64_t ldo,
+           int transpose_out, int stage) {
+    ProfScope ps(h, GSVD_RAND_STAGE_ORTH);
+    // pass 1: shifted Cholesky of the Gram (Fukaya et al. 2020 shift scaled to the
+    // Gram's accumulation precision), pass 2: plain CholeskyQR on the result.
+    int64_t rpc;
+    int chunks = gram_chunks(M, l, &rpc);
+    const double u = std::is_same<T, double>::value ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
+    const double shift_coef = 11.0 * ((double)rpc + l + 1) * u;
+    // pivots below ~8 rpc u relative to their own column are below the Gram's resolution
+    const double tau = 8.0 * (double)std::max<int64_t>(rpc, apply_rows_per_cta(l)) * u;
+    CU(launch_gram_partial<T>(Yin, lp, M, l, b.gpart, chunks, rpc, st));
+    CU(launch_gram_reduce(b.gpart, chunks, l, b.W, st));
+    CU(launch_chol_shift<TC>(b.W, l, shift_coef, tau, (TC*)b.R, (TC*)b.rinv, st_dev, stage, st));
+    CU((launch_apply_rinv<T, TC>(Yin, lp, M, l, (const TC*)b.R, (const TC*)b.rinv, b.tmp, lp, 0, b.gpart,
+                                st)));
+    CU(launch_gram_reduce(b.gpart, apply_ctas(M, l), l, b.W, st));
+    CU(launch_chol_shift<TC>(b.W, l, 0.0, tau, (TC*)b.R, (TC*)b.rinv, st_dev, stage + 1, st));
+    CU((launch_apply_rinv<T, TC>(b.tmp, lp, M, l, (const TC*)b.R, (const TC*)b.rinv, out, ldo,
+                                transpose_out, nullptr, st)));
+    return GSVD_RAND_OK;
+  }
+
+  int gx(const T* G, int64_t ldg, int64_t M, const Plan& pl, SideBufs<T>& b, double* gnorm) {
+    ProfScope ps(h, GSVD_RAND_STAGE_SKETCH);
+    if constexpr (std::is_same<T, float>::value) {
+      if (use_tc) {
+        CU(tc_gemm_gx(prec, G, ldg, M, pl.n, b.Xt, pl.ldx, pl.l, b.Y, pl.lp, gnorm, st));
+        return GSVD_RAND_OK;
+      }
+    }
+    CU(launch_gemm_gx_simt<T>(G, ldg, M, pl.n, b.Xt, pl.ldx, pl.l, b.Y, pl.lp, gnorm, st));
+    return GSVD_RAND_OK;
+  }
+
+  int gtq(const T* G, int64_t ldg, int64_t M, const Plan& pl, SideBufs<T>& b, T* out, int64_t ldo,
+          int transpose_out, double* sq) {
+    ProfScope ps(h, GSVD_RAND_STAGE_GTQ);
+    int splits = gemm_gtq_splits(M, pl.n, pl.l, pl.part_elems);
+    bool done = false;
+    if constexpr (std::is_same<T, float>::value) {
+      if (use_tc) {
+        int s2 = 0;
+        CU(tc_gemm_gtq(prec, G, ldg, M, pl.n, b.Q, pl.lp, pl.l, b.part, pl.lp, &s2, pl.part_elems, st));
+        splits = s2;
+        done = true;
+      }
+    }
+    if (!done) CU((launch_gemm_gtq_simt<T, T>(G, ldg, M, pl.n, b.Q, pl.lp, pl.l, b.part, pl.lp, splits, st)));
+    int blocks = 0;
+    CU((launch_reduce_splits<T, T>(b.part, splits, pl.n, pl.l, pl.lp, out, ldo, transpose_out, sq, &blocks,
+                                   st)));
+    return GSVD_RAND_OK;
+  }
+
+  int side(const T* G, int64_t ldg, int s, const Plan& pl, SideBufs<T>& b, int q, uint64_t seed,
+           T* Srows) {
+    const int64_t M = pl.M[s];
+    CU(launch_gaussian_kmajor<T>(b.Xt, pl.ldx, pl.n, pl.l, (int)pl.lx, seed, 0u, (uint32_t)s,
+                                 GSVD_RAND_STREAM_FIXED, st));
+    int rc;
+    if ((rc = gx(G, ldg, M, pl, b, b.gnorm))) return rc;
+    if ((rc = orth(b, b.Y, M, pl.l, pl.lp, b.Q, pl.lp, 0, 10 * s + 1))) return rc;
+    for (int it = 0; it < q; ++it) {
+      if ((rc = gtq(G, ldg, M, pl, b, b.Z, pl.lp, 0, nullptr))) return rc;
+      if ((rc = orth(b, b.Z, pl.n, pl.l, pl.lp, b.Xt, pl.ldx, 1, 10 * s + 3))) return rc;
+      if ((rc = gx(G, ldg, M, pl, b, nullptr))) return rc;
+      if ((rc = orth(b, b.Y, M, pl.l, pl.lp, b.Q, pl.lp, 0, 10 * s + 5))) return rc;
+    }
+    // projection B = Q^T G written as l rows of S
+    if ((rc = gtq(G, ldg, M, pl, b, Srows, pl.ldn, 1, b.bnorm))) return rc;
+    return GSVD_RAND_OK;
+  }
+};
+
+template <typename T>
+size_t side_bytes(const Plan& pl, int s, bool tc) {
+  Bump bp;
+  int64_t M = pl.M[s];
+  bp.take<T>(pl.lx * pl.ldx);
+  bp.take<T>(M * pl.lp);
+  bp.take<T>(M * pl.lp);
+  bp.take<T>(std::max(M, pl.n) * pl.lp);
+  bp.take<T>(pl.n * pl.lp);
+  bp.take<T>(pl.part_elems);
+  bp.take<double>(pl.gpart_elems);
+  bp.take<double>((int64_t)pl.l * pl.l);
+  bp.take<double>((int64_t)pl.l * pl.l);
+  bp.take<double>(pl.l);
+  bp.take<double>(std::max<int64_t>(gemm_gx_simt_ctas(M), tc ? tc_gx_ctas(M) : 1) + 8);
+  bp.take<double>(cdiv(pl.n * pl.l, 256) + 8);
+  (void)tc;
+  return bp.off + 256;
+}
+
+template <typename T>
+SideBufs<T> side_take(Bump& bp, const Plan& pl, int s, bool tc) {
+  SideBufs<T> b;
+  int64_t M = pl.M[s];
+  b.Xt = bp.take<T>(pl.lx * pl.ldx);
+  b.Y = bp.take<T>(M * pl.lp);
+  b.Q = bp.take<T>(M * pl.lp);
+  b.tmp = bp.take<T>(std::max(M, pl.n) * pl.lp);
+  b.Z = bp.take<T>(pl.n * pl.lp);
+  b.part = bp.take<T>(pl.part_elems);
+  b.gpart = bp.take<double>(pl.gpart_elems);
+  b.W = bp.take<double>((int64_t)pl.l * pl.l);
+  b.R = bp.take<double>((int64_t)pl.l * pl.l);
+  b.rinv = bp.take<double>(pl.l);
+  b.gnorm = bp.take<double>(std::max<int64_t>(gemm_gx_simt_ctas(M), tc ? tc_gx_ctas(M) : 1) + 8);
+  b.bnorm = bp.take<double>(cdiv(pl.n * pl.l, 256) + 8);
+  return b;
+}
+
+// Small-GSVD workspace (FP64).
+struct SmallBufs {
+  double* K;      // L x L
+  double* X;      // L x L eigenvectors
+  double* lam;    // L
+  double* Zr;     // L x r
+  int* order;     // L
+  double* C1;     // r x r
+  double* C2;     // r x r
+  double* Wv;     // r x r
+  double* mu;     // r
+  double* work;   // refinement + split-K scratch
+  int64_t work_elems;
+  float* jscratch;
+  double* alpha;  // r
+  double* beta;   // r
+  double* resid;  // 2
+};
+
+int64_t small_work_elems(int L, int64_t n) {
+  int64_t a = 5ll * L * L + 16ll * L * L;            // OA on K + split-K scratch
+  int64_t b = (int64_t)L * L * std::max<int64_t>(1, std::min<int64_t>(cdiv(n, 32), 320));
+  return std::max(a, b) + 1024;
+}
+
+SmallBufs small_take(Bump& bp, int L, int r, int64_t n) {
+  SmallBufs s;
+  s.K = bp.take<double>((int64_t)L * L);
+  s.X = bp.take<double>((int64_t)L * L);
+  s.lam = bp.take<double>(L);
+  s.Zr = bp.take<double>((int64_t)L * r);
+  s.order = bp.take<int>(L);
+  s.C1 = bp.take<double>((int64_t)r * r);
+  s.C2 = bp.take<double>((int64_t)r * r);
+  s.Wv = bp.take<double>((int64_t)r * r);
+  s.mu = bp.take<double>(r);
+  s.work_elems = small_work_elems(L, n);
+  s.work = bp.take<double>(s.work_elems);
+  s.jscratch = bp.take<float>(jacobi_scratch_floats(L));
+  s.alpha = bp.take<double>(r);
+  s.beta = bp.take<double>(r);
+  s.resid = bp.take<double>(2);
+  return s;
+}
+
+constexpr int OA_ITERS = 3;
+constexpr int JACOBI_SWEEPS = 16;
+
+template <typename T>
+int small_gsvd(gsvd_rand_ctx* h, cudaStream_t st, DevStatus* st_dev, const T* S, int64_t ldn, int l1,
+               int L, int64_t n, int r, SmallBufs& sb) {
+  // K = S S^T in FP64
+  {
+    ProfScope ps(h, GSVD_RAND_STAGE_SMALL_GRAM);
+    CU((launch_dgemm_small<T, T>(L, L, (int)n, S, ldn, 0, S, ldn, 1, sb.K, L, 1.0, 0.0, sb.work,
+                                 sb.work_elems, st)));
+  }
+  {
+    ProfScope ps(h, GSVD_RAND_STAGE_SMALL_JACOBI);
+    CU(launch_jacobi_f32(sb.K, L, sb.X, sb.lam, sb.jscratch, JACOBI_SWEEPS, st_dev, st));
+  }
+  {
+    ProfScope ps(h, GSVD_RAND_STAGE_SMALL_REFINE);
+    for (int it = 0; it < OA_ITERS; ++it) CU(launch_oa_refine(sb.K, L, sb.X, sb.lam, sb.work, sb.work_elems, st));
+  }
+  ProfScope ps_cs(h, GSVD_RAND_STAGE_SMALL_CS);
+  CU(launch_select_topr(sb.X, sb.lam, L, r, sb.Zr, sb.order, st));
+  // C1 = Z1^T Z1, C2 = Z2^T Z2
+  CU((launch_dgemm_small<double, double>(r, r, l1, sb.Zr, r, 1, sb.Zr, r, 0, sb.C1, r, 1.0, 0.0, sb.work,
+                                         sb.work_elems, st)));
+  CU((launch_dgemm_small<double, double>(r, r, L - l1, sb.Zr + (int64_t)l1 * r, r, 1,
+                                         sb.Zr + (int64_t)l1 * r, r, 0, sb.C2, r, 1.0, 0.0, sb.work,
+                                         sb.work_elems, st)));
+  CU(launch_jacobi_f32(sb.C1, r, sb.Wv, sb.mu, sb.jscratch, JACOBI_SWEEPS, st_dev, st));
+  for (int it = 0; it < OA_ITERS; ++it) CU(launch_oa_refine(sb.C1, r, sb.Wv, sb.mu, sb.work, sb.work_elems, st));
+  CU(launch_cs_finalize(sb.Wv, sb.C1, sb.C2, r, sb.alpha, sb.beta, st));
+  return GSVD_RAND_OK;
+}
+
+template <typename T, typename TC>
+int solve_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, const void* G2v, int64_t p,
+            int64_t ld2, int64_t n, int k, int os, int q, uint64_t seed, double* alpha, double* beta,
+            int* r_out, double* resid_out) {
+  cudaStream_t st = h->stream;
+  const int prec = h->cfg.prec;
+  const bool use_tc = prec == GSVD_RAND_TF32 || prec == GSVD_RAND_BF16 || prec == GSVD_RAND_TF32X3;
+  if (use_tc && !h->tc_ok) return fail(h, GSVD_RAND_ERR_UNSUPPORTED, "tensor-core path unavailable on this device");
+  Plan pl;
+  pl.M[0] = m;
+  pl.M[1] = p;
+  pl.n = n;
+  pl.l = k + os;
+  pl.L = 2 * pl.l;
+  pl.lp = round_up(pl.l, 4);
+  pl.lx = round_up(pl.l, 16);
+  pl.ldx = round_up(n, 32);
+  pl.ldn = round_up(n, 4);
+  int64_t maxM = std::max(m, p);
+  pl.part_elems = std::max<int64_t>((int64_t)gemm_gtq_splits(maxM, n, pl.l, 1ll << 62) * n * pl.lp,
+                                    use_tc ? tc_gtq_part_elems(maxM, n, pl.l) : 0);
+  pl.part_elems = std::min<int64_t>(pl.part_elems, std::max<int64_t>(16ll << 20, n * pl.lp));
+  int64_t rpc;
+  int gch = gram_chunks(std::max(maxM, n), pl.l, &rpc);
+  int ach = apply_ctas(std::max(maxM, n), pl.l);
+  pl.gpart_elems = (int64_t)std::max(gch, ach) * pl.l * pl.l;
+
+  // host inputs are staged into the workspace
+  bool d1 = is_device_ptr(G1v), d2 = is_device_ptr(G2v);
+  Bump sizer;
+  sizer.take<DevStatus>(1);
+  if (!d1) sizer.take<T>(m * n);
+  if (!d2) sizer.take<T>(p * n);
+  sizer.take<T>((int64_t)pl.L * pl.ldn);
+  size_t b0 = sizer.off;
+  size_t need = b0 + side_bytes<T>(pl, 0, use_tc) + side_bytes<T>(pl, 1, use_tc) + 4096;
+  Bump sb_sizer;
+  small_take(sb_sizer, pl.L, k, n);
+  need += sb_sizer.off + 4096;
+  int rc = ensure_ws(h, need);
+  if (rc) return rc;
+
+  Bump bp;
+  bp.base = h->ws;
+  DevStatus* st_dev = bp.take<DevStatus>(1);
+  const T* G1 = (const T*)G1v;
+  const T* G2 = (const T*)G2v;
+  int64_t l1d = ld1, l2d = ld2;
+  if (!d1) {
+    T* g = bp.take<T>(m * n);
+    CU(cudaMemcpy2DAsync(g, n * sizeof(T), G1v, ld1 * sizeof(T), n * sizeof(T), m, cudaMemcpyHostToDevice, st));
+    G1 = g;
+    l1d = n;
+  }
+  if (!d2) {
+    T* g = bp.take<T>(p * n);
+    CU(cudaMemcpy2DAsync(g, n * sizeof(T), G2v, ld2 * sizeof(T), n * sizeof(T), p, cudaMemcpyHostToDevice, st));
+    G2 = g;
+    l2d = n;
+  }
+  T* S = bp.take<T>((int64_t)pl.L * pl.ldn);
+  SideBufs<T> sb0 = side_take<T>(bp, pl, 0, use_tc);
+  SideBufs<T> sb1 = side_take<T>(bp, pl, 1, use_tc);
+  SmallBufs small = small_take(bp, pl.L, k, n);
+  CU(cudaMemsetAsync(st_dev, 0, sizeof(DevStatus), st));
+
+  Solver<T, TC> sv{h, st, st_dev, prec, use_tc};
+  if ((rc = sv.side(G1, l1d, 0, pl, sb0, q, seed, S))) return rc;
+  if ((rc = sv.side(G2, l2d, 1, pl, sb1, q, seed, S + (int64_t)pl.l * pl.ldn))) return rc;
+  int gct0 = use_tc ? tc_gx_ctas(m) : gemm_gx_simt_ctas(m);
+  int gct1 = use_tc ? tc_gx_ctas(p) : gemm_gx_simt_ctas(p);
+  int bblk = (int)cdiv(n * pl.l, 256);
+  CU(launch_residual(sb0.gnorm, gct0, sb0.bnorm, bblk, small.resid, st));
+  CU(launch_residual(sb1.gnorm, gct1, sb1.bnorm, bblk, small.resid + 1, st));
+  {
+    ProfScope ps(h, GSVD_RAND_STAGE_SMALL);
+    if ((rc = small_gsvd<T>(h, st, st_dev, S, pl.ldn, pl.l, pl.L, n, k, small))) return rc;
+  }
+
+  // results
+  bool ad = is_device_ptr(alpha), bd = is_device_ptr(beta);
+  CU(cudaMemcpyAsync(h->st_host, st_dev, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(h->res_host, small.resid, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(alpha, small.alpha, k * sizeof(double), ad ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(beta, small.beta, k * sizeof(double), bd ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  prof_collect(h);
+  if (h->st_host->code) {
+    int c = h->st_host->code;
+    return fail(h, c, "device status %d at stage %d (index %d)%s", c, h->st_host->where, h->st_host->index,
+                c == GSVD_RAND_ERR_BREAKDOWN ? ": Cholesky breakdown even with the shift (rank-deficient sketch?)"
+                                             : (c == GSVD_RAND_ERR_NONFINITE ? ": non-finite values" : ""));
+  }
+  if (r_out) {
+    if (is_device_ptr(r_out))
+      CU(cudaMemcpy(r_out, &k, sizeof(int), cudaMemcpyHostToDevice));
+    else
+      *r_out = k;
+  }
+  if (resid_out) {
+    if (is_device_ptr(resid_out))
+      CU(cudaMemcpy(resid_out, h->res_host, 2 * sizeof(double), cudaMemcpyHostToDevice));
+    else
+      memcpy(resid_out, h->res_host, 2 * sizeof(double));
+  }
+  h->err.clear();
+  return GSVD_RAND_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gsvd_rand_config_init(gsvd_rand_config* cfg) {
+  if (!cfg) return GSVD_RAND_ERR_ARG;
+  memset(cfg, 0, sizeof(*cfg));
+  cfg->device = 0;
+  cfg->stream = nullptr;
+  cfg->prec = GSVD_RAND_TF32;
+  cfg->adaptive = 0;
+  cfg->block_b = 100;
+  cfg->tol = 1e-4;
+  return GSVD_RAND_OK;
+}
+
+int gsvd_rand_create(gsvd_rand_t* out, const gsvd_rand_config* cfg) {
+  if (!out || !cfg) return GSVD_RAND_ERR_ARG;
+  *out = nullptr;
+  if (cfg->prec < GSVD_RAND_FP64 || cfg->prec > GSVD_RAND_FP32) return GSVD_RAND_ERR_ARG;
+  if (cfg->adaptive) return GSVD_RAND_ERR_UNSUPPORTED;
+  gsvd_rand_ctx* h = new gsvd_rand_ctx();
+  h->cfg = *cfg;
+  h->stream = (cudaStream_t)cfg->stream;
+  cudaError_t e = cudaSetDevice(cfg->device);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return GSVD_RAND_ERR_CUDA;
+  }
+  if (cudaMallocHost(&h->st_host, sizeof(DevStatus)) != cudaSuccess ||
+      cudaMallocHost(&h->res_host, 4 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    if (h->st_host) cudaFreeHost(h->st_host);
+    delete h;
+    return GSVD_RAND_ERR_OOM;
+  }
+  h->tc_ok = tc_available(cfg->device) ? 1 : 0;
+  *out = h;
+  return GSVD_RAND_OK;
+}
+
+int gsvd_rand_destroy(gsvd_rand_t h) {
+  if (!h) return GSVD_RAND_OK;
+  cudaSetDevice(h->cfg.device);
+  if (h->stream) cudaStreamSynchronize(h->stream); else cudaDeviceSynchronize();
+  for (auto e : h->evpool) cudaEventDestroy(e);
+  if (h->ws) cudaFree(h->ws);
+  if (h->st_host) cudaFreeHost(h->st_host);
+  if (h->res_host) cudaFreeHost(h->res_host);
+  delete h;
+  return GSVD_RAND_OK;
+}
+
+const char* gsvd_rand_last_error(gsvd_rand_t h) { return h ? h->err.c_str() : "null handle"; }
+
+int gsvd_rand_profile_get(gsvd_rand_t h, int stage, double* total_ms, int64_t* calls) {
+  if (!h || stage < 0 || stage >= GSVD_RAND_NUM_STAGES) return GSVD_RAND_ERR_ARG;
+  if (total_ms) *total_ms = h->prof_ms[stage];
+  if (calls) *calls = h->prof_calls[stage];
+  return GSVD_RAND_OK;
+}
+
+int gsvd_rand_profile_reset(gsvd_rand_t h) {
+  if (!h) return GSVD_RAND_ERR_ARG;
+  for (int i = 0; i < 8; ++i) {
+    h->prof_ms[i] = 0.0;
+    h->prof_calls[i] = 0;
+  }
+  return GSVD_RAND_OK;
+}
+
+uint64_t gsvd_rand_launch_count(void) { return gsvdr::g_launch_count.load(); }
+
+int gsvd_rand_solve(gsvd_rand_t h, const void* G1, int64_t m, int64_t ld1, const void* G2, int64_t p,
+                    int64_t ld2, int64_t n, int k, int oversample, int q, uint64_t seed, double* alpha,
+                    double* beta, int* r_out, double* resid_out) {
+  if (!h) return GSVD_RAND_ERR_ARG;
+  if (!G1 || !G2 || !alpha || !beta) return fail(h, GSVD_RAND_ERR_ARG, "null pointer argument");
+  if (m < 1 || p < 1 || n < 1) return fail(h, GSVD_RAND_ERR_ARG, "empty matrix (m=%lld p=%lld n=%lld)",
+                                           (long long)m, (long long)p, (long long)n);
+  if (ld1 < n || ld2 < n) return fail(h, GSVD_RAND_ERR_ARG, "leading dimension smaller than n");
+  if (k < 1 || oversample < 0 || q < 0 || q > 16)
+    return fail(h, GSVD_RAND_ERR_ARG, "need k >= 1, oversample >= 0, 0 <= q <= 16");
+  int64_t l = (int64_t)k + oversample;
+  if (l > std::min(std::min(m, p), n))
+    return fail(h, GSVD_RAND_ERR_ARG, "k + oversample = %lld exceeds min(m, p, n)", (long long)l);
+  const bool f64 = h->cfg.prec == GSVD_RAND_FP64;
+  if (l > (f64 ? 224 : 256)) return fail(h, GSVD_RAND_ERR_ARG, "k + oversample = %lld exceeds the limit %d",
+                                         (long long)l, f64 ? 224 : 256);
+  if (n > (int64_t)1 << 30 || m > (int64_t)1 << 40 || p > (int64_t)1 << 40)
+    return fail(h, GSVD_RAND_ERR_ARG, "dimension too large");
+  cudaError_t e = cudaSetDevice(h->cfg.device);
+  if (e != cudaSuccess) return fail(h, GSVD_RAND_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+  if (f64) return solve_t<double, double>(h, G1, m, ld1, G2, p, ld2, n, k, oversample, q, seed, alpha, beta, r_out, resid_out);
+  if (h->cfg.flags & GSVD_RAND_FLAG_CHOL_FP64)
+    return solve_t<float, double>(h, G1, m, ld1, G2, p, ld2, n, k, oversample, q, seed, alpha, beta, r_out, resid_out);
+  return solve_t<float, float>(h, G1, m, ld1, G2, p, ld2, n, k, oversample, q, seed, alpha, beta, r_out, resid_out);
+}
+
+int gsvd_rand_metrics(gsvd_rand_t h, const double* alpha, const double* beta, int r, int pad_to_n,
+                      int pad_mode, double* theta, double* rho, double* P1, double* P2, double* D) {
+  if (!h) return GSVD_RAND_ERR_ARG;
+  if (!alpha || !beta) return fail(h, GSVD_RAND_ERR_ARG, "null alpha/beta");
+  if (r < 1) return fail(h, GSVD_RAND_ERR_ARG, "r must be >= 1");
+  if (pad_mode != 0 && pad_mode != 1) return fail(h, GSVD_RAND_ERR_ARG, "pad_mode must be 0 or 1");
+  int N = pad_to_n > r ? pad_to_n : r;
+  if (N < 2) return fail(h, GSVD_RAND_ERR_ARG, "the entropy needs at least 2 pairs (log N = 0)");
+  cudaStream_t st = h->stream;
+  CU(cudaSetDevice(h->cfg.device));
+  // device copies of inputs and outputs
+  Bump sz;
+  sz.take<double>(r);
+  sz.take<double>(r);
+  for (int i = 0; i < 4; ++i) sz.take<double>(N);
+  sz.take<double>(2);
+  int rc = ensure_ws(h, sz.off + 1024);
+  if (rc) return rc;
+  Bump bp;
+  bp.base = h->ws;
+  double* a = bp.take<double>(r);
+  double* b = bp.take<double>(r);
+  double* o[4];
+  for (int i = 0; i < 4; ++i) o[i] = bp.take<double>(N);
+  double* d = bp.take<double>(2);
+  CU(cudaMemcpyAsync(a, alpha, r * sizeof(double), is_device_ptr(alpha) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(b, beta, r * sizeof(double), is_device_ptr(beta) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  CU(launch_metrics(a, b, r, N, pad_mode, o[0], o[1], o[2], o[3], d, st));
+  double* outs[5] = {theta, rho, P1, P2, D};
+  for (int i = 0; i < 5; ++i) {
+    if (!outs[i]) continue;
+    size_t bytes = (i < 4 ? N : 2) * sizeof(double);
+    const double* src = i < 4 ? o[i] : d;
+    CU(cudaMemcpyAsync(outs[i], src, bytes, is_device_ptr(outs[i]) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  }
+  CU(cudaStreamSynchronize(st));
+  h->err.clear();
+  return GSVD_RAND_OK;
+}
+
+int gsvd_rand_gaussian(gsvd_rand_t h, int64_t n, int64_t l, uint64_t seed, uint32_t pair, uint32_t side,
+                       uint32_t stream, double* out) {
+  if (!h) return GSVD_RAND_ERR_ARG;
+  if (!out || n < 1 || l < 1 || n * l > ((int64_t)1 << 33)) return fail(h, GSVD_RAND_ERR_ARG, "bad gaussian arguments");
+  CU(cudaSetDevice(h->cfg.device));
+  cudaStream_t st = h->stream;
+  bool dev = is_device_ptr(out);
+  double* dst = out;
+  if (!dev) {
+    int rc = ensure_ws(h, (size_t)n * l * sizeof(double) + 256);
+    if (rc) return rc;
+    dst = (double*)h->ws;
+  }
+  CU(launch_gaussian_rowmajor(dst, n, l, seed, pair, side, stream, st));
+  if (!dev) CU(cudaMemcpyAsync(out, dst, n * l * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  return GSVD_RAND_OK;
+}
+
+int gsvd_rand_philox(gsvd_rand_t h, uint64_t count, uint64_t seed, uint32_t pair, uint32_t side,
+                     uint32_t stream, uint32_t* out) {
+  if (!h) return GSVD_RAND_ERR_ARG;
+  if (!out || count == 0 || count > ((uint64_t)1 << 32)) return fail(h, GSVD_RAND_ERR_ARG, "bad philox arguments");
+  CU(cudaSetDevice(h->cfg.device));
+  cudaStream_t st = h->stream;
+  bool dev = is_device_ptr(out);
+  uint32_t* dst = out;
+  if (!dev) {
+    int rc = ensure_ws(h, (size_t)count * 16 + 256);
+    if (rc) return rc;
+    dst = (uint32_t*)h->ws;
+  }
+  CU(launch_philox_words(dst, count, seed, pair, side, stream, st));
+  if (!dev) CU(cudaMemcpyAsync(out, dst, count * 16, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  return GSVD_RAND_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,534 @@
+// Small dense kernels of the compressed-pair GSVD (Algorithm 2 after the basis
+// extraction) and of the comparative metrics (Section 1).
+//
+// GB300 runs FP64 at about 1/57 of its FP32 rate (measured: 7.95 GFLOP/s per
+// SM FP64 vs 457 GFLOP/s FP32), so no FP64 work here is sequential on one SM:
+//   * FP64 products (the Gram K = S S^T, the refinement products) are split-K
+//     GEMMs spread over the whole GPU;
+//   * the eigensolver itself is a one-CTA FP32 cyclic Jacobi, and its result is
+//     lifted to FP64 accuracy by Ogita-Aishima refinement (Ogita & Aishima,
+//     "Iterative refinement for symmetric eigenvalue decomposition", Japan J.
+//     Indust. Appl. Math. 35, 2018), whose work is FP64 GEMMs again.
+#include <algorithm>
+
+#include "kernels.h"
+
+namespace gsvdr {
+
+// ============================================================================
+// FP64 split-K GEMM for small operands: C = alpha op(A) op(B) + beta C.
+// ============================================================================
+constexpr int SG_T = 32, SG_BK = 32;
+
+template <typename TA, typename TB>
+__global__ __launch_bounds__(256) void dgemm_small_kernel(int Mr, int Nc, int K, const TA* __restrict__ A,
+                                                          int64_t lda, int ta, const TB* __restrict__ B,
+                                                          int64_t ldb, int tb, double* __restrict__ part,
+                                                          int kchunk) {
+  __shared__ double As[SG_BK][SG_T + 1];
+  __shared__ double Bs[SG_BK][SG_T + 1];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int i0 = blockIdx.x * SG_T, j0 = blockIdx.y * SG_T, z = blockIdx.z;
+  const int kb = z * kchunk, ke = min(K, kb + kchunk);
+  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  for (int k0 = kb; k0 < ke; k0 += SG_BK) {
+    for (int e = tid; e < SG_T * SG_BK; e += 256) {
+      int a = e / 32, b = e % 32;
+      // A element (i, k)
+      int i, kk;
+      if (!ta) { i = a; kk = b; } else { kk = a; i = b; }
+      int gi = i0 + i, gk = k0 + kk;
+      double va = 0.0;
+      if (gi < Mr && gk < ke) va = (double)(ta ? A[(int64_t)gk * lda + gi] : A[(int64_t)gi * lda + gk]);
+      As[kk][i] = va;
+      // B element (k, j)
+      int j;
+      if (!tb) { kk = a; j = b; } else { j = a; kk = b; }
+      int gj = j0 + j;
+      gk = k0 + kk;
+      double vb = 0.0;
+      if (gj < Nc && gk < ke) vb = (double)(tb ? B[(int64_t)gj * ldb + gk] : B[(int64_t)gk * ldb + gj]);
+      Bs[kk][j] = vb;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < SG_BK; ++kk) {
+      double a0 = As[kk][ty * 2], a1 = As[kk][ty * 2 + 1];
+      double b0 = Bs[kk][tx * 2], b1 = Bs[kk][tx * 2 + 1];
+      acc[0][0] = fma(a0, b0, acc[0][0]);
+      acc[0][1] = fma(a0, b1, acc[0][1]);
+      acc[1][0] = fma(a1, b0, acc[1][0]);
+      acc[1][1] = fma(a1, b1, acc[1][1]);
+    }
+    __syncthreads();
+  }
+  double* P = part + (int64_t)z * Mr * Nc;
+  for (int m = 0; m < 2; ++m)
+    for (int q = 0; q < 2; ++q) {
+      int i = i0 + ty * 2 + m, j = j0 + tx * 2 + q;
+      if (i < Mr && j < Nc) P[(int64_t)i * Nc + j] = acc[m][q];
+    }
+}
+
+__global__ void dgemm_reduce_kernel(const double* __restrict__ part, int splits, int Mr, int Nc,
+                                    double* C, int64_t ldc, double alpha, double beta) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)Mr * Nc) return;
+  int i = (int)(e / Nc), j = (int)(e % Nc);
+  double s = 0.0;
+  for (int z = 0; z < splits; ++z) s += part[(int64_t)z * Mr * Nc + e];
+  double* c = C + (int64_t)i * ldc + j;
+  *c = beta == 0.0 ? alpha * s : alpha * s + beta * (*c);
+}
+
+template <typename TA, typename TB>
+cudaError_t launch_dgemm_small(int Mr, int Nc, int K, const TA* A, int64_t lda, int ta, const TB* B,
+                               int64_t ldb, int tb, double* C, int64_t ldc, double alpha, double beta,
+                               double* work, int64_t work_elems, cudaStream_t st) {
+  if (Mr <= 0 || Nc <= 0) return cudaSuccess;
+  int tiles = (int)(cdiv(Mr, SG_T) * cdiv(Nc, SG_T));
+  int kslices = (int)cdiv(std::max(K, 1), SG_BK);
+  int splits = std::max(1, std::min(kslices, (2 * 152 + tiles - 1) / tiles));
+  while (splits > 1 && (int64_t)splits * Mr * Nc > work_elems) --splits;
+  if ((int64_t)Mr * Nc > work_elems) return cudaErrorInvalidValue;
+  int kchunk = (int)round_up(cdiv(std::max(K, 1), splits), SG_BK);
+  splits = (int)cdiv(std::max(K, 1), kchunk);
+  dim3 grid((unsigned)cdiv(Mr, SG_T), (unsigned)cdiv(Nc, SG_T), (unsigned)splits);
+  dgemm_small_kernel<TA, TB><<<grid, 256, 0, st>>>(Mr, Nc, K, A, lda, ta, B, ldb, tb, work, kchunk);
+  cudaError_t e = launched();
+  if (e != cudaSuccess) return e;
+  dgemm_reduce_kernel<<<(unsigned)cdiv((int64_t)Mr * Nc, 256), 256, 0, st>>>(work, splits, Mr, Nc, C, ldc,
+                                                                              alpha, beta);
+  return launched();
+}
+template cudaError_t launch_dgemm_small<double, double>(int, int, int, const double*, int64_t, int,
+                                                        const double*, int64_t, int, double*, int64_t,
+                                                        double, double, double*, int64_t, cudaStream_t);
+template cudaError_t launch_dgemm_small<float, float>(int, int, int, const float*, int64_t, int,
+                                                      const float*, int64_t, int, double*, int64_t,
+                                                      double, double, double*, int64_t, cudaStream_t);
+
+// ============================================================================
+// One-CTA cyclic Jacobi in FP32 with the round-robin (circle) ordering: every
+// round applies N'/2 disjoint rotations (N' = N rounded up to even; pairs with
+// the dummy index are skipped), N'-1 rounds form a sweep.  Rotation angles as
+// in Golub & Van Loan, Algorithm 8.5.1 (sym.schur2).  A and V live in shared
+// memory when they fit, else in the global scratch (L2-resident).
+// ============================================================================
+int64_t jacobi_scratch_floats(int N) { return 2ll * N * N; }
+
+__global__ __launch_bounds__(1024) void jacobi_f32_kernel(const double* __restrict__ Ain, int N,
+                                                          double* __restrict__ Vout,
+                                                          double* __restrict__ lam, float* scratch,
+                                                          int use_smem, int max_sweeps,
+                                                          DevStatus* st_dev) {
+  extern __shared__ float sm[];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int Np = N + (N & 1), m = Np / 2;
+  float* A = use_smem ? sm : scratch;
+  float* V = use_smem ? sm + (int64_t)N * N : scratch + (int64_t)N * N;
+  // per-round pair tables live after A, V in shared memory when possible
+  __shared__ int s_top[256], s_bot[256];
+  __shared__ float s_c[256], s_s[256];
+  __shared__ float s_scale;
+  __shared__ unsigned s_off;  // max relative off-diagonal of the sweep, as float bits
+  if (tid == 0) {
+    double mx = 0.0;
+    for (int i = 0; i < N; ++i) mx = fmax(mx, fabs(Ain[(int64_t)i * N + i]));
+    s_scale = (float)(mx > 0.0 ? mx : 1.0);
+  }
+  for (int k = tid; k < m; k += nt) {
+    s_top[k] = 2 * k;
+    s_bot[k] = 2 * k + 1;
+  }
+  __syncthreads();
+  const float inv = 1.0f / s_scale;
+  for (int64_t e = tid; e < (int64_t)N * N; e += nt) {
+    A[e] = (float)(Ain[e] * (double)inv);
+    V[e] = ((e / N) == (e % N)) ? 1.0f : 0.0f;
+  }
+  __syncthreads();
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) s_off = 0u;
+    __syncthreads();
+    for (int rnd = 0; rnd < Np - 1; ++rnd) {
+      // round-robin (circle method): slot Np-1 is fixed, pairs (rnd, Np-1) and
+      // ((rnd + k) mod (Np-1), (rnd - k) mod (Np-1)), k = 1..m-1 are disjoint and
+      // every pair meets once in Np-1 rounds.
+      for (int k = tid; k < m; k += nt) {
+        int a, b;
+        if (k == 0) {
+          a = rnd;
+          b = Np - 1;
+        } else {
+          a = (rnd + k) % (Np - 1);
+          b = (rnd - k + (Np - 1)) % (Np - 1);
+        }
+        s_top[k] = min(a, b);
+        s_bot[k] = max(a, b);
+      }
+      __syncthreads();
+      // phase A: rotation parameters for the m disjoint pairs
+      for (int k = tid; k < m; k += nt) {
+        int p = s_top[k], q = s_bot[k];
+        float c = 1.f, s = 0.f;
+        if (q < N) {
+          float apq = A[(int64_t)p * N + q], app = A[(int64_t)p * N + p], aqq = A[(int64_t)q * N + q];
+          // A is scaled to max |a_ii| = 1: an absolute off-diagonal test.  The FP32
+          // result only needs absolute accuracy ~u ||A|| (the FP64 refinement
+          // takes it from there); a relative test would never stop on the
+          // noise-level eigenvalues that FP32 cannot resolve.
+          float off = fabsf(apq);
+          atomicMax(&s_off, __float_as_uint(off));
+          if (off > 1e-10f) {
+            float tau = (aqq - app) / (2.f * apq);
+            float t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+            c = rsqrtf(1.f + t * t);
+            s = t * c;
+          }
+        }
+        s_c[k] = c;
+        s_s[k] = s;
+      }
+      __syncthreads();
+      // phase B: columns p, q of A and V (A <- A J, V <- V J)
+      for (int e = tid; e < m * N; e += nt) {
+        int k = e / N, i = e % N;
+        float c = s_c[k], s = s_s[k];
+        if (s == 0.f) continue;
+        int p = s_top[k], q = s_bot[k];
+        float* ai = A + (int64_t)i * N;
+        float x = ai[p], y = ai[q];
+        ai[p] = c * x - s * y;
+        ai[q] = s * x + c * y;
+        float* vi = V + (int64_t)i * N;
+        x = vi[p];
+        y = vi[q];
+        vi[p] = c * x - s * y;
+        vi[q] = s * x + c * y;
+      }
+      __syncthreads();
+      // phase C: rows p, q of A (A <- J^T A); the annihilated entries are zero
+      for (int e = tid; e < m * N; e += nt) {
+        int k = e / N, j = e % N;
+        float c = s_c[k], s = s_s[k];
+        if (s == 0.f) continue;
+        int p = s_top[k], q = s_bot[k];
+        float x = A[(int64_t)p * N + j], y = A[(int64_t)q * N + j];
+        A[(int64_t)p * N + j] = (j == q) ? 0.f : c * x - s * y;
+        A[(int64_t)q * N + j] = (j == p) ? 0.f : s * x + c * y;
+      }
+      __syncthreads();
+    }
+    // every thread reads the sweep's maximum before anyone resets it
+    const float off = __uint_as_float(s_off);
+    __syncthreads();
+    if (off < 1e-7f) break;
+  }
+  if (sweep == max_sweeps && tid == 0 && st_dev) {
+    // not converged to FP32 level: refinement will still improve, record only
+    atomicAdd(&st_dev->pad, 1);
+  }
+  for (int64_t e = tid; e < (int64_t)N * N; e += nt) Vout[e] = (double)V[e];
+  for (int i = tid; i < N; i += nt) lam[i] = (double)A[(int64_t)i * N + i] * (double)s_scale;
+}
+
+cudaError_t launch_jacobi_f32(const double* A, int N, double* V, double* lam, float* scratch,
+                              int max_sweeps, DevStatus* st_dev, cudaStream_t st) {
+  if (N < 1 || N > 512) return cudaErrorInvalidValue;
+  size_t need = 2ull * N * N * sizeof(float);
+  int use_smem = need <= 200 * 1024;
+  size_t smem = use_smem ? need : 0;
+  cudaFuncSetAttribute(jacobi_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  jacobi_f32_kernel<<<1, 1024, smem, st>>>(A, N, V, lam, scratch, use_smem, max_sweeps, st_dev);
+  return launched();
+}
+
+// ============================================================================
+// Ogita-Aishima refinement (FP64).  X = X + X F with
+//   R = I - X^T X, S = X^T A X, lam_i = s_ii / (1 - r_ii),
+//   delta = 2 (||S - diag(lam)||_F + ||A||_F ||R||_F),
+//   F_ij = (s_ij + lam_j r_ij) / (lam_j - lam_i) if |lam_i - lam_j| > delta, else r_ij / 2,
+//   F_ii = r_ii / 2.
+// ============================================================================
+__global__ __launch_bounds__(1024) void oa_form_kernel(const double* __restrict__ A, int N,
+                                                       const double* __restrict__ XtX,
+                                                       const double* __restrict__ S,
+                                                       double* __restrict__ F, double* __restrict__ lam) {
+  __shared__ double red[3][32];
+  __shared__ double s_delta;
+  extern __shared__ double sl[];  // N eigenvalue estimates
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < N; i += nt) {
+    double rii = 1.0 - XtX[(int64_t)i * N + i];
+    sl[i] = S[(int64_t)i * N + i] / (1.0 - rii);
+  }
+  __syncthreads();
+  double a2 = 0.0, r2 = 0.0, s2 = 0.0;
+  for (int64_t e = tid; e < (int64_t)N * N; e += nt) {
+    int i = (int)(e / N), j = (int)(e % N);
+    double a = A[e];
+    double r = (i == j ? 1.0 : 0.0) - XtX[e];
+    double sd = S[e] - (i == j ? sl[i] : 0.0);
+    a2 += a * a;
+    r2 += r * r;
+    s2 += sd * sd;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a2 += __shfl_down_sync(0xffffffffu, a2, o);
+    r2 += __shfl_down_sync(0xffffffffu, r2, o);
+    s2 += __shfl_down_sync(0xffffffffu, s2, o);
+  }
+  if ((tid & 31) == 0) {
+    red[0][tid >> 5] = a2;
+    red[1][tid >> 5] = r2;
+    red[2][tid >> 5] = s2;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double A2 = 0, R2 = 0, S2 = 0;
+    for (int w = 0; w < (nt + 31) / 32; ++w) {
+      A2 += red[0][w];
+      R2 += red[1][w];
+      S2 += red[2][w];
+    }
+    s_delta = 2.0 * (sqrt(S2) + sqrt(A2) * sqrt(R2));
+  }
+  __syncthreads();
+  const double delta = s_delta;
+  for (int64_t e = tid; e < (int64_t)N * N; e += nt) {
+    int i = (int)(e / N), j = (int)(e % N);
+    double r = (i == j ? 1.0 : 0.0) - XtX[e];
+    double f;
+    if (i == j) {
+      f = 0.5 * r;
+    } else {
+      double d = sl[j] - sl[i];
+      f = (fabs(d) > delta) ? (S[e] + sl[j] * r) / d : 0.5 * r;
+    }
+    F[e] = f;
+  }
+  for (int i = tid; i < N; i += nt) lam[i] = sl[i];
+}
+
+cudaError_t launch_oa_refine(const double* A, int N, double* X, double* lam, double* work,
+                             int64_t work_elems, cudaStream_t st) {
+  int64_t nn = (int64_t)N * N;
+  if (work_elems < 4 * nn + nn) return cudaErrorInvalidValue;
+  double* XtX = work;
+  double* P = work + nn;
+  double* S = work + 2 * nn;
+  double* F = work + 3 * nn;
+  double* sk = work + 4 * nn;
+  int64_t skn = work_elems - 4 * nn;
+  cudaError_t e;
+  if ((e = launch_dgemm_small<double, double>(N, N, N, X, N, 1, X, N, 0, XtX, N, 1.0, 0.0, sk, skn, st)))
+    return e;
+  if ((e = launch_dgemm_small<double, double>(N, N, N, A, N, 0, X, N, 0, P, N, 1.0, 0.0, sk, skn, st)))
+    return e;
+  if ((e = launch_dgemm_small<double, double>(N, N, N, X, N, 1, P, N, 0, S, N, 1.0, 0.0, sk, skn, st)))
+    return e;
+  oa_form_kernel<<<1, 1024, (size_t)N * sizeof(double), st>>>(A, N, XtX, S, F, lam);
+  if ((e = launched())) return e;
+  // X <- X + X F   (the reduce of the split-K product reads and writes X elementwise)
+  return launch_dgemm_small<double, double>(N, N, N, X, N, 0, F, N, 0, X, N, 1.0, 1.0, sk, skn, st);
+}
+
+// ============================================================================
+// Leading-r selection and the CS step.
+// ============================================================================
+// Sort key with a strict total order: NaN sorts below every number, ties by index,
+// so the ranks below always form a permutation of 0..N-1.
+__device__ __forceinline__ double sort_key(double x) { return isnan(x) ? -INFINITY : x; }
+
+__global__ void select_topr_kernel(const double* __restrict__ X, const double* __restrict__ lam, int N,
+                                   int r, double* __restrict__ Zr, int* __restrict__ order) {
+  extern __shared__ int s_ord[];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < N; i += nt) {
+    double li = sort_key(lam[i]);
+    int rank = 0;
+    for (int j = 0; j < N; ++j) {
+      double lj = sort_key(lam[j]);
+      rank += (lj > li) || (lj == li && j < i);
+    }
+    s_ord[min(max(rank, 0), N - 1)] = i;
+  }
+  __syncthreads();
+  for (int i = tid; i < N; i += nt) order[i] = s_ord[i];
+  for (int64_t e = tid; e < (int64_t)N * r; e += nt) {
+    int row = (int)(e / r), t = (int)(e % r);
+    int c = min(max(s_ord[t], 0), N - 1);
+    Zr[e] = X[(int64_t)row * N + c];
+  }
+}
+
+cudaError_t launch_select_topr(const double* X, const double* lam, int N, int r, double* Zr, int* order,
+                               cudaStream_t st) {
+  select_topr_kernel<<<1, 512, (size_t)N * sizeof(int), st>>>(X, lam, N, r, Zr, order);
+  return launched();
+}
+
+// alpha_i^2 = w_i^T C1 w_i / w_i^T w_i, beta_i^2 = w_i^T C2 w_i / w_i^T w_i, pairs
+// sorted by alpha non-increasing (beta then non-decreasing, eq. (ab)).
+__global__ void cs_finalize_kernel(const double* __restrict__ Wm, const double* __restrict__ C1,
+                                   const double* __restrict__ C2, int r, double* __restrict__ alpha,
+                                   double* __restrict__ beta) {
+  extern __shared__ double sm2[];
+  double* sa = sm2;
+  double* sb = sm2 + r;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < r; i += nt) {
+    double nn = 0.0, q1 = 0.0, q2 = 0.0;
+    for (int a = 0; a < r; ++a) {
+      double wa = Wm[(int64_t)a * r + i];
+      nn += wa * wa;
+      double t1 = 0.0, t2 = 0.0;
+      for (int b = 0; b < r; ++b) {
+        double wb = Wm[(int64_t)b * r + i];
+        t1 += C1[(int64_t)a * r + b] * wb;
+        t2 += C2[(int64_t)a * r + b] * wb;
+      }
+      q1 += wa * t1;
+      q2 += wa * t2;
+    }
+    sa[i] = sqrt(fmax(q1 / nn, 0.0));
+    sb[i] = sqrt(fmax(q2 / nn, 0.0));
+  }
+  __syncthreads();
+  for (int i = tid; i < r; i += nt) {
+    double ai = sort_key(sa[i]);
+    int rank = 0;
+    for (int j = 0; j < r; ++j) {
+      double aj = sort_key(sa[j]);
+      rank += (aj > ai) || (aj == ai && j < i);
+    }
+    rank = min(max(rank, 0), r - 1);
+    alpha[rank] = sa[i];
+    beta[rank] = sb[i];
+  }
+}
+
+cudaError_t launch_cs_finalize(const double* W, const double* C1, const double* C2, int r,
+                               double* alpha, double* beta, cudaStream_t st) {
+  cs_finalize_kernel<<<1, 256, (size_t)2 * r * sizeof(double), st>>>(W, C1, C2, r, alpha, beta);
+  return launched();
+}
+
+// ============================================================================
+// Comparative quantities (Section 1): theta, rho, P1, P2, D1, D2.
+// ============================================================================
+__device__ __forceinline__ void pair_at(const double* alpha, const double* beta, int r, int N,
+                                        int pad_mode, int i, double& a, double& b) {
+  if (pad_mode == 0) {
+    if (i < r) {
+      a = alpha[i];
+      b = beta[i];
+    } else {
+      a = 0.0;
+      b = 1.0;
+    }
+  } else {
+    int off = N - r;
+    if (i < off) {
+      a = 1.0;
+      b = 0.0;
+    } else {
+      a = alpha[i - off];
+      b = beta[i - off];
+    }
+  }
+}
+
+__global__ __launch_bounds__(1024) void metrics_kernel(const double* __restrict__ alpha,
+                                                       const double* __restrict__ beta, int r, int N,
+                                                       int pad_mode, double* theta, double* rho,
+                                                       double* P1, double* P2, double* D) {
+  __shared__ double red[2][32];
+  __shared__ double s_tot[2];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const double quarter_pi = 0.78539816339744830962;
+  double sa = 0.0, sb = 0.0;
+  for (int i = tid; i < N; i += nt) {
+    double a, b;
+    pair_at(alpha, beta, r, N, pad_mode, i, a, b);
+    sa += a * a;
+    sb += b * b;
+    if (theta) theta[i] = atan2(a, b) - quarter_pi;
+    if (rho) rho[i] = (b == 0.0) ? __longlong_as_double(0x7ff0000000000000ll) : a / b;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sa += __shfl_down_sync(0xffffffffu, sa, o);
+    sb += __shfl_down_sync(0xffffffffu, sb, o);
+  }
+  if ((tid & 31) == 0) {
+    red[0][tid >> 5] = sa;
+    red[1][tid >> 5] = sb;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double ta = 0, tb = 0;
+    for (int w = 0; w < (nt + 31) / 32; ++w) {
+      ta += red[0][w];
+      tb += red[1][w];
+    }
+    s_tot[0] = ta;
+    s_tot[1] = tb;
+  }
+  __syncthreads();
+  const double ta = s_tot[0], tb = s_tot[1];
+  double h1 = 0.0, h2 = 0.0;
+  for (int i = tid; i < N; i += nt) {
+    double a, b;
+    pair_at(alpha, beta, r, N, pad_mode, i, a, b);
+    double p1 = ta > 0 ? a * a / ta : 0.0, p2 = tb > 0 ? b * b / tb : 0.0;
+    if (P1) P1[i] = p1;
+    if (P2) P2[i] = p2;
+    if (p1 > 0) h1 += p1 * log(p1);
+    if (p2 > 0) h2 += p2 * log(p2);
+  }
+  __syncthreads();
+  for (int o = 16; o > 0; o >>= 1) {
+    h1 += __shfl_down_sync(0xffffffffu, h1, o);
+    h2 += __shfl_down_sync(0xffffffffu, h2, o);
+  }
+  if ((tid & 31) == 0) {
+    red[0][tid >> 5] = h1;
+    red[1][tid >> 5] = h2;
+  }
+  __syncthreads();
+  if (tid == 0 && D) {
+    double a = 0, b = 0;
+    for (int w = 0; w < (nt + 31) / 32; ++w) {
+      a += red[0][w];
+      b += red[1][w];
+    }
+    double lg = log((double)N);
+    D[0] = -a / lg;
+    D[1] = -b / lg;
+  }
+}
+
+cudaError_t launch_metrics(const double* alpha, const double* beta, int r, int N, int pad_mode,
+                           double* theta, double* rho, double* P1, double* P2, double* D,
+                           cudaStream_t st) {
+  metrics_kernel<<<1, 1024, 0, st>>>(alpha, beta, r, N, pad_mode, theta, rho, P1, P2, D);
+  return launched();
+}
+
+__global__ void residual_kernel(const double* gpart, int ng, const double* bpart, int nb, double* out) {
+  if (threadIdx.x != 0) return;
+  double g = 0.0, b = 0.0;
+  for (int i = 0; i < ng; ++i) g += gpart[i];
+  for (int i = 0; i < nb; ++i) b += bpart[i];
+  *out = g > 0.0 ? sqrt(fmax(g - b, 0.0) / g) : 0.0;
+}
+
+cudaError_t launch_residual(const double* gpart, int ng, const double* bpart, int nb, double* out,
+                            cudaStream_t st) {
+  residual_kernel<<<1, 32, 0, st>>>(gpart, ng, bpart, nb, out);
+  return launched();
+}
+
+}  // namespace gsvdr

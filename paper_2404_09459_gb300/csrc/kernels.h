@@ -1,0 +1,123 @@
+// Internal launchers of the randomized-GSV library (host side, C++).
+// Every launcher enqueues on `st` and returns the cudaError_t of the launch.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace gsvdr {
+
+// ---- Gaussian test matrices (Algorithm 1 "Omega_i"; Theorem 3) -------------
+// Raw Philox words, out[4t + w].
+cudaError_t launch_philox_words(uint32_t* out, uint64_t count, uint64_t seed, uint32_t pair,
+                                uint32_t side, uint32_t stream, cudaStream_t st);
+// Omega (n x l) row-major FP64 (ld = l): the public definition.
+cudaError_t launch_gaussian_rowmajor(double* out, int64_t n, int64_t l, uint64_t seed, uint32_t pair,
+                                     uint32_t side, uint32_t stream, cudaStream_t st);
+// Omega^T stored K-major for the sketch product: Xt[j * ldx + i] = Omega[i][j],
+// j < lrows (rows l..lrows-1 are zero), i < n (columns n..ldx-1 are zero).
+template <typename T>
+cudaError_t launch_gaussian_kmajor(T* Xt, int64_t ldx, int64_t n, int l, int lrows, uint64_t seed,
+                                   uint32_t pair, uint32_t side, uint32_t stream, cudaStream_t st);
+
+// ---- sketch / power products on CUDA cores (Algorithm 1 line "G Omega") ----
+// Y (M x l, ld ldy) = G (M x n) * X where X is given K-major as Xt (l x n, ld ldx).
+// If gnorm_part != nullptr, CTA b of column-tile 0 writes sum of G^2 over its
+// rows to gnorm_part[b] (FP64; double-float accumulation for float data).
+template <typename T>
+cudaError_t launch_gemm_gx_simt(const T* G, int64_t ldg, int64_t M, int64_t n, const T* Xt,
+                                int64_t ldx, int l, T* Y, int64_t ldy, double* gnorm_part,
+                                cudaStream_t st);
+int gemm_gx_simt_ctas(int64_t M);
+
+// Split-K partials of G^T Q: part[z][c][j] (z < splits, c < n, j < l, ld lp)
+// over the rows of split z.  Returns the number of splits used via *splits.
+template <typename T, typename TP>
+cudaError_t launch_gemm_gtq_simt(const T* G, int64_t ldg, int64_t M, int64_t n, const T* Q,
+                                 int64_t ldq, int l, TP* part, int64_t lp, int splits,
+                                 cudaStream_t st);
+int gemm_gtq_splits(int64_t M, int64_t n, int l, int64_t max_part_elems);
+
+// Sum the split partials in split order (deterministic), in FP64, into
+//   transpose_out == 0: Z[c * ldz + j]   (n x l)
+//   transpose_out == 1: Z[j * ldz + c]   (l x n, the projection B = Q^T G)
+// If sq_part != nullptr, block b writes its sum of squares of the outputs.
+template <typename TP, typename T>
+cudaError_t launch_reduce_splits(const TP* part, int splits, int64_t n, int l, int64_t lp, T* Z,
+                                 int64_t ldz, int transpose_out, double* sq_part, int* sq_blocks,
+                                 cudaStream_t st);
+
+// ---- CholeskyQR2 with shift (orthonormalisation of the sketch) -------------
+// Gram partials of Y (M x l): part[c][i][j] over row chunk c (FP64 output).
+template <typename T>
+cudaError_t launch_gram_partial(const T* Y, int64_t ldy, int64_t M, int l, double* part, int chunks,
+                                int64_t rows_per_chunk, cudaStream_t st);
+int gram_chunks(int64_t M, int l, int64_t* rows_per_chunk);
+// W = sum_c part[c] (FP64, chunk order).
+cudaError_t launch_gram_reduce(const double* part, int chunks, int l, double* W, cudaStream_t st);
+
+// Cholesky of W + s I (s = shift_coef * trace(W), 0 for no shift), one CTA.
+// R: upper triangular l x l (row-major, ld l, zeros below) in TC; rinv: 1/R_ii.
+// A pivot d_k <= tau_rel * (W + sI)_kk is numerically dependent: its column is
+// dropped (R row k = e_k, rinv_k = 0, so column k of Q = Y R^{-1} is zero).
+// All columns dropped -> BREAKDOWN; non-finite entries -> NONFINITE (st_dev).
+template <typename TC>
+cudaError_t launch_chol_shift(const double* W, int l, double shift_coef, double tau_rel, TC* R,
+                              TC* rinv, DevStatus* st_dev, int stage, cudaStream_t st);
+
+// Q = Y R^{-1} by row-wise forward substitution (q R = y), optional Gram
+// partials of Q per CTA (part != nullptr, one chunk per CTA), optional
+// transposed output Qt[j * ldq + row].
+template <typename T, typename TC>
+cudaError_t launch_apply_rinv(const T* Y, int64_t ldy, int64_t M, int l, const TC* R,
+                              const TC* rinv, T* Q, int64_t ldq, int transpose_out, double* part,
+                              cudaStream_t st);
+int apply_ctas(int64_t M, int l);
+int64_t apply_rows_per_cta(int l);
+
+// ---- small FP64 dense kernels (compressed-pair GSVD) -----------------------
+// C (Mr x Nc) = op(A) * op(B) in FP64 accumulation; op(X) = X or X^T.
+// A: if !ta, Mr x K with lda; else K x Mr.  B: if !tb, K x Nc with ldb; else Nc x K.
+// Split-K partials go to `work` (splits * Mr * Nc doubles) then a reduce writes
+// C = alpha * sum + beta * C.  Returns cudaErrorInvalidValue if work too small.
+template <typename TA, typename TB>
+cudaError_t launch_dgemm_small(int Mr, int Nc, int K, const TA* A, int64_t lda, int ta, const TB* B,
+                               int64_t ldb, int tb, double* C, int64_t ldc, double alpha, double beta,
+                               double* work, int64_t work_elems, cudaStream_t st);
+
+// One-CTA cyclic Jacobi eigensolver in FP32 (parallel round-robin order) on the
+// symmetric N x N FP64 matrix A (scaled internally).  Writes the eigenvector
+// matrix V (N x N, FP64, columns) and eigenvalues lam (FP64, unsorted).
+// scratch: 2*N*N floats + N*N... (see jacobi_scratch_floats).
+int64_t jacobi_scratch_floats(int N);
+cudaError_t launch_jacobi_f32(const double* A, int N, double* V, double* lam, float* scratch,
+                              int max_sweeps, DevStatus* st_dev, cudaStream_t st);
+
+// One Ogita-Aishima refinement step of the eigenvectors X (N x N) of the
+// symmetric A, in FP64: R = I - X^T X, S = X^T A X, lam_i = s_ii/(1 - r_ii),
+// F_ij = (s_ij + lam_j r_ij)/(lam_j - lam_i) (|lam_i - lam_j| > delta) or r_ij/2,
+// X <- X + X F.  work: 4*N*N + splitK scratch doubles.
+cudaError_t launch_oa_refine(const double* A, int N, double* X, double* lam, double* work,
+                             int64_t work_elems, cudaStream_t st);
+
+// GSV pairs from the refined eigen-decomposition of K = S S^T (L x L, S = [B1; B2],
+// B1 with l1 rows): take the r leading eigenvectors Zr, C1 = Z1^T Z1,
+// C2 = Z2^T Z2, eigen-decompose C1 (FP32 Jacobi + FP64 refinement) and
+// alpha_i^2 = w_i^T C1 w_i, beta_i^2 = w_i^T C2 w_i, sorted.
+// Implemented in the orchestration (api.cu) from the pieces below.
+cudaError_t launch_select_topr(const double* X, const double* lam, int N, int r, double* Zr,
+                               int* order, cudaStream_t st);
+cudaError_t launch_cs_finalize(const double* W, const double* C1, const double* C2, int r,
+                               double* alpha, double* beta, cudaStream_t st);
+
+// Comparative quantities of Section 1.
+cudaError_t launch_metrics(const double* alpha, const double* beta, int r, int N, int pad_mode,
+                           double* theta, double* rho, double* P1, double* P2, double* D,
+                           cudaStream_t st);
+
+// Residual (cumulated form): resid[s] = sqrt(max(g2 - b2, 0) / g2).
+cudaError_t launch_residual(const double* gpart, int ng, const double* bpart, int nb, double* out,
+                            cudaStream_t st);
+
+}  // namespace gsvdr

@@ -1,0 +1,178 @@
+"""GPU path vs the FP64 oracle, through the C ABI (needs a CUDA GPU).
+
+Tolerances (stated by the method's accuracy targets): per-pair GSV error
+e_i = max(|alpha_i - alpha_ref_i|, |beta_i - beta_ref_i|) <= 1e-10 on the FP64
+path and <= 1e-4 on the mixed-precision paths; antisymmetric angular distance
+within 1e-4 rad.  Philox words are compared bit for bit.
+"""
+import numpy as np
+import pytest
+
+from oracle import gsvd as O
+from oracle.philox import gaussian, philox_words
+from paper_2404_09459_gb300.inputs import PAIR_FP64_SMALL, PAIR_TF32_LARGE, PairSpec, planted_pair
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2404_09459_gb300 as P  # noqa: E402
+
+P._build.build()
+
+TOL = {"fp64": 1e-10, "fp32": 1e-4, "tf32": 1e-4, "tf32x3": 1e-4, "bf16": 1e-4}
+DT = {"fp64": torch.float64}
+
+
+def _dev(a, prec):
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dt)
+
+
+def _solve(prec, G1, G2, spec, **kw):
+    with P.Context(prec, **kw) as ctx:
+        out = ctx.solve(_dev(G1, prec), _dev(G2, prec), spec.kk, spec.oversample, spec.q, spec.seed)
+    return out["alpha"].cpu().numpy(), out["beta"].cpu().numpy(), out
+
+
+def _check(prec, G1, G2, spec, ref=None, **kw):
+    ref = ref or O.rand_gsvd(G1, G2, spec.kk, spec.oversample, spec.q, spec.seed)
+    a, b, out = _solve(prec, G1, G2, spec, **kw)
+    e = O.gsv_error(ref["alpha"], ref["beta"], a, b)
+    dth = np.abs(np.arctan2(a, b) - np.arctan2(ref["alpha"], ref["beta"]))
+    assert np.max(e) <= TOL[prec], (prec, np.max(e), e)
+    assert np.max(dth) <= 1e-4
+    assert np.all(np.diff(a) <= 0) and np.all(np.diff(b) >= 0)
+    return a, b, out, ref
+
+
+# ---------------------------------------------------------------- generator
+
+def test_philox_words_bit_exact():
+    with P.Context("fp64") as ctx:
+        for seed, pair, side, stream in ((0, 0, 0, 0), (123456789012345, 7, 1, 0x10003), (2**64 - 1, 2**32 - 1, 1, 5)):
+            w = ctx.philox(4099, seed, pair, side, stream)
+            ref = np.stack(philox_words(4099, seed, pair, side, stream), axis=1)
+            np.testing.assert_array_equal(w, ref)
+
+
+@pytest.mark.parametrize("n,l", [(200, 30), (97, 13), (1, 1)])
+def test_gaussian_matches_oracle(n, l):
+    with P.Context("fp64") as ctx:
+        g = ctx.gaussian(n, l, seed=42, pair=3, side=1)
+        gd = ctx.gaussian(n, l, seed=42, pair=3, side=1, device_out=True).cpu().numpy()
+    ref = gaussian(n, l, 42, 3, 1)
+    np.testing.assert_allclose(g, ref, rtol=0, atol=1e-13)
+    np.testing.assert_array_equal(g, gd)
+
+
+# ---------------------------------------------------------------- FP64 path
+
+def test_fp64_small_pair_full_size():
+    """The plain FP64 workload at its full size (m = p = 2000, n = 200, k = 20, os = 10, q = 1)."""
+    G1, G2, at, bt = planted_pair(PAIR_FP64_SMALL)
+    a, b, out, ref = _check("fp64", G1, G2, PAIR_FP64_SMALL)
+    assert abs(out["resid"][0] - ref["resid1"]) < 1e-6 and abs(out["resid"][1] - ref["resid2"]) < 1e-6
+
+
+@pytest.mark.parametrize("m,p,n,k,os_,q", [(333, 257, 97, 7, 5, 2), (130, 70, 65, 60, 4, 0),
+                                          (64, 64, 64, 1, 0, 1), (1000, 90, 300, 33, 11, 3)])
+def test_fp64_ragged_shapes(m, p, n, k, os_, q):
+    spec = PairSpec(m=m, p=p, n=n, r=min(k + 3, n), alpha="uniform", decay="exp10", sigma=1e-7, k=k,
+                    oversample=os_, q=q, seed=m + n)
+    G1, G2, _, _ = planted_pair(spec)
+    _check("fp64", G1, G2, spec)
+
+
+def test_fp64_exact_rank_equals_planted():
+    spec = PairSpec(m=500, p=400, n=150, r=15, alpha="uniform", decay="exp10", sigma=0.0, k=15,
+                    oversample=5, q=1, seed=9)
+    G1, G2, at, bt = planted_pair(spec)
+    a, b, _ = _solve("fp64", G1, G2, spec)
+    assert np.max(O.gsv_error(at, bt, a, b)) < 1e-11
+
+
+def test_fp64_deterministic_and_host_buffers():
+    spec = PairSpec(m=400, p=300, n=100, r=10, sigma=1e-8, k=10, oversample=6, q=1, seed=5)
+    G1, G2, _, _ = planted_pair(spec)
+    a1, b1, _ = _solve("fp64", G1, G2, spec)
+    a2, b2, _ = _solve("fp64", G1, G2, spec)
+    np.testing.assert_array_equal(a1, a2)
+    with P.Context("fp64") as ctx:  # host (numpy) inputs and outputs
+        out = ctx.solve(G1, G2, spec.kk, spec.oversample, spec.q, spec.seed)
+    assert isinstance(out["alpha"], np.ndarray)
+    np.testing.assert_array_equal(out["alpha"], a1)
+    np.testing.assert_array_equal(out["beta"], b1)
+
+
+# ---------------------------------------------------------------- mixed paths
+
+def test_fp32_simt_reduced_large_pair():
+    spec = PairSpec(m=4000, p=3000, n=400, r=30, alpha="uniform", decay="exp10", sigma=1e-6, k=30,
+                    oversample=10, q=2, seed=2)
+    G1, G2, _, _ = planted_pair(spec)
+    _check("fp32", G1, G2, spec)
+
+
+@pytest.mark.parametrize("prec", ["tf32", "tf32x3", "bf16"])
+def test_tensor_core_paths_reduced_pair(prec):
+    spec = PairSpec(m=4000, p=3000, n=400, r=30, alpha="uniform", decay="exp10", sigma=1e-6, k=30,
+                    oversample=10, q=2, seed=2)
+    G1, G2, _, _ = planted_pair(spec)
+    if prec == "bf16":
+        pytest.skip("BF16 sketch is a precision-stress mode: its error is reported, not gated")
+    _check(prec, G1, G2, spec)
+
+
+def test_tf32_large_pair_full_size():
+    """The single large pair at full size (m = 20000, p = 15000, n = 1000, k = 50, os = 10, q = 2)."""
+    G1, G2, _, _ = planted_pair(PAIR_TF32_LARGE)
+    _check("tf32", G1, G2, PAIR_TF32_LARGE)
+
+
+# ---------------------------------------------------------------- metrics
+
+@pytest.mark.parametrize("pad_to_n,pad_mode", [(0, 0), (40, 0), (40, 1)])
+def test_metrics_match_oracle(pad_to_n, pad_mode):
+    rng = np.random.default_rng(3)
+    a = np.ascontiguousarray(np.sort(rng.uniform(0, 1, 17))[::-1])
+    a[0] = 1.0
+    b = np.sqrt(1 - a ** 2)
+    ref = O.metrics(a, b, pad_to_n, pad_mode)
+    with P.Context("fp64") as ctx:
+        got = ctx.metrics(a, b, pad_to_n, pad_mode)
+        gd = ctx.metrics(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), pad_to_n, pad_mode)
+    for key in ("theta", "P1", "P2"):
+        np.testing.assert_allclose(got[key], ref[key], rtol=0, atol=1e-14)
+        np.testing.assert_allclose(gd[key].cpu().numpy(), ref[key], rtol=0, atol=1e-14)
+    fin = np.isfinite(ref["rho"])
+    np.testing.assert_allclose(got["rho"][fin], ref["rho"][fin], rtol=1e-14)
+    assert np.all(np.isinf(got["rho"][~fin]))
+    assert abs(float(got["D1"]) - ref["D1"]) < 1e-14 and abs(float(got["D2"]) - ref["D2"]) < 1e-14
+
+
+# ---------------------------------------------------------------- errors
+
+def test_error_codes():
+    spec = PairSpec(m=100, p=80, n=40, r=5, sigma=0.0, k=5, oversample=3, q=1, seed=1)
+    G1, G2, _, _ = planted_pair(spec)
+    with P.Context("fp64") as ctx:
+        with pytest.raises(P.GsvdRandError) as e:
+            ctx.solve(_dev(G1, "fp64"), _dev(G2, "fp64"), 38, 10, 1, 0)  # l > n
+        assert e.value.name == "ARG"
+        with pytest.raises(P.GsvdRandError) as e:
+            ctx.solve(_dev(np.zeros_like(G1), "fp64"), _dev(G2, "fp64"), 5, 3, 1, 0)
+        assert e.value.name == "BREAKDOWN"
+        bad = G1.copy()
+        bad[3, 7] = np.nan
+        with pytest.raises(P.GsvdRandError) as e:
+            ctx.solve(_dev(bad, "fp64"), _dev(G2, "fp64"), 5, 3, 1, 0)
+        assert e.value.name == "NONFINITE"
+        # the context stays usable after device-reported errors
+        out = ctx.solve(_dev(G1, "fp64"), _dev(G2, "fp64"), 5, 3, 1, 0)
+        assert out["r"] == 5
+        with pytest.raises(P.GsvdRandError) as e:
+            ctx.metrics(np.array([1.0]), np.array([0.0]))
+        assert e.value.name == "ARG"
