@@ -31,7 +31,7 @@ from paper_2404_09459_gb300.inputs import (PAIR_BF16_STRESS, PAIR_FP64_SMALL, PA
                                            planted_pair, planted_pair_torch)
 
 WORKLOADS = {
-    "tf32_large": (PAIR_TF32_LARGE, "tf32"),
+    "tf32_large": (PAIR_TF32_LARGE, "tf32x3"),
     "fp64_small": (PAIR_FP64_SMALL, "fp64"),
     "bf16_stress": (PAIR_BF16_STRESS, "bf16"),
 }

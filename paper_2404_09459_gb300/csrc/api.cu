@@ -6,8 +6,8 @@
 //   q times: Z = G^T Q, Zh = orth(Z), Y = G Zh, Q = orth(Y)  (power / subspace iteration)
 //   B_s = Q^T G (rows of the stack S), ||G||^2 - ||B||^2    (projection, cumulated residual)
 // then the compressed-pair GSVD in FP64 (Algorithm 2, rank-revealing reading):
-//   K = S S^T, leading-k eigenvectors Zr (FP32 Jacobi + FP64 Ogita-Aishima),
-//   C1 = Z1^T Z1, C2 = Z2^T Z2, alpha^2 / beta^2 from the eigenvectors of C1.
+//   K = S S^T, leading-k eigenvectors Zr (FP32 tridiagonal + FP64 Ogita-Aishima),
+//   W = eigenvectors of C1 = Z1^T Z1, alpha_i = ||Z1 w_i||, beta_i = ||Z2 w_i||.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -167,8 +167,8 @@ struct SideBufs {
   T* part;        // splits x n x lp  (split-K partials of G^T Q)
   double* gpart;  // Gram partials
   double* W;      // l x l
-  void* R;        // l x l (TC)
-  void* rinv;     // l (TC)
+  void* R;        // l x l R^{-1} of the current CholeskyQR pass (TC)
+  void* cscr;     // Cholesky scratch (TC), when shared memory is too small
   double* gnorm;  // sketch-CTA partial sums of G^2
   double* bnorm;  // reduce-block partial sums of B^2
 };
@@ -207,13 +207,11 @@ struct Solver {
     const double tau = 8.0 * (double)std::max<int64_t>(rpc, apply_rows_per_cta(l)) * u;
     CU(launch_gram_partial<T>(Yin, lp, M, l, b.gpart, chunks, rpc, st));
     CU(launch_gram_reduce(b.gpart, chunks, l, b.W, st));
-    CU(launch_chol_shift<TC>(b.W, l, shift_coef, tau, (TC*)b.R, (TC*)b.rinv, st_dev, stage, st));
-    CU((launch_apply_rinv<T, TC>(Yin, lp, M, l, (const TC*)b.R, (const TC*)b.rinv, b.tmp, lp, 0, b.gpart,
-                                st)));
+    CU(launch_chol_shift<TC>(b.W, l, shift_coef, tau, (TC*)b.R, (TC*)b.cscr, st_dev, stage, st));
+    CU((launch_apply_rinv<T, TC>(Yin, lp, M, l, (const TC*)b.R, b.tmp, lp, 0, b.gpart, st)));
     CU(launch_gram_reduce(b.gpart, apply_ctas(M, l), l, b.W, st));
-    CU(launch_chol_shift<TC>(b.W, l, 0.0, tau, (TC*)b.R, (TC*)b.rinv, st_dev, stage + 1, st));
-    CU((launch_apply_rinv<T, TC>(b.tmp, lp, M, l, (const TC*)b.R, (const TC*)b.rinv, out, ldo,
-                                transpose_out, nullptr, st)));
+    CU(launch_chol_shift<TC>(b.W, l, 0.0, tau, (TC*)b.R, (TC*)b.cscr, st_dev, stage + 1, st));
+    CU((launch_apply_rinv<T, TC>(b.tmp, lp, M, l, (const TC*)b.R, out, ldo, transpose_out, nullptr, st)));
     return GSVD_RAND_OK;
   }
 
@@ -221,7 +219,7 @@ struct Solver {
     ProfScope ps(h, GSVD_RAND_STAGE_SKETCH);
     if constexpr (std::is_same<T, float>::value) {
       if (use_tc) {
-        CU(tc_gemm_gx(prec, G, ldg, M, pl.n, b.Xt, pl.ldx, pl.l, b.Y, pl.lp, gnorm, st));
+        CU(tc_gemm_gx(prec, G, ldg, M, pl.n, b.Xt, pl.ldx, pl.l, b.Y, pl.lp, gnorm, st_dev, st));
         return GSVD_RAND_OK;
       }
     }
@@ -237,7 +235,9 @@ struct Solver {
     if constexpr (std::is_same<T, float>::value) {
       if (use_tc) {
         int s2 = 0;
-        CU(tc_gemm_gtq(prec, G, ldg, M, pl.n, b.Q, pl.lp, pl.l, b.part, pl.lp, &s2, pl.part_elems, st));
+        // in tensor-core mode Q is kept transposed (Q^T: lx x ldm, K-major operand)
+        CU(tc_gemm_gtq(prec, G, ldg, M, pl.n, b.Q, round_up(M, 4), pl.l, b.part, pl.lp, &s2, pl.part_elems, st_dev,
+                       st));
         splits = s2;
         done = true;
       }
@@ -254,14 +254,20 @@ struct Solver {
     const int64_t M = pl.M[s];
     CU(launch_gaussian_kmajor<T>(b.Xt, pl.ldx, pl.n, pl.l, (int)pl.lx, seed, 0u, (uint32_t)s,
                                  GSVD_RAND_STREAM_FIXED, st));
+    // Q layout: row-major M x lp for the CUDA-core product, transposed Q^T
+    // (lx x ldm, padding rows zero) as the K-major operand of the tensor-core one
+    const int qt = use_tc ? 1 : 0;
+    const int64_t ldq = use_tc ? round_up(M, 4) : pl.lp;
+    if (use_tc)
+      CU(cudaMemsetAsync(b.Q + (int64_t)pl.l * ldq, 0, (size_t)(pl.lx - pl.l) * ldq * sizeof(T), st));
     int rc;
     if ((rc = gx(G, ldg, M, pl, b, b.gnorm))) return rc;
-    if ((rc = orth(b, b.Y, M, pl.l, pl.lp, b.Q, pl.lp, 0, 10 * s + 1))) return rc;
+    if ((rc = orth(b, b.Y, M, pl.l, pl.lp, b.Q, ldq, qt, 10 * s + 1))) return rc;
     for (int it = 0; it < q; ++it) {
       if ((rc = gtq(G, ldg, M, pl, b, b.Z, pl.lp, 0, nullptr))) return rc;
       if ((rc = orth(b, b.Z, pl.n, pl.l, pl.lp, b.Xt, pl.ldx, 1, 10 * s + 3))) return rc;
       if ((rc = gx(G, ldg, M, pl, b, nullptr))) return rc;
-      if ((rc = orth(b, b.Y, M, pl.l, pl.lp, b.Q, pl.lp, 0, 10 * s + 5))) return rc;
+      if ((rc = orth(b, b.Y, M, pl.l, pl.lp, b.Q, ldq, qt, 10 * s + 5))) return rc;
     }
     // projection B = Q^T G written as l rows of S
     if ((rc = gtq(G, ldg, M, pl, b, Srows, pl.ldn, 1, b.bnorm))) return rc;
@@ -270,22 +276,13 @@ struct Solver {
 };
 
 template <typename T>
+SideBufs<T> side_take(Bump& bp, const Plan& pl, int s, bool tc);
+
+// Bytes carved by side_take (the same code run on a null base).
+template <typename T>
 size_t side_bytes(const Plan& pl, int s, bool tc) {
   Bump bp;
-  int64_t M = pl.M[s];
-  bp.take<T>(pl.lx * pl.ldx);
-  bp.take<T>(M * pl.lp);
-  bp.take<T>(M * pl.lp);
-  bp.take<T>(std::max(M, pl.n) * pl.lp);
-  bp.take<T>(pl.n * pl.lp);
-  bp.take<T>(pl.part_elems);
-  bp.take<double>(pl.gpart_elems);
-  bp.take<double>((int64_t)pl.l * pl.l);
-  bp.take<double>((int64_t)pl.l * pl.l);
-  bp.take<double>(pl.l);
-  bp.take<double>(std::max<int64_t>(gemm_gx_simt_ctas(M), tc ? tc_gx_ctas(M) : 1) + 8);
-  bp.take<double>(cdiv(pl.n * pl.l, 256) + 8);
-  (void)tc;
+  side_take<T>(bp, pl, s, tc);
   return bp.off + 256;
 }
 
@@ -295,14 +292,14 @@ SideBufs<T> side_take(Bump& bp, const Plan& pl, int s, bool tc) {
   int64_t M = pl.M[s];
   b.Xt = bp.take<T>(pl.lx * pl.ldx);
   b.Y = bp.take<T>(M * pl.lp);
-  b.Q = bp.take<T>(M * pl.lp);
+  b.Q = bp.take<T>(std::max(M * pl.lp, pl.lx * round_up(M, 4)));
   b.tmp = bp.take<T>(std::max(M, pl.n) * pl.lp);
   b.Z = bp.take<T>(pl.n * pl.lp);
   b.part = bp.take<T>(pl.part_elems);
   b.gpart = bp.take<double>(pl.gpart_elems);
   b.W = bp.take<double>((int64_t)pl.l * pl.l);
   b.R = bp.take<double>((int64_t)pl.l * pl.l);
-  b.rinv = bp.take<double>(pl.l);
+  b.cscr = bp.take<double>(chol_scratch_elems(pl.l));
   b.gnorm = bp.take<double>(std::max<int64_t>(gemm_gx_simt_ctas(M), tc ? tc_gx_ctas(M) : 1) + 8);
   b.bnorm = bp.take<double>(cdiv(pl.n * pl.l, 256) + 8);
   return b;
@@ -325,6 +322,7 @@ struct SmallBufs {
   double* alpha;  // r
   double* beta;   // r
   double* resid;  // 2
+  double* U1;     // L x r   ([Z1; Z2] W)
 };
 
 int64_t small_work_elems(int L, int64_t n) {
@@ -346,20 +344,32 @@ SmallBufs small_take(Bump& bp, int L, int r, int64_t n) {
   s.mu = bp.take<double>(r);
   s.work_elems = small_work_elems(L, n);
   s.work = bp.take<double>(s.work_elems);
-  s.jscratch = bp.take<float>(jacobi_scratch_floats(L));
+  s.jscratch = bp.take<float>(eig_scratch_floats(L));
   s.alpha = bp.take<double>(r);
   s.beta = bp.take<double>(r);
   s.resid = bp.take<double>(2);
+  s.U1 = bp.take<double>((int64_t)L * r);
   return s;
 }
 
-constexpr int OA_ITERS = 3;
-constexpr int JACOBI_SWEEPS = 16;
+// Ogita-Aishima iterations after the FP32 start: the error squares per step once
+// the gaps exceed the threshold delta, so two reach FP64 accuracy for gaps
+// >~1e-3 ||K||.  K = S S^T squares the spectrum: eigenvalues 1e-6 ||K|| apart
+// start as one cluster and separate only as delta shrinks, hence five on the
+// FP64 path (1e-10 target) and three on the mixed paths (1e-4 target).
+template <typename T>
+constexpr int oa_iters() {
+  return std::is_same<T, double>::value ? 5 : 3;
+}
 
+// Compressed-pair GSVD (Algorithm 2 with the rank-revealing reading): the r
+// leading left singular vectors Zr of S = [B1; B2] are the leading eigenvectors
+// of K = S S^T (FP64 Gram; FP32 tridiagonal start; FP64 Ogita-Aishima
+// refinement of the full eigenbasis), then the CS split: W = eigenvectors of
+// Z1^T Z1 (the same two stages), alpha_i = ||Z1 w_i||, beta_i = ||Z2 w_i||.
 template <typename T>
 int small_gsvd(gsvd_rand_ctx* h, cudaStream_t st, DevStatus* st_dev, const T* S, int64_t ldn, int l1,
                int L, int64_t n, int r, SmallBufs& sb) {
-  // K = S S^T in FP64
   {
     ProfScope ps(h, GSVD_RAND_STAGE_SMALL_GRAM);
     CU((launch_dgemm_small<T, T>(L, L, (int)n, S, ldn, 0, S, ldn, 1, sb.K, L, 1.0, 0.0, sb.work,
@@ -367,23 +377,25 @@ int small_gsvd(gsvd_rand_ctx* h, cudaStream_t st, DevStatus* st_dev, const T* S,
   }
   {
     ProfScope ps(h, GSVD_RAND_STAGE_SMALL_JACOBI);
-    CU(launch_jacobi_f32(sb.K, L, sb.X, sb.lam, sb.jscratch, JACOBI_SWEEPS, st_dev, st));
+    CU(launch_eig_f32(sb.K, L, sb.X, sb.lam, sb.jscratch, st));
   }
   {
     ProfScope ps(h, GSVD_RAND_STAGE_SMALL_REFINE);
-    for (int it = 0; it < OA_ITERS; ++it) CU(launch_oa_refine(sb.K, L, sb.X, sb.lam, sb.work, sb.work_elems, st));
+    for (int it = 0; it < oa_iters<T>(); ++it) CU(launch_oa_refine(sb.K, L, sb.X, sb.lam, sb.work, sb.work_elems, st));
   }
   ProfScope ps_cs(h, GSVD_RAND_STAGE_SMALL_CS);
   CU(launch_select_topr(sb.X, sb.lam, L, r, sb.Zr, sb.order, st));
-  // C1 = Z1^T Z1, C2 = Z2^T Z2
+  const int l2 = L - l1;
+  const double* Z2 = sb.Zr + (int64_t)l1 * r;
   CU((launch_dgemm_small<double, double>(r, r, l1, sb.Zr, r, 1, sb.Zr, r, 0, sb.C1, r, 1.0, 0.0, sb.work,
                                          sb.work_elems, st)));
-  CU((launch_dgemm_small<double, double>(r, r, L - l1, sb.Zr + (int64_t)l1 * r, r, 1,
-                                         sb.Zr + (int64_t)l1 * r, r, 0, sb.C2, r, 1.0, 0.0, sb.work,
+  CU(launch_eig_f32(sb.C1, r, sb.Wv, sb.mu, sb.jscratch, st));
+  for (int it = 0; it < oa_iters<T>(); ++it) CU(launch_oa_refine(sb.C1, r, sb.Wv, sb.mu, sb.work, sb.work_elems, st));
+  CU((launch_dgemm_small<double, double>(l1, r, r, sb.Zr, r, 0, sb.Wv, r, 0, sb.U1, r, 1.0, 0.0, sb.work,
                                          sb.work_elems, st)));
-  CU(launch_jacobi_f32(sb.C1, r, sb.Wv, sb.mu, sb.jscratch, JACOBI_SWEEPS, st_dev, st));
-  for (int it = 0; it < OA_ITERS; ++it) CU(launch_oa_refine(sb.C1, r, sb.Wv, sb.mu, sb.work, sb.work_elems, st));
-  CU(launch_cs_finalize(sb.Wv, sb.C1, sb.C2, r, sb.alpha, sb.beta, st));
+  CU((launch_dgemm_small<double, double>(l2, r, r, Z2, r, 0, sb.Wv, r, 0, sb.U1 + (int64_t)l1 * r, r, 1.0, 0.0,
+                                         sb.work, sb.work_elems, st)));
+  CU(launch_cs_norms(sb.U1, l1, sb.U1 + (int64_t)l1 * r, l2, r, sb.alpha, sb.beta, st));
   return GSVD_RAND_OK;
 }
 
@@ -393,8 +405,15 @@ int solve_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, const voi
             int* r_out, double* resid_out) {
   cudaStream_t st = h->stream;
   const int prec = h->cfg.prec;
-  const bool use_tc = prec == GSVD_RAND_TF32 || prec == GSVD_RAND_BF16 || prec == GSVD_RAND_TF32X3;
+  if (prec == GSVD_RAND_BF16)
+    return fail(h, GSVD_RAND_ERR_UNSUPPORTED, "precision mode %d is not built yet", prec);
+  bool use_tc = prec == GSVD_RAND_TF32 || prec == GSVD_RAND_TF32X3;
   if (use_tc && !h->tc_ok) return fail(h, GSVD_RAND_ERR_UNSUPPORTED, "tensor-core path unavailable on this device");
+  // host inputs are staged with a 16-byte-multiple row stride; device inputs that
+  // TMA cannot address (unaligned base or row stride) run the CUDA-core FP32 products
+  const int64_t lds = round_up(n, 4);
+  bool d1 = is_device_ptr(G1v), d2 = is_device_ptr(G2v);
+  if (use_tc && ((d1 && !tc_shape_ok(G1v, ld1, k + os)) || (d2 && !tc_shape_ok(G2v, ld2, k + os)))) use_tc = false;
   Plan pl;
   pl.M[0] = m;
   pl.M[1] = p;
@@ -415,11 +434,10 @@ int solve_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, const voi
   pl.gpart_elems = (int64_t)std::max(gch, ach) * pl.l * pl.l;
 
   // host inputs are staged into the workspace
-  bool d1 = is_device_ptr(G1v), d2 = is_device_ptr(G2v);
   Bump sizer;
   sizer.take<DevStatus>(1);
-  if (!d1) sizer.take<T>(m * n);
-  if (!d2) sizer.take<T>(p * n);
+  if (!d1) sizer.take<T>(m * lds);
+  if (!d2) sizer.take<T>(p * lds);
   sizer.take<T>((int64_t)pl.L * pl.ldn);
   size_t b0 = sizer.off;
   size_t need = b0 + side_bytes<T>(pl, 0, use_tc) + side_bytes<T>(pl, 1, use_tc) + 4096;
@@ -436,16 +454,16 @@ int solve_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, const voi
   const T* G2 = (const T*)G2v;
   int64_t l1d = ld1, l2d = ld2;
   if (!d1) {
-    T* g = bp.take<T>(m * n);
-    CU(cudaMemcpy2DAsync(g, n * sizeof(T), G1v, ld1 * sizeof(T), n * sizeof(T), m, cudaMemcpyHostToDevice, st));
+    T* g = bp.take<T>(m * lds);
+    CU(cudaMemcpy2DAsync(g, lds * sizeof(T), G1v, ld1 * sizeof(T), n * sizeof(T), m, cudaMemcpyHostToDevice, st));
     G1 = g;
-    l1d = n;
+    l1d = lds;
   }
   if (!d2) {
-    T* g = bp.take<T>(p * n);
-    CU(cudaMemcpy2DAsync(g, n * sizeof(T), G2v, ld2 * sizeof(T), n * sizeof(T), p, cudaMemcpyHostToDevice, st));
+    T* g = bp.take<T>(p * lds);
+    CU(cudaMemcpy2DAsync(g, lds * sizeof(T), G2v, ld2 * sizeof(T), n * sizeof(T), p, cudaMemcpyHostToDevice, st));
     G2 = g;
-    l2d = n;
+    l2d = lds;
   }
   T* S = bp.take<T>((int64_t)pl.L * pl.ldn);
   SideBufs<T> sb0 = side_take<T>(bp, pl, 0, use_tc);

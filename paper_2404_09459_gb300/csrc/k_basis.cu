@@ -443,42 +443,50 @@ template cudaError_t launch_gram_partial<double>(const double*, int64_t, int64_t
 template cudaError_t launch_gram_partial<float>(const float*, int64_t, int64_t, int, double*, int,
                                                 int64_t, cudaStream_t);
 
+// W[i][j] = W[j][i] = sum_c part[c][min(i,j)][max(i,j)], one warp per entry
+// (fixed lane/shuffle order: deterministic).
 __global__ void gram_reduce_kernel(const double* __restrict__ part, int chunks, int l,
                                    double* __restrict__ W) {
-  int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= l * l) return;
-  int i = e / l, j = e % l;
-  int a = min(i, j), b = max(i, j);
-  const double* p = part + (int64_t)a * l + b;
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wid >= (int64_t)l * l) return;
+  const int i = (int)(wid / l), j = (int)(wid % l);
+  if (j < i) return;
+  const double* p = part + (int64_t)i * l + j;
   double s = 0.0;
-  for (int c = 0; c < chunks; ++c) s += p[(int64_t)c * l * l];
-  W[e] = s;
+  for (int c = lane; c < chunks; c += 32) s += p[(int64_t)c * l * l];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) {
+    W[(int64_t)i * l + j] = s;
+    W[(int64_t)j * l + i] = s;
+  }
 }
 
 cudaError_t launch_gram_reduce(const double* part, int chunks, int l, double* W, cudaStream_t st) {
-  gram_reduce_kernel<<<(unsigned)cdiv((int64_t)l * l, 256), 256, 0, st>>>(part, chunks, l, W);
+  const int64_t threads = (int64_t)l * l * 32;
+  gram_reduce_kernel<<<(unsigned)cdiv(threads, 256), 256, 0, st>>>(part, chunks, l, W);
   return launched();
 }
 
 // ============================================================================
-// Shifted Cholesky, one CTA, packed upper triangle in shared memory.
-// Right-looking with the unscaled pivot row (one barrier per step); rows are
-// scaled by 1/sqrt(pivot) at the end since no later step reads them.
+// Shifted Cholesky, one CTA of 32 x 32 threads, full storage (odd stride) in
+// shared memory: right-looking with the unscaled pivot row, one barrier per
+// step.  Then R^{-1} by back substitution, one warp per column.
 // ============================================================================
-__device__ __forceinline__ int up_idx(int i, int j, int l) { return i * l - (i * (i - 1)) / 2 + (j - i); }
-
 template <typename TC>
 __global__ __launch_bounds__(1024) void chol_shift_kernel(const double* __restrict__ W, int l,
                                                           double shift_coef, double tau_rel,
-                                                          TC* __restrict__ R, TC* __restrict__ rinv,
-                                                          DevStatus* st_dev, int stage) {
+                                                          TC* __restrict__ Rinv, DevStatus* st_dev,
+                                                          int stage, TC* gscr, int use_smem) {
   extern __shared__ unsigned char smem_raw[];
-  TC* A = reinterpret_cast<TC*>(smem_raw);
+  const int lda = l | 1;
+  TC* A = use_smem ? reinterpret_cast<TC*>(smem_raw) : gscr;  // l x lda: A, later R
+  TC* X = A + (int64_t)l * lda;                               // l x lda: R^{-1}
   __shared__ double s_shift;
   __shared__ int s_bad;
   __shared__ TC s_odiag[256];
   __shared__ unsigned char s_drop[256];
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
   if (tid == 0) {
     double tr = 0.0;
     bool fin = true;
@@ -492,43 +500,39 @@ __global__ __launch_bounds__(1024) void chol_shift_kernel(const double* __restri
   }
   __syncthreads();
   const double sh = s_shift;
-  for (int e = tid; e < l * l; e += nt) {
-    int i = e / l, j = e % l;
-    if (j >= i) {
-      double v = W[e] + (i == j ? sh : 0.0);
+  for (int i = ty; i < l; i += 32)
+    for (int j = tx; j < l; j += 32) {
+      double v = W[(int64_t)i * l + j] + (i == j ? sh : 0.0);
       if (!isfinite(v)) s_bad = 2;
-      A[up_idx(i, j, l)] = (TC)v;
+      A[(int64_t)i * lda + j] = (TC)v;
       if (i == j) {
         s_odiag[i] = (TC)v;
         s_drop[i] = 0;
       }
     }
-  }
   __syncthreads();
   int bad_k = -1;
   if (s_bad == 0) {
     for (int k = 0; k < l; ++k) {
-      TC d = A[up_idx(k, k, l)];
+      const TC d = A[(int64_t)k * lda + k];
       if (!isfinite(d)) {
         bad_k = k;
         break;
       }
-      // A pivot that is not above the Gram's resolution relative to its own
-      // column is numerically dependent on the previous columns: drop it (its
-      // column of Q becomes zero and adds a zero row to Q^T G).
+      // A pivot not above the Gram's resolution relative to its own column is
+      // numerically dependent on the previous columns: drop it (its column of
+      // Q becomes zero and adds a zero row to Q^T G).
       if (!(d > (TC)tau_rel * s_odiag[k])) {
         if (tid == 0) s_drop[k] = 1;
         continue;
       }
-      TC dinv = TC(1) / d;
-      int t = l - k - 1;
-      const TC* rowk = A + up_idx(k, k, l);  // rowk[j - k] = A[k][j]
-      for (int e = tid; e < t * t; e += nt) {
-        int ii = e / t, jj = e % t;
-        if (jj >= ii) {
-          int i = k + 1 + ii, j = k + 1 + jj;
-          A[up_idx(i, j, l)] -= rowk[i - k] * rowk[j - k] * dinv;
-        }
+      const TC dinv = TC(1) / d;
+      const TC* rowk = A + (int64_t)k * lda;
+      for (int i = k + 1 + ty; i < l; i += 32) {
+        const TC aki = rowk[i] * dinv;
+        TC* ai = A + (int64_t)i * lda;
+        for (int j = k + 1 + tx; j < l; j += 32)
+          if (j >= i) ai[j] -= aki * rowk[j];
       }
       __syncthreads();
     }
@@ -540,32 +544,55 @@ __global__ __launch_bounds__(1024) void chol_shift_kernel(const double* __restri
     if (tid == 0) set_status(st_dev, (s_bad == 2 || bad_k >= 0) ? -4 : -5, stage, bad_k);
     return;
   }
-  // scale rows, write R (zeros below the diagonal) and 1/R_kk (0 for dropped columns)
-  for (int e = tid; e < l * l; e += nt) {
-    int i = e / l, j = e % l;
-    TC v = TC(0);
+  // R = rows scaled by 1/sqrt(pivot) (rows of dropped pivots = e_k), in place
+  for (int i = ty; i < l; i += 32) {
     const bool dr = s_drop[i] != 0;
-    if (j >= i) {
-      if (dr) {
-        v = (j == i) ? TC(1) : TC(0);
-      } else {
-        TC rk = sqrt(A[up_idx(i, i, l)]);
-        v = (j == i) ? rk : A[up_idx(i, j, l)] / rk;
-      }
+    const TC rk = dr ? TC(1) : sqrt(A[(int64_t)i * lda + i]);
+    for (int j = tx; j < l; j += 32) {
+      TC v = TC(0);
+      if (j == i) v = rk;
+      else if (j > i && !dr) v = A[(int64_t)i * lda + j] / rk;
+      // written after every thread has read its pivot: separate pass below
+      X[(int64_t)i * lda + j] = v;
     }
-    R[e] = v;
-    if (j == i) rinv[i] = dr ? TC(0) : TC(1) / sqrt(A[up_idx(i, i, l)]);
   }
+  __syncthreads();
+  for (int i = ty; i < l; i += 32)
+    for (int j = tx; j < l; j += 32) A[(int64_t)i * lda + j] = X[(int64_t)i * lda + j];
+  __syncthreads();
+  // R^{-1}: column j by back substitution, X[i][j] = -(sum_{k=i+1..j} R[i][k] X[k][j]) / R[i][i]
+  for (int j = ty; j < l; j += 32) {
+    for (int i = j + 1 + tx; i < l; i += 32) X[(int64_t)i * lda + j] = TC(0);
+    if (tx == 0) X[(int64_t)j * lda + j] = TC(1) / A[(int64_t)j * lda + j];
+    __syncwarp();
+    for (int i = j - 1; i >= 0; --i) {
+      TC s = TC(0);
+      for (int k = i + 1 + tx; k <= j; k += 32) s += A[(int64_t)i * lda + k] * X[(int64_t)k * lda + j];
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (tx == 0) X[(int64_t)i * lda + j] = -s / A[(int64_t)i * lda + i];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  // dropped columns of Y contribute nothing: zero column k of R^{-1}
+  for (int i = ty; i < l; i += 32)
+    for (int j = tx; j < l; j += 32) {
+      TC v = (j >= i && !s_drop[j]) ? X[(int64_t)i * lda + j] : TC(0);
+      Rinv[(int64_t)i * l + j] = v;
+    }
 }
 
+int64_t chol_scratch_elems(int l) { return 2ll * l * (l | 1); }
+
 template <typename TC>
-cudaError_t launch_chol_shift(const double* W, int l, double shift_coef, double tau_rel, TC* R,
-                              TC* rinv, DevStatus* st_dev, int stage, cudaStream_t st) {
-  size_t smem = (size_t)l * (l + 1) / 2 * sizeof(TC);
-  if (smem > 200 * 1024 || l > 256) return cudaErrorInvalidValue;
+cudaError_t launch_chol_shift(const double* W, int l, double shift_coef, double tau_rel, TC* Rinv,
+                              TC* scratch, DevStatus* st_dev, int stage, cudaStream_t st) {
+  if (l < 1 || l > 256) return cudaErrorInvalidValue;
+  size_t smem = (size_t)chol_scratch_elems(l) * sizeof(TC);
+  int use_smem = smem <= 200 * 1024;
   cudaFuncSetAttribute(chol_shift_kernel<TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  int threads = l >= 64 ? 1024 : 256;
-  chol_shift_kernel<TC><<<1, threads, smem, st>>>(W, l, shift_coef, tau_rel, R, rinv, st_dev, stage);
+  chol_shift_kernel<TC><<<1, 1024, use_smem ? smem : 0, st>>>(W, l, shift_coef, tau_rel, Rinv, st_dev, stage,
+                                                              scratch, use_smem);
   return launched();
 }
 template cudaError_t launch_chol_shift<double>(const double*, int, double, double, double*, double*,
@@ -574,53 +601,62 @@ template cudaError_t launch_chol_shift<float>(const double*, int, double, double
                                               DevStatus*, int, cudaStream_t);
 
 // ============================================================================
-// Q = Y R^{-1}: each thread solves one row q R = y by forward substitution in
-// shared memory (four partial sums for ILP); optional fused Gram partial of
-// the produced rows and optional transposed store.
+// Q = Y R^{-1} (R^{-1} upper triangular, staged in shared memory) over a tile
+// of rows per CTA; optional Gram partial of the produced rows (one chunk per
+// CTA) and optional transposed store Qt[j * ldq + row].
 // ============================================================================
 int64_t apply_rows_per_cta(int l) { return l <= 64 ? 128 : (l <= 128 ? 64 : 32); }
 int apply_ctas(int64_t M, int l) { return (int)cdiv(M, apply_rows_per_cta(l)); }
 
 template <typename T, typename TC>
-__global__ void apply_rinv_kernel(const T* __restrict__ Y, int64_t ldy, int64_t M, int l,
-                                  const TC* __restrict__ R, const TC* __restrict__ rinv, T* Q,
-                                  int64_t ldq, int transpose_out, double* part, int64_t rpc) {
+__global__ __launch_bounds__(256) void apply_rinv_kernel(const T* __restrict__ Y, int64_t ldy, int64_t M, int l,
+                                                         const TC* __restrict__ Rinv, T* Q, int64_t ldq,
+                                                         int transpose_out, double* part, int64_t rpc,
+                                                         int r_smem) {
   extern __shared__ unsigned char smem_raw[];
-  T* Ys = reinterpret_cast<T*>(smem_raw);
-  const int ls = l + 1;  // odd stride: conflict-free row access
+  const int ls = l | 1;
+  // R^{-1} in shared memory when it fits next to the tiles, else read through L1
+  const int rld = r_smem ? ls : l;
+  TC* Rsm = reinterpret_cast<TC*>(smem_raw);
+  const TC* Rs = r_smem ? Rsm : Rinv;
+  T* Ys = reinterpret_cast<T*>(smem_raw + (r_smem ? (size_t)l * ls * sizeof(TC) : 0));  // rpc x ls
+  T* Qs = Ys + rpc * ls;                                                                 // rpc x ls
   const int tid = threadIdx.x, nt = blockDim.x;
   const int64_t r0 = (int64_t)blockIdx.x * rpc;
   const int rows = (int)(rpc < M - r0 ? rpc : M - r0);
+  if (r_smem)
+    for (int e = tid; e < l * l; e += nt) {
+      int i = e / l, j = e % l;
+      Rsm[i * ls + j] = Rinv[e];
+    }
   for (int e = tid; e < rows * l; e += nt) {
     int r = e / l, j = e % l;
     Ys[r * ls + j] = Y[(r0 + r) * ldy + j];
   }
   __syncthreads();
-  for (int r = tid; r < rows; r += nt) {
-    T* y = Ys + r * ls;
-    for (int j = 0; j < l; ++j) {
-      T a0 = y[j], a1 = T(0), a2 = T(0), a3 = T(0);
-      int k = 0;
-      for (; k + 3 < j; k += 4) {
-        a0 -= y[k] * (T)R[(int64_t)k * l + j];
-        a1 -= y[k + 1] * (T)R[(int64_t)(k + 1) * l + j];
-        a2 -= y[k + 2] * (T)R[(int64_t)(k + 2) * l + j];
-        a3 -= y[k + 3] * (T)R[(int64_t)(k + 3) * l + j];
-      }
-      for (; k < j; ++k) a0 -= y[k] * (T)R[(int64_t)k * l + j];
-      y[j] = ((a0 + a1) + (a2 + a3)) * (T)rinv[j];
+  // q[r][j] = sum_{i <= j} y[r][i] Rinv[i][j]; thread -> (r, j) with j fastest
+  for (int e = tid; e < rows * l; e += nt) {
+    const int r = e / l, j = e % l;
+    const T* y = Ys + r * ls;
+    T a0 = T(0), a1 = T(0);
+    int i = 0;
+    for (; i + 1 <= j; i += 2) {
+      a0 = fma(y[i], (T)Rs[i * rld + j], a0);
+      a1 = fma(y[i + 1], (T)Rs[(i + 1) * rld + j], a1);
     }
+    if (i <= j) a0 = fma(y[i], (T)Rs[i * rld + j], a0);
+    Qs[r * ls + j] = a0 + a1;
   }
   __syncthreads();
   if (transpose_out) {
     for (int e = tid; e < rows * l; e += nt) {
       int j = e / rows, r = e % rows;
-      Q[(int64_t)j * ldq + r0 + r] = Ys[r * ls + j];
+      Q[(int64_t)j * ldq + r0 + r] = Qs[r * ls + j];
     }
   } else {
     for (int e = tid; e < rows * l; e += nt) {
       int r = e / l, j = e % l;
-      Q[(r0 + r) * ldq + j] = Ys[r * ls + j];
+      Q[(r0 + r) * ldq + j] = Qs[r * ls + j];
     }
   }
   if (part) {
@@ -628,34 +664,39 @@ __global__ void apply_rinv_kernel(const T* __restrict__ Y, int64_t ldy, int64_t 
     for (int e = tid; e < l * l; e += nt) {
       int i = e / l, j = e % l;
       if (j < i) continue;
-      T s = T(0);
-      for (int r = 0; r < rows; ++r) s = fma(Ys[r * ls + i], Ys[r * ls + j], s);
-      P[e] = (double)s;
+      T s0 = T(0), s1 = T(0);
+      int r = 0;
+      for (; r + 1 < rows; r += 2) {
+        s0 = fma(Qs[r * ls + i], Qs[r * ls + j], s0);
+        s1 = fma(Qs[(r + 1) * ls + i], Qs[(r + 1) * ls + j], s1);
+      }
+      if (r < rows) s0 = fma(Qs[r * ls + i], Qs[r * ls + j], s0);
+      P[e] = (double)s0 + (double)s1;
     }
   }
 }
 
 template <typename T, typename TC>
-cudaError_t launch_apply_rinv(const T* Y, int64_t ldy, int64_t M, int l, const TC* R,
-                              const TC* rinv, T* Q, int64_t ldq, int transpose_out, double* part,
-                              cudaStream_t st) {
+cudaError_t launch_apply_rinv(const T* Y, int64_t ldy, int64_t M, int l, const TC* Rinv, T* Q, int64_t ldq,
+                              int transpose_out, double* part, cudaStream_t st) {
   int64_t rpc = apply_rows_per_cta(l);
-  size_t smem = (size_t)rpc * (l + 1) * sizeof(T);
+  const int ls = l | 1;
+  const size_t tiles = 2 * (size_t)rpc * ls * sizeof(T);
+  const size_t rbytes = (size_t)l * ls * sizeof(TC);
+  const int r_smem = tiles + rbytes <= 200 * 1024;
+  const size_t smem = tiles + (r_smem ? rbytes : 0);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   cudaFuncSetAttribute(apply_rinv_kernel<T, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   unsigned blocks = (unsigned)cdiv(M, rpc);
-  apply_rinv_kernel<T, TC><<<blocks, 256, smem, st>>>(Y, ldy, M, l, R, rinv, Q, ldq, transpose_out,
-                                                      part, rpc);
+  apply_rinv_kernel<T, TC><<<blocks, 256, smem, st>>>(Y, ldy, M, l, Rinv, Q, ldq, transpose_out, part, rpc,
+                                                      r_smem);
   return launched();
 }
-template cudaError_t launch_apply_rinv<double, double>(const double*, int64_t, int64_t, int,
-                                                       const double*, const double*, double*,
-                                                       int64_t, int, double*, cudaStream_t);
-template cudaError_t launch_apply_rinv<float, float>(const float*, int64_t, int64_t, int,
-                                                     const float*, const float*, float*, int64_t,
-                                                     int, double*, cudaStream_t);
-template cudaError_t launch_apply_rinv<float, double>(const float*, int64_t, int64_t, int,
-                                                      const double*, const double*, float*, int64_t,
-                                                      int, double*, cudaStream_t);
+template cudaError_t launch_apply_rinv<double, double>(const double*, int64_t, int64_t, int, const double*,
+                                                       double*, int64_t, int, double*, cudaStream_t);
+template cudaError_t launch_apply_rinv<float, float>(const float*, int64_t, int64_t, int, const float*, float*,
+                                                     int64_t, int, double*, cudaStream_t);
+template cudaError_t launch_apply_rinv<float, double>(const float*, int64_t, int64_t, int, const double*, float*,
+                                                      int64_t, int, double*, cudaStream_t);
 
 }  // namespace gsvdr

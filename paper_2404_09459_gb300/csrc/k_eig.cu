@@ -1,0 +1,321 @@
+// All eigenpairs of a small symmetric matrix in FP32, one CTA: the start that
+// the FP64 Ogita-Aishima refinement of the compressed-pair GSVD lifts to FP64.
+//
+//   1. Householder tridiagonalisation T = Q^T A Q (Golub & Van Loan, Alg. 8.3.1),
+//      the matrix-vector product one warp per row;
+//   2. every eigenvalue of T by Sturm-count bisection, one thread each;
+//   3. its eigenvector of T from the twisted factorisation of T - lambda I
+//      (stationary L D L^T from the top, U D U^T from the bottom, twist index
+//      at the smallest |gamma_k|; Dhillon & Parlett, Lin. Alg. Appl. 387, 2004),
+//      one thread each, rescaled on the fly against overflow;
+//   4. back-transformation X = Q Z, one warp per column;
+//   5. two-pass modified Gram-Schmidt: the columns that are numerically
+//      dependent (eigenvectors of a tight cluster) are set aside in the first
+//      pass and replaced in the second by pseudo-random vectors orthogonalised
+//      against all the others, so they span the cluster's invariant subspace.
+#include <algorithm>
+
+#include "kernels.h"
+
+namespace gsvdr {
+
+namespace {
+
+__device__ __forceinline__ float warp_sum(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sum; every thread receives the total.
+__device__ float block_sum_f(float v, float* red) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, ln = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (ln == 0) red[w] = v;
+  __syncthreads();
+  float s = 0.f;
+  for (int i = 0; i < nw; ++i) s += red[i];
+  return s;
+}
+
+// Number of eigenvalues of T (d, e2 = e^2) smaller than x.
+__device__ int sturm_count(const float* d, const float* e2, int N, float x, float pivmin) {
+  int c = 0;
+  float q = d[0] - x;
+  if (fabsf(q) < pivmin) q = -pivmin;
+  c += q < 0.f;
+  for (int i = 1; i < N; ++i) {
+    q = d[i] - x - e2[i - 1] / q;
+    if (fabsf(q) < pivmin) q = -pivmin;
+    c += q < 0.f;
+  }
+  return c;
+}
+
+__device__ __forceinline__ float hash_unit(uint32_t a, uint32_t b) {
+  uint32_t h = a * 0x9E3779B1u ^ (b + 0x7F4A7C15u) * 0x85EBCA77u;
+  h ^= h >> 15;
+  h *= 0x2C1B3C6Du;
+  h ^= h >> 12;
+  h *= 0x297A2D39u;
+  h ^= h >> 15;
+  return (float)(h >> 8) * 5.9604645e-08f - 0.5f;
+}
+
+}  // namespace
+
+int64_t eig_scratch_floats(int N) {
+  const int lda = N | 1;
+  return 2ll * N * lda + 8ll * N + 2ll * N * N;
+}
+
+__global__ __launch_bounds__(1024) void eig_f32_kernel(const double* __restrict__ Ain, int N,
+                                                       double* __restrict__ Xout, double* __restrict__ lam,
+                                                       float* __restrict__ gscr, int use_smem) {
+  extern __shared__ float sm[];
+  __shared__ float red[32];
+  __shared__ float s_scale, s_bound[2];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nwarp = nt >> 5;
+  const int lda = N | 1;  // odd stride: column walks are bank-conflict free
+  float* base = use_smem ? sm : gscr;
+  float* A = base;                       // N x lda: A, then the reflectors; later scratch
+  float* Z = A + (int64_t)N * lda;       // N x lda: eigenvectors (column j)
+  float* d = Z + (int64_t)N * lda;       // N
+  float* e = d + N;                      // N
+  float* e2 = e + N;                     // N
+  float* beta = e2 + N;                  // N
+  float* v = beta + N;                   // N  (reflector / projection coefficients)
+  float* p = v + N;                      // N
+  float* cf = p + N;                     // N  (MGS coefficients)
+  float* nrm = cf + N;                   // N  (column flags)
+  float* LU = use_smem ? gscr : base + 2ll * N * lda + 8ll * N;  // 2 N x N per-thread pivots
+
+  if (tid == 0) {
+    double mx = 0.0;
+    for (int i = 0; i < N; ++i) mx = fmax(mx, fabs(Ain[(int64_t)i * N + i]));
+    s_scale = (float)(mx > 0.0 && isfinite(mx) ? mx : 1.0);
+  }
+  __syncthreads();
+  const float inv = 1.0f / s_scale;
+  for (int i = warp; i < N; i += nwarp)
+    for (int j = lane; j < N; j += 32) A[(int64_t)i * lda + j] = (float)(Ain[(int64_t)i * N + j] * (double)inv);
+  __syncthreads();
+
+  // ---- 1. tridiagonalisation: reflector k zeroes A[k+2:, k] ------------------
+  for (int k = 0; k + 2 < N; ++k) {
+    const int m = N - k - 1;
+    const float x0 = A[(int64_t)(k + 1) * lda + k];
+    float part = 0.f;
+    for (int i = tid; i < m; i += nt) {
+      float xi = A[(int64_t)(k + 1 + i) * lda + k];
+      part += xi * xi;
+    }
+    const float sig2 = block_sum_f(part, red);
+    const float sig = sqrtf(sig2);
+    const float alpha = x0 >= 0.f ? -sig : sig;  // H x = alpha e1
+    const float vtv = 2.f * (sig2 - x0 * alpha);
+    const float bk = (sig > 0.f && vtv > 0.f) ? 2.f / vtv : 0.f;
+    for (int i = tid; i < m; i += nt) v[i] = (i == 0) ? (x0 - alpha) : A[(int64_t)(k + 1 + i) * lda + k];
+    if (tid == 0) {
+      beta[k] = bk;
+      e[k] = (bk > 0.f) ? alpha : x0;
+    }
+    __syncthreads();
+    if (bk > 0.f) {
+      // p = bk A22 v, one warp per row
+      for (int i = warp; i < m; i += nwarp) {
+        const float* ai = A + (int64_t)(k + 1 + i) * lda + (k + 1);
+        float s = 0.f;
+        for (int j = lane; j < m; j += 32) s = fmaf(ai[j], v[j], s);
+        s = warp_sum(s);
+        if (lane == 0) p[i] = bk * s;
+      }
+      __syncthreads();
+      float pv = 0.f;
+      for (int i = tid; i < m; i += nt) pv += p[i] * v[i];
+      const float kk = 0.5f * bk * block_sum_f(pv, red);
+      for (int i = tid; i < m; i += nt) p[i] -= kk * v[i];  // p := w = p - (bk/2)(p^T v) v
+      __syncthreads();
+      for (int i = warp; i < m; i += nwarp) {
+        float* ai = A + (int64_t)(k + 1 + i) * lda + (k + 1);
+        const float vi = v[i], wi = p[i];
+        for (int j = lane; j < m; j += 32) ai[j] -= vi * p[j] + wi * v[j];
+      }
+    }
+    // keep the reflector in column k below the diagonal
+    for (int i = tid; i < m; i += nt) A[(int64_t)(k + 1 + i) * lda + k] = v[i];
+    __syncthreads();
+  }
+  for (int i = tid; i < N; i += nt) d[i] = A[(int64_t)i * lda + i];
+  if (tid == 0) {
+    if (N >= 2) e[N - 2] = A[(int64_t)(N - 1) * lda + (N - 2)];
+    for (int k = (N >= 2 ? N - 2 : 0); k < N; ++k) beta[k] = 0.f;
+  }
+  __syncthreads();
+  for (int i = tid; i < N - 1; i += nt) e2[i] = e[i] * e[i];
+  if (tid == 0) {
+    float lo = d[0], hi = d[0];
+    for (int i = 0; i < N; ++i) {
+      float rad = (i > 0 ? fabsf(e[i - 1]) : 0.f) + (i < N - 1 ? fabsf(e[i]) : 0.f);
+      lo = fminf(lo, d[i] - rad);
+      hi = fmaxf(hi, d[i] + rad);
+    }
+    float pad = 1e-6f * fmaxf(fabsf(lo), fabsf(hi)) + 1e-30f;
+    s_bound[0] = lo - pad;
+    s_bound[1] = hi + pad;
+  }
+  __syncthreads();
+  const float tnorm = fmaxf(fabsf(s_bound[0]), fabsf(s_bound[1]));
+  const float pivmin = fmaxf(1e-30f, 1e-12f * tnorm);
+  const float atol = 4.f * 5.96e-8f * tnorm;
+
+  // ---- 2 + 3. eigenvalue j (ascending) and its tridiagonal eigenvector -------
+  for (int j = tid; j < N; j += nt) {
+    float lo = s_bound[0], hi = s_bound[1];
+    for (int it = 0; it < 64; ++it) {
+      const float mid = 0.5f * (lo + hi);
+      if (mid <= lo || mid >= hi || hi - lo <= atol) break;
+      if (sturm_count(d, e2, N, mid, pivmin) > j)
+        hi = mid;
+      else
+        lo = mid;
+    }
+    const float lm = 0.5f * (lo + hi);
+    lam[j] = (double)lm * (double)s_scale;
+    float* L = LU + (int64_t)j * N;
+    float* U = LU + (int64_t)N * N + (int64_t)j * N;
+    float dp = d[0] - lm;
+    if (fabsf(dp) < pivmin) dp = -pivmin;
+    L[0] = dp;
+    for (int i = 0; i + 1 < N; ++i) {
+      dp = d[i + 1] - lm - (e[i] / dp) * e[i];
+      if (fabsf(dp) < pivmin) dp = -pivmin;
+      L[i + 1] = dp;
+    }
+    float dm = d[N - 1] - lm;
+    if (fabsf(dm) < pivmin) dm = -pivmin;
+    U[N - 1] = dm;
+    for (int i = N - 2; i >= 0; --i) {
+      dm = d[i] - lm - (e[i] / dm) * e[i];
+      if (fabsf(dm) < pivmin) dm = -pivmin;
+      U[i] = dm;
+    }
+    int kt = 0;
+    float best = 3.4e38f;
+    for (int i = 0; i < N; ++i) {
+      const float g = fabsf(L[i] + U[i] - (d[i] - lm));
+      if (g < best) {
+        best = g;
+        kt = i;
+      }
+    }
+    // z_kt = 1; z_i = -(e_i / d+_i) z_{i+1} upward; z_{i+1} = -(e_i / d-_{i+1}) z_i downward.
+    // Entries are rescaled when they grow past 2^60 (the direction is what matters).
+    Z[(int64_t)kt * lda + j] = 1.f;
+    float z = 1.f;
+    for (int i = kt - 1; i >= 0; --i) {
+      z = -(e[i] / L[i]) * z;
+      if (fabsf(z) > 1.15e18f) {
+        for (int t = i + 1; t <= kt; ++t) Z[(int64_t)t * lda + j] *= 8.67e-19f;
+        z *= 8.67e-19f;
+      }
+      Z[(int64_t)i * lda + j] = z;
+    }
+    z = Z[(int64_t)kt * lda + j];
+    for (int i = kt; i + 1 < N; ++i) {
+      z = -(e[i] / U[i + 1]) * z;
+      if (fabsf(z) > 1.15e18f) {
+        for (int t = 0; t <= i; ++t) Z[(int64_t)t * lda + j] *= 8.67e-19f;
+        z *= 8.67e-19f;
+      }
+      Z[(int64_t)(i + 1) * lda + j] = z;
+    }
+    float s = 0.f;
+    for (int i = 0; i < N; ++i) s = fmaf(Z[(int64_t)i * lda + j], Z[(int64_t)i * lda + j], s);
+    const bool ok = s > 0.f && isfinite(s);
+    const float sc = ok ? rsqrtf(s) : 0.f;
+    for (int i = 0; i < N; ++i) Z[(int64_t)i * lda + j] = ok ? Z[(int64_t)i * lda + j] * sc : (i == j ? 1.f : 0.f);
+  }
+  __syncthreads();
+
+  // ---- 4. X = H_0 ... H_{N-3} Z, one warp per column (no block barriers) -----
+  for (int j = warp; j < N; j += nwarp) {
+    for (int k = N - 3; k >= 0; --k) {
+      const float bk = beta[k];
+      if (bk == 0.f) continue;
+      const int m = N - k - 1;
+      float s = 0.f;
+      for (int i = lane; i < m; i += 32) s = fmaf(A[(int64_t)(k + 1 + i) * lda + k], Z[(int64_t)(k + 1 + i) * lda + j], s);
+      s = warp_sum(s) * bk;
+      for (int i = lane; i < m; i += 32) Z[(int64_t)(k + 1 + i) * lda + j] -= s * A[(int64_t)(k + 1 + i) * lda + k];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+
+  // ---- 5. two-pass MGS on the columns, dependent ones replaced last ----------
+  // pass 0 orthonormalises the independent columns and flags the others (nrm = -1);
+  // pass 1 replaces each flagged column by a pseudo-random vector orthogonalised
+  // (twice) against every column already accepted.
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int j = 0; j < N; ++j) {
+      if (pass == 1) {
+        if (nrm[j] >= 0.f) continue;
+        for (int i = tid; i < N; i += nt) Z[(int64_t)i * lda + j] = hash_unit((uint32_t)j, (uint32_t)i);
+        __syncthreads();
+      }
+      float n0 = 0.f;
+      for (int i = tid; i < N; i += nt) n0 = fmaf(Z[(int64_t)i * lda + j], Z[(int64_t)i * lda + j], n0);
+      n0 = block_sum_f(n0, red);
+      for (int rep = 0; rep < 2; ++rep) {
+        // coefficients against accepted columns c (pass 0: c < j; pass 1: all c != j not flagged)
+        for (int c = warp; c < N; c += nwarp) {
+          const bool acc = (c != j) && (pass == 0 ? (c < j && nrm[c] >= 0.f) : (nrm[c] >= 0.f));
+          float s = 0.f;
+          if (acc)
+            for (int i = lane; i < N; i += 32) s = fmaf(Z[(int64_t)i * lda + c], Z[(int64_t)i * lda + j], s);
+          s = warp_sum(s);
+          if (lane == 0) cf[c] = acc ? s : 0.f;
+        }
+        __syncthreads();
+        for (int i = tid; i < N; i += nt) {
+          float s = 0.f;
+          for (int c = 0; c < N; ++c) s = fmaf(Z[(int64_t)i * lda + c], cf[c], s);
+          p[i] = s;
+        }
+        __syncthreads();
+        for (int i = tid; i < N; i += nt) Z[(int64_t)i * lda + j] -= p[i];
+        __syncthreads();
+      }
+      float n1 = 0.f;
+      for (int i = tid; i < N; i += nt) n1 = fmaf(Z[(int64_t)i * lda + j], Z[(int64_t)i * lda + j], n1);
+      n1 = block_sum_f(n1, red);
+      // dependent if less than ~1e-3 of its length survives the projection
+      const bool dep = !(n1 > 1e-6f * n0) || !(n1 > 0.f);
+      if (pass == 0 && dep) {
+        if (tid == 0) nrm[j] = -1.f;
+        for (int i = tid; i < N; i += nt) Z[(int64_t)i * lda + j] = 0.f;
+      } else {
+        const float sc = rsqrtf(n1 > 0.f ? n1 : 1.f);
+        for (int i = tid; i < N; i += nt) Z[(int64_t)i * lda + j] *= sc;
+        if (tid == 0) nrm[j] = 1.f;
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = warp; i < N; i += nwarp)
+    for (int j = lane; j < N; j += 32) Xout[(int64_t)i * N + j] = (double)Z[(int64_t)i * lda + j];
+}
+
+cudaError_t launch_eig_f32(const double* A, int N, double* X, double* lam, float* scratch, cudaStream_t st) {
+  if (N < 1 || N > 1024) return cudaErrorInvalidValue;
+  const int lda = N | 1;
+  const size_t smem = (2ull * N * lda + 8ull * N) * sizeof(float);
+  const int use_smem = smem <= 200 * 1024;
+  cudaFuncSetAttribute(eig_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  eig_f32_kernel<<<1, 1024, use_smem ? smem : 0, st>>>(A, N, X, lam, scratch, use_smem);
+  return launched();
+}
+
+}  // namespace gsvdr

@@ -19,6 +19,9 @@ namespace gsvdr {
 // FP64 split-K GEMM for small operands: C = alpha op(A) op(B) + beta C.
 // ============================================================================
 constexpr int SG_T = 32, SG_BK = 32;
+// The tile loader maps e -> (e / 32, e % 32) onto both operand tiles: square 32 x 32.
+static_assert(SG_T == 32 && SG_BK == 32, "dgemm_small_kernel's loader assumes 32 x 32 tiles");
+constexpr int SG_KGRAIN = 8;  // split-K chunks are multiples of 8 (partial tiles are zero-filled)
 
 template <typename TA, typename TB>
 __global__ __launch_bounds__(256) void dgemm_small_kernel(int Mr, int Nc, int K, const TA* __restrict__ A,
@@ -51,8 +54,9 @@ __global__ __launch_bounds__(256) void dgemm_small_kernel(int Mr, int Nc, int K,
       Bs[kk][j] = vb;
     }
     __syncthreads();
+    const int kk_end = min(SG_BK, ke - k0);
 #pragma unroll 8
-    for (int kk = 0; kk < SG_BK; ++kk) {
+    for (int kk = 0; kk < kk_end; ++kk) {
       double a0 = As[kk][ty * 2], a1 = As[kk][ty * 2 + 1];
       double b0 = Bs[kk][tx * 2], b1 = Bs[kk][tx * 2 + 1];
       acc[0][0] = fma(a0, b0, acc[0][0]);
@@ -87,11 +91,11 @@ cudaError_t launch_dgemm_small(int Mr, int Nc, int K, const TA* A, int64_t lda, 
                                double* work, int64_t work_elems, cudaStream_t st) {
   if (Mr <= 0 || Nc <= 0) return cudaSuccess;
   int tiles = (int)(cdiv(Mr, SG_T) * cdiv(Nc, SG_T));
-  int kslices = (int)cdiv(std::max(K, 1), SG_BK);
+  int kslices = (int)cdiv(std::max(K, 1), SG_KGRAIN);
   int splits = std::max(1, std::min(kslices, (2 * 152 + tiles - 1) / tiles));
   while (splits > 1 && (int64_t)splits * Mr * Nc > work_elems) --splits;
   if ((int64_t)Mr * Nc > work_elems) return cudaErrorInvalidValue;
-  int kchunk = (int)round_up(cdiv(std::max(K, 1), splits), SG_BK);
+  int kchunk = (int)round_up(cdiv(std::max(K, 1), splits), SG_KGRAIN);
   splits = (int)cdiv(std::max(K, 1), kchunk);
   dim3 grid((unsigned)cdiv(Mr, SG_T), (unsigned)cdiv(Nc, SG_T), (unsigned)splits);
   dgemm_small_kernel<TA, TB><<<grid, 256, 0, st>>>(Mr, Nc, K, A, lda, ta, B, ldb, tb, work, kchunk);
@@ -115,7 +119,7 @@ template cudaError_t launch_dgemm_small<float, float>(int, int, int, const float
 // in Golub & Van Loan, Algorithm 8.5.1 (sym.schur2).  A and V live in shared
 // memory when they fit, else in the global scratch (L2-resident).
 // ============================================================================
-int64_t jacobi_scratch_floats(int N) { return 2ll * N * N; }
+int64_t jacobi_scratch_floats(int N) { return 2ll * N * (N | 1); }
 
 __global__ __launch_bounds__(1024) void jacobi_f32_kernel(const double* __restrict__ Ain, int N,
                                                           double* __restrict__ Vout,
@@ -124,38 +128,36 @@ __global__ __launch_bounds__(1024) void jacobi_f32_kernel(const double* __restri
                                                           DevStatus* st_dev) {
   extern __shared__ float sm[];
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nwarp = nt >> 5;
   const int Np = N + (N & 1), m = Np / 2;
+  const int lda = N | 1;  // odd row stride: column walks are bank-conflict free
   float* A = use_smem ? sm : scratch;
-  float* V = use_smem ? sm + (int64_t)N * N : scratch + (int64_t)N * N;
-  // per-round pair tables live after A, V in shared memory when possible
-  __shared__ int s_top[256], s_bot[256];
+  float* V = A + (int64_t)N * lda;
+  __shared__ int s_p[256], s_q[256];
   __shared__ float s_c[256], s_s[256];
   __shared__ float s_scale;
-  __shared__ unsigned s_off;  // max relative off-diagonal of the sweep, as float bits
+  __shared__ unsigned s_off;  // max |a_pq| of the sweep (scaled A), as float bits
   if (tid == 0) {
     double mx = 0.0;
     for (int i = 0; i < N; ++i) mx = fmax(mx, fabs(Ain[(int64_t)i * N + i]));
-    s_scale = (float)(mx > 0.0 ? mx : 1.0);
-  }
-  for (int k = tid; k < m; k += nt) {
-    s_top[k] = 2 * k;
-    s_bot[k] = 2 * k + 1;
+    s_scale = (float)(mx > 0.0 && isfinite(mx) ? mx : 1.0);
   }
   __syncthreads();
   const float inv = 1.0f / s_scale;
-  for (int64_t e = tid; e < (int64_t)N * N; e += nt) {
-    A[e] = (float)(Ain[e] * (double)inv);
-    V[e] = ((e / N) == (e % N)) ? 1.0f : 0.0f;
-  }
+  for (int i = warp; i < N; i += nwarp)
+    for (int j = lane; j < N; j += 32) {
+      A[(int64_t)i * lda + j] = (float)(Ain[(int64_t)i * N + j] * (double)inv);
+      V[(int64_t)i * lda + j] = (i == j) ? 1.0f : 0.0f;
+    }
   __syncthreads();
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
     if (tid == 0) s_off = 0u;
     __syncthreads();
     for (int rnd = 0; rnd < Np - 1; ++rnd) {
-      // round-robin (circle method): slot Np-1 is fixed, pairs (rnd, Np-1) and
-      // ((rnd + k) mod (Np-1), (rnd - k) mod (Np-1)), k = 1..m-1 are disjoint and
-      // every pair meets once in Np-1 rounds.
+      // phase A: the round's disjoint pairs (circle method: slot Np-1 fixed;
+      // pairs (rnd, Np-1) and ((rnd + k) mod (Np-1), (rnd - k) mod (Np-1)); every
+      // pair meets once in Np-1 rounds) and their rotation parameters.
       for (int k = tid; k < m; k += nt) {
         int a, b;
         if (k == 0) {
@@ -165,16 +167,10 @@ __global__ __launch_bounds__(1024) void jacobi_f32_kernel(const double* __restri
           a = (rnd + k) % (Np - 1);
           b = (rnd - k + (Np - 1)) % (Np - 1);
         }
-        s_top[k] = min(a, b);
-        s_bot[k] = max(a, b);
-      }
-      __syncthreads();
-      // phase A: rotation parameters for the m disjoint pairs
-      for (int k = tid; k < m; k += nt) {
-        int p = s_top[k], q = s_bot[k];
+        const int p = min(a, b), q = max(a, b);
         float c = 1.f, s = 0.f;
         if (q < N) {
-          float apq = A[(int64_t)p * N + q], app = A[(int64_t)p * N + p], aqq = A[(int64_t)q * N + q];
+          float apq = A[(int64_t)p * lda + q], app = A[(int64_t)p * lda + p], aqq = A[(int64_t)q * lda + q];
           // A is scaled to max |a_ii| = 1: an absolute off-diagonal test.  The FP32
           // result only needs absolute accuracy ~u ||A|| (the FP64 refinement
           // takes it from there); a relative test would never stop on the
@@ -188,36 +184,42 @@ __global__ __launch_bounds__(1024) void jacobi_f32_kernel(const double* __restri
             s = t * c;
           }
         }
+        s_p[k] = p;
+        s_q[k] = q;
         s_c[k] = c;
         s_s[k] = s;
       }
       __syncthreads();
-      // phase B: columns p, q of A and V (A <- A J, V <- V J)
-      for (int e = tid; e < m * N; e += nt) {
-        int k = e / N, i = e % N;
-        float c = s_c[k], s = s_s[k];
+      // phase B: columns p, q of A and V (A <- A J, V <- V J); warp per pair, lane per row
+      for (int k = warp; k < m; k += nwarp) {
+        const float c = s_c[k], s = s_s[k];
         if (s == 0.f) continue;
-        int p = s_top[k], q = s_bot[k];
-        float* ai = A + (int64_t)i * N;
-        float x = ai[p], y = ai[q];
-        ai[p] = c * x - s * y;
-        ai[q] = s * x + c * y;
-        float* vi = V + (int64_t)i * N;
-        x = vi[p];
-        y = vi[q];
-        vi[p] = c * x - s * y;
-        vi[q] = s * x + c * y;
+        const int p = s_p[k], q = s_q[k];
+        for (int i = lane; i < N; i += 32) {
+          float* ai = A + (int64_t)i * lda;
+          float x = ai[p], y = ai[q];
+          ai[p] = c * x - s * y;
+          ai[q] = s * x + c * y;
+          float* vi = V + (int64_t)i * lda;
+          x = vi[p];
+          y = vi[q];
+          vi[p] = c * x - s * y;
+          vi[q] = s * x + c * y;
+        }
       }
       __syncthreads();
-      // phase C: rows p, q of A (A <- J^T A); the annihilated entries are zero
-      for (int e = tid; e < m * N; e += nt) {
-        int k = e / N, j = e % N;
-        float c = s_c[k], s = s_s[k];
+      // phase C: rows p, q of A (A <- J^T A); the annihilated entries are set to zero
+      for (int k = warp; k < m; k += nwarp) {
+        const float c = s_c[k], s = s_s[k];
         if (s == 0.f) continue;
-        int p = s_top[k], q = s_bot[k];
-        float x = A[(int64_t)p * N + j], y = A[(int64_t)q * N + j];
-        A[(int64_t)p * N + j] = (j == q) ? 0.f : c * x - s * y;
-        A[(int64_t)q * N + j] = (j == p) ? 0.f : s * x + c * y;
+        const int p = s_p[k], q = s_q[k];
+        float* ap = A + (int64_t)p * lda;
+        float* aq = A + (int64_t)q * lda;
+        for (int j = lane; j < N; j += 32) {
+          float x = ap[j], y = aq[j];
+          ap[j] = (j == q) ? 0.f : c * x - s * y;
+          aq[j] = (j == p) ? 0.f : s * x + c * y;
+        }
       }
       __syncthreads();
     }
@@ -227,17 +229,18 @@ __global__ __launch_bounds__(1024) void jacobi_f32_kernel(const double* __restri
     if (off < 1e-7f) break;
   }
   if (sweep == max_sweeps && tid == 0 && st_dev) {
-    // not converged to FP32 level: refinement will still improve, record only
+    // not converged to FP32 level: the refinement still improves it; counted only
     atomicAdd(&st_dev->pad, 1);
   }
-  for (int64_t e = tid; e < (int64_t)N * N; e += nt) Vout[e] = (double)V[e];
-  for (int i = tid; i < N; i += nt) lam[i] = (double)A[(int64_t)i * N + i] * (double)s_scale;
+  for (int i = warp; i < N; i += nwarp)
+    for (int j = lane; j < N; j += 32) Vout[(int64_t)i * N + j] = (double)V[(int64_t)i * lda + j];
+  for (int i = tid; i < N; i += nt) lam[i] = (double)A[(int64_t)i * lda + i] * (double)s_scale;
 }
 
 cudaError_t launch_jacobi_f32(const double* A, int N, double* V, double* lam, float* scratch,
                               int max_sweeps, DevStatus* st_dev, cudaStream_t st) {
   if (N < 1 || N > 512) return cudaErrorInvalidValue;
-  size_t need = 2ull * N * N * sizeof(float);
+  size_t need = (size_t)jacobi_scratch_floats(N) * sizeof(float);
   int use_smem = need <= 200 * 1024;
   size_t smem = use_smem ? need : 0;
   cudaFuncSetAttribute(jacobi_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -252,25 +255,20 @@ cudaError_t launch_jacobi_f32(const double* A, int N, double* V, double* lam, fl
 //   F_ij = (s_ij + lam_j r_ij) / (lam_j - lam_i) if |lam_i - lam_j| > delta, else r_ij / 2,
 //   F_ii = r_ii / 2.
 // ============================================================================
-__global__ __launch_bounds__(1024) void oa_form_kernel(const double* __restrict__ A, int N,
-                                                       const double* __restrict__ XtX,
-                                                       const double* __restrict__ S,
-                                                       double* __restrict__ F, double* __restrict__ lam) {
-  __shared__ double red[3][32];
-  __shared__ double s_delta;
-  extern __shared__ double sl[];  // N eigenvalue estimates
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int i = tid; i < N; i += nt) {
-    double rii = 1.0 - XtX[(int64_t)i * N + i];
-    sl[i] = S[(int64_t)i * N + i] / (1.0 - rii);
-  }
-  __syncthreads();
+// Partial Frobenius sums of A, R = I - X^T X and S - diag(lam) per CTA; CTA 0
+// also writes lam_i = s_ii / (x_i^T x_i) (= s_ii / (1 - r_ii)).
+__global__ void oa_norms_kernel(const double* __restrict__ A, int N, const double* __restrict__ XtX,
+                                const double* __restrict__ S, double* __restrict__ part,
+                                double* __restrict__ lam) {
+  __shared__ double red[3][8];
+  const int64_t nn = (int64_t)N * N;
   double a2 = 0.0, r2 = 0.0, s2 = 0.0;
-  for (int64_t e = tid; e < (int64_t)N * N; e += nt) {
-    int i = (int)(e / N), j = (int)(e % N);
-    double a = A[e];
-    double r = (i == j ? 1.0 : 0.0) - XtX[e];
-    double sd = S[e] - (i == j ? sl[i] : 0.0);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nn; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / N), j = (int)(e % N);
+    const double a = A[e];
+    const double r = (i == j ? 1.0 : 0.0) - XtX[e];
+    double sd = S[e];
+    if (i == j) sd -= S[e] / XtX[e];
     a2 += a * a;
     r2 += r * r;
     s2 += sd * sd;
@@ -280,48 +278,65 @@ __global__ __launch_bounds__(1024) void oa_form_kernel(const double* __restrict_
     r2 += __shfl_down_sync(0xffffffffu, r2, o);
     s2 += __shfl_down_sync(0xffffffffu, s2, o);
   }
-  if ((tid & 31) == 0) {
-    red[0][tid >> 5] = a2;
-    red[1][tid >> 5] = r2;
-    red[2][tid >> 5] = s2;
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = a2;
+    red[1][threadIdx.x >> 5] = r2;
+    red[2][threadIdx.x >> 5] = s2;
   }
   __syncthreads();
-  if (tid == 0) {
+  if (threadIdx.x < 3) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[threadIdx.x][w];
+    part[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = t;
+  }
+  if (blockIdx.x == 0)
+    for (int i = threadIdx.x; i < N; i += blockDim.x) lam[i] = S[(int64_t)i * N + i] / XtX[(int64_t)i * N + i];
+}
+
+// F_ij = (s_ij + lam_j r_ij) / (lam_j - lam_i) if |lam_i - lam_j| > delta else r_ij / 2,
+// delta = 2 (||S - D||_F + ||A||_F ||R||_F) from the partial sums.
+__global__ void oa_form_kernel(int N, const double* __restrict__ XtX, const double* __restrict__ S,
+                               const double* __restrict__ part, int nparts, const double* __restrict__ lam,
+                               double* __restrict__ F) {
+  __shared__ double s_delta;
+  if (threadIdx.x == 0) {
     double A2 = 0, R2 = 0, S2 = 0;
-    for (int w = 0; w < (nt + 31) / 32; ++w) {
-      A2 += red[0][w];
-      R2 += red[1][w];
-      S2 += red[2][w];
+    for (int b = 0; b < nparts; ++b) {
+      A2 += part[b];
+      R2 += part[nparts + b];
+      S2 += part[2 * nparts + b];
     }
     s_delta = 2.0 * (sqrt(S2) + sqrt(A2) * sqrt(R2));
   }
   __syncthreads();
   const double delta = s_delta;
-  for (int64_t e = tid; e < (int64_t)N * N; e += nt) {
-    int i = (int)(e / N), j = (int)(e % N);
-    double r = (i == j ? 1.0 : 0.0) - XtX[e];
+  const int64_t nn = (int64_t)N * N;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nn; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / N), j = (int)(e % N);
+    const double r = (i == j ? 1.0 : 0.0) - XtX[e];
     double f;
     if (i == j) {
       f = 0.5 * r;
     } else {
-      double d = sl[j] - sl[i];
-      f = (fabs(d) > delta) ? (S[e] + sl[j] * r) / d : 0.5 * r;
+      const double d = lam[j] - lam[i];
+      f = (fabs(d) > delta) ? (S[e] + lam[j] * r) / d : 0.5 * r;
     }
     F[e] = f;
   }
-  for (int i = tid; i < N; i += nt) lam[i] = sl[i];
 }
 
 cudaError_t launch_oa_refine(const double* A, int N, double* X, double* lam, double* work,
                              int64_t work_elems, cudaStream_t st) {
-  int64_t nn = (int64_t)N * N;
-  if (work_elems < 4 * nn + nn) return cudaErrorInvalidValue;
+  const int64_t nn = (int64_t)N * N;
+  const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(128, cdiv(nn, 1024)));
+  if (work_elems < 4 * nn + 3 * nb + nn) return cudaErrorInvalidValue;
   double* XtX = work;
   double* P = work + nn;
   double* S = work + 2 * nn;
   double* F = work + 3 * nn;
-  double* sk = work + 4 * nn;
-  int64_t skn = work_elems - 4 * nn;
+  double* part = work + 4 * nn;
+  double* sk = part + 3 * nb;
+  const int64_t skn = work_elems - 4 * nn - 3 * nb;
   cudaError_t e;
   if ((e = launch_dgemm_small<double, double>(N, N, N, X, N, 1, X, N, 0, XtX, N, 1.0, 0.0, sk, skn, st)))
     return e;
@@ -329,7 +344,9 @@ cudaError_t launch_oa_refine(const double* A, int N, double* X, double* lam, dou
     return e;
   if ((e = launch_dgemm_small<double, double>(N, N, N, X, N, 1, P, N, 0, S, N, 1.0, 0.0, sk, skn, st)))
     return e;
-  oa_form_kernel<<<1, 1024, (size_t)N * sizeof(double), st>>>(A, N, XtX, S, F, lam);
+  oa_norms_kernel<<<nb, 256, 0, st>>>(A, N, XtX, S, part, lam);
+  if ((e = launched())) return e;
+  oa_form_kernel<<<nb, 256, 0, st>>>(N, XtX, S, part, nb, lam, F);
   if ((e = launched())) return e;
   // X <- X + X F   (the reduce of the split-K product reads and writes X elementwise)
   return launch_dgemm_small<double, double>(N, N, N, X, N, 0, F, N, 0, X, N, 1.0, 1.0, sk, skn, st);
@@ -370,38 +387,28 @@ cudaError_t launch_select_topr(const double* X, const double* lam, int N, int r,
   return launched();
 }
 
-// alpha_i^2 = w_i^T C1 w_i / w_i^T w_i, beta_i^2 = w_i^T C2 w_i / w_i^T w_i, pairs
-// sorted by alpha non-increasing (beta then non-decreasing, eq. (ab)).
-__global__ void cs_finalize_kernel(const double* __restrict__ Wm, const double* __restrict__ C1,
-                                   const double* __restrict__ C2, int r, double* __restrict__ alpha,
-                                   double* __restrict__ beta) {
-  extern __shared__ double sm2[];
-  double* sa = sm2;
-  double* sb = sm2 + r;
+// alpha_i = ||U1[:, i]||, beta_i = ||U2[:, i]|| (U1 = Z1 W, U2 = Z2 W), normalised to
+// alpha^2 + beta^2 = 1, sorted by alpha non-increasing (eq. (ab)).
+__global__ void cs_norms_kernel(const double* __restrict__ U1, int l1, const double* __restrict__ U2, int l2,
+                                int r, double* __restrict__ alpha, double* __restrict__ beta) {
+  extern __shared__ double sab[];
+  double* sa = sab;
+  double* sb = sab + r;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int i = tid; i < r; i += nt) {
-    double nn = 0.0, q1 = 0.0, q2 = 0.0;
-    for (int a = 0; a < r; ++a) {
-      double wa = Wm[(int64_t)a * r + i];
-      nn += wa * wa;
-      double t1 = 0.0, t2 = 0.0;
-      for (int b = 0; b < r; ++b) {
-        double wb = Wm[(int64_t)b * r + i];
-        t1 += C1[(int64_t)a * r + b] * wb;
-        t2 += C2[(int64_t)a * r + b] * wb;
-      }
-      q1 += wa * t1;
-      q2 += wa * t2;
-    }
-    sa[i] = sqrt(fmax(q1 / nn, 0.0));
-    sb[i] = sqrt(fmax(q2 / nn, 0.0));
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < l1; ++k) a = fma(U1[(int64_t)k * r + i], U1[(int64_t)k * r + i], a);
+    for (int k = 0; k < l2; ++k) b = fma(U2[(int64_t)k * r + i], U2[(int64_t)k * r + i], b);
+    double nn = sqrt(a + b);
+    sa[i] = nn > 0.0 ? sqrt(a) / nn : 0.0;
+    sb[i] = nn > 0.0 ? sqrt(b) / nn : 0.0;
   }
   __syncthreads();
   for (int i = tid; i < r; i += nt) {
-    double ai = sort_key(sa[i]);
+    double ai = isnan(sa[i]) ? -1.0 : sa[i];
     int rank = 0;
     for (int j = 0; j < r; ++j) {
-      double aj = sort_key(sa[j]);
+      double aj = isnan(sa[j]) ? -1.0 : sa[j];
       rank += (aj > ai) || (aj == ai && j < i);
     }
     rank = min(max(rank, 0), r - 1);
@@ -410,11 +417,12 @@ __global__ void cs_finalize_kernel(const double* __restrict__ Wm, const double* 
   }
 }
 
-cudaError_t launch_cs_finalize(const double* W, const double* C1, const double* C2, int r,
-                               double* alpha, double* beta, cudaStream_t st) {
-  cs_finalize_kernel<<<1, 256, (size_t)2 * r * sizeof(double), st>>>(W, C1, C2, r, alpha, beta);
+cudaError_t launch_cs_norms(const double* U1, int l1, const double* U2, int l2, int r, double* alpha,
+                            double* beta, cudaStream_t st) {
+  cs_norms_kernel<<<1, 256, (size_t)2 * r * sizeof(double), st>>>(U1, l1, U2, l2, r, alpha, beta);
   return launched();
 }
+
 
 // ============================================================================
 // Comparative quantities (Section 1): theta, rho, P1, P2, D1, D2.

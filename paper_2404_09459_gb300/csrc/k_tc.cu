@@ -1,18 +1,538 @@
-// Tensor-core products (tcgen05 + TMA).  Not built yet: reports unavailable.
+// Tensor-core products of the basis extraction on sm_103a: tcgen05.mma with
+// TF32 operands and FP32 accumulation in tensor memory, operands staged by TMA
+// (cp.async.bulk.tensor, 128-byte swizzle) through an mbarrier pipeline.
+//
+//   GX  : Y (M x l) = G (M x n) X        A = G tile (128 rows, K-major),
+//                                        B = X^T tile (K-major), one CTA per 128 rows.
+//   GTQ : Z (n x l) = G^T Q, split-K     A = G^T tile (128 columns of G, MN-major),
+//                                        B = Q^T tile (K-major), one CTA per
+//                                        (128 columns, row chunk); FP32 partials.
+//
+// Warp roles (6 warps): warp 0 issues TMA, warp 1 owns the tensor memory and
+// issues the MMAs (one thread), warps 2-5 drain the accumulator (tcgen05.ld)
+// and, on the first sketch pass, fold ||G||_F^2 from the staged tiles.  Every
+// mbarrier wait is bounded; a timeout is reported as GSVD_RAND_ERR_TIMEOUT.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+
+#include "kernels.h"
 #include "tc.h"
 
 namespace gsvdr {
 
-bool tc_available(int) { return false; }
-cudaError_t tc_gemm_gx(int, const float*, int64_t, int64_t, int64_t, const float*, int64_t, int, float*,
-                       int64_t, double*, cudaStream_t) {
-  return cudaErrorNotSupported;
+namespace {
+
+constexpr int TC_BM = 128;       // MMA M (rows of the accumulator / TMEM lanes)
+constexpr int TC_BK = 32;        // K depth of one stage: 32 floats = one 128-byte swizzle row
+constexpr int TC_KSTEP = 8;      // K of one tf32 MMA (32 bytes)
+constexpr int TC_A_BYTES = TC_BM * TC_BK * 4;  // 16 KB
+constexpr uint32_t WAIT_SPINS = 1u << 22;      // bounded waits (try_wait suspends per call)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
-int tc_gx_ctas(int64_t) { return 1; }
-cudaError_t tc_gemm_gtq(int, const float*, int64_t, int64_t, int64_t, const float*, int64_t, int, float*,
-                        int64_t, int*, int64_t, cudaStream_t) {
-  return cudaErrorNotSupported;
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
-int64_t tc_gtq_part_elems(int64_t, int64_t, int) { return 0; }
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false if this thread gave up or another role already did.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  for (uint32_t it = 0; it < WAIT_SPINS; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+  }
+  *abort_flag = 1;
+  return false;
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// Arrive on `bar` once all previously issued MMAs of this thread have completed.
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor (tcgen05): start address, leading and stride
+// byte offsets (all >> 4), descriptor version 1, 128-byte swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor, kind::tf32: D = F32, A = B = TF32, A/B major bits, N >> 3, M >> 4.
+__host__ __device__ constexpr uint32_t idesc_tf32(uint32_t m, uint32_t n, uint32_t a_mn, uint32_t b_mn) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | (a_mn << 15) | (b_mn << 16) | ((n >> 3) << 17) | ((m >> 4) << 24);
+}
+
+struct SqAccF {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    float p = v * v;
+    float e = fmaf(v, v, -p);
+    float t = hi + p;
+    float z = t - hi;
+    lo += ((hi - (t - z)) + (p - z)) + e;
+    hi = t;
+  }
+};
+
+}  // namespace
+
+// Byte offsets of the buffers inside one pipeline stage (all 1024-byte aligned):
+//   A    TMA target for A: the G tile K-major (GX) or the staged G tile (GTQ)
+//   B    TMA target for B (X^T or Q^T tile, K-major)
+//   AK   K-major A fed to the MMA (= A in GX, the transposed tile in GTQ)
+//   ALO  (3xTF32) A - tf32(A) in the layout of AK;  BLO  (3xTF32) B - tf32(B)
+struct StageLayout {
+  uint32_t a, b, ak, alo, blo, bytes;
+  __host__ __device__ StageLayout(int mode, bool split, int nmma) {
+    const uint32_t nb = ((uint32_t)nmma * TC_BK * 4 + 1023u) & ~1023u;
+    a = 0;
+    b = TC_A_BYTES;
+    uint32_t o = b + nb;
+    ak = a;
+    if (mode == 1) {
+      ak = o;
+      o += TC_A_BYTES;
+    }
+    alo = blo = 0;
+    if (split) {
+      alo = o;
+      o += TC_A_BYTES;
+      blo = o;
+      o += nb;
+    }
+    bytes = o;
+  }
+};
+
+__device__ __forceinline__ float tf32_lo(float x) {
+  return x - __uint_as_float(__float_as_uint(x) & 0xffffe000u);  // exact; the MMA truncates x to its high part
+}
+
+// mode 0 (GX): tile = blockIdx.x (rows m0 = 128 tile), K = n.
+// mode 1 (GTQ): tile = blockIdx.x (G columns c0 = 128 tile), split = blockIdx.y (rows).
+// SPLIT: 3xTF32, D += A_hi B_hi + A_lo B_hi + A_hi B_lo (the tensor core truncates
+// each FP32 operand to TF32, so A_hi is A itself and A_lo = A - tf32(A)).
+template <int MODE, bool NORM, bool SPLIT>
+__global__ __launch_bounds__(192) void tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
+                                                      const __grid_constant__ CUtensorMap mapB, float* __restrict__ out,
+                                                      int64_t ldo, int64_t out_rows, int ncols, int nmma, int tmem_cols,
+                                                      int64_t kdim, int64_t rows_per_split, int64_t split_stride,
+                                                      int stages, double* __restrict__ gnorm_part, DevStatus* st_dev) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const StageLayout L(MODE, SPLIT, nmma);
+  const uint32_t b_bytes = (uint32_t)nmma * TC_BK * 4;
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + (size_t)stages * L.bytes);
+  uint64_t* empty = full + stages;
+  uint64_t* tfull = empty + stages;  // operands prepared by the epilogue warps
+  uint64_t* accum = tfull + stages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+  // The tensor cores take TF32 operands K-major only, so in GTQ the epilogue
+  // warps transpose each staged G tile (32 rows x 128 columns, unswizzled)
+  // into the K-major 128-byte-swizzled layout of A (128 rows x 32 floats).
+  constexpr bool TRANSPOSE = MODE == 1;
+  constexpr bool PREP = TRANSPOSE || SPLIT;         // MMA waits for the prepared operands
+  constexpr bool EPI_STAGE = PREP || NORM;          // epilogue warps visit every stage
+  __shared__ int s_abort;
+  __shared__ double s_red[4];
+
+  int64_t k_begin, k_end;
+  if (MODE == 0) {
+    k_begin = 0;
+    k_end = kdim;
+  } else {
+    k_begin = (int64_t)blockIdx.y * rows_per_split;
+    k_end = min(kdim, k_begin + rows_per_split);
+  }
+  const int ktiles = (int)((k_end - k_begin + TC_BK - 1) / TC_BK);
+  const int tile0 = blockIdx.x * TC_BM;
+
+  if (tid == 0) {
+    s_abort = 0;
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], EPI_STAGE ? 5 : 1);
+      mbar_init(&tfull[s], 4);
+    }
+    mbar_init(accum, 1);
+    fence_barrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, (uint32_t)tmem_cols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  volatile int* abort_flag = &s_abort;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      int issued = 0;
+      for (int kt = 0; kt < ktiles; ++kt) {
+        const int s = kt % stages;
+        const uint32_t ph = (uint32_t)(kt / stages) & 1u;
+        if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) break;
+        ++issued;
+        uint8_t* st = base + (size_t)s * L.bytes;
+        mbar_expect_tx(&full[s], (uint32_t)TC_A_BYTES + b_bytes);
+        const int k0 = (int)(k_begin + (int64_t)kt * TC_BK);
+        if (MODE == 0) {
+          tma_load_2d(st + L.a, &mapA, &full[s], k0, tile0);  // G[tile0.., k0..]: 128 rows x 32 floats
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q)  // G[k0.., tile0 + 32q ..]: 32 rows x 32 floats, unswizzled
+            tma_load_2d(st + L.a + q * (TC_BK * 128), &mapA, &full[s], tile0 + 32 * q, k0);
+        }
+        tma_load_2d(st + L.b, &mapB, &full[s], k0, 0);  // B^T rows 0..nmma-1, K k0..k0+31
+      }
+      if (*abort_flag) {
+        // drain: wait (bounded) until the copies this thread issued have landed
+        for (int kt = max(0, issued - stages); kt < issued; ++kt) {
+          volatile int none = 0;
+          mbar_wait(&full[kt % stages], (uint32_t)(kt / stages) & 1u, &none);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const uint32_t idesc = idesc_tf32(TC_BM, (uint32_t)nmma, 0u, 0u);
+      for (int kt = 0; kt < ktiles; ++kt) {
+        const int s = kt % stages;
+        const uint32_t ph = (uint32_t)(kt / stages) & 1u;
+        if (!mbar_wait(PREP ? &tfull[s] : &full[s], ph, abort_flag)) break;
+        tc_fence_after();
+        const uint32_t st = smem_u32(base + (size_t)s * L.bytes);
+#pragma unroll
+        for (int ks = 0; ks < TC_BK / TC_KSTEP; ++ks) {
+          // K-major operands: 8-row groups 1024 B apart, K step = 32 B inside the swizzle row
+          const uint64_t adesc = smem_desc(st + L.ak + ks * 32, 16, 1024);
+          const uint64_t bdesc = smem_desc(st + L.b + ks * 32, 16, 1024);
+          mma_tf32(tmem, adesc, bdesc, idesc, (kt > 0 || ks > 0) ? 1u : 0u);
+          if (SPLIT) {
+            mma_tf32(tmem, smem_desc(st + L.alo + ks * 32, 16, 1024), bdesc, idesc, 1u);
+            mma_tf32(tmem, adesc, smem_desc(st + L.blo + ks * 32, 16, 1024), idesc, 1u);
+          }
+        }
+        mma_commit(&empty[s]);
+      }
+      // always: arrives once every MMA issued above has completed (at once if none),
+      // so after the epilogue's wait no MMA is in flight when the TMEM is freed
+      mma_commit(accum);
+    }
+  } else {
+    // ---------------- epilogue (warps 2-5) ----------------
+    const int q = warp & 3;  // TMEM sub-partition of this warp: lanes 32q .. 32q + 31
+    const int et = tid - 64;  // 0..127
+    SqAccF sq;
+    if (EPI_STAGE) {
+      for (int kt = 0; kt < ktiles; ++kt) {
+        const int s = kt % stages;
+        const uint32_t ph = (uint32_t)(kt / stages) & 1u;
+        if (!mbar_wait(&full[s], ph, abort_flag)) break;
+        uint8_t* st = base + (size_t)s * L.bytes;
+        if (TRANSPOSE) {
+          // thread c owns row c of the K-major tile: staged value (k, c) sits at
+          // (c / 32) * 4 KB + k * 128 B + (c % 32) * 4 B; row c is 128 B whose
+          // 16-byte chunk ch lands at chunk ch ^ (c % 8) (128-byte swizzle).
+          const int c = et;
+          const float* stg = reinterpret_cast<const float*>(st + L.a + (c >> 5) * (TC_BK * 128)) + (c & 31);
+          uint8_t* row = st + L.ak + c * 128;
+          uint8_t* rlo = st + L.alo + c * 128;
+#pragma unroll
+          for (int ch = 0; ch < 8; ++ch) {
+            float4 v = make_float4(stg[(4 * ch + 0) * 32], stg[(4 * ch + 1) * 32], stg[(4 * ch + 2) * 32],
+                                   stg[(4 * ch + 3) * 32]);
+            const int off = (ch ^ (c & 7)) << 4;
+            *reinterpret_cast<float4*>(row + off) = v;
+            if (SPLIT)
+              *reinterpret_cast<float4*>(rlo + off) = make_float4(tf32_lo(v.x), tf32_lo(v.y), tf32_lo(v.z), tf32_lo(v.w));
+          }
+        } else if (SPLIT || NORM) {
+          // elementwise on the swizzled tile: the layout is preserved
+          const float4* a4 = reinterpret_cast<const float4*>(st + L.a);
+          float4* lo4 = reinterpret_cast<float4*>(st + L.alo);
+          for (int i = et; i < TC_A_BYTES / 16; i += 128) {
+            float4 v = a4[i];
+            if (NORM) {
+              sq.add(v.x);
+              sq.add(v.y);
+              sq.add(v.z);
+              sq.add(v.w);
+            }
+            if (SPLIT) lo4[i] = make_float4(tf32_lo(v.x), tf32_lo(v.y), tf32_lo(v.z), tf32_lo(v.w));
+          }
+        }
+        if (SPLIT) {
+          const float4* b4 = reinterpret_cast<const float4*>(st + L.b);
+          float4* blo4 = reinterpret_cast<float4*>(st + L.blo);
+          for (int i = et; i < (int)(b_bytes / 16); i += 128) {
+            float4 v = b4[i];
+            blo4[i] = make_float4(tf32_lo(v.x), tf32_lo(v.y), tf32_lo(v.z), tf32_lo(v.w));
+          }
+        }
+        // make the generic-proxy writes visible to the tensor cores (async proxy)
+        if (PREP) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) {
+          if (PREP) mbar_arrive(&tfull[s]);
+          mbar_arrive(&empty[s]);
+        }
+      }
+    }
+    const bool ok = mbar_wait(accum, 0, abort_flag);
+    tc_fence_after();
+    if (ok && ktiles > 0) {
+      const int row = 32 * q + lane;
+      const int64_t grow = (int64_t)tile0 + row;
+      float* dst = out + (MODE == 1 ? (int64_t)blockIdx.y * split_stride : 0) + grow * ldo;
+      for (int c0 = 0; c0 < nmma; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
+        if (grow < out_rows) {
+#pragma unroll
+          for (int j = 0; j < 16; j += 4) {
+            const int c = c0 + j;
+            if (c + 3 < ncols) {
+              *reinterpret_cast<float4*>(dst + c) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+            } else {
+              for (int t = 0; t < 4; ++t)
+                if (c + t < ncols) dst[c + t] = v[j + t];
+            }
+          }
+        }
+      }
+    }
+    if (NORM) {
+      double s = (double)sq.hi + (double)sq.lo;
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      if (lane == 0) s_red[q] = s;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (NORM && tid == 0) gnorm_part[blockIdx.x] = s_red[0] + s_red[1] + s_red[2] + s_red[3];
+  if (tid == 0 && s_abort) set_status(st_dev, -7, 200 + MODE, blockIdx.x);
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, (uint32_t)tmem_cols);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// 2-D FP32 tensor map, dims {inner, outer}, row stride in elements, box {32, box_outer},
+// 128 B swizzle (or none).
+bool make_map(CUtensorMap* m, const void* ptr, uint64_t inner, uint64_t outer, uint64_t ld, uint32_t box_outer,
+              bool swizzle = true) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {ld * 4};
+  cuuint32_t box[2] = {32, box_outer};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+int pick_stages(int nmma, int mode, bool split) {
+  const int stage = (int)StageLayout(mode, split, nmma).bytes;
+  // two CTAs per SM when the pipeline fits in ~110 KB, else one deeper pipeline
+  int s = (110 * 1024 - 2048) / stage;
+  if (s < 3) s = std::min(6, (210 * 1024 - 2048) / stage);
+  return std::max(2, std::min(s, 8));
+}
+
+size_t smem_bytes(int nmma, int stages, int mode, bool split) {
+  return 1024 + (size_t)stages * StageLayout(mode, split, nmma).bytes + (3 * (size_t)stages + 1) * 8 + 16;
+}
+
+int tmem_cols_for(int nmma) {
+  int c = 32;
+  while (c < nmma) c <<= 1;
+  return c;
+}
+
+}  // namespace
+
+bool tc_available(int device) {
+  cudaDeviceProp p;
+  if (cudaGetDeviceProperties(&p, device) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return p.major == 10 && p.minor == 3 && encode_fn() != nullptr;
+}
+
+bool tc_shape_ok(const void* G, int64_t ldg, int l) {
+  return ((uintptr_t)G % 16 == 0) && (ldg % 4 == 0) && l >= 1 && l <= 256;
+}
+
+int tc_gx_ctas(int64_t M) { return (int)cdiv(M, TC_BM); }
+
+template <int MODE, bool NORM, bool SPLIT>
+void launch_tc(dim3 grid, size_t smem, cudaStream_t st, const CUtensorMap& ma, const CUtensorMap& mb, float* out,
+               int64_t ldo, int64_t out_rows, int ncols, int nmma, int64_t kdim, int64_t rps, int64_t split_stride,
+               int stages, double* gnorm_part, DevStatus* st_dev) {
+  cudaFuncSetAttribute(tc_gemm_kernel<MODE, NORM, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  tc_gemm_kernel<MODE, NORM, SPLIT><<<grid, 192, smem, st>>>(ma, mb, out, ldo, out_rows, ncols, nmma, tmem_cols_for(nmma),
+                                                             kdim, rps, split_stride, stages, gnorm_part, st_dev);
+}
+
+cudaError_t tc_gemm_gx(int prec, const float* G, int64_t ldg, int64_t M, int64_t n, const float* Xt, int64_t ldx,
+                       int l, float* Y, int64_t ldy, double* gnorm_part, DevStatus* st_dev, cudaStream_t st) {
+  const bool split = prec == 3;  // GSVD_RAND_TF32X3
+  const int nmma = (int)round_up(l, 16);
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, G, (uint64_t)n, (uint64_t)M, (uint64_t)ldg, TC_BM)) return cudaErrorInvalidValue;
+  if (!make_map(&mb, Xt, (uint64_t)n, (uint64_t)nmma, (uint64_t)ldx, (uint32_t)nmma)) return cudaErrorInvalidValue;
+  const int stages = pick_stages(nmma, 0, split);
+  const size_t smem = smem_bytes(nmma, stages, 0, split);
+  const dim3 grid((unsigned)cdiv(M, TC_BM));
+  if (gnorm_part) {
+    if (split)
+      launch_tc<0, true, true>(grid, smem, st, ma, mb, Y, ldy, M, l, nmma, n, 0, 0, stages, gnorm_part, st_dev);
+    else
+      launch_tc<0, true, false>(grid, smem, st, ma, mb, Y, ldy, M, l, nmma, n, 0, 0, stages, gnorm_part, st_dev);
+  } else {
+    if (split)
+      launch_tc<0, false, true>(grid, smem, st, ma, mb, Y, ldy, M, l, nmma, n, 0, 0, stages, nullptr, st_dev);
+    else
+      launch_tc<0, false, false>(grid, smem, st, ma, mb, Y, ldy, M, l, nmma, n, 0, 0, stages, nullptr, st_dev);
+  }
+  return launched();
+}
+
+int tc_gtq_splits(int64_t M, int64_t n) {
+  const int64_t ctiles = cdiv(n, TC_BM);
+  int64_t s = std::max<int64_t>(1, (2 * 152 + ctiles - 1) / ctiles);
+  s = std::min<int64_t>(s, std::max<int64_t>(1, cdiv(M, 4 * TC_BK)));
+  return (int)s;
+}
+
+int64_t tc_gtq_part_elems(int64_t M, int64_t n, int l) {
+  return (int64_t)tc_gtq_splits(M, n) * n * round_up(l, 4);
+}
+
+cudaError_t tc_gemm_gtq(int prec, const float* G, int64_t ldg, int64_t M, int64_t n, const float* Qt, int64_t ldq,
+                        int l, float* part, int64_t lp, int* splits_out, int64_t max_part_elems, DevStatus* st_dev,
+                        cudaStream_t st) {
+  const int nmma = (int)round_up(l, 16);
+  int splits = tc_gtq_splits(M, n);
+  while (splits > 1 && (int64_t)splits * n * lp > max_part_elems) --splits;
+  // split boundaries on stage (32-row) boundaries so that no tile crosses into the next split
+  const int64_t rps = round_up(cdiv(M, splits), TC_BK);
+  splits = (int)cdiv(M, rps);
+  *splits_out = splits;
+  CUtensorMap ma, mb;
+  // G tiles are staged unswizzled (32 rows x 32 columns per box) and transposed in shared memory
+  if (!make_map(&ma, G, (uint64_t)n, (uint64_t)M, (uint64_t)ldg, TC_BK, false)) return cudaErrorInvalidValue;
+  if (!make_map(&mb, Qt, (uint64_t)M, (uint64_t)nmma, (uint64_t)ldq, (uint32_t)nmma)) return cudaErrorInvalidValue;
+  const bool split = prec == 3;  // GSVD_RAND_TF32X3
+  const int stages = pick_stages(nmma, 1, split);
+  const size_t smem = smem_bytes(nmma, stages, 1, split);
+  const dim3 grid((unsigned)cdiv(n, TC_BM), (unsigned)splits);
+  if (split)
+    launch_tc<1, false, true>(grid, smem, st, ma, mb, part, lp, n, l, nmma, M, rps, n * lp, stages, nullptr, st_dev);
+  else
+    launch_tc<1, false, false>(grid, smem, st, ma, mb, part, lp, n, l, nmma, M, rps, n * lp, stages, nullptr, st_dev);
+  return launched();
+}
 
 }  // namespace gsvdr

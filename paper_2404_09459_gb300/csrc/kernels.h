@@ -57,22 +57,23 @@ int gram_chunks(int64_t M, int l, int64_t* rows_per_chunk);
 // W = sum_c part[c] (FP64, chunk order).
 cudaError_t launch_gram_reduce(const double* part, int chunks, int l, double* W, cudaStream_t st);
 
-// Cholesky of W + s I (s = shift_coef * trace(W), 0 for no shift), one CTA.
-// R: upper triangular l x l (row-major, ld l, zeros below) in TC; rinv: 1/R_ii.
-// A pivot d_k <= tau_rel * (W + sI)_kk is numerically dependent: its column is
-// dropped (R row k = e_k, rinv_k = 0, so column k of Q = Y R^{-1} is zero).
-// All columns dropped -> BREAKDOWN; non-finite entries -> NONFINITE (st_dev).
+// Cholesky of W + s I (s = shift_coef * trace(W), 0 for no shift), one CTA,
+// and the explicit inverse of the factor: Rinv (l x l, row-major, upper
+// triangular, TC).  A pivot d_k <= tau_rel * (W + sI)_kk is numerically
+// dependent: its column is dropped (column k of Rinv is zero, so column k of
+// Q = Y Rinv is zero).  All columns dropped -> BREAKDOWN; non-finite -> NONFINITE.
+// scratch: chol_scratch_elems(l) TC values (used when shared memory is too small).
+int64_t chol_scratch_elems(int l);
 template <typename TC>
-cudaError_t launch_chol_shift(const double* W, int l, double shift_coef, double tau_rel, TC* R,
-                              TC* rinv, DevStatus* st_dev, int stage, cudaStream_t st);
+cudaError_t launch_chol_shift(const double* W, int l, double shift_coef, double tau_rel, TC* Rinv,
+                              TC* scratch, DevStatus* st_dev, int stage, cudaStream_t st);
 
-// Q = Y R^{-1} by row-wise forward substitution (q R = y), optional Gram
-// partials of Q per CTA (part != nullptr, one chunk per CTA), optional
-// transposed output Qt[j * ldq + row].
+// Q = Y Rinv (upper triangular) per tile of rows, optional Gram partials of Q
+// per CTA (part != nullptr, one chunk per CTA), optional transposed output
+// Qt[j * ldq + row].
 template <typename T, typename TC>
-cudaError_t launch_apply_rinv(const T* Y, int64_t ldy, int64_t M, int l, const TC* R,
-                              const TC* rinv, T* Q, int64_t ldq, int transpose_out, double* part,
-                              cudaStream_t st);
+cudaError_t launch_apply_rinv(const T* Y, int64_t ldy, int64_t M, int l, const TC* Rinv, T* Q, int64_t ldq,
+                              int transpose_out, double* part, cudaStream_t st);
 int apply_ctas(int64_t M, int l);
 int64_t apply_rows_per_cta(int l);
 
@@ -94,6 +95,13 @@ int64_t jacobi_scratch_floats(int N);
 cudaError_t launch_jacobi_f32(const double* A, int N, double* V, double* lam, float* scratch,
                               int max_sweeps, DevStatus* st_dev, cudaStream_t st);
 
+// All eigenpairs of the symmetric N x N FP64 matrix A in FP32, one CTA
+// (tridiagonalisation, bisection, twisted factorisation, back-transformation,
+// two-pass MGS with cluster replacement): X (N x N, FP64, orthonormal columns),
+// lam (N, ascending).  scratch: eig_scratch_floats(N) floats.
+int64_t eig_scratch_floats(int N);
+cudaError_t launch_eig_f32(const double* A, int N, double* X, double* lam, float* scratch, cudaStream_t st);
+
 // One Ogita-Aishima refinement step of the eigenvectors X (N x N) of the
 // symmetric A, in FP64: R = I - X^T X, S = X^T A X, lam_i = s_ii/(1 - r_ii),
 // F_ij = (s_ij + lam_j r_ij)/(lam_j - lam_i) (|lam_i - lam_j| > delta) or r_ij/2,
@@ -101,20 +109,20 @@ cudaError_t launch_jacobi_f32(const double* A, int N, double* V, double* lam, fl
 cudaError_t launch_oa_refine(const double* A, int N, double* X, double* lam, double* work,
                              int64_t work_elems, cudaStream_t st);
 
-// GSV pairs from the refined eigen-decomposition of K = S S^T (L x L, S = [B1; B2],
-// B1 with l1 rows): take the r leading eigenvectors Zr, C1 = Z1^T Z1,
-// C2 = Z2^T Z2, eigen-decompose C1 (FP32 Jacobi + FP64 refinement) and
-// alpha_i^2 = w_i^T C1 w_i, beta_i^2 = w_i^T C2 w_i, sorted.
-// Implemented in the orchestration (api.cu) from the pieces below.
+// Gather the r leading eigenvectors (by lam, descending; NaN last) of X (N x N)
+// into Zr (N x r); order receives the permutation.
 cudaError_t launch_select_topr(const double* X, const double* lam, int N, int r, double* Zr,
                                int* order, cudaStream_t st);
-cudaError_t launch_cs_finalize(const double* W, const double* C1, const double* C2, int r,
-                               double* alpha, double* beta, cudaStream_t st);
 
 // Comparative quantities of Section 1.
 cudaError_t launch_metrics(const double* alpha, const double* beta, int r, int N, int pad_mode,
                            double* theta, double* rho, double* P1, double* P2, double* D,
                            cudaStream_t st);
+
+// GSV pairs from U1 = Z1 W (l1 x r) and U2 = Z2 W (l2 x r): alpha_i = ||U1[:, i]||,
+// beta_i = ||U2[:, i]||, normalised to alpha^2 + beta^2 = 1, sorted (eq. (ab)).
+cudaError_t launch_cs_norms(const double* U1, int l1, const double* U2, int l2, int r, double* alpha,
+                            double* beta, cudaStream_t st);
 
 // Residual (cumulated form): resid[s] = sqrt(max(g2 - b2, 0) / g2).
 cudaError_t launch_residual(const double* gpart, int ng, const double* bpart, int nb, double* out,

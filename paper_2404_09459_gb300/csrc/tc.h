@@ -3,21 +3,27 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "common.cuh"
+
 namespace gsvdr {
 
-// True when the device is sm_103 / sm_100 class and the tcgen05 kernels were built.
+// True when the device is sm_103 and the driver exposes tensor-map encoding.
 bool tc_available(int device);
+// TMA addressing constraints: 16-byte aligned base, row stride a multiple of 16 bytes, l <= 256.
+bool tc_shape_ok(const void* G, int64_t ldg, int l);
 
-// Y (M x l, ld ldy, float) = G (M x n, float) * X, X given K-major as Xt (lx x n, ld ldx).
-// prec selects TF32, TF32X3 or BF16 operands; accumulation is FP32.
-// gnorm_part: per-CTA FP64 partial sums of G^2 (nullptr to skip), tc_gx_ctas(M) entries.
-cudaError_t tc_gemm_gx(int prec, const float* G, int64_t ldg, int64_t M, int64_t n, const float* Xt,
-                       int64_t ldx, int l, float* Y, int64_t ldy, double* gnorm_part, cudaStream_t st);
+// Y (M x l, ld ldy) = G (M x n, ld ldg) X with X given K-major as Xt (round_up(l,16) x n,
+// ld ldx, rows l.. zero).  TF32 operands, FP32 accumulation.  gnorm_part (or nullptr):
+// per-CTA FP64 sums of G^2, tc_gx_ctas(M) entries.  A timed-out pipeline wait sets
+// TIMEOUT in st_dev.
+cudaError_t tc_gemm_gx(int prec, const float* G, int64_t ldg, int64_t M, int64_t n, const float* Xt, int64_t ldx,
+                       int l, float* Y, int64_t ldy, double* gnorm_part, DevStatus* st_dev, cudaStream_t st);
 int tc_gx_ctas(int64_t M);
 
-// Split-K partials of Z = G^T Q: part[z][c][j] (FP32), *splits receives the split count.
-cudaError_t tc_gemm_gtq(int prec, const float* G, int64_t ldg, int64_t M, int64_t n, const float* Q,
-                        int64_t ldq, int l, float* part, int64_t lp, int* splits, int64_t max_part_elems,
+// Split-K partials of Z = G^T Q with Q given transposed as Qt (round_up(l,16) x M, ld ldq,
+// rows l.. zero): part[z][c][j] (FP32, ld lp); *splits receives the split count.
+cudaError_t tc_gemm_gtq(int prec, const float* G, int64_t ldg, int64_t M, int64_t n, const float* Qt, int64_t ldq,
+                        int l, float* part, int64_t lp, int* splits, int64_t max_part_elems, DevStatus* st_dev,
                         cudaStream_t st);
 int64_t tc_gtq_part_elems(int64_t M, int64_t n, int l);
 

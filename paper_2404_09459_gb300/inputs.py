@@ -114,13 +114,12 @@ def planted_pair_torch(spec: PairSpec, device="cuda", dtype=None):
     d = planted_scale(spec)
 
     def haar(rows, cols):
-        a = torch.randn(rows, cols, generator=g, device=device, dtype=torch.float64)
-        q, r = torch.linalg.qr(a)
-        return q * torch.sign(torch.diagonal(r))[None, :]
+        # the thin QR of the Gaussian block runs on the host (numpy / LAPACK)
+        return torch.from_numpy(_haar_columns(rng, rows, cols)).to(device)
 
     U = haar(spec.m, spec.r)
     V = haar(spec.p, spec.r)
-    O = haar(spec.n, spec.r).T
+    O = haar(spec.n, spec.r).T.contiguous()
     ad = torch.tensor(alpha * d, device=device)
     bd = torch.tensor(beta * d, device=device)
     out = []
