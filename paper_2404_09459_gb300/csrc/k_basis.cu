@@ -469,130 +469,122 @@ cudaError_t launch_gram_reduce(const double* part, int chunks, int l, double* W,
 }
 
 // ============================================================================
-// Shifted Cholesky, one CTA of 32 x 32 threads, full storage (odd stride) in
-// shared memory: right-looking with the unscaled pivot row, one barrier per
-// step.  Then R^{-1} by back substitution, one warp per column.
+// Shifted Cholesky with the inverse factor in the same sweep, one CTA of 32
+// warps.  Gaussian elimination on the augmented pair [W | I] by symmetric
+// pivots turns W into U = D L^T and I into L^{-1} (W = L D L^T, L unit lower),
+// so R = D^{1/2} L^T and R^{-1} = L^{-T} D^{-1/2}: no separate triangular
+// inverse.  Both halves share one l x lda array M: the upper triangle
+// (j >= i) holds the reduced W, the strict lower triangle row i holds the
+// off-diagonal part of row i of L^{-1}.  Pivot k updates, for every row
+// i > k, the columns c < k (L^{-1} part), c = k (the new multiplier) and
+// c >= i (trailing W): one barrier per pivot, rows spread over warps,
+// columns over lanes.
 // ============================================================================
+constexpr int CHOL_THREADS = 1024;
+
 template <typename TC>
-__global__ __launch_bounds__(1024) void chol_shift_kernel(const double* __restrict__ W, int l,
-                                                          double shift_coef, double tau_rel,
-                                                          TC* __restrict__ Rinv, DevStatus* st_dev,
-                                                          int stage, TC* gscr, int use_smem) {
+__global__ __launch_bounds__(CHOL_THREADS) void chol_shift_kernel(const double* __restrict__ W, int l,
+                                                                  double shift_coef, double tau_rel,
+                                                                  TC* __restrict__ Rinv, DevStatus* st_dev,
+                                                                  int stage, TC* gscr, int use_smem) {
   extern __shared__ unsigned char smem_raw[];
   const int lda = l | 1;
-  TC* A = use_smem ? reinterpret_cast<TC*>(smem_raw) : gscr;  // l x lda: A, later R
-  TC* X = A + (int64_t)l * lda;                               // l x lda: R^{-1}
-  __shared__ double s_shift;
-  __shared__ int s_bad;
-  __shared__ TC s_odiag[256];
-  __shared__ unsigned char s_drop[256];
-  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  TC* M = use_smem ? reinterpret_cast<TC*>(smem_raw) : gscr;
+  __shared__ double s_tr;
+  __shared__ int s_bad, s_kept;
+  __shared__ TC s_odiag[256], s_scale[256];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = CHOL_THREADS / 32;
   if (tid == 0) {
-    double tr = 0.0;
-    bool fin = true;
-    for (int i = 0; i < l; ++i) {
-      double d = W[(int64_t)i * l + i];
-      tr += d;
-      fin = fin && isfinite(d);
-    }
-    s_shift = shift_coef * tr;
-    s_bad = fin ? 0 : 2;
+    s_bad = 0;
+    s_kept = 0;
   }
   __syncthreads();
-  const double sh = s_shift;
-  for (int i = ty; i < l; i += 32)
-    for (int j = tx; j < l; j += 32) {
-      double v = W[(int64_t)i * l + j] + (i == j ? sh : 0.0);
+  for (int i = warp; i < l; i += NW)
+    for (int j = lane; j < l; j += 32) {
+      const double v = W[(int64_t)i * l + j];
       if (!isfinite(v)) s_bad = 2;
-      A[(int64_t)i * lda + j] = (TC)v;
-      if (i == j) {
-        s_odiag[i] = (TC)v;
-        s_drop[i] = 0;
-      }
+      M[(int64_t)i * lda + j] = j >= i ? (TC)v : TC(0);
     }
+  if (warp == 0) {  // trace in FP64
+    double t = 0.0;
+    for (int i = lane; i < l; i += 32) t += W[(int64_t)i * l + i];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0) s_tr = t;
+  }
   __syncthreads();
+  const double sh = shift_coef * s_tr;
+  for (int i = tid; i < l; i += CHOL_THREADS) {
+    const TC v = (TC)((double)W[(int64_t)i * l + i] + sh);
+    M[(int64_t)i * lda + i] = v;
+    s_odiag[i] = v;
+  }
+  __syncthreads();
+  // A pivot not above the Gram's resolution relative to its own (shifted)
+  // diagonal is numerically dependent on the earlier columns: it is skipped
+  // (no elimination with it) and its column of R^{-1} is zero, so the
+  // matching column of Q is zero and adds a zero row to Q^T G.  The final
+  // M[k][k] is the pivot seen at step k, so the test is repeated afterwards.
+  auto dropped = [&](int k, TC d) { return !(d > (TC)tau_rel * s_odiag[k]); };
   int bad_k = -1;
   if (s_bad == 0) {
     for (int k = 0; k < l; ++k) {
-      const TC d = A[(int64_t)k * lda + k];
+      const TC* rowk = M + (int64_t)k * lda;
+      const TC d = rowk[k];
       if (!isfinite(d)) {
         bad_k = k;
         break;
       }
-      // A pivot not above the Gram's resolution relative to its own column is
-      // numerically dependent on the previous columns: drop it (its column of
-      // Q becomes zero and adds a zero row to Q^T G).
-      if (!(d > (TC)tau_rel * s_odiag[k])) {
-        if (tid == 0) s_drop[k] = 1;
-        continue;
-      }
+      if (dropped(k, d)) continue;
       const TC dinv = TC(1) / d;
-      const TC* rowk = A + (int64_t)k * lda;
-      for (int i = k + 1 + ty; i < l; i += 32) {
-        const TC aki = rowk[i] * dinv;
-        TC* ai = A + (int64_t)i * lda;
-        for (int j = k + 1 + tx; j < l; j += 32)
-          if (j >= i) ai[j] -= aki * rowk[j];
+      for (int i = k + 1 + warp; i < l; i += NW) {
+        const TC f = rowk[i] * dinv;
+        TC* ri = M + (int64_t)i * lda;
+        for (int c = lane; c < k; c += 32) ri[c] -= f * rowk[c];
+        if (lane == 0) ri[k] = -f;
+        for (int c = i + lane; c < l; c += 32) ri[c] -= f * rowk[c];
       }
       __syncthreads();
     }
   }
   __syncthreads();
-  int kept = 0;
-  for (int i = 0; i < l; ++i) kept += s_drop[i] ? 0 : 1;
-  if (bad_k >= 0 || s_bad || kept == 0) {
+  if (warp == 0 && bad_k < 0 && s_bad == 0) {
+    int c = 0;
+    for (int i = lane; i < l; i += 32) {
+      const TC d = M[(int64_t)i * lda + i];
+      const bool dr = dropped(i, d);
+      s_scale[i] = dr ? TC(0) : TC(1) / sqrt(d);
+      c += dr ? 0 : 1;
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if (lane == 0) s_kept = c;
+  }
+  __syncthreads();
+  if (bad_k >= 0 || s_bad || s_kept == 0) {
     if (tid == 0) set_status(st_dev, (s_bad == 2 || bad_k >= 0) ? -4 : -5, stage, bad_k);
     return;
   }
-  // R = rows scaled by 1/sqrt(pivot) (rows of dropped pivots = e_k), in place
-  for (int i = ty; i < l; i += 32) {
-    const bool dr = s_drop[i] != 0;
-    const TC rk = dr ? TC(1) : sqrt(A[(int64_t)i * lda + i]);
-    for (int j = tx; j < l; j += 32) {
+  // R^{-1}[c][j] = L^{-1}[j][c] / sqrt(d_j) for c <= j (L^{-1}[j][j] = 1)
+  for (int c = warp; c < l; c += NW)
+    for (int j = lane; j < l; j += 32) {
       TC v = TC(0);
-      if (j == i) v = rk;
-      else if (j > i && !dr) v = A[(int64_t)i * lda + j] / rk;
-      // written after every thread has read its pivot: separate pass below
-      X[(int64_t)i * lda + j] = v;
-    }
-  }
-  __syncthreads();
-  for (int i = ty; i < l; i += 32)
-    for (int j = tx; j < l; j += 32) A[(int64_t)i * lda + j] = X[(int64_t)i * lda + j];
-  __syncthreads();
-  // R^{-1}: column j by back substitution, X[i][j] = -(sum_{k=i+1..j} R[i][k] X[k][j]) / R[i][i]
-  for (int j = ty; j < l; j += 32) {
-    for (int i = j + 1 + tx; i < l; i += 32) X[(int64_t)i * lda + j] = TC(0);
-    if (tx == 0) X[(int64_t)j * lda + j] = TC(1) / A[(int64_t)j * lda + j];
-    __syncwarp();
-    for (int i = j - 1; i >= 0; --i) {
-      TC s = TC(0);
-      for (int k = i + 1 + tx; k <= j; k += 32) s += A[(int64_t)i * lda + k] * X[(int64_t)k * lda + j];
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (tx == 0) X[(int64_t)i * lda + j] = -s / A[(int64_t)i * lda + i];
-      __syncwarp();
-    }
-  }
-  __syncthreads();
-  // dropped columns of Y contribute nothing: zero column k of R^{-1}
-  for (int i = ty; i < l; i += 32)
-    for (int j = tx; j < l; j += 32) {
-      TC v = (j >= i && !s_drop[j]) ? X[(int64_t)i * lda + j] : TC(0);
-      Rinv[(int64_t)i * l + j] = v;
+      if (j == c) v = s_scale[j];
+      else if (j > c) v = M[(int64_t)j * lda + c] * s_scale[j];
+      Rinv[(int64_t)c * l + j] = v;
     }
 }
 
-int64_t chol_scratch_elems(int l) { return 2ll * l * (l | 1); }
+int64_t chol_scratch_elems(int l) { return (int64_t)l * (l | 1); }
 
 template <typename TC>
 cudaError_t launch_chol_shift(const double* W, int l, double shift_coef, double tau_rel, TC* Rinv,
                               TC* scratch, DevStatus* st_dev, int stage, cudaStream_t st) {
   if (l < 1 || l > 256) return cudaErrorInvalidValue;
   size_t smem = (size_t)chol_scratch_elems(l) * sizeof(TC);
-  int use_smem = smem <= 200 * 1024;
-  cudaFuncSetAttribute(chol_shift_kernel<TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  chol_shift_kernel<TC><<<1, 1024, use_smem ? smem : 0, st>>>(W, l, shift_coef, tau_rel, Rinv, st_dev, stage,
-                                                              scratch, use_smem);
+  int use_smem = smem <= 216 * 1024;
+  cudaFuncSetAttribute(chol_shift_kernel<TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 216 * 1024);
+  chol_shift_kernel<TC><<<1, CHOL_THREADS, use_smem ? smem : 0, st>>>(W, l, shift_coef, tau_rel, Rinv, st_dev,
+                                                                      stage, scratch, use_smem);
   return launched();
 }
 template cudaError_t launch_chol_shift<double>(const double*, int, double, double, double*, double*,
@@ -601,77 +593,108 @@ template cudaError_t launch_chol_shift<float>(const double*, int, double, double
                                               DevStatus*, int, cudaStream_t);
 
 // ============================================================================
-// Q = Y R^{-1} (R^{-1} upper triangular, staged in shared memory) over a tile
-// of rows per CTA; optional Gram partial of the produced rows (one chunk per
-// CTA) and optional transposed store Qt[j * ldq + row].
+// Q = Y R^{-1} over a tile of rows per CTA, register-blocked: 16 x 16 threads,
+// thread (ty, tx) computes rows ty + 16 rr (rr < RT) x columns tx CT + cc
+// (cc < CT) with lpad = 16 CT >= l.  Optional Gram partial of the produced rows
+// (4 x 4 register blocks) and optional transposed store Qt[j * ldq + row].
 // ============================================================================
-int64_t apply_rows_per_cta(int l) { return l <= 64 ? 128 : (l <= 128 ? 64 : 32); }
+int apply_ct(int l) { return l <= 64 ? 4 : (l <= 128 ? 8 : 16); }
+int64_t apply_rows_per_cta(int l) { return l <= 64 ? 128 : 32; }
 int apply_ctas(int64_t M, int l) { return (int)cdiv(M, apply_rows_per_cta(l)); }
 
-template <typename T, typename TC>
+// RS: R^{-1} staged in shared memory (else read through L1 from global).
+template <typename T, typename TC, int CT, int RT, bool RS>
 __global__ __launch_bounds__(256) void apply_rinv_kernel(const T* __restrict__ Y, int64_t ldy, int64_t M, int l,
                                                          const TC* __restrict__ Rinv, T* Q, int64_t ldq,
-                                                         int transpose_out, double* part, int64_t rpc,
-                                                         int r_smem) {
+                                                         int transpose_out, double* part) {
+  constexpr int LP = 16 * CT;      // padded column count
+  constexpr int ROWS = 16 * RT;    // rows per CTA
+  constexpr int LS = LP + 1;       // odd stride of the row tiles
   extern __shared__ unsigned char smem_raw[];
-  const int ls = l | 1;
-  // R^{-1} in shared memory when it fits next to the tiles, else read through L1
-  const int rld = r_smem ? ls : l;
-  TC* Rsm = reinterpret_cast<TC*>(smem_raw);
-  const TC* Rs = r_smem ? Rsm : Rinv;
-  T* Ys = reinterpret_cast<T*>(smem_raw + (r_smem ? (size_t)l * ls * sizeof(TC) : 0));  // rpc x ls
-  T* Qs = Ys + rpc * ls;                                                                 // rpc x ls
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int64_t r0 = (int64_t)blockIdx.x * rpc;
-  const int rows = (int)(rpc < M - r0 ? rpc : M - r0);
-  if (r_smem)
-    for (int e = tid; e < l * l; e += nt) {
-      int i = e / l, j = e % l;
-      Rsm[i * ls + j] = Rinv[e];
+  T* Rs = reinterpret_cast<T*>(smem_raw);  // LP x LP (zero padded), when RS
+  T* Ys = Rs + (RS ? LP * LP : 0);         // ROWS x LS
+  T* Qs = Ys + ROWS * LS;                  // ROWS x LS
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t r0 = (int64_t)blockIdx.x * ROWS;
+  const int rows = (int)(ROWS < M - r0 ? ROWS : M - r0);
+  if (RS)
+    for (int e = tid; e < LP * LP; e += 256) {
+      const int i = e / LP, j = e % LP;
+      Rs[e] = (i < l && j < l) ? (T)Rinv[(int64_t)i * l + j] : T(0);
     }
-  for (int e = tid; e < rows * l; e += nt) {
-    int r = e / l, j = e % l;
-    Ys[r * ls + j] = Y[(r0 + r) * ldy + j];
+  for (int e = tid; e < ROWS * LP; e += 256) {
+    const int r = e / LP, j = e % LP;
+    Ys[r * LS + j] = (r < rows && j < l) ? Y[(r0 + r) * ldy + j] : T(0);
   }
   __syncthreads();
-  // q[r][j] = sum_{i <= j} y[r][i] Rinv[i][j]; thread -> (r, j) with j fastest
-  for (int e = tid; e < rows * l; e += nt) {
-    const int r = e / l, j = e % l;
-    const T* y = Ys + r * ls;
-    T a0 = T(0), a1 = T(0);
-    int i = 0;
-    for (; i + 1 <= j; i += 2) {
-      a0 = fma(y[i], (T)Rs[i * rld + j], a0);
-      a1 = fma(y[i + 1], (T)Rs[(i + 1) * rld + j], a1);
+  T acc[RT][CT];
+#pragma unroll
+  for (int a = 0; a < RT; ++a)
+#pragma unroll
+    for (int b = 0; b < CT; ++b) acc[a][b] = T(0);
+  for (int i = 0; i < l; ++i) {
+    T av[RT], bv[CT];
+#pragma unroll
+    for (int rr = 0; rr < RT; ++rr) av[rr] = Ys[(ty + 16 * rr) * LS + i];
+#pragma unroll
+    for (int cc = 0; cc < CT; ++cc) {
+      const int j = tx * CT + cc;
+      bv[cc] = RS ? Rs[i * LP + j] : (j < l ? (T)Rinv[(int64_t)i * l + j] : T(0));
     }
-    if (i <= j) a0 = fma(y[i], (T)Rs[i * rld + j], a0);
-    Qs[r * ls + j] = a0 + a1;
+#pragma unroll
+    for (int rr = 0; rr < RT; ++rr)
+#pragma unroll
+      for (int cc = 0; cc < CT; ++cc) acc[rr][cc] = fma(av[rr], bv[cc], acc[rr][cc]);
   }
+#pragma unroll
+  for (int rr = 0; rr < RT; ++rr)
+#pragma unroll
+    for (int cc = 0; cc < CT; ++cc) Qs[(ty + 16 * rr) * LS + tx * CT + cc] = acc[rr][cc];
   __syncthreads();
   if (transpose_out) {
-    for (int e = tid; e < rows * l; e += nt) {
-      int j = e / rows, r = e % rows;
-      Q[(int64_t)j * ldq + r0 + r] = Qs[r * ls + j];
+    for (int e = tid; e < rows * l; e += 256) {
+      const int j = e / rows, r = e % rows;
+      Q[(int64_t)j * ldq + r0 + r] = Qs[r * LS + j];
     }
   } else {
-    for (int e = tid; e < rows * l; e += nt) {
-      int r = e / l, j = e % l;
-      Q[(r0 + r) * ldq + j] = Qs[r * ls + j];
+    for (int e = tid; e < rows * l; e += 256) {
+      const int r = e / l, j = e % l;
+      Q[(r0 + r) * ldq + j] = Qs[r * LS + j];
     }
   }
   if (part) {
+    // Gram of the tile: thread (ty, tx) owns the CT x CT block (ty CT.., tx CT..), upper blocks only
     double* P = part + (int64_t)blockIdx.x * l * l;
-    for (int e = tid; e < l * l; e += nt) {
-      int i = e / l, j = e % l;
-      if (j < i) continue;
-      T s0 = T(0), s1 = T(0);
-      int r = 0;
-      for (; r + 1 < rows; r += 2) {
-        s0 = fma(Qs[r * ls + i], Qs[r * ls + j], s0);
-        s1 = fma(Qs[(r + 1) * ls + i], Qs[(r + 1) * ls + j], s1);
-      }
-      if (r < rows) s0 = fma(Qs[r * ls + i], Qs[r * ls + j], s0);
-      P[e] = (double)s0 + (double)s1;
+    if (tx >= ty) {
+      for (int bi = 0; bi < CT; bi += 4)
+        for (int bj = 0; bj < CT; bj += 4) {
+          T g[4][4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) g[a][b] = T(0);
+          const int i0 = ty * CT + bi, j0 = tx * CT + bj;
+          for (int r = 0; r < rows; ++r) {
+            const T* qr = Qs + r * LS;
+            T x[4], y[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+              x[a] = qr[i0 + a];
+              y[a] = qr[j0 + a];
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+              for (int b = 0; b < 4; ++b) g[a][b] = fma(x[a], y[b], g[a][b]);
+          }
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+              const int i = i0 + a, j = j0 + b;
+              if (i < l && j < l && j >= i) P[(int64_t)i * l + j] = (double)g[a][b];
+            }
+        }
     }
   }
 }
@@ -679,17 +702,28 @@ __global__ __launch_bounds__(256) void apply_rinv_kernel(const T* __restrict__ Y
 template <typename T, typename TC>
 cudaError_t launch_apply_rinv(const T* Y, int64_t ldy, int64_t M, int l, const TC* Rinv, T* Q, int64_t ldq,
                               int transpose_out, double* part, cudaStream_t st) {
-  int64_t rpc = apply_rows_per_cta(l);
-  const int ls = l | 1;
-  const size_t tiles = 2 * (size_t)rpc * ls * sizeof(T);
-  const size_t rbytes = (size_t)l * ls * sizeof(TC);
-  const int r_smem = tiles + rbytes <= 200 * 1024;
-  const size_t smem = tiles + (r_smem ? rbytes : 0);
-  if (smem > 200 * 1024) return cudaErrorInvalidValue;
-  cudaFuncSetAttribute(apply_rinv_kernel<T, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  unsigned blocks = (unsigned)cdiv(M, rpc);
-  apply_rinv_kernel<T, TC><<<blocks, 256, smem, st>>>(Y, ldy, M, l, Rinv, Q, ldq, transpose_out, part, rpc,
-                                                      r_smem);
+  if (l < 1 || l > 256) return cudaErrorInvalidValue;
+  const int ct = apply_ct(l);
+  const int lp = 16 * ct, rows = (int)apply_rows_per_cta(l);
+  const size_t tiles = 2 * (size_t)rows * (lp + 1) * sizeof(T);
+  const bool rs = ct <= 8;  // R^{-1} (lp x lp) staged for l <= 128: <= 128 KB in FP64
+  const size_t smem = tiles + (rs ? (size_t)lp * lp * sizeof(T) : 0);
+  if (smem > 220 * 1024) return cudaErrorInvalidValue;
+  const unsigned blocks = (unsigned)cdiv(M, rows);
+#define GSVDR_APPLY(CTV, RTV, RSV)                                                                              \
+  do {                                                                                                          \
+    cudaFuncSetAttribute(apply_rinv_kernel<T, TC, CTV, RTV, RSV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                         (int)smem);                                                                            \
+    apply_rinv_kernel<T, TC, CTV, RTV, RSV><<<blocks, 256, smem, st>>>(Y, ldy, M, l, Rinv, Q, ldq,            \
+                                                                      transpose_out, part);                    \
+  } while (0)
+  if (ct == 4)
+    GSVDR_APPLY(4, 8, true);
+  else if (ct == 8)
+    GSVDR_APPLY(8, 2, true);
+  else
+    GSVDR_APPLY(16, 2, false);
+#undef GSVDR_APPLY
   return launched();
 }
 template cudaError_t launch_apply_rinv<double, double>(const double*, int64_t, int64_t, int, const double*,
