@@ -49,6 +49,7 @@ extern "C" {
 #define GSVD_RAND_ERR_TOL_MISS (-6)    /* adaptive basis reached its column cap above tol */
 #define GSVD_RAND_ERR_TIMEOUT (-7)     /* a bounded device-side wait ran out */
 #define GSVD_RAND_ERR_UNSUPPORTED (-8) /* option not built / not available on this device */
+#define GSVD_RAND_ERR_TOO_LARGE (-9)   /* size above the fixed limit of gsvd_rand_metrics_noalloc */
 
 /* Arithmetic of the sketch, power and projection products.
  *   FP64   : G is double; all products in FP64 (the plain path).
@@ -146,6 +147,36 @@ int gsvd_rand_solve(gsvd_rand_t h, const void *G1, int64_t m, int64_t ld1, const
 int gsvd_rand_metrics(gsvd_rand_t h, const double *alpha, const double *beta, int r,
                       int pad_to_n, int pad_mode, double *theta, double *rho, double *P1,
                       double *P2, double *D);
+
+/* Largest pair count N (after padding) that gsvd_rand_metrics_noalloc accepts. */
+#define GSVD_RAND_NOALLOC_MAX_N 32768
+
+/* gsvd_rand_metrics for callers that cannot let a library allocate device
+ * memory.  The paper has no counterpart: this is a service entry point.
+ * Outputs and arguments are those of gsvd_rand_metrics (same formulas, same
+ * padding); results agree with it to rounding (the entropy sums are added in
+ * another order).  Differences:
+ *   - No handle: `device` is the GPU to run on and `stream` a cudaStream_t
+ *     (NULL = the legacy default stream).  The caller's current device is
+ *     restored before returning.
+ *   - Nothing is allocated (no cudaMalloc, no pinned host memory).  Scratch is
+ *     one fixed array of about 1.5 MiB in the library's static device memory,
+ *     held on every GPU that loads the library until the process exits.
+ *     Device pointers are used in place; host inputs and outputs pass through
+ *     that scratch.  Its block counter is cleared on the stream at each call.
+ *   - N = max(r, pad_to_n) <= GSVD_RAND_NOALLOC_MAX_N, else
+ *     GSVD_RAND_ERR_TOO_LARGE and nothing is enqueued.
+ *   - The first call on each device looks up the scratch address there (and so
+ *     loads the library's device code on that device); make that first call
+ *     before any stream capture.
+ *   - All calls on one device share the one scratch array: calls that overlap
+ *     in time (from several host threads, or on several streams) race and can
+ *     return wrong results.  Each call synchronises `stream` before it returns.
+ * Errors: ARG (as gsvd_rand_metrics, or a bad device), TOO_LARGE, CUDA.
+ * There is no message string: the return code is the whole report. */
+int gsvd_rand_metrics_noalloc(int device, void *stream, const double *alpha, const double *beta,
+                              int r, int pad_to_n, int pad_mode, double *theta, double *rho,
+                              double *P1, double *P2, double *D);
 
 /* The Gaussian test matrix the solver draws: out (n x l, row-major, ld = l)
  * with out[i][j] from Philox4x32-10 (Salmon et al., SC'11) and Box-Muller:

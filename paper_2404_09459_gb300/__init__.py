@@ -13,16 +13,18 @@ import os
 
 from ._build import LIB
 
-__all__ = ["Context", "GsvdRandError", "load_library", "PREC", "LIB"]
+__all__ = ["Context", "GsvdRandError", "load_library", "metrics_noalloc", "PREC", "LIB", "NOALLOC_MAX_N"]
 
 PREC = {"fp64": 0, "tf32": 1, "bf16": 2, "tf32x3": 3, "fp32": 4}
 ERRORS = {-1: "ARG", -2: "OOM", -3: "CUDA", -4: "NONFINITE", -5: "BREAKDOWN", -6: "TOL_MISS",
-          -7: "TIMEOUT", -8: "UNSUPPORTED"}
+          -7: "TIMEOUT", -8: "UNSUPPORTED", -9: "TOO_LARGE"}
 FLAG_CHOL_FP64 = 1
 
 EXPORTS = ("gsvd_rand_config_init", "gsvd_rand_create", "gsvd_rand_destroy", "gsvd_rand_last_error",
            "gsvd_rand_solve", "gsvd_rand_metrics", "gsvd_rand_gaussian", "gsvd_rand_philox",
-           "gsvd_rand_profile_get", "gsvd_rand_profile_reset", "gsvd_rand_launch_count")
+           "gsvd_rand_profile_get", "gsvd_rand_profile_reset", "gsvd_rand_launch_count",
+           "gsvd_rand_metrics_noalloc")
+NOALLOC_MAX_N = 32768
 FLAG_PROFILE = 2
 STAGES = ("sketch", "gtq", "orth", "small", "small_gram", "small_jacobi", "small_refine", "small_cs")
 
@@ -67,6 +69,7 @@ def load_library(path: str | None = None):
     lib.gsvd_rand_profile_reset.argtypes = [vp]
     lib.gsvd_rand_launch_count.argtypes = []
     lib.gsvd_rand_launch_count.restype = C.c_uint64
+    lib.gsvd_rand_metrics_noalloc.argtypes = [i32, vp, vp, vp, i32, i32, i32, vp, vp, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("gsvd_rand_last_error", "gsvd_rand_launch_count"):
             getattr(lib, name).restype = C.c_int
@@ -232,3 +235,44 @@ class Context:
         out, ptr = self._out_vec(False, 4 * count, "u32")
         self._check(self.lib.gsvd_rand_philox(self.h, count, seed, pair, side, stream, ptr))
         return out.reshape(count, 4)
+
+
+def metrics_noalloc(alpha, beta, pad_to_n: int = 0, pad_mode: int = 0, device: int = 0, stream=None, out=None):
+    """Context.metrics through gsvd_rand_metrics_noalloc, for callers that must not
+    allocate device memory: the library uses a fixed static scratch instead.
+
+    numpy inputs give numpy outputs (host memory only).  CUDA tensor inputs need
+    `out`, a dict of caller-owned CUDA float64 tensors theta, rho, P1, P2 (N each)
+    and D (2), which is filled and returned; nothing is allocated on the device.
+    stream: a torch.cuda.Stream, a raw cudaStream_t int, or None (legacy default
+    stream).  N = max(len(alpha), pad_to_n) must not exceed NOALLOC_MAX_N.
+    Calls that overlap in time share the scratch and race."""
+    import numpy as np
+    lib = load_library()
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    sp = C.c_void_p(int(stream) if stream else 0)
+    if _is_torch(alpha) and alpha.is_cuda:
+        if out is None:
+            raise ValueError("CUDA inputs need caller-owned outputs: out=dict(theta, rho, P1, P2, D)")
+        pa, pb, r = alpha.data_ptr(), beta.data_ptr(), alpha.numel()
+        N = max(pad_to_n, r)
+        for key, size in (("theta", N), ("rho", N), ("P1", N), ("P2", N), ("D", 2)):
+            t = out[key]
+            if not (t.is_cuda and t.dtype == alpha.dtype and t.numel() >= size and t.is_contiguous()):
+                raise ValueError(f"out[{key!r}] must be a contiguous CUDA float64 tensor of >= {size} elements")
+        ptrs = [out[k].data_ptr() for k in ("theta", "rho", "P1", "P2", "D")]
+        res = out
+    else:
+        a = np.ascontiguousarray(alpha, dtype=np.float64)
+        b = np.ascontiguousarray(beta, dtype=np.float64)
+        pa, pb, r = a.ctypes.data, b.ctypes.data, a.size
+        N = max(pad_to_n, r)
+        res = {k: np.empty(N if k != "D" else 2) for k in ("theta", "rho", "P1", "P2", "D")}
+        ptrs = [res[k].ctypes.data for k in ("theta", "rho", "P1", "P2", "D")]
+    rc = lib.gsvd_rand_metrics_noalloc(device, sp, pa, pb, r, pad_to_n, pad_mode, *ptrs)
+    if rc:
+        why = (f"N = {N} pairs exceeds the fixed limit {NOALLOC_MAX_N}" if rc == -9
+               else "bad arguments or CUDA failure")
+        raise GsvdRandError(rc, why)
+    return dict(theta=res["theta"], rho=res["rho"], P1=res["P1"], P2=res["P2"], D1=res["D"][0], D2=res["D"][1])

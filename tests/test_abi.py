@@ -50,3 +50,9 @@ def test_config_init_defaults(lib):
     assert lib.gsvd_rand_config_init(ctypes.byref(cfg)) == 0
     assert cfg.prec == P.PREC["tf32"] and cfg.block_b == 100 and abs(cfg.tol - 1e-4) < 1e-18
     assert lib.gsvd_rand_config_init(None) == -1
+
+
+def test_noalloc_limit_matches_header():
+    import paper_2404_09459_gb300 as P
+    m = re.search(r"#define GSVD_RAND_NOALLOC_MAX_N (\d+)", open(HEADER).read())
+    assert m and int(m.group(1)) == P.NOALLOC_MAX_N
