@@ -353,6 +353,201 @@ cudaError_t launch_oa_refine(const double* A, int N, double* X, double* lam, dou
 }
 
 // ============================================================================
+// The cluster across the cut.  The Ogita-Aishima step only orthogonalises
+// eigenvector pairs whose eigenvalues lie within delta of each other; with an
+// FP32 start, delta stays near the start's error, so such a cluster is never
+// split.  Only a cluster that straddles the cut between the r-th and
+// (r+1)-th largest eigenvalue changes the selected span, so that one block of
+// S = X^T A X (from the last refinement step) is diagonalised here: shifted
+// by its mean and scaled to unit size, which resolves the block's own
+// spread, by parallel cyclic Jacobi in FP32 (round-robin pairs).  Its columns
+// of X are then rotated, X_c <- X_c V_c, and the following refinement steps
+// re-orthogonalise in FP64 and separate them.
+// Work layout (as launch_oa_refine): XtX, P, S, F (N x N each), part (3 nb).
+// V_c goes to F, the cluster's column indices and size to P.
+// ============================================================================
+constexpr int CUT_CMAX = 128;
+
+__global__ __launch_bounds__(1024) void oa_cut_cluster_kernel(int N, int r, const double* __restrict__ XtX,
+                                                              const double* __restrict__ S,
+                                                              const double* __restrict__ part, int nparts,
+                                                              const double* __restrict__ lam,
+                                                              double* __restrict__ Vc, int* __restrict__ cinfo) {
+  extern __shared__ float cut_sm[];
+  __shared__ int s_ord[512];
+  __shared__ int s_lo, s_c;
+  __shared__ double s_delta, s_mu, s_scale;
+  __shared__ int s_p[CUT_CMAX / 2], s_q[CUT_CMAX / 2];
+  __shared__ float s_cs[CUT_CMAX / 2], s_sn[CUT_CMAX / 2];
+  __shared__ unsigned s_off;
+  const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nwarp = nt >> 5;
+  if (tid == 0) {
+    double A2 = 0, R2 = 0, S2 = 0;
+    for (int b = 0; b < nparts; ++b) {
+      A2 += part[b];
+      R2 += part[nparts + b];
+      S2 += part[2 * nparts + b];
+    }
+    s_delta = 2.0 * (sqrt(S2) + sqrt(A2) * sqrt(R2));
+  }
+  // descending rank of every eigenvalue (NaN last, ties by index): s_ord[rank] = index
+  for (int i = tid; i < N; i += nt) {
+    const double li = isnan(lam[i]) ? -INFINITY : lam[i];
+    int rank = 0;
+    for (int j = 0; j < N; ++j) {
+      const double lj = isnan(lam[j]) ? -INFINITY : lam[j];
+      rank += (lj > li) || (lj == li && j < i);
+    }
+    s_ord[min(rank, N - 1)] = i;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const double d = s_delta;
+    auto lm = [&](int rk) { return lam[s_ord[rk]]; };
+    int lo = r - 1, hi = r + 1;  // ranks [lo, hi)
+    if (r < 1 || r >= N || !(lm(r - 1) - lm(r) <= d)) {
+      lo = 0;
+      hi = 0;
+    } else {
+      while (lo > 0 && lm(lo - 1) - lm(lo) <= d && hi - lo < CUT_CMAX) --lo;
+      while (hi < N && lm(hi - 1) - lm(hi) <= d && hi - lo < CUT_CMAX) ++hi;
+    }
+    s_lo = lo;
+    s_c = hi - lo;
+    cinfo[0] = hi - lo;
+  }
+  __syncthreads();
+  const int c = s_c, lo = s_lo;
+  if (c < 2) return;
+  const int lda = c | 1;
+  float* T = cut_sm;
+  float* V = cut_sm + c * lda;
+  for (int a = tid; a < c; a += nt) cinfo[1 + a] = s_ord[lo + a];
+  if (tid == 0) {
+    double mu = 0.0;
+    for (int a = 0; a < c; ++a) {
+      const int ia = s_ord[lo + a];
+      mu += S[(int64_t)ia * N + ia] / XtX[(int64_t)ia * N + ia];
+    }
+    s_mu = mu / c;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double mx = 0.0;
+    for (int a = 0; a < c; ++a) {
+      const int ia = s_ord[lo + a];
+      mx = fmax(mx, fabs(S[(int64_t)ia * N + ia] / XtX[(int64_t)ia * N + ia] - s_mu));
+      for (int b = 0; b < c; ++b) mx = fmax(mx, fabs(S[(int64_t)ia * N + s_ord[lo + b]]) * (a != b));
+    }
+    s_scale = (mx > 0.0 && isfinite(mx)) ? mx : 1.0;
+  }
+  __syncthreads();
+  const double inv = 1.0 / s_scale, mu = s_mu;
+  for (int e = tid; e < c * c; e += nt) {
+    const int a = e / c, b = e % c, ia = s_ord[lo + a], ib = s_ord[lo + b];
+    double t = 0.5 * (S[(int64_t)ia * N + ib] + S[(int64_t)ib * N + ia]);
+    if (a == b) t = t / XtX[(int64_t)ia * N + ia] - mu;
+    T[a * lda + b] = (float)(t * inv);
+    V[a * lda + b] = a == b ? 1.f : 0.f;
+  }
+  __syncthreads();
+  const int cp = c + (c & 1), m = cp / 2;
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    if (tid == 0) s_off = 0u;
+    __syncthreads();
+    for (int rnd = 0; rnd < cp - 1; ++rnd) {
+      for (int k = tid; k < m; k += nt) {
+        int a = k == 0 ? rnd : (rnd + k) % (cp - 1);
+        int b = k == 0 ? cp - 1 : (rnd - k + (cp - 1)) % (cp - 1);
+        const int p = min(a, b), q = max(a, b);
+        float cs = 1.f, sn = 0.f;
+        if (q < c) {
+          const float apq = T[p * lda + q], app = T[p * lda + p], aqq = T[q * lda + q];
+          atomicMax(&s_off, __float_as_uint(fabsf(apq)));
+          if (fabsf(apq) > 1e-12f) {
+            const float tau = (aqq - app) / (2.f * apq);
+            const float t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+            cs = rsqrtf(1.f + t * t);
+            sn = t * cs;
+          }
+        }
+        s_p[k] = p;
+        s_q[k] = q;
+        s_cs[k] = cs;
+        s_sn[k] = sn;
+      }
+      __syncthreads();
+      for (int k = warp; k < m; k += nwarp) {  // columns p, q of T and V
+        const float cs = s_cs[k], sn = s_sn[k];
+        if (sn == 0.f) continue;
+        const int p = s_p[k], q = s_q[k];
+        for (int i = lane; i < c; i += 32) {
+          float x = T[i * lda + p], y = T[i * lda + q];
+          T[i * lda + p] = cs * x - sn * y;
+          T[i * lda + q] = sn * x + cs * y;
+          x = V[i * lda + p];
+          y = V[i * lda + q];
+          V[i * lda + p] = cs * x - sn * y;
+          V[i * lda + q] = sn * x + cs * y;
+        }
+      }
+      __syncthreads();
+      for (int k = warp; k < m; k += nwarp) {  // rows p, q of T
+        const float cs = s_cs[k], sn = s_sn[k];
+        if (sn == 0.f) continue;
+        const int p = s_p[k], q = s_q[k];
+        for (int j = lane; j < c; j += 32) {
+          const float x = T[p * lda + j], y = T[q * lda + j];
+          T[p * lda + j] = (j == q) ? 0.f : cs * x - sn * y;
+          T[q * lda + j] = (j == p) ? 0.f : sn * x + cs * y;
+        }
+      }
+      __syncthreads();
+    }
+    const float off = __uint_as_float(s_off);
+    __syncthreads();
+    if (off < 1e-6f) break;
+  }
+  for (int e = tid; e < c * c; e += nt) Vc[e] = (double)V[(e / c) * lda + e % c];
+}
+
+// X[:, idx] <- X[:, idx] V_c, one CTA per row of X.
+__global__ __launch_bounds__(128) void cut_rotate_kernel(int N, double* __restrict__ X, const double* __restrict__ Vc,
+                                                         const int* __restrict__ cinfo) {
+  __shared__ double row[CUT_CMAX];
+  const int c = cinfo[0];
+  if (c < 2) return;
+  const int i = blockIdx.x;
+  for (int b = threadIdx.x; b < c; b += blockDim.x) row[b] = X[(int64_t)i * N + cinfo[1 + b]];
+  __syncthreads();
+  for (int a = threadIdx.x; a < c; a += blockDim.x) {
+    double t = 0.0;
+    for (int b = 0; b < c; ++b) t += row[b] * Vc[(int64_t)b * c + a];
+    X[(int64_t)i * N + cinfo[1 + a]] = t;
+  }
+}
+
+cudaError_t launch_oa_cut_cluster(int N, int r, double* X, const double* lam, double* work, int64_t work_elems,
+                                  cudaStream_t st) {
+  const int64_t nn = (int64_t)N * N;
+  const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(128, cdiv(nn, 1024)));
+  if (N > 512 || work_elems < 4 * nn + 3 * nb + nn) return cudaErrorInvalidValue;
+  const double* XtX = work;
+  int* cinfo = reinterpret_cast<int*>(work + nn);
+  const double* S = work + 2 * nn;
+  double* Vc = work + 3 * nn;
+  const double* part = work + 4 * nn;
+  const int cmax = std::min(N, CUT_CMAX);
+  const size_t smem = (size_t)2 * cmax * (cmax | 1) * sizeof(float);
+  cudaFuncSetAttribute(oa_cut_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  oa_cut_cluster_kernel<<<1, 1024, smem, st>>>(N, r, XtX, S, part, nb, lam, Vc, cinfo);
+  cudaError_t e = launched();
+  if (e) return e;
+  cut_rotate_kernel<<<N, 128, 0, st>>>(N, X, Vc, cinfo);
+  return launched();
+}
+
+// ============================================================================
 // Leading-r selection and the CS step.
 // ============================================================================
 // Sort key with a strict total order: NaN sorts below every number, ties by index,

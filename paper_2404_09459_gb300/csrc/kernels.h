@@ -111,6 +111,12 @@ cudaError_t launch_oa_refine(const double* A, int N, double* X, double* lam, dou
 
 // Gather the r leading eigenvectors (by lam, descending; NaN last) of X (N x N)
 // into Zr (N x r); order receives the permutation.
+// The cluster of eigenvalues (within the last refinement step's delta) that
+// straddles the cut between the r-th and (r+1)-th largest: its block of
+// X^T A X is diagonalised (FP32 Jacobi, shifted and scaled) and its columns of
+// X rotated.  Uses the work buffer of the preceding launch_oa_refine call.
+cudaError_t launch_oa_cut_cluster(int N, int r, double* X, const double* lam, double* work, int64_t work_elems,
+                                  cudaStream_t st);
 cudaError_t launch_select_topr(const double* X, const double* lam, int N, int r, double* Zr,
                                int* order, cudaStream_t st);
 
