@@ -383,8 +383,11 @@ int small_gsvd(gsvd_rand_ctx* h, cudaStream_t st, DevStatus* st_dev, const T* S,
     ProfScope ps(h, GSVD_RAND_STAGE_SMALL_REFINE);
     for (int it = 0; it < oa_iters<T>(); ++it) {
       CU(launch_oa_refine(sb.K, L, sb.X, sb.lam, sb.work, sb.work_elems, st));
-      // after two steps the start's error is gone but a cluster across the cut is not split
-      if (it == 1) CU(launch_oa_cut_cluster(L, r, sb.X, sb.lam, sb.work, sb.work_elems, st));
+      // after two steps the start's error is gone but a cluster across the cut is not split;
+      // on the FP64 path the split is repeated after the third step, whose delta (set by
+      // the second step's Newton correction) takes in the whole unresolved group
+      if (it == 1 || (it == 2 && oa_iters<T>() > 3))
+        CU(launch_oa_cut_cluster(L, r, sb.X, sb.lam, sb.work, sb.work_elems, st));
     }
   }
   ProfScope ps_cs(h, GSVD_RAND_STAGE_SMALL_CS);

@@ -308,9 +308,381 @@ __global__ __launch_bounds__(1024) void eig_f32_kernel(const double* __restrict_
     for (int j = lane; j < N; j += 32) Xout[(int64_t)i * N + j] = (double)Z[(int64_t)i * lda + j];
 }
 
+// ============================================================================
+// The same method for N <= 128 with the matrix in registers.  Thread (w, t)
+// of a 32 x 32 grid (warp w, lane t) holds entries (w + 32 r, t + 32 c),
+// r, c < 4, of A during the reduction and entries (t + 32 r, w + 32 c) of the
+// eigenvector matrix during the back-transformation, so that a row sum (the
+// product A v) and a column sum (v^T Z) are warp sums and the updates stay in
+// registers; shared memory carries only vectors, the reflectors and Z.
+//   1. Householder tridiagonalisation, two barriers per step;
+//   2. eigenvalues by multisection: 4 threads per eigenvalue evaluate Sturm
+//      counts at 4 interior points, shrinking the bracket 5-fold per pass;
+//      eigenvectors of T by the twisted factorisation, one thread each;
+//   3. within each cluster of eigenvalues (gap below 1e-3 of ||T||) the
+//      vectors are orthogonalised by classical Gram-Schmidt applied twice,
+//      column by column with the whole CTA; a column with less than 1e-3 of
+//      its length left is set aside and replaced at the end by a pseudo-random
+//      vector orthogonalised against every accepted column;
+//   4. X = H_0 ... H_{N-3} Z, reflector by reflector, no block barriers.
+// ============================================================================
+namespace {
+constexpr int E_NMAX = 128;
+constexpr float E_CLUSTER = 1e-3f;
+
+template <int R, int C>
+__device__ __forceinline__ float pick(const float (&a)[R][C], int r, int c) {
+  float v = 0.f;
+#pragma unroll
+  for (int i = 0; i < R; ++i)
+#pragma unroll
+    for (int j = 0; j < C; ++j)
+      if (i == r && j == c) v = a[i][j];
+  return v;
+}
+}  // namespace
+
+__global__ __launch_bounds__(1024) void eig128_kernel(const double* __restrict__ Ain, int N,
+                                                      double* __restrict__ Xout, double* __restrict__ lam,
+                                                      float* __restrict__ Ug) {
+  extern __shared__ float esm[];
+  __shared__ float s_d[E_NMAX], s_e[E_NMAX], s_beta[E_NMAX], s_col[2][E_NMAX], s_p[E_NMAX], s_lam[E_NMAX];
+  __shared__ float2 s_de[E_NMAX];
+  __shared__ float s_cf[E_NMAX], s_flag[E_NMAX];
+  __shared__ int s_cstart[E_NMAX];
+  __shared__ float s_scale, s_bound[2], s_nrm;
+  const int tid = threadIdx.x, w = tid >> 5, t = tid & 31;
+  const int lda = N | 1;
+  float* Vref = esm;                       // N x 128: reflector k in row k (zero up to row k)
+  float* Zs = esm + (size_t)N * E_NMAX;    // N x lda: eigenvectors of T, column j
+  float* Us = Zs + (size_t)N * lda;        // N x lda: U pivots of the twisted factorisation, row j
+
+  if (w == 0) {
+    double mx = 0.0;
+    for (int i = t; i < N; i += 32) mx = fmax(mx, fabs(Ain[(int64_t)i * N + i]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (t == 0) s_scale = (float)(mx > 0.0 && isfinite(mx) ? mx : 1.0);
+  }
+  __syncthreads();
+  const float inv = 1.0f / s_scale;
+  float a[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int i = w + 32 * r, j = t + 32 * c;
+      a[r][c] = (i < N && j < N) ? (float)(Ain[(int64_t)i * N + j] * (double)inv) : 0.f;
+    }
+
+  // ---- 1. tridiagonalisation ------------------------------------------------
+  for (int k = 0; k + 2 < N; ++k) {
+    float* col = s_col[k & 1];
+    if (t == (k & 31)) {  // column k of the current matrix, rows w + 32 r
+      switch (k >> 5) {
+#define EIG_COL(C) \
+  case C:          \
+    for (int r = 0; r < 4; ++r) col[w + 32 * r] = a[r][C]; \
+    break;
+        EIG_COL(0) EIG_COL(1) EIG_COL(2) EIG_COL(3)
+#undef EIG_COL
+      }
+    }
+    __syncthreads();
+    if (w == 0) {  // reflector H = I - beta v v^T with H x = alpha e_1, x = column k below row k
+      const float x0 = col[k + 1];
+      float sg = 0.f;
+      for (int i = k + 1 + t; i < N; i += 32) sg = fmaf(col[i], col[i], sg);
+      for (int o = 16; o > 0; o >>= 1) sg += __shfl_xor_sync(0xffffffffu, sg, o);
+      const float sig = sqrtf(sg);
+      const float alpha = x0 >= 0.f ? -sig : sig;
+      const float vtv = 2.f * (sg - x0 * alpha);
+      const float bk = (sig > 0.f && vtv > 0.f) ? 2.f / vtv : 0.f;
+      for (int i = t; i < E_NMAX; i += 32)
+        Vref[(size_t)k * E_NMAX + i] = (bk > 0.f && i > k && i < N) ? (i == k + 1 ? x0 - alpha : col[i]) : 0.f;
+      if (t == 0) {
+        s_beta[k] = bk;
+        s_e[k] = bk > 0.f ? alpha : x0;
+        s_d[k] = col[k];
+      }
+    }
+    __syncthreads();
+    const float bk = s_beta[k];
+    if (bk == 0.f) continue;  // uniform: nothing to annihilate
+    const float* vk = Vref + (size_t)k * E_NMAX;
+    float vr[4], vc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      vr[q] = vk[w + 32 * q];
+      vc[q] = vk[t + 32 * q];
+    }
+    // p = beta A v over the active rows; per-warp share of p^T v
+    float pvw = 0.f;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      float sr = 0.f;
+      if (w + 32 * r > k) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (32 * c + 31 > k) sr = fmaf(a[r][c], vc[c], sr);
+        for (int o = 16; o > 0; o >>= 1) sr += __shfl_xor_sync(0xffffffffu, sr, o);
+        sr *= bk;
+        pvw = fmaf(sr, vr[r], pvw);
+      }
+      if (t == 0) s_p[w + 32 * r] = sr;
+    }
+    if (t == 0) s_cf[w] = pvw;
+    __syncthreads();
+    // w = p - (beta/2)(p^T v) v ;  A <- A - v w^T - w v^T
+    float pv = s_cf[t];
+    for (int o = 16; o > 0; o >>= 1) pv += __shfl_xor_sync(0xffffffffu, pv, o);
+    const float kk = 0.5f * bk * pv;
+    float wr[4], wc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      wr[q] = s_p[w + 32 * q] - kk * vr[q];
+      wc[q] = s_p[t + 32 * q] - kk * vc[q];
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      if (w + 32 * r > k) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (32 * c + 31 > k) a[r][c] -= vr[r] * wc[c] + wr[r] * vc[c];
+      }
+  }
+  // the trailing 2 x 2 (or 1 x 1) block
+  if (N >= 2) {
+    if (t == ((N - 2) & 31) && w == ((N - 2) & 31)) s_d[N - 2] = pick(a, (N - 2) >> 5, (N - 2) >> 5);
+    if (t == ((N - 2) & 31) && w == ((N - 1) & 31)) s_e[N - 2] = pick(a, (N - 1) >> 5, (N - 2) >> 5);
+    if (tid == 0) s_beta[N - 2] = 0.f;
+  }
+  if (t == ((N - 1) & 31) && w == ((N - 1) & 31)) s_d[N - 1] = pick(a, (N - 1) >> 5, (N - 1) >> 5);
+  if (tid == 0) s_beta[N - 1] = 0.f;
+  __syncthreads();
+
+  // ---- 2. eigenvalues (multisection) and eigenvectors of T ------------------
+  if (w == 0) {
+    float lo = 3.4e38f, hi = -3.4e38f;
+    for (int i = t; i < N; i += 32) {
+      const float rad = (i > 0 ? fabsf(s_e[i - 1]) : 0.f) + (i < N - 1 ? fabsf(s_e[i]) : 0.f);
+      lo = fminf(lo, s_d[i] - rad);
+      hi = fmaxf(hi, s_d[i] + rad);
+      s_de[i] = make_float2(s_d[i], i > 0 ? s_e[i - 1] * s_e[i - 1] : 0.f);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (t == 0) {
+      const float pad = 1e-6f * fmaxf(fabsf(lo), fabsf(hi)) + 1e-30f;
+      s_bound[0] = lo - pad;
+      s_bound[1] = hi + pad;
+    }
+  }
+  __syncthreads();
+  const float tnorm = fmaxf(fabsf(s_bound[0]), fabsf(s_bound[1]));
+  const float pivmin = fmaxf(1e-30f, 1e-12f * tnorm);
+  if (tid < 4 * E_NMAX) {  // 4 points per eigenvalue: the bracket shrinks 5-fold per pass
+    const int j = min(tid >> 2, N - 1), sub = tid & 3;
+    float lo = s_bound[0], hi = s_bound[1];
+    for (int it = 0; it < 10; ++it) {
+      const float wd = hi - lo;
+      const float x = lo + wd * (float)(sub + 1) * 0.2f;
+      int cnt = 0;
+      float q = 1.f;
+      for (int i = 0; i < N; ++i) {
+        const float2 de = s_de[i];
+        q = (de.x - x) - (i > 0 ? __fdividef(de.y, q) : 0.f);
+        if (fabsf(q) < pivmin) q = -pivmin;
+        cnt += q < 0.f;
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, cnt > j);
+      const unsigned bits = (bal >> (t & 28)) & 0xfu;
+      const int sl = bits ? __ffs(bits) - 1 : 4;
+      const float nlo = sl == 0 ? lo : lo + wd * (float)sl * 0.2f;
+      const float nhi = sl == 4 ? hi : lo + wd * (float)(sl + 1) * 0.2f;
+      lo = nlo;
+      hi = fmaxf(nhi, nlo);
+    }
+    if (sub == 0 && (tid >> 2) < N) {
+      const float lm = 0.5f * (lo + hi);
+      s_lam[j] = lm;
+      lam[j] = (double)lm * (double)s_scale;
+    }
+  }
+  __syncthreads();
+  if (tid < N) {  // eigenvector j of T: twisted factorisation (L in Zs column j, U in Us row j)
+    const int j = tid;
+    const float lm = s_lam[j];
+    float* U = Us + (size_t)j * lda;
+    float dp = s_d[0] - lm;
+    if (fabsf(dp) < pivmin) dp = -pivmin;
+    Zs[j] = dp;
+    for (int i = 0; i + 1 < N; ++i) {
+      dp = s_d[i + 1] - lm - __fdividef(s_e[i], dp) * s_e[i];
+      if (fabsf(dp) < pivmin) dp = -pivmin;
+      Zs[(size_t)(i + 1) * lda + j] = dp;
+    }
+    float dm = s_d[N - 1] - lm;
+    if (fabsf(dm) < pivmin) dm = -pivmin;
+    U[N - 1] = dm;
+    int kt = N - 1;
+    float best = fabsf(Zs[(size_t)(N - 1) * lda + j] + dm - (s_d[N - 1] - lm));
+    for (int i = N - 2; i >= 0; --i) {
+      dm = s_d[i] - lm - __fdividef(s_e[i], dm) * s_e[i];
+      if (fabsf(dm) < pivmin) dm = -pivmin;
+      U[i] = dm;
+      const float g = fabsf(Zs[(size_t)i * lda + j] + dm - (s_d[i] - lm));
+      if (g < best) {
+        best = g;
+        kt = i;
+      }
+    }
+    // z_kt = 1; upward z_i = -(e_i / L_i) z_{i+1} (L_i read just before it is overwritten);
+    // downward z_{i+1} = -(e_i / U_{i+1}) z_i; entries are rescaled when they grow past 2^60
+    float zkt = 1.f, z = 1.f;
+    for (int i = kt - 1; i >= 0; --i) {
+      z = -__fdividef(s_e[i], Zs[(size_t)i * lda + j]) * z;
+      if (fabsf(z) > 1.15e18f) {
+        for (int u = i + 1; u < kt; ++u) Zs[(size_t)u * lda + j] *= 8.67e-19f;
+        zkt *= 8.67e-19f;
+        z *= 8.67e-19f;
+      }
+      Zs[(size_t)i * lda + j] = z;
+    }
+    Zs[(size_t)kt * lda + j] = zkt;
+    z = zkt;
+    for (int i = kt; i + 1 < N; ++i) {
+      z = -__fdividef(s_e[i], U[i + 1]) * z;
+      if (fabsf(z) > 1.15e18f) {
+        for (int u = 0; u <= i; ++u) Zs[(size_t)u * lda + j] *= 8.67e-19f;
+        z *= 8.67e-19f;
+      }
+      Zs[(size_t)(i + 1) * lda + j] = z;
+    }
+  }
+  __syncthreads();
+  // normalise the columns and mark the cluster starts
+  for (int j = w; j < N; j += 32) {
+    float s2 = 0.f;
+    for (int i = t; i < N; i += 32) s2 = fmaf(Zs[(size_t)i * lda + j], Zs[(size_t)i * lda + j], s2);
+    for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    const bool ok = s2 > 0.f && isfinite(s2);
+    const float sc = ok ? rsqrtf(s2) : 0.f;
+    for (int i = t; i < N; i += 32) Zs[(size_t)i * lda + j] = ok ? Zs[(size_t)i * lda + j] * sc : (i == j ? 1.f : 0.f);
+  }
+  if (tid == 0) {
+    int st = 0;
+    for (int j = 0; j < N; ++j) {
+      if (j > 0 && !(s_lam[j] - s_lam[j - 1] <= E_CLUSTER * tnorm)) st = j;
+      s_cstart[j] = st;
+      s_flag[j] = 1.f;
+    }
+  }
+  __syncthreads();
+
+  // ---- 3. clustered columns: CGS2 against the accepted columns of the cluster -
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int j = 0; j < N; ++j) {
+      const int cs = pass == 0 ? s_cstart[j] : 0;
+      if (pass == 0 && cs == j) continue;  // first of its cluster (or a singleton)
+      if (pass == 1) {
+        if (s_flag[j] >= 0.f) continue;
+        for (int i = tid; i < N; i += 1024) Zs[(size_t)i * lda + j] = hash_unit((uint32_t)j, (uint32_t)i);
+        __syncthreads();
+      }
+      const int ce = pass == 0 ? j : N;
+      for (int rep = 0; rep < 2; ++rep) {
+        for (int c = cs + w; c < ce; c += 32) {
+          const bool acc = c != j && s_flag[c] >= 0.f;
+          float s = 0.f;
+          if (acc)
+            for (int i = t; i < N; i += 32) s = fmaf(Zs[(size_t)i * lda + c], Zs[(size_t)i * lda + j], s);
+          for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+          if (t == 0) s_cf[c] = acc ? s : 0.f;
+        }
+        __syncthreads();
+        {
+          const int i = tid >> 3, part = tid & 7;
+          float s = 0.f;
+          if (i < N)
+            for (int c = cs + part; c < ce; c += 8) s = fmaf(Zs[(size_t)i * lda + c], s_cf[c], s);
+          s += __shfl_xor_sync(0xffffffffu, s, 1);
+          s += __shfl_xor_sync(0xffffffffu, s, 2);
+          s += __shfl_xor_sync(0xffffffffu, s, 4);
+          __syncthreads();
+          if (i < N && part == 0) Zs[(size_t)i * lda + j] -= s;
+        }
+        __syncthreads();
+      }
+      if (w == 0) {
+        float s2 = 0.f;
+        for (int i = t; i < N; i += 32) s2 = fmaf(Zs[(size_t)i * lda + j], Zs[(size_t)i * lda + j], s2);
+        for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        // the column was unit length (pass 0) or ~N/12 (pass 1) before the projection
+        const float before = pass == 0 ? 1.f : (float)N / 12.f;
+        const bool dep = !(s2 > 1e-6f * before) || !(s2 > 0.f);
+        if (t == 0) {
+          s_nrm = dep && pass == 0 ? 0.f : rsqrtf(s2 > 0.f ? s2 : 1.f);
+          s_flag[j] = dep && pass == 0 ? -1.f : 1.f;
+        }
+      }
+      __syncthreads();
+      const float sc = s_nrm;
+      for (int i = tid; i < N; i += 1024) Zs[(size_t)i * lda + j] *= sc;
+      __syncthreads();
+    }
+  }
+
+  // ---- 4. back-transformation with Z in registers ---------------------------
+  float z[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int i = t + 32 * r, j = w + 32 * c;
+      z[r][c] = (i < N && j < N) ? Zs[(size_t)i * lda + j] : 0.f;
+    }
+  for (int k = N - 3; k >= 0; --k) {
+    const float bk = s_beta[k];
+    if (bk == 0.f) continue;
+    float v[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) v[r] = Vref[(size_t)k * E_NMAX + t + 32 * r];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float s = 0.f;
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        if (32 * r + 31 > k) s = fmaf(v[r], z[r][c], s);
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      s *= bk;
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        if (32 * r + 31 > k) z[r][c] -= s * v[r];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int i = t + 32 * r, j = w + 32 * c;
+      if (i < N && j < N) Zs[(size_t)i * lda + j] = z[r][c];
+    }
+  __syncthreads();
+  for (int e = tid; e < N * N; e += 1024) Xout[e] = (double)Zs[(size_t)(e / N) * lda + e % N];
+}
+
 cudaError_t launch_eig_f32(const double* A, int N, double* X, double* lam, float* scratch, cudaStream_t st) {
   if (N < 1 || N > 1024) return cudaErrorInvalidValue;
   const int lda = N | 1;
+  if (N <= E_NMAX) {
+    const size_t smem = ((size_t)N * E_NMAX + 2 * (size_t)N * lda) * sizeof(float);
+    cudaFuncSetAttribute(eig128_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    eig128_kernel<<<1, 1024, smem, st>>>(A, N, X, lam, scratch);
+    return launched();
+  }
   const size_t smem = (2ull * N * lda + 8ull * N) * sizeof(float);
   const int use_smem = smem <= 200 * 1024;
   cudaFuncSetAttribute(eig_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
