@@ -204,12 +204,12 @@ struct Solver {
     const double u = std::is_same<T, double>::value ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
     const double shift_coef = 11.0 * ((double)rpc + l + 1) * u;
     // pivots below ~8 rpc u relative to their own column are below the Gram's resolution
-    const double tau = 8.0 * (double)std::max<int64_t>(rpc, apply_rows_per_cta(l)) * u;
+    const double tau = 8.0 * (double)std::max<int64_t>(rpc, apply_rows_per_cta(l, (int)sizeof(T))) * u;
     CU(launch_gram_partial<T>(Yin, lp, M, l, b.gpart, chunks, rpc, st));
     CU(launch_gram_reduce(b.gpart, chunks, l, b.W, st));
     CU(launch_chol_shift<TC>(b.W, l, shift_coef, tau, (TC*)b.R, (TC*)b.cscr, st_dev, stage, st));
     CU((launch_apply_rinv<T, TC>(Yin, lp, M, l, (const TC*)b.R, b.tmp, lp, 0, b.gpart, st)));
-    CU(launch_gram_reduce(b.gpart, apply_ctas(M, l), l, b.W, st));
+    CU(launch_gram_reduce(b.gpart, apply_ctas(M, l, (int)sizeof(T)), l, b.W, st));
     CU(launch_chol_shift<TC>(b.W, l, 0.0, tau, (TC*)b.R, (TC*)b.cscr, st_dev, stage + 1, st));
     CU((launch_apply_rinv<T, TC>(b.tmp, lp, M, l, (const TC*)b.R, out, ldo, transpose_out, nullptr, st)));
     return GSVD_RAND_OK;
@@ -437,7 +437,7 @@ int solve_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, const voi
   pl.part_elems = std::min<int64_t>(pl.part_elems, std::max<int64_t>(16ll << 20, n * pl.lp));
   int64_t rpc;
   int gch = gram_chunks(std::max(maxM, n), pl.l, &rpc);
-  int ach = apply_ctas(std::max(maxM, n), pl.l);
+  int ach = apply_ctas(std::max(maxM, n), pl.l, (int)sizeof(T));
   pl.gpart_elems = (int64_t)std::max(gch, ach) * pl.l * pl.l;
 
   // host inputs are staged into the workspace

@@ -574,12 +574,153 @@ __global__ __launch_bounds__(CHOL_THREADS) void chol_shift_kernel(const double* 
     }
 }
 
+// The same elimination for l <= 64 with the augmented rows in registers:
+// 8 warps, thread (w, t) holds rows i = w + 8 r (r < 8) and the column slots
+// t, t + 32 of W and of L^{-1} (32 values).  Step k publishes row k through a
+// double-buffered shared row; every row i > k subtracts (W_ik / W_kk) times it,
+// on all columns: entries left of the pivot become (rounding-level) zeros or
+// lower-triangle values that are never read.  One barrier per step.
+constexpr int CHOL64_THREADS = 256;
+
+template <typename TC>
+__global__ __launch_bounds__(CHOL64_THREADS, 1) void chol64_kernel(const double* __restrict__ W, int l,
+                                                                double shift_coef, double tau_rel,
+                                                                TC* __restrict__ Rinv, DevStatus* st_dev,
+                                                                int stage) {
+  __shared__ TC s_row[2][128];
+  __shared__ TC s_odiag[64], s_scale[64];
+  __shared__ double s_tr;
+  __shared__ int s_bad, s_kept;
+  const int tid = threadIdx.x, w = tid >> 5, t = tid & 31;
+  if (tid == 0) {
+    s_bad = 0;
+    s_kept = 0;
+  }
+  if (w == 0) {
+    double tr = 0.0;
+    for (int i = t; i < l; i += 32) tr += W[(int64_t)i * l + i];
+    for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+    if (t == 0) s_tr = tr;
+  }
+  __syncthreads();
+  const double sh = shift_coef * s_tr;
+  TC a[8][4];
+  bool bad = false;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int i = w + 8 * r;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int j = t + 32 * c;
+      double v = (i < l && j < l) ? W[(int64_t)i * l + j] : 0.0;
+      bad |= !isfinite(v);
+      if (i == j && i < l) {
+        v += sh;
+        s_odiag[i] = (TC)v;
+      }
+      a[r][c] = (TC)v;
+      a[r][2 + c] = (i == j && i < l) ? TC(1) : TC(0);
+    }
+  }
+  if (bad) s_bad = 2;
+  __syncthreads();
+  auto dropped = [&](int k, TC d) { return !(d > (TC)tau_rel * s_odiag[k]); };
+  int bad_k = -1;
+  if (s_bad == 0) {
+    for (int k = 0; k < l; ++k) {
+      TC* row = s_row[k & 1];
+      if (w == (k & 7)) {
+        switch (k >> 3) {
+#define CHOL64_PUB(R) \
+  case R:              \
+    for (int c = 0; c < 4; ++c) row[t + 32 * c] = a[R][c]; \
+    break;
+          CHOL64_PUB(0) CHOL64_PUB(1) CHOL64_PUB(2) CHOL64_PUB(3)
+          CHOL64_PUB(4) CHOL64_PUB(5) CHOL64_PUB(6) CHOL64_PUB(7)
+#undef CHOL64_PUB
+        }
+      }
+      __syncthreads();
+      const TC d = row[k];
+      if (!isfinite(d)) {
+        bad_k = k;
+        break;
+      }
+      if (dropped(k, d)) continue;
+      const TC dinv = TC(1) / d;
+      TC rc[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) rc[c] = row[t + 32 * c];
+      // live column slots (uniform): W columns in (k, l), L^{-1} columns in [0, min(k, l - 1)];
+      // worth testing only at the FP64 rate
+      bool live[4];
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        live[c] = sizeof(TC) == 4 || (32 * c < l && 32 * c + 31 > k);
+        live[2 + c] = sizeof(TC) == 4 || (32 * c < l && 32 * c <= k);
+      }
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int i = w + 8 * r;
+        if (i > k && i < l) {
+          const TC f = row[i] * dinv;
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            if (live[c]) a[r][c] -= f * rc[c];
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // the pivots are the final diagonal entries (row k is not touched after step k)
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int i = w + 8 * r;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+      if (i < l && t + 32 * c == i) s_row[0][i] = a[r][c];
+  }
+  __syncthreads();
+  if (w == 0 && bad_k < 0 && s_bad == 0) {
+    int kept = 0;
+    for (int i = t; i < l; i += 32) {
+      const TC d = s_row[0][i];
+      const bool dr = dropped(i, d);
+      s_scale[i] = dr ? TC(0) : TC(1) / sqrt(d);
+      kept += dr ? 0 : 1;
+    }
+    for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(0xffffffffu, kept, o);
+    if (t == 0) s_kept = kept;
+  }
+  __syncthreads();
+  if (bad_k >= 0 || s_bad || s_kept == 0) {
+    if (tid == 0) set_status(st_dev, (s_bad == 2 || bad_k >= 0) ? -4 : -5, stage, bad_k);
+    return;
+  }
+  // R^{-1}[c][j] = L^{-1}[j][c] / sqrt(d_j) for c <= j, zero below the diagonal
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int j = w + 8 * r;
+    if (j >= l) continue;
+    const TC sj = s_scale[j];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int cc = t + 32 * c;
+      if (cc < l) Rinv[(int64_t)cc * l + j] = cc <= j ? a[r][2 + c] * sj : TC(0);
+    }
+  }
+}
+
 int64_t chol_scratch_elems(int l) { return (int64_t)l * (l | 1); }
 
 template <typename TC>
 cudaError_t launch_chol_shift(const double* W, int l, double shift_coef, double tau_rel, TC* Rinv,
                               TC* scratch, DevStatus* st_dev, int stage, cudaStream_t st) {
   if (l < 1 || l > 256) return cudaErrorInvalidValue;
+  if (l <= 64) {
+    chol64_kernel<TC><<<1, CHOL64_THREADS, 0, st>>>(W, l, shift_coef, tau_rel, Rinv, st_dev, stage);
+    return launched();
+  }
   size_t smem = (size_t)chol_scratch_elems(l) * sizeof(TC);
   int use_smem = smem <= 216 * 1024;
   cudaFuncSetAttribute(chol_shift_kernel<TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 216 * 1024);
@@ -599,8 +740,9 @@ template cudaError_t launch_chol_shift<float>(const double*, int, double, double
 // (4 x 4 register blocks) and optional transposed store Qt[j * ldq + row].
 // ============================================================================
 int apply_ct(int l) { return l <= 64 ? 4 : (l <= 128 ? 8 : 16); }
-int64_t apply_rows_per_cta(int l) { return l <= 64 ? 128 : 32; }
-int apply_ctas(int64_t M, int l) { return (int)cdiv(M, apply_rows_per_cta(l)); }
+// FP64 tiles are smaller: at the FP64 rate the work of a 128-row tile would leave most SMs idle
+int64_t apply_rows_per_cta(int l, int elem_bytes) { return l <= 64 ? (elem_bytes == 8 ? 32 : 128) : 32; }
+int apply_ctas(int64_t M, int l, int elem_bytes) { return (int)cdiv(M, apply_rows_per_cta(l, elem_bytes)); }
 
 // RS: R^{-1} staged in shared memory (else read through L1 from global).
 template <typename T, typename TC, int CT, int RT, bool RS>
@@ -704,7 +846,7 @@ cudaError_t launch_apply_rinv(const T* Y, int64_t ldy, int64_t M, int l, const T
                               int transpose_out, double* part, cudaStream_t st) {
   if (l < 1 || l > 256) return cudaErrorInvalidValue;
   const int ct = apply_ct(l);
-  const int lp = 16 * ct, rows = (int)apply_rows_per_cta(l);
+  const int lp = 16 * ct, rows = (int)apply_rows_per_cta(l, (int)sizeof(T));
   const size_t tiles = 2 * (size_t)rows * (lp + 1) * sizeof(T);
   const bool rs = ct <= 8;  // R^{-1} (lp x lp) staged for l <= 128: <= 128 KB in FP64
   const size_t smem = tiles + (rs ? (size_t)lp * lp * sizeof(T) : 0);
@@ -717,7 +859,9 @@ cudaError_t launch_apply_rinv(const T* Y, int64_t ldy, int64_t M, int l, const T
     apply_rinv_kernel<T, TC, CTV, RTV, RSV><<<blocks, 256, smem, st>>>(Y, ldy, M, l, Rinv, Q, ldq,            \
                                                                       transpose_out, part);                    \
   } while (0)
-  if (ct == 4)
+  if (ct == 4 && sizeof(T) == 8)
+    GSVDR_APPLY(4, 2, true);
+  else if (ct == 4)
     GSVDR_APPLY(4, 8, true);
   else if (ct == 8)
     GSVDR_APPLY(8, 2, true);

@@ -74,8 +74,8 @@ cudaError_t launch_chol_shift(const double* W, int l, double shift_coef, double 
 template <typename T, typename TC>
 cudaError_t launch_apply_rinv(const T* Y, int64_t ldy, int64_t M, int l, const TC* Rinv, T* Q, int64_t ldq,
                               int transpose_out, double* part, cudaStream_t st);
-int apply_ctas(int64_t M, int l);
-int64_t apply_rows_per_cta(int l);
+int apply_ctas(int64_t M, int l, int elem_bytes);
+int64_t apply_rows_per_cta(int l, int elem_bytes);
 
 // ---- small FP64 dense kernels (compressed-pair GSVD) -----------------------
 // C (Mr x Nc) = op(A) * op(B) in FP64 accumulation; op(X) = X or X^T.
