@@ -193,15 +193,28 @@ struct Solver {
   DevStatus* st_dev;
   int prec;
   bool use_tc;
+  void* bar;  // grid barrier of the fused CholeskyQR2 (zeroed at solve start)
 
   int orth(SideBufs<T>& b, const T* Yin, int64_t M, int l, int64_t lp, T* out, int64_t ldo,
            int transpose_out, int stage) {
     ProfScope ps(h, GSVD_RAND_STAGE_ORTH);
     // pass 1: shifted Cholesky of the Gram (Fukaya et al. 2020 shift scaled to the
     // Gram's accumulation precision), pass 2: plain CholeskyQR on the result.
+    const double u = std::is_same<T, double>::value ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
+    {
+      // one persistent cooperative kernel when the rows fit in the SMs' shared memory
+      int64_t rp = 0;
+      const int ctas = cholqr2_fused_plan<T, TC>(M, l, &rp);
+      if (ctas > 0 && ctas <= cholqr2_fused_max_ctas()) {
+        const double shift_f = 11.0 * ((double)rp + l + 1) * u;
+        const double tau_f = 8.0 * (double)rp * u;
+        CU((launch_cholqr2_fused<T, TC>(Yin, lp, M, l, ctas, rp, out, ldo, transpose_out, b.gpart, b.W, bar,
+                                        shift_f, tau_f, st_dev, stage, st)));
+        return GSVD_RAND_OK;
+      }
+    }
     int64_t rpc;
     int chunks = gram_chunks(M, l, &rpc);
-    const double u = std::is_same<T, double>::value ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
     const double shift_coef = 11.0 * ((double)rpc + l + 1) * u;
     // pivots below ~8 rpc u relative to their own column are below the Gram's resolution
     const double tau = 8.0 * (double)std::max<int64_t>(rpc, apply_rows_per_cta(l, (int)sizeof(T))) * u;
@@ -438,11 +451,12 @@ int solve_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, const voi
   int64_t rpc;
   int gch = gram_chunks(std::max(maxM, n), pl.l, &rpc);
   int ach = apply_ctas(std::max(maxM, n), pl.l, (int)sizeof(T));
-  pl.gpart_elems = (int64_t)std::max(gch, ach) * pl.l * pl.l;
+  pl.gpart_elems = (int64_t)std::max(std::max(gch, ach), cholqr2_fused_max_ctas()) * pl.l * pl.l;
 
   // host inputs are staged into the workspace
   Bump sizer;
   sizer.take<DevStatus>(1);
+  sizer.take<unsigned char>((int64_t)cholqr2_fused_bar_bytes());
   if (!d1) sizer.take<T>(m * lds);
   if (!d2) sizer.take<T>(p * lds);
   sizer.take<T>((int64_t)pl.L * pl.ldn);
@@ -457,6 +471,7 @@ int solve_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, const voi
   Bump bp;
   bp.base = h->ws;
   DevStatus* st_dev = bp.take<DevStatus>(1);
+  void* bar = bp.take<unsigned char>((int64_t)cholqr2_fused_bar_bytes());
   const T* G1 = (const T*)G1v;
   const T* G2 = (const T*)G2v;
   int64_t l1d = ld1, l2d = ld2;
@@ -477,8 +492,9 @@ int solve_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, const voi
   SideBufs<T> sb1 = side_take<T>(bp, pl, 1, use_tc);
   SmallBufs small = small_take(bp, pl.L, k, n);
   CU(cudaMemsetAsync(st_dev, 0, sizeof(DevStatus), st));
+  CU(cudaMemsetAsync(bar, 0, cholqr2_fused_bar_bytes(), st));
 
-  Solver<T, TC> sv{h, st, st_dev, prec, use_tc};
+  Solver<T, TC> sv{h, st, st_dev, prec, use_tc, bar};
   if ((rc = sv.side(G1, l1d, 0, pl, sb0, q, seed, S))) return rc;
   if ((rc = sv.side(G2, l2d, 1, pl, sb1, q, seed, S + (int64_t)pl.l * pl.ldn))) return rc;
   int gct0 = use_tc ? tc_gx_ctas(m) : gemm_gx_simt_ctas(m);

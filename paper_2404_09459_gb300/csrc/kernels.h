@@ -111,6 +111,19 @@ cudaError_t launch_oa_refine(const double* A, int N, double* X, double* lam, dou
 
 // Gather the r leading eigenvectors (by lam, descending; NaN last) of X (N x N)
 // into Zr (N x r); order receives the permutation.
+// CholeskyQR2 of M x l (l <= 64) as one cooperative persistent kernel (k_cholqr.cu).
+// plan: the CTA count (0 when the shape does not fit: then use the separate
+// kernels) and the rows per CTA.  part needs ctas * l * l doubles; bar is
+// cholqr2_fused_bar_bytes() of device memory, zeroed once before first use.
+size_t cholqr2_fused_bar_bytes();
+int cholqr2_fused_max_ctas();
+template <typename T, typename TC>
+int cholqr2_fused_plan(int64_t M, int l, int64_t* rows_per);
+template <typename T, typename TC>
+cudaError_t launch_cholqr2_fused(const T* Y, int64_t ldy, int64_t M, int l, int ctas, int64_t rows_per, T* Q,
+                                 int64_t ldq, int transpose_out, double* part, double* W, void* bar,
+                                 double shift_coef, double tau_rel, DevStatus* st_dev, int stage, cudaStream_t st);
+
 // The cluster of eigenvalues (within the last refinement step's delta) that
 // straddles the cut between the r-th and (r+1)-th largest: its block of
 // X^T A X is diagonalised (FP32 Jacobi, shifted and scaled) and its columns of

@@ -136,6 +136,16 @@ def test_tf32x3_unaligned_rows_use_cuda_cores():
     _check("tf32x3", G1, G2, spec)
 
 
+@pytest.mark.parametrize("prec,m,p,n,k,os_", [("tf32x3", 3000, 2500, 400, 70, 10), ("fp64", 6000, 5000, 300, 20, 8)])
+def test_separate_kernel_cholqr(prec, m, p, n, k, os_):
+    # l = 80 > 64 (mixed) and 6000-row FP64 sides: CholeskyQR2 as separate kernels instead of the
+    # single persistent kernel
+    spec = PairSpec(m=m, p=p, n=n, r=k + 2, alpha="uniform", decay="exp10", sigma=1e-7, k=k, oversample=os_,
+                    q=1, seed=m)
+    G1, G2, _, _ = planted_pair(spec)
+    _check(prec, G1, G2, spec)
+
+
 @pytest.mark.parametrize("prec", ["bf16"])
 def test_unbuilt_precisions_report_unsupported(prec):
     spec = PairSpec(m=200, p=200, n=64, r=5, sigma=1e-6, k=5, oversample=3, q=1, seed=4)
