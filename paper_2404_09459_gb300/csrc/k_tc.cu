@@ -439,6 +439,29 @@ int pick_stages(int nmma, int mode, bool split) {
   return std::max(2, std::min(s, 8));
 }
 
+// The deepest pipeline that still lets `per_sm` CTAs share an SM.
+int stages_for(int nmma, int mode, bool split, int per_sm) {
+  const int stage = (int)StageLayout(mode, split, nmma).bytes;
+  const int budget = (per_sm >= 2 ? 110 : 210) * 1024 - 2048;
+  return std::max(2, std::min(budget / stage, 8));
+}
+
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      n = 152;
+    }
+  }
+  return n;
+}
+
+// CTAs of a launch with this dynamic shared memory that fit on one SM (228 KB per SM,
+// about 1 KB reserved per CTA).
+int ctas_per_sm(size_t smem) { return std::max(1, (int)((228 * 1024) / (smem + 1024))); }
+
 size_t smem_bytes(int nmma, int stages, int mode, bool split) {
   return 1024 + (size_t)stages * StageLayout(mode, split, nmma).bytes + (3 * (size_t)stages + 1) * 8 + 16;
 }
@@ -482,9 +505,14 @@ cudaError_t tc_gemm_gx(int prec, const float* G, int64_t ldg, int64_t M, int64_t
   CUtensorMap ma, mb;
   if (!make_map(&ma, G, (uint64_t)n, (uint64_t)M, (uint64_t)ldg, TC_BM)) return cudaErrorInvalidValue;
   if (!make_map(&mb, Xt, (uint64_t)n, (uint64_t)nmma, (uint64_t)ldx, (uint32_t)nmma)) return cudaErrorInvalidValue;
-  const int stages = pick_stages(nmma, 0, split);
+  // one wave: when the row tiles exceed the SMs at full depth, a shallower pipeline lets
+  // two CTAs share an SM so that every tile runs at once
+  const int64_t tiles = cdiv(M, TC_BM);
+  int stages = pick_stages(nmma, 0, split);
+  if (tiles > (int64_t)sm_count() * ctas_per_sm(smem_bytes(nmma, stages, 0, split)))
+    stages = stages_for(nmma, 0, split, 2);
   const size_t smem = smem_bytes(nmma, stages, 0, split);
-  const dim3 grid((unsigned)cdiv(M, TC_BM));
+  const dim3 grid((unsigned)tiles);
   if (gnorm_part) {
     if (split)
       launch_tc<0, true, true>(grid, smem, st, ma, mb, Y, ldy, M, l, nmma, n, 0, 0, stages, gnorm_part, st_dev);
@@ -499,22 +527,26 @@ cudaError_t tc_gemm_gx(int prec, const float* G, int64_t ldg, int64_t M, int64_t
   return launched();
 }
 
-int tc_gtq_splits(int64_t M, int64_t n) {
+// Row splits of G^T Q: as many as fill the resident CTA slots in one wave.
+int tc_gtq_splits(int64_t M, int64_t n, int prec) {
   const int64_t ctiles = cdiv(n, TC_BM);
-  int64_t s = std::max<int64_t>(1, (2 * 152 + ctiles - 1) / ctiles);
+  const int nmma = 64;  // slots are sized for the widest basis on the fast path
+  const bool split = prec == 3;
+  const int per_sm = ctas_per_sm(smem_bytes(nmma, pick_stages(nmma, 1, split), 1, split));
+  int64_t s = std::max<int64_t>(1, (int64_t)sm_count() * per_sm / ctiles);
   s = std::min<int64_t>(s, std::max<int64_t>(1, cdiv(M, 4 * TC_BK)));
   return (int)s;
 }
 
 int64_t tc_gtq_part_elems(int64_t M, int64_t n, int l) {
-  return (int64_t)tc_gtq_splits(M, n) * n * round_up(l, 4);
+  return (int64_t)std::max(tc_gtq_splits(M, n, 1), tc_gtq_splits(M, n, 3)) * n * round_up(l, 4);
 }
 
 cudaError_t tc_gemm_gtq(int prec, const float* G, int64_t ldg, int64_t M, int64_t n, const float* Qt, int64_t ldq,
                         int l, float* part, int64_t lp, int* splits_out, int64_t max_part_elems, DevStatus* st_dev,
                         cudaStream_t st) {
   const int nmma = (int)round_up(l, 16);
-  int splits = tc_gtq_splits(M, n);
+  int splits = tc_gtq_splits(M, n, prec);
   while (splits > 1 && (int64_t)splits * n * lp > max_part_elems) --splits;
   // split boundaries on stage (32-row) boundaries so that no tile crosses into the next split
   const int64_t rps = round_up(cdiv(M, splits), TC_BK);
