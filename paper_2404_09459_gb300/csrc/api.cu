@@ -390,7 +390,9 @@ int small_gsvd(gsvd_rand_ctx* h, cudaStream_t st, DevStatus* st_dev, const T* S,
   }
   {
     ProfScope ps(h, GSVD_RAND_STAGE_SMALL_JACOBI);
-    CU(launch_eig_f32(sb.K, L, sb.X, sb.lam, sb.jscratch, st));
+    // K = S S^T: eigenvalues below ~1e-6 ||K|| are FP32 noise; their vectors only need to span
+    // the complement (the top-k cut and the refinement take it from there)
+    CU(launch_eig_f32(sb.K, L, sb.X, sb.lam, sb.jscratch, st, 1e-6));
   }
   {
     ProfScope ps(h, GSVD_RAND_STAGE_SMALL_REFINE);

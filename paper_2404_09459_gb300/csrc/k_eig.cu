@@ -344,12 +344,12 @@ __device__ __forceinline__ float pick(const float (&a)[R][C], int r, int c) {
 
 __global__ __launch_bounds__(1024) void eig128_kernel(const double* __restrict__ Ain, int N,
                                                       double* __restrict__ Xout, double* __restrict__ lam,
-                                                      float* __restrict__ Ug) {
+                                                      float* __restrict__ Ug, float noise_rel) {
   extern __shared__ float esm[];
   __shared__ float s_d[E_NMAX], s_e[E_NMAX], s_beta[E_NMAX], s_col[2][E_NMAX], s_p[E_NMAX], s_lam[E_NMAX];
   __shared__ float2 s_de[E_NMAX];
   __shared__ float s_cf[E_NMAX], s_flag[E_NMAX];
-  __shared__ int s_cstart[E_NMAX];
+  __shared__ int s_cstart[E_NMAX], s_prev[E_NMAX], s_np, s_npan;
   __shared__ float s_scale, s_bound[2], s_nrm;
   const int tid = threadIdx.x, w = tid >> 5, t = tid & 31;
   const int lda = N | 1;
@@ -571,12 +571,14 @@ __global__ __launch_bounds__(1024) void eig128_kernel(const double* __restrict__
     const float sc = ok ? rsqrtf(s2) : 0.f;
     for (int i = t; i < N; i += 32) Zs[(size_t)i * lda + j] = ok ? Zs[(size_t)i * lda + j] * sc : (i == j ? 1.f : 0.f);
   }
+  // flags: 1 accepted, -1 set aside (dependent), 2 noise (|lambda| below noise_rel ||T||: filled
+  // at the end with the orthogonal complement of the other columns)
   if (tid == 0) {
     int st = 0;
     for (int j = 0; j < N; ++j) {
       if (j > 0 && !(s_lam[j] - s_lam[j - 1] <= E_CLUSTER * tnorm)) st = j;
       s_cstart[j] = st;
-      s_flag[j] = 1.f;
+      s_flag[j] = (noise_rel > 0.f && fabsf(s_lam[j]) <= noise_rel * tnorm) ? 2.f : 1.f;
     }
   }
   __syncthreads();
@@ -585,6 +587,7 @@ __global__ __launch_bounds__(1024) void eig128_kernel(const double* __restrict__
   for (int pass = 0; pass < 2; ++pass) {
     for (int j = 0; j < N; ++j) {
       const int cs = pass == 0 ? s_cstart[j] : 0;
+      if (s_flag[j] == 2.f) continue;      // noise column: filled by the complement below
       if (pass == 0 && cs == j) continue;  // first of its cluster (or a singleton)
       if (pass == 1) {
         if (s_flag[j] >= 0.f) continue;
@@ -594,7 +597,7 @@ __global__ __launch_bounds__(1024) void eig128_kernel(const double* __restrict__
       const int ce = pass == 0 ? j : N;
       for (int rep = 0; rep < 2; ++rep) {
         for (int c = cs + w; c < ce; c += 32) {
-          const bool acc = c != j && s_flag[c] >= 0.f;
+          const bool acc = c != j && s_flag[c] == 1.f;
           float s = 0.f;
           if (acc)
             for (int i = t; i < N; i += 32) s = fmaf(Zs[(size_t)i * lda + c], Zs[(size_t)i * lda + j], s);
@@ -632,6 +635,76 @@ __global__ __launch_bounds__(1024) void eig128_kernel(const double* __restrict__
       for (int i = tid; i < N; i += 1024) Zs[(size_t)i * lda + j] *= sc;
       __syncthreads();
     }
+  }
+
+  // ---- 3c. noise columns: orthonormal complement of the other columns --------
+  // Householder QR of the n_nn other columns (copied into Us): the reflectors
+  // H_0 .. H_{n_nn-1} applied to the unit vectors e_{n_nn} .. e_{N-1} span the
+  // orthogonal complement of those columns, orthonormal by construction.
+  if (tid == 0) {
+    int nn = 0, nz = 0;
+    for (int j = 0; j < N; ++j) {
+      if (s_flag[j] == 2.f)
+        s_prev[nz++] = j;  // noise columns
+      else
+        s_cstart[nn++] = j;  // the others (cluster starts are no longer needed)
+    }
+    s_np = nn;
+    s_npan = nz;
+  }
+  __syncthreads();
+  if (s_npan > 0) {
+    const int nn = s_np, nz = s_npan;
+    float* V = Us;  // N x lda, column c = other column s_cstart[c]
+    for (int e = tid; e < N * nn; e += 1024) {
+      const int i = e / nn, c = e % nn;
+      V[(size_t)i * lda + c] = Zs[(size_t)i * lda + s_cstart[c]];
+    }
+    __syncthreads();
+    for (int k = 0; k < nn; ++k) {
+      if (w == 0) {
+        float sg = 0.f;
+        for (int i = k + t; i < N; i += 32) sg = fmaf(V[(size_t)i * lda + k], V[(size_t)i * lda + k], sg);
+        for (int o = 16; o > 0; o >>= 1) sg += __shfl_xor_sync(0xffffffffu, sg, o);
+        const float x0 = V[(size_t)k * lda + k];
+        const float sig = sqrtf(sg);
+        const float alpha = x0 >= 0.f ? -sig : sig;
+        const float den = sg - x0 * alpha;
+        const float bk = (sig > 0.f && den > 0.f) ? 1.f / den : 0.f;
+        __syncwarp();
+        if (t == 0) {
+          V[(size_t)k * lda + k] = x0 - alpha;  // v_k in place (rows k..N-1)
+          s_cf[k] = bk;
+        }
+      }
+      __syncthreads();
+      const float bk = s_cf[k];
+      for (int j = k + 1 + w; j < nn && bk != 0.f; j += 32) {
+        float d = 0.f;
+        for (int i = k + t; i < N; i += 32) d = fmaf(V[(size_t)i * lda + k], V[(size_t)i * lda + j], d);
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        d *= bk;
+        for (int i = k + t; i < N; i += 32) V[(size_t)i * lda + j] -= d * V[(size_t)i * lda + k];
+      }
+      __syncthreads();
+    }
+    // Q e_{nn + q} into noise column q, reflectors in reverse order, a warp per column
+    for (int q = w; q < nz; q += 32) {
+      const int col = s_prev[q];
+      for (int i = t; i < N; i += 32) Zs[(size_t)i * lda + col] = (i == nn + q) ? 1.f : 0.f;
+      __syncwarp();
+      for (int k = nn - 1; k >= 0; --k) {
+        const float bk = s_cf[k];
+        if (bk == 0.f) continue;
+        float d = 0.f;
+        for (int i = k + t; i < N; i += 32) d = fmaf(V[(size_t)i * lda + k], Zs[(size_t)i * lda + col], d);
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        d *= bk;
+        for (int i = k + t; i < N; i += 32) Zs[(size_t)i * lda + col] -= d * V[(size_t)i * lda + k];
+        __syncwarp();
+      }
+    }
+    __syncthreads();
   }
 
   // ---- 4. back-transformation with Z in registers ---------------------------
@@ -674,13 +747,14 @@ __global__ __launch_bounds__(1024) void eig128_kernel(const double* __restrict__
   for (int e = tid; e < N * N; e += 1024) Xout[e] = (double)Zs[(size_t)(e / N) * lda + e % N];
 }
 
-cudaError_t launch_eig_f32(const double* A, int N, double* X, double* lam, float* scratch, cudaStream_t st) {
+cudaError_t launch_eig_f32(const double* A, int N, double* X, double* lam, float* scratch, cudaStream_t st,
+                           double noise_rel) {
   if (N < 1 || N > 1024) return cudaErrorInvalidValue;
   const int lda = N | 1;
   if (N <= E_NMAX) {
     const size_t smem = ((size_t)N * E_NMAX + 2 * (size_t)N * lda) * sizeof(float);
     cudaFuncSetAttribute(eig128_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    eig128_kernel<<<1, 1024, smem, st>>>(A, N, X, lam, scratch);
+    eig128_kernel<<<1, 1024, smem, st>>>(A, N, X, lam, scratch, (float)noise_rel);
     return launched();
   }
   const size_t smem = (2ull * N * lda + 8ull * N) * sizeof(float);

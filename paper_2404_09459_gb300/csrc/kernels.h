@@ -100,7 +100,10 @@ cudaError_t launch_jacobi_f32(const double* A, int N, double* V, double* lam, fl
 // two-pass MGS with cluster replacement): X (N x N, FP64, orthonormal columns),
 // lam (N, ascending).  scratch: eig_scratch_floats(N) floats.
 int64_t eig_scratch_floats(int N);
-cudaError_t launch_eig_f32(const double* A, int N, double* X, double* lam, float* scratch, cudaStream_t st);
+// noise_rel > 0 (N <= 128): eigenvectors of eigenvalues with |lambda| <= noise_rel ||A||, which FP32
+// cannot resolve, are replaced by an orthonormal basis of the complement of the others.
+cudaError_t launch_eig_f32(const double* A, int N, double* X, double* lam, float* scratch, cudaStream_t st,
+                           double noise_rel = 0.0);
 
 // One Ogita-Aishima refinement step of the eigenvectors X (N x N) of the
 // symmetric A, in FP64: R = I - X^T X, S = X^T A X, lam_i = s_ii/(1 - r_ii),
