@@ -79,9 +79,14 @@ typedef struct {
   int device;        /* CUDA device ordinal the context is bound to */
   void *stream;      /* cudaStream_t to enqueue on; NULL = the legacy default stream */
   int prec;          /* gsvd_rand_prec */
-  int adaptive;      /* 0: fixed rank k + oversample (Theorem 3); reserved for Algorithm 1 */
-  int block_b;       /* Algorithm 1 block size b (paper: 100) */
-  double tol;        /* Algorithm 1 relative residual tolerance */
+  int adaptive;      /* 0: fixed rank k + oversample (Theorem 3) with q power steps;
+                        1: bases by Algorithm 1 (blocks of block_b columns until the cumulated
+                        relative residual is <= tol, at most min(M, n, 256) columns per side) */
+  int block_b;       /* Algorithm 1 block size b (paper: 100), 1..256 (FP64: ..224) */
+  double tol;        /* Algorithm 1 relative residual tolerance.  The cumulated residual of
+                        Section 2 cancels below about sqrt(u) of ||G||_F (u of the basis'
+                        orthonormality): tolerances below ~1e-7 (FP64) or ~1e-3 (FP32 data)
+                        may not be certified and end in GSVD_RAND_ERR_TOL_MISS */
   int use_learned;   /* reserved: learned (k, q) proposal */
   const char *mlp_path; /* reserved */
   int flags;         /* GSVD_RAND_FLAG_* */
@@ -129,7 +134,13 @@ const char *gsvd_rand_last_error(gsvd_rand_t h);
  *   resid_out : may be NULL; receives 2 doubles, the relative residual
  *             ||(I - Q_s Q_s^T) G_s||_F / ||G_s||_F of each side in the
  *             cumulated form sqrt(||G_s||_F^2 - ||Q_s^T G_s||_F^2) (Section 2)
- * Errors: ARG, OOM, CUDA, NONFINITE, BREAKDOWN.  Synchronises cfg->stream. */
+ * With cfg->adaptive = 1 the bases come from Algorithm 1 instead (Omega_i from
+ * counter words (t, 0, s, 0x10000 + i)); oversample and q are not used, k is the
+ * capacity of alpha/beta and min(k, l1 + l2) pairs are returned (*r_out), and
+ * resid_out receives the final cumulated estimates.  When a side reaches its
+ * column cap above tol the results are still written and TOL_MISS is returned.
+ * Errors: ARG, OOM, CUDA, NONFINITE, BREAKDOWN, TOL_MISS (adaptive).
+ * Synchronises cfg->stream. */
 int gsvd_rand_solve(gsvd_rand_t h, const void *G1, int64_t m, int64_t ld1, const void *G2,
                     int64_t p, int64_t ld2, int64_t n, int k, int oversample, int q,
                     uint64_t seed, double *alpha, double *beta, int *r_out, double *resid_out);
@@ -198,6 +209,11 @@ int gsvd_rand_philox(gsvd_rand_t h, uint64_t count, uint64_t seed, uint32_t pair
  * context has GSVD_RAND_FLAG_PROFILE.  Errors: ARG (bad stage). */
 int gsvd_rand_profile_get(gsvd_rand_t h, int stage, double *total_ms, int64_t *calls);
 int gsvd_rand_profile_reset(gsvd_rand_t h);
+
+/* Columns of the two bases used by the last gsvd_rand_solve on h: k + oversample each on
+ * the fixed path, the Algorithm 1 block counts times block_b (or the cap) on the adaptive
+ * path.  Errors: ARG (NULL handle). */
+int gsvd_rand_basis_cols(gsvd_rand_t h, int *l1, int *l2);
 
 /* Total number of CUDA kernels this library has launched in this process. */
 uint64_t gsvd_rand_launch_count(void);

@@ -12,6 +12,7 @@ algorithms for GSVs", arXiv:2404.09459):
   gsvd.pencil_gsvd     brute force for tiny pairs (symmetric-definite pencil)
   gsvd.rand_gsvd       Algorithm 2 with the fixed-rank basis of Theorem 3 + q power steps
   gsvd.adaptive_basis  Algorithm 1 (BasisExt) with the cumulated residual of Section 2
+  gsvd.rand_gsvd_adaptive  Algorithm 2 on the Algorithm 1 bases
   gsvd.metrics         theta, rho, P1, P2, D1, D2 of Section 1
   gsvd.perturbation_E  the E of Lemma "per" / Theorem "exp" (Section 3)
 

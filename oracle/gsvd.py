@@ -182,6 +182,31 @@ def adaptive_basis(G, tol: float, b: int, seed: int, pair: int = 0, side: int = 
     return Q, hist
 
 
+def rand_gsvd_adaptive(G1, G2, tol: float, b: int, seed: int, r: int, pair: int = 0,
+                       max_cols: int | None = None):
+    """Algorithm 2 on the bases of Algorithm 1 (adaptive range finder per side).
+
+    Q_s = adaptive_basis(G_s, tol, b) (blocks of b columns until the cumulated
+    relative residual is <= tol or the column cap is reached), B_s = Q_s^T G_s,
+    then the GSVs of the stack [B1; B2] truncated to min(r, l1 + l2).  Returns a
+    dict with alpha, beta, the column counts l1, l2 and the residual estimate
+    histories of both sides.
+    """
+    out = {"hist": []}
+    Bs, ls = [], []
+    for s, G in enumerate((G1, G2)):
+        G = np.asarray(G, dtype=np.float64)
+        Q, hist = adaptive_basis(G, tol, b, seed, pair, s, max_cols)
+        Bs.append(Q.T @ G)
+        ls.append(Q.shape[1])
+        out["hist"].append(hist)
+    S = np.vstack(Bs)
+    rr = min(r, S.shape[0])
+    alpha, beta, _ = gsv_from_stack(S, ls[0], rr)
+    out.update(alpha=alpha, beta=beta, l1=ls[0], l2=ls[1])
+    return out
+
+
 def metrics(alpha, beta, pad_to_n: int = 0, pad_mode: int = 0):
     """Comparative quantities of Section 1 from GSV pairs.
 

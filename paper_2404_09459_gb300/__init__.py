@@ -23,7 +23,7 @@ FLAG_CHOL_FP64 = 1
 EXPORTS = ("gsvd_rand_config_init", "gsvd_rand_create", "gsvd_rand_destroy", "gsvd_rand_last_error",
            "gsvd_rand_solve", "gsvd_rand_metrics", "gsvd_rand_gaussian", "gsvd_rand_philox",
            "gsvd_rand_profile_get", "gsvd_rand_profile_reset", "gsvd_rand_launch_count",
-           "gsvd_rand_metrics_noalloc")
+           "gsvd_rand_metrics_noalloc", "gsvd_rand_basis_cols")
 NOALLOC_MAX_N = 32768
 FLAG_PROFILE = 2
 STAGES = ("sketch", "gtq", "orth", "small", "small_gram", "small_jacobi", "small_refine", "small_cs")
@@ -70,6 +70,7 @@ def load_library(path: str | None = None):
     lib.gsvd_rand_launch_count.argtypes = []
     lib.gsvd_rand_launch_count.restype = C.c_uint64
     lib.gsvd_rand_metrics_noalloc.argtypes = [i32, vp, vp, vp, i32, i32, i32, vp, vp, vp, vp, vp]
+    lib.gsvd_rand_basis_cols.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     for name in EXPORTS:
         if name not in ("gsvd_rand_last_error", "gsvd_rand_launch_count"):
             getattr(lib, name).restype = C.c_int
@@ -110,13 +111,17 @@ class Context:
     stream without torch).
     """
 
-    def __init__(self, prec: str = "tf32", device: int = 0, stream=None, flags: int = 0):
+    def __init__(self, prec: str = "tf32", device: int = 0, stream=None, flags: int = 0,
+                 adaptive: bool = False, block_b: int = 100, tol: float = 1e-4):
         self.lib = load_library()
         cfg = _Config()
         self.lib.gsvd_rand_config_init(C.byref(cfg))
         cfg.device = device
         cfg.prec = PREC[prec]
         cfg.flags = flags
+        cfg.adaptive = 1 if adaptive else 0
+        cfg.block_b = block_b
+        cfg.tol = tol
         if stream is None:
             try:
                 import torch
@@ -185,7 +190,14 @@ class Context:
         rc = self.lib.gsvd_rand_solve(self.h, p1, m, ld1, p2, p, ld2, n1, k, oversample, q, seed, pa, pb,
                                       C.addressof(r), C.addressof(resid))
         self._check(rc)
-        return dict(alpha=alpha, beta=beta, r=r.value, resid=(resid[0], resid[1]))
+        rr = r.value
+        return dict(alpha=alpha[:rr], beta=beta[:rr], r=rr, resid=(resid[0], resid[1]))
+
+    def basis_cols(self):
+        """Columns (l1, l2) of the two bases of the last solve."""
+        a, b = C.c_int(0), C.c_int(0)
+        self._check(self.lib.gsvd_rand_basis_cols(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
 
     def metrics(self, alpha, beta, pad_to_n: int = 0, pad_mode: int = 0):
         """Section 1 quantities: dict(theta, rho, P1, P2, D1, D2)."""

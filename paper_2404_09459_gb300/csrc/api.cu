@@ -33,6 +33,7 @@ struct gsvd_rand_ctx {
   DevStatus* st_host = nullptr;  // pinned
   double* res_host = nullptr;    // pinned, 4 doubles
   int tc_ok = -1;                // tensor-core path usable on this device
+  int last_cols[2] = {0, 0};     // basis columns per side of the last solve
   // optional per-stage CUDA-event timing (GSVD_RAND_FLAG_PROFILE)
   struct Rec {
     int stage;
@@ -224,7 +225,13 @@ struct Solver {
     CU((launch_apply_rinv<T, TC>(Yin, lp, M, l, (const TC*)b.R, b.tmp, lp, 0, b.gpart, st)));
     CU(launch_gram_reduce(b.gpart, apply_ctas(M, l, (int)sizeof(T)), l, b.W, st));
     CU(launch_chol_shift<TC>(b.W, l, 0.0, tau, (TC*)b.R, (TC*)b.cscr, st_dev, stage + 1, st));
-    CU((launch_apply_rinv<T, TC>(b.tmp, lp, M, l, (const TC*)b.R, out, ldo, transpose_out, nullptr, st)));
+    // CholeskyQR a third time (shifted CholeskyQR3): the shifted first pass leaves Q1
+    // far from orthonormal when Y is ill-conditioned (rank-deficient sketches)
+    T* q2 = b.tmp + (int64_t)M * lp;
+    CU((launch_apply_rinv<T, TC>(b.tmp, lp, M, l, (const TC*)b.R, q2, lp, 0, b.gpart, st)));
+    CU(launch_gram_reduce(b.gpart, apply_ctas(M, l, (int)sizeof(T)), l, b.W, st));
+    CU(launch_chol_shift<TC>(b.W, l, 0.0, tau, (TC*)b.R, (TC*)b.cscr, st_dev, stage + 1, st));
+    CU((launch_apply_rinv<T, TC>(q2, lp, M, l, (const TC*)b.R, out, ldo, transpose_out, nullptr, st)));
     return GSVD_RAND_OK;
   }
 
@@ -306,7 +313,7 @@ SideBufs<T> side_take(Bump& bp, const Plan& pl, int s, bool tc) {
   b.Xt = bp.take<T>(pl.lx * pl.ldx);
   b.Y = bp.take<T>(M * pl.lp);
   b.Q = bp.take<T>(std::max(M * pl.lp, pl.lx * round_up(M, 4)));
-  b.tmp = bp.take<T>(std::max(M, pl.n) * pl.lp);
+  b.tmp = bp.take<T>(2 * std::max(M, pl.n) * pl.lp);
   b.Z = bp.take<T>(pl.n * pl.lp);
   b.part = bp.take<T>(pl.part_elems);
   b.gpart = bp.take<double>(pl.gpart_elems);
@@ -369,10 +376,11 @@ SmallBufs small_take(Bump& bp, int L, int r, int64_t n) {
 // the gaps exceed the threshold delta, so two reach FP64 accuracy for gaps
 // >~1e-3 ||K||.  K = S S^T squares the spectrum: eigenvalues 1e-6 ||K|| apart
 // start as one cluster and separate only as delta shrinks, hence five on the
-// FP64 path (1e-10 target) and three on the mixed paths (1e-4 target).
+// FP64 path (1e-10 target; a sixth absorbs the slower start of graded spectra) and three on
+// the mixed paths (1e-4 target).
 template <typename T>
 constexpr int oa_iters() {
-  return std::is_same<T, double>::value ? 5 : 3;
+  return std::is_same<T, double>::value ? 6 : 3;
 }
 
 // Compressed-pair GSVD (Algorithm 2 with the rank-revealing reading): the r
@@ -523,6 +531,7 @@ int solve_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, const voi
                 c == GSVD_RAND_ERR_BREAKDOWN ? ": Cholesky breakdown even with the shift (rank-deficient sketch?)"
                                              : (c == GSVD_RAND_ERR_NONFINITE ? ": non-finite values" : ""));
   }
+  h->last_cols[0] = h->last_cols[1] = pl.l;
   if (r_out) {
     if (is_device_ptr(r_out))
       CU(cudaMemcpy(r_out, &k, sizeof(int), cudaMemcpyHostToDevice));
@@ -535,6 +544,227 @@ int solve_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, const voi
     else
       memcpy(resid_out, h->res_host, 2 * sizeof(double));
   }
+  h->err.clear();
+  return GSVD_RAND_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 1 (BasisExt) per side, then Algorithm 2 on the compressed pair.
+// Per block i: Omega_i (n x b, Philox stream 0x10000 + i), Y = G Omega_i, twice
+// Y -= Q (Q^T Y), P = orth(Y), P = orth(P - Q (Q^T P)), Q = [Q P], and the
+// cumulated residual sqrt(||G||^2 - sum_i ||P_i^T G||^2) / ||G|| (Section 2),
+// read back to the host to decide the stop.  Q is row-major M x capp; the
+// projections and G^T P run on CUDA cores, Y = G Omega_i on tensor cores in
+// the TF32 modes.  The cumulated form cancels below about sqrt(u) of ||G||
+// (u of the basis' orthonormality): ~1e-8 in FP64, ~3e-4 with FP32 data.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void sub_inplace_kernel(T* __restrict__ Y, int64_t ldy, const T* __restrict__ D, int64_t ldd,
+                                   int64_t M, int cols) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= M * cols) return;
+  const int64_t i = e / cols;
+  const int j = (int)(e % cols);
+  Y[i * ldy + j] -= D[i * ldd + j];
+}
+
+template <typename T, typename TC>
+int solve_adaptive_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, const void* G2v, int64_t p,
+                     int64_t ld2, int64_t n, int k, uint64_t seed, double* alpha, double* beta, int* r_out,
+                     double* resid_out) {
+  cudaStream_t st = h->stream;
+  const int prec = h->cfg.prec;
+  if (prec == GSVD_RAND_BF16)
+    return fail(h, GSVD_RAND_ERR_UNSUPPORTED, "precision mode %d is not built yet", prec);
+  const int bsz = h->cfg.block_b;
+  const double tol = h->cfg.tol;
+  if (bsz < 1 || bsz > 256) return fail(h, GSVD_RAND_ERR_ARG, "block_b must be in [1, 256]");
+  if (!(tol >= 0.0)) return fail(h, GSVD_RAND_ERR_ARG, "tol must be >= 0");
+  bool use_tc = prec == GSVD_RAND_TF32 || prec == GSVD_RAND_TF32X3;
+  if (use_tc && !h->tc_ok) return fail(h, GSVD_RAND_ERR_UNSUPPORTED, "tensor-core path unavailable on this device");
+  const int64_t lds = round_up(n, 4);
+  const bool d1 = is_device_ptr(G1v), d2 = is_device_ptr(G2v);
+  if (use_tc && ((d1 && !tc_shape_ok(G1v, ld1, bsz)) || (d2 && !tc_shape_ok(G2v, ld2, bsz)))) use_tc = false;
+  const int64_t Ms[2] = {m, p};
+  int cap[2];
+  for (int s = 0; s < 2; ++s) cap[s] = (int)std::min<int64_t>(std::min<int64_t>(Ms[s], n), 256);
+  const int capmax = std::max(cap[0], cap[1]);
+  const int64_t capp = round_up(capmax, 4), bp = round_up(bsz, 4), bx = round_up(bsz, 16);
+  const int64_t ldx = round_up(n, 32), ldc = round_up(capmax, 32), ldn = round_up(n, 4);
+  const int64_t maxM = std::max(m, p);
+  const int Lmax = cap[0] + cap[1];
+  const int64_t part_elems = std::max<int64_t>(16ll << 20, n * capp);
+  int64_t rpc;
+  const int gch = gram_chunks(maxM, bsz, &rpc);
+  const int ach = apply_ctas(maxM, bsz, (int)sizeof(T));
+  const int64_t gpart_elems = (int64_t)std::max(std::max(gch, ach), cholqr2_fused_max_ctas()) * bsz * bsz;
+  const int gn = std::max(use_tc ? tc_gx_ctas(maxM) : 1, gemm_gx_simt_ctas(maxM)) + 8;
+  const int64_t sqn = cdiv(n * capp, 256) + 8;
+
+  // workspace: status, barrier, staged inputs, the two bases, shared block buffers, S, small GSVD
+  auto carve = [&](Bump& bp_) {
+    struct {
+      DevStatus* st_dev; void* bar; T* g[2]; T* Q[2]; T* Xt; T* Y; T* QC; T* Ct; T* Z; T* part; double* sq;
+      double* gn; SideBufs<T> ob; T* S;
+    } w{};
+    w.st_dev = bp_.take<DevStatus>(1);
+    w.bar = bp_.take<unsigned char>((int64_t)cholqr2_fused_bar_bytes());
+    w.g[0] = d1 ? nullptr : bp_.take<T>(m * lds);
+    w.g[1] = d2 ? nullptr : bp_.take<T>(p * lds);
+    for (int s = 0; s < 2; ++s) w.Q[s] = bp_.take<T>(Ms[s] * capp);
+    w.Xt = bp_.take<T>(bx * ldx);
+    w.Y = bp_.take<T>(maxM * bp);
+    w.QC = bp_.take<T>(maxM * bp);
+    w.Ct = bp_.take<T>(bp * ldc);
+    w.Z = bp_.take<T>(std::max<int64_t>(n, capp) * bp);
+    w.part = bp_.take<T>(part_elems);
+    w.sq = bp_.take<double>(sqn);
+    w.gn = bp_.take<double>(gn);
+    w.ob.tmp = bp_.take<T>(2 * std::max<int64_t>(maxM, n) * bp);
+    w.ob.gpart = bp_.take<double>(gpart_elems);
+    w.ob.W = bp_.take<double>((int64_t)bsz * bsz);
+    w.ob.R = bp_.take<double>((int64_t)bsz * bsz);
+    w.ob.cscr = bp_.take<double>(chol_scratch_elems(bsz));
+    w.S = bp_.take<T>((int64_t)Lmax * ldn);
+    return w;
+  };
+  Bump sizer;
+  carve(sizer);
+  Bump sb_sizer;
+  small_take(sb_sizer, Lmax, k, n);
+  int rc = ensure_ws(h, sizer.off + sb_sizer.off + 8192);
+  if (rc) return rc;
+  Bump bpw;
+  bpw.base = h->ws;
+  auto w = carve(bpw);
+  SmallBufs small = small_take(bpw, Lmax, k, n);
+  const T* Gs[2] = {(const T*)G1v, (const T*)G2v};
+  int64_t ldg[2] = {ld1, ld2};
+  const void* src[2] = {G1v, G2v};
+  const bool dev[2] = {d1, d2};
+  for (int s = 0; s < 2; ++s)
+    if (!dev[s]) {
+      CU(cudaMemcpy2DAsync(w.g[s], lds * sizeof(T), src[s], ldg[s] * sizeof(T), n * sizeof(T), Ms[s],
+                           cudaMemcpyHostToDevice, st));
+      Gs[s] = w.g[s];
+      ldg[s] = lds;
+    }
+  CU(cudaMemsetAsync(w.st_dev, 0, sizeof(DevStatus), st));
+  CU(cudaMemsetAsync(w.bar, 0, cholqr2_fused_bar_bytes(), st));
+  Solver<T, TC> sv{h, st, w.st_dev, prec, use_tc, w.bar};
+  std::vector<double> host(std::max<int64_t>(sqn, gn));
+
+  // Y (M x bi, ld ldy) -= Qb (M x cols) (Qb^T Y)
+  auto project = [&](const T* Qb, int64_t M, int cols, T* Yp, int64_t ldy, int bi) -> int {
+    const int splits = gemm_gtq_splits(M, cols, bi, part_elems);
+    CU((launch_gemm_gtq_simt<T, T>(Qb, capp, M, cols, Yp, ldy, bi, w.part, bp, splits, st)));
+    int blocks = 0;
+    CU((launch_reduce_splits<T, T>(w.part, splits, cols, bi, bp, w.Ct, ldc, 1, nullptr, &blocks, st)));
+    CU(launch_gemm_gx_simt<T>(Qb, capp, M, cols, w.Ct, ldc, bi, w.QC, bp, nullptr, st));
+    sub_inplace_kernel<T><<<(unsigned)cdiv(M * bi, 256), 256, 0, st>>>(Yp, ldy, w.QC, bp, M, bi);
+    CU(launched());
+    return GSVD_RAND_OK;
+  };
+
+  int cols[2] = {0, 0};
+  double est[2] = {1.0, 1.0};
+  bool miss = false;
+  for (int s = 0; s < 2; ++s) {
+    const int64_t M = Ms[s];
+    const T* G = Gs[s];
+    T* Q = w.Q[s];
+    double g2 = 0.0, acc = 0.0;
+    int c = 0;
+    for (int i = 0; c < cap[s]; ++i) {
+      const int bi = std::min(bsz, cap[s] - c);
+      CU(launch_gaussian_kmajor<T>(w.Xt, ldx, n, bi, (int)round_up(bi, 16), seed, 0u, (uint32_t)s,
+                                   (uint32_t)(GSVD_RAND_STREAM_ADAPTIVE + i), st));
+      {
+        ProfScope ps(h, GSVD_RAND_STAGE_SKETCH);
+        double* gnp = i == 0 ? w.gn : nullptr;
+        bool done = false;
+        if constexpr (std::is_same<T, float>::value) {
+          if (use_tc) {
+            CU(tc_gemm_gx(prec, G, ldg[s], M, n, w.Xt, ldx, bi, w.Y, bp, gnp, w.st_dev, st));
+            done = true;
+          }
+        }
+        if (!done) CU(launch_gemm_gx_simt<T>(G, ldg[s], M, n, w.Xt, ldx, bi, w.Y, bp, gnp, st));
+      }
+      if (i == 0) {
+        const int ng = use_tc ? tc_gx_ctas(M) : gemm_gx_simt_ctas(M);
+        CU(cudaMemcpyAsync(host.data(), w.gn, ng * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CU(cudaStreamSynchronize(st));
+        for (int j = 0; j < ng; ++j) g2 += host[j];
+      }
+      if (c > 0)
+        for (int rep = 0; rep < 2; ++rep)
+          if ((rc = project(Q, M, c, w.Y, bp, bi))) return rc;
+      if ((rc = sv.orth(w.ob, w.Y, M, bi, bp, Q + c, capp, 0, 10 * s + 1))) return rc;
+      if (c > 0) {
+        if ((rc = project(Q, M, c, Q + c, capp, bi))) return rc;
+        if ((rc = sv.orth(w.ob, Q + c, M, bi, capp, Q + c, capp, 0, 10 * s + 3))) return rc;
+      }
+      c += bi;
+      // ||P^T G||_F^2 of the new block
+      {
+        ProfScope ps(h, GSVD_RAND_STAGE_GTQ);
+        const int splits = gemm_gtq_splits(M, n, bi, part_elems);
+        CU((launch_gemm_gtq_simt<T, T>(G, ldg[s], M, n, Q + (c - bi), capp, bi, w.part, bp, splits, st)));
+        int blocks = 0;
+        CU((launch_reduce_splits<T, T>(w.part, splits, n, bi, bp, w.Z, bp, 0, w.sq, &blocks, st)));
+        CU(cudaMemcpyAsync(host.data(), w.sq, blocks * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CU(cudaStreamSynchronize(st));
+        for (int j = 0; j < blocks; ++j) acc += host[j];
+      }
+      est[s] = g2 > 0.0 ? std::sqrt(std::max(g2 - acc, 0.0) / g2) : 0.0;
+      if (est[s] <= tol) break;
+    }
+    cols[s] = c;
+    if (est[s] > tol) miss = true;
+  }
+  // B_s = Q_s^T G_s as rows of S, then the compressed-pair GSVD
+  for (int s = 0; s < 2; ++s) {
+    ProfScope ps(h, GSVD_RAND_STAGE_GTQ);
+    const int splits = gemm_gtq_splits(Ms[s], n, cols[s], part_elems);
+    CU((launch_gemm_gtq_simt<T, T>(Gs[s], ldg[s], Ms[s], n, w.Q[s], capp, cols[s], w.part, capp, splits, st)));
+    int blocks = 0;
+    CU((launch_reduce_splits<T, T>(w.part, splits, n, cols[s], capp, w.S + (s ? (int64_t)cols[0] * ldn : 0), ldn,
+                                   1, nullptr, &blocks, st)));
+  }
+  const int L = cols[0] + cols[1];
+  const int r = std::min(k, L);
+  {
+    ProfScope ps(h, GSVD_RAND_STAGE_SMALL);
+    if ((rc = small_gsvd<T>(h, st, w.st_dev, w.S, ldn, cols[0], L, n, r, small))) return rc;
+  }
+  const bool ad = is_device_ptr(alpha), bd = is_device_ptr(beta);
+  CU(cudaMemcpyAsync(h->st_host, w.st_dev, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(alpha, small.alpha, r * sizeof(double), ad ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(beta, small.beta, r * sizeof(double), bd ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  prof_collect(h);
+  if (h->st_host->code) {
+    const int c = h->st_host->code;
+    return fail(h, c, "device status %d at stage %d (index %d)", c, h->st_host->where, h->st_host->index);
+  }
+  if (r_out) {
+    if (is_device_ptr(r_out))
+      CU(cudaMemcpy(r_out, &r, sizeof(int), cudaMemcpyHostToDevice));
+    else
+      *r_out = r;
+  }
+  if (resid_out) {
+    if (is_device_ptr(resid_out))
+      CU(cudaMemcpy(resid_out, est, 2 * sizeof(double), cudaMemcpyHostToDevice));
+    else
+      memcpy(resid_out, est, 2 * sizeof(double));
+  }
+  h->last_cols[0] = cols[0];
+  h->last_cols[1] = cols[1];
+  if (miss)
+    return fail(h, GSVD_RAND_ERR_TOL_MISS, "basis reached its cap (%d, %d columns) with residual (%.3g, %.3g) above %g",
+                cols[0], cols[1], est[0], est[1], tol);
   h->err.clear();
   return GSVD_RAND_OK;
 }
@@ -559,7 +789,7 @@ int gsvd_rand_create(gsvd_rand_t* out, const gsvd_rand_config* cfg) {
   if (!out || !cfg) return GSVD_RAND_ERR_ARG;
   *out = nullptr;
   if (cfg->prec < GSVD_RAND_FP64 || cfg->prec > GSVD_RAND_FP32) return GSVD_RAND_ERR_ARG;
-  if (cfg->adaptive) return GSVD_RAND_ERR_UNSUPPORTED;
+  if (cfg->adaptive != 0 && cfg->adaptive != 1) return GSVD_RAND_ERR_ARG;
   gsvd_rand_ctx* h = new gsvd_rand_ctx();
   h->cfg = *cfg;
   h->stream = (cudaStream_t)cfg->stream;
@@ -613,6 +843,13 @@ int gsvd_rand_profile_reset(gsvd_rand_t h) {
 
 uint64_t gsvd_rand_launch_count(void) { return gsvdr::g_launch_count.load(); }
 
+int gsvd_rand_basis_cols(gsvd_rand_t h, int* l1, int* l2) {
+  if (!h) return GSVD_RAND_ERR_ARG;
+  if (l1) *l1 = h->last_cols[0];
+  if (l2) *l2 = h->last_cols[1];
+  return GSVD_RAND_OK;
+}
+
 int gsvd_rand_solve(gsvd_rand_t h, const void* G1, int64_t m, int64_t ld1, const void* G2, int64_t p,
                     int64_t ld2, int64_t n, int k, int oversample, int q, uint64_t seed, double* alpha,
                     double* beta, int* r_out, double* resid_out) {
@@ -623,16 +860,28 @@ int gsvd_rand_solve(gsvd_rand_t h, const void* G1, int64_t m, int64_t ld1, const
   if (ld1 < n || ld2 < n) return fail(h, GSVD_RAND_ERR_ARG, "leading dimension smaller than n");
   if (k < 1 || oversample < 0 || q < 0 || q > 16)
     return fail(h, GSVD_RAND_ERR_ARG, "need k >= 1, oversample >= 0, 0 <= q <= 16");
-  int64_t l = (int64_t)k + oversample;
-  if (l > std::min(std::min(m, p), n))
-    return fail(h, GSVD_RAND_ERR_ARG, "k + oversample = %lld exceeds min(m, p, n)", (long long)l);
   const bool f64 = h->cfg.prec == GSVD_RAND_FP64;
-  if (l > (f64 ? 224 : 256)) return fail(h, GSVD_RAND_ERR_ARG, "k + oversample = %lld exceeds the limit %d",
-                                         (long long)l, f64 ? 224 : 256);
+  int64_t l = (int64_t)k + oversample;
+  if (h->cfg.adaptive) {
+    if (k > 512) return fail(h, GSVD_RAND_ERR_ARG, "k = %d exceeds the 512 pairs of two 256-column bases", k);
+    if (f64 && h->cfg.block_b > 224) return fail(h, GSVD_RAND_ERR_ARG, "block_b exceeds the FP64 limit 224");
+  } else {
+    if (l > std::min(std::min(m, p), n))
+      return fail(h, GSVD_RAND_ERR_ARG, "k + oversample = %lld exceeds min(m, p, n)", (long long)l);
+    if (l > (f64 ? 224 : 256)) return fail(h, GSVD_RAND_ERR_ARG, "k + oversample = %lld exceeds the limit %d",
+                                           (long long)l, f64 ? 224 : 256);
+  }
   if (n > (int64_t)1 << 30 || m > (int64_t)1 << 40 || p > (int64_t)1 << 40)
     return fail(h, GSVD_RAND_ERR_ARG, "dimension too large");
   cudaError_t e = cudaSetDevice(h->cfg.device);
   if (e != cudaSuccess) return fail(h, GSVD_RAND_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+  if (h->cfg.adaptive) {
+    // Algorithm 1 bases (k = output capacity; oversample and q are not used)
+    if (f64) return solve_adaptive_t<double, double>(h, G1, m, ld1, G2, p, ld2, n, k, seed, alpha, beta, r_out, resid_out);
+    if (h->cfg.flags & GSVD_RAND_FLAG_CHOL_FP64)
+      return solve_adaptive_t<float, double>(h, G1, m, ld1, G2, p, ld2, n, k, seed, alpha, beta, r_out, resid_out);
+    return solve_adaptive_t<float, float>(h, G1, m, ld1, G2, p, ld2, n, k, seed, alpha, beta, r_out, resid_out);
+  }
   if (f64) return solve_t<double, double>(h, G1, m, ld1, G2, p, ld2, n, k, oversample, q, seed, alpha, beta, r_out, resid_out);
   if (h->cfg.flags & GSVD_RAND_FLAG_CHOL_FP64)
     return solve_t<float, double>(h, G1, m, ld1, G2, p, ld2, n, k, oversample, q, seed, alpha, beta, r_out, resid_out);

@@ -520,12 +520,19 @@ __global__ __launch_bounds__(CHOL_THREADS) void chol_shift_kernel(const double* 
     s_odiag[i] = v;
   }
   __syncthreads();
-  // A pivot not above the Gram's resolution relative to its own (shifted)
-  // diagonal is numerically dependent on the earlier columns: it is skipped
-  // (no elimination with it) and its column of R^{-1} is zero, so the
-  // matching column of Q is zero and adds a zero row to Q^T G.  The final
-  // M[k][k] is the pivot seen at step k, so the test is repeated afterwards.
-  auto dropped = [&](int k, TC d) { return !(d > (TC)tau_rel * s_odiag[k]); };
+  // A pivot at or below the Gram's resolution relative to its own (shifted)
+  // diagonal is numerically dependent on the earlier columns.  Dropping it
+  // would take its direction out of the span (weak directions of the sketch go
+  // with it), so it is clamped to that floor instead; the next CholeskyQR pass
+  // re-orthonormalises the column.  The final M[k][k] is the pivot seen at step
+  // k, so the same rule is applied again afterwards.
+  // effective pivot: d when above tau times the column's own (shifted) diagonal, else that
+  // floor (the column keeps its direction in the span; a later pass re-orthonormalises it);
+  // 0 (column dropped) only when the floor itself is zero (a zero column)
+  auto pivot = [&](int k, TC d) -> TC {
+    const TC fl = (TC)tau_rel * s_odiag[k];
+    return d > fl ? d : (fl > TC(0) ? fl : TC(0));
+  };
   int bad_k = -1;
   if (s_bad == 0) {
     for (int k = 0; k < l; ++k) {
@@ -535,8 +542,9 @@ __global__ __launch_bounds__(CHOL_THREADS) void chol_shift_kernel(const double* 
         bad_k = k;
         break;
       }
-      if (dropped(k, d)) continue;
-      const TC dinv = TC(1) / d;
+      const TC pv = pivot(k, d);
+      if (pv == TC(0)) continue;
+      const TC dinv = TC(1) / pv;
       for (int i = k + 1 + warp; i < l; i += NW) {
         const TC f = rowk[i] * dinv;
         TC* ri = M + (int64_t)i * lda;
@@ -552,8 +560,9 @@ __global__ __launch_bounds__(CHOL_THREADS) void chol_shift_kernel(const double* 
     int c = 0;
     for (int i = lane; i < l; i += 32) {
       const TC d = M[(int64_t)i * lda + i];
-      const bool dr = dropped(i, d);
-      s_scale[i] = dr ? TC(0) : TC(1) / sqrt(d);
+      const TC pv = pivot(i, d);
+      const bool dr = pv == TC(0);
+      s_scale[i] = dr ? TC(0) : TC(1) / sqrt(pv);
       c += dr ? 0 : 1;
     }
     for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
@@ -624,7 +633,13 @@ __global__ __launch_bounds__(CHOL64_THREADS, 1) void chol64_kernel(const double*
   }
   if (bad) s_bad = 2;
   __syncthreads();
-  auto dropped = [&](int k, TC d) { return !(d > (TC)tau_rel * s_odiag[k]); };
+  // effective pivot: d when above tau times the column's own (shifted) diagonal, else that
+  // floor (the column keeps its direction in the span; a later pass re-orthonormalises it);
+  // 0 (column dropped) only when the floor itself is zero (a zero column)
+  auto pivot = [&](int k, TC d) -> TC {
+    const TC fl = (TC)tau_rel * s_odiag[k];
+    return d > fl ? d : (fl > TC(0) ? fl : TC(0));
+  };
   int bad_k = -1;
   if (s_bad == 0) {
     for (int k = 0; k < l; ++k) {
@@ -646,8 +661,9 @@ __global__ __launch_bounds__(CHOL64_THREADS, 1) void chol64_kernel(const double*
         bad_k = k;
         break;
       }
-      if (dropped(k, d)) continue;
-      const TC dinv = TC(1) / d;
+      const TC pv = pivot(k, d);
+      if (pv == TC(0)) continue;
+      const TC dinv = TC(1) / pv;
       TC rc[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) rc[c] = row[t + 32 * c];
@@ -685,8 +701,9 @@ __global__ __launch_bounds__(CHOL64_THREADS, 1) void chol64_kernel(const double*
     int kept = 0;
     for (int i = t; i < l; i += 32) {
       const TC d = s_row[0][i];
-      const bool dr = dropped(i, d);
-      s_scale[i] = dr ? TC(0) : TC(1) / sqrt(d);
+      const TC pv = pivot(i, d);
+      const bool dr = pv == TC(0);
+      s_scale[i] = dr ? TC(0) : TC(1) / sqrt(pv);
       kept += dr ? 0 : 1;
     }
     for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(0xffffffffu, kept, o);

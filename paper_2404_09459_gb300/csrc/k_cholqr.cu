@@ -12,7 +12,8 @@
 //      with the register-resident elimination on [W | I] and keeps R^{-1} in
 //      shared memory: all CTAs take the same decisions, so none waits for
 //      another;
-//   4. the CTA's rows times R^{-1}: in place (pass 1) or to Q (pass 2).
+//   4. the CTA's rows times R^{-1}, in place; a third pass runs when the second
+//      factor is ill-conditioned (see below); the last pass writes Q.
 // The grid barrier is a sense-reversing counter with a bounded spin: after
 // about 2^22 polls a CTA sets GSVD_RAND_ERR_TIMEOUT and an abort flag that
 // releases every other waiting CTA.  The launch is cooperative, so all CTAs
@@ -82,7 +83,8 @@ __device__ bool grid_barrier(GridBar* b, DevStatus* st, int stage) {
 // every CTA computes the same result.
 template <typename T, typename TC>
 __device__ bool chol_block(const double* W, int l, double shift, double tau_rel, T* Rs, DevStatus* st_dev,
-                           int stage, bool report) {
+                           int stage, bool report, float* cond2_out) {
+  __shared__ float s_cond2;
   __shared__ TC s_row[2][128];
   __shared__ TC s_odiag[64], s_scale[64];
   __shared__ int s_bad, s_kept;
@@ -120,7 +122,13 @@ __device__ bool chol_block(const double* W, int l, double shift, double tau_rel,
   }
   if (bad) s_bad = 2;
   __syncthreads();
-  auto dropped = [&](int k, TC d) { return !(d > (TC)tau_rel * s_odiag[k]); };
+  // effective pivot: d when above tau times the column's own (shifted) diagonal, else that
+  // floor (the column keeps its direction in the span; a later pass re-orthonormalises it);
+  // 0 (column dropped) only when the floor itself is zero (a zero column)
+  auto pivot = [&](int k, TC d) -> TC {
+    const TC fl = (TC)tau_rel * s_odiag[k];
+    return d > fl ? d : (fl > TC(0) ? fl : TC(0));
+  };
   // publish row k of the augmented matrix into s_row[k & 1] (its owner warp)
   auto publish = [&](int k) {
     TC* row = s_row[k & 1];
@@ -145,11 +153,12 @@ __device__ bool chol_block(const double* W, int l, double shift, double tau_rel,
         break;
       }
       const int k1 = k + 1, w1 = k1 & 7;
-      if (dropped(k, d)) {
+      const TC pv = pivot(k, d);
+      if (pv == TC(0)) {
         if (w == w1 && k1 < l) publish(k1);  // row k + 1 is unchanged by a dropped pivot
         continue;
       }
-      const TC dinv = sizeof(TC) == 4 ? (TC)__frcp_rn((float)d) : TC(1) / d;
+      const TC dinv = sizeof(TC) == 4 ? (TC)__frcp_rn((float)pv) : TC(1) / pv;
       TC rc[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) rc[c] = row[t + 32 * c];
@@ -197,16 +206,30 @@ __device__ bool chol_block(const double* W, int l, double shift, double tau_rel,
   __syncthreads();
   if (w == 0 && bad_k < 0 && s_bad == 0) {
     int kept = 0;
+    float dmin = 3.4e38f, dmax = 0.f;
     for (int i = t; i < l; i += 32) {
       const TC d = s_row[0][i];
-      const bool dr = dropped(i, d);
-      s_scale[i] = dr ? TC(0) : TC(1) / sqrt(d);
+      const TC pv = pivot(i, d);
+      const bool dr = pv == TC(0);
+      s_scale[i] = dr ? TC(0) : TC(1) / sqrt(pv);
       kept += dr ? 0 : 1;
+      if (!dr) {
+        dmin = fminf(dmin, (float)pv);
+        dmax = fmaxf(dmax, (float)pv);
+      }
     }
-    for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(0xffffffffu, kept, o);
-    if (t == 0) s_kept = kept;
+    for (int o = 16; o > 0; o >>= 1) {
+      kept += __shfl_xor_sync(0xffffffffu, kept, o);
+      dmin = fminf(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
+      dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    }
+    if (t == 0) {
+      s_kept = kept;
+      s_cond2 = dmin > 0.f ? dmax / dmin : 3.4e38f;  // (max / min kept diagonal of R)^2
+    }
   }
   __syncthreads();
+  if (cond2_out) *cond2_out = s_cond2;
   if (bad_k >= 0 || s_bad || s_kept == 0) {
     if (report && tid == 0) set_status(st_dev, (s_bad == 2 || bad_k >= 0) ? -4 : -5, stage, bad_k);
     return false;
@@ -247,7 +270,13 @@ __global__ __launch_bounds__(FQ_THREADS, 1) void cholqr2_fused_kernel(
   }
   __syncthreads();
   const int64_t ll = (int64_t)l * l;
-  for (int pass = 0; pass < 2; ++pass) {
+  // shifted CholeskyQR, then CholeskyQR; a third pass (as in shifted CholeskyQR3, Fukaya et
+  // al. 2020) when the second factor shows that Q1 was far from orthonormal, so that Q2 can
+  // be off by kappa(R2)^2 u: above ~1e-12 (FP64) or ~1e-6 (FP32)
+  const float cond2_max = sizeof(T) == 8 ? 1e4f : 16.f;
+  bool third = false;
+  for (int pass = 0; pass < 3; ++pass) {
+    if (pass == 2 && !third) break;
     // 1. Gram partial of the tile: thread (ty, tx) forms the 4 x 4 block (4 ty.., 4 tx..);
     //    the upper blocks are stored
     {
@@ -308,10 +337,41 @@ __global__ __launch_bounds__(FQ_THREADS, 1) void cholqr2_fused_kernel(
       }
     }
     if (!grid_barrier(bar, st_dev, stage + pass)) return;
-    // 3. R^{-1} in every CTA
-    if (!chol_block<T, TC>(W, l, pass == 0 ? shift_coef : 0.0, tau_rel, Rs, st_dev, stage + pass,
-                           blockIdx.x == 0))
-      return;
+    // 3. R^{-1} in every CTA (every CTA takes the same decisions).  When the third
+    //    pass finds Q2 orthonormal to first order (max |W - I| <= 0.05), one
+    //    Newton-Schulz step X = (3 I - W) / 2 (error O(||W - I||^2)) takes the place
+    //    of the Cholesky; a Q2 further off (clamped pivots) gets a full CholeskyQR.
+    bool newton = false;
+    if (pass == 2) {
+      __shared__ float s_dev[FQ_THREADS / 32];
+      float dv = 0.f;
+      for (int64_t e = tid; e < ll; e += FQ_THREADS) {
+        const int i = (int)(e / l), j = (int)(e % l);
+        dv = fmaxf(dv, (float)fabs(__ldcg(W + e) - (i == j ? 1.0 : 0.0)));
+      }
+      for (int o = 16; o > 0; o >>= 1) dv = fmaxf(dv, __shfl_xor_sync(0xffffffffu, dv, o));
+      if ((tid & 31) == 0) s_dev[tid >> 5] = dv;
+      __syncthreads();
+      float mx = 0.f;
+      for (int q = 0; q < FQ_THREADS / 32; ++q) mx = fmaxf(mx, s_dev[q]);
+      newton = mx <= 0.05f;
+      __syncthreads();
+    }
+    if (!newton) {
+      float cond2 = 0.f;
+      if (!chol_block<T, TC>(W, l, pass == 0 ? shift_coef : 0.0, tau_rel, Rs, st_dev, stage + (pass > 0),
+                             blockIdx.x == 0, &cond2))
+        return;
+      if (pass == 1) third = cond2 > cond2_max;
+    } else {
+      for (int e = tid; e < FQ_LP * FQ_LP; e += FQ_THREADS) {
+        const int i = e / FQ_LP, j = e % FQ_LP;
+        double v = 0.0;
+        if (i < l && j < l) v = (i == j ? 1.5 : 0.0) - 0.5 * __ldcg(W + (int64_t)i * l + j);
+        Rs[e] = (T)v;
+      }
+      __syncthreads();
+    }
     // 4. rows x R^{-1}
     T acc[FQ_RT][4];
 #pragma unroll

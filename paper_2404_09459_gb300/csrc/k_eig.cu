@@ -114,9 +114,11 @@ __global__ __launch_bounds__(1024) void eig_f32_kernel(const double* __restrict_
     const float sig2 = block_sum_f(part, red);
     const float sig = sqrtf(sig2);
     const float alpha = x0 >= 0.f ? -sig : sig;  // H x = alpha e1
-    const float vtv = 2.f * (sig2 - x0 * alpha);
-    const float bk = (sig > 0.f && vtv > 0.f) ? 2.f / vtv : 0.f;
-    for (int i = tid; i < m; i += nt) v[i] = (i == 0) ? (x0 - alpha) : A[(int64_t)(k + 1 + i) * lda + k];
+    // normalised reflector (v_0 = 1, tau in [1, 2]): bounded for any scale of the column
+    const bool refl = sig > 0.f && isfinite(sig);
+    const float bk = refl ? (alpha - x0) / alpha : 0.f;
+    const float vs = refl ? 1.f / (x0 - alpha) : 0.f;
+    for (int i = tid; i < m; i += nt) v[i] = (i == 0) ? 1.f : A[(int64_t)(k + 1 + i) * lda + k] * vs;
     if (tid == 0) {
       beta[k] = bk;
       e[k] = (bk > 0.f) ? alpha : x0;
@@ -388,17 +390,21 @@ __global__ __launch_bounds__(1024) void eig128_kernel(const double* __restrict__
       }
     }
     __syncthreads();
-    if (w == 0) {  // reflector H = I - beta v v^T with H x = alpha e_1, x = column k below row k
+    if (w == 0) {
+      // reflector H = I - tau v v^T with H x = alpha e_1, x = column k below row k, in the
+      // normalised form v_0 = 1, v_i = x_i / (x0 - alpha), tau = (alpha - x0) / alpha in
+      // [1, 2]: bounded for any scale of x (an unnormalised 2 / v^T v overflows on tiny columns)
       const float x0 = col[k + 1];
       float sg = 0.f;
       for (int i = k + 1 + t; i < N; i += 32) sg = fmaf(col[i], col[i], sg);
       for (int o = 16; o > 0; o >>= 1) sg += __shfl_xor_sync(0xffffffffu, sg, o);
       const float sig = sqrtf(sg);
       const float alpha = x0 >= 0.f ? -sig : sig;
-      const float vtv = 2.f * (sg - x0 * alpha);
-      const float bk = (sig > 0.f && vtv > 0.f) ? 2.f / vtv : 0.f;
+      const bool refl = sig > 0.f && isfinite(sig);
+      const float bk = refl ? (alpha - x0) / alpha : 0.f;
+      const float vs = refl ? 1.f / (x0 - alpha) : 0.f;
       for (int i = t; i < E_NMAX; i += 32)
-        Vref[(size_t)k * E_NMAX + i] = (bk > 0.f && i > k && i < N) ? (i == k + 1 ? x0 - alpha : col[i]) : 0.f;
+        Vref[(size_t)k * E_NMAX + i] = (refl && i > k && i < N) ? (i == k + 1 ? 1.f : col[i] * vs) : 0.f;
       if (t == 0) {
         s_beta[k] = bk;
         s_e[k] = bk > 0.f ? alpha : x0;

@@ -146,6 +146,56 @@ def test_separate_kernel_cholqr(prec, m, p, n, k, os_):
     _check(prec, G1, G2, spec)
 
 
+# Algorithm 1 bases.  The pairs are chosen so that the cumulated residual falls from above
+# 1e-2 to far below tol within one block on both sides (the stop is an integer decision
+# taken from floating-point values computed differently on each side).
+ADAPTIVE_CASES = [
+    ("fp64", PairSpec(m=1500, p=1200, n=300, r=40, alpha="uniform", decay="exp10", sigma=1e-12, seed=31), 16, 1e-6, 40),
+    ("tf32x3", PairSpec(m=3000, p=2500, n=400, r=30, alpha="uniform", decay="exp10", sigma=1e-8, seed=32), 12, 1e-3, 30),
+    ("tf32x3", PairSpec(m=4000, p=3000, n=500, r=60, alpha="uniform", decay="exp10", sigma=1e-8, seed=33), 64, 1e-3, 60),
+    # b = 100 (the paper's block): separate-kernel CholeskyQR and a 200 x 200 small eigenproblem
+    ("tf32x3", PairSpec(m=5000, p=4000, n=600, r=90, alpha="uniform", decay="logspace02", sigma=1e-8, seed=34), 100, 1e-3, 90),
+]
+
+
+@pytest.mark.parametrize("prec,spec,b,tol,k", ADAPTIVE_CASES)
+def test_adaptive_basis_matches_oracle(prec, spec, b, tol, k):
+    G1, G2, _, _ = planted_pair(spec)
+    ref = O.rand_gsvd_adaptive(G1, G2, tol=tol, b=b, seed=7, r=k)
+    with P.Context(prec, adaptive=True, block_b=b, tol=tol) as ctx:
+        out = ctx.solve(_dev(G1, prec), _dev(G2, prec), k, 0, 0, 7)
+        l1, l2 = ctx.basis_cols()
+    assert (l1, l2) == (ref["l1"], ref["l2"])
+    assert out["r"] == min(k, l1 + l2)
+    a, b_ = out["alpha"].cpu().numpy(), out["beta"].cpu().numpy()
+    e = O.gsv_error(ref["alpha"], ref["beta"], a, b_)
+    assert np.max(e) <= TOL[prec], np.max(e)
+    assert max(out["resid"]) <= tol
+
+
+@pytest.mark.parametrize("prec,sigma,q", [("fp64", 1e-12, 1), ("fp64", 1e-12, 0), ("fp32", 1e-8, 0), ("tf32x3", 1e-8, 0),
+                                           ("tf32x3", 0.0, 0)])
+def test_rank_deficient_sketch(prec, sigma, q):
+    # k equals the planted rank and the oversampled columns see only noise below the data's
+    # precision (or none): the sketch is numerically rank-deficient.  Small Householder
+    # columns must not overflow the reflector, and no weak direction may leave the basis.
+    spec = PairSpec(m=4000, p=3000, n=500, r=60, alpha="uniform", decay="exp10", sigma=sigma, k=60,
+                    oversample=4, q=q, seed=33)
+    G1, G2, _, _ = planted_pair(spec)
+    _check(prec, G1, G2, spec)
+
+
+def test_adaptive_cap_reached_reports_tol_miss():
+    # 256-column cap below n = 300 with a noisy pair: the tolerance cannot be met
+    spec = PairSpec(m=600, p=500, n=300, r=20, sigma=1e-2, seed=35)
+    G1, G2, _, _ = planted_pair(spec)
+    with P.Context("fp64", adaptive=True, block_b=64, tol=1e-6) as ctx:
+        with pytest.raises(P.GsvdRandError) as e:
+            ctx.solve(_dev(G1, "fp64"), _dev(G2, "fp64"), 20, 0, 0, 1)
+        assert e.value.name == "TOL_MISS"
+        assert ctx.basis_cols() == (256, 256)
+
+
 @pytest.mark.parametrize("prec", ["bf16"])
 def test_unbuilt_precisions_report_unsupported(prec):
     spec = PairSpec(m=200, p=200, n=64, r=5, sigma=1e-6, k=5, oversample=3, q=1, seed=4)

@@ -280,6 +280,20 @@ def test_adaptive_full_when_tolerance_unreachable():
     assert np.linalg.norm(G - Q @ (Q.T @ G)) < 1e-12 * np.linalg.norm(G)
 
 
+def test_adaptive_gsvd_recovers_planted_pairs():
+    # Algorithm 1 + Algorithm 2 on a noise-free pair of exact rank 13: the bases
+    # cover the rank (ceil(13 / 5) = 3 blocks per side) and the GSVs are the
+    # planted ones (Section 2: exact when the basis captures range(G_s)).
+    spec = PairSpec(m=160, p=120, n=70, r=13, alpha="uniform", decay="exp10", sigma=0.0, seed=21)
+    G1, G2, at, bt = planted_pair(spec)
+    # the cumulated residual sqrt(||G||^2 - sum ||P_i^T G||^2) cannot resolve less than about
+    # sqrt(u) ||G|| (cancellation), so the tolerance sits above 1e-8
+    out = O.rand_gsvd_adaptive(G1, G2, tol=1e-6, b=5, seed=3, r=13)
+    assert out["l1"] == 15 and out["l2"] == 15
+    assert all(h[-1] <= 1e-6 for h in out["hist"]) and all(h[-2] > 1e-2 for h in out["hist"])
+    assert np.max(O.gsv_error(at, bt, out["alpha"], out["beta"])) < 1e-11
+
+
 # ---------------------------------------------------------------- metrics (Section 1)
 
 def test_metrics_equal_significance():
