@@ -5,7 +5,11 @@ power iterations, the projections, the FP64 compressed-pair GSVD), inputs
 resident in HBM.  Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload tf32_large|fp64_small|bf16_stress] [--prec tf32|fp32|...]
+                  [--workload tf32_large|fp64_small|bf16_stress|batched] [--prec tf32|fp32|...]
+
+--workload batched: 256 uneven pairs (m, p ~ U[2000, 30000], n ~ U[100, 1000],
+k = rank ~ U[10, 100], oversample 10, q = 1) per step, solved by one
+gsvd_rand_solve_batched call over concurrent worker streams.
 
 Multi-GPU (torchrun, N > 1): every rank solves its own independent pairs (the
 units shard with no data-path collective): weak scaling, value = pairs of all
@@ -28,12 +32,13 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 from paper_2404_09459_gb300.inputs import (PAIR_BF16_STRESS, PAIR_FP64_SMALL, PAIR_TF32_LARGE,  # noqa: E402
-                                           planted_pair, planted_pair_torch)
+                                           planted_pair, planted_pair_torch, uneven_batch)
 
 WORKLOADS = {
     "tf32_large": (PAIR_TF32_LARGE, "tf32x3"),
     "fp64_small": (PAIR_FP64_SMALL, "fp64"),
     "bf16_stress": (PAIR_BF16_STRESS, "bf16"),
+    "batched": (None, "tf32x3"),  # 256 uneven pairs, one batched call per step
 }
 METRIC = "pairs/sec and sketch TFLOP/s at GSV rel-err <=1e-4, chosen form vs plain FP64"
 DTYPE = {"tf32": "tf32", "tf32x3": "tf32x3", "bf16": "bf16", "fp32": "f32", "fp64": "f64"}
@@ -141,6 +146,17 @@ def run_reference(args, rank, world):
     spec, prec = WORKLOADS[args.workload]
     if rank != 0:
         return
+    if spec is None:  # batched workload: the oracle on a bounded sample of the batch, per step
+        specs = uneven_batch(args.pairs, seed=1)
+        s = oracle_batch_sample(specs, seconds=10.0, max_pairs=4)
+        line = {"impl": "reference", "metric": METRIC, "value": s["value"], "unit": "pairs/s", "n_gpus": world,
+                "steps": 1, "warmup": 0, "ms_per_step": 1e3 / s["value"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"batch of {args.pairs} uneven pairs (oracle on a sample)"},
+                "cpu_baseline": s,
+                "e2e": {"value": s["value"], "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
     from oracle import gsvd as O
     G1, G2, _, _ = planted_pair(spec)
     for _ in range(args.warmup):
@@ -160,6 +176,101 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def oracle_batch_sample(specs, seconds=20.0, max_pairs=16):
+    """The FP64 oracle on the first pairs of a batch (only the solves are timed)."""
+    from oracle import gsvd as O
+    spent, done = 0.0, 0
+    for s in specs[:max_pairs]:
+        G1, G2, _, _ = planted_pair(s)
+        t0 = time.perf_counter()
+        O.rand_gsvd(G1, G2, s.kk, s.oversample, s.q, s.seed)
+        spent += time.perf_counter() - t0
+        done += 1
+        if spent > seconds:
+            break
+    return {"value": done / spent, "unit": "pairs/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{done} pairs of the batch with the FP64 oracle (OpenBLAS, {os.cpu_count()} threads); "
+                      "input generation not timed"}
+
+
+def run_batched(args, rank, world):
+    """--workload batched: one step = one batched solve of 256 uneven pairs."""
+    import torch
+    import paper_2404_09459_gb300 as P
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    P._build.build()
+    prec = args.prec or "tf32x3"
+    npairs = args.pairs
+    specs = uneven_batch(npairs, seed=1 + rank)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    mats = [planted_pair_torch(s, device=f"cuda:{local}", dtype=dt)[:2] for s in specs]
+    pairs = [dict(G1=G1, G2=G2, k=s.kk, oversample=s.oversample, q=s.q, seed=s.seed, pair=i)
+             for i, (s, (G1, G2)) in enumerate(zip(specs, mats))]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")
+    ctx = P.Context(prec, device=local)
+    for _ in range(args.warmup):
+        ctx.solve_batched(pairs, workers=args.workers)
+    torch.cuda.synchronize()
+    l0 = ctx.launch_count()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    times = []
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            barrier()
+            t0 = time.perf_counter()
+            ctx.solve_batched(pairs, workers=args.workers)  # synchronous: returns after the worker streams
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+    launches = (ctx.launch_count() - l0) // args.steps
+    sec = sum(times)
+    if dist is not None:
+        t = torch.tensor([sec], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        sec = float(t.item())
+    value = world * npairs * args.steps / sec
+    ms_step = 1e3 * sec / args.steps
+    flops = sum(sketch_flops(s) for s in specs)
+    # the same batch one pair after another (one stream), for the batching gain
+    seq_ctx = P.Context(prec, device=local)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s, (G1, G2) in zip(specs, mats):
+        seq_ctx.solve(G1, G2, s.kk, s.oversample, s.q, s.seed)
+    torch.cuda.synchronize()
+    seq_s = time.perf_counter() - t0
+    seq_ctx.close()
+    cpu = oracle_batch_sample(specs) if rank == 0 and not args.no_cpu_baseline else None
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": DTYPE.get(prec, prec), "data": "synthetic",
+                "config": {"workload": f"batch of {npairs} uneven pairs: m, p ~ U[2000, 30000], n ~ U[100, 1000], "
+                                       f"k = rank ~ U[10, 100], oversample 10, q 1; {prec} products, FP64 small GSVD; "
+                                       f"{args.workers} concurrent worker streams",
+                           "l2": "flushed between timed steps (256 MiB write)",
+                           "timing": "host clock around the synchronous batched call, device synchronised on both sides",
+                           "parallelism": f"independent batches, {world} rank(s)"},
+                "sketch_tflops": flops / (ms_step / 1e3) / 1e12,
+                "sequential": {"value": npairs / seq_s, "unit": "pairs/s",
+                               "batching_speedup": value / world / (npairs / seq_s)},
+                "cpu_baseline": cpu, "gpu_launches": int(launches), "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -170,6 +281,8 @@ def main():
     ap.add_argument("--prec", default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison leg")
+    ap.add_argument("--pairs", type=int, default=256, help="batched workload: pairs per step")
+    ap.add_argument("--workers", type=int, default=16, help="batched workload: concurrent worker streams")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -178,6 +291,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "batched":
+        return run_batched(args, rank, world)
 
     import torch
     import paper_2404_09459_gb300 as P

@@ -145,6 +145,34 @@ int gsvd_rand_solve(gsvd_rand_t h, const void *G1, int64_t m, int64_t ld1, const
                     int64_t p, int64_t ld2, int64_t n, int k, int oversample, int q,
                     uint64_t seed, double *alpha, double *beta, int *r_out, double *resid_out);
 
+/* One pair of a batched solve: the arguments of gsvd_rand_solve, the Philox counter word
+ * 'pair' (side s of this pair uses counter words (t, pair, s, stream)), and the
+ * per-pair return code written by gsvd_rand_solve_batched. */
+typedef struct {
+  const void *G1;
+  int64_t m, ld1;
+  const void *G2;
+  int64_t p, ld2;
+  int64_t n;
+  int k, oversample, q;
+  uint64_t seed;
+  uint32_t pair;
+  double *alpha, *beta; /* capacity k each */
+  int *r_out;           /* may be NULL */
+  double *resid_out;    /* may be NULL (2 doubles) */
+  int status;           /* out: GSVD_RAND_OK or the pair's error code */
+} gsvd_rand_pair;
+
+/* Many independent pairs at once (the batched form of gsvd_rand_solve, with h's
+ * configuration).  The pairs are spread over `workers` concurrent solves (<= 0: 8;
+ * at most 64), each a sub-context of h with its own stream and workspace, kept
+ * for later calls; while one pair runs its single-SM small GSVD, others use the
+ * rest of the GPU.  Pairs are taken largest first.  Every pair's result and
+ * status are written; returns GSVD_RAND_OK when all succeeded, else the status
+ * of the first failing pair (by index).  Synchronises the worker streams (not
+ * cfg->stream).  Errors: ARG, OOM, CUDA, and any per-pair error. */
+int gsvd_rand_solve_batched(gsvd_rand_t h, int npairs, gsvd_rand_pair *pairs, int workers);
+
 /* Comparative quantities of Section 1 for r GSV pairs (alpha non-increasing,
  * beta non-decreasing):
  *   theta[i] = atan2(alpha_i, beta_i) - pi/4      (antisymmetric angular distance)

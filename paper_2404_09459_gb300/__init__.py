@@ -23,7 +23,7 @@ FLAG_CHOL_FP64 = 1
 EXPORTS = ("gsvd_rand_config_init", "gsvd_rand_create", "gsvd_rand_destroy", "gsvd_rand_last_error",
            "gsvd_rand_solve", "gsvd_rand_metrics", "gsvd_rand_gaussian", "gsvd_rand_philox",
            "gsvd_rand_profile_get", "gsvd_rand_profile_reset", "gsvd_rand_launch_count",
-           "gsvd_rand_metrics_noalloc", "gsvd_rand_basis_cols")
+           "gsvd_rand_metrics_noalloc", "gsvd_rand_basis_cols", "gsvd_rand_solve_batched")
 NOALLOC_MAX_N = 32768
 FLAG_PROFILE = 2
 STAGES = ("sketch", "gtq", "orth", "small", "small_gram", "small_jacobi", "small_refine", "small_cs")
@@ -34,6 +34,13 @@ class GsvdRandError(RuntimeError):
         super().__init__(f"gsvd_rand error {code} ({ERRORS.get(code, '?')}): {msg}")
         self.code = code
         self.name = ERRORS.get(code, "?")
+
+
+class _Pair(C.Structure):
+    _fields_ = [("G1", C.c_void_p), ("m", C.c_int64), ("ld1", C.c_int64), ("G2", C.c_void_p), ("p", C.c_int64),
+                ("ld2", C.c_int64), ("n", C.c_int64), ("k", C.c_int), ("oversample", C.c_int), ("q", C.c_int),
+                ("seed", C.c_uint64), ("pair", C.c_uint32), ("alpha", C.c_void_p), ("beta", C.c_void_p),
+                ("r_out", C.c_void_p), ("resid_out", C.c_void_p), ("status", C.c_int)]
 
 
 class _Config(C.Structure):
@@ -71,6 +78,7 @@ def load_library(path: str | None = None):
     lib.gsvd_rand_launch_count.restype = C.c_uint64
     lib.gsvd_rand_metrics_noalloc.argtypes = [i32, vp, vp, vp, i32, i32, i32, vp, vp, vp, vp, vp]
     lib.gsvd_rand_basis_cols.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    lib.gsvd_rand_solve_batched.argtypes = [vp, i32, C.POINTER(_Pair), i32]
     for name in EXPORTS:
         if name not in ("gsvd_rand_last_error", "gsvd_rand_launch_count"):
             getattr(lib, name).restype = C.c_int
@@ -192,6 +200,37 @@ class Context:
         self._check(rc)
         rr = r.value
         return dict(alpha=alpha[:rr], beta=beta[:rr], r=rr, resid=(resid[0], resid[1]))
+
+    def solve_batched(self, pairs, workers: int = 8):
+        """Many independent pairs at once.  pairs: sequence of dicts with G1, G2, k and optional
+        oversample (10), q (1), seed (0), pair (its index).  Returns a list of dict(alpha, beta, r,
+        resid, status); raises GsvdRandError if any pair failed (after all ran)."""
+        want = "f64" if self.prec == "fp64" else "f32"
+        arr = (_Pair * len(pairs))()
+        outs, keep = [], []
+        for i, d in enumerate(pairs):
+            p1, m, n1, ld1, dev1, k1 = _mat_ptr(d["G1"], want)
+            p2, p, n2, ld2, dev2, k2 = _mat_ptr(d["G2"], want)
+            if n1 != n2:
+                raise ValueError(f"pair {i}: G1 and G2 must have the same number of columns")
+            k = int(d["k"])
+            alpha, pa = self._out_vec(dev1, k)
+            beta, pb = self._out_vec(dev1, k)
+            r = C.c_int(0)
+            resid = (C.c_double * 2)()
+            q = arr[i]
+            q.G1, q.m, q.ld1, q.G2, q.p, q.ld2, q.n = p1, m, ld1, p2, p, ld2, n1
+            q.k, q.oversample, q.q = k, int(d.get("oversample", 10)), int(d.get("q", 1))
+            q.seed, q.pair = int(d.get("seed", 0)), int(d.get("pair", i))
+            q.alpha, q.beta, q.r_out, q.resid_out = pa, pb, C.addressof(r), C.addressof(resid)
+            outs.append((alpha, beta, r, resid))
+            keep += [k1, k2]
+        rc = self.lib.gsvd_rand_solve_batched(self.h, len(pairs), arr, workers)
+        res = [dict(alpha=a[:r.value], beta=b[:r.value], r=r.value, resid=(rs[0], rs[1]), status=arr[i].status)
+               for i, (a, b, r, rs) in enumerate(outs)]
+        del keep
+        self._check(rc)
+        return res
 
     def basis_cols(self):
         """Columns (l1, l2) of the two bases of the last solve."""

@@ -16,6 +16,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/gsvd_rand.h"
@@ -34,6 +35,9 @@ struct gsvd_rand_ctx {
   double* res_host = nullptr;    // pinned, 4 doubles
   int tc_ok = -1;                // tensor-core path usable on this device
   int last_cols[2] = {0, 0};     // basis columns per side of the last solve
+  uint32_t pair_word = 0;        // Philox counter word 'pair' of the current solve
+  bool owns_stream = false;      // stream created by the library (batched workers)
+  std::vector<gsvd_rand_ctx*> workers;  // sub-contexts of gsvd_rand_solve_batched
   // optional per-stage CUDA-event timing (GSVD_RAND_FLAG_PROFILE)
   struct Rec {
     int stage;
@@ -272,7 +276,7 @@ struct Solver {
   int side(const T* G, int64_t ldg, int s, const Plan& pl, SideBufs<T>& b, int q, uint64_t seed,
            T* Srows) {
     const int64_t M = pl.M[s];
-    CU(launch_gaussian_kmajor<T>(b.Xt, pl.ldx, pl.n, pl.l, (int)pl.lx, seed, 0u, (uint32_t)s,
+    CU(launch_gaussian_kmajor<T>(b.Xt, pl.ldx, pl.n, pl.l, (int)pl.lx, seed, h->pair_word, (uint32_t)s,
                                  GSVD_RAND_STREAM_FIXED, st));
     // Q layout: row-major M x lp for the CUDA-core product, transposed Q^T
     // (lx x ldm, padding rows zero) as the K-major operand of the tensor-core one
@@ -677,7 +681,7 @@ int solve_adaptive_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, 
     int c = 0;
     for (int i = 0; c < cap[s]; ++i) {
       const int bi = std::min(bsz, cap[s] - c);
-      CU(launch_gaussian_kmajor<T>(w.Xt, ldx, n, bi, (int)round_up(bi, 16), seed, 0u, (uint32_t)s,
+      CU(launch_gaussian_kmajor<T>(w.Xt, ldx, n, bi, (int)round_up(bi, 16), seed, h->pair_word, (uint32_t)s,
                                    (uint32_t)(GSVD_RAND_STREAM_ADAPTIVE + i), st));
       {
         ProfScope ps(h, GSVD_RAND_STAGE_SKETCH);
@@ -813,8 +817,11 @@ int gsvd_rand_create(gsvd_rand_t* out, const gsvd_rand_config* cfg) {
 
 int gsvd_rand_destroy(gsvd_rand_t h) {
   if (!h) return GSVD_RAND_OK;
+  for (auto wk : h->workers) gsvd_rand_destroy(wk);
+  h->workers.clear();
   cudaSetDevice(h->cfg.device);
   if (h->stream) cudaStreamSynchronize(h->stream); else cudaDeviceSynchronize();
+  if (h->owns_stream && h->stream) cudaStreamDestroy(h->stream);
   for (auto e : h->evpool) cudaEventDestroy(e);
   if (h->ws) cudaFree(h->ws);
   if (h->st_host) cudaFreeHost(h->st_host);
@@ -886,6 +893,62 @@ int gsvd_rand_solve(gsvd_rand_t h, const void* G1, int64_t m, int64_t ld1, const
   if (h->cfg.flags & GSVD_RAND_FLAG_CHOL_FP64)
     return solve_t<float, double>(h, G1, m, ld1, G2, p, ld2, n, k, oversample, q, seed, alpha, beta, r_out, resid_out);
   return solve_t<float, float>(h, G1, m, ld1, G2, p, ld2, n, k, oversample, q, seed, alpha, beta, r_out, resid_out);
+}
+
+int gsvd_rand_solve_batched(gsvd_rand_t h, int npairs, gsvd_rand_pair* pairs, int workers) {
+  if (!h || npairs < 0 || (npairs > 0 && !pairs)) return GSVD_RAND_ERR_ARG;
+  if (npairs == 0) return GSVD_RAND_OK;
+  if (workers <= 0) workers = 8;
+  workers = std::min(std::min(workers, 64), npairs);
+  CU(cudaSetDevice(h->cfg.device));
+  // sub-contexts with their own non-blocking streams and workspaces, kept for later calls
+  while ((int)h->workers.size() < workers) {
+    gsvd_rand_config c = h->cfg;
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, GSVD_RAND_ERR_CUDA, "cannot create a worker stream");
+    }
+    c.stream = s;
+    gsvd_rand_t w = nullptr;
+    const int rc = gsvd_rand_create(&w, &c);
+    if (rc) {
+      cudaStreamDestroy(s);
+      return fail(h, rc, "cannot create a worker context");
+    }
+    w->owns_stream = true;
+    h->workers.push_back(w);
+  }
+  // largest pairs first, dealt round-robin: a worker's workspace grows on its first pair only
+  std::vector<int> order(npairs);
+  for (int i = 0; i < npairs; ++i) order[i] = i;
+  auto size_of = [&](int i) {
+    const gsvd_rand_pair& q = pairs[i];
+    return (double)(q.m + q.p) * (double)q.n * (double)(q.k + q.oversample);
+  };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return size_of(a) > size_of(b); });
+  std::vector<std::string> msgs(npairs);
+  std::vector<std::thread> pool;
+  for (int wi = 0; wi < workers; ++wi) {
+    pool.emplace_back([&, wi]() {
+      gsvd_rand_ctx* w = h->workers[wi];
+      cudaSetDevice(w->cfg.device);
+      for (int j = wi; j < npairs; j += workers) {
+        gsvd_rand_pair& q = pairs[order[j]];
+        w->pair_word = q.pair;
+        q.status = gsvd_rand_solve(w, q.G1, q.m, q.ld1, q.G2, q.p, q.ld2, q.n, q.k, q.oversample, q.q, q.seed,
+                                   q.alpha, q.beta, q.r_out, q.resid_out);
+        if (q.status) msgs[order[j]] = w->err;
+      }
+      w->pair_word = 0;
+    });
+  }
+  for (auto& t : pool) t.join();
+  for (int i = 0; i < npairs; ++i)
+    if (pairs[i].status)
+      return fail(h, pairs[i].status, "pair %d (first failing pair): %s", i, msgs[i].c_str());
+  h->err.clear();
+  return GSVD_RAND_OK;
 }
 
 int gsvd_rand_metrics(gsvd_rand_t h, const double* alpha, const double* beta, int r, int pad_to_n,

@@ -872,7 +872,7 @@ cudaError_t launch_apply_rinv(const T* Y, int64_t ldy, int64_t M, int l, const T
 #define GSVDR_APPLY(CTV, RTV, RSV)                                                                              \
   do {                                                                                                          \
     cudaFuncSetAttribute(apply_rinv_kernel<T, TC, CTV, RTV, RSV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                         (int)smem);                                                                            \
+                         220 * 1024); /* a fixed cap: concurrent launches must not lower it */                  \
     apply_rinv_kernel<T, TC, CTV, RTV, RSV><<<blocks, 256, smem, st>>>(Y, ldy, M, l, Rinv, Q, ldq,            \
                                                                       transpose_out, part);                    \
   } while (0)

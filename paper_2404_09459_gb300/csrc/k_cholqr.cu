@@ -19,6 +19,7 @@
 // releases every other waiting CTA.  The launch is cooperative, so all CTAs
 // are resident.
 #include <algorithm>
+#include <mutex>
 
 #include "kernels.h"
 
@@ -422,30 +423,38 @@ int cholqr2_fused_max_ctas() { return 160; }
 template <typename T, typename TC>
 int cholqr2_fused_plan(int64_t M, int l, int64_t* rows_per) {
   if (l < 1 || l > FQ_LP) return 0;
-  // per device: SM count and resident CTAs per SM of this instantiation (looked up once)
+  // per device: SM count and resident CTAs per SM of this instantiation, looked up once
+  // under a lock (the batched workers call this concurrently)
+  static std::mutex mu;
   static int cached[64][2] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
-  if (cached[dev][0] == 0) {
-    int sms = 0, per_sm = 0;
-    const size_t smem = fq_smem_bytes<T>();
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaFuncSetAttribute(cholqr2_fused_kernel<T, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cholqr2_fused_kernel<T, TC>, FQ_THREADS, smem) !=
-            cudaSuccess) {
-      cudaGetLastError();
-      cached[dev][0] = -1;
-    } else {
-      cached[dev][0] = sms;
-      cached[dev][1] = per_sm;
+  int sms_c, per_c;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (cached[dev][0] == 0) {
+      int sms = 0, per_sm = 0;
+      const size_t smem = fq_smem_bytes<T>();
+      if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+          cudaFuncSetAttribute(cholqr2_fused_kernel<T, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+              cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cholqr2_fused_kernel<T, TC>, FQ_THREADS, smem) !=
+              cudaSuccess) {
+        cudaGetLastError();
+        cached[dev][0] = -1;
+      } else {
+        cached[dev][1] = per_sm;
+        cached[dev][0] = sms;
+      }
     }
+    sms_c = cached[dev][0];
+    per_c = cached[dev][1];
   }
-  if (cached[dev][0] <= 0 || cached[dev][1] < 1) return 0;
-  const int64_t max_ctas = std::min<int64_t>((int64_t)cached[dev][0] * cached[dev][1], cholqr2_fused_max_ctas());
+  if (sms_c <= 0 || per_c < 1) return 0;
+  const int64_t max_ctas = std::min<int64_t>((int64_t)sms_c * per_c, cholqr2_fused_max_ctas());
   // FP64 tiles stay short: at the FP64 rate a full tile is too slow for one SM
   const int64_t row_cap = sizeof(T) == 8 ? 32 : FQ_ROWS;
-  int64_t ctas = std::min<int64_t>(std::min<int64_t>(cached[dev][0], max_ctas), cdiv(M, 16));
+  int64_t ctas = std::min<int64_t>(std::min<int64_t>(sms_c, max_ctas), cdiv(M, 16));
   const int64_t rp = cdiv(M, ctas);
   if (rp > row_cap) return 0;
   *rows_per = rp;

@@ -759,7 +759,8 @@ cudaError_t launch_eig_f32(const double* A, int N, double* X, double* lam, float
   const int lda = N | 1;
   if (N <= E_NMAX) {
     const size_t smem = ((size_t)N * E_NMAX + 2 * (size_t)N * lda) * sizeof(float);
-    cudaFuncSetAttribute(eig128_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // a fixed cap (N = 128 needs 197,632 bytes): concurrent launches must not lower it
+    cudaFuncSetAttribute(eig128_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     eig128_kernel<<<1, 1024, smem, st>>>(A, N, X, lam, scratch, (float)noise_rel);
     return launched();
   }

@@ -539,7 +539,9 @@ cudaError_t launch_oa_cut_cluster(int N, int r, double* X, const double* lam, do
   const double* part = work + 4 * nn;
   const int cmax = std::min(N, CUT_CMAX);
   const size_t smem = (size_t)2 * cmax * (cmax | 1) * sizeof(float);
-  cudaFuncSetAttribute(oa_cut_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // a fixed cap (the largest cluster block): concurrent launches must not lower it
+  cudaFuncSetAttribute(oa_cut_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)(2 * CUT_CMAX * (CUT_CMAX | 1) * sizeof(float)));
   oa_cut_cluster_kernel<<<1, 1024, smem, st>>>(N, r, XtX, S, part, nb, lam, Vc, cinfo);
   cudaError_t e = launched();
   if (e) return e;

@@ -398,19 +398,18 @@ __global__ __launch_bounds__(192) void tc_gemm_kernel(const __grid_constant__ CU
 // ---------------------------------------------------------------------------
 namespace {
 
+// Looked up once; a function-local static initialised by a call is thread-safe (concurrent
+// first calls from the batched workers wait for the one initialisation).
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    else
-      cudaGetLastError();
-  }
+      return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    cudaGetLastError();
+    return nullptr;
+  }();
   return fn;
 }
 
@@ -447,14 +446,15 @@ int stages_for(int nmma, int mode, bool split, int per_sm) {
 }
 
 int sm_count() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+  static const int n = []() {
+    int dev = 0, c = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        c <= 0) {
       cudaGetLastError();
-      n = 152;
+      c = 152;
     }
-  }
+    return c;
+  }();
   return n;
 }
 
@@ -493,7 +493,8 @@ template <int MODE, bool NORM, bool SPLIT>
 void launch_tc(dim3 grid, size_t smem, cudaStream_t st, const CUtensorMap& ma, const CUtensorMap& mb, float* out,
                int64_t ldo, int64_t out_rows, int ncols, int nmma, int64_t kdim, int64_t rps, int64_t split_stride,
                int stages, double* gnorm_part, DevStatus* st_dev) {
-  cudaFuncSetAttribute(tc_gemm_kernel<MODE, NORM, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // a fixed cap (pipelines are sized to stay below it): concurrent launches must not lower it
+  cudaFuncSetAttribute(tc_gemm_kernel<MODE, NORM, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
   tc_gemm_kernel<MODE, NORM, SPLIT><<<grid, 192, smem, st>>>(ma, mb, out, ldo, out_rows, ncols, nmma, tmem_cols_for(nmma),
                                                              kdim, rps, split_stride, stages, gnorm_part, st_dev);
 }

@@ -185,6 +185,53 @@ def test_rank_deficient_sketch(prec, sigma, q):
     _check(prec, G1, G2, spec)
 
 
+def _batch_specs(count, seed):
+    rng = np.random.default_rng(seed)
+    specs = []
+    for i in range(count):
+        m, p = (int(x) for x in rng.integers(400, 3000, 2))
+        n = int(rng.integers(100, 400))
+        r = int(rng.integers(5, 40))
+        specs.append(PairSpec(m=m, p=p, n=n, r=r, alpha="uniform", decay="exp10", sigma=1e-6, k=r,
+                              oversample=8, q=1, seed=100 + i))
+    return specs
+
+
+@pytest.mark.parametrize("prec", ["fp64", "tf32x3"])
+def test_batched_uneven_pairs_match_oracle(prec):
+    specs = _batch_specs(10, 5 if prec == "fp64" else 6)
+    mats = [planted_pair(s)[:2] for s in specs]
+    pairs = [dict(G1=_dev(G1, prec), G2=_dev(G2, prec), k=s.kk, oversample=s.oversample, q=s.q, seed=s.seed,
+                  pair=i) for i, (s, (G1, G2)) in enumerate(zip(specs, mats))]
+    with P.Context(prec) as ctx:
+        outs = ctx.solve_batched(pairs, workers=4)
+        again = ctx.solve_batched(pairs, workers=3)
+    for i, (s, (G1, G2), out) in enumerate(zip(specs, mats, outs)):
+        assert out["status"] == 0 and out["r"] == s.kk
+        ref = O.rand_gsvd(G1, G2, s.kk, s.oversample, s.q, s.seed, pair=i)
+        e = O.gsv_error(ref["alpha"], ref["beta"], out["alpha"].cpu().numpy(), out["beta"].cpu().numpy())
+        assert np.max(e) <= TOL[prec], (i, np.max(e))
+        np.testing.assert_array_equal(out["alpha"].cpu().numpy(), again[i]["alpha"].cpu().numpy())
+
+
+def test_batched_equals_single_solves_and_reports_per_pair_status():
+    specs = _batch_specs(5, 7)
+    mats = [planted_pair(s)[:2] for s in specs]
+    pairs = [dict(G1=_dev(G1, "tf32x3"), G2=_dev(G2, "tf32x3"), k=s.kk, oversample=s.oversample, q=s.q,
+                  seed=s.seed, pair=0) for s, (G1, G2) in zip(specs, mats)]
+    with P.Context("tf32x3") as ctx:
+        outs = ctx.solve_batched(pairs, workers=2)
+        for s, (G1, G2), out in zip(specs, mats, outs):
+            single = ctx.solve(_dev(G1, "tf32x3"), _dev(G2, "tf32x3"), s.kk, s.oversample, s.q, s.seed)
+            np.testing.assert_array_equal(single["alpha"].cpu().numpy(), out["alpha"].cpu().numpy())
+        # one bad pair (k + oversample > n) fails alone; the others still run
+        bad = dict(pairs[1])
+        bad["k"] = 500
+        with pytest.raises(P.GsvdRandError) as e:
+            ctx.solve_batched([pairs[0], bad, pairs[2]], workers=2)
+        assert e.value.name == "ARG"
+
+
 def test_adaptive_cap_reached_reports_tol_miss():
     # 256-column cap below n = 300 with a noisy pair: the tolerance cannot be met
     spec = PairSpec(m=600, p=500, n=300, r=20, sigma=1e-2, seed=35)
