@@ -58,7 +58,15 @@ extern "C" {
  *            small GSVD in FP64.
  *   TF32X3 : as TF32, with each operand split hi + lo and three tensor products
  *            (hi*hi + hi*lo + lo*hi), about FP32 accuracy.
- *   BF16   : G is float; products with BF16 inputs and FP32 accumulation.
+ *   BF16   : G is bfloat16; products on tensor cores (kind::f16) with FP32
+ *            accumulation.  G is read in place when its base is 16-byte aligned and
+ *            its row stride a multiple of 8 elements, else copied into the workspace.  Omega is
+ *            the FP64 Gaussian rounded to the nearest FP32 and then to the nearest
+ *            BF16, so the sketch G Omega is exact up to FP32 accumulation.  The power
+ *            steps round their FP32 operand (Q, then Z) to BF16, or split it into
+ *            BF16 hi + lo halves (two products) under GSVD_RAND_FLAG_BF16_SPLIT_POWER;
+ *            the projection Q^T G always takes Q as hi + lo.  CholeskyQR2 and the
+ *            small GSVD as in TF32.  Adaptive mode is not available in BF16.
  *   FP32   : G is float; products with FP32 CUDA-core FMAs (no tensor cores).  */
 typedef enum {
   GSVD_RAND_FP64 = 0,
@@ -95,6 +103,7 @@ typedef struct {
 /* flags */
 #define GSVD_RAND_FLAG_CHOL_FP64 1 /* mixed precisions: run the CholeskyQR factorisations in FP64 */
 #define GSVD_RAND_FLAG_PROFILE 2   /* time each stage with CUDA events on the solve stream */
+#define GSVD_RAND_FLAG_BF16_SPLIT_POWER 4 /* BF16: power-step operands as hi + lo (two products) */
 
 /* Stages timed under GSVD_RAND_FLAG_PROFILE. */
 #define GSVD_RAND_STAGE_SKETCH 0 /* Y = G X products (sketch and power steps) */

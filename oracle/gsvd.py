@@ -100,15 +100,36 @@ def pencil_gsvd(G1: np.ndarray, G2: np.ndarray):
     return alpha, beta
 
 
-def basis_fixed(G: np.ndarray, l: int, q: int, seed: int, pair: int = 0, side: int = 0):
+def round_bf16(x) -> np.ndarray:
+    """Each entry rounded to the nearest FP32, then to the nearest bfloat16 (8-bit
+    significand), ties to even both times; returned as float32.
+
+    bfloat16 keeps the upper 16 bits of an IEEE binary32 word.  Round half to even on
+    the 16 dropped bits: add 0x7FFF plus the lowest kept bit, then clear the dropped
+    bits (a carry into the exponent is the correct round-up across a binade).
+    """
+    f = np.ascontiguousarray(np.asarray(x, dtype=np.float64).astype(np.float32))
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32)
+
+
+def basis_fixed(G: np.ndarray, l: int, q: int, seed: int, pair: int = 0, side: int = 0,
+                omega_round: str | None = None):
     """Fixed-rank randomized range finder with q power iterations.
 
     Y = G Omega (Omega n x l Gaussian, Theorem 3 with l = k + p), Q = orth(Y);
     then q times: Z = orth(G^T Q), Q = orth(G Z)  (subspace iteration,
     Halko-Martinsson-Tropp 2011 Alg. 4.4).  Returns Q (M x l).
+    omega_round="bf16" draws the same Omega rounded to bfloat16 (round_bf16), the test
+    matrix of the BF16 mode: still Gaussian up to a 2^-8 relative perturbation.
     """
     n = G.shape[1]
     Om = gaussian(n, l, seed, pair, side, STREAM_FIXED)
+    if omega_round == "bf16":
+        Om = round_bf16(Om).astype(np.float64)
+    elif omega_round is not None:
+        raise ValueError(f"unknown omega_round {omega_round!r}")
     Q = orth(G @ Om)
     for _ in range(q):
         Z = orth(G.T @ Q)
@@ -116,7 +137,8 @@ def basis_fixed(G: np.ndarray, l: int, q: int, seed: int, pair: int = 0, side: i
     return Q
 
 
-def rand_gsvd(G1, G2, k: int, oversample: int, q: int, seed: int, pair: int = 0):
+def rand_gsvd(G1, G2, k: int, oversample: int, q: int, seed: int, pair: int = 0,
+              omega_round: str | None = None):
     """Algorithm 2 with the fixed-rank basis extraction: the method as the GPU runs it.
 
     For each side s: Q_s = basis_fixed(G_s), B_s = Q_s^T G_s; then the GSVs of
@@ -130,7 +152,7 @@ def rand_gsvd(G1, G2, k: int, oversample: int, q: int, seed: int, pair: int = 0)
     out = {}
     Bs = []
     for s, G in enumerate((G1, G2)):
-        Q = basis_fixed(G, l, q, seed, pair, s)
+        Q = basis_fixed(G, l, q, seed, pair, s, omega_round)
         B = Q.T @ G
         out[f"Q{s + 1}"] = Q
         out[f"B{s + 1}"] = B

@@ -26,6 +26,7 @@ EXPORTS = ("gsvd_rand_config_init", "gsvd_rand_create", "gsvd_rand_destroy", "gs
            "gsvd_rand_metrics_noalloc", "gsvd_rand_basis_cols", "gsvd_rand_solve_batched")
 NOALLOC_MAX_N = 32768
 FLAG_PROFILE = 2
+FLAG_BF16_SPLIT_POWER = 4
 STAGES = ("sketch", "gtq", "orth", "small", "small_gram", "small_jacobi", "small_refine", "small_cs")
 
 
@@ -95,14 +96,14 @@ def _mat_ptr(x, want_dtype: str):
     """(pointer, rows, cols, ld, on_device, keepalive) of a row-major matrix."""
     if _is_torch(x):
         import torch
-        dt = {"f64": torch.float64, "f32": torch.float32}[want_dtype]
+        dt = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[want_dtype]
         if x.dtype != dt:
             raise TypeError(f"expected {dt}, got {x.dtype}")
         if x.dim() != 2 or x.stride(1) != 1:
             raise ValueError("matrix must be 2-D with unit column stride (row-major)")
         return x.data_ptr(), x.shape[0], x.shape[1], max(x.stride(0), x.shape[1]), x.is_cuda, x
     import numpy as np
-    dt = {"f64": np.float64, "f32": np.float32}[want_dtype]
+    dt = {"f64": np.float64, "f32": np.float32, "bf16": np.uint16}[want_dtype]  # bf16: raw bit patterns
     a = np.asarray(x)
     if a.dtype != dt:
         raise TypeError(f"expected {np.dtype(dt)}, got {a.dtype}")
@@ -182,11 +183,14 @@ class Context:
         return a, a.ctypes.data
 
     # ------------------------------------------------------------------ API
+    def _g_dtype(self):
+        return {"fp64": "f64", "bf16": "bf16"}.get(self.prec, "f32")
+
     def solve(self, G1, G2, k: int, oversample: int = 10, q: int = 1, seed: int = 0):
         """Randomized GSVs of {G1, G2}: dict(alpha, beta, r, resid).
 
         Outputs live where G1 lives (CUDA tensors for CUDA inputs, numpy otherwise)."""
-        want = "f64" if self.prec == "fp64" else "f32"
+        want = self._g_dtype()
         p1, m, n1, ld1, dev1, k1 = _mat_ptr(G1, want)
         p2, p, n2, ld2, dev2, k2 = _mat_ptr(G2, want)
         if n1 != n2:
@@ -205,7 +209,7 @@ class Context:
         """Many independent pairs at once.  pairs: sequence of dicts with G1, G2, k and optional
         oversample (10), q (1), seed (0), pair (its index).  Returns a list of dict(alpha, beta, r,
         resid, status); raises GsvdRandError if any pair failed (after all ran)."""
-        want = "f64" if self.prec == "fp64" else "f32"
+        want = self._g_dtype()
         arr = (_Pair * len(pairs))()
         outs, keep = [], []
         for i, d in enumerate(pairs):

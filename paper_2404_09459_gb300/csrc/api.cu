@@ -176,6 +176,10 @@ struct SideBufs {
   void* cscr;     // Cholesky scratch (TC), when shared memory is too small
   double* gnorm;  // sketch-CTA partial sums of G^2
   double* bnorm;  // reduce-block partial sums of B^2
+  void* Xh;       // BF16 mode: hi / lo halves of Xt (lx x ldx)
+  void* Xl;
+  void* Qh;       // BF16 mode: hi / lo halves of Q^T (lx x round_up(M, 8))
+  void* Ql;
 };
 
 struct Plan {
@@ -199,6 +203,8 @@ struct Solver {
   int prec;
   bool use_tc;
   void* bar;  // grid barrier of the fused CholeskyQR2 (zeroed at solve start)
+  bool bf16;         // G is BF16: products on kind::f16 tensor cores
+  bool split_power;  // BF16: power-step operands as hi + lo (two products)
 
   int orth(SideBufs<T>& b, const T* Yin, int64_t M, int l, int64_t lp, T* out, int64_t ldo,
            int transpose_out, int stage) {
@@ -223,25 +229,47 @@ struct Solver {
     const double shift_coef = 11.0 * ((double)rpc + l + 1) * u;
     // pivots below ~8 rpc u relative to their own column are below the Gram's resolution
     const double tau = 8.0 * (double)std::max<int64_t>(rpc, apply_rows_per_cta(l, (int)sizeof(T))) * u;
-    CU(launch_gram_partial<T>(Yin, lp, M, l, b.gpart, chunks, rpc, st));
-    CU(launch_gram_reduce(b.gpart, chunks, l, b.W, st));
+    // the Gram of each new Q: fused into Q = Y R^{-1} (one partial per row tile) for l <= 64;
+    // for wider bases one l x l partial per 32-row tile would be GBs of partials, so the
+    // chunked Gram kernel reads Q again instead
+    const bool fuse = apply_fuses_gram(l);
+    auto gram_of = [&](const T* X) -> int {
+      CU(launch_gram_partial<T>(X, lp, M, l, b.gpart, chunks, rpc, st));
+      CU(launch_gram_reduce(b.gpart, chunks, l, b.W, st));
+      return GSVD_RAND_OK;
+    };
+    int rc;
+    if ((rc = gram_of(Yin))) return rc;
     CU(launch_chol_shift<TC>(b.W, l, shift_coef, tau, (TC*)b.R, (TC*)b.cscr, st_dev, stage, st));
-    CU((launch_apply_rinv<T, TC>(Yin, lp, M, l, (const TC*)b.R, b.tmp, lp, 0, b.gpart, st)));
-    CU(launch_gram_reduce(b.gpart, apply_ctas(M, l, (int)sizeof(T)), l, b.W, st));
+    CU((launch_apply_rinv<T, TC>(Yin, lp, M, l, (const TC*)b.R, b.tmp, lp, 0, fuse ? b.gpart : nullptr, st)));
+    if (fuse)
+      CU(launch_gram_reduce(b.gpart, apply_ctas(M, l, (int)sizeof(T)), l, b.W, st));
+    else if ((rc = gram_of(b.tmp)))
+      return rc;
     CU(launch_chol_shift<TC>(b.W, l, 0.0, tau, (TC*)b.R, (TC*)b.cscr, st_dev, stage + 1, st));
     // CholeskyQR a third time (shifted CholeskyQR3): the shifted first pass leaves Q1
     // far from orthonormal when Y is ill-conditioned (rank-deficient sketches)
     T* q2 = b.tmp + (int64_t)M * lp;
-    CU((launch_apply_rinv<T, TC>(b.tmp, lp, M, l, (const TC*)b.R, q2, lp, 0, b.gpart, st)));
-    CU(launch_gram_reduce(b.gpart, apply_ctas(M, l, (int)sizeof(T)), l, b.W, st));
+    CU((launch_apply_rinv<T, TC>(b.tmp, lp, M, l, (const TC*)b.R, q2, lp, 0, fuse ? b.gpart : nullptr, st)));
+    if (fuse)
+      CU(launch_gram_reduce(b.gpart, apply_ctas(M, l, (int)sizeof(T)), l, b.W, st));
+    else if ((rc = gram_of(q2)))
+      return rc;
     CU(launch_chol_shift<TC>(b.W, l, 0.0, tau, (TC*)b.R, (TC*)b.cscr, st_dev, stage + 1, st));
     CU((launch_apply_rinv<T, TC>(q2, lp, M, l, (const TC*)b.R, out, ldo, transpose_out, nullptr, st)));
     return GSVD_RAND_OK;
   }
 
-  int gx(const T* G, int64_t ldg, int64_t M, const Plan& pl, SideBufs<T>& b, double* gnorm) {
+  // Y = G X.  BF16 mode: X from its BF16 halves (lo: two products).
+  int gx(const void* Gv, int64_t ldg, int64_t M, const Plan& pl, SideBufs<T>& b, double* gnorm, bool lo = false) {
     ProfScope ps(h, GSVD_RAND_STAGE_SKETCH);
+    const T* G = static_cast<const T*>(Gv);
     if constexpr (std::is_same<T, float>::value) {
+      if (bf16) {
+        CU(tc_gemm_gx_bf16(Gv, ldg, M, pl.n, b.Xh, lo ? b.Xl : nullptr, pl.ldx, pl.l, b.Y, pl.lp, gnorm, st_dev,
+                           st));
+        return GSVD_RAND_OK;
+      }
       if (use_tc) {
         CU(tc_gemm_gx(prec, G, ldg, M, pl.n, b.Xt, pl.ldx, pl.l, b.Y, pl.lp, gnorm, st_dev, st));
         return GSVD_RAND_OK;
@@ -251,13 +279,20 @@ struct Solver {
     return GSVD_RAND_OK;
   }
 
-  int gtq(const T* G, int64_t ldg, int64_t M, const Plan& pl, SideBufs<T>& b, T* out, int64_t ldo,
-          int transpose_out, double* sq) {
+  int gtq(const void* Gv, int64_t ldg, int64_t M, const Plan& pl, SideBufs<T>& b, T* out, int64_t ldo,
+          int transpose_out, double* sq, bool lo = false) {
     ProfScope ps(h, GSVD_RAND_STAGE_GTQ);
+    const T* G = static_cast<const T*>(Gv);
     int splits = gemm_gtq_splits(M, pl.n, pl.l, pl.part_elems);
     bool done = false;
     if constexpr (std::is_same<T, float>::value) {
-      if (use_tc) {
+      if (bf16) {
+        int s2 = 0;
+        CU(tc_gemm_gtq_bf16(Gv, ldg, M, pl.n, b.Qh, lo ? b.Ql : nullptr, round_up(M, 8), pl.l, b.part, pl.lp, &s2,
+                            pl.part_elems, st_dev, st));
+        splits = s2;
+        done = true;
+      } else if (use_tc) {
         int s2 = 0;
         // in tensor-core mode Q is kept transposed (Q^T: lx x ldm, K-major operand)
         CU(tc_gemm_gtq(prec, G, ldg, M, pl.n, b.Q, round_up(M, 4), pl.l, b.part, pl.lp, &s2, pl.part_elems, st_dev,
@@ -273,11 +308,27 @@ struct Solver {
     return GSVD_RAND_OK;
   }
 
-  int side(const T* G, int64_t ldg, int s, const Plan& pl, SideBufs<T>& b, int q, uint64_t seed,
+  // BF16 halves of Q^T (the B operand of G^T Q) and of Xt (of G X)
+  int split_q(SideBufs<T>& b, int64_t M, const Plan& pl, bool lo) {
+    if constexpr (std::is_same<T, float>::value)
+      CU(launch_split_bf16(b.Q, round_up(M, 4), pl.lx, M, b.Qh, lo ? b.Ql : nullptr, round_up(M, 8), st));
+    return GSVD_RAND_OK;
+  }
+  int split_x(SideBufs<T>& b, const Plan& pl, bool lo) {
+    if constexpr (std::is_same<T, float>::value)
+      CU(launch_split_bf16(b.Xt, pl.ldx, pl.lx, pl.n, b.Xh, lo ? b.Xl : nullptr, pl.ldx, st));
+    return GSVD_RAND_OK;
+  }
+
+  int side(const void* G, int64_t ldg, int s, const Plan& pl, SideBufs<T>& b, int q, uint64_t seed,
            T* Srows) {
     const int64_t M = pl.M[s];
-    CU(launch_gaussian_kmajor<T>(b.Xt, pl.ldx, pl.n, pl.l, (int)pl.lx, seed, h->pair_word, (uint32_t)s,
-                                 GSVD_RAND_STREAM_FIXED, st));
+    if (bf16)
+      CU(launch_gaussian_kmajor_bf16(b.Xh, pl.ldx, pl.n, pl.l, (int)pl.lx, seed, h->pair_word, (uint32_t)s,
+                                     GSVD_RAND_STREAM_FIXED, st));
+    else
+      CU(launch_gaussian_kmajor<T>(b.Xt, pl.ldx, pl.n, pl.l, (int)pl.lx, seed, h->pair_word, (uint32_t)s,
+                                   GSVD_RAND_STREAM_FIXED, st));
     // Q layout: row-major M x lp for the CUDA-core product, transposed Q^T
     // (lx x ldm, padding rows zero) as the K-major operand of the tensor-core one
     const int qt = use_tc ? 1 : 0;
@@ -287,31 +338,36 @@ struct Solver {
     int rc;
     if ((rc = gx(G, ldg, M, pl, b, b.gnorm))) return rc;
     if ((rc = orth(b, b.Y, M, pl.l, pl.lp, b.Q, ldq, qt, 10 * s + 1))) return rc;
+    // BF16 mode: the power steps take their FP32 operand rounded to BF16 (or as hi + lo
+    // with split_power); the projection always takes Q as hi + lo
     for (int it = 0; it < q; ++it) {
-      if ((rc = gtq(G, ldg, M, pl, b, b.Z, pl.lp, 0, nullptr))) return rc;
+      if (bf16 && (rc = split_q(b, M, pl, split_power))) return rc;
+      if ((rc = gtq(G, ldg, M, pl, b, b.Z, pl.lp, 0, nullptr, split_power))) return rc;
       if ((rc = orth(b, b.Z, pl.n, pl.l, pl.lp, b.Xt, pl.ldx, 1, 10 * s + 3))) return rc;
-      if ((rc = gx(G, ldg, M, pl, b, nullptr))) return rc;
+      if (bf16 && (rc = split_x(b, pl, split_power))) return rc;
+      if ((rc = gx(G, ldg, M, pl, b, nullptr, split_power))) return rc;
       if ((rc = orth(b, b.Y, M, pl.l, pl.lp, b.Q, ldq, qt, 10 * s + 5))) return rc;
     }
     // projection B = Q^T G written as l rows of S
-    if ((rc = gtq(G, ldg, M, pl, b, Srows, pl.ldn, 1, b.bnorm))) return rc;
+    if (bf16 && (rc = split_q(b, M, pl, true))) return rc;
+    if ((rc = gtq(G, ldg, M, pl, b, Srows, pl.ldn, 1, b.bnorm, true))) return rc;
     return GSVD_RAND_OK;
   }
 };
 
 template <typename T>
-SideBufs<T> side_take(Bump& bp, const Plan& pl, int s, bool tc);
+SideBufs<T> side_take(Bump& bp, const Plan& pl, int s, bool tc, bool bf16);
 
 // Bytes carved by side_take (the same code run on a null base).
 template <typename T>
-size_t side_bytes(const Plan& pl, int s, bool tc) {
+size_t side_bytes(const Plan& pl, int s, bool tc, bool bf16) {
   Bump bp;
-  side_take<T>(bp, pl, s, tc);
+  side_take<T>(bp, pl, s, tc, bf16);
   return bp.off + 256;
 }
 
 template <typename T>
-SideBufs<T> side_take(Bump& bp, const Plan& pl, int s, bool tc) {
+SideBufs<T> side_take(Bump& bp, const Plan& pl, int s, bool tc, bool bf16) {
   SideBufs<T> b;
   int64_t M = pl.M[s];
   b.Xt = bp.take<T>(pl.lx * pl.ldx);
@@ -326,6 +382,13 @@ SideBufs<T> side_take(Bump& bp, const Plan& pl, int s, bool tc) {
   b.cscr = bp.take<double>(chol_scratch_elems(pl.l));
   b.gnorm = bp.take<double>(std::max<int64_t>(gemm_gx_simt_ctas(M), tc ? tc_gx_ctas(M) : 1) + 8);
   b.bnorm = bp.take<double>(cdiv(pl.n * pl.l, 256) + 8);
+  b.Xh = b.Xl = b.Qh = b.Ql = nullptr;
+  if (bf16) {
+    b.Xh = bp.take<uint16_t>(pl.lx * pl.ldx);
+    b.Xl = bp.take<uint16_t>(pl.lx * pl.ldx);
+    b.Qh = bp.take<uint16_t>(pl.lx * round_up(M, 8));
+    b.Ql = bp.take<uint16_t>(pl.lx * round_up(M, 8));
+  }
   return b;
 }
 
@@ -439,15 +502,19 @@ int solve_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, const voi
             int* r_out, double* resid_out) {
   cudaStream_t st = h->stream;
   const int prec = h->cfg.prec;
-  if (prec == GSVD_RAND_BF16)
-    return fail(h, GSVD_RAND_ERR_UNSUPPORTED, "precision mode %d is not built yet", prec);
-  bool use_tc = prec == GSVD_RAND_TF32 || prec == GSVD_RAND_TF32X3;
+  const bool bf16 = prec == GSVD_RAND_BF16;
+  bool use_tc = prec == GSVD_RAND_TF32 || prec == GSVD_RAND_TF32X3 || bf16;
   if (use_tc && !h->tc_ok) return fail(h, GSVD_RAND_ERR_UNSUPPORTED, "tensor-core path unavailable on this device");
-  // host inputs are staged with a 16-byte-multiple row stride; device inputs that
-  // TMA cannot address (unaligned base or row stride) run the CUDA-core FP32 products
-  const int64_t lds = round_up(n, 4);
-  bool d1 = is_device_ptr(G1v), d2 = is_device_ptr(G2v);
-  if (use_tc && ((d1 && !tc_shape_ok(G1v, ld1, k + os)) || (d2 && !tc_shape_ok(G2v, ld2, k + os)))) use_tc = false;
+  // host inputs are staged with a 16-byte-multiple row stride; FP32 device inputs that
+  // TMA cannot address (unaligned base or row stride) run the CUDA-core products, BF16
+  // ones (no CUDA-core path) are staged like host inputs
+  const int eg = bf16 ? 2 : (int)sizeof(T);  // bytes per element of G
+  const int64_t lds = round_up(n, 16 / eg);
+  const bool dev1 = is_device_ptr(G1v), dev2 = is_device_ptr(G2v);
+  const bool ok1 = dev1 && tc_shape_ok(G1v, ld1, k + os, eg), ok2 = dev2 && tc_shape_ok(G2v, ld2, k + os, eg);
+  // d1 / d2: G is used in place (else staged into the workspace)
+  const bool d1 = dev1 && (ok1 || !bf16), d2 = dev2 && (ok2 || !bf16);
+  if (use_tc && !bf16 && ((dev1 && !ok1) || (dev2 && !ok2))) use_tc = false;
   Plan pl;
   pl.M[0] = m;
   pl.M[1] = p;
@@ -464,18 +531,18 @@ int solve_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, const voi
   pl.part_elems = std::min<int64_t>(pl.part_elems, std::max<int64_t>(16ll << 20, n * pl.lp));
   int64_t rpc;
   int gch = gram_chunks(std::max(maxM, n), pl.l, &rpc);
-  int ach = apply_ctas(std::max(maxM, n), pl.l, (int)sizeof(T));
+  int ach = apply_fuses_gram(pl.l) ? apply_ctas(std::max(maxM, n), pl.l, (int)sizeof(T)) : 0;
   pl.gpart_elems = (int64_t)std::max(std::max(gch, ach), cholqr2_fused_max_ctas()) * pl.l * pl.l;
 
   // host inputs are staged into the workspace
   Bump sizer;
   sizer.take<DevStatus>(1);
   sizer.take<unsigned char>((int64_t)cholqr2_fused_bar_bytes());
-  if (!d1) sizer.take<T>(m * lds);
-  if (!d2) sizer.take<T>(p * lds);
+  if (!d1) sizer.take<unsigned char>(m * lds * eg);
+  if (!d2) sizer.take<unsigned char>(p * lds * eg);
   sizer.take<T>((int64_t)pl.L * pl.ldn);
   size_t b0 = sizer.off;
-  size_t need = b0 + side_bytes<T>(pl, 0, use_tc) + side_bytes<T>(pl, 1, use_tc) + 4096;
+  size_t need = b0 + side_bytes<T>(pl, 0, use_tc, bf16) + side_bytes<T>(pl, 1, use_tc, bf16) + 4096;
   Bump sb_sizer;
   small_take(sb_sizer, pl.L, k, n);
   need += sb_sizer.off + 4096;
@@ -486,29 +553,31 @@ int solve_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, const voi
   bp.base = h->ws;
   DevStatus* st_dev = bp.take<DevStatus>(1);
   void* bar = bp.take<unsigned char>((int64_t)cholqr2_fused_bar_bytes());
-  const T* G1 = (const T*)G1v;
-  const T* G2 = (const T*)G2v;
+  const void* G1 = G1v;
+  const void* G2 = G2v;
   int64_t l1d = ld1, l2d = ld2;
   if (!d1) {
-    T* g = bp.take<T>(m * lds);
-    CU(cudaMemcpy2DAsync(g, lds * sizeof(T), G1v, ld1 * sizeof(T), n * sizeof(T), m, cudaMemcpyHostToDevice, st));
+    unsigned char* g = bp.take<unsigned char>(m * lds * eg);
+    CU(cudaMemcpy2DAsync(g, lds * eg, G1v, ld1 * eg, n * eg, m, dev1 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                         st));
     G1 = g;
     l1d = lds;
   }
   if (!d2) {
-    T* g = bp.take<T>(p * lds);
-    CU(cudaMemcpy2DAsync(g, lds * sizeof(T), G2v, ld2 * sizeof(T), n * sizeof(T), p, cudaMemcpyHostToDevice, st));
+    unsigned char* g = bp.take<unsigned char>(p * lds * eg);
+    CU(cudaMemcpy2DAsync(g, lds * eg, G2v, ld2 * eg, n * eg, p, dev2 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                         st));
     G2 = g;
     l2d = lds;
   }
   T* S = bp.take<T>((int64_t)pl.L * pl.ldn);
-  SideBufs<T> sb0 = side_take<T>(bp, pl, 0, use_tc);
-  SideBufs<T> sb1 = side_take<T>(bp, pl, 1, use_tc);
+  SideBufs<T> sb0 = side_take<T>(bp, pl, 0, use_tc, bf16);
+  SideBufs<T> sb1 = side_take<T>(bp, pl, 1, use_tc, bf16);
   SmallBufs small = small_take(bp, pl.L, k, n);
   CU(cudaMemsetAsync(st_dev, 0, sizeof(DevStatus), st));
   CU(cudaMemsetAsync(bar, 0, cholqr2_fused_bar_bytes(), st));
 
-  Solver<T, TC> sv{h, st, st_dev, prec, use_tc, bar};
+  Solver<T, TC> sv{h, st, st_dev, prec, use_tc, bar, bf16, (h->cfg.flags & GSVD_RAND_FLAG_BF16_SPLIT_POWER) != 0};
   if ((rc = sv.side(G1, l1d, 0, pl, sb0, q, seed, S))) return rc;
   if ((rc = sv.side(G2, l2d, 1, pl, sb1, q, seed, S + (int64_t)pl.l * pl.ldn))) return rc;
   int gct0 = use_tc ? tc_gx_ctas(m) : gemm_gx_simt_ctas(m);
@@ -578,8 +647,7 @@ int solve_adaptive_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, 
                      double* resid_out) {
   cudaStream_t st = h->stream;
   const int prec = h->cfg.prec;
-  if (prec == GSVD_RAND_BF16)
-    return fail(h, GSVD_RAND_ERR_UNSUPPORTED, "precision mode %d is not built yet", prec);
+  if (prec == GSVD_RAND_BF16) return fail(h, GSVD_RAND_ERR_UNSUPPORTED, "adaptive mode is not available in BF16");
   const int bsz = h->cfg.block_b;
   const double tol = h->cfg.tol;
   if (bsz < 1 || bsz > 256) return fail(h, GSVD_RAND_ERR_ARG, "block_b must be in [1, 256]");
@@ -600,7 +668,7 @@ int solve_adaptive_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, 
   const int64_t part_elems = std::max<int64_t>(16ll << 20, n * capp);
   int64_t rpc;
   const int gch = gram_chunks(maxM, bsz, &rpc);
-  const int ach = apply_ctas(maxM, bsz, (int)sizeof(T));
+  const int ach = apply_fuses_gram(bsz) ? apply_ctas(maxM, bsz, (int)sizeof(T)) : 0;
   const int64_t gpart_elems = (int64_t)std::max(std::max(gch, ach), cholqr2_fused_max_ctas()) * bsz * bsz;
   const int gn = std::max(use_tc ? tc_gx_ctas(maxM) : 1, gemm_gx_simt_ctas(maxM)) + 8;
   const int64_t sqn = cdiv(n * capp, 256) + 8;

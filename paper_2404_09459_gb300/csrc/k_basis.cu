@@ -2,6 +2,8 @@
 // and power products (the FP64 / FP32 paths), split-K reduction, the Gram
 // matrix, the shifted Cholesky factorisation and the triangular apply of
 // CholeskyQR2.  Tensor-core products live in k_tc.cu.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 
 #include "kernels.h"
@@ -93,6 +95,69 @@ template cudaError_t launch_gaussian_kmajor<double>(double*, int64_t, int64_t, i
                                                     uint32_t, uint32_t, uint32_t, cudaStream_t);
 template cudaError_t launch_gaussian_kmajor<float>(float*, int64_t, int64_t, int, int, uint64_t,
                                                    uint32_t, uint32_t, uint32_t, cudaStream_t);
+
+// Omega^T K-major in BF16, the sketch operand of the BF16 mode: each entry is the
+// FP64 Gaussian rounded to the nearest FP32, then to the nearest BF16 (ties to even).
+__global__ void gaussian_kmajor_bf16_kernel(__nv_bfloat16* Xt, int64_t ldx, int64_t n, int l, int lrows,
+                                            uint32_t k0, uint32_t k1, uint32_t pair, uint32_t side,
+                                            uint32_t stream) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y;
+  if (i >= ldx || j >= lrows) return;
+  float v = 0.f;
+  if (i < n && j < l) v = (float)gaussian_at<double>(i * (int64_t)l + j, k0, k1, pair, side, stream);
+  Xt[(int64_t)j * ldx + i] = __float2bfloat16_rn(v);
+}
+
+cudaError_t launch_gaussian_kmajor_bf16(void* Xt, int64_t ldx, int64_t n, int l, int lrows, uint64_t seed,
+                                        uint32_t pair, uint32_t side, uint32_t stream, cudaStream_t st) {
+  dim3 grid((unsigned)cdiv(ldx, 256), (unsigned)lrows);
+  gaussian_kmajor_bf16_kernel<<<grid, 256, 0, st>>>(static_cast<__nv_bfloat16*>(Xt), ldx, n, l, lrows,
+                                                    (uint32_t)seed, (uint32_t)(seed >> 32), pair, side, stream);
+  return launched();
+}
+
+// hi = bf16(x) and lo = bf16(x - hi) (x - hi is exact in FP32), both to nearest even, so
+// that hi + lo carries x to about 2^-16 of its size.  Eight columns per thread.
+__global__ void split_bf16_kernel(const float* __restrict__ src, int64_t lds, int64_t rows, int64_t cols,
+                                  __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, int64_t ldd,
+                                  int vec) {
+  const int64_t groups = (cols + 7) / 8;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= rows * groups) return;
+  const int64_t r = t / groups, c0 = (t % groups) * 8;
+  const float* x = src + r * lds + c0;
+  if (vec && c0 + 8 <= cols) {
+    const float4 a = *reinterpret_cast<const float4*>(x), b = *reinterpret_cast<const float4*>(x + 4);
+    const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    __align__(16) __nv_bfloat16 h[8], w[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      h[e] = __float2bfloat16_rn(v[e]);
+      w[e] = __float2bfloat16_rn(v[e] - __bfloat162float(h[e]));
+    }
+    *reinterpret_cast<uint4*>(hi + r * ldd + c0) = *reinterpret_cast<const uint4*>(h);
+    if (lo) *reinterpret_cast<uint4*>(lo + r * ldd + c0) = *reinterpret_cast<const uint4*>(w);
+    return;
+  }
+  for (int e = 0; e < 8 && c0 + e < cols; ++e) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(x[e]);
+    hi[r * ldd + c0 + e] = h;
+    if (lo) lo[r * ldd + c0 + e] = __float2bfloat16_rn(x[e] - __bfloat162float(h));
+  }
+}
+
+cudaError_t launch_split_bf16(const float* src, int64_t lds, int64_t rows, int64_t cols, void* hi, void* lo,
+                              int64_t ldd, cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  const int vec = ((uintptr_t)src % 16 == 0) && (lds % 4 == 0) && ((uintptr_t)hi % 16 == 0) &&
+                  ((uintptr_t)lo % 16 == 0) && (ldd % 8 == 0);
+  const int64_t threads = rows * ((cols + 7) / 8);
+  split_bf16_kernel<<<(unsigned)cdiv(threads, 256), 256, 0, st>>>(src, lds, rows, cols,
+                                                                  static_cast<__nv_bfloat16*>(hi),
+                                                                  static_cast<__nv_bfloat16*>(lo), ldd, vec);
+  return launched();
+}
 
 // ============================================================================
 // Sum of squares accumulators: FP64 for double data, double-float (Knuth
@@ -760,6 +825,7 @@ int apply_ct(int l) { return l <= 64 ? 4 : (l <= 128 ? 8 : 16); }
 // FP64 tiles are smaller: at the FP64 rate the work of a 128-row tile would leave most SMs idle
 int64_t apply_rows_per_cta(int l, int elem_bytes) { return l <= 64 ? (elem_bytes == 8 ? 32 : 128) : 32; }
 int apply_ctas(int64_t M, int l, int elem_bytes) { return (int)cdiv(M, apply_rows_per_cta(l, elem_bytes)); }
+bool apply_fuses_gram(int l) { return l <= 64; }
 
 // RS: R^{-1} staged in shared memory (else read through L1 from global).
 template <typename T, typename TC, int CT, int RT, bool RS>

@@ -1,6 +1,8 @@
 // Tensor-core products of the basis extraction on sm_103a: tcgen05.mma with
-// TF32 operands and FP32 accumulation in tensor memory, operands staged by TMA
-// (cp.async.bulk.tensor, 128-byte swizzle) through an mbarrier pipeline.
+// TF32 (kind::tf32) or BF16 (kind::f16) operands and FP32 accumulation in
+// tensor memory, operands staged by TMA (cp.async.bulk.tensor, 128-byte
+// swizzle) through an mbarrier pipeline.  One stage holds 128 bytes of K per
+// operand row: 32 FP32 or 64 BF16 elements.
 //
 //   GX  : Y (M x l) = G (M x n) X        A = G tile (128 rows, K-major),
 //                                        B = X^T tile (K-major), one CTA per 128 rows.
@@ -25,8 +27,8 @@ namespace gsvdr {
 namespace {
 
 constexpr int TC_BM = 128;       // MMA M (rows of the accumulator / TMEM lanes)
-constexpr int TC_BK = 32;        // K depth of one stage: 32 floats = one 128-byte swizzle row
-constexpr int TC_KSTEP = 8;      // K of one tf32 MMA (32 bytes)
+constexpr int TC_BK = 32;        // K depth of one FP32 stage: 32 floats = one 128-byte swizzle row
+constexpr int TC_KSTEP_BYTES = 32;  // K of one MMA: 8 TF32 or 16 BF16 elements
 constexpr int TC_A_BYTES = TC_BM * TC_BK * 4;  // 16 KB
 constexpr uint32_t WAIT_SPINS = 1u << 22;      // bounded waits (try_wait suspends per call)
 
@@ -96,6 +98,15 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
 // Arrive on `bar` once all previously issued MMAs of this thread have completed.
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -131,6 +142,10 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
 __host__ __device__ constexpr uint32_t idesc_tf32(uint32_t m, uint32_t n, uint32_t a_mn, uint32_t b_mn) {
   return (1u << 4) | (2u << 7) | (2u << 10) | (a_mn << 15) | (b_mn << 16) | ((n >> 3) << 17) | ((m >> 4) << 24);
 }
+// kind::f16 with A = B = BF16 (format 1), D = F32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(uint32_t m, uint32_t n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((m >> 4) << 24);
+}
 
 struct SqAccF {
   float hi = 0.f, lo = 0.f;
@@ -150,11 +165,12 @@ struct SqAccF {
 //   A    TMA target for A: the G tile K-major (GX) or the staged G tile (GTQ)
 //   B    TMA target for B (X^T or Q^T tile, K-major)
 //   AK   K-major A fed to the MMA (= A in GX, the transposed tile in GTQ)
-//   ALO  (3xTF32) A - tf32(A) in the layout of AK;  BLO  (3xTF32) B - tf32(B)
+//   ALO  (3xTF32) A - tf32(A) in the layout of AK
+//   BLO  (3xTF32) B - tf32(B); (BF16 split) TMA target for the low half of B
 struct StageLayout {
   uint32_t a, b, ak, alo, blo, bytes;
-  __host__ __device__ StageLayout(int mode, bool split, int nmma) {
-    const uint32_t nb = ((uint32_t)nmma * TC_BK * 4 + 1023u) & ~1023u;
+  __host__ __device__ StageLayout(int mode, bool split, int nmma, int eb = 4) {
+    const uint32_t nb = ((uint32_t)nmma * 128u + 1023u) & ~1023u;
     a = 0;
     b = TC_A_BYTES;
     uint32_t o = b + nb;
@@ -165,8 +181,10 @@ struct StageLayout {
     }
     alo = blo = 0;
     if (split) {
-      alo = o;
-      o += TC_A_BYTES;
+      if (eb == 4) {
+        alo = o;
+        o += TC_A_BYTES;
+      }
       blo = o;
       o += nb;
     }
@@ -180,30 +198,36 @@ __device__ __forceinline__ float tf32_lo(float x) {
 
 // mode 0 (GX): tile = blockIdx.x (rows m0 = 128 tile), K = n.
 // mode 1 (GTQ): tile = blockIdx.x (G columns c0 = 128 tile), split = blockIdx.y (rows).
-// SPLIT: 3xTF32, D += A_hi B_hi + A_lo B_hi + A_hi B_lo (the tensor core truncates
-// each FP32 operand to TF32, so A_hi is A itself and A_lo = A - tf32(A)).
-template <int MODE, bool NORM, bool SPLIT>
+// EB = 4 (FP32 data, kind::tf32).  SPLIT: 3xTF32, D += A_hi B_hi + A_lo B_hi + A_hi B_lo
+// (the tensor core truncates each FP32 operand to TF32, so A_hi is A itself and
+// A_lo = A - tf32(A), formed in shared memory).
+// EB = 2 (BF16 data, kind::f16).  G is exact in BF16; SPLIT: B comes as two BF16
+// halves hi + lo (both loaded by TMA, mapB2 = lo), D += A B_hi + A B_lo.
+template <int MODE, bool NORM, bool SPLIT, int EB>
 __global__ __launch_bounds__(192) void tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
-                                                      const __grid_constant__ CUtensorMap mapB, float* __restrict__ out,
+                                                      const __grid_constant__ CUtensorMap mapB,
+                                                      const __grid_constant__ CUtensorMap mapB2, float* __restrict__ out,
                                                       int64_t ldo, int64_t out_rows, int ncols, int nmma, int tmem_cols,
                                                       int64_t kdim, int64_t rows_per_split, int64_t split_stride,
                                                       int stages, double* __restrict__ gnorm_part, DevStatus* st_dev) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
+  constexpr int BKE = 128 / EB;  // K elements of one stage
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const StageLayout L(MODE, SPLIT, nmma);
-  const uint32_t b_bytes = (uint32_t)nmma * TC_BK * 4;
+  const StageLayout L(MODE, SPLIT, nmma, EB);
+  const uint32_t b_bytes = (uint32_t)nmma * 128u;
   uint64_t* full = reinterpret_cast<uint64_t*>(base + (size_t)stages * L.bytes);
   uint64_t* empty = full + stages;
   uint64_t* tfull = empty + stages;  // operands prepared by the epilogue warps
   uint64_t* accum = tfull + stages;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
-  // The tensor cores take TF32 operands K-major only, so in GTQ the epilogue
-  // warps transpose each staged G tile (32 rows x 128 columns, unswizzled)
-  // into the K-major 128-byte-swizzled layout of A (128 rows x 32 floats).
+  // The tensor cores are fed K-major operands only here, so in GTQ the epilogue
+  // warps transpose each staged G tile (BKE rows x 128 columns, unswizzled)
+  // into the K-major 128-byte-swizzled layout of A (128 rows x 128 bytes).
   constexpr bool TRANSPOSE = MODE == 1;
-  constexpr bool PREP = TRANSPOSE || SPLIT;         // MMA waits for the prepared operands
-  constexpr bool EPI_STAGE = PREP || NORM;          // epilogue warps visit every stage
+  constexpr bool PREP = TRANSPOSE || (SPLIT && EB == 4);  // MMA waits for the prepared operands
+  constexpr bool EPI_STAGE = PREP || NORM;                // epilogue warps visit every stage
+  constexpr bool B2 = SPLIT && EB == 2;                    // second B operand by TMA
   __shared__ int s_abort;
   __shared__ double s_red[4];
 
@@ -215,7 +239,7 @@ __global__ __launch_bounds__(192) void tc_gemm_kernel(const __grid_constant__ CU
     k_begin = (int64_t)blockIdx.y * rows_per_split;
     k_end = min(kdim, k_begin + rows_per_split);
   }
-  const int ktiles = (int)((k_end - k_begin + TC_BK - 1) / TC_BK);
+  const int ktiles = (int)((k_end - k_begin + BKE - 1) / BKE);
   const int tile0 = blockIdx.x * TC_BM;
 
   if (tid == 0) {
@@ -248,16 +272,19 @@ __global__ __launch_bounds__(192) void tc_gemm_kernel(const __grid_constant__ CU
         if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) break;
         ++issued;
         uint8_t* st = base + (size_t)s * L.bytes;
-        mbar_expect_tx(&full[s], (uint32_t)TC_A_BYTES + b_bytes);
-        const int k0 = (int)(k_begin + (int64_t)kt * TC_BK);
+        mbar_expect_tx(&full[s], (uint32_t)TC_A_BYTES + b_bytes * (B2 ? 2u : 1u));
+        const int k0 = (int)(k_begin + (int64_t)kt * BKE);
         if (MODE == 0) {
-          tma_load_2d(st + L.a, &mapA, &full[s], k0, tile0);  // G[tile0.., k0..]: 128 rows x 32 floats
+          tma_load_2d(st + L.a, &mapA, &full[s], k0, tile0);  // G[tile0.., k0..]: 128 rows x 128 bytes
         } else {
+          // G[k0.., tile0 + ..]: BKE rows x 128 columns as unswizzled boxes of 128-byte rows
+          constexpr int NBOX = 128 / BKE;
 #pragma unroll
-          for (int q = 0; q < 4; ++q)  // G[k0.., tile0 + 32q ..]: 32 rows x 32 floats, unswizzled
-            tma_load_2d(st + L.a + q * (TC_BK * 128), &mapA, &full[s], tile0 + 32 * q, k0);
+          for (int q = 0; q < NBOX; ++q)
+            tma_load_2d(st + L.a + q * (BKE * 128), &mapA, &full[s], tile0 + BKE * q, k0);
         }
-        tma_load_2d(st + L.b, &mapB, &full[s], k0, 0);  // B^T rows 0..nmma-1, K k0..k0+31
+        tma_load_2d(st + L.b, &mapB, &full[s], k0, 0);  // B^T rows 0..nmma-1, K k0..k0+BKE-1
+        if (B2) tma_load_2d(st + L.blo, &mapB2, &full[s], k0, 0);
       }
       if (*abort_flag) {
         // drain: wait (bounded) until the copies this thread issued have landed
@@ -270,7 +297,7 @@ __global__ __launch_bounds__(192) void tc_gemm_kernel(const __grid_constant__ CU
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
-      const uint32_t idesc = idesc_tf32(TC_BM, (uint32_t)nmma, 0u, 0u);
+      const uint32_t idesc = EB == 4 ? idesc_tf32(TC_BM, (uint32_t)nmma, 0u, 0u) : idesc_bf16(TC_BM, (uint32_t)nmma);
       for (int kt = 0; kt < ktiles; ++kt) {
         const int s = kt % stages;
         const uint32_t ph = (uint32_t)(kt / stages) & 1u;
@@ -278,14 +305,20 @@ __global__ __launch_bounds__(192) void tc_gemm_kernel(const __grid_constant__ CU
         tc_fence_after();
         const uint32_t st = smem_u32(base + (size_t)s * L.bytes);
 #pragma unroll
-        for (int ks = 0; ks < TC_BK / TC_KSTEP; ++ks) {
+        for (int ks = 0; ks < 128 / TC_KSTEP_BYTES; ++ks) {
           // K-major operands: 8-row groups 1024 B apart, K step = 32 B inside the swizzle row
-          const uint64_t adesc = smem_desc(st + L.ak + ks * 32, 16, 1024);
-          const uint64_t bdesc = smem_desc(st + L.b + ks * 32, 16, 1024);
-          mma_tf32(tmem, adesc, bdesc, idesc, (kt > 0 || ks > 0) ? 1u : 0u);
-          if (SPLIT) {
-            mma_tf32(tmem, smem_desc(st + L.alo + ks * 32, 16, 1024), bdesc, idesc, 1u);
-            mma_tf32(tmem, adesc, smem_desc(st + L.blo + ks * 32, 16, 1024), idesc, 1u);
+          const uint64_t adesc = smem_desc(st + L.ak + ks * TC_KSTEP_BYTES, 16, 1024);
+          const uint64_t bdesc = smem_desc(st + L.b + ks * TC_KSTEP_BYTES, 16, 1024);
+          const uint32_t acc = (kt > 0 || ks > 0) ? 1u : 0u;
+          if (EB == 4) {
+            mma_tf32(tmem, adesc, bdesc, idesc, acc);
+            if (SPLIT) {
+              mma_tf32(tmem, smem_desc(st + L.alo + ks * TC_KSTEP_BYTES, 16, 1024), bdesc, idesc, 1u);
+              mma_tf32(tmem, adesc, smem_desc(st + L.blo + ks * TC_KSTEP_BYTES, 16, 1024), idesc, 1u);
+            }
+          } else {
+            mma_f16(tmem, adesc, bdesc, idesc, acc);
+            if (SPLIT) mma_f16(tmem, adesc, smem_desc(st + L.blo + ks * TC_KSTEP_BYTES, 16, 1024), idesc, 1u);
           }
         }
         mma_commit(&empty[s]);
@@ -305,7 +338,7 @@ __global__ __launch_bounds__(192) void tc_gemm_kernel(const __grid_constant__ CU
         const uint32_t ph = (uint32_t)(kt / stages) & 1u;
         if (!mbar_wait(&full[s], ph, abort_flag)) break;
         uint8_t* st = base + (size_t)s * L.bytes;
-        if (TRANSPOSE) {
+        if (TRANSPOSE && EB == 4) {
           // thread c owns row c of the K-major tile: staged value (k, c) sits at
           // (c / 32) * 4 KB + k * 128 B + (c % 32) * 4 B; row c is 128 B whose
           // 16-byte chunk ch lands at chunk ch ^ (c % 8) (128-byte swizzle).
@@ -322,22 +355,60 @@ __global__ __launch_bounds__(192) void tc_gemm_kernel(const __grid_constant__ CU
             if (SPLIT)
               *reinterpret_cast<float4*>(rlo + off) = make_float4(tf32_lo(v.x), tf32_lo(v.y), tf32_lo(v.z), tf32_lo(v.w));
           }
-        } else if (SPLIT || NORM) {
+        } else if (TRANSPOSE) {
+          // BF16: thread (cp, h) takes columns 2cp, 2cp+1 and K rows 32h .. 32h+31.  The
+          // staged 32-bit word (k, cp) holds (k, 2cp) low and (k, 2cp+1) high, at
+          // (cp / 32) * 8 KB + k * 128 B + (cp % 32) * 4 B.  Two such words of rows k, k+1
+          // give one word of row 2cp and one of row 2cp+1 of the K-major tile.
+          const int cp = et & 63, hh = et >> 6;
+          const uint32_t* stg = reinterpret_cast<const uint32_t*>(st + L.a + (cp >> 5) * (64 * 128)) + (cp & 31);
+          const int r0 = 2 * cp, r1 = 2 * cp + 1;
+          uint8_t* row0 = st + L.ak + r0 * 128;
+          uint8_t* row1 = st + L.ak + r1 * 128;
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc) {
+            const int ch = 4 * hh + cc;  // 16-byte chunk: K = 8ch .. 8ch + 7
+            uint32_t w[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) w[i] = stg[(8 * ch + i) * 32];
+            uint4 a0, a1;
+            a0.x = __byte_perm(w[0], w[1], 0x5410);
+            a0.y = __byte_perm(w[2], w[3], 0x5410);
+            a0.z = __byte_perm(w[4], w[5], 0x5410);
+            a0.w = __byte_perm(w[6], w[7], 0x5410);
+            a1.x = __byte_perm(w[0], w[1], 0x7632);
+            a1.y = __byte_perm(w[2], w[3], 0x7632);
+            a1.z = __byte_perm(w[4], w[5], 0x7632);
+            a1.w = __byte_perm(w[6], w[7], 0x7632);
+            *reinterpret_cast<uint4*>(row0 + ((ch ^ (r0 & 7)) << 4)) = a0;
+            *reinterpret_cast<uint4*>(row1 + ((ch ^ (r1 & 7)) << 4)) = a1;
+          }
+        } else if ((SPLIT && EB == 4) || NORM) {
           // elementwise on the swizzled tile: the layout is preserved
           const float4* a4 = reinterpret_cast<const float4*>(st + L.a);
           float4* lo4 = reinterpret_cast<float4*>(st + L.alo);
           for (int i = et; i < TC_A_BYTES / 16; i += 128) {
             float4 v = a4[i];
-            if (NORM) {
-              sq.add(v.x);
-              sq.add(v.y);
-              sq.add(v.z);
-              sq.add(v.w);
+            if (EB == 4) {
+              if (NORM) {
+                sq.add(v.x);
+                sq.add(v.y);
+                sq.add(v.z);
+                sq.add(v.w);
+              }
+              if (SPLIT) lo4[i] = make_float4(tf32_lo(v.x), tf32_lo(v.y), tf32_lo(v.z), tf32_lo(v.w));
+            } else {
+              const uint32_t w[4] = {__float_as_uint(v.x), __float_as_uint(v.y), __float_as_uint(v.z),
+                                     __float_as_uint(v.w)};
+#pragma unroll
+              for (int t = 0; t < 4; ++t) {
+                sq.add(__uint_as_float(w[t] << 16));
+                sq.add(__uint_as_float(w[t] & 0xffff0000u));
+              }
             }
-            if (SPLIT) lo4[i] = make_float4(tf32_lo(v.x), tf32_lo(v.y), tf32_lo(v.z), tf32_lo(v.w));
           }
         }
-        if (SPLIT) {
+        if (SPLIT && EB == 4) {
           const float4* b4 = reinterpret_cast<const float4*>(st + L.b);
           float4* blo4 = reinterpret_cast<float4*>(st + L.blo);
           for (int i = et; i < (int)(b_bytes / 16); i += 128) {
@@ -413,25 +484,26 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 2-D FP32 tensor map, dims {inner, outer}, row stride in elements, box {32, box_outer},
-// 128 B swizzle (or none).
+// 2-D tensor map of FP32 (eb = 4) or BF16 (eb = 2) elements, dims {inner, outer}, row
+// stride in elements, box {128 bytes of elements, box_outer}, 128 B swizzle (or none).
 bool make_map(CUtensorMap* m, const void* ptr, uint64_t inner, uint64_t outer, uint64_t ld, uint32_t box_outer,
-              bool swizzle = true) {
+              bool swizzle = true, int eb = 4) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {inner, outer};
-  cuuint64_t strides[1] = {ld * 4};
-  cuuint32_t box[2] = {32, box_outer};
+  cuuint64_t strides[1] = {ld * (uint64_t)eb};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / eb), box_outer};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+  CUresult r = fn(m, eb == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                  const_cast<void*>(ptr), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
-int pick_stages(int nmma, int mode, bool split) {
-  const int stage = (int)StageLayout(mode, split, nmma).bytes;
+int pick_stages(int nmma, int mode, bool split, int eb = 4) {
+  const int stage = (int)StageLayout(mode, split, nmma, eb).bytes;
   // two CTAs per SM when the pipeline fits in ~110 KB, else one deeper pipeline
   int s = (110 * 1024 - 2048) / stage;
   if (s < 3) s = std::min(6, (210 * 1024 - 2048) / stage);
@@ -439,8 +511,8 @@ int pick_stages(int nmma, int mode, bool split) {
 }
 
 // The deepest pipeline that still lets `per_sm` CTAs share an SM.
-int stages_for(int nmma, int mode, bool split, int per_sm) {
-  const int stage = (int)StageLayout(mode, split, nmma).bytes;
+int stages_for(int nmma, int mode, bool split, int per_sm, int eb = 4) {
+  const int stage = (int)StageLayout(mode, split, nmma, eb).bytes;
   const int budget = (per_sm >= 2 ? 110 : 210) * 1024 - 2048;
   return std::max(2, std::min(budget / stage, 8));
 }
@@ -462,8 +534,8 @@ int sm_count() {
 // about 1 KB reserved per CTA).
 int ctas_per_sm(size_t smem) { return std::max(1, (int)((228 * 1024) / (smem + 1024))); }
 
-size_t smem_bytes(int nmma, int stages, int mode, bool split) {
-  return 1024 + (size_t)stages * StageLayout(mode, split, nmma).bytes + (3 * (size_t)stages + 1) * 8 + 16;
+size_t smem_bytes(int nmma, int stages, int mode, bool split, int eb = 4) {
+  return 1024 + (size_t)stages * StageLayout(mode, split, nmma, eb).bytes + (3 * (size_t)stages + 1) * 8 + 16;
 }
 
 int tmem_cols_for(int nmma) {
@@ -483,20 +555,22 @@ bool tc_available(int device) {
   return p.major == 10 && p.minor == 3 && encode_fn() != nullptr;
 }
 
-bool tc_shape_ok(const void* G, int64_t ldg, int l) {
-  return ((uintptr_t)G % 16 == 0) && (ldg % 4 == 0) && l >= 1 && l <= 256;
+bool tc_shape_ok(const void* G, int64_t ldg, int l, int eb) {
+  return ((uintptr_t)G % 16 == 0) && ((ldg * eb) % 16 == 0) && l >= 1 && l <= 256;
 }
 
 int tc_gx_ctas(int64_t M) { return (int)cdiv(M, TC_BM); }
 
-template <int MODE, bool NORM, bool SPLIT>
+template <int MODE, bool NORM, bool SPLIT, int EB = 4>
 void launch_tc(dim3 grid, size_t smem, cudaStream_t st, const CUtensorMap& ma, const CUtensorMap& mb, float* out,
                int64_t ldo, int64_t out_rows, int ncols, int nmma, int64_t kdim, int64_t rps, int64_t split_stride,
-               int stages, double* gnorm_part, DevStatus* st_dev) {
+               int stages, double* gnorm_part, DevStatus* st_dev, const CUtensorMap* mb2 = nullptr) {
   // a fixed cap (pipelines are sized to stay below it): concurrent launches must not lower it
-  cudaFuncSetAttribute(tc_gemm_kernel<MODE, NORM, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-  tc_gemm_kernel<MODE, NORM, SPLIT><<<grid, 192, smem, st>>>(ma, mb, out, ldo, out_rows, ncols, nmma, tmem_cols_for(nmma),
-                                                             kdim, rps, split_stride, stages, gnorm_part, st_dev);
+  cudaFuncSetAttribute(tc_gemm_kernel<MODE, NORM, SPLIT, EB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       220 * 1024);
+  tc_gemm_kernel<MODE, NORM, SPLIT, EB><<<grid, 192, smem, st>>>(ma, mb, mb2 ? *mb2 : mb, out, ldo, out_rows, ncols,
+                                                                 nmma, tmem_cols_for(nmma), kdim, rps, split_stride,
+                                                                 stages, gnorm_part, st_dev);
 }
 
 cudaError_t tc_gemm_gx(int prec, const float* G, int64_t ldg, int64_t M, int64_t n, const float* Xt, int64_t ldx,
@@ -540,7 +614,9 @@ int tc_gtq_splits(int64_t M, int64_t n, int prec) {
 }
 
 int64_t tc_gtq_part_elems(int64_t M, int64_t n, int l) {
-  return (int64_t)std::max(tc_gtq_splits(M, n, 1), tc_gtq_splits(M, n, 3)) * n * round_up(l, 4);
+  const int s = std::max(std::max(tc_gtq_splits(M, n, 1), tc_gtq_splits(M, n, 3)),
+                         std::max(tc_gtq_splits_bf16(M, n, false), tc_gtq_splits_bf16(M, n, true)));
+  return (int64_t)s * n * round_up(l, 4);
 }
 
 cudaError_t tc_gemm_gtq(int prec, const float* G, int64_t ldg, int64_t M, int64_t n, const float* Qt, int64_t ldq,
@@ -565,6 +641,81 @@ cudaError_t tc_gemm_gtq(int prec, const float* G, int64_t ldg, int64_t M, int64_
     launch_tc<1, false, true>(grid, smem, st, ma, mb, part, lp, n, l, nmma, M, rps, n * lp, stages, nullptr, st_dev);
   else
     launch_tc<1, false, false>(grid, smem, st, ma, mb, part, lp, n, l, nmma, M, rps, n * lp, stages, nullptr, st_dev);
+  return launched();
+}
+
+// ---------------------------------------------------------------------------
+// BF16 data (kind::f16).  G is BF16 row-major; the B operands come K-major as
+// BF16 hi (+ lo) halves written by split_bf16.
+// ---------------------------------------------------------------------------
+cudaError_t tc_gemm_gx_bf16(const void* G, int64_t ldg, int64_t M, int64_t n, const void* Xh, const void* Xl,
+                            int64_t ldx, int l, float* Y, int64_t ldy, double* gnorm_part, DevStatus* st_dev,
+                            cudaStream_t st) {
+  const bool split = Xl != nullptr;
+  const int nmma = (int)round_up(l, 16);
+  CUtensorMap ma, mb, mb2;
+  if (!make_map(&ma, G, (uint64_t)n, (uint64_t)M, (uint64_t)ldg, TC_BM, true, 2)) return cudaErrorInvalidValue;
+  if (!make_map(&mb, Xh, (uint64_t)n, (uint64_t)nmma, (uint64_t)ldx, (uint32_t)nmma, true, 2))
+    return cudaErrorInvalidValue;
+  if (split && !make_map(&mb2, Xl, (uint64_t)n, (uint64_t)nmma, (uint64_t)ldx, (uint32_t)nmma, true, 2))
+    return cudaErrorInvalidValue;
+  const int64_t tiles = cdiv(M, TC_BM);
+  int stages = pick_stages(nmma, 0, split, 2);
+  if (tiles > (int64_t)sm_count() * ctas_per_sm(smem_bytes(nmma, stages, 0, split, 2)))
+    stages = stages_for(nmma, 0, split, 2, 2);
+  const size_t smem = smem_bytes(nmma, stages, 0, split, 2);
+  const dim3 grid((unsigned)tiles);
+  const CUtensorMap* m2 = split ? &mb2 : nullptr;
+  if (gnorm_part) {
+    if (split)
+      launch_tc<0, true, true, 2>(grid, smem, st, ma, mb, Y, ldy, M, l, nmma, n, 0, 0, stages, gnorm_part, st_dev, m2);
+    else
+      launch_tc<0, true, false, 2>(grid, smem, st, ma, mb, Y, ldy, M, l, nmma, n, 0, 0, stages, gnorm_part, st_dev);
+  } else {
+    if (split)
+      launch_tc<0, false, true, 2>(grid, smem, st, ma, mb, Y, ldy, M, l, nmma, n, 0, 0, stages, nullptr, st_dev, m2);
+    else
+      launch_tc<0, false, false, 2>(grid, smem, st, ma, mb, Y, ldy, M, l, nmma, n, 0, 0, stages, nullptr, st_dev);
+  }
+  return launched();
+}
+
+int tc_gtq_splits_bf16(int64_t M, int64_t n, bool split) {
+  const int64_t ctiles = cdiv(n, TC_BM);
+  const int nmma = 64;
+  const int per_sm = ctas_per_sm(smem_bytes(nmma, pick_stages(nmma, 1, split, 2), 1, split, 2));
+  int64_t s = std::max<int64_t>(1, (int64_t)sm_count() * per_sm / ctiles);
+  s = std::min<int64_t>(s, std::max<int64_t>(1, cdiv(M, 2 * 64)));
+  return (int)s;
+}
+
+cudaError_t tc_gemm_gtq_bf16(const void* G, int64_t ldg, int64_t M, int64_t n, const void* Qh, const void* Ql,
+                             int64_t ldq, int l, float* part, int64_t lp, int* splits_out, int64_t max_part_elems,
+                             DevStatus* st_dev, cudaStream_t st) {
+  const bool split = Ql != nullptr;
+  const int nmma = (int)round_up(l, 16);
+  int splits = tc_gtq_splits_bf16(M, n, split);
+  while (splits > 1 && (int64_t)splits * n * lp > max_part_elems) --splits;
+  // split boundaries on stage (64-row) boundaries so that no tile crosses into the next split
+  const int64_t rps = round_up(cdiv(M, splits), 64);
+  splits = (int)cdiv(M, rps);
+  *splits_out = splits;
+  CUtensorMap ma, mb, mb2;
+  // G tiles are staged unswizzled (64 rows x 64 columns per box) and transposed in shared memory
+  if (!make_map(&ma, G, (uint64_t)n, (uint64_t)M, (uint64_t)ldg, 64, false, 2)) return cudaErrorInvalidValue;
+  if (!make_map(&mb, Qh, (uint64_t)M, (uint64_t)nmma, (uint64_t)ldq, (uint32_t)nmma, true, 2))
+    return cudaErrorInvalidValue;
+  if (split && !make_map(&mb2, Ql, (uint64_t)M, (uint64_t)nmma, (uint64_t)ldq, (uint32_t)nmma, true, 2))
+    return cudaErrorInvalidValue;
+  const int stages = pick_stages(nmma, 1, split, 2);
+  const size_t smem = smem_bytes(nmma, stages, 1, split, 2);
+  const dim3 grid((unsigned)cdiv(n, TC_BM), (unsigned)splits);
+  if (split)
+    launch_tc<1, false, true, 2>(grid, smem, st, ma, mb, part, lp, n, l, nmma, M, rps, n * lp, stages, nullptr,
+                                 st_dev, &mb2);
+  else
+    launch_tc<1, false, false, 2>(grid, smem, st, ma, mb, part, lp, n, l, nmma, M, rps, n * lp, stages, nullptr,
+                                  st_dev);
   return launched();
 }
 

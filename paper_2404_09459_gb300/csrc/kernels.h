@@ -21,6 +21,14 @@ template <typename T>
 cudaError_t launch_gaussian_kmajor(T* Xt, int64_t ldx, int64_t n, int l, int lrows, uint64_t seed,
                                    uint32_t pair, uint32_t side, uint32_t stream, cudaStream_t st);
 
+// The same in BF16 (FP64 Gaussian -> nearest FP32 -> nearest BF16), ld a multiple of 8.
+cudaError_t launch_gaussian_kmajor_bf16(void* Xt, int64_t ldx, int64_t n, int l, int lrows, uint64_t seed,
+                                        uint32_t pair, uint32_t side, uint32_t stream, cudaStream_t st);
+// BF16 halves of an FP32 matrix (rows x cols, ld lds): hi = bf16(x), lo = bf16(x - hi)
+// (lo may be nullptr), ld ldd.  Columns cols.. of the destination are not written.
+cudaError_t launch_split_bf16(const float* src, int64_t lds, int64_t rows, int64_t cols, void* hi, void* lo,
+                              int64_t ldd, cudaStream_t st);
+
 // ---- sketch / power products on CUDA cores (Algorithm 1 line "G Omega") ----
 // Y (M x l, ld ldy) = G (M x n) * X where X is given K-major as Xt (l x n, ld ldx).
 // If gnorm_part != nullptr, CTA b of column-tile 0 writes sum of G^2 over its
@@ -75,6 +83,8 @@ template <typename T, typename TC>
 cudaError_t launch_apply_rinv(const T* Y, int64_t ldy, int64_t M, int l, const TC* Rinv, T* Q, int64_t ldq,
                               int transpose_out, double* part, cudaStream_t st);
 int apply_ctas(int64_t M, int l, int elem_bytes);
+// Whether the CholeskyQR passes take the Gram of Q from Q = Y R^{-1} (partials per row tile).
+bool apply_fuses_gram(int l);
 int64_t apply_rows_per_cta(int l, int elem_bytes);
 
 // ---- small FP64 dense kernels (compressed-pair GSVD) -----------------------

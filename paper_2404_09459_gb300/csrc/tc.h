@@ -9,8 +9,9 @@ namespace gsvdr {
 
 // True when the device is sm_103 and the driver exposes tensor-map encoding.
 bool tc_available(int device);
-// TMA addressing constraints: 16-byte aligned base, row stride a multiple of 16 bytes, l <= 256.
-bool tc_shape_ok(const void* G, int64_t ldg, int l);
+// TMA addressing constraints: 16-byte aligned base, row stride (ldg elements of eb bytes)
+// a multiple of 16 bytes, l <= 256.
+bool tc_shape_ok(const void* G, int64_t ldg, int l, int eb = 4);
 
 // Y (M x l, ld ldy) = G (M x n, ld ldg) X with X given K-major as Xt (round_up(l,16) x n,
 // ld ldx, rows l.. zero).  TF32 operands, FP32 accumulation.  gnorm_part (or nullptr):
@@ -26,5 +27,18 @@ cudaError_t tc_gemm_gtq(int prec, const float* G, int64_t ldg, int64_t M, int64_
                         int l, float* part, int64_t lp, int* splits, int64_t max_part_elems, DevStatus* st_dev,
                         cudaStream_t st);
 int64_t tc_gtq_part_elems(int64_t M, int64_t n, int l);
+
+// BF16 data (G row-major BF16, ld a multiple of 8): Y = G X with X given K-major as BF16
+// halves Xh (+ Xl, or nullptr for one product), each round_up(l,16) x n with ld ldx
+// (a multiple of 8), padding rows zero.  FP32 accumulation.
+cudaError_t tc_gemm_gx_bf16(const void* G, int64_t ldg, int64_t M, int64_t n, const void* Xh, const void* Xl,
+                            int64_t ldx, int l, float* Y, int64_t ldy, double* gnorm_part, DevStatus* st_dev,
+                            cudaStream_t st);
+// Split-K partials of Z = G^T Q with Q^T given as BF16 halves Qh (+ Ql), round_up(l,16) x M
+// with ld ldq (a multiple of 8), padding rows zero.
+cudaError_t tc_gemm_gtq_bf16(const void* G, int64_t ldg, int64_t M, int64_t n, const void* Qh, const void* Ql,
+                             int64_t ldq, int l, float* part, int64_t lp, int* splits, int64_t max_part_elems,
+                             DevStatus* st_dev, cudaStream_t st);
+int tc_gtq_splits_bf16(int64_t M, int64_t n, bool split);
 
 }  // namespace gsvdr

@@ -34,6 +34,11 @@ def _dev(a, prec):
     return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dt)
 
 
+def _bf16(a):
+    """FP64 host matrix -> BF16 CPU tensor (to nearest FP32, then to nearest BF16)."""
+    return torch.from_numpy(np.ascontiguousarray(a)).to(torch.float32).to(torch.bfloat16)
+
+
 def _solve(prec, G1, G2, spec, **kw):
     with P.Context(prec, **kw) as ctx:
         out = ctx.solve(_dev(G1, prec), _dev(G2, prec), spec.kk, spec.oversample, spec.q, spec.seed)
@@ -243,13 +248,23 @@ def test_adaptive_cap_reached_reports_tol_miss():
         assert ctx.basis_cols() == (256, 256)
 
 
-@pytest.mark.parametrize("prec", ["bf16"])
-def test_unbuilt_precisions_report_unsupported(prec):
+def test_bf16_adaptive_refused_and_unaligned_inputs_staged():
     spec = PairSpec(m=200, p=200, n=64, r=5, sigma=1e-6, k=5, oversample=3, q=1, seed=4)
     G1, G2, _, _ = planted_pair(spec)
-    with pytest.raises(P.GsvdRandError) as e:
-        _solve(prec, G1, G2, spec)
+    g1, g2 = _bf16(G1).cuda(), _bf16(G2).cuda()
+    with P.Context("bf16", adaptive=1, block_b=8, tol=1e-2) as ctx:
+        with pytest.raises(P.GsvdRandError) as e:
+            ctx.solve(g1, g2, 5, 0, 0, 1)
     assert e.value.name == "UNSUPPORTED"
+    wide = torch.zeros(200, 68, dtype=torch.bfloat16, device="cuda")
+    wide[:, 1:65] = g1
+    with P.Context("bf16") as ctx:
+        ref = ctx.solve(g1, g2, 5, 3, 1, 4)
+        # base 2 bytes past a 16-byte boundary: staged into the workspace, same result
+        got = ctx.solve(wide[:, 1:65], g2, 5, 3, 1, 4)
+        host = ctx.solve(_bf16(G1), _bf16(G2), 5, 3, 1, 4)
+    torch.testing.assert_close(got["alpha"], ref["alpha"], rtol=0, atol=0)
+    np.testing.assert_array_equal(host["alpha"], ref["alpha"].cpu().numpy())
 
 
 def test_tf32x3_large_pair_full_size():
@@ -260,6 +275,66 @@ def test_tf32x3_large_pair_full_size():
                       PAIR_TF32_LARGE.seed)
     _check("tf32x3", G1, G2, PAIR_TF32_LARGE, ref=ref)
     _check("tf32", G1, G2, PAIR_TF32_LARGE, ref=ref)
+
+
+# ---------------------------------------------------------------- BF16 mode
+# G is stored in BF16.  Parity is against the oracle run on the same BF16-rounded G
+# (converted exactly to FP64) with the same BF16-rounded Omega, so that the error is
+# that of the GPU arithmetic: FP32 accumulation, FP32 CholeskyQR data and the power
+# steps' BF16 operands.  The storage error itself (vs the unrounded FP64 pair) is
+# the precision stress the bench reports; it is not a parity quantity.
+
+def _check_bf16(G1, G2, spec, flags=0, gate=None):
+    b1, b2 = _bf16(G1), _bf16(G2)
+    ref = O.rand_gsvd(b1.double().numpy(), b2.double().numpy(), spec.kk, spec.oversample, spec.q, spec.seed,
+                      omega_round="bf16")
+    with P.Context("bf16", flags=flags) as ctx:
+        out = ctx.solve(b1.cuda(), b2.cuda(), spec.kk, spec.oversample, spec.q, spec.seed)
+    a, b = out["alpha"].cpu().numpy(), out["beta"].cpu().numpy()
+    gate = spec.kk if gate is None else gate
+    e = O.gsv_error(ref["alpha"], ref["beta"], a, b)[:gate]
+    dth = np.abs(np.arctan2(a, b) - np.arctan2(ref["alpha"], ref["beta"]))[:gate]
+    assert np.max(e) <= TOL["bf16"], (np.max(e), e)
+    assert np.max(dth) <= 1e-4
+    assert np.all(np.diff(a) <= 0) and np.all(np.diff(b) >= 0)
+    return a, b, ref
+
+
+BF16_CASES = [
+    PairSpec(m=3000, p=2500, n=300, r=12, alpha="uniform", decay="exp10", sigma=1e-6, k=12, oversample=8, q=1,
+             seed=1),  # n not a multiple of 8: G staged into an aligned copy
+    PairSpec(m=4100, p=3000, n=520, r=20, alpha="uniform", decay="exp10", sigma=1e-6, k=20, oversample=10, q=2,
+             seed=2),  # ragged row tiles and K tail
+    PairSpec(m=2000, p=1800, n=200, r=20, alpha="uniform", decay="exp10", sigma=1e-6, k=20, oversample=10, q=0,
+             seed=3),  # projection straight after the sketch
+]
+
+
+@pytest.mark.parametrize("flags", [0, P.FLAG_BF16_SPLIT_POWER])
+@pytest.mark.parametrize("spec", BF16_CASES, ids=lambda s: f"m{s.m}n{s.n}q{s.q}")
+def test_bf16_matches_oracle_on_rounded_inputs(spec, flags):
+    G1, G2, _, _ = planted_pair(spec)
+    _check_bf16(G1, G2, spec, flags)
+
+
+def test_bf16_slow_decay_gated_above_noise_floor():
+    """Slow decay d_i = i^-1.5 with sigma = 1e-5: pairs whose scale is below ten times the
+    noise floor sigma (sqrt(M) + sqrt(n)) are noise-determined and not gated."""
+    spec = PairSpec(m=5000, p=4000, n=777, r=50, alpha="uniform", decay="pow15", sigma=1e-5, k=50,
+                    oversample=14, q=2, seed=4)
+    G1, G2, _, _ = planted_pair(spec)
+    floor = spec.sigma * (np.sqrt(spec.m) + np.sqrt(spec.n))
+    gate = int(np.sum(np.arange(1, spec.r + 1) ** -1.5 >= 10 * floor))
+    assert gate >= 15
+    for flags in (0, P.FLAG_BF16_SPLIT_POWER):
+        _check_bf16(G1, G2, spec, flags, gate=gate)
+
+
+def test_bf16_large_pair_full_size():
+    """The single large pair (m = 20000, p = 15000, n = 1000, k = 50, os = 10, q = 2) stored in BF16."""
+    G1, G2, _, _ = planted_pair(PAIR_TF32_LARGE)
+    _check_bf16(G1, G2, PAIR_TF32_LARGE)
+    _check_bf16(G1, G2, PAIR_TF32_LARGE, P.FLAG_BF16_SPLIT_POWER)
 
 
 # ---------------------------------------------------------------- metrics

@@ -379,3 +379,53 @@ def test_power_iterations_keep_small_directions():
     G2 = (V * (b * d)) @ Ot.T
     out = O.rand_gsvd(G1, G2, r, 4, 4, seed=3)
     assert np.max(O.gsv_error(a, b, out["alpha"], out["beta"])) < 1e-5
+
+
+def test_round_bf16_ties_carries_and_bound():
+    # bfloat16 keeps 8 significand bits: spacing 2^-7 on [1, 2).  Values are written
+    # from that spacing, not from the rounding formula.
+    x = np.array([1.0, -2.5, 0.0, 1 + 2.0 ** -8, 1 + 3 * 2.0 ** -8, 1 + 2.0 ** -8 + 2.0 ** -20,
+                  2 - 2.0 ** -9, -(1 + 2.0 ** -8 + 2.0 ** -20), 3.0 * 2.0 ** -130])
+    want = np.array([1.0, -2.5, 0.0, 1.0, 1 + 2.0 ** -6, 1 + 2.0 ** -7,
+                     2.0, -(1 + 2.0 ** -7), 3.0 * 2.0 ** -130], dtype=np.float32)
+    np.testing.assert_array_equal(O.round_bf16(x), want)
+    # FP32 first: 1 + 2^-8 + 2^-30 rounds to 1 + 2^-8 in FP32 (a tie in BF16, to even 1.0),
+    # while rounding the FP64 value directly to 8 bits would give 1 + 2^-7
+    assert O.round_bf16(np.array([1 + 2.0 ** -8 + 2.0 ** -30]))[0] == np.float32(1.0)
+    rng = _rng(21)
+    v = rng.standard_normal(20000) * 10.0 ** rng.uniform(-6, 6, 20000)
+    r = O.round_bf16(v).astype(np.float64)
+    f = v.astype(np.float32).astype(np.float64)
+    assert np.all(np.abs(r - f) <= 2.0 ** -8 * np.abs(f))  # unit roundoff of an 8-bit significand
+    # the 256 representable significands of a binade map to themselves
+    grid = 1.0 + np.arange(128) / 128.0
+    np.testing.assert_array_equal(O.round_bf16(grid), grid.astype(np.float32))
+
+
+def test_round_bf16_matches_torch_conversion():
+    torch = pytest.importorskip("torch")
+    rng = _rng(22)
+    v = (rng.standard_normal(50000) * 10.0 ** rng.uniform(-3, 3, 50000)).astype(np.float32)
+    ref = torch.from_numpy(v).to(torch.bfloat16).to(torch.float32).numpy()
+    np.testing.assert_array_equal(O.round_bf16(v), ref)
+
+
+def test_bf16_omega_sketch_stays_a_range_finder():
+    # The rounded test matrix is a 2^-8 relative perturbation of a Gaussian one: on an
+    # exact-rank pair the randomized GSVs still equal the planted ones.
+    rng = _rng(23)
+    m, p, n, r = 120, 100, 40, 6
+    a = np.sort(rng.uniform(0.1, 0.9, r))[::-1]
+    b = np.sqrt(1 - a ** 2)
+    U, _ = np.linalg.qr(rng.standard_normal((m, r)))
+    V, _ = np.linalg.qr(rng.standard_normal((p, r)))
+    Ot, _ = np.linalg.qr(rng.standard_normal((n, r)))
+    d = np.linspace(1, 0.3, r)
+    G1 = (U * (a * d)) @ Ot.T
+    G2 = (V * (b * d)) @ Ot.T
+    plain = O.rand_gsvd(G1, G2, r, 4, 0, seed=5)
+    rounded = O.rand_gsvd(G1, G2, r, 4, 0, seed=5, omega_round="bf16")
+    assert np.max(O.gsv_error(a, b, rounded["alpha"], rounded["beta"])) < 1e-12
+    assert np.max(O.gsv_error(plain["alpha"], plain["beta"], rounded["alpha"], rounded["beta"])) < 1e-12
+    with pytest.raises(ValueError):
+        O.rand_gsvd(G1, G2, r, 4, 0, seed=5, omega_round="fp8")
