@@ -337,6 +337,31 @@ def test_bf16_large_pair_full_size():
     _check_bf16(G1, G2, PAIR_TF32_LARGE, P.FLAG_BF16_SPLIT_POWER)
 
 
+def test_bf16_stress_full_size():
+    """The precision-stress pair at full size (m = 120000, p = 80000, n = 4000, r = 200, d_i = i^-1.5,
+    sigma = 1e-4, k = 200, os = 20, q = 3; l = 220, L = 440) with G in BF16 and split power steps.
+    The noise floor sigma (sqrt(m) + sqrt(n)) = 0.041 buries all but the leading pairs: those with
+    d_i >= 10x the floor are held to 1e-4, the noise-determined rest is checked for validity."""
+    from paper_2404_09459_gb300.inputs import PAIR_BF16_STRESS as S, planted_pair_torch
+    G1, G2, _, _ = planted_pair_torch(S)
+    b1, b2 = G1.to(torch.bfloat16), G2.to(torch.bfloat16)
+    del G1, G2
+    with P.Context("bf16", flags=P.FLAG_BF16_SPLIT_POWER) as ctx:
+        out = ctx.solve(b1, b2, S.kk, S.oversample, S.q, S.seed)
+    a, b = out["alpha"].cpu().numpy(), out["beta"].cpu().numpy()
+    ref = O.rand_gsvd(b1.double().cpu().numpy(), b2.double().cpu().numpy(), S.kk, S.oversample, S.q, S.seed,
+                      omega_round="bf16")
+    floor = S.sigma * (np.sqrt(S.m) + np.sqrt(S.n))
+    gate = int(np.sum(np.arange(1, S.r + 1) ** -1.5 >= 10 * floor))
+    e = O.gsv_error(ref["alpha"], ref["beta"], a, b)
+    assert gate >= 1 and np.max(e[:gate]) <= TOL["bf16"], e[:gate]
+    assert np.all(np.diff(a) <= 0) and np.all(np.diff(b) >= 0)
+    assert np.all((a >= 0) & (a <= 1 + 1e-12) & (b >= 0) & (b <= 1 + 1e-12))
+    assert np.max(np.abs(a ** 2 + b ** 2 - 1)) < 1e-10
+    # noise-determined pairs: reported, held only to ten times the target (measured max 1.3e-4)
+    assert np.max(e) <= 10 * TOL["bf16"], (np.max(e), np.median(e))
+
+
 # ---------------------------------------------------------------- metrics
 
 @pytest.mark.parametrize("pad_to_n,pad_mode", [(0, 0), (40, 0), (40, 1)])
