@@ -95,8 +95,12 @@ typedef struct {
                         Section 2 cancels below about sqrt(u) of ||G||_F (u of the basis'
                         orthonormality): tolerances below ~1e-7 (FP64) or ~1e-3 (FP32 data)
                         may not be certified and end in GSVD_RAND_ERR_TOL_MISS */
-  int use_learned;   /* reserved: learned (k, q) proposal */
-  const char *mlp_path; /* reserved */
+  int use_learned;   /* 1: k and q of the fixed-rank solve from the learned proposal (probe
+                        features -> network), with Algorithm 1 (block_b, tol) as the fallback
+                        when the proposed bases miss tol; k of gsvd_rand_solve is then the
+                        output capacity and the cap on the proposed k */
+  const char *mlp_path; /* network file for use_learned (see gsvd_rand_mlp_load), or NULL
+                           to set the network later with gsvd_rand_mlp_set */
   int flags;         /* GSVD_RAND_FLAG_* */
 } gsvd_rand_config;
 
@@ -104,6 +108,8 @@ typedef struct {
 #define GSVD_RAND_FLAG_CHOL_FP64 1 /* mixed precisions: run the CholeskyQR factorisations in FP64 */
 #define GSVD_RAND_FLAG_PROFILE 2   /* time each stage with CUDA events on the solve stream */
 #define GSVD_RAND_FLAG_BF16_SPLIT_POWER 4 /* BF16: power-step operands as hi + lo (two products) */
+#define GSVD_RAND_FLAG_BASIS_ONLY 8 /* bases and residuals only: no compressed-pair GSVD, alpha and
+                                       beta may be NULL and are not written, *r_out = 0 */
 
 /* Stages timed under GSVD_RAND_FLAG_PROFILE. */
 #define GSVD_RAND_STAGE_SKETCH 0 /* Y = G X products (sketch and power steps) */
@@ -254,6 +260,76 @@ int gsvd_rand_basis_cols(gsvd_rand_t h, int *l1, int *l2);
 
 /* Total number of CUDA kernels this library has launched in this process. */
 uint64_t gsvd_rand_launch_count(void);
+
+/* ---------------------------------------------------------------------------
+ * Learned (k, q) proposal.  The paper has no learned component: Algorithm 1
+ * (Section 2) chooses the basis size adaptively, the fixed-rank method of
+ * Section 3 needs k (and the power steps q) given.  A small classifier maps
+ * cheap probe features of the pair to (k bucket, q) for the fixed-rank solve;
+ * Algorithm 1 labels its training pairs and takes over whenever the proposed
+ * bases miss the tolerance.
+ *
+ * Features (64 floats, side 1 then side 2): with Omega_p the n x 16 Gaussian
+ * of Philox stream GSVD_RAND_STREAM_PROBE, Y = G Omega_p and Z = G^T Y,
+ * log10 of the eigenvalues of Y^T Y / (16 ||G||_F^2) and of
+ * Z^T Z / (16 ||G||_F^4), each descending, clipped to [-12, 1].
+ * Network: x^ = (x - mean) / std, h1 = relu(x^ W1 + b1), h2 = relu(h1 W2 + b2),
+ * z = h2 W3 + b3; W1 64 x 128, W2 128 x 128, W3 128 x 37, row-major; params is
+ * W1 | b1 | W2 | b2 | W3 | b3 (GSVD_RAND_MLP_PARAMS floats), norm is mean | std
+ * (128 floats).  z[0:32]: k bucket b (k = 4b+1 .. 4b+4; the solve takes 4b+4 of the
+ * smallest bucket whose cumulative softmax probability reaches GSVD_RAND_MLP_KQUANTILE),
+ * z[32:37]: q = 0..4 (the solve takes the argmax).  Loss: softmax cross-entropy of each head, batch means,
+ * summed.  All network pointers are device pointers unless stated.
+ * --------------------------------------------------------------------------- */
+#define GSVD_RAND_MLP_IN 64
+#define GSVD_RAND_MLP_HID 128
+#define GSVD_RAND_MLP_KCLS 32
+#define GSVD_RAND_MLP_QCLS 5
+#define GSVD_RAND_MLP_KBUCKET 4
+#define GSVD_RAND_MLP_PROBE 16
+#define GSVD_RAND_MLP_KQUANTILE 0.9 /* the learned solve takes the smallest k bucket whose
+                                       cumulative softmax probability reaches this level */
+#define GSVD_RAND_MLP_PARAMS (64 * 128 + 128 + 128 * 128 + 128 + 128 * 37 + 37)
+
+/* The 64 probe features of {G1, G2} (layouts and precision as gsvd_rand_solve;
+ * the Philox pair word is 0).  feats: 64 floats, device or host.  Errors: ARG
+ * (m, p or n below 16), OOM, CUDA. */
+int gsvd_rand_probe_features(gsvd_rand_t h, const void *G1, int64_t m, int64_t ld1, const void *G2, int64_t p,
+                             int64_t ld2, int64_t n, uint64_t seed, float *feats);
+
+/* Logits (B x 37) of the features X (B x 64); bf16 != 0 rounds the weight matrices
+ * to BF16 (the inference form), else FP32.  Errors: ARG, OOM, CUDA. */
+int gsvd_rand_mlp_forward(gsvd_rand_t h, const float *params, const float *norm, const float *X, int B, int bf16,
+                          float *logits);
+
+/* Mean loss (*loss, one device float) and its gradient (GSVD_RAND_MLP_PARAMS floats)
+ * over the batch X (B x 64) with labels yk (k bucket) and yq (q), FP32.
+ * Errors: ARG, OOM, CUDA. */
+int gsvd_rand_mlp_loss_grad(gsvd_rand_t h, const float *params, const float *norm, const float *X, const int *yk,
+                            const int *yq, int B, float *grad, float *loss);
+
+/* One Adam step t >= 1 (Kingma & Ba 2015, bias-corrected) on params with moments m, v.
+ * Errors: ARG, CUDA. */
+int gsvd_rand_mlp_adam(gsvd_rand_t h, float *params, float *m, float *v, const float *grad, int t, float lr,
+                       float beta1, float beta2, float eps);
+
+/* `steps` minibatch steps of B rows each: step i uses rows order[i B .. i B + B - 1] of
+ * X, yk, yq, then Adam (beta 0.9, 0.999, eps 1e-8) at step t0 + i + 1; loss_hist[i]
+ * receives its loss.  Errors: ARG, OOM, CUDA. */
+int gsvd_rand_mlp_train(gsvd_rand_t h, float *params, float *m, float *v, const float *norm, const float *X,
+                        const int *yk, const int *yq, const int *order, int steps, int B, int t0, float lr,
+                        float *loss_hist);
+
+/* The network of the learned solve: params and norm copied from device or host
+ * memory.  Errors: ARG, OOM, CUDA. */
+int gsvd_rand_mlp_set(gsvd_rand_t h, const float *params, const float *norm);
+
+/* The network from a file: "GSVDMLP1", int32 {64, 128, 32, 5}, then norm (128
+ * floats) and params, little-endian.  Errors: ARG (missing or malformed file). */
+int gsvd_rand_mlp_load(gsvd_rand_t h, const char *path);
+
+/* k and q of the last learned solve, and fallback = 1 when Algorithm 1 solved it. */
+int gsvd_rand_last_plan(gsvd_rand_t h, int *k, int *q, int *fallback);
 
 #ifdef __cplusplus
 }

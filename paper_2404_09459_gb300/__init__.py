@@ -23,10 +23,15 @@ FLAG_CHOL_FP64 = 1
 EXPORTS = ("gsvd_rand_config_init", "gsvd_rand_create", "gsvd_rand_destroy", "gsvd_rand_last_error",
            "gsvd_rand_solve", "gsvd_rand_metrics", "gsvd_rand_gaussian", "gsvd_rand_philox",
            "gsvd_rand_profile_get", "gsvd_rand_profile_reset", "gsvd_rand_launch_count",
-           "gsvd_rand_metrics_noalloc", "gsvd_rand_basis_cols", "gsvd_rand_solve_batched")
+           "gsvd_rand_metrics_noalloc", "gsvd_rand_basis_cols", "gsvd_rand_solve_batched",
+           "gsvd_rand_probe_features", "gsvd_rand_mlp_forward", "gsvd_rand_mlp_loss_grad", "gsvd_rand_mlp_adam",
+           "gsvd_rand_mlp_train", "gsvd_rand_mlp_set", "gsvd_rand_mlp_load", "gsvd_rand_last_plan")
 NOALLOC_MAX_N = 32768
 FLAG_PROFILE = 2
 FLAG_BF16_SPLIT_POWER = 4
+FLAG_BASIS_ONLY = 8
+MLP_IN, MLP_HID, MLP_KCLS, MLP_QCLS, MLP_KBUCKET = 64, 128, 32, 5, 4
+MLP_PARAMS = 64 * 128 + 128 + 128 * 128 + 128 + 128 * 37 + 37
 STAGES = ("sketch", "gtq", "orth", "small", "small_gram", "small_jacobi", "small_refine", "small_cs")
 
 
@@ -80,6 +85,15 @@ def load_library(path: str | None = None):
     lib.gsvd_rand_metrics_noalloc.argtypes = [i32, vp, vp, vp, i32, i32, i32, vp, vp, vp, vp, vp]
     lib.gsvd_rand_basis_cols.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     lib.gsvd_rand_solve_batched.argtypes = [vp, i32, C.POINTER(_Pair), i32]
+    f32 = C.c_float
+    lib.gsvd_rand_probe_features.argtypes = [vp, vp, i64, i64, vp, i64, i64, i64, u64, vp]
+    lib.gsvd_rand_mlp_forward.argtypes = [vp, vp, vp, vp, i32, i32, vp]
+    lib.gsvd_rand_mlp_loss_grad.argtypes = [vp, vp, vp, vp, vp, vp, i32, vp, vp]
+    lib.gsvd_rand_mlp_adam.argtypes = [vp, vp, vp, vp, vp, i32, f32, f32, f32, f32]
+    lib.gsvd_rand_mlp_train.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, i32, i32, i32, f32, vp]
+    lib.gsvd_rand_mlp_set.argtypes = [vp, vp, vp]
+    lib.gsvd_rand_mlp_load.argtypes = [vp, C.c_char_p]
+    lib.gsvd_rand_last_plan.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
     for name in EXPORTS:
         if name not in ("gsvd_rand_last_error", "gsvd_rand_launch_count"):
             getattr(lib, name).restype = C.c_int
@@ -121,7 +135,8 @@ class Context:
     """
 
     def __init__(self, prec: str = "tf32", device: int = 0, stream=None, flags: int = 0,
-                 adaptive: bool = False, block_b: int = 100, tol: float = 1e-4):
+                 adaptive: bool = False, block_b: int = 100, tol: float = 1e-4, use_learned: bool = False,
+                 mlp_path: str | None = None):
         self.lib = load_library()
         cfg = _Config()
         self.lib.gsvd_rand_config_init(C.byref(cfg))
@@ -131,6 +146,10 @@ class Context:
         cfg.adaptive = 1 if adaptive else 0
         cfg.block_b = block_b
         cfg.tol = tol
+        cfg.use_learned = 1 if use_learned else 0
+        self._learned = bool(use_learned)
+        self._mlp_path = mlp_path.encode() if mlp_path else None
+        cfg.mlp_path = self._mlp_path
         if stream is None:
             try:
                 import torch
@@ -235,6 +254,104 @@ class Context:
         del keep
         self._check(rc)
         return res
+
+    # ------------------------------------------------------------------ learned proposal
+    def probe_features(self, G1, G2, seed: int = 0):
+        """The 64 probe features (float32; a CUDA tensor for CUDA inputs, numpy otherwise)."""
+        want = self._g_dtype()
+        p1, m, n1, ld1, dev1, k1 = _mat_ptr(G1, want)
+        p2, p, n2, ld2, dev2, k2 = _mat_ptr(G2, want)
+        if n1 != n2:
+            raise ValueError("G1 and G2 must have the same number of columns")
+        if dev1:
+            import torch
+            out = torch.empty(MLP_IN, dtype=torch.float32, device=f"cuda:{self.device}")
+            ptr = out.data_ptr()
+        else:
+            import numpy as np
+            out = np.empty(MLP_IN, dtype=np.float32)
+            ptr = out.ctypes.data
+        self._check(self.lib.gsvd_rand_probe_features(self.h, p1, m, ld1, p2, p, ld2, n1, seed, ptr))
+        return out
+
+    @staticmethod
+    def _dev_ptr(t, dtype, numel=None):
+        import torch
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+            raise TypeError(f"expected a contiguous CUDA {dtype} tensor")
+        if numel is not None and t.numel() < numel:
+            raise ValueError(f"tensor holds {t.numel()} elements, {numel} needed")
+        return t.data_ptr()
+
+    def mlp_forward(self, params, norm, X, bf16: bool = False):
+        """Logits (B x 37) of X (B x 64); all CUDA float32 tensors."""
+        import torch
+        B = X.shape[0]
+        z = torch.empty(B, MLP_KCLS + MLP_QCLS, dtype=torch.float32, device=X.device)
+        f = torch.float32
+        self._check(self.lib.gsvd_rand_mlp_forward(self.h, self._dev_ptr(params, f, MLP_PARAMS),
+                                                   self._dev_ptr(norm, f, 2 * MLP_IN), self._dev_ptr(X, f, B * MLP_IN),
+                                                   B, 1 if bf16 else 0, z.data_ptr()))
+        return z
+
+    def mlp_loss_grad(self, params, norm, X, yk, yq):
+        """(loss, grad) of the batch; labels int32 CUDA tensors."""
+        import torch
+        B = X.shape[0]
+        f, i = torch.float32, torch.int32
+        grad = torch.empty(MLP_PARAMS, dtype=f, device=X.device)
+        loss = torch.empty(1, dtype=f, device=X.device)
+        self._check(self.lib.gsvd_rand_mlp_loss_grad(self.h, self._dev_ptr(params, f, MLP_PARAMS),
+                                                     self._dev_ptr(norm, f, 2 * MLP_IN),
+                                                     self._dev_ptr(X, f, B * MLP_IN), self._dev_ptr(yk, i, B),
+                                                     self._dev_ptr(yq, i, B), B, grad.data_ptr(), loss.data_ptr()))
+        return float(loss.item()), grad
+
+    def mlp_adam(self, params, m, v, grad, t: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8):
+        import torch
+        f = torch.float32
+        self._check(self.lib.gsvd_rand_mlp_adam(self.h, self._dev_ptr(params, f, MLP_PARAMS),
+                                                self._dev_ptr(m, f, MLP_PARAMS), self._dev_ptr(v, f, MLP_PARAMS),
+                                                self._dev_ptr(grad, f, MLP_PARAMS), t, lr, beta1, beta2, eps))
+
+    def mlp_train(self, params, m, v, norm, X, yk, yq, order, B: int, t0: int, lr: float):
+        """len(order) // B Adam steps over the row indices `order` (int32 CUDA); returns the
+        per-step losses (CUDA float32)."""
+        import torch
+        f, i = torch.float32, torch.int32
+        N = X.shape[0]
+        steps = order.numel() // B
+        hist = torch.empty(max(steps, 1), dtype=f, device=X.device)
+        self._check(self.lib.gsvd_rand_mlp_train(
+            self.h, self._dev_ptr(params, f, MLP_PARAMS), self._dev_ptr(m, f, MLP_PARAMS),
+            self._dev_ptr(v, f, MLP_PARAMS), self._dev_ptr(norm, f, 2 * MLP_IN), self._dev_ptr(X, f, N * MLP_IN),
+            self._dev_ptr(yk, i, N), self._dev_ptr(yq, i, N), self._dev_ptr(order, i, steps * B), steps, B, t0,
+            lr, hist.data_ptr()))
+        return hist[:steps]
+
+    def mlp_set(self, params, norm):
+        """The network of the learned solve (float32, CUDA tensors or numpy)."""
+        import numpy as np
+        keep = []
+
+        def ptr(a):
+            if _is_torch(a):
+                a = a.contiguous()
+                keep.append(a)
+                return a.data_ptr()
+            a = np.ascontiguousarray(a, dtype=np.float32)
+            keep.append(a)
+            return a.ctypes.data
+        self._check(self.lib.gsvd_rand_mlp_set(self.h, ptr(params), ptr(norm)))
+
+    def mlp_load(self, path: str):
+        self._check(self.lib.gsvd_rand_mlp_load(self.h, path.encode()))
+
+    def last_plan(self):
+        """(k, q, fallback) of the last learned solve."""
+        k, q, fb = C.c_int(0), C.c_int(0), C.c_int(0)
+        self._check(self.lib.gsvd_rand_last_plan(self.h, C.byref(k), C.byref(q), C.byref(fb)))
+        return k.value, q.value, bool(fb.value)
 
     def basis_cols(self):
         """Columns (l1, l2) of the two bases of the last solve."""

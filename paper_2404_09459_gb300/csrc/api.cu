@@ -12,6 +12,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -38,6 +39,10 @@ struct gsvd_rand_ctx {
   uint32_t pair_word = 0;        // Philox counter word 'pair' of the current solve
   bool owns_stream = false;      // stream created by the library (batched workers)
   std::vector<gsvd_rand_ctx*> workers;  // sub-contexts of gsvd_rand_solve_batched
+  // learned proposal: network (params | norm), then features, logits and scratch of one pair
+  float* mlp_dev = nullptr;
+  bool mlp_ready = false;
+  int last_plan[3] = {0, 0, 0};  // k, q and whether Algorithm 1 took over, of the last learned solve
   // optional per-stage CUDA-event timing (GSVD_RAND_FLAG_PROFILE)
   struct Rec {
     int stage;
@@ -585,17 +590,22 @@ int solve_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, const voi
   int bblk = (int)cdiv(n * pl.l, 256);
   CU(launch_residual(sb0.gnorm, gct0, sb0.bnorm, bblk, small.resid, st));
   CU(launch_residual(sb1.gnorm, gct1, sb1.bnorm, bblk, small.resid + 1, st));
-  {
+  const bool basis_only = (h->cfg.flags & GSVD_RAND_FLAG_BASIS_ONLY) != 0;
+  if (!basis_only) {
     ProfScope ps(h, GSVD_RAND_STAGE_SMALL);
     if ((rc = small_gsvd<T>(h, st, st_dev, S, pl.ldn, pl.l, pl.L, n, k, small))) return rc;
   }
 
   // results
-  bool ad = is_device_ptr(alpha), bd = is_device_ptr(beta);
   CU(cudaMemcpyAsync(h->st_host, st_dev, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
   CU(cudaMemcpyAsync(h->res_host, small.resid, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
-  CU(cudaMemcpyAsync(alpha, small.alpha, k * sizeof(double), ad ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
-  CU(cudaMemcpyAsync(beta, small.beta, k * sizeof(double), bd ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  if (!basis_only) {
+    bool ad = is_device_ptr(alpha), bd = is_device_ptr(beta);
+    CU(cudaMemcpyAsync(alpha, small.alpha, k * sizeof(double), ad ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       st));
+    CU(cudaMemcpyAsync(beta, small.beta, k * sizeof(double), bd ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       st));
+  }
   CU(cudaStreamSynchronize(st));
   prof_collect(h);
   if (h->st_host->code) {
@@ -606,10 +616,11 @@ int solve_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, const voi
   }
   h->last_cols[0] = h->last_cols[1] = pl.l;
   if (r_out) {
+    const int r = basis_only ? 0 : k;
     if (is_device_ptr(r_out))
-      CU(cudaMemcpy(r_out, &k, sizeof(int), cudaMemcpyHostToDevice));
+      CU(cudaMemcpy(r_out, &r, sizeof(int), cudaMemcpyHostToDevice));
     else
-      *r_out = k;
+      *r_out = r;
   }
   if (resid_out) {
     if (is_device_ptr(resid_out))
@@ -795,8 +806,9 @@ int solve_adaptive_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, 
     cols[s] = c;
     if (est[s] > tol) miss = true;
   }
+  const bool basis_only = (h->cfg.flags & GSVD_RAND_FLAG_BASIS_ONLY) != 0;
   // B_s = Q_s^T G_s as rows of S, then the compressed-pair GSVD
-  for (int s = 0; s < 2; ++s) {
+  for (int s = 0; s < 2 && !basis_only; ++s) {
     ProfScope ps(h, GSVD_RAND_STAGE_GTQ);
     const int splits = gemm_gtq_splits(Ms[s], n, cols[s], part_elems);
     CU((launch_gemm_gtq_simt<T, T>(Gs[s], ldg[s], Ms[s], n, w.Q[s], capp, cols[s], w.part, capp, splits, st)));
@@ -805,15 +817,19 @@ int solve_adaptive_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, 
                                    1, nullptr, &blocks, st)));
   }
   const int L = cols[0] + cols[1];
-  const int r = std::min(k, L);
-  {
+  const int r = basis_only ? 0 : std::min(k, L);
+  if (!basis_only) {
     ProfScope ps(h, GSVD_RAND_STAGE_SMALL);
     if ((rc = small_gsvd<T>(h, st, w.st_dev, w.S, ldn, cols[0], L, n, r, small))) return rc;
   }
-  const bool ad = is_device_ptr(alpha), bd = is_device_ptr(beta);
   CU(cudaMemcpyAsync(h->st_host, w.st_dev, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
-  CU(cudaMemcpyAsync(alpha, small.alpha, r * sizeof(double), ad ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
-  CU(cudaMemcpyAsync(beta, small.beta, r * sizeof(double), bd ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  if (!basis_only) {
+    const bool ad = is_device_ptr(alpha), bd = is_device_ptr(beta);
+    CU(cudaMemcpyAsync(alpha, small.alpha, r * sizeof(double), ad ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       st));
+    CU(cudaMemcpyAsync(beta, small.beta, r * sizeof(double), bd ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       st));
+  }
   CU(cudaStreamSynchronize(st));
   prof_collect(h);
   if (h->st_host->code) {
@@ -839,6 +855,190 @@ int solve_adaptive_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, 
                 cols[0], cols[1], est[0], est[1], tol);
   h->err.clear();
   return GSVD_RAND_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Probe features of the learned proposal: per side Y = G Omega_p (n x 16,
+// Philox stream GSVD_RAND_STREAM_PROBE), Z = G^T Y, the 16 x 16 Grams of Y and
+// Z, and the features from their eigenvalues (k_mlp.cu).  The products and
+// Grams are the solve's own kernels at l = 16.
+// ---------------------------------------------------------------------------
+template <typename T, typename TC>
+int probe_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, const void* G2v, int64_t p, int64_t ld2,
+            int64_t n, uint64_t seed, float* feats) {
+  constexpr int PL = 16;
+  cudaStream_t st = h->stream;
+  const int prec = h->cfg.prec;
+  const bool bf16 = prec == GSVD_RAND_BF16;
+  bool use_tc = prec == GSVD_RAND_TF32 || prec == GSVD_RAND_TF32X3 || bf16;
+  if (use_tc && !h->tc_ok) return fail(h, GSVD_RAND_ERR_UNSUPPORTED, "tensor-core path unavailable on this device");
+  const int eg = bf16 ? 2 : (int)sizeof(T);
+  const int64_t lds = round_up(n, 16 / eg);
+  const bool dev1 = is_device_ptr(G1v), dev2 = is_device_ptr(G2v);
+  const bool ok1 = dev1 && tc_shape_ok(G1v, ld1, PL, eg), ok2 = dev2 && tc_shape_ok(G2v, ld2, PL, eg);
+  const bool d1 = dev1 && (ok1 || !bf16), d2 = dev2 && (ok2 || !bf16);
+  if (use_tc && !bf16 && ((dev1 && !ok1) || (dev2 && !ok2))) use_tc = false;
+  Plan pl;
+  pl.M[0] = m;
+  pl.M[1] = p;
+  pl.n = n;
+  pl.l = PL;
+  pl.L = 2 * PL;
+  pl.lp = PL;
+  pl.lx = PL;
+  pl.ldx = round_up(n, 32);
+  pl.ldn = round_up(n, 4);
+  const int64_t maxM = std::max(m, p);
+  pl.part_elems = std::max<int64_t>((int64_t)gemm_gtq_splits(maxM, n, PL, 1ll << 62) * n * PL,
+                                    use_tc ? tc_gtq_part_elems(maxM, n, PL) : 0);
+  pl.part_elems = std::min<int64_t>(pl.part_elems, std::max<int64_t>(16ll << 20, n * PL));
+  int64_t rpc;
+  const int gch = gram_chunks(std::max(maxM, n), PL, &rpc);
+  pl.gpart_elems = (int64_t)std::max(gch, apply_ctas(std::max(maxM, n), PL, (int)sizeof(T))) * PL * PL;
+  Bump sizer;
+  sizer.take<DevStatus>(1);
+  if (!d1) sizer.take<unsigned char>(m * lds * eg);
+  if (!d2) sizer.take<unsigned char>(p * lds * eg);
+  int rc = ensure_ws(h, sizer.off + side_bytes<T>(pl, 0, use_tc, bf16) + side_bytes<T>(pl, 1, use_tc, bf16) + 4096);
+  if (rc) return rc;
+  Bump bp;
+  bp.base = h->ws;
+  DevStatus* st_dev = bp.take<DevStatus>(1);
+  const void* Gs[2] = {G1v, G2v};
+  int64_t ldg[2] = {ld1, ld2};
+  const int64_t Ms[2] = {m, p};
+  const bool dv[2] = {dev1, dev2}, inplace[2] = {d1, d2};
+  for (int s = 0; s < 2; ++s)
+    if (!inplace[s]) {
+      unsigned char* g = bp.take<unsigned char>(Ms[s] * lds * eg);
+      CU(cudaMemcpy2DAsync(g, lds * eg, Gs[s], ldg[s] * eg, n * eg, Ms[s],
+                           dv[s] ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+      Gs[s] = g;
+      ldg[s] = lds;
+    }
+  SideBufs<T> sb[2] = {side_take<T>(bp, pl, 0, use_tc, bf16), side_take<T>(bp, pl, 1, use_tc, bf16)};
+  CU(cudaMemsetAsync(st_dev, 0, sizeof(DevStatus), st));
+  Solver<T, TC> sv{h, st, st_dev, prec, use_tc, nullptr, bf16, true};
+  for (int s = 0; s < 2; ++s) {
+    SideBufs<T>& b = sb[s];
+    const int64_t M = Ms[s];
+    if (bf16)
+      CU(launch_gaussian_kmajor_bf16(b.Xh, pl.ldx, n, PL, PL, seed, h->pair_word, (uint32_t)s,
+                                     GSVD_RAND_STREAM_PROBE, st));
+    else
+      CU(launch_gaussian_kmajor<T>(b.Xt, pl.ldx, n, PL, PL, seed, h->pair_word, (uint32_t)s, GSVD_RAND_STREAM_PROBE,
+                                   st));
+    if ((rc = sv.gx(Gs[s], ldg[s], M, pl, b, b.gnorm))) return rc;
+    if (use_tc) {
+      CU(launch_transpose<T>(b.Y, pl.lp, M, PL, b.Q, round_up(M, 4), st));
+      if (bf16 && (rc = sv.split_q(b, M, pl, true))) return rc;
+    } else {
+      b.Q = b.Y;  // the CUDA-core G^T Q reads Q row-major with ld lp
+    }
+    if ((rc = sv.gtq(Gs[s], ldg[s], M, pl, b, b.Z, pl.lp, 0, nullptr, true))) return rc;
+    int64_t rpy, rpz;
+    const int cy = gram_chunks(M, PL, &rpy), cz = gram_chunks(n, PL, &rpz);
+    CU(launch_gram_partial<T>(b.Y, pl.lp, M, PL, b.gpart, cy, rpy, st));
+    CU(launch_gram_reduce(b.gpart, cy, PL, b.W, st));
+    CU(launch_gram_partial<T>(b.Z, pl.lp, n, PL, b.gpart, cz, rpz, st));
+    CU(launch_gram_reduce(b.gpart, cz, PL, (double*)b.R, st));
+    const int gct = use_tc ? tc_gx_ctas(M) : gemm_gx_simt_ctas(M);
+    CU(launch_probe_features(b.W, (const double*)b.R, b.gnorm, gct, feats + 32 * s, st));
+  }
+  CU(cudaMemcpyAsync(h->st_host, st_dev, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  if (h->st_host->code)
+    return fail(h, h->st_host->code, "device status %d at stage %d (index %d)", h->st_host->code, h->st_host->where,
+                h->st_host->index);
+  return GSVD_RAND_OK;
+}
+
+int probe_dispatch(gsvd_rand_ctx* h, const void* G1, int64_t m, int64_t ld1, const void* G2, int64_t p, int64_t ld2,
+                   int64_t n, uint64_t seed, float* feats_dev) {
+  if (h->cfg.prec == GSVD_RAND_FP64) return probe_t<double, double>(h, G1, m, ld1, G2, p, ld2, n, seed, feats_dev);
+  return probe_t<float, float>(h, G1, m, ld1, G2, p, ld2, n, seed, feats_dev);
+}
+
+// The fixed-rank or adaptive solve (arguments already checked).
+int solve_dispatch(gsvd_rand_ctx* h, bool adaptive, const void* G1, int64_t m, int64_t ld1, const void* G2, int64_t p,
+                   int64_t ld2, int64_t n, int k, int oversample, int q, uint64_t seed, double* alpha, double* beta,
+                   int* r_out, double* resid_out) {
+  const bool f64 = h->cfg.prec == GSVD_RAND_FP64;
+  const bool c64 = (h->cfg.flags & GSVD_RAND_FLAG_CHOL_FP64) != 0;
+  if (adaptive) {
+    if (f64) return solve_adaptive_t<double, double>(h, G1, m, ld1, G2, p, ld2, n, k, seed, alpha, beta, r_out, resid_out);
+    if (c64) return solve_adaptive_t<float, double>(h, G1, m, ld1, G2, p, ld2, n, k, seed, alpha, beta, r_out, resid_out);
+    return solve_adaptive_t<float, float>(h, G1, m, ld1, G2, p, ld2, n, k, seed, alpha, beta, r_out, resid_out);
+  }
+  if (f64) return solve_t<double, double>(h, G1, m, ld1, G2, p, ld2, n, k, oversample, q, seed, alpha, beta, r_out, resid_out);
+  if (c64) return solve_t<float, double>(h, G1, m, ld1, G2, p, ld2, n, k, oversample, q, seed, alpha, beta, r_out, resid_out);
+  return solve_t<float, float>(h, G1, m, ld1, G2, p, ld2, n, k, oversample, q, seed, alpha, beta, r_out, resid_out);
+}
+
+constexpr int MLP_IN = GSVD_RAND_MLP_IN, MLP_OUT = GSVD_RAND_MLP_KCLS + GSVD_RAND_MLP_QCLS;
+constexpr int64_t MLP_NORM = GSVD_RAND_MLP_PARAMS, MLP_FEATS = MLP_NORM + 2 * MLP_IN, MLP_LOGITS = MLP_FEATS + 64,
+                  MLP_SCR = MLP_LOGITS + 64;
+
+int mlp_alloc(gsvd_rand_ctx* h) {
+  if (h->mlp_dev) return GSVD_RAND_OK;
+  const size_t bytes = (size_t)(MLP_SCR + mlp_scratch_floats(16)) * sizeof(float);
+  if (cudaMalloc(&h->mlp_dev, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    h->mlp_dev = nullptr;
+    return fail(h, GSVD_RAND_ERR_OOM, "cannot allocate the network buffer");
+  }
+  return GSVD_RAND_OK;
+}
+
+// Learned proposal: probe features -> network (BF16 weights) -> (k bucket, q) -> the
+// fixed-rank solve with k = min(top of the bucket, capacity); when its cumulated
+// residual exceeds tol on either side, Algorithm 1 (block_b, tol) solves the pair
+// instead and returns the same number of pairs.
+int solve_learned(gsvd_rand_ctx* h, const void* G1, int64_t m, int64_t ld1, const void* G2, int64_t p, int64_t ld2,
+                  int64_t n, int kcap, int oversample, uint64_t seed, double* alpha, double* beta, int* r_out,
+                  double* resid_out) {
+  if (!h->mlp_ready) return fail(h, GSVD_RAND_ERR_ARG, "use_learned without a network (mlp_path or gsvd_rand_mlp_set)");
+  float* F = h->mlp_dev;
+  int rc = probe_dispatch(h, G1, m, ld1, G2, p, ld2, n, seed, F + MLP_FEATS);
+  if (rc) return rc;
+  CU(mlp_forward(F, F + MLP_NORM, F + MLP_FEATS, 1, 1, F + MLP_LOGITS, F + MLP_SCR, h->stream));
+  float z[MLP_OUT];
+  CU(cudaMemcpyAsync(z, F + MLP_LOGITS, sizeof(z), cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  // k: the smallest bucket whose cumulative softmax probability reaches GSVD_RAND_MLP_KQUANTILE
+  // (a miss costs a fallback, an oversized basis only some columns); q: the most probable
+  int kb = 0, q = 0;
+  {
+    double mx = z[0], tot = 0.0, cum = 0.0;
+    for (int j = 1; j < GSVD_RAND_MLP_KCLS; ++j) mx = std::max(mx, (double)z[j]);
+    for (int j = 0; j < GSVD_RAND_MLP_KCLS; ++j) tot += std::exp((double)z[j] - mx);
+    for (kb = 0; kb < GSVD_RAND_MLP_KCLS - 1; ++kb) {
+      cum += std::exp((double)z[kb] - mx) / tot;
+      if (cum >= GSVD_RAND_MLP_KQUANTILE) break;
+    }
+  }
+  for (int j = 1; j < GSVD_RAND_MLP_QCLS; ++j)
+    if (z[GSVD_RAND_MLP_KCLS + q] < z[GSVD_RAND_MLP_KCLS + j]) q = j;
+  const int64_t lmax = std::min<int64_t>(std::min(std::min(m, p), n), h->cfg.prec == GSVD_RAND_FP64 ? 224 : 256);
+  int k = std::min<int64_t>(std::min(GSVD_RAND_MLP_KBUCKET * (kb + 1), kcap), lmax - oversample);
+  k = std::max(k, 1);
+  h->last_plan[0] = k;
+  h->last_plan[1] = q;
+  h->last_plan[2] = 0;
+  double res[2] = {0.0, 0.0};
+  rc = solve_dispatch(h, false, G1, m, ld1, G2, p, ld2, n, k, oversample, q, seed, alpha, beta, r_out, res);
+  if (rc == GSVD_RAND_OK && res[0] <= h->cfg.tol && res[1] <= h->cfg.tol) {
+    if (resid_out) {
+      if (is_device_ptr(resid_out))
+        CU(cudaMemcpy(resid_out, res, sizeof(res), cudaMemcpyHostToDevice));
+      else
+        memcpy(resid_out, res, sizeof(res));
+    }
+    return GSVD_RAND_OK;
+  }
+  if (rc != GSVD_RAND_OK && rc != GSVD_RAND_ERR_BREAKDOWN) return rc;
+  h->last_plan[2] = 1;
+  return solve_dispatch(h, true, G1, m, ld1, G2, p, ld2, n, k, oversample, q, seed, alpha, beta, r_out, resid_out);
 }
 
 }  // namespace
@@ -879,6 +1079,13 @@ int gsvd_rand_create(gsvd_rand_t* out, const gsvd_rand_config* cfg) {
     return GSVD_RAND_ERR_OOM;
   }
   h->tc_ok = tc_available(cfg->device) ? 1 : 0;
+  if (cfg->use_learned && cfg->mlp_path) {
+    const int rc = gsvd_rand_mlp_load(h, cfg->mlp_path);
+    if (rc) {
+      gsvd_rand_destroy(h);
+      return rc;
+    }
+  }
   *out = h;
   return GSVD_RAND_OK;
 }
@@ -892,6 +1099,7 @@ int gsvd_rand_destroy(gsvd_rand_t h) {
   if (h->owns_stream && h->stream) cudaStreamDestroy(h->stream);
   for (auto e : h->evpool) cudaEventDestroy(e);
   if (h->ws) cudaFree(h->ws);
+  if (h->mlp_dev) cudaFree(h->mlp_dev);
   if (h->st_host) cudaFreeHost(h->st_host);
   if (h->res_host) cudaFreeHost(h->res_host);
   delete h;
@@ -929,7 +1137,9 @@ int gsvd_rand_solve(gsvd_rand_t h, const void* G1, int64_t m, int64_t ld1, const
                     int64_t ld2, int64_t n, int k, int oversample, int q, uint64_t seed, double* alpha,
                     double* beta, int* r_out, double* resid_out) {
   if (!h) return GSVD_RAND_ERR_ARG;
-  if (!G1 || !G2 || !alpha || !beta) return fail(h, GSVD_RAND_ERR_ARG, "null pointer argument");
+  const bool basis_only = (h->cfg.flags & GSVD_RAND_FLAG_BASIS_ONLY) != 0;
+  if (!G1 || !G2 || (!basis_only && (!alpha || !beta))) return fail(h, GSVD_RAND_ERR_ARG, "null pointer argument");
+  if (h->cfg.use_learned && basis_only) return fail(h, GSVD_RAND_ERR_ARG, "use_learned solves are not basis-only");
   if (m < 1 || p < 1 || n < 1) return fail(h, GSVD_RAND_ERR_ARG, "empty matrix (m=%lld p=%lld n=%lld)",
                                            (long long)m, (long long)p, (long long)n);
   if (ld1 < n || ld2 < n) return fail(h, GSVD_RAND_ERR_ARG, "leading dimension smaller than n");
@@ -937,7 +1147,9 @@ int gsvd_rand_solve(gsvd_rand_t h, const void* G1, int64_t m, int64_t ld1, const
     return fail(h, GSVD_RAND_ERR_ARG, "need k >= 1, oversample >= 0, 0 <= q <= 16");
   const bool f64 = h->cfg.prec == GSVD_RAND_FP64;
   int64_t l = (int64_t)k + oversample;
-  if (h->cfg.adaptive) {
+  if (h->cfg.use_learned) {
+    if (k > 4 * GSVD_RAND_MLP_KCLS) return fail(h, GSVD_RAND_ERR_ARG, "k = %d exceeds the largest bucket", k);
+  } else if (h->cfg.adaptive) {
     if (k > 512) return fail(h, GSVD_RAND_ERR_ARG, "k = %d exceeds the 512 pairs of two 256-column bases", k);
     if (f64 && h->cfg.block_b > 224) return fail(h, GSVD_RAND_ERR_ARG, "block_b exceeds the FP64 limit 224");
   } else {
@@ -950,17 +1162,11 @@ int gsvd_rand_solve(gsvd_rand_t h, const void* G1, int64_t m, int64_t ld1, const
     return fail(h, GSVD_RAND_ERR_ARG, "dimension too large");
   cudaError_t e = cudaSetDevice(h->cfg.device);
   if (e != cudaSuccess) return fail(h, GSVD_RAND_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
-  if (h->cfg.adaptive) {
-    // Algorithm 1 bases (k = output capacity; oversample and q are not used)
-    if (f64) return solve_adaptive_t<double, double>(h, G1, m, ld1, G2, p, ld2, n, k, seed, alpha, beta, r_out, resid_out);
-    if (h->cfg.flags & GSVD_RAND_FLAG_CHOL_FP64)
-      return solve_adaptive_t<float, double>(h, G1, m, ld1, G2, p, ld2, n, k, seed, alpha, beta, r_out, resid_out);
-    return solve_adaptive_t<float, float>(h, G1, m, ld1, G2, p, ld2, n, k, seed, alpha, beta, r_out, resid_out);
-  }
-  if (f64) return solve_t<double, double>(h, G1, m, ld1, G2, p, ld2, n, k, oversample, q, seed, alpha, beta, r_out, resid_out);
-  if (h->cfg.flags & GSVD_RAND_FLAG_CHOL_FP64)
-    return solve_t<float, double>(h, G1, m, ld1, G2, p, ld2, n, k, oversample, q, seed, alpha, beta, r_out, resid_out);
-  return solve_t<float, float>(h, G1, m, ld1, G2, p, ld2, n, k, oversample, q, seed, alpha, beta, r_out, resid_out);
+  if (h->cfg.use_learned)
+    return solve_learned(h, G1, m, ld1, G2, p, ld2, n, k, oversample, seed, alpha, beta, r_out, resid_out);
+  // adaptive: Algorithm 1 bases (k = output capacity; oversample and q are not used)
+  return solve_dispatch(h, h->cfg.adaptive != 0, G1, m, ld1, G2, p, ld2, n, k, oversample, q, seed, alpha, beta,
+                        r_out, resid_out);
 }
 
 int gsvd_rand_solve_batched(gsvd_rand_t h, int npairs, gsvd_rand_pair* pairs, int workers) {
@@ -987,6 +1193,11 @@ int gsvd_rand_solve_batched(gsvd_rand_t h, int npairs, gsvd_rand_pair* pairs, in
     w->owns_stream = true;
     h->workers.push_back(w);
   }
+  if (h->mlp_ready)
+    for (auto w : h->workers) {
+      const int rc = gsvd_rand_mlp_set(w, h->mlp_dev, h->mlp_dev + MLP_NORM);
+      if (rc) return fail(h, rc, "cannot copy the network to a worker");
+    }
   // largest pairs first, dealt round-robin: a worker's workspace grows on its first pair only
   std::vector<int> order(npairs);
   for (int i = 0; i < npairs; ++i) order[i] = i;
@@ -1094,6 +1305,119 @@ int gsvd_rand_philox(gsvd_rand_t h, uint64_t count, uint64_t seed, uint32_t pair
   CU(launch_philox_words(dst, count, seed, pair, side, stream, st));
   if (!dev) CU(cudaMemcpyAsync(out, dst, count * 16, cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
+  return GSVD_RAND_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Learned (k, q) proposal
+// ---------------------------------------------------------------------------
+int gsvd_rand_probe_features(gsvd_rand_t h, const void* G1, int64_t m, int64_t ld1, const void* G2, int64_t p,
+                             int64_t ld2, int64_t n, uint64_t seed, float* feats) {
+  if (!h) return GSVD_RAND_ERR_ARG;
+  if (!G1 || !G2 || !feats) return fail(h, GSVD_RAND_ERR_ARG, "null pointer argument");
+  if (m < GSVD_RAND_MLP_PROBE || p < GSVD_RAND_MLP_PROBE || n < GSVD_RAND_MLP_PROBE || ld1 < n || ld2 < n)
+    return fail(h, GSVD_RAND_ERR_ARG, "the probe needs m, p, n >= 16 and ld >= n");
+  CU(cudaSetDevice(h->cfg.device));
+  int rc = mlp_alloc(h);
+  if (rc) return rc;
+  float* dst = h->mlp_dev + MLP_FEATS;
+  rc = probe_dispatch(h, G1, m, ld1, G2, p, ld2, n, seed, dst);
+  if (rc) return rc;
+  CU(cudaMemcpyAsync(feats, dst, MLP_IN * sizeof(float), is_device_ptr(feats) ? cudaMemcpyDeviceToDevice
+                                                                               : cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  return GSVD_RAND_OK;
+}
+
+int gsvd_rand_mlp_set(gsvd_rand_t h, const float* params, const float* norm) {
+  if (!h) return GSVD_RAND_ERR_ARG;
+  if (!params || !norm) return fail(h, GSVD_RAND_ERR_ARG, "null pointer argument");
+  CU(cudaSetDevice(h->cfg.device));
+  int rc = mlp_alloc(h);
+  if (rc) return rc;
+  CU(cudaMemcpyAsync(h->mlp_dev, params, GSVD_RAND_MLP_PARAMS * sizeof(float), cudaMemcpyDefault, h->stream));
+  CU(cudaMemcpyAsync(h->mlp_dev + MLP_NORM, norm, 2 * MLP_IN * sizeof(float), cudaMemcpyDefault, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  h->mlp_ready = true;
+  return GSVD_RAND_OK;
+}
+
+int gsvd_rand_mlp_load(gsvd_rand_t h, const char* path) {
+  if (!h) return GSVD_RAND_ERR_ARG;
+  if (!path) return fail(h, GSVD_RAND_ERR_ARG, "null path");
+  FILE* f = fopen(path, "rb");
+  if (!f) return fail(h, GSVD_RAND_ERR_ARG, "cannot open %s", path);
+  char magic[8];
+  int32_t dims[4];
+  std::vector<float> buf(GSVD_RAND_MLP_PARAMS + 2 * MLP_IN);
+  const bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "GSVDMLP1", 8) == 0 && fread(dims, 4, 4, f) == 4 &&
+                  dims[0] == MLP_IN && dims[1] == GSVD_RAND_MLP_HID && dims[2] == GSVD_RAND_MLP_KCLS &&
+                  dims[3] == GSVD_RAND_MLP_QCLS && fread(buf.data(), 4, buf.size(), f) == buf.size();
+  fclose(f);
+  if (!ok) return fail(h, GSVD_RAND_ERR_ARG, "%s is not a 64-128-128-37 network file", path);
+  return gsvd_rand_mlp_set(h, buf.data() + 2 * MLP_IN, buf.data());
+}
+
+int gsvd_rand_mlp_forward(gsvd_rand_t h, const float* params, const float* norm, const float* X, int B, int bf16,
+                          float* logits) {
+  if (!h) return GSVD_RAND_ERR_ARG;
+  if (!params || !norm || !X || !logits || B < 1) return fail(h, GSVD_RAND_ERR_ARG, "bad network arguments");
+  CU(cudaSetDevice(h->cfg.device));
+  int rc = ensure_ws(h, (size_t)mlp_scratch_floats(B) * sizeof(float) + 256);
+  if (rc) return rc;
+  CU(mlp_forward(params, norm, X, B, bf16, logits, (float*)h->ws, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  return GSVD_RAND_OK;
+}
+
+int gsvd_rand_mlp_loss_grad(gsvd_rand_t h, const float* params, const float* norm, const float* X, const int* yk,
+                            const int* yq, int B, float* grad, float* loss) {
+  if (!h) return GSVD_RAND_ERR_ARG;
+  if (!params || !norm || !X || !yk || !yq || !grad || !loss || B < 1)
+    return fail(h, GSVD_RAND_ERR_ARG, "bad network arguments");
+  CU(cudaSetDevice(h->cfg.device));
+  int rc = ensure_ws(h, (size_t)mlp_scratch_floats(B) * sizeof(float) + 256);
+  if (rc) return rc;
+  CU(mlp_loss_grad(params, norm, X, yk, yq, nullptr, B, grad, loss, (float*)h->ws, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  return GSVD_RAND_OK;
+}
+
+int gsvd_rand_mlp_adam(gsvd_rand_t h, float* params, float* m, float* v, const float* grad, int t, float lr,
+                       float beta1, float beta2, float eps) {
+  if (!h) return GSVD_RAND_ERR_ARG;
+  if (!params || !m || !v || !grad || t < 1) return fail(h, GSVD_RAND_ERR_ARG, "bad Adam arguments");
+  CU(cudaSetDevice(h->cfg.device));
+  CU(mlp_adam(params, m, v, grad, t, lr, beta1, beta2, eps, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  return GSVD_RAND_OK;
+}
+
+int gsvd_rand_mlp_train(gsvd_rand_t h, float* params, float* m, float* v, const float* norm, const float* X,
+                        const int* yk, const int* yq, const int* order, int steps, int B, int t0, float lr,
+                        float* loss_hist) {
+  if (!h) return GSVD_RAND_ERR_ARG;
+  if (!params || !m || !v || !norm || !X || !yk || !yq || !order || !loss_hist || steps < 0 || B < 1 || t0 < 0)
+    return fail(h, GSVD_RAND_ERR_ARG, "bad training arguments");
+  CU(cudaSetDevice(h->cfg.device));
+  const size_t scr = (size_t)mlp_scratch_floats(B);
+  int rc = ensure_ws(h, (scr + GSVD_RAND_MLP_PARAMS) * sizeof(float) + 1024);
+  if (rc) return rc;
+  float* s = (float*)h->ws;
+  float* grad = s + ((scr + 63) & ~(size_t)63);
+  for (int i = 0; i < steps; ++i) {
+    CU(mlp_loss_grad(params, norm, X, yk, yq, order + (int64_t)i * B, B, grad, loss_hist + i, s, h->stream));
+    CU(mlp_adam(params, m, v, grad, t0 + i + 1, lr, 0.9f, 0.999f, 1e-8f, h->stream));
+  }
+  CU(cudaStreamSynchronize(h->stream));
+  return GSVD_RAND_OK;
+}
+
+int gsvd_rand_last_plan(gsvd_rand_t h, int* k, int* q, int* fallback) {
+  if (!h) return GSVD_RAND_ERR_ARG;
+  if (k) *k = h->last_plan[0];
+  if (q) *q = h->last_plan[1];
+  if (fallback) *fallback = h->last_plan[2];
   return GSVD_RAND_OK;
 }
 

@@ -117,6 +117,37 @@ cudaError_t launch_gaussian_kmajor_bf16(void* Xt, int64_t ldx, int64_t n, int l,
   return launched();
 }
 
+// Qt[j][i] = Y[i][j] (i < M, j < l): a row-major M x l tile into the K-major layout
+// of the tensor-core operands, 32 x 32 tiles through shared memory.
+template <typename T>
+__global__ void transpose_kernel(const T* __restrict__ Y, int64_t ldy, int64_t M, int l, T* __restrict__ Qt,
+                                 int64_t ldq) {
+  __shared__ T t[32][33];
+  const int64_t i0 = (int64_t)blockIdx.x * 32;
+  const int j0 = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int64_t i = i0 + r;
+    const int j = j0 + threadIdx.x;
+    t[r][threadIdx.x] = (i < M && j < l) ? Y[i * ldy + j] : T(0);
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int j = j0 + r;
+    const int64_t i = i0 + threadIdx.x;
+    if (j < l && i < M) Qt[(int64_t)j * ldq + i] = t[threadIdx.x][r];
+  }
+}
+
+template <typename T>
+cudaError_t launch_transpose(const T* Y, int64_t ldy, int64_t M, int l, T* Qt, int64_t ldq, cudaStream_t st) {
+  if (M <= 0 || l <= 0) return cudaSuccess;
+  transpose_kernel<T><<<dim3((unsigned)cdiv(M, 32), (unsigned)cdiv(l, 32)), dim3(32, 8), 0, st>>>(Y, ldy, M, l, Qt,
+                                                                                               ldq);
+  return launched();
+}
+template cudaError_t launch_transpose<float>(const float*, int64_t, int64_t, int, float*, int64_t, cudaStream_t);
+template cudaError_t launch_transpose<double>(const double*, int64_t, int64_t, int, double*, int64_t, cudaStream_t);
+
 // hi = bf16(x) and lo = bf16(x - hi) (x - hi is exact in FP32), both to nearest even, so
 // that hi + lo carries x to about 2^-16 of its size.  Eight columns per thread.
 __global__ void split_bf16_kernel(const float* __restrict__ src, int64_t lds, int64_t rows, int64_t cols,

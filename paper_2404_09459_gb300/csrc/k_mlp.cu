@@ -1,0 +1,322 @@
+// The learned (k, q) proposal: probe features of a pair and the 64-128-128-37
+// classifier that reads them (training and inference kernels).
+//
+// Features (per side, from the 16-column probe Y = G Omega_p and Z = G^T Y):
+// log10 of the eigenvalues of Y^T Y over 16 ||G||_F^2 and of Z^T Z over
+// 16 ||G||_F^4, descending, clipped to [-12, 1].  The 16 x 16 eigenvalues come
+// from cyclic Jacobi in FP64 (Golub & Van Loan, Alg. 8.5.3), one warp per Gram.
+//
+// Network: x^ = (x - mean) / std; h1 = relu(x^ W1 + b1); h2 = relu(h1 W2 + b2);
+// z = h2 W3 + b3 (W row-major in x out).  Loss: softmax cross-entropy of the
+// k head (z[0:32]) plus that of the q head (z[32:37]), batch means.  Adam
+// (Kingma & Ba 2015) with bias correction.  Every sum runs in a fixed order
+// (no atomics), so training is reproducible bit for bit.
+#include <cuda_bf16.h>
+
+#include "kernels.h"
+
+namespace gsvdr {
+
+namespace {
+
+constexpr int MI = 64, MH = 128, MK = 32, MQ = 5, MO = MK + MQ;
+constexpr int O_W1 = 0, O_B1 = O_W1 + MI * MH, O_W2 = O_B1 + MH, O_B2 = O_W2 + MH * MH, O_W3 = O_B2 + MH,
+              O_B3 = O_W3 + MH * MO, NPAR = O_B3 + MO;
+constexpr float FEAT_LO = -12.f, FEAT_HI = 1.f;
+
+__device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+// ---------------------------------------------------------------- features
+// Cyclic Jacobi on a symmetric 16 x 16 matrix in shared memory (row-major), by one
+// warp: lanes 0..15 own index i of the rotated rows / columns.  Returns the
+// eigenvalues in lane order (lane i < 16 holds lambda_i, unsorted).
+__device__ double jacobi16_warp(double* A) {
+  const int lane = threadIdx.x & 31;
+  const bool act = lane < 16;
+  for (int sweep = 0; sweep < 20; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    if (act)
+      for (int j = 0; j < 16; ++j) {
+        const double v = A[lane * 16 + j];
+        tot += v * v;
+        if (j != lane) off += v * v;
+      }
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    }
+    if (!(off > 1e-30 * tot)) break;
+    for (int p = 0; p < 15; ++p)
+      for (int q = p + 1; q < 16; ++q) {
+        const double apq = A[p * 16 + q];
+        if (apq == 0.0) continue;
+        const double app = A[p * 16 + p], aqq = A[q * 16 + q];
+        const double tau = (aqq - app) / (2.0 * apq);
+        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+        __syncwarp();
+        if (act) {  // rows p, q
+          const double xp = A[p * 16 + lane], xq = A[q * 16 + lane];
+          A[p * 16 + lane] = c * xp - s * xq;
+          A[q * 16 + lane] = s * xp + c * xq;
+        }
+        __syncwarp();
+        if (act) {  // columns p, q
+          const double xp = A[lane * 16 + p], xq = A[lane * 16 + q];
+          A[lane * 16 + p] = c * xp - s * xq;
+          A[lane * 16 + q] = s * xp + c * xq;
+        }
+        __syncwarp();
+      }
+  }
+  return act ? A[lane * 16 + lane] : 0.0;
+}
+
+}  // namespace
+
+// One CTA of 2 warps per side: warp 0 takes W1 = Y^T Y, warp 1 W2 = Z^T Z.
+// gpart: the sketch CTAs' partial sums of G^2 (gcount entries).
+__global__ void probe_features_kernel(const double* __restrict__ W1, const double* __restrict__ W2,
+                                      const double* __restrict__ gpart, int gcount, float* __restrict__ feats) {
+  __shared__ double A[2][256];
+  __shared__ double s_g2;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 0) {
+    double g = 0.0;
+    for (int i = lane; i < gcount; i += 32) g += gpart[i];
+    for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+    if (lane == 0) s_g2 = g;
+  }
+  const double* W = warp == 0 ? W1 : W2;
+  for (int e = lane; e < 256; e += 32) {
+    const int i = e >> 4, j = e & 15;
+    A[warp][e] = W[(i <= j ? i : j) * 16 + (i <= j ? j : i)];  // the Gram partials hold the upper triangle
+  }
+  __syncthreads();
+  const double lam = jacobi16_warp(A[warp]);
+  // rank of lane's eigenvalue in descending order (ties by lane index)
+  int rank = 0;
+  for (int j = 0; j < 16; ++j) {
+    const double o = __shfl_sync(0xffffffffu, lam, j);
+    rank += (o > lam) || (o == lam && j < lane);
+  }
+  if (lane < 16) {
+    const double den = 16.0 * (warp == 0 ? s_g2 : s_g2 * s_g2);
+    const double r = lam > 0.0 && den > 0.0 ? lam / den : 0.0;
+    float f = r > 0.0 ? (float)log10(r) : FEAT_LO;
+    f = fminf(fmaxf(f, FEAT_LO), FEAT_HI);
+    feats[warp * 16 + rank] = f;
+  }
+}
+
+cudaError_t launch_probe_features(const double* W1, const double* W2, const double* gpart, int gcount,
+                                  float* feats, cudaStream_t st) {
+  probe_features_kernel<<<1, 64, 0, st>>>(W1, W2, gpart, gcount, feats);
+  return launched();
+}
+
+// ---------------------------------------------------------------- network
+// Dense layer out[b][j] = act(sum_i in[b][i] W[i][j] + bias[j]) for a block of 16
+// rows; in is either the raw features (normalised here) or a previous layer.
+// rows: optional gather indices into `in` (training minibatches).
+template <bool NORM_IN, bool RELU, bool BF16W>
+__global__ __launch_bounds__(128) void dense_kernel(const float* __restrict__ in, const int* __restrict__ rows,
+                                                    int B, int din, int dout, const float* __restrict__ W,
+                                                    const float* __restrict__ bias, const float* __restrict__ norm,
+                                                    float* __restrict__ pre, float* __restrict__ out) {
+  __shared__ float xs[16][MH + 1];
+  const int b0 = blockIdx.x * 16, tid = threadIdx.x;
+  for (int e = tid; e < 16 * din; e += 128) {
+    const int r = e / din, i = e % din;
+    float v = 0.f;
+    if (b0 + r < B) {
+      const int src = rows ? rows[b0 + r] : b0 + r;
+      v = in[(int64_t)src * din + i];
+      if (NORM_IN) v = (v - norm[i]) / norm[MI + i];
+    }
+    xs[r][i] = v;
+  }
+  __syncthreads();
+  for (int j = tid; j < dout; j += 128) {
+    float acc[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) acc[r] = 0.f;
+    for (int i = 0; i < din; ++i) {
+      float w = W[i * dout + j];
+      if (BF16W) w = bf16_round(w);
+#pragma unroll
+      for (int r = 0; r < 16; ++r) acc[r] = fmaf(xs[r][i], w, acc[r]);
+    }
+    const float bj = bias[j];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      if (b0 + r >= B) break;
+      const float a = acc[r] + bj;
+      if (pre) pre[(int64_t)(b0 + r) * dout + j] = a;
+      out[(int64_t)(b0 + r) * dout + j] = RELU ? fmaxf(a, 0.f) : a;
+    }
+  }
+}
+
+// Softmax cross-entropy of both heads: dz = (softmax - onehot) / B, per-row loss.
+__global__ void softmax_ce_kernel(const float* __restrict__ z, const int* __restrict__ yk,
+                                  const int* __restrict__ yq, const int* __restrict__ rows, int B,
+                                  float* __restrict__ dz, float* __restrict__ row_loss) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const int src = rows ? rows[b] : b;
+  const float* zb = z + (int64_t)b * MO;
+  float* db = dz + (int64_t)b * MO;
+  float loss = 0.f;
+  for (int head = 0; head < 2; ++head) {
+    const int o = head ? MK : 0, c = head ? MQ : MK, y = head ? yq[src] : yk[src];
+    float mx = zb[o];
+    for (int j = 1; j < c; ++j) mx = fmaxf(mx, zb[o + j]);
+    float s = 0.f;
+    for (int j = 0; j < c; ++j) s += expf(zb[o + j] - mx);
+    const float ls = logf(s);
+    loss += -(zb[o + y] - mx - ls);
+    for (int j = 0; j < c; ++j) db[o + j] = (expf(zb[o + j] - mx - ls) - (j == y ? 1.f : 0.f)) / (float)B;
+  }
+  row_loss[b] = loss;
+}
+
+// dW[i][j] = sum_b h[b][i] dz[b][j] and db[j] = sum_b dz[b][j] (thread per (i, j)).
+__global__ void dense_wgrad_kernel(const float* __restrict__ h, int B, int din, int dout,
+                                   const float* __restrict__ dz, float* __restrict__ dW, float* __restrict__ db) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < din * dout) {
+    const int i = e / dout, j = e % dout;
+    float s = 0.f;
+    for (int b = 0; b < B; ++b) s = fmaf(h[(int64_t)b * din + i], dz[(int64_t)b * dout + j], s);
+    dW[e] = s;
+  }
+  if (e < dout) {
+    float s = 0.f;
+    for (int b = 0; b < B; ++b) s += dz[(int64_t)b * dout + e];
+    db[e] = s;
+  }
+}
+
+// dh[b][i] = (sum_j dz[b][j] W[i][j]) * (pre[b][i] > 0).
+__global__ void dense_xgrad_kernel(const float* __restrict__ dz, int B, int din, int dout,
+                                   const float* __restrict__ W, const float* __restrict__ pre,
+                                   float* __restrict__ dh) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= B * din) return;
+  const int b = e / din, i = e % din;
+  float s = 0.f;
+  for (int j = 0; j < dout; ++j) s = fmaf(dz[(int64_t)b * dout + j], W[i * dout + j], s);
+  dh[e] = pre[e] > 0.f ? s : 0.f;
+}
+
+__global__ void sum_rows_kernel(const float* __restrict__ v, int B, float* __restrict__ out) {
+  __shared__ float red[256];
+  float s = 0.f;
+  for (int i = threadIdx.x; i < B; i += 256) s += v[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0] / (float)B;
+}
+
+__global__ void adam_kernel(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
+                            const float* __restrict__ g, int n, float lr, float b1, float b2, float eps, float c1,
+                            float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// ---------------------------------------------------------------- host side
+
+int64_t mlp_param_count() { return NPAR; }
+int64_t mlp_scratch_floats(int B) {
+  // x^ (B x 64), a1, h1, a2, h2 (B x 128 each), z, dz (B x 37), d2, d1 (B x 128), row loss (B)
+  return (int64_t)B * (MI + 4 * MH + 2 * MO + 2 * MH + 1) + 64;
+}
+
+namespace {
+struct MlpScratch {
+  float *x, *a1, *h1, *a2, *h2, *z, *dz, *d2, *d1, *rl;
+  MlpScratch(float* s, int B) {
+    x = s;
+    a1 = x + (int64_t)B * MI;
+    h1 = a1 + (int64_t)B * MH;
+    a2 = h1 + (int64_t)B * MH;
+    h2 = a2 + (int64_t)B * MH;
+    z = h2 + (int64_t)B * MH;
+    dz = z + (int64_t)B * MO;
+    d2 = dz + (int64_t)B * MO;
+    d1 = d2 + (int64_t)B * MH;
+    rl = d1 + (int64_t)B * MH;
+  }
+};
+
+__global__ void gather_norm_kernel(const float* __restrict__ X, const int* __restrict__ rows, int B,
+                                   const float* __restrict__ norm, float* __restrict__ xh) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= B * MI) return;
+  const int b = e / MI, i = e % MI;
+  const int src = rows ? rows[b] : b;
+  xh[e] = (X[(int64_t)src * MI + i] - norm[i]) / norm[MI + i];
+}
+
+cudaError_t forward_into(const float* P, const float* norm, const float* X, const int* rows, int B, bool bf16,
+                         MlpScratch& s, float* logits, cudaStream_t st) {
+  const unsigned g16 = (unsigned)cdiv(B, 16);
+  if (bf16) {
+    dense_kernel<true, true, true><<<g16, 128, 0, st>>>(X, rows, B, MI, MH, P + O_W1, P + O_B1, norm, s.a1, s.h1);
+    dense_kernel<false, true, true><<<g16, 128, 0, st>>>(s.h1, nullptr, B, MH, MH, P + O_W2, P + O_B2, nullptr,
+                                                          s.a2, s.h2);
+    dense_kernel<false, false, true><<<g16, 128, 0, st>>>(s.h2, nullptr, B, MH, MO, P + O_W3, P + O_B3, nullptr,
+                                                           nullptr, logits);
+  } else {
+    dense_kernel<true, true, false><<<g16, 128, 0, st>>>(X, rows, B, MI, MH, P + O_W1, P + O_B1, norm, s.a1, s.h1);
+    dense_kernel<false, true, false><<<g16, 128, 0, st>>>(s.h1, nullptr, B, MH, MH, P + O_W2, P + O_B2, nullptr,
+                                                           s.a2, s.h2);
+    dense_kernel<false, false, false><<<g16, 128, 0, st>>>(s.h2, nullptr, B, MH, MO, P + O_W3, P + O_B3, nullptr,
+                                                            nullptr, logits);
+  }
+  return launched();
+}
+}  // namespace
+
+cudaError_t mlp_forward(const float* P, const float* norm, const float* X, int B, int bf16, float* logits,
+                        float* scratch, cudaStream_t st) {
+  MlpScratch s(scratch, B);
+  return forward_into(P, norm, X, nullptr, B, bf16 != 0, s, logits, st);
+}
+
+cudaError_t mlp_loss_grad(const float* P, const float* norm, const float* X, const int* yk, const int* yq,
+                          const int* rows, int B, float* grad, float* loss, float* scratch, cudaStream_t st) {
+  MlpScratch s(scratch, B);
+  cudaError_t e = forward_into(P, norm, X, rows, B, false, s, s.z, st);
+  if (e != cudaSuccess) return e;
+  gather_norm_kernel<<<(unsigned)cdiv((int64_t)B * MI, 256), 256, 0, st>>>(X, rows, B, norm, s.x);
+  softmax_ce_kernel<<<(unsigned)cdiv(B, 128), 128, 0, st>>>(s.z, yk, yq, rows, B, s.dz, s.rl);
+  sum_rows_kernel<<<1, 256, 0, st>>>(s.rl, B, loss);
+  dense_wgrad_kernel<<<(unsigned)cdiv(MH * MO, 256), 256, 0, st>>>(s.h2, B, MH, MO, s.dz, grad + O_W3, grad + O_B3);
+  dense_xgrad_kernel<<<(unsigned)cdiv((int64_t)B * MH, 256), 256, 0, st>>>(s.dz, B, MH, MO, P + O_W3, s.a2, s.d2);
+  dense_wgrad_kernel<<<(unsigned)cdiv(MH * MH, 256), 256, 0, st>>>(s.h1, B, MH, MH, s.d2, grad + O_W2, grad + O_B2);
+  dense_xgrad_kernel<<<(unsigned)cdiv((int64_t)B * MH, 256), 256, 0, st>>>(s.d2, B, MH, MH, P + O_W2, s.a1, s.d1);
+  dense_wgrad_kernel<<<(unsigned)cdiv(MI * MH, 256), 256, 0, st>>>(s.x, B, MI, MH, s.d1, grad + O_W1, grad + O_B1);
+  return launched();
+}
+
+cudaError_t mlp_adam(float* P, float* m, float* v, const float* grad, int t, float lr, float b1, float b2, float eps,
+                     cudaStream_t st) {
+  const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
+  adam_kernel<<<(unsigned)cdiv(NPAR, 256), 256, 0, st>>>(P, m, v, grad, NPAR, lr, b1, b2, eps, c1, c2);
+  return launched();
+}
+
+}  // namespace gsvdr

@@ -24,6 +24,9 @@ cudaError_t launch_gaussian_kmajor(T* Xt, int64_t ldx, int64_t n, int l, int lro
 // The same in BF16 (FP64 Gaussian -> nearest FP32 -> nearest BF16), ld a multiple of 8.
 cudaError_t launch_gaussian_kmajor_bf16(void* Xt, int64_t ldx, int64_t n, int l, int lrows, uint64_t seed,
                                         uint32_t pair, uint32_t side, uint32_t stream, cudaStream_t st);
+// Qt[j * ldq + i] = Y[i * ldy + j] for i < M, j < l.
+template <typename T>
+cudaError_t launch_transpose(const T* Y, int64_t ldy, int64_t M, int l, T* Qt, int64_t ldq, cudaStream_t st);
 // BF16 halves of an FP32 matrix (rows x cols, ld lds): hi = bf16(x), lo = bf16(x - hi)
 // (lo may be nullptr), ld ldd.  Columns cols.. of the destination are not written.
 cudaError_t launch_split_bf16(const float* src, int64_t lds, int64_t rows, int64_t cols, void* hi, void* lo,
@@ -159,5 +162,22 @@ cudaError_t launch_cs_norms(const double* U1, int l1, const double* U2, int l2, 
 // Residual (cumulated form): resid[s] = sqrt(max(g2 - b2, 0) / g2).
 cudaError_t launch_residual(const double* gpart, int ng, const double* bpart, int nb, double* out,
                             cudaStream_t st);
+
+// ---- learned (k, q) proposal (k_mlp.cu) ----------------------------------------
+// Features of one side from W1 = Y^T Y, W2 = Z^T Z (16 x 16 FP64, full) and the
+// sketch's partial sums of G^2 (gcount entries): 32 floats.
+cudaError_t launch_probe_features(const double* W1, const double* W2, const double* gpart, int gcount,
+                                  float* feats, cudaStream_t st);
+int64_t mlp_param_count();
+int64_t mlp_scratch_floats(int B);
+// Logits (B x 37) of X (B x 64); bf16: weight matrices rounded to BF16.
+cudaError_t mlp_forward(const float* P, const float* norm, const float* X, int B, int bf16, float* logits,
+                        float* scratch, cudaStream_t st);
+// Mean loss (one float) and its gradient (mlp_param_count() floats) over rows
+// `rows` (B indices, or nullptr for 0..B-1) of X, yk, yq.
+cudaError_t mlp_loss_grad(const float* P, const float* norm, const float* X, const int* yk, const int* yq,
+                          const int* rows, int B, float* grad, float* loss, float* scratch, cudaStream_t st);
+cudaError_t mlp_adam(float* P, float* m, float* v, const float* grad, int t, float lr, float b1, float b2, float eps,
+                     cudaStream_t st);
 
 }  // namespace gsvdr

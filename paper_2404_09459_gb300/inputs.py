@@ -152,3 +152,23 @@ def uneven_batch(npairs: int = 256, seed: int = 0, m_range=(2000, 30000), n_rang
         specs.append(PairSpec(m=m, p=p, n=n, r=r, alpha="uniform", decay="exp10", sigma=sigma,
                               k=r, oversample=oversample, q=q, seed=seed * 100003 + i))
     return specs
+
+
+def learned_pairs(npairs: int, seed: int = 0, sigma: float = 1e-9, m_range=(2000, 30000), n_range=(100, 1000),
+                  r_range=(10, 100), oversample: int = 10):
+    """Pairs of the learned-proposal workload: the uneven-batch laws (m, p, n, r, alpha, exp(-i/10)
+    scale) with noise sigma; at the batch's sigma = 1e-6 the noise alone is ~2e-3 of ||G||_F, above
+    the 1e-4 residual tolerance the labels are taken at, so every basis narrower than n would miss."""
+    return uneven_batch(npairs, seed, m_range=m_range, n_range=n_range, r_range=r_range, oversample=oversample,
+                        q=1, sigma=sigma)
+
+
+def mlp_init(seed: int = 0) -> np.ndarray:
+    """Initial parameters of the 64-128-128-37 network (flat float32, W1 | b1 | W2 | b2 | W3 | b3,
+    row-major): He-normal weights N(0, 2 / fan_in), zero biases."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 6412837]))
+    parts = []
+    for fin, fout in ((64, 128), (128, 128), (128, 37)):
+        parts.append(rng.standard_normal(fin * fout) * np.sqrt(2.0 / fin))
+        parts.append(np.zeros(fout))
+    return np.concatenate(parts).astype(np.float32)
