@@ -64,9 +64,10 @@ __device__ __forceinline__ float hash_unit(uint32_t a, uint32_t b) {
 
 }  // namespace
 
+int64_t eig_big_scratch_floats(int N);
 int64_t eig_scratch_floats(int N) {
   const int lda = N | 1;
-  return 2ll * N * lda + 8ll * N + 2ll * N * N;
+  return std::max<int64_t>(2ll * N * lda + 8ll * N + 2ll * N * N, eig_big_scratch_floats(N));
 }
 
 __global__ __launch_bounds__(1024) void eig_f32_kernel(const double* __restrict__ Ain, int N,
@@ -753,6 +754,408 @@ __global__ __launch_bounds__(1024) void eig128_kernel(const double* __restrict__
   for (int e = tid; e < N * N; e += 1024) Xout[e] = (double)Zs[(size_t)(e / N) * lda + e % N];
 }
 
+// ============================================================================
+// The same method for 128 < N <= 512, one CTA of 1024 threads.  The matrix is
+// kept as its packed lower triangle, Ap[i (i + 1) / 2 + j] = A_ij (j <= i), in
+// shared memory while it fits (N <= 318), else in global scratch; the
+// reflector of step k overwrites column k below the diagonal.  The
+// eigenvectors of T, their factorisation pivots and the complement's
+// reflectors live column-major in global scratch (each column contiguous).
+//   1. Householder tridiagonalisation, three barriers per step: the reflector
+//      (one warp), p = beta A v (a warp per row, reading the row part and the
+//      column part of the packed triangle), then the rank-2 update;
+//   2.-3c. as in eig128 (multisection, twisted factorisation, cluster CGS2,
+//      orthonormal complement of the noise columns);
+//   4. X = H_0 ... H_{N-3} Z, a warp per column of Z held in registers.
+// ============================================================================
+namespace {
+constexpr int EB_NMAX = 512;
+constexpr int EB_SMEM_NMAX = 318;  // N (N + 1) / 2 floats = 202,884 bytes: with ~24 KB static, within 227 KB
+__device__ __forceinline__ int pk(int i, int j) { return ((i * (i + 1)) >> 1) + j; }  // j <= i
+}  // namespace
+
+int64_t eig_big_scratch_floats(int N) { return 4ll * N * N + (int64_t)N * (N + 1) / 2 + 64; }
+
+__global__ __launch_bounds__(1024) void eig_big_kernel(const double* __restrict__ Ain, int N,
+                                                       double* __restrict__ Xout, double* __restrict__ lam,
+                                                       float* __restrict__ gscr, float noise_rel, int ap_smem) {
+  extern __shared__ float ebsm[];
+  __shared__ float s_d[EB_NMAX], s_e[EB_NMAX], s_beta[EB_NMAX], s_v[EB_NMAX], s_p[EB_NMAX], s_lam[EB_NMAX];
+  __shared__ float s_cf[EB_NMAX], s_flag[EB_NMAX];
+  __shared__ float2 s_de[EB_NMAX];
+  __shared__ int s_cstart[EB_NMAX], s_prev[EB_NMAX], s_np, s_npan;
+  __shared__ float s_red[32], s_scale, s_bound[2], s_nrm;
+  const int tid = threadIdx.x, w = tid >> 5, t = tid & 31;
+  const size_t NN = (size_t)N * N;
+  float* ZT = gscr;        // N x N column-major: eigenvectors of T, then of A
+  float* LT = ZT + NN;     // N x N column-major: L pivots of eigenvalue j in column j
+  float* UT = LT + NN;     // N x N column-major: U pivots
+  float* VT = UT + NN;     // N x N column-major: the complement's Householder columns
+  float* Ap = ap_smem ? ebsm : VT + NN;
+
+  if (w == 0) {
+    double mx = 0.0;
+    for (int i = t; i < N; i += 32) mx = fmax(mx, fabs(Ain[(int64_t)i * N + i]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (t == 0) s_scale = (float)(mx > 0.0 && isfinite(mx) ? mx : 1.0);
+  }
+  __syncthreads();
+  const float inv = 1.0f / s_scale;
+  for (int i = w; i < N; i += 32)
+    for (int j = t; j <= i; j += 32) Ap[pk(i, j)] = (float)(Ain[(int64_t)i * N + j] * (double)inv);
+  for (int i = tid; i < N; i += 1024) s_v[i] = 0.f;
+  __syncthreads();
+
+  // ---- 1. tridiagonalisation ------------------------------------------------
+  for (int k = 0; k + 2 < N; ++k) {
+    if (w == 0) {
+      const float x0 = Ap[pk(k + 1, k)];
+      float sg = 0.f;
+      for (int i = k + 1 + t; i < N; i += 32) {
+        const float x = Ap[pk(i, k)];
+        sg = fmaf(x, x, sg);
+      }
+      for (int o = 16; o > 0; o >>= 1) sg += __shfl_xor_sync(0xffffffffu, sg, o);
+      const float sig = sqrtf(sg);
+      const float alpha = x0 >= 0.f ? -sig : sig;
+      const bool refl = sig > 0.f && isfinite(sig);
+      const float bk = refl ? (alpha - x0) / alpha : 0.f;  // normalised reflector, v_0 = 1, bk in [1, 2]
+      const float vs = refl ? 1.f / (x0 - alpha) : 0.f;
+      if (refl)
+        for (int i = k + 1 + t; i < N; i += 32) {
+          const float v = i == k + 1 ? 1.f : Ap[pk(i, k)] * vs;
+          s_v[i] = v;
+          Ap[pk(i, k)] = v;  // kept for the back-transformation
+        }
+      if (t == 0) {
+        s_beta[k] = bk;
+        s_e[k] = bk > 0.f ? alpha : x0;
+        s_d[k] = Ap[pk(k, k)];
+        s_v[k] = 0.f;
+      }
+    }
+    __syncthreads();
+    const float bk = s_beta[k];
+    if (bk == 0.f) continue;  // uniform: nothing to annihilate
+    // p = bk A22 v (rows k+1 .. N-1), per-warp share of p^T v
+    float pvw = 0.f;
+    for (int i = k + 1 + w; i < N; i += 32) {
+      float s = 0.f;
+      for (int j = k + 1 + t; j < N; j += 32) s = fmaf(j <= i ? Ap[pk(i, j)] : Ap[pk(j, i)], s_v[j], s);
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      s *= bk;
+      pvw = fmaf(s, s_v[i], pvw);
+      if (t == 0) s_p[i] = s;
+    }
+    if (t == 0) s_red[w] = pvw;
+    __syncthreads();
+    float pv = s_red[t];
+    for (int o = 16; o > 0; o >>= 1) pv += __shfl_xor_sync(0xffffffffu, pv, o);
+    const float kk = 0.5f * bk * pv;
+    // A22 <- A22 - v w^T - w v^T with w = p - kk v, on the packed lower triangle
+    for (int i = k + 1 + w; i < N; i += 32) {
+      const float vi = s_v[i], wi = s_p[i] - kk * vi;
+      float* row = Ap + pk(i, 0);
+      for (int j = k + 1 + t; j <= i; j += 32) {
+        const float vj = s_v[j], wj = s_p[j] - kk * vj;
+        row[j] -= vi * wj + wi * vj;
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (N >= 2) {
+      s_d[N - 2] = Ap[pk(N - 2, N - 2)];
+      s_e[N - 2] = Ap[pk(N - 1, N - 2)];
+      s_beta[N - 2] = 0.f;
+    }
+    s_d[N - 1] = Ap[pk(N - 1, N - 1)];
+    s_beta[N - 1] = 0.f;
+  }
+  __syncthreads();
+
+  // ---- 2. eigenvalues (multisection) and eigenvectors of T ------------------
+  if (w == 0) {
+    float lo = 3.4e38f, hi = -3.4e38f;
+    for (int i = t; i < N; i += 32) {
+      const float rad = (i > 0 ? fabsf(s_e[i - 1]) : 0.f) + (i < N - 1 ? fabsf(s_e[i]) : 0.f);
+      lo = fminf(lo, s_d[i] - rad);
+      hi = fmaxf(hi, s_d[i] + rad);
+      s_de[i] = make_float2(s_d[i], i > 0 ? s_e[i - 1] * s_e[i - 1] : 0.f);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (t == 0) {
+      const float pad = 1e-6f * fmaxf(fabsf(lo), fabsf(hi)) + 1e-30f;
+      s_bound[0] = lo - pad;
+      s_bound[1] = hi + pad;
+    }
+  }
+  __syncthreads();
+  const float tnorm = fmaxf(fabsf(s_bound[0]), fabsf(s_bound[1]));
+  const float pivmin = fmaxf(1e-30f, 1e-12f * tnorm);
+  for (int base = 0; base < N; base += 256) {  // 4 points per eigenvalue, 256 eigenvalues per round
+    const int j0 = base + (tid >> 2), sub = tid & 3;
+    const int j = min(j0, N - 1);
+    float lo = s_bound[0], hi = s_bound[1];
+    for (int it = 0; it < 10; ++it) {
+      const float wd = hi - lo;
+      const float x = lo + wd * (float)(sub + 1) * 0.2f;
+      int cnt = 0;
+      float q = 1.f;
+      for (int i = 0; i < N; ++i) {
+        const float2 de = s_de[i];
+        q = (de.x - x) - (i > 0 ? __fdividef(de.y, q) : 0.f);
+        if (fabsf(q) < pivmin) q = -pivmin;
+        cnt += q < 0.f;
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, cnt > j);
+      const unsigned bits = (bal >> (t & 28)) & 0xfu;
+      const int sl = bits ? __ffs(bits) - 1 : 4;
+      const float nlo = sl == 0 ? lo : lo + wd * (float)sl * 0.2f;
+      const float nhi = sl == 4 ? hi : lo + wd * (float)(sl + 1) * 0.2f;
+      lo = nlo;
+      hi = fmaxf(nhi, nlo);
+    }
+    if (sub == 0 && j0 < N) {
+      const float lm = 0.5f * (lo + hi);
+      s_lam[j0] = lm;
+      lam[j0] = (double)lm * (double)s_scale;
+    }
+  }
+  __syncthreads();
+  for (int j = tid; j < N; j += 1024) {  // eigenvector j of T by the twisted factorisation
+    const float lm = s_lam[j];
+    float* Z = ZT + (size_t)j * N;
+    float* Lc = LT + (size_t)j * N;
+    float* U = UT + (size_t)j * N;
+    float dp = s_d[0] - lm;
+    if (fabsf(dp) < pivmin) dp = -pivmin;
+    Lc[0] = dp;
+    for (int i = 0; i + 1 < N; ++i) {
+      dp = s_d[i + 1] - lm - __fdividef(s_e[i], dp) * s_e[i];
+      if (fabsf(dp) < pivmin) dp = -pivmin;
+      Lc[i + 1] = dp;
+    }
+    float dm = s_d[N - 1] - lm;
+    if (fabsf(dm) < pivmin) dm = -pivmin;
+    U[N - 1] = dm;
+    int kt = N - 1;
+    float best = fabsf(Lc[N - 1] + dm - (s_d[N - 1] - lm));
+    for (int i = N - 2; i >= 0; --i) {
+      dm = s_d[i] - lm - __fdividef(s_e[i], dm) * s_e[i];
+      if (fabsf(dm) < pivmin) dm = -pivmin;
+      U[i] = dm;
+      const float g = fabsf(Lc[i] + dm - (s_d[i] - lm));
+      if (g < best) {
+        best = g;
+        kt = i;
+      }
+    }
+    // z_kt = 1; upward z_i = -(e_i / L_i) z_{i+1}; downward z_{i+1} = -(e_i / U_{i+1}) z_i;
+    // entries are rescaled when they grow past 2^60
+    float zkt = 1.f, z = 1.f;
+    for (int i = kt - 1; i >= 0; --i) {
+      z = -__fdividef(s_e[i], Lc[i]) * z;
+      if (fabsf(z) > 1.15e18f) {
+        for (int u = i + 1; u < kt; ++u) Z[u] *= 8.67e-19f;
+        zkt *= 8.67e-19f;
+        z *= 8.67e-19f;
+      }
+      Z[i] = z;
+    }
+    Z[kt] = zkt;
+    z = zkt;
+    for (int i = kt; i + 1 < N; ++i) {
+      z = -__fdividef(s_e[i], U[i + 1]) * z;
+      if (fabsf(z) > 1.15e18f) {
+        for (int u = 0; u <= i; ++u) Z[u] *= 8.67e-19f;
+        z *= 8.67e-19f;
+      }
+      Z[i + 1] = z;
+    }
+  }
+  __syncthreads();
+  for (int j = w; j < N; j += 32) {  // normalise the columns
+    float* Z = ZT + (size_t)j * N;
+    float s2 = 0.f;
+    for (int i = t; i < N; i += 32) s2 = fmaf(Z[i], Z[i], s2);
+    for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    const bool ok = s2 > 0.f && isfinite(s2);
+    const float sc = ok ? rsqrtf(s2) : 0.f;
+    for (int i = t; i < N; i += 32) Z[i] = ok ? Z[i] * sc : (i == j ? 1.f : 0.f);
+  }
+  // flags: 1 accepted, -1 set aside (dependent), 2 noise (filled with the complement)
+  if (tid == 0) {
+    int st = 0;
+    for (int j = 0; j < N; ++j) {
+      if (j > 0 && !(s_lam[j] - s_lam[j - 1] <= E_CLUSTER * tnorm)) st = j;
+      s_cstart[j] = st;
+      s_flag[j] = (noise_rel > 0.f && fabsf(s_lam[j]) <= noise_rel * tnorm) ? 2.f : 1.f;
+    }
+  }
+  __syncthreads();
+
+  // ---- 3. clustered columns: CGS2 against the accepted columns of the cluster -
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int j = 0; j < N; ++j) {
+      const int cs = pass == 0 ? s_cstart[j] : 0;
+      if (s_flag[j] == 2.f) continue;
+      if (pass == 0 && cs == j) continue;
+      float* Zj = ZT + (size_t)j * N;
+      if (pass == 1) {
+        if (s_flag[j] >= 0.f) continue;
+        for (int i = tid; i < N; i += 1024) Zj[i] = hash_unit((uint32_t)j, (uint32_t)i);
+        __syncthreads();
+      }
+      const int ce = pass == 0 ? j : N;
+      for (int rep = 0; rep < 2; ++rep) {
+        for (int c = cs + w; c < ce; c += 32) {
+          const bool acc = c != j && s_flag[c] == 1.f;
+          float s = 0.f;
+          if (acc) {
+            const float* Zc = ZT + (size_t)c * N;
+            for (int i = t; i < N; i += 32) s = fmaf(Zc[i], Zj[i], s);
+          }
+          for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+          if (t == 0) s_cf[c] = acc ? s : 0.f;
+        }
+        __syncthreads();
+        for (int i0 = 0; i0 < N; i0 += 128) {
+          const int i = i0 + (tid >> 3), part = tid & 7;
+          float s = 0.f;
+          if (i < N)
+            for (int c = cs + part; c < ce; c += 8) s = fmaf(ZT[(size_t)c * N + i], s_cf[c], s);
+          s += __shfl_xor_sync(0xffffffffu, s, 1);
+          s += __shfl_xor_sync(0xffffffffu, s, 2);
+          s += __shfl_xor_sync(0xffffffffu, s, 4);
+          if (i < N && part == 0) Zj[i] -= s;
+        }
+        __syncthreads();
+      }
+      if (w == 0) {
+        float s2 = 0.f;
+        for (int i = t; i < N; i += 32) s2 = fmaf(Zj[i], Zj[i], s2);
+        for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        const float before = pass == 0 ? 1.f : (float)N / 12.f;
+        const bool dep = !(s2 > 1e-6f * before) || !(s2 > 0.f);
+        if (t == 0) {
+          s_nrm = dep && pass == 0 ? 0.f : rsqrtf(s2 > 0.f ? s2 : 1.f);
+          s_flag[j] = dep && pass == 0 ? -1.f : 1.f;
+        }
+      }
+      __syncthreads();
+      const float sc = s_nrm;
+      for (int i = tid; i < N; i += 1024) Zj[i] *= sc;
+      __syncthreads();
+    }
+  }
+
+  // ---- 3c. noise columns: orthonormal complement of the other columns --------
+  if (tid == 0) {
+    int nn = 0, nz = 0;
+    for (int j = 0; j < N; ++j) {
+      if (s_flag[j] == 2.f)
+        s_prev[nz++] = j;
+      else
+        s_cstart[nn++] = j;
+    }
+    s_np = nn;
+    s_npan = nz;
+  }
+  __syncthreads();
+  if (s_npan > 0) {
+    const int nn = s_np, nz = s_npan;
+    for (int c = w; c < nn; c += 32) {
+      const float* src = ZT + (size_t)s_cstart[c] * N;
+      float* dst = VT + (size_t)c * N;
+      for (int i = t; i < N; i += 32) dst[i] = src[i];
+    }
+    __syncthreads();
+    for (int k = 0; k < nn; ++k) {
+      float* Vk = VT + (size_t)k * N;
+      if (w == 0) {
+        float sg = 0.f;
+        for (int i = k + t; i < N; i += 32) sg = fmaf(Vk[i], Vk[i], sg);
+        for (int o = 16; o > 0; o >>= 1) sg += __shfl_xor_sync(0xffffffffu, sg, o);
+        const float x0 = Vk[k];
+        const float sig = sqrtf(sg);
+        const float alpha = x0 >= 0.f ? -sig : sig;
+        const float den = sg - x0 * alpha;
+        const float bk = (sig > 0.f && den > 0.f) ? 1.f / den : 0.f;
+        __syncwarp();
+        if (t == 0) {
+          Vk[k] = x0 - alpha;
+          s_cf[k] = bk;
+        }
+      }
+      __syncthreads();
+      const float bk = s_cf[k];
+      for (int j = k + 1 + w; j < nn && bk != 0.f; j += 32) {
+        float* Vj = VT + (size_t)j * N;
+        float d = 0.f;
+        for (int i = k + t; i < N; i += 32) d = fmaf(Vk[i], Vj[i], d);
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        d *= bk;
+        for (int i = k + t; i < N; i += 32) Vj[i] -= d * Vk[i];
+      }
+      __syncthreads();
+    }
+    for (int q = w; q < nz; q += 32) {
+      float* Zc = ZT + (size_t)s_prev[q] * N;
+      for (int i = t; i < N; i += 32) Zc[i] = (i == nn + q) ? 1.f : 0.f;
+      __syncwarp();
+      for (int k = nn - 1; k >= 0; --k) {
+        const float bk = s_cf[k];
+        if (bk == 0.f) continue;
+        const float* Vk = VT + (size_t)k * N;
+        float d = 0.f;
+        for (int i = k + t; i < N; i += 32) d = fmaf(Vk[i], Zc[i], d);
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        d *= bk;
+        for (int i = k + t; i < N; i += 32) Zc[i] -= d * Vk[i];
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- 4. back-transformation, a warp per column of Z in registers -----------
+  constexpr int NR = EB_NMAX / 32;
+  for (int j = w; j < N; j += 32) {
+    const float* Zc = ZT + (size_t)j * N;
+    float z[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const int i = t + 32 * r;
+      z[r] = i < N ? Zc[i] : 0.f;
+    }
+    for (int k = N - 3; k >= 0; --k) {
+      const float bk = s_beta[k];
+      if (bk == 0.f) continue;
+      float v[NR];
+      float s = 0.f;
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        const int i = t + 32 * r;
+        v[r] = (i > k && i < N) ? Ap[pk(i, k)] : 0.f;
+        s = fmaf(v[r], z[r], s);
+      }
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      s *= bk;
+#pragma unroll
+      for (int r = 0; r < NR; ++r) z[r] -= s * v[r];
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const int i = t + 32 * r;
+      if (i < N) Xout[(int64_t)i * N + j] = (double)z[r];
+    }
+  }
+}
+
 cudaError_t launch_eig_f32(const double* A, int N, double* X, double* lam, float* scratch, cudaStream_t st,
                            double noise_rel) {
   if (N < 1 || N > 1024) return cudaErrorInvalidValue;
@@ -762,6 +1165,14 @@ cudaError_t launch_eig_f32(const double* A, int N, double* X, double* lam, float
     // a fixed cap (N = 128 needs 197,632 bytes): concurrent launches must not lower it
     cudaFuncSetAttribute(eig128_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     eig128_kernel<<<1, 1024, smem, st>>>(A, N, X, lam, scratch, (float)noise_rel);
+    return launched();
+  }
+  if (N <= EB_NMAX) {
+    const int ap_smem = N <= EB_SMEM_NMAX;
+    const size_t smem = ap_smem ? (size_t)N * (N + 1) / 2 * sizeof(float) : 0;
+    // a fixed cap: concurrent launches must not lower it
+    cudaFuncSetAttribute(eig_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 202 * 1024);
+    eig_big_kernel<<<1, 1024, smem, st>>>(A, N, X, lam, scratch, (float)noise_rel, ap_smem);
     return launched();
   }
   const size_t smem = (2ull * N * lda + 8ull * N) * sizeof(float);

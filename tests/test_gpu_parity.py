@@ -277,6 +277,31 @@ def test_tf32x3_large_pair_full_size():
     _check("tf32", G1, G2, PAIR_TF32_LARGE, ref=ref)
 
 
+# ---------------------------------------------------------------- wide compressed pairs
+# L = l1 + l2 above 128 runs the packed-triangle eigensolver (shared memory up to
+# L = 318, global scratch above).
+
+@pytest.mark.parametrize("prec,m,p,n,k,os_,q", [
+    ("fp64", 3000, 2600, 400, 90, 10, 1),      # L = 200
+    ("tf32x3", 5000, 4100, 600, 110, 14, 1),   # L = 248
+    ("fp32", 3000, 2500, 500, 170, 10, 1),     # L = 360: matrix in global scratch
+], ids=["L200-fp64", "L248-tf32x3", "L360-fp32"])
+def test_wide_compressed_pair(prec, m, p, n, k, os_, q):
+    # scale law logspace(0, 2) over r = k planted pairs: every returned pair is a signal pair well
+    # above the noise (a noise-determined pair has an arbitrary alpha and would interleave with the
+    # others in the sorted output); the oversampled columns carry noise only, so the eigensolver's
+    # noise-complement path runs too
+    spec = PairSpec(m=m, p=p, n=n, r=k, alpha="uniform", decay="logspace02", sigma=1e-7, k=k, oversample=os_, q=q,
+                    seed=m + k)
+    G1, G2, _, _ = planted_pair(spec)
+    ref = O.rand_gsvd(G1, G2, spec.kk, spec.oversample, spec.q, spec.seed)
+    a, b, _ = _solve(prec, G1, G2, spec)
+    e = O.gsv_error(ref["alpha"], ref["beta"], a, b)
+    assert np.max(e) <= TOL[prec], (np.max(e), e)
+    assert np.all(np.diff(a) <= 0) and np.all(np.diff(b) >= 0)
+    assert np.max(np.abs(a ** 2 + b ** 2 - 1)) < 1e-10
+
+
 # ---------------------------------------------------------------- BF16 mode
 # G is stored in BF16.  Parity is against the oracle run on the same BF16-rounded G
 # (converted exactly to FP64) with the same BF16-rounded Omega, so that the error is
