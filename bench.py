@@ -5,11 +5,14 @@ power iterations, the projections, the FP64 compressed-pair GSVD), inputs
 resident in HBM.  Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload tf32_large|fp64_small|bf16_stress|batched] [--prec tf32|fp32|...]
+                  [--workload tf32_large|fp64_small|bf16_stress|batched|learned] [--prec tf32|fp32|...]
 
 --workload batched: 256 uneven pairs (m, p ~ U[2000, 30000], n ~ U[100, 1000],
 k = rank ~ U[10, 100], oversample 10, q = 1) per step, solved by one
 gsvd_rand_solve_batched call over concurrent worker streams.
+
+--workload learned: the learned (k, q) proposal (train on the GPU, then solve held-out
+pairs; compared with Algorithm 1 alone and the plain fixed-rank method).
 
 Multi-GPU (torchrun, N > 1): every rank solves its own independent pairs (the
 units shard with no data-path collective): weak scaling, value = pairs of all
@@ -39,7 +42,11 @@ WORKLOADS = {
     "fp64_small": (PAIR_FP64_SMALL, "fp64"),
     "bf16_stress": (PAIR_BF16_STRESS, "bf16"),
     "batched": (None, "tf32x3"),  # 256 uneven pairs, one batched call per step
+    "learned": (None, "fp64"),    # learned (k, q) proposal: train, then held-out pairs
 }
+# context flags per precision: the BF16 mode runs its power steps on hi + lo halves (the
+# single-product form misses the 1e-4 target on the slow-decay pair)
+FLAGS = {"bf16": 4}
 METRIC = "pairs/sec and sketch TFLOP/s at GSV rel-err <=1e-4, chosen form vs plain FP64"
 DTYPE = {"tf32": "tf32", "tf32x3": "tf32x3", "bf16": "bf16", "fp32": "f32", "fp64": "f64"}
 
@@ -52,8 +59,9 @@ def peaks():
 
 
 def workload_desc(spec, prec):
+    extra = ", G stored BF16, power steps on BF16 hi + lo" if prec == "bf16" else ""
     return (f"single pair m={spec.m} p={spec.p} n={spec.n} rank={spec.r} k={spec.kk} "
-            f"oversample={spec.oversample} q={spec.q}, {prec} sketch/power/projection, FP64 small GSVD")
+            f"oversample={spec.oversample} q={spec.q}, {prec} sketch/power/projection{extra}, FP64 small GSVD")
 
 
 def sketch_traffic(prec, workload):
@@ -146,13 +154,17 @@ def run_reference(args, rank, world):
     spec, prec = WORKLOADS[args.workload]
     if rank != 0:
         return
-    if spec is None:  # batched workload: the oracle on a bounded sample of the batch, per step
-        specs = uneven_batch(args.pairs, seed=1)
-        s = oracle_batch_sample(specs, seconds=10.0, max_pairs=4)
+    if spec is None:  # batched / learned: the oracle on a bounded sample of the pairs, per step
+        if args.workload == "learned":
+            from paper_2404_09459_gb300.inputs import learned_pairs
+            s = oracle_learned_sample(learned_pairs(args.holdout, seed=2), seconds=10.0)
+        else:
+            s = oracle_batch_sample(uneven_batch(args.pairs, seed=1), seconds=10.0, max_pairs=4)
         line = {"impl": "reference", "metric": METRIC, "value": s["value"], "unit": "pairs/s", "n_gpus": world,
                 "steps": 1, "warmup": 0, "ms_per_step": 1e3 / s["value"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": f"batch of {args.pairs} uneven pairs (oracle on a sample)"},
+                "config": {"workload": (f"batch of {args.pairs} uneven pairs" if args.workload == "batched" else
+                                        f"learned-proposal held-out pairs ({args.holdout})") + " (oracle on a sample)"},
                 "cpu_baseline": s,
                 "e2e": {"value": s["value"], "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
@@ -271,6 +283,120 @@ def run_batched(args, rank, world):
         dist.destroy_process_group()
 
 
+def run_learned(args, rank, world):
+    """--workload learned: the learned (k, q) proposal on pairs of the uneven-batch laws (sigma
+    1e-9, FP64, residual tolerance 1e-4).  Labels (Algorithm 1 + fixed-rank bases) and training
+    run on the GPU first (not timed); one timed step = solving every held-out pair with the
+    learned proposal (probe, network, fixed-rank solve, Algorithm 1 fallback on a miss).  The
+    same pairs are also solved once by Algorithm 1 alone (b = 16), by the fixed-rank method at
+    the one (k, q) that the training labels need at most, and with the labels as a perfect
+    proposal.  Timing: host clock around each synchronous solve (generation not timed)."""
+    import tempfile
+    import torch
+    import paper_2404_09459_gb300 as P
+    from paper_2404_09459_gb300 import learn
+    from paper_2404_09459_gb300.inputs import learned_pairs
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    P._build.build()
+    tol, os_ = 1e-4, 10
+    tr = learned_pairs(args.train, seed=1 + 7919 * rank)
+    ho = learned_pairs(args.holdout, seed=2 + 7919 * rank)
+    t0 = time.perf_counter()
+    X, yk, yq, kad = learn.make_dataset(tr, tol, os_, local)
+    t_label = time.perf_counter() - t0
+    Xh, ykh, yqh, _ = learn.make_dataset(ho, tol, os_, local)
+    t0 = time.perf_counter()
+    params, norm, hist = learn.train(X, yk, yq, epochs=args.epochs, batch=256, lr=1e-3, device=local)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    pk, pq = learn.predict(params, norm, Xh, device=local, quantile=0.9)
+    pk0, _ = learn.predict(params, norm, Xh, device=local)
+    path = os.path.join(tempfile.mkdtemp(), "net.bin")
+    learn.save(path, params, norm)
+
+    def arm(make, plans=None, reps=1):
+        learn.timed_solves(ho[:2], make, 128, os_, local, plans[:2] if plans else None)  # warm-up
+        rows = []
+        for _ in range(reps):
+            rows += learn.timed_solves(ho, make, 128, os_, local, plans)
+        secs = sum(r["seconds"] for r in rows)
+        cert = float(np.mean([r["status"] == "ok" and max(r["resid"]) <= tol for r in rows]))
+        return rows, {"value": len(rows) / secs, "unit": "pairs/s", "certified": cert}
+
+    def mk_learned():
+        return P.Context("fp64", device=local, use_learned=True, mlp_path=path, tol=tol, block_b=16)
+
+    lmax = [min(s.m, s.p, s.n, 224) - os_ for s in ho]
+    hopeless = yk == 31
+    kfix = learn.k_of_bucket(int(yk.max()))
+    qfix = int(yq[yq < 4].max()) if np.any(yq < 4) else 4
+    barrier = (lambda: (dist.barrier(), torch.cuda.synchronize())) if dist else torch.cuda.synchronize
+    with ClockSampler(local) as clk:
+        barrier()
+        t0 = time.perf_counter()
+        rows, learned = arm(mk_learned, reps=args.steps)
+        barrier()
+        wall = time.perf_counter() - t0
+    fallback = float(np.mean([r["plan"][2] for r in rows]))
+    _, adaptive = arm(lambda: P.Context("fp64", device=local, adaptive=True, tol=tol, block_b=16))
+    _, plain = arm(lambda: P.Context("fp64", device=local),
+                   plans=[(max(1, min(kfix, lm)), qfix) for lm in lmax])
+    _, perfect = arm(lambda: P.Context("fp64", device=local),
+                     plans=[(max(1, min(learn.k_of_bucket(b), lm)), int(q)) for b, q, lm in zip(ykh, yqh, lmax)])
+    value = learned["value"]
+    if dist is not None:
+        t = torch.tensor([len(rows) / value], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        value = world * len(rows) / float(t.item())
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = oracle_learned_sample(ho)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+                "warmup": 2, "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": (f"learned k/q proposal: {args.train} training + {args.holdout} held-out pairs "
+                                        "of the uneven-batch laws (m, p ~ U[2000, 30000], n ~ U[100, 1000], "
+                                        "r ~ U[10, 100], exp(-i/10) scale, sigma 1e-9), FP64, residual tol 1e-4, "
+                                        "oversample 10; one step solves every held-out pair"),
+                           "timing": "host clock around each synchronous solve, device synchronised",
+                           "parallelism": f"independent pairs, {world} rank(s)"},
+                "arms": {"learned": learned, "adaptive_alg1_b16": adaptive,
+                         "plain_fixed_rank": dict(plain, k=kfix, q=qfix), "perfect_proposal": perfect},
+                "gain": {"vs_adaptive": value / adaptive["value"], "vs_plain_fixed_rank": value / plain["value"]},
+                "learned": {"fallback_rate": fallback, "label_seconds": t_label, "train_seconds": t_train,
+                            "final_loss": float(hist[-1]), "holdout_k_bucket_acc": float(np.mean(pk0 == ykh)),
+                            "holdout_q_acc": float(np.mean(pq == yqh)),
+                            "holdout_under_k_at_q90": float(np.mean(pk < ykh)),
+                            "label_q_counts": np.bincount(yq, minlength=5).tolist(),
+                            "hopeless_labels": int(hopeless.sum())},
+                "cpu_baseline": cpu, "gpu_launches": None, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def oracle_learned_sample(specs, seconds=20.0, max_pairs=4):
+    """The FP64 oracle's Algorithm 1 (b = 16, tol 1e-4) on a few held-out pairs (host cores)."""
+    from oracle import gsvd as O
+    done, t_total = 0, 0.0
+    for s in specs[:max_pairs]:
+        G1, G2, _, _ = planted_pair(s)
+        t0 = time.perf_counter()
+        O.rand_gsvd_adaptive(G1, G2, 1e-4, 16, s.seed, 128)
+        t_total += time.perf_counter() - t0
+        done += 1
+        if t_total > seconds:
+            break
+    return {"value": done / t_total, "unit": "pairs/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{done} held-out pairs solved by the oracle's Algorithm 1 (b = 16, tol 1e-4)"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -283,6 +409,9 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison leg")
     ap.add_argument("--pairs", type=int, default=256, help="batched workload: pairs per step")
     ap.add_argument("--workers", type=int, default=16, help="batched workload: concurrent worker streams")
+    ap.add_argument("--train", type=int, default=1024, help="learned workload: training pairs")
+    ap.add_argument("--holdout", type=int, default=128, help="learned workload: held-out pairs")
+    ap.add_argument("--epochs", type=int, default=60, help="learned workload: training epochs")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -293,6 +422,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "batched":
         return run_batched(args, rank, world)
+    if args.workload == "learned":
+        return run_learned(args, rank, world)
 
     import torch
     import paper_2404_09459_gb300 as P
@@ -311,9 +442,13 @@ def main():
     rspec = replace(spec, seed=spec.seed + 1000 * rank)
     dt = torch.float64 if prec == "fp64" else torch.float32
     G1, G2, _, _ = planted_pair_torch(rspec, device=f"cuda:{local}", dtype=dt)
+    if prec == "bf16":
+        dt = torch.bfloat16
+        G1, G2 = G1.to(dt), G2.to(dt)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")  # > 129 MB L2
+    flags = FLAGS.get(prec, 0)
 
-    ctx = P.Context(prec, device=local)
+    ctx = P.Context(prec, device=local, flags=flags)
     for _ in range(args.warmup):
         ctx.solve(G1, G2, spec.kk, spec.oversample, spec.q, rspec.seed)
     torch.cuda.synchronize()
@@ -345,7 +480,7 @@ def main():
     tflops = sketch_flops(spec) / (ms_step / 1e3) / 1e12
 
     # per-stage device time of the same solve (CUDA events on the solve stream)
-    pctx = P.Context(prec, device=local, flags=P.FLAG_PROFILE)
+    pctx = P.Context(prec, device=local, flags=P.FLAG_PROFILE | flags)
     pctx.solve(G1, G2, spec.kk, spec.oversample, spec.q, rspec.seed)
     pctx.profile(reset=True)
     for i in range(args.steps):
@@ -360,23 +495,32 @@ def main():
     # roofline of the sketch product Y = G X (HBM-bound: G read once per launch)
     pk = peaks()
     sk_ms, sk_calls = prof["sketch"]
-    el = 8 if prec == "fp64" else 4
-    # algorithmic bytes per launch averaged over both sides: G + X + Y
-    bytes_per_launch = sum((M * spec.n + spec.l * spec.n + M * spec.l) * el for M in (spec.m, spec.p)) / 2
-    achieved = bytes_per_launch / (sk_ms / sk_calls / 1e3) / 1e9 if sk_calls else None
+    el = 8 if prec == "fp64" else (2 if prec == "bf16" else 4)
+    # algorithmic bytes per launch averaged over both sides: G (el bytes) + X (el) + Y (FP32 / FP64)
+    ey = 8 if prec == "fp64" else 4
+    bytes_per_launch = sum(M * spec.n * el + spec.l * spec.n * el + M * spec.l * ey for M in (spec.m, spec.p)) / 2
+    launch_s = sk_ms / sk_calls / 1e3 if sk_calls else None
+    achieved = bytes_per_launch / launch_s / 1e9 if sk_calls else None
     roof = {"kernel": "sketch product Y = G X", "bound": "hbm", "achieved": achieved,
             "peak": pk.get("hbm_gbs"), "unit": "GB/s",
             "frac": (achieved / pk["hbm_gbs"]) if achieved else None,
             "traffic": sketch_traffic(prec, args.workload), "bytes_per_launch": bytes_per_launch,
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if not pk.get("fallback") else "fallback"}
+    if prec in ("bf16", "tf32", "tf32x3") and sk_calls:
+        # the same launches against the tensor peak: BF16 measured; TF32 at half of it (nominal ratio)
+        flops_per_launch = sum(2.0 * M * spec.n * spec.l for M in (spec.m, spec.p)) / 2
+        tpk = pk.get("bf16_tflops", 1900.0) * (1.0 if prec == "bf16" else 0.5)
+        roof["tensor"] = {"achieved_tflops": flops_per_launch / launch_s / 1e12, "peak_tflops": tpk,
+                          "frac": flops_per_launch / launch_s / 1e12 / tpk,
+                          "peak_source": "measured bf16_tflops" + ("" if prec == "bf16" else " x 0.5 (TF32 nominal)")}
 
     # end to end through the public API with host (pinned) buffers
     h1 = torch.empty(G1.shape, dtype=dt, pin_memory=True)
     h2 = torch.empty(G2.shape, dtype=dt, pin_memory=True)
     h1.copy_(G1)
     h2.copy_(G2)
-    n1, n2 = h1.numpy(), h2.numpy()
-    ectx = P.Context(prec, device=local)
+    n1, n2 = h1, h2  # host (pinned) tensors: the library stages them into HBM inside the call
+    ectx = P.Context(prec, device=local, flags=flags)
     ectx.solve(n1, n2, spec.kk, spec.oversample, spec.q, rspec.seed)
     barrier()
     t0 = time.perf_counter()

@@ -238,30 +238,33 @@ struct Solver {
     // for wider bases one l x l partial per 32-row tile would be GBs of partials, so the
     // chunked Gram kernel reads Q again instead
     const bool fuse = apply_fuses_gram(l);
-    auto gram_of = [&](const T* X) -> int {
-      CU(launch_gram_partial<T>(X, lp, M, l, b.gpart, chunks, rpc, st));
+    auto gram_of = [&](const T* X, int64_t ldx) -> int {
+      CU(launch_gram_partial<T>(X, ldx, M, l, b.gpart, chunks, rpc, st));
       CU(launch_gram_reduce(b.gpart, chunks, l, b.W, st));
       return GSVD_RAND_OK;
     };
+    // the intermediate bases live in b.tmp with their own compact row stride (b.tmp holds
+    // 2 x rows x round_up(l, 4)), whatever the stride of the input
+    const int64_t lt = round_up(l, 4);
     int rc;
-    if ((rc = gram_of(Yin))) return rc;
+    if ((rc = gram_of(Yin, lp))) return rc;
     CU(launch_chol_shift<TC>(b.W, l, shift_coef, tau, (TC*)b.R, (TC*)b.cscr, st_dev, stage, st));
-    CU((launch_apply_rinv<T, TC>(Yin, lp, M, l, (const TC*)b.R, b.tmp, lp, 0, fuse ? b.gpart : nullptr, st)));
+    CU((launch_apply_rinv<T, TC>(Yin, lp, M, l, (const TC*)b.R, b.tmp, lt, 0, fuse ? b.gpart : nullptr, st)));
     if (fuse)
       CU(launch_gram_reduce(b.gpart, apply_ctas(M, l, (int)sizeof(T)), l, b.W, st));
-    else if ((rc = gram_of(b.tmp)))
+    else if ((rc = gram_of(b.tmp, lt)))
       return rc;
     CU(launch_chol_shift<TC>(b.W, l, 0.0, tau, (TC*)b.R, (TC*)b.cscr, st_dev, stage + 1, st));
     // CholeskyQR a third time (shifted CholeskyQR3): the shifted first pass leaves Q1
     // far from orthonormal when Y is ill-conditioned (rank-deficient sketches)
-    T* q2 = b.tmp + (int64_t)M * lp;
-    CU((launch_apply_rinv<T, TC>(b.tmp, lp, M, l, (const TC*)b.R, q2, lp, 0, fuse ? b.gpart : nullptr, st)));
+    T* q2 = b.tmp + (int64_t)M * lt;
+    CU((launch_apply_rinv<T, TC>(b.tmp, lt, M, l, (const TC*)b.R, q2, lt, 0, fuse ? b.gpart : nullptr, st)));
     if (fuse)
       CU(launch_gram_reduce(b.gpart, apply_ctas(M, l, (int)sizeof(T)), l, b.W, st));
-    else if ((rc = gram_of(q2)))
+    else if ((rc = gram_of(q2, lt)))
       return rc;
     CU(launch_chol_shift<TC>(b.W, l, 0.0, tau, (TC*)b.R, (TC*)b.cscr, st_dev, stage + 1, st));
-    CU((launch_apply_rinv<T, TC>(q2, lp, M, l, (const TC*)b.R, out, ldo, transpose_out, nullptr, st)));
+    CU((launch_apply_rinv<T, TC>(q2, lt, M, l, (const TC*)b.R, out, ldo, transpose_out, nullptr, st)));
     return GSVD_RAND_OK;
   }
 

@@ -4,7 +4,7 @@
 // Features (per side, from the 16-column probe Y = G Omega_p and Z = G^T Y):
 // log10 of the eigenvalues of Y^T Y over 16 ||G||_F^2 and of Z^T Z over
 // 16 ||G||_F^4, descending, clipped to [-12, 1].  The 16 x 16 eigenvalues come
-// from cyclic Jacobi in FP64 (Golub & Van Loan, Alg. 8.5.3), one warp per Gram.
+// from a Householder tridiagonalisation and Sturm bisection in FP64, one warp per Gram.
 //
 // Network: x^ = (x - mean) / std; h1 = relu(x^ W1 + b1); h2 = relu(h1 W2 + b2);
 // z = h2 W3 + b3 (W row-major in x out).  Loss: softmax cross-entropy of the
@@ -27,49 +27,79 @@ constexpr float FEAT_LO = -12.f, FEAT_HI = 1.f;
 __device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
 // ---------------------------------------------------------------- features
-// Cyclic Jacobi on a symmetric 16 x 16 matrix in shared memory (row-major), by one
-// warp: lanes 0..15 own index i of the rotated rows / columns.  Returns the
-// eigenvalues in lane order (lane i < 16 holds lambda_i, unsorted).
-__device__ double jacobi16_warp(double* A) {
+// Eigenvalues of a symmetric 16 x 16 matrix in shared memory (row-major), by one
+// warp: Householder tridiagonalisation (Golub & Van Loan, Alg. 8.3.1; lane i owns
+// row i), then Sturm-count bisection, lane j < 16 finding the j-th smallest
+// eigenvalue.  Absolute accuracy ~ u ||A||, as Jacobi's.  Returns lambda_j in lane j.
+__device__ double eig16_warp(double* A, double* d, double* e2) {
   const int lane = threadIdx.x & 31;
   const bool act = lane < 16;
-  for (int sweep = 0; sweep < 20; ++sweep) {
-    double off = 0.0, tot = 0.0;
-    if (act)
-      for (int j = 0; j < 16; ++j) {
-        const double v = A[lane * 16 + j];
-        tot += v * v;
-        if (j != lane) off += v * v;
+  for (int k = 0; k < 14; ++k) {
+    // reflector of column k below the diagonal: v = x - alpha e_1, H = I - v v^T / (sg - x0 alpha)
+    const double x = (act && lane > k) ? A[lane * 16 + k] : 0.0;
+    double sg = x * x;
+    for (int o = 16; o > 0; o >>= 1) sg += __shfl_xor_sync(0xffffffffu, sg, o);
+    const double x0 = A[(k + 1) * 16 + k];
+    const double sig = sqrt(sg);
+    const double alpha = x0 >= 0.0 ? -sig : sig;
+    const double den = sg - x0 * alpha;
+    const bool refl = sig > 0.0 && den > 0.0;
+    const double v = (lane == k + 1) ? x0 - alpha : x;  // zero at and above row k
+    // p = A v / den (lane i: row i), then w = p - (p^T v / (2 den)) v
+    double p = 0.0;
+    if (refl)  // uniform: every lane runs the shuffles, rows 0..15 accumulate
+      for (int j = k + 1; j < 16; ++j) {
+        const double vj = __shfl_sync(0xffffffffu, v, j);
+        if (act) p = fma(A[lane * 16 + j], vj, p);
       }
-    for (int o = 16; o > 0; o >>= 1) {
-      off += __shfl_xor_sync(0xffffffffu, off, o);
-      tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    p = refl ? p / den : 0.0;
+    double pv = p * v;
+    for (int o = 16; o > 0; o >>= 1) pv += __shfl_xor_sync(0xffffffffu, pv, o);
+    const double wv = p - (refl ? 0.5 * pv / den : 0.0) * v;
+    __syncwarp();
+    if (refl)  // A <- A - v w^T - w v^T on the trailing block (rows and columns > k)
+      for (int j = k + 1; j < 16; ++j) {
+        const double wj = __shfl_sync(0xffffffffu, wv, j), vj = __shfl_sync(0xffffffffu, v, j);
+        if (act && lane > k) A[lane * 16 + j] -= v * wj + wv * vj;
+      }
+    __syncwarp();
+    if (lane == 0) {
+      d[k] = A[k * 16 + k];
+      e2[k] = refl ? alpha * alpha : x0 * x0;
     }
-    if (!(off > 1e-30 * tot)) break;
-    for (int p = 0; p < 15; ++p)
-      for (int q = p + 1; q < 16; ++q) {
-        const double apq = A[p * 16 + q];
-        if (apq == 0.0) continue;
-        const double app = A[p * 16 + p], aqq = A[q * 16 + q];
-        const double tau = (aqq - app) / (2.0 * apq);
-        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-        const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
-        __syncwarp();
-        if (act) {  // rows p, q
-          const double xp = A[p * 16 + lane], xq = A[q * 16 + lane];
-          A[p * 16 + lane] = c * xp - s * xq;
-          A[q * 16 + lane] = s * xp + c * xq;
-        }
-        __syncwarp();
-        if (act) {  // columns p, q
-          const double xp = A[lane * 16 + p], xq = A[lane * 16 + q];
-          A[lane * 16 + p] = c * xp - s * xq;
-          A[lane * 16 + q] = s * xp + c * xq;
-        }
-        __syncwarp();
-      }
+    __syncwarp();
   }
-  return act ? A[lane * 16 + lane] : 0.0;
+  if (lane == 0) {
+    d[14] = A[14 * 16 + 14];
+    d[15] = A[15 * 16 + 15];
+    e2[14] = A[15 * 16 + 14] * A[15 * 16 + 14];
+  }
+  __syncwarp();
+  // Gershgorin bounds, then bisection on the Sturm count of T - x I
+  double lo = 0.0, hi = 0.0;
+  for (int i = 0; i < 16; ++i) {
+    const double r = (i > 0 ? sqrt(e2[i - 1]) : 0.0) + (i < 15 ? sqrt(e2[i]) : 0.0);
+    lo = fmin(lo, d[i] - r);
+    hi = fmax(hi, d[i] + r);
+  }
+  const double nrm = fmax(fabs(lo), fabs(hi));
+  const double pivmin = fmax(1e-300, 1e-30 * nrm);
+  const int j = lane & 15;
+  for (int it = 0; it < 64 && hi - lo > 1e-17 * nrm; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    int cnt = 0;
+    double q = 1.0;
+    for (int i = 0; i < 16; ++i) {
+      q = (d[i] - mid) - (i > 0 ? e2[i - 1] / q : 0.0);
+      if (fabs(q) < pivmin) q = -pivmin;
+      cnt += q < 0.0;
+    }
+    if (cnt > j)
+      hi = mid;
+    else
+      lo = mid;
+  }
+  return 0.5 * (lo + hi);
 }
 
 }  // namespace
@@ -78,7 +108,7 @@ __device__ double jacobi16_warp(double* A) {
 // gpart: the sketch CTAs' partial sums of G^2 (gcount entries).
 __global__ void probe_features_kernel(const double* __restrict__ W1, const double* __restrict__ W2,
                                       const double* __restrict__ gpart, int gcount, float* __restrict__ feats) {
-  __shared__ double A[2][256];
+  __shared__ double A[2][256], D[2][16], E2[2][16];
   __shared__ double s_g2;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == 0) {
@@ -93,13 +123,8 @@ __global__ void probe_features_kernel(const double* __restrict__ W1, const doubl
     A[warp][e] = W[(i <= j ? i : j) * 16 + (i <= j ? j : i)];  // the Gram partials hold the upper triangle
   }
   __syncthreads();
-  const double lam = jacobi16_warp(A[warp]);
-  // rank of lane's eigenvalue in descending order (ties by lane index)
-  int rank = 0;
-  for (int j = 0; j < 16; ++j) {
-    const double o = __shfl_sync(0xffffffffu, lam, j);
-    rank += (o > lam) || (o == lam && j < lane);
-  }
+  const double lam = eig16_warp(A[warp], D[warp], E2[warp]);
+  const int rank = 15 - lane;  // lane j holds the j-th smallest: descending position 15 - j
   if (lane < 16) {
     const double den = 16.0 * (warp == 0 ? s_g2 : s_g2 * s_g2);
     const double r = lam > 0.0 && den > 0.0 ? lam / den : 0.0;
