@@ -68,10 +68,12 @@ def sketch_traffic(prec, workload):
     """DRAM bytes per sketch launch from the committed ncu capture, or None when the capture
     does not cover this workload/precision or the kernel source changed since it was taken."""
     import hashlib
-    if workload != "tf32_large" or prec != "tf32x3":
+    files = {("tf32_large", "tf32x3"): "sketch_traffic_tf32x3_large_pair.json",
+             ("bf16_stress", "bf16"): "sketch_traffic_bf16_stress_pair.json"}
+    if (workload, prec) not in files:
         return None
     try:
-        rec = json.load(open(os.path.join(ROOT, "profiles", "sketch_traffic_tf32x3_large_pair.json")))
+        rec = json.load(open(os.path.join(ROOT, "profiles", files[(workload, prec)])))
         src = open(os.path.join(ROOT, rec["source"]), "rb").read()
     except Exception:
         return None
