@@ -9,7 +9,9 @@ resident in HBM.  Prints one JSON line (rank 0).
 
 --workload batched: 256 uneven pairs (m, p ~ U[2000, 30000], n ~ U[100, 1000],
 k = rank ~ U[10, 100], oversample 10, q = 1) per step, solved by one
-gsvd_rand_solve_batched call over concurrent worker streams.
+gsvd_rand_solve_grouped call (every step one launch for all pairs, the launch
+sequence replayed from a CUDA graph); --batched-mode workers runs
+gsvd_rand_solve_batched over concurrent worker streams instead.
 
 --workload learned: the learned (k, q) proposal (train on the GPU, then solve held-out
 pairs; compared with Algorithm 1 alone and the plain fixed-rank method).
@@ -35,7 +37,7 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 from paper_2404_09459_gb300.inputs import (PAIR_BF16_STRESS, PAIR_FP64_SMALL, PAIR_TF32_LARGE,  # noqa: E402
-                                           planted_pair, planted_pair_torch, uneven_batch)
+                                           aligned_rows, planted_pair, planted_pair_torch, uneven_batch)
 
 WORKLOADS = {
     "tf32_large": (PAIR_TF32_LARGE, "tf32x3"),
@@ -222,13 +224,23 @@ def run_batched(args, rank, world):
     npairs = args.pairs
     specs = uneven_batch(npairs, seed=1 + rank)
     dt = torch.float64 if prec == "fp64" else torch.float32
-    mats = [planted_pair_torch(s, device=f"cuda:{local}", dtype=dt)[:2] for s in specs]
+    # rows stored with a 16-byte-multiple stride, so that the tensor-core products read G in place
+    mats = [tuple(aligned_rows(G) for G in planted_pair_torch(s, device=f"cuda:{local}", dtype=dt)[:2])
+            for s in specs]
     pairs = [dict(G1=G1, G2=G2, k=s.kk, oversample=s.oversample, q=s.q, seed=s.seed, pair=i)
              for i, (s, (G1, G2)) in enumerate(zip(specs, mats))]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")
     ctx = P.Context(prec, device=local)
+    grouped = args.batched_mode == "grouped"
+
+    def step():
+        if grouped:
+            ctx.solve_grouped(pairs)  # one launch per step for all pairs, replayed from a CUDA graph
+        else:
+            ctx.solve_batched(pairs, workers=args.workers)  # synchronous: returns after the worker streams
+
     for _ in range(args.warmup):
-        ctx.solve_batched(pairs, workers=args.workers)
+        step()
     torch.cuda.synchronize()
     l0 = ctx.launch_count()
 
@@ -243,10 +255,21 @@ def run_batched(args, rank, world):
             flush.fill_(i & 0xFF)
             barrier()
             t0 = time.perf_counter()
-            ctx.solve_batched(pairs, workers=args.workers)  # synchronous: returns after the worker streams
+            step()
             torch.cuda.synchronize()
             times.append(time.perf_counter() - t0)
     launches = (ctx.launch_count() - l0) // args.steps
+    info = ctx.grouped_info() if grouped else None
+    # the other batched form on the same pairs, for comparison (grouped vs concurrent workers)
+    other = None
+    if grouped and args.steps > 0:
+        ctx.solve_batched(pairs, workers=args.workers)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.solve_batched(pairs, workers=args.workers)
+        torch.cuda.synchronize()
+        other = {"value": npairs / (time.perf_counter() - t0), "unit": "pairs/s",
+                 "form": f"{args.workers} concurrent worker streams, per-pair launches"}
     sec = sum(times)
     if dist is not None:
         t = torch.tensor([sec], device=f"cuda:{local}")
@@ -271,7 +294,10 @@ def run_batched(args, rank, world):
                 "vs_baseline": None, "dtype": DTYPE.get(prec, prec), "data": "synthetic",
                 "config": {"workload": f"batch of {npairs} uneven pairs: m, p ~ U[2000, 30000], n ~ U[100, 1000], "
                                        f"k = rank ~ U[10, 100], oversample 10, q 1; {prec} products, FP64 small GSVD; "
-                                       f"{args.workers} concurrent worker streams",
+                                       + ("grouped: one launch per step for all pairs (persistent grouped tcgen05 "
+                                          "products, batched CholeskyQR and compressed-pair kernels), replayed from "
+                                          "a captured CUDA graph" if grouped else
+                                          f"{args.workers} concurrent worker streams"),
                            "l2": "flushed between timed steps (256 MiB write)",
                            "timing": "host clock around the synchronous batched call, device synchronised on both sides",
                            "parallelism": f"independent batches, {world} rank(s)"},
@@ -279,6 +305,13 @@ def run_batched(args, rank, world):
                 "sequential": {"value": npairs / seq_s, "unit": "pairs/s",
                                "batching_speedup": value / world / (npairs / seq_s)},
                 "cpu_baseline": cpu, "gpu_launches": int(launches), "clocks": clk.summary()}
+        if info is not None:
+            line["grouped"] = {"tuned_stages_ctas_per_sm": {"first_sketch": info["tuned"][0],
+                                                            "power_sketch": info["tuned"][1],
+                                                            "gtq_projection": info["tuned"][2]},
+                               "graph_captures": info["captures"], "graph_replays": info["replays"],
+                               "launches_per_replay": info["launches"]}
+            line["worker_streams"] = other
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist is not None:
@@ -411,6 +444,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison leg")
     ap.add_argument("--pairs", type=int, default=256, help="batched workload: pairs per step")
     ap.add_argument("--workers", type=int, default=16, help="batched workload: concurrent worker streams")
+    ap.add_argument("--batched-mode", default="grouped", choices=["grouped", "workers"],
+                    help="batched workload: one grouped solve (default) or concurrent per-pair solves")
     ap.add_argument("--train", type=int, default=1024, help="learned workload: training pairs")
     ap.add_argument("--holdout", type=int, default=128, help="learned workload: held-out pairs")
     ap.add_argument("--epochs", type=int, default=60, help="learned workload: training epochs")

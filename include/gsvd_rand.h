@@ -188,6 +188,38 @@ typedef struct {
  * cfg->stream).  Errors: ARG, OOM, CUDA, and any per-pair error. */
 int gsvd_rand_solve_batched(gsvd_rand_t h, int npairs, gsvd_rand_pair *pairs, int workers);
 
+/* Many independent pairs solved as one group (fixed-rank solves, cfg->prec TF32 or
+ * TF32X3): every step runs once for all pairs, so each launch holds the work of the
+ * whole batch (Algorithms 1 and 2 of Section 2 per pair, as gsvd_rand_solve):
+ *   - the products Y = G X, G^T Q and Q^T G of all sides are persistent grouped
+ *     tcgen05 launches over one tile table (per-problem tensor maps, tiles longest
+ *     first, double-buffered tensor-memory accumulators); their pipeline depth and
+ *     CTAs per SM are picked by a built-in autotuner (timed on the first batch of
+ *     each size bucket; the choice does not change the results);
+ *   - the shifted CholeskyQR3 passes, the split reductions, the residuals and the
+ *     compressed-pair GSVDs run as batched kernels (one table entry per problem).
+ * The whole launch sequence is captured into a CUDA graph and replayed while the
+ * pairs' inputs (pointers, shapes, k, oversample, q, seed, pair word) stay the same;
+ * the first call of a new batch builds the plan, uploads the tables, tunes and
+ * captures (it costs several solves).  Results go to each pair's alpha / beta
+ * (device or host; resid_out and r_out as in gsvd_rand_solve).  Per pair:
+ * l = k + oversample <= min(m, p, n) and <= 128, q <= 16, G1 and G2 device FP32 with
+ * 16-byte aligned rows; pairs may differ in every size and in q.  A pair that breaks
+ * these rules gets status ARG and is left out; the others are solved.  The grouped
+ * path chunks its Gram sums differently from gsvd_rand_solve, so results agree with it
+ * to rounding (not bit for bit); repeated calls are bit-identical.  The plan, tables
+ * and graph live in device memory owned by h (freed by gsvd_rand_destroy).
+ * Returns GSVD_RAND_OK when all pairs succeeded, else the status of the first
+ * failing pair.  Ordered after and before cfg->stream; synchronises.
+ * Errors: ARG, OOM, CUDA, UNSUPPORTED (precision, adaptive / learned / basis-only
+ * contexts, no sm_103 tensor cores), and per-pair NONFINITE, BREAKDOWN, TIMEOUT. */
+int gsvd_rand_solve_grouped(gsvd_rand_t h, int npairs, gsvd_rand_pair *pairs);
+
+/* The last grouped plan of h: tuned[6] = (stages, CTAs per SM) of the first sketch,
+ * the power-step sketch and the G^T Q / projection products; the graph captures and
+ * replays so far and the kernel launches per replay.  Any pointer may be NULL. */
+int gsvd_rand_grouped_info(gsvd_rand_t h, int *tuned, int64_t *captures, int64_t *replays, int64_t *launches);
+
 /* Comparative quantities of Section 1 for r GSV pairs (alpha non-increasing,
  * beta non-decreasing):
  *   theta[i] = atan2(alpha_i, beta_i) - pi/4      (antisymmetric angular distance)

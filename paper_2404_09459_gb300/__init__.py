@@ -25,7 +25,8 @@ EXPORTS = ("gsvd_rand_config_init", "gsvd_rand_create", "gsvd_rand_destroy", "gs
            "gsvd_rand_profile_get", "gsvd_rand_profile_reset", "gsvd_rand_launch_count",
            "gsvd_rand_metrics_noalloc", "gsvd_rand_basis_cols", "gsvd_rand_solve_batched",
            "gsvd_rand_probe_features", "gsvd_rand_mlp_forward", "gsvd_rand_mlp_loss_grad", "gsvd_rand_mlp_adam",
-           "gsvd_rand_mlp_train", "gsvd_rand_mlp_set", "gsvd_rand_mlp_load", "gsvd_rand_last_plan")
+           "gsvd_rand_mlp_train", "gsvd_rand_mlp_set", "gsvd_rand_mlp_load", "gsvd_rand_last_plan",
+           "gsvd_rand_solve_grouped", "gsvd_rand_grouped_info")
 NOALLOC_MAX_N = 32768
 FLAG_PROFILE = 2
 FLAG_BF16_SPLIT_POWER = 4
@@ -85,6 +86,9 @@ def load_library(path: str | None = None):
     lib.gsvd_rand_metrics_noalloc.argtypes = [i32, vp, vp, vp, i32, i32, i32, vp, vp, vp, vp, vp]
     lib.gsvd_rand_basis_cols.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     lib.gsvd_rand_solve_batched.argtypes = [vp, i32, C.POINTER(_Pair), i32]
+    lib.gsvd_rand_solve_grouped.argtypes = [vp, i32, C.POINTER(_Pair)]
+    lib.gsvd_rand_grouped_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                           C.POINTER(C.c_int64)]
     f32 = C.c_float
     lib.gsvd_rand_probe_features.argtypes = [vp, vp, i64, i64, vp, i64, i64, i64, u64, vp]
     lib.gsvd_rand_mlp_forward.argtypes = [vp, vp, vp, vp, i32, i32, vp]
@@ -228,6 +232,24 @@ class Context:
         """Many independent pairs at once.  pairs: sequence of dicts with G1, G2, k and optional
         oversample (10), q (1), seed (0), pair (its index).  Returns a list of dict(alpha, beta, r,
         resid, status); raises GsvdRandError if any pair failed (after all ran)."""
+        return self._many(pairs, workers)
+
+    def solve_grouped(self, pairs, host_out: bool = False):
+        """The same as solve_batched, as one grouped solve: every step one launch for all pairs,
+        the sequence captured into a CUDA graph and replayed while the inputs stay the same.
+        host_out: alpha / beta returned in host memory (numpy) even for device inputs."""
+        return self._many(pairs, None, host_out)
+
+    def grouped_info(self):
+        """dict(tuned=[(stages, ctas_per_sm)] x 3 (first sketch, power sketch, G^T Q), captures,
+        replays, launches per replay) of the last grouped plan."""
+        t = (C.c_int * 6)()
+        c, r, n = C.c_int64(0), C.c_int64(0), C.c_int64(0)
+        self._check(self.lib.gsvd_rand_grouped_info(self.h, t, C.byref(c), C.byref(r), C.byref(n)))
+        return dict(tuned=[(t[0], t[1]), (t[2], t[3]), (t[4], t[5])], captures=c.value, replays=r.value,
+                    launches=n.value)
+
+    def _many(self, pairs, workers, host_out=False):
         want = self._g_dtype()
         arr = (_Pair * len(pairs))()
         outs, keep = [], []
@@ -237,8 +259,8 @@ class Context:
             if n1 != n2:
                 raise ValueError(f"pair {i}: G1 and G2 must have the same number of columns")
             k = int(d["k"])
-            alpha, pa = self._out_vec(dev1, k)
-            beta, pb = self._out_vec(dev1, k)
+            alpha, pa = self._out_vec(dev1 and not host_out, k)
+            beta, pb = self._out_vec(dev1 and not host_out, k)
             r = C.c_int(0)
             resid = (C.c_double * 2)()
             q = arr[i]
@@ -248,7 +270,10 @@ class Context:
             q.alpha, q.beta, q.r_out, q.resid_out = pa, pb, C.addressof(r), C.addressof(resid)
             outs.append((alpha, beta, r, resid))
             keep += [k1, k2]
-        rc = self.lib.gsvd_rand_solve_batched(self.h, len(pairs), arr, workers)
+        if workers is None:
+            rc = self.lib.gsvd_rand_solve_grouped(self.h, len(pairs), arr)
+        else:
+            rc = self.lib.gsvd_rand_solve_batched(self.h, len(pairs), arr, workers)
         res = [dict(alpha=a[:r.value], beta=b[:r.value], r=r.value, resid=(rs[0], rs[1]), status=arr[i].status)
                for i, (a, b, r, rs) in enumerate(outs)]
         del keep

@@ -16,8 +16,13 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
+#include <map>
+#include <memory>
+#include <mutex>
 #include <string>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "../../include/gsvd_rand.h"
@@ -39,6 +44,7 @@ struct gsvd_rand_ctx {
   uint32_t pair_word = 0;        // Philox counter word 'pair' of the current solve
   bool owns_stream = false;      // stream created by the library (batched workers)
   std::vector<gsvd_rand_ctx*> workers;  // sub-contexts of gsvd_rand_solve_batched
+  struct GroupState* grp = nullptr;     // gsvd_rand_solve_grouped: plan, tables and captured graph
   // learned proposal: network (params | norm), then features, logits and scratch of one pair
   float* mlp_dev = nullptr;
   bool mlp_ready = false;
@@ -1044,6 +1050,880 @@ int solve_learned(gsvd_rand_ctx* h, const void* G1, int64_t m, int64_t ld1, cons
   return solve_dispatch(h, true, G1, m, ld1, G2, p, ld2, n, k, oversample, q, seed, alpha, beta, r_out, resid_out);
 }
 
+
+// ---------------------------------------------------------------------------
+// Grouped solve: every pair of a batch in one launch per step.  The products
+// are persistent grouped tcgen05 launches over a tile table, the other steps
+// the batched kernels (argument tables in device memory).  The launch
+// sequence is captured into a CUDA graph once per batch layout and replayed
+// while the pairs (pointers, shapes, parameters) stay the same; the tables are
+// uploaded with the plan, outside the graph.
+// ---------------------------------------------------------------------------
+}  // namespace
+
+struct GroupState {
+  std::vector<unsigned char> key;    // the batch the graph was captured for
+  cudaStream_t stream = nullptr;     // capture stream (non-blocking, owned)
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  unsigned char* host = nullptr;     // pinned: table staging, then the results block
+  size_t host_bytes = 0;
+  char* ws = nullptr;                // device workspace of the grouped solve (its own: single solves on
+  size_t ws_bytes = 0;               // the same context reuse theirs freely)
+  uint64_t launches_per_replay = 0;
+  int64_t captures = 0, replays = 0;
+  int tuned[3][2] = {{0, 0}, {0, 0}, {0, 0}};  // (stages, CTAs per SM): first sketch, power sketch, G^T Q
+  // results
+  size_t res_off = 0, res_bytes = 0;  // results block inside the workspace
+  std::vector<int> valid;             // pair index of each solved pair
+  struct Out {
+    size_t a_off, b_off;  // alpha / beta of the pair in the results block
+    int k;
+  };
+  std::vector<Out> outs;
+  unsigned char* scat_host = nullptr;  // pinned scatter table (results to device destinations)
+  size_t scat_cap = 0;
+  void* scat_dev = nullptr;
+  size_t scat_dev_cap = 0;
+};
+
+namespace {
+
+void group_free(GroupState* g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  if (g->stream) cudaStreamDestroy(g->stream);
+  if (g->ev_in) cudaEventDestroy(g->ev_in);
+  if (g->ev_out) cudaEventDestroy(g->ev_out);
+  if (g->host) cudaFreeHost(g->host);
+  if (g->scat_host) cudaFreeHost(g->scat_host);
+  if (g->scat_dev) cudaFree(g->scat_dev);
+  if (g->ws) cudaFree(g->ws);
+  delete g;
+}
+
+// The autotuner of the grouped products: per (mode, precision, norm, widest basis,
+// tile-count and k-depth buckets), the pipeline depth and CTAs per SM that ran fastest
+// on the first batch of that bucket (CUDA events, one warm-up launch, two timed).
+// These choices do not change results (the split-K partition is fixed by rule).
+struct TuneKey {
+  int mode, prec, norm, nmma, tbucket, kbucket;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(mode, prec, norm, nmma, tbucket, kbucket) <
+           std::tie(o.mode, o.prec, o.norm, o.nmma, o.tbucket, o.kbucket);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tune;
+
+int ilog2_bucket(int64_t v) {
+  int b = 0;
+  while (v > 1) {
+    v >>= 1;
+    ++b;
+  }
+  return b;
+}
+
+int tune_group(gsvd_rand_ctx* h, cudaStream_t st, int mode, int prec, bool norm, const void* table, int nprob,
+               int64_t ntiles, int nmma_max, int64_t kmean, DevStatus* st_dev, int* stages_out, int* per_sm_out) {
+  const TuneKey key{mode, prec, norm ? 1 : 0, nmma_max, ilog2_bucket(ntiles), ilog2_bucket(kmean)};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      *stages_out = it->second.first;
+      *per_sm_out = it->second.second;
+      return GSVD_RAND_OK;
+    }
+  }
+  std::vector<std::pair<int, int>> cand;
+  for (int per_sm = 2; per_sm >= 1; --per_sm) {
+    if (per_sm == 2 && 2 * round_up(nmma_max, 32) > 256) continue;
+    const int ms = tc_group_max_stages(mode, prec, nmma_max, per_sm);
+    for (int s : {2, 3, 4, 6, 8})
+      if (s <= ms) cand.push_back({s, per_sm});
+    if (ms >= 2 && ms != 2 && ms != 3 && ms != 4 && ms != 6 && ms != 8) cand.push_back({ms, per_sm});
+  }
+  if (cand.empty()) return fail(h, GSVD_RAND_ERR_UNSUPPORTED, "no pipeline fits the widest basis (%d)", nmma_max);
+  cudaEvent_t a, b;
+  CU(cudaEventCreate(&a));
+  CU(cudaEventCreate(&b));
+  float best = 3.4e38f;
+  std::pair<int, int> pick = cand[0];
+  for (auto& c : cand) {
+    CU(tc_group_launch(mode, prec, norm, table, nprob, ntiles, nmma_max, c.first, c.second, st_dev, st));
+    CU(cudaEventRecord(a, st));
+    for (int r = 0; r < 2; ++r)
+      CU(tc_group_launch(mode, prec, norm, table, nprob, ntiles, nmma_max, c.first, c.second, st_dev, st));
+    CU(cudaEventRecord(b, st));
+    CU(cudaEventSynchronize(b));
+    float ms = 0.f;
+    CU(cudaEventElapsedTime(&ms, a, b));
+    if (ms < best) {
+      best = ms;
+      pick = c;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = pick;
+  }
+  *stages_out = pick.first;
+  *per_sm_out = pick.second;
+  return GSVD_RAND_OK;
+}
+
+// Host-side table arena: tables are appended (256-byte aligned) and later copied to the
+// device in one transfer; a table's device address is dev + its offset.
+struct Arena {
+  std::vector<unsigned char> buf;
+  size_t add(const void* p, size_t bytes) {
+    const size_t off = (buf.size() + 255) & ~size_t(255);
+    buf.resize(off + bytes);
+    if (p) memcpy(buf.data() + off, p, bytes);
+    return off;
+  }
+  template <typename T>
+  size_t add(const std::vector<T>& v) {
+    return add(v.data(), v.size() * sizeof(T));
+  }
+};
+
+// Per-side and per-pair buffers of the grouped solve.
+struct GSide {
+  const float* G;
+  int64_t ldg, M, n;
+  int l, lx;
+  int64_t lp, ldx, ldm, lt;
+  float *Xt, *Y, *Qt, *tmp, *Z, *part;
+  double *gpart, *W, *gnorm, *bnorm;
+  float* R;
+  int splits;
+  int64_t rps;
+  int gchunks;
+  int64_t grpc;
+};
+struct GPair {
+  int k, l, L, q;
+  int64_t n, ldn;
+  float* S;
+  double *K, *X, *lam, *Zr, *C1, *Wv, *mu, *U1, *XtX, *P, *S2, *F, *opart;
+  int* order;
+  float* jscr;
+  DevStatus* st;
+  double* resid;
+  double *alpha, *beta;  // cs_norms destinations
+};
+
+struct GroupBuild {
+  std::vector<GSide> sides;
+  std::vector<GPair> prs;
+  Arena arena;
+  // launches, replayed in order; each receives the device address of the table arena
+  std::vector<std::function<cudaError_t(const unsigned char*, cudaStream_t)>> ops;
+  struct Gemm {
+    int mode;
+    bool norm;
+    size_t off;
+    int nprob, nmma;
+    int64_t ntiles, kmean;
+    int tune_slot;
+    int stages, per_sm;  // picked by the autotuner for this launch's own shape
+  };
+  std::vector<Gemm> gemms;
+  size_t ws_bytes = 0;
+};
+
+constexpr int64_t GROUP_GRAM_ROWS = 1024;  // rows per Gram chunk
+constexpr int64_t GROUP_GTQ_ROWS = 4096;   // rows per split of G^T Q
+
+// Lays out the workspace (base == nullptr: sizes only) and records the launch sequence.
+int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int prec, char* base, GroupBuild& gb) {
+  Bump bp;
+  bp.base = base;
+  const int np = (int)pv.size();
+  // results block (one transfer back): statuses, residuals, alpha / beta of host destinations
+  GroupState* g = h->grp;
+  DevStatus* st_all = bp.take<DevStatus>(np);
+  double* resid_all = bp.take<double>(2ll * np);
+  g->outs.assign(np, GroupState::Out{});
+  gb.prs.resize(np);
+  for (int i = 0; i < np; ++i) {
+    const gsvd_rand_pair& q = *pv[i];
+    GroupState::Out& o = g->outs[i];
+    o.k = q.k;
+    double* a = bp.take<double>(q.k);
+    double* b = bp.take<double>(q.k);
+    o.a_off = (size_t)((char*)a - base);
+    o.b_off = (size_t)((char*)b - base);
+    gb.prs[i].alpha = a;
+    gb.prs[i].beta = b;
+  }
+  bp.take<unsigned char>(1);
+  g->res_off = 0;
+  g->res_bytes = bp.off;
+  gb.sides.resize(2 * np);
+  for (int i = 0; i < np; ++i) {
+    const gsvd_rand_pair& q = *pv[i];
+    GPair& P = gb.prs[i];
+    P.k = q.k;
+    P.l = q.k + q.oversample;
+    P.L = 2 * P.l;
+    P.q = q.q;
+    P.n = q.n;
+    P.ldn = round_up(q.n, 4);
+    P.st = st_all + i;
+    P.resid = resid_all + 2 * i;
+    for (int s = 0; s < 2; ++s) {
+      GSide& S = gb.sides[2 * i + s];
+      S.G = static_cast<const float*>(s ? q.G2 : q.G1);
+      S.ldg = s ? q.ld2 : q.ld1;
+      S.M = s ? q.p : q.m;
+      S.n = q.n;
+      S.l = P.l;
+      S.lx = (int)round_up(P.l, 16);
+      S.lp = round_up(P.l, 4);
+      S.lt = S.lp;
+      S.ldx = round_up(q.n, 32);
+      S.ldm = round_up(S.M, 4);
+      S.Xt = bp.take<float>((int64_t)S.lx * S.ldx);
+      S.Y = bp.take<float>(S.M * S.lp);
+      S.Qt = bp.take<float>((int64_t)S.lx * S.ldm);
+      S.tmp = bp.take<float>(2 * std::max(S.M, S.n) * S.lt);
+      S.Z = bp.take<float>(S.n * S.lp);
+      S.rps = round_up(cdiv(S.M, cdiv(S.M, GROUP_GTQ_ROWS)), 32);
+      S.splits = (int)cdiv(S.M, S.rps);
+      S.part = bp.take<float>((int64_t)S.splits * S.n * S.lp);
+      const int64_t mx = std::max(S.M, S.n);
+      S.gchunks = (int)cdiv(mx, GROUP_GRAM_ROWS);
+      S.grpc = 0;
+      S.gpart = bp.take<double>((int64_t)S.gchunks * P.l * P.l);
+      S.W = bp.take<double>((int64_t)P.l * P.l);
+      S.R = bp.take<float>((int64_t)P.l * P.l);
+      S.gnorm = bp.take<double>(4 * cdiv(S.M, 128));
+      S.bnorm = bp.take<double>(cdiv(S.n * P.l, 256));
+    }
+  const int L = P.L;
+    P.S = bp.take<float>((int64_t)L * P.ldn);
+    P.K = bp.take<double>((int64_t)L * L);
+    P.X = bp.take<double>((int64_t)L * L);
+    P.lam = bp.take<double>(L);
+    P.Zr = bp.take<double>((int64_t)L * P.k);
+    P.order = bp.take<int>(L);
+    P.C1 = bp.take<double>((int64_t)P.k * P.k);
+    P.Wv = bp.take<double>((int64_t)P.k * P.k);
+    P.mu = bp.take<double>(P.k);
+    P.U1 = bp.take<double>((int64_t)L * P.k);
+    P.XtX = bp.take<double>((int64_t)L * L);
+    P.P = bp.take<double>((int64_t)L * L);
+    P.S2 = bp.take<double>((int64_t)L * L);
+    P.F = bp.take<double>((int64_t)L * L);
+    P.opart = bp.take<double>(4);
+    P.jscr = bp.take<float>(eig_scratch_floats(L));
+  }
+  gb.ws_bytes = bp.off;
+
+  // ---- the launch sequence ----
+  const int ns = 2 * np;
+  Arena& A = gb.arena;
+  auto& ops = gb.ops;
+  const double u = 5.9604644775390625e-08;  // FP32 unit roundoff
+  // statuses to zero on every replay
+  {
+    DevStatus* st0 = st_all;
+    ops.push_back([st0, np](const unsigned char*, cudaStream_t st) {
+      return cudaMemsetAsync(st0, 0, (size_t)np * sizeof(DevStatus), st);
+    });
+  }
+  // Omega^T for every side
+  {
+    std::vector<GaussB> t(ns);
+    int64_t mldx = 0;
+    int mlr = 0;
+    for (int j = 0; j < ns; ++j) {
+      const GSide& S = gb.sides[j];
+      const gsvd_rand_pair& q = *pv[j / 2];
+      t[j] = GaussB{S.Xt, S.ldx, S.n, S.l, S.lx, q.seed, q.pair, (uint32_t)(j & 1), GSVD_RAND_STREAM_FIXED, 0};
+      mldx = std::max(mldx, S.ldx);
+      mlr = std::max(mlr, S.lx);
+    }
+    const size_t off = A.add(t);
+    ops.push_back([off, ns, mldx, mlr](const unsigned char* d, cudaStream_t st) {
+      return launch_gaussian_kmajor_b(reinterpret_cast<const GaussB*>(d + off), ns, mldx, mlr, st);
+    });
+  }
+  // grouped products
+  // sides still iterating at power step `it` (pairs may differ in q); it < 0: every side
+  std::vector<int> act;
+  auto set_active = [&](int it) {
+    act.clear();
+    for (int j = 0; j < ns; ++j)
+      if (it < 0 || gb.prs[j / 2].q > it) act.push_back(j);
+  };
+  auto add_gemm = [&](int mode, bool norm, int slot) {
+    const int na = (int)act.size();
+    std::vector<TcGroupSpec> sp(na);
+    int64_t ksum = 0;
+    for (int a = 0; a < na; ++a) {
+      const GSide& S = gb.sides[act[a]];
+      TcGroupSpec& x = sp[a];
+      memset(&x, 0, sizeof(x));
+      x.G = S.G;
+      x.ldg = S.ldg;
+      x.M = S.M;
+      x.n = S.n;
+      x.l = S.l;
+      x.ldo = S.lp;
+      if (mode == 0) {
+        x.Bt = S.Xt;
+        x.ldb = S.ldx;
+        x.out = S.Y;
+        x.gnorm_part = norm ? S.gnorm : nullptr;
+        ksum += S.n;
+      } else {
+        x.Bt = S.Qt;
+        x.ldb = S.ldm;
+        x.out = S.part;
+        x.splits = S.splits;
+        x.rps = S.rps;
+        x.split_stride = S.n * S.lp;
+        ksum += S.rps;
+      }
+    }
+    const int64_t ntiles = tc_group_tiles(mode, sp.data(), na);
+    const size_t bytes = tc_group_table_bytes(na, ntiles);
+    size_t off = A.add(nullptr, bytes);
+    int nmma = 16;
+    for (int a = 0; a < na; ++a) nmma = std::max(nmma, (int)round_up(gb.sides[act[a]].l, 16));
+    if (base && !tc_group_build(mode, sp.data(), na, A.buf.data() + off, &nmma)) return false;
+    gb.gemms.push_back(GroupBuild::Gemm{mode, norm, off, na, nmma, ntiles, ksum / std::max(na, 1), slot, 0, 0});
+    const size_t gi = gb.gemms.size() - 1;
+    DevStatus* sd = st_all;
+    ops.push_back([gi, &gb, sd, prec](const unsigned char* d, cudaStream_t st) {
+      const GroupBuild::Gemm& G = gb.gemms[gi];
+      return tc_group_launch(G.mode, prec, G.norm, d + G.off, G.nprob, G.ntiles, G.nmma, G.stages, G.per_sm, sd, st);
+    });
+    return true;
+  };
+  // split reduction of G^T Q: into Z (power step) or into the rows of S (projection)
+  auto add_reduce = [&](bool proj) {
+    const int na = (int)act.size();
+    std::vector<ReduceB> t(na);
+    int64_t mx = 0;
+    for (int a = 0; a < na; ++a) {
+      const int j = act[a];
+      const GSide& S = gb.sides[j];
+      const GPair& P = gb.prs[j / 2];
+      ReduceB& r = t[a];
+      memset(&r, 0, sizeof(r));
+      r.part = S.part;
+      r.splits = S.splits;
+      r.l = S.l;
+      r.n = S.n;
+      r.lp = S.lp;
+      if (proj) {
+        r.Z = P.S + (int64_t)(j & 1) * S.l * P.ldn;
+        r.ldz = P.ldn;
+        r.transpose_out = 1;
+        r.sq_part = S.bnorm;
+      } else {
+        r.Z = S.Z;
+        r.ldz = S.lp;
+      }
+      mx = std::max(mx, S.n * S.l);
+    }
+    const size_t off = A.add(t);
+    ops.push_back([off, na, mx](const unsigned char* d, cudaStream_t st) {
+      return launch_reduce_splits_b(reinterpret_cast<const ReduceB*>(d + off), na, mx, st);
+    });
+  };
+  // shifted CholeskyQR3 of every side's basis (as Solver::orth without the fused kernel):
+  // which 0: Y (M x l) -> Q^T; 1: Z (n x l) -> X^T
+  auto add_orth = [&](int which, int stage0) {
+    for (int cls = 0; cls < 2; ++cls) {
+      std::vector<int> js;
+      int maxl = 0;
+      for (int j : act)
+        if ((gb.sides[j].l > 64) == (cls == 1)) {
+          js.push_back(j);
+          maxl = std::max(maxl, gb.sides[j].l);
+        }
+      if (js.empty()) continue;
+      const int nj = (int)js.size();
+      const int64_t arows = cls ? 32 : 128;
+      int maxch = 1;
+      int64_t maxM = 1;
+      std::vector<const float*> in(nj);
+      std::vector<int64_t> ldin(nj), rows(nj);
+      for (int t = 0; t < nj; ++t) {
+        const GSide& S = gb.sides[js[t]];
+        in[t] = which == 0 ? S.Y : S.Z;
+        ldin[t] = S.lp;
+        rows[t] = which == 0 ? S.M : S.n;
+        maxM = std::max(maxM, rows[t]);
+      }
+      for (int pass = 0; pass < 3; ++pass) {
+        std::vector<GramB> gt(nj);
+        std::vector<GramRedB> rt(nj);
+        std::vector<CholB> ct(nj);
+        std::vector<ApplyB> at(nj);
+        for (int t = 0; t < nj; ++t) {
+          const GSide& S = gb.sides[js[t]];
+          const int64_t M = rows[t];
+          const int64_t rpc = round_up(cdiv(M, cdiv(M, GROUP_GRAM_ROWS)), 16);
+          const int chunks = (int)cdiv(M, rpc);
+          maxch = std::max(maxch, chunks);
+          const float* src = pass == 0 ? in[t] : (pass == 1 ? S.tmp : S.tmp + M * S.lt);
+          const int64_t lds = pass == 0 ? ldin[t] : S.lt;
+          gt[t] = GramB{src, lds, M, rpc, S.l, chunks, S.gpart};
+          rt[t] = GramRedB{S.gpart, chunks, S.l, S.W};
+          const double shift = pass == 0 ? 11.0 * ((double)rpc + S.l + 1) * u : 0.0;
+          const double tau = 8.0 * (double)std::max<int64_t>(rpc, arows) * u;
+          ct[t] = CholB{S.W, shift, tau, S.R, gb.prs[js[t] / 2].st, S.l,
+                        10 * (js[t] & 1) + stage0 + (pass > 0 ? 1 : 0)};
+          ApplyB& a = at[t];
+          a.Y = src;
+          a.ldy = lds;
+          a.M = M;
+          a.Rinv = S.R;
+          a.l = S.l;
+          if (pass < 2) {
+            a.Q = pass == 0 ? S.tmp : S.tmp + M * S.lt;
+            a.ldq = S.lt;
+            a.transpose_out = 0;
+          } else {
+            a.Q = which == 0 ? S.Qt : S.Xt;
+            a.ldq = which == 0 ? S.ldm : S.ldx;
+            a.transpose_out = 1;
+          }
+        }
+        const size_t og = A.add(gt), orr = A.add(rt), oc = A.add(ct), oa = A.add(at);
+        const int mch = maxch;
+        const int64_t mM = maxM;
+        const int ml = maxl;
+        ops.push_back([og, orr, oc, oa, nj, mch, ml, mM](const unsigned char* d, cudaStream_t st) {
+          cudaError_t e;
+          if ((e = launch_gram_partial_b(reinterpret_cast<const GramB*>(d + og), nj, mch, ml, st))) return e;
+          if ((e = launch_gram_reduce_b(reinterpret_cast<const GramRedB*>(d + orr), nj, ml, st))) return e;
+          if ((e = launch_chol_b(reinterpret_cast<const CholB*>(d + oc), nj, ml, st))) return e;
+          return launch_apply_rinv_b(reinterpret_cast<const ApplyB*>(d + oa), nj, mM, ml, st);
+        });
+      }
+    }
+  };
+
+  set_active(-1);
+  if (!add_gemm(0, true, 0)) return fail(h, GSVD_RAND_ERR_ARG, "tensor map of a grouped product rejected");
+  add_orth(0, 1);
+  int qmax = 0;
+  for (auto* q : pv) qmax = std::max(qmax, q->q);
+  for (int it = 0; it < qmax; ++it) {
+    set_active(it);
+    if (!add_gemm(1, false, 2)) return fail(h, GSVD_RAND_ERR_ARG, "tensor map of a grouped product rejected");
+    add_reduce(false);
+    add_orth(1, 3);
+    if (!add_gemm(0, false, 1)) return fail(h, GSVD_RAND_ERR_ARG, "tensor map of a grouped product rejected");
+    add_orth(0, 5);
+  }
+  set_active(-1);
+  if (!add_gemm(1, false, 2)) return fail(h, GSVD_RAND_ERR_ARG, "tensor map of a grouped product rejected");
+  add_reduce(true);
+  {
+    std::vector<ResidB> t(ns);
+    for (int j = 0; j < ns; ++j) {
+      const GSide& S = gb.sides[j];
+      t[j] = ResidB{S.gnorm, S.bnorm, gb.prs[j / 2].resid + (j & 1), (int)(4 * cdiv(S.M, 128)),
+                    (int)cdiv(S.n * S.l, 256)};
+    }
+    const size_t off = A.add(t);
+    ops.push_back([off, ns](const unsigned char* d, cudaStream_t st) {
+      return launch_residual_b(reinterpret_cast<const ResidB*>(d + off), ns, st);
+    });
+  }
+
+  // ---- compressed-pair GSVDs ----
+  int maxL = 0, maxk = 0, maxl1 = 0;
+  for (auto& P : gb.prs) {
+    maxL = std::max(maxL, P.L);
+    maxk = std::max(maxk, P.k);
+    maxl1 = std::max(maxl1, P.l);
+  }
+  {
+    std::vector<DgemmB> t(np);
+    for (int i = 0; i < np; ++i) {
+      const GPair& P = gb.prs[i];
+      DgemmB& x = t[i];
+      memset(&x, 0, sizeof(x));
+      x.A = P.S;
+      x.B = P.S;
+      x.C = P.K;
+      x.lda = x.ldb = P.ldn;
+      x.ldc = P.L;
+      x.alpha = 1.0;
+      x.Mr = x.Nc = P.L;
+      x.K = (int)P.n;
+      x.ta = 0;
+      x.tb = 1;
+    }
+    const size_t off = A.add(t);
+    const int mL = maxL;
+    ops.push_back([off, np, mL](const unsigned char* d, cudaStream_t st) {
+      return launch_dgemm_b<float, float>(reinterpret_cast<const DgemmB*>(d + off), np, mL, mL, st);
+    });
+  }
+  // FP32 eigensolver starts, split by size class
+  auto add_eig = [&](bool c1) {
+    for (int cls = 0; cls < 2; ++cls) {
+      std::vector<EigB> t;
+      int mN = 0;
+      for (int i = 0; i < np; ++i) {
+        const GPair& P = gb.prs[i];
+        const int N = c1 ? P.k : P.L;
+        if ((N > 128) != (cls == 1)) continue;
+        t.push_back(c1 ? EigB{P.C1, P.Wv, P.mu, P.jscr, 0.f, N} : EigB{P.K, P.X, P.lam, P.jscr, 1e-6f, N});
+        mN = std::max(mN, N);
+      }
+      if (t.empty()) continue;
+      const size_t off = A.add(t);
+      const int cnt = (int)t.size();
+      ops.push_back([off, cnt, mN](const unsigned char* d, cudaStream_t st) {
+        return launch_eig_f32_b(reinterpret_cast<const EigB*>(d + off), cnt, mN, st);
+      });
+    }
+  };
+  // Ogita-Aishima steps (three: the mixed-precision count), the cut cluster after the second
+  auto add_oa = [&](bool c1) {
+    std::vector<OaB> t(np);
+    int mN = 0;
+    for (int i = 0; i < np; ++i) {
+      const GPair& P = gb.prs[i];
+      const int N = c1 ? P.k : P.L;
+      t[i] = OaB{c1 ? P.C1 : P.K, c1 ? P.Wv : P.X, c1 ? P.mu : P.lam, P.XtX, P.P, P.S2, P.F, P.opart, N, P.k};
+      mN = std::max(mN, N);
+    }
+    std::vector<DgemmB> dg(4 * (size_t)np);
+    oa_b_tables(t.data(), np, dg.data());
+    const size_t ot = A.add(t), od = A.add(dg);
+    for (int it = 0; it < 3; ++it) {
+      ops.push_back([ot, od, np, mN](const unsigned char* d, cudaStream_t st) {
+        return launch_oa_refine_b(reinterpret_cast<const OaB*>(d + ot), reinterpret_cast<const DgemmB*>(d + od), np,
+                                  mN, st);
+      });
+      if (!c1 && it == 1)
+        ops.push_back([ot, np, mN](const unsigned char* d, cudaStream_t st) {
+          return launch_oa_cut_cluster_b(reinterpret_cast<const OaB*>(d + ot), np, mN, st);
+        });
+    }
+  };
+  add_eig(false);
+  add_oa(false);
+  {
+    std::vector<SelB> t(np);
+    for (int i = 0; i < np; ++i) {
+      const GPair& P = gb.prs[i];
+      t[i] = SelB{P.X, P.lam, P.Zr, P.order, P.L, P.k};
+    }
+    const size_t off = A.add(t);
+    const int mL = maxL;
+    ops.push_back([off, np, mL](const unsigned char* d, cudaStream_t st) {
+      return launch_select_topr_b(reinterpret_cast<const SelB*>(d + off), np, mL, st);
+    });
+  }
+  {
+    std::vector<DgemmB> t(np);
+    for (int i = 0; i < np; ++i) {
+      const GPair& P = gb.prs[i];
+      DgemmB& x = t[i];
+      memset(&x, 0, sizeof(x));
+      x.A = P.Zr;
+      x.B = P.Zr;
+      x.C = P.C1;
+      x.lda = x.ldb = P.k;
+      x.ldc = P.k;
+      x.alpha = 1.0;
+      x.Mr = x.Nc = P.k;
+      x.K = P.l;
+      x.ta = 1;
+      x.tb = 0;
+    }
+    const size_t off = A.add(t);
+    const int mk = maxk;
+    ops.push_back([off, np, mk](const unsigned char* d, cudaStream_t st) {
+      return launch_dgemm_b<double, double>(reinterpret_cast<const DgemmB*>(d + off), np, mk, mk, st);
+    });
+  }
+  add_eig(true);
+  add_oa(true);
+  {
+    std::vector<DgemmB> t(2 * (size_t)np);
+    for (int i = 0; i < np; ++i) {
+      const GPair& P = gb.prs[i];
+      for (int s = 0; s < 2; ++s) {
+        DgemmB& x = t[2 * i + s];
+        memset(&x, 0, sizeof(x));
+        x.A = P.Zr + (int64_t)s * P.l * P.k;
+        x.B = P.Wv;
+        x.C = P.U1 + (int64_t)s * P.l * P.k;
+        x.lda = x.ldb = x.ldc = P.k;
+        x.alpha = 1.0;
+        x.Mr = P.l;
+        x.Nc = P.k;
+        x.K = P.k;
+      }
+    }
+    const size_t off = A.add(t);
+    const int ml = maxl1, mk = maxk, n2 = 2 * np;
+    ops.push_back([off, n2, ml, mk](const unsigned char* d, cudaStream_t st) {
+      return launch_dgemm_b<double, double>(reinterpret_cast<const DgemmB*>(d + off), n2, ml, mk, st);
+    });
+  }
+  {
+    std::vector<CsB> t(np);
+    for (int i = 0; i < np; ++i) {
+      const GPair& P = gb.prs[i];
+      t[i] = CsB{P.U1, P.U1 + (int64_t)P.l * P.k, P.alpha, P.beta, P.l, P.l, P.k, 0};
+    }
+    const size_t off = A.add(t);
+    const int mk = maxk;
+    ops.push_back([off, np, mk](const unsigned char* d, cudaStream_t st) {
+      return launch_cs_norms_b(reinterpret_cast<const CsB*>(d + off), np, mk, st);
+    });
+  }
+  return GSVD_RAND_OK;
+}
+
+int solve_grouped(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs) {
+  const int prec = h->cfg.prec;
+  if (prec != GSVD_RAND_TF32 && prec != GSVD_RAND_TF32X3)
+    return fail(h, GSVD_RAND_ERR_UNSUPPORTED, "grouped solves run the TF32 / 3xTF32 tensor-core products");
+  if (h->cfg.adaptive || h->cfg.use_learned || (h->cfg.flags & GSVD_RAND_FLAG_BASIS_ONLY))
+    return fail(h, GSVD_RAND_ERR_UNSUPPORTED, "grouped solves are fixed-rank solves with the compressed-pair GSVD");
+  if (h->tc_ok < 0) h->tc_ok = tc_available(h->cfg.device) ? 1 : 0;
+  if (!h->tc_ok) return fail(h, GSVD_RAND_ERR_UNSUPPORTED, "tensor-core path unavailable on this device");
+  CU(cudaSetDevice(h->cfg.device));
+  // the key of this batch: every argument but the status slots
+  std::vector<unsigned char> key((size_t)npairs * sizeof(gsvd_rand_pair) + 2 * sizeof(int));
+  memcpy(key.data(), &prec, sizeof(int));
+  memcpy(key.data() + sizeof(int), &h->cfg.flags, sizeof(int));
+  for (int i = 0; i < npairs; ++i) {
+    // the outputs are copied out of the results block after the graph: not part of the key
+    gsvd_rand_pair c;
+    memset(&c, 0, sizeof(c));
+    c.G1 = pairs[i].G1;
+    c.m = pairs[i].m;
+    c.ld1 = pairs[i].ld1;
+    c.G2 = pairs[i].G2;
+    c.p = pairs[i].p;
+    c.ld2 = pairs[i].ld2;
+    c.n = pairs[i].n;
+    c.k = pairs[i].k;
+    c.oversample = pairs[i].oversample;
+    c.q = pairs[i].q;
+    c.seed = pairs[i].seed;
+    c.pair = pairs[i].pair;
+    c.alpha = reinterpret_cast<double*>((uintptr_t)(pairs[i].alpha != nullptr));
+    c.beta = reinterpret_cast<double*>((uintptr_t)(pairs[i].beta != nullptr));
+    memcpy(key.data() + 2 * sizeof(int) + (size_t)i * sizeof(gsvd_rand_pair), &c, sizeof(c));
+  }
+  if (!h->grp) {
+    h->grp = new GroupState();
+    CU(cudaStreamCreateWithFlags(&h->grp->stream, cudaStreamNonBlocking));
+    CU(cudaEventCreateWithFlags(&h->grp->ev_in, cudaEventDisableTiming));
+    CU(cudaEventCreateWithFlags(&h->grp->ev_out, cudaEventDisableTiming));
+  }
+  GroupState* g = h->grp;
+  cudaStream_t gs = g->stream;
+  // order after the caller's stream
+  CU(cudaEventRecord(g->ev_in, h->stream));
+  CU(cudaStreamWaitEvent(gs, g->ev_in, 0));
+  if (!(g->exec && key == g->key)) {
+    // validate; invalid pairs get ARG and stay out of the group
+    std::vector<gsvd_rand_pair*> pv;
+    g->valid.clear();
+    for (int i = 0; i < npairs; ++i) {
+      gsvd_rand_pair& q = pairs[i];
+      const int64_t l = (int64_t)q.k + q.oversample;
+      bool ok = q.G1 && q.G2 && q.alpha && q.beta && q.m >= 1 && q.p >= 1 && q.n >= 1 && q.ld1 >= q.n &&
+                q.ld2 >= q.n && q.k >= 1 && q.oversample >= 0 && q.q >= 0 && q.q <= 16 && l <= 128 &&
+                l <= std::min(std::min(q.m, q.p), q.n) && is_device_ptr(q.G1) && is_device_ptr(q.G2) &&
+                tc_shape_ok(q.G1, q.ld1, (int)l) && tc_shape_ok(q.G2, q.ld2, (int)l);
+      q.status = ok ? GSVD_RAND_OK : GSVD_RAND_ERR_ARG;
+      if (ok) {
+        pv.push_back(&q);
+        g->valid.push_back(i);
+      }
+    }
+    if (g->exec) {
+      cudaGraphExecDestroy(g->exec);
+      g->exec = nullptr;
+    }
+    if (g->graph) {
+      cudaGraphDestroy(g->graph);
+      g->graph = nullptr;
+    }
+    g->key.clear();
+    if (pv.empty()) {
+      for (int i = 0; i < npairs; ++i)
+        if (pairs[i].status) return fail(h, pairs[i].status, "pair %d: invalid arguments for a grouped solve", i);
+      return GSVD_RAND_OK;
+    }
+    // pass 1: sizes; pass 2: the real layout and tables
+    GroupBuild sizer;
+    int rc = group_build(h, pv, prec, nullptr, sizer);
+    if (rc) return rc;
+    const size_t tab_bytes = (sizer.arena.buf.size() + 255) & ~size_t(255);
+    const size_t need = sizer.ws_bytes + tab_bytes + 4096;
+    if (need > g->ws_bytes) {
+      if (g->ws) cudaFree(g->ws);
+      g->ws = nullptr;
+      g->ws_bytes = 0;
+      const size_t want = need + need / 8;
+      if (cudaMalloc(&g->ws, want) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, GSVD_RAND_ERR_OOM, "grouped workspace allocation of %zu bytes failed", want);
+      }
+      g->ws_bytes = want;
+    }
+    GroupBuild* gbp = new GroupBuild();
+    std::unique_ptr<GroupBuild> gb_own(gbp);
+    GroupBuild& gb = *gbp;
+    if ((rc = group_build(h, pv, prec, g->ws, gb))) return rc;
+    unsigned char* dtab = reinterpret_cast<unsigned char*>(g->ws) + ((gb.ws_bytes + 255) & ~size_t(255));
+    if (gb.arena.buf.size() > tab_bytes) return fail(h, GSVD_RAND_ERR_CUDA, "table layout changed between passes");
+    // pinned staging of the tables (and later the results)
+    const size_t hb = std::max(gb.arena.buf.size(), g->res_bytes) + 256;
+    if (g->host_bytes < hb) {
+      if (g->host) cudaFreeHost(g->host);
+      g->host = nullptr;
+      g->host_bytes = 0;
+      CU(cudaMallocHost(&g->host, hb));
+      g->host_bytes = hb;
+    }
+    memcpy(g->host, gb.arena.buf.data(), gb.arena.buf.size());
+    CU(cudaMemcpyAsync(dtab, g->host, gb.arena.buf.size(), cudaMemcpyHostToDevice, gs));
+    // padding rows of the K-major bases stay zero (nothing writes them)
+    for (auto& S : gb.sides)
+      if (S.lx > S.l) CU(cudaMemsetAsync(S.Qt + (int64_t)S.l * S.ldm, 0, (size_t)(S.lx - S.l) * S.ldm * sizeof(float), gs));
+    CU(cudaStreamSynchronize(gs));
+    // autotune the products (outside the graph; results do not depend on the choice)
+    DevStatus* st0 = reinterpret_cast<DevStatus*>(g->ws);
+    for (auto& G : gb.gemms) {
+      int s_ = 0, p_ = 0;
+      if ((rc = tune_group(h, gs, G.mode, prec, G.norm, dtab + G.off, G.nprob, G.ntiles, G.nmma, G.kmean, st0, &s_,
+                           &p_)))
+        return rc;
+      G.stages = s_;
+      G.per_sm = p_;
+      g->tuned[G.tune_slot][0] = s_;  // reported: the last launch of each kind
+      g->tuned[G.tune_slot][1] = p_;
+    }
+    // capture the launch sequence
+    const uint64_t c0 = g_launch_count.load();
+    CU(cudaStreamBeginCapture(gs, cudaStreamCaptureModeRelaxed));
+    cudaError_t ce = cudaSuccess;
+    size_t bad_op = 0;
+    for (auto& op : gb.ops) {
+      if ((ce = op(dtab, gs)) != cudaSuccess) break;
+      ++bad_op;
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(gs, &graph);
+    if (ce != cudaSuccess || ee != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return fail(h, GSVD_RAND_ERR_CUDA, "capture of the grouped solve failed at step %zu of %zu: %s", bad_op,
+                  gb.ops.size(), cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+    }
+    g->launches_per_replay = g_launch_count.load() - c0;
+    g_launch_count.fetch_sub(g->launches_per_replay);  // counted when the graph runs
+    g->graph = graph;
+    CU(cudaGraphInstantiate(&g->exec, graph, 0));
+    g->key.swap(key);
+    g->captures += 1;
+  } else {
+    for (int i = 0; i < npairs; ++i) pairs[i].status = GSVD_RAND_ERR_ARG;
+    for (int i : g->valid) pairs[i].status = GSVD_RAND_OK;
+  }
+  CU(cudaGraphLaunch(g->exec, gs));
+  g_launch_count.fetch_add(g->launches_per_replay);
+  g->replays += 1;
+  // alpha / beta to device destinations: one scatter launch from a small table; host
+  // destinations are filled from the results block below
+  const int nv = (int)g->valid.size();
+  {
+    std::vector<ScatterB> sc;
+    for (int t = 0; t < nv; ++t) {
+      const gsvd_rand_pair& q = pairs[g->valid[t]];
+      const GroupState::Out& o = g->outs[t];
+      if (is_device_ptr(q.alpha))
+        sc.push_back(ScatterB{reinterpret_cast<const double*>(g->ws + o.a_off), q.alpha, o.k, 0});
+      if (is_device_ptr(q.beta))
+        sc.push_back(ScatterB{reinterpret_cast<const double*>(g->ws + o.b_off), q.beta, o.k, 0});
+    }
+    if (!sc.empty()) {
+      const size_t bytes = sc.size() * sizeof(ScatterB);
+      if (g->scat_cap < bytes) {
+        CU(cudaStreamSynchronize(gs));
+        if (g->scat_host) cudaFreeHost(g->scat_host);
+        g->scat_host = nullptr;
+        g->scat_cap = 0;
+        CU(cudaMallocHost(&g->scat_host, 2 * bytes));
+        g->scat_cap = 2 * bytes;
+      }
+      if (g->scat_dev_cap < bytes) {
+        CU(cudaStreamSynchronize(gs));
+        if (g->scat_dev) cudaFree(g->scat_dev);
+        g->scat_dev = nullptr;
+        g->scat_dev_cap = 0;
+        CU(cudaMalloc(&g->scat_dev, 2 * bytes));
+        g->scat_dev_cap = 2 * bytes;
+      }
+      memcpy(g->scat_host, sc.data(), bytes);
+      CU(cudaMemcpyAsync(g->scat_dev, g->scat_host, bytes, cudaMemcpyHostToDevice, gs));
+      CU(launch_scatter_b(reinterpret_cast<const ScatterB*>(g->scat_dev), (int)sc.size(), gs));
+    }
+  }
+  // statuses, residuals and alpha / beta in one transfer
+  CU(cudaMemcpyAsync(g->host, g->ws + g->res_off, g->res_bytes, cudaMemcpyDeviceToHost, gs));
+  CU(cudaEventRecord(g->ev_out, gs));
+  CU(cudaStreamWaitEvent(h->stream, g->ev_out, 0));
+  CU(cudaStreamSynchronize(gs));
+  const DevStatus* sth = reinterpret_cast<const DevStatus*>(g->host);
+  const double* rh = reinterpret_cast<const double*>(g->host + ((nv * sizeof(DevStatus) + 255) & ~size_t(255)));
+  int first_bad = -1;
+  for (int t = 0; t < nv; ++t) {
+    gsvd_rand_pair& q = pairs[g->valid[t]];
+    const GroupState::Out& o = g->outs[t];
+    q.status = sth[t].code;
+    if (!is_device_ptr(q.alpha)) memcpy(q.alpha, g->host + (o.a_off - g->res_off), (size_t)o.k * sizeof(double));
+    if (!is_device_ptr(q.beta)) memcpy(q.beta, g->host + (o.b_off - g->res_off), (size_t)o.k * sizeof(double));
+    if (q.resid_out) {
+      if (is_device_ptr(q.resid_out))
+        CU(cudaMemcpy(q.resid_out, rh + 2 * t, 2 * sizeof(double), cudaMemcpyHostToDevice));
+      else
+        memcpy(q.resid_out, rh + 2 * t, 2 * sizeof(double));
+    }
+    if (q.r_out) {
+      const int r = q.k;
+      if (is_device_ptr(q.r_out))
+        CU(cudaMemcpy(q.r_out, &r, sizeof(int), cudaMemcpyHostToDevice));
+      else
+        *q.r_out = r;
+    }
+  }
+  for (int i = 0; i < npairs; ++i)
+    if (pairs[i].status && first_bad < 0) first_bad = i;
+  if (first_bad >= 0)
+    return fail(h, pairs[first_bad].status, "pair %d (first failing pair): status %d", first_bad,
+                pairs[first_bad].status);
+  h->err.clear();
+  return GSVD_RAND_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1098,6 +1978,11 @@ int gsvd_rand_destroy(gsvd_rand_t h) {
   for (auto wk : h->workers) gsvd_rand_destroy(wk);
   h->workers.clear();
   cudaSetDevice(h->cfg.device);
+  if (h->grp) {
+    cudaStreamSynchronize(h->grp->stream);
+    group_free(h->grp);
+    h->grp = nullptr;
+  }
   if (h->stream) cudaStreamSynchronize(h->stream); else cudaDeviceSynchronize();
   if (h->owns_stream && h->stream) cudaStreamDestroy(h->stream);
   for (auto e : h->evpool) cudaEventDestroy(e);
@@ -1230,6 +2115,23 @@ int gsvd_rand_solve_batched(gsvd_rand_t h, int npairs, gsvd_rand_pair* pairs, in
     if (pairs[i].status)
       return fail(h, pairs[i].status, "pair %d (first failing pair): %s", i, msgs[i].c_str());
   h->err.clear();
+  return GSVD_RAND_OK;
+}
+
+int gsvd_rand_solve_grouped(gsvd_rand_t h, int npairs, gsvd_rand_pair* pairs) {
+  if (!h || npairs < 0 || (npairs > 0 && !pairs)) return GSVD_RAND_ERR_ARG;
+  if (npairs == 0) return GSVD_RAND_OK;
+  return solve_grouped(h, npairs, pairs);
+}
+
+int gsvd_rand_grouped_info(gsvd_rand_t h, int* tuned, int64_t* captures, int64_t* replays, int64_t* launches) {
+  if (!h) return GSVD_RAND_ERR_ARG;
+  GroupState* g = h->grp;
+  if (tuned)
+    for (int i = 0; i < 6; ++i) tuned[i] = g ? g->tuned[i / 2][i % 2] : 0;
+  if (captures) *captures = g ? g->captures : 0;
+  if (replays) *replays = g ? g->replays : 0;
+  if (launches) *launches = g ? (int64_t)g->launches_per_replay : 0;
   return GSVD_RAND_OK;
 }
 

@@ -404,10 +404,10 @@ template cudaError_t launch_gemm_gtq_simt<float, float>(const float*, int64_t, i
 
 // Deterministic split reduction (FP64 accumulation, split order).
 template <typename TP, typename T>
-__global__ void reduce_splits_kernel(const TP* __restrict__ part, int splits, int64_t n, int l,
-                                     int64_t lp, T* __restrict__ Z, int64_t ldz, int transpose_out,
-                                     double* sq_part) {
-  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void reduce_splits_body(const TP* __restrict__ part, int splits, int64_t n, int l,
+                                                   int64_t lp, T* __restrict__ Z, int64_t ldz, int transpose_out,
+                                                   double* sq_part, int bx) {
+  int64_t e = (int64_t)bx * blockDim.x + threadIdx.x;
   int64_t total = n * l;
   double v = 0.0;
   double sq = 0.0;
@@ -431,8 +431,15 @@ __global__ void reduce_splits_kernel(const TP* __restrict__ part, int splits, in
   }
   if (sq_part) {
     double s = block_sum_double(sq);
-    if (threadIdx.x == 0) sq_part[blockIdx.x] = s;
+    if (threadIdx.x == 0) sq_part[bx] = s;
   }
+}
+
+template <typename TP, typename T>
+__global__ void reduce_splits_kernel(const TP* __restrict__ part, int splits, int64_t n, int l,
+                                     int64_t lp, T* __restrict__ Z, int64_t ldz, int transpose_out,
+                                     double* sq_part) {
+  reduce_splits_body<TP, T>(part, splits, n, l, lp, Z, ldz, transpose_out, sq_part, (int)blockIdx.x);
 }
 
 template <typename TP, typename T>
@@ -460,15 +467,12 @@ template cudaError_t launch_reduce_splits<float, float>(const float*, int, int64
 constexpr int GR_T = 64, GR_BK = 16;
 
 template <typename T>
-__global__ __launch_bounds__(256) void gram_partial_kernel(const T* __restrict__ Y, int64_t ldy,
-                                                           int64_t M, int l, double* __restrict__ part,
-                                                           int64_t rows_per_chunk) {
-  const int ti = blockIdx.y, tj = blockIdx.z;
-  if (ti > tj) return;
+__device__ __forceinline__ void gram_partial_body(const T* __restrict__ Y, int64_t ldy, int64_t M, int l,
+                                                  double* __restrict__ part, int64_t rows_per_chunk, int c, int ti,
+                                                  int tj) {
   __shared__ T As[GR_BK][GR_T + 1];
   __shared__ T Bs[GR_BK][GR_T + 1];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int c = blockIdx.x;
   const int64_t rbeg = (int64_t)c * rows_per_chunk, rend = min(M, rbeg + rows_per_chunk);
   const int i0 = ti * GR_T, j0 = tj * GR_T;
   T acc[4][4];
@@ -513,6 +517,14 @@ __global__ __launch_bounds__(256) void gram_partial_kernel(const T* __restrict__
   }
 }
 
+template <typename T>
+__global__ __launch_bounds__(256) void gram_partial_kernel(const T* __restrict__ Y, int64_t ldy,
+                                                           int64_t M, int l, double* __restrict__ part,
+                                                           int64_t rows_per_chunk) {
+  if (blockIdx.y > blockIdx.z) return;
+  gram_partial_body<T>(Y, ldy, M, l, part, rows_per_chunk, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z);
+}
+
 int gram_chunks(int64_t M, int l, int64_t* rows_per_chunk) {
   int64_t t = cdiv(l, GR_T);
   int64_t upper = t * (t + 1) / 2;
@@ -541,9 +553,9 @@ template cudaError_t launch_gram_partial<float>(const float*, int64_t, int64_t, 
 
 // W[i][j] = W[j][i] = sum_c part[c][min(i,j)][max(i,j)], one warp per entry
 // (fixed lane/shuffle order: deterministic).
-__global__ void gram_reduce_kernel(const double* __restrict__ part, int chunks, int l,
-                                   double* __restrict__ W) {
-  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+__device__ __forceinline__ void gram_reduce_body(const double* __restrict__ part, int chunks, int l,
+                                                 double* __restrict__ W, int bx) {
+  const int64_t wid = ((int64_t)bx * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (wid >= (int64_t)l * l) return;
   const int i = (int)(wid / l), j = (int)(wid % l);
@@ -556,6 +568,11 @@ __global__ void gram_reduce_kernel(const double* __restrict__ part, int chunks, 
     W[(int64_t)i * l + j] = s;
     W[(int64_t)j * l + i] = s;
   }
+}
+
+__global__ void gram_reduce_kernel(const double* __restrict__ part, int chunks, int l,
+                                   double* __restrict__ W) {
+  gram_reduce_body(part, chunks, l, W, (int)blockIdx.x);
 }
 
 cudaError_t launch_gram_reduce(const double* part, int chunks, int l, double* W, cudaStream_t st) {
@@ -579,10 +596,9 @@ cudaError_t launch_gram_reduce(const double* part, int chunks, int l, double* W,
 constexpr int CHOL_THREADS = 1024;
 
 template <typename TC>
-__global__ __launch_bounds__(CHOL_THREADS) void chol_shift_kernel(const double* __restrict__ W, int l,
-                                                                  double shift_coef, double tau_rel,
-                                                                  TC* __restrict__ Rinv, DevStatus* st_dev,
-                                                                  int stage, TC* gscr, int use_smem) {
+__device__ __forceinline__ void chol_shift_body(const double* __restrict__ W, int l, double shift_coef,
+                                                double tau_rel, TC* __restrict__ Rinv, DevStatus* st_dev, int stage,
+                                                TC* gscr, int use_smem) {
   extern __shared__ unsigned char smem_raw[];
   const int lda = l | 1;
   TC* M = use_smem ? reinterpret_cast<TC*>(smem_raw) : gscr;
@@ -679,6 +695,14 @@ __global__ __launch_bounds__(CHOL_THREADS) void chol_shift_kernel(const double* 
     }
 }
 
+template <typename TC>
+__global__ __launch_bounds__(CHOL_THREADS) void chol_shift_kernel(const double* __restrict__ W, int l,
+                                                                  double shift_coef, double tau_rel,
+                                                                  TC* __restrict__ Rinv, DevStatus* st_dev,
+                                                                  int stage, TC* gscr, int use_smem) {
+  chol_shift_body<TC>(W, l, shift_coef, tau_rel, Rinv, st_dev, stage, gscr, use_smem);
+}
+
 // The same elimination for l <= 64 with the augmented rows in registers:
 // 8 warps, thread (w, t) holds rows i = w + 8 r (r < 8) and the column slots
 // t, t + 32 of W and of L^{-1} (32 values).  Step k publishes row k through a
@@ -688,10 +712,8 @@ __global__ __launch_bounds__(CHOL_THREADS) void chol_shift_kernel(const double* 
 constexpr int CHOL64_THREADS = 256;
 
 template <typename TC>
-__global__ __launch_bounds__(CHOL64_THREADS, 1) void chol64_kernel(const double* __restrict__ W, int l,
-                                                                double shift_coef, double tau_rel,
-                                                                TC* __restrict__ Rinv, DevStatus* st_dev,
-                                                                int stage) {
+__device__ __forceinline__ void chol64_body(const double* __restrict__ W, int l, double shift_coef, double tau_rel,
+                                            TC* __restrict__ Rinv, DevStatus* st_dev, int stage) {
   __shared__ TC s_row[2][128];
   __shared__ TC s_odiag[64], s_scale[64];
   __shared__ double s_tr;
@@ -824,6 +846,14 @@ __global__ __launch_bounds__(CHOL64_THREADS, 1) void chol64_kernel(const double*
   }
 }
 
+template <typename TC>
+__global__ __launch_bounds__(CHOL64_THREADS, 1) void chol64_kernel(const double* __restrict__ W, int l,
+                                                                double shift_coef, double tau_rel,
+                                                                TC* __restrict__ Rinv, DevStatus* st_dev,
+                                                                int stage) {
+  chol64_body<TC>(W, l, shift_coef, tau_rel, Rinv, st_dev, stage);
+}
+
 int64_t chol_scratch_elems(int l) { return (int64_t)l * (l | 1); }
 
 template <typename TC>
@@ -860,9 +890,9 @@ bool apply_fuses_gram(int l) { return l <= 64; }
 
 // RS: R^{-1} staged in shared memory (else read through L1 from global).
 template <typename T, typename TC, int CT, int RT, bool RS>
-__global__ __launch_bounds__(256) void apply_rinv_kernel(const T* __restrict__ Y, int64_t ldy, int64_t M, int l,
-                                                         const TC* __restrict__ Rinv, T* Q, int64_t ldq,
-                                                         int transpose_out, double* part) {
+__device__ __forceinline__ void apply_rinv_body(const T* __restrict__ Y, int64_t ldy, int64_t M, int l,
+                                                const TC* __restrict__ Rinv, T* Q, int64_t ldq, int transpose_out,
+                                                double* part, int bx) {
   constexpr int LP = 16 * CT;      // padded column count
   constexpr int ROWS = 16 * RT;    // rows per CTA
   constexpr int LS = LP + 1;       // odd stride of the row tiles
@@ -871,7 +901,7 @@ __global__ __launch_bounds__(256) void apply_rinv_kernel(const T* __restrict__ Y
   T* Ys = Rs + (RS ? LP * LP : 0);         // ROWS x LS
   T* Qs = Ys + ROWS * LS;                  // ROWS x LS
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int64_t r0 = (int64_t)blockIdx.x * ROWS;
+  const int64_t r0 = (int64_t)bx * ROWS;
   const int rows = (int)(ROWS < M - r0 ? ROWS : M - r0);
   if (RS)
     for (int e = tid; e < LP * LP; e += 256) {
@@ -920,7 +950,7 @@ __global__ __launch_bounds__(256) void apply_rinv_kernel(const T* __restrict__ Y
   }
   if (part) {
     // Gram of the tile: thread (ty, tx) owns the CT x CT block (ty CT.., tx CT..), upper blocks only
-    double* P = part + (int64_t)blockIdx.x * l * l;
+    double* P = part + (int64_t)bx * l * l;
     if (tx >= ty) {
       for (int bi = 0; bi < CT; bi += 4)
         for (int bj = 0; bj < CT; bj += 4) {
@@ -953,6 +983,13 @@ __global__ __launch_bounds__(256) void apply_rinv_kernel(const T* __restrict__ Y
         }
     }
   }
+}
+
+template <typename T, typename TC, int CT, int RT, bool RS>
+__global__ __launch_bounds__(256) void apply_rinv_kernel(const T* __restrict__ Y, int64_t ldy, int64_t M, int l,
+                                                         const TC* __restrict__ Rinv, T* Q, int64_t ldq,
+                                                         int transpose_out, double* part) {
+  apply_rinv_body<T, TC, CT, RT, RS>(Y, ldy, M, l, Rinv, Q, ldq, transpose_out, part, (int)blockIdx.x);
 }
 
 template <typename T, typename TC>
@@ -990,5 +1027,122 @@ template cudaError_t launch_apply_rinv<float, float>(const float*, int64_t, int6
                                                      int64_t, int, double*, cudaStream_t);
 template cudaError_t launch_apply_rinv<float, double>(const float*, int64_t, int64_t, int, const double*, float*,
                                                       int64_t, int, double*, cudaStream_t);
+
+
+// ============================================================================
+// Batched forms: one launch for many problems (the sides of the pairs of a
+// grouped solve).  Argument tables live in device memory, one entry per
+// problem (blockIdx.z, or blockIdx.x for one CTA per problem); grids are sized
+// for the largest problem and the CTAs past a smaller problem's extent return
+// at once (uniformly per CTA, before any barrier).
+// ============================================================================
+__global__ void gaussian_kmajor_b_kernel(const GaussB* __restrict__ tab) {
+  const GaussB a = tab[blockIdx.z];
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i >= a.ldx || j >= a.lrows) return;
+  float v = 0.f;
+  if (i < a.n && j < a.l)
+    v = gaussian_at<float>(i * (int64_t)a.l + j, (uint32_t)a.seed, (uint32_t)(a.seed >> 32), a.pair, a.side,
+                           a.stream);
+  a.Xt[(int64_t)j * a.ldx + i] = v;
+}
+
+cudaError_t launch_gaussian_kmajor_b(const GaussB* tab, int nprob, int64_t max_ldx, int max_lrows, cudaStream_t st) {
+  if (nprob <= 0) return cudaSuccess;
+  gaussian_kmajor_b_kernel<<<dim3((unsigned)cdiv(max_ldx, 256), (unsigned)max_lrows, (unsigned)nprob), 256, 0, st>>>(tab);
+  return launched();
+}
+
+__global__ void reduce_splits_b_kernel(const ReduceB* __restrict__ tab) {
+  const ReduceB& a = tab[blockIdx.z];
+  if ((int64_t)blockIdx.x * blockDim.x >= a.n * a.l) return;
+  reduce_splits_body<float, float>(a.part, a.splits, a.n, a.l, a.lp, a.Z, a.ldz, a.transpose_out, a.sq_part,
+                                   (int)blockIdx.x);
+}
+
+cudaError_t launch_reduce_splits_b(const ReduceB* tab, int nprob, int64_t max_nl, cudaStream_t st) {
+  if (nprob <= 0) return cudaSuccess;
+  reduce_splits_b_kernel<<<dim3((unsigned)cdiv(max_nl, 256), 1, (unsigned)nprob), 256, 0, st>>>(tab);
+  return launched();
+}
+
+__global__ __launch_bounds__(256) void gram_partial_b_kernel(const GramB* __restrict__ tab, int tdim) {
+  const GramB& a = tab[blockIdx.z];
+  const int ti = (int)blockIdx.y / tdim, tj = (int)blockIdx.y % tdim;
+  const int t = (a.l + GR_T - 1) / GR_T;
+  if ((int)blockIdx.x >= a.chunks || ti >= t || tj >= t || ti > tj) return;
+  gram_partial_body<float>(a.Y, a.ldy, a.M, a.l, a.part, a.rpc, (int)blockIdx.x, ti, tj);
+}
+
+cudaError_t launch_gram_partial_b(const GramB* tab, int nprob, int max_chunks, int max_l, cudaStream_t st) {
+  if (nprob <= 0) return cudaSuccess;
+  const int t = (int)cdiv(max_l, GR_T);
+  gram_partial_b_kernel<<<dim3((unsigned)max_chunks, (unsigned)(t * t), (unsigned)nprob), 256, 0, st>>>(tab, t);
+  return launched();
+}
+
+__global__ void gram_reduce_b_kernel(const GramRedB* __restrict__ tab) {
+  const GramRedB& a = tab[blockIdx.z];
+  if ((((int64_t)blockIdx.x * blockDim.x) >> 5) >= (int64_t)a.l * a.l) return;
+  gram_reduce_body(a.part, a.chunks, a.l, a.W, (int)blockIdx.x);
+}
+
+cudaError_t launch_gram_reduce_b(const GramRedB* tab, int nprob, int max_l, cudaStream_t st) {
+  if (nprob <= 0) return cudaSuccess;
+  const int64_t threads = (int64_t)max_l * max_l * 32;
+  gram_reduce_b_kernel<<<dim3((unsigned)cdiv(threads, 256), 1, (unsigned)nprob), 256, 0, st>>>(tab);
+  return launched();
+}
+
+__global__ __launch_bounds__(CHOL64_THREADS, 1) void chol64_b_kernel(const CholB* __restrict__ tab) {
+  const CholB& a = tab[blockIdx.x];
+  chol64_body<float>(a.W, a.l, a.shift_coef, a.tau_rel, a.Rinv, a.st, a.stage);
+}
+
+__global__ __launch_bounds__(CHOL_THREADS) void chol_shift_b_kernel(const CholB* __restrict__ tab) {
+  const CholB& a = tab[blockIdx.x];
+  chol_shift_body<float>(a.W, a.l, a.shift_coef, a.tau_rel, a.Rinv, a.st, a.stage, nullptr, 1);
+}
+
+cudaError_t launch_chol_b(const CholB* tab, int nprob, int max_l, cudaStream_t st) {
+  if (nprob <= 0) return cudaSuccess;
+  if (max_l < 1 || max_l > 128) return cudaErrorInvalidValue;
+  if (max_l <= 64) {
+    chol64_b_kernel<<<nprob, CHOL64_THREADS, 0, st>>>(tab);
+    return launched();
+  }
+  const size_t smem = (size_t)chol_scratch_elems(max_l) * sizeof(float);
+  cudaFuncSetAttribute(chol_shift_b_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 216 * 1024);
+  chol_shift_b_kernel<<<nprob, CHOL_THREADS, smem, st>>>(tab);
+  return launched();
+}
+
+template <int CT, int RT>
+__global__ __launch_bounds__(256) void apply_rinv_b_kernel(const ApplyB* __restrict__ tab) {
+  const ApplyB& a = tab[blockIdx.z];
+  if ((int64_t)blockIdx.x * (16 * RT) >= a.M) return;
+  apply_rinv_body<float, float, CT, RT, true>(a.Y, a.ldy, a.M, a.l, a.Rinv, a.Q, a.ldq, a.transpose_out, nullptr,
+                                              (int)blockIdx.x);
+}
+
+int64_t apply_b_rows(int max_l) { return max_l <= 64 ? 128 : 32; }
+
+cudaError_t launch_apply_rinv_b(const ApplyB* tab, int nprob, int64_t max_M, int max_l, cudaStream_t st) {
+  if (nprob <= 0) return cudaSuccess;
+  if (max_l < 1 || max_l > 128) return cudaErrorInvalidValue;
+  const int ct = max_l <= 64 ? 4 : 8, rt = max_l <= 64 ? 8 : 2;
+  const int lp = 16 * ct, rows = 16 * rt;
+  const size_t smem = 2 * (size_t)rows * (lp + 1) * sizeof(float) + (size_t)lp * lp * sizeof(float);
+  const dim3 grid((unsigned)cdiv(max_M, rows), 1, (unsigned)nprob);
+  if (ct == 4) {
+    cudaFuncSetAttribute(apply_rinv_b_kernel<4, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    apply_rinv_b_kernel<4, 8><<<grid, 256, smem, st>>>(tab);
+  } else {
+    cudaFuncSetAttribute(apply_rinv_b_kernel<8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    apply_rinv_b_kernel<8, 2><<<grid, 256, smem, st>>>(tab);
+  }
+  return launched();
+}
 
 }  // namespace gsvdr

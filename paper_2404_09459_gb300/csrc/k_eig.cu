@@ -345,9 +345,8 @@ __device__ __forceinline__ float pick(const float (&a)[R][C], int r, int c) {
 }
 }  // namespace
 
-__global__ __launch_bounds__(1024) void eig128_kernel(const double* __restrict__ Ain, int N,
-                                                      double* __restrict__ Xout, double* __restrict__ lam,
-                                                      float* __restrict__ Ug, float noise_rel) {
+__device__ __forceinline__ void eig128_body(const double* __restrict__ Ain, int N, double* __restrict__ Xout,
+                                            double* __restrict__ lam, float* __restrict__ Ug, float noise_rel) {
   extern __shared__ float esm[];
   __shared__ float s_d[E_NMAX], s_e[E_NMAX], s_beta[E_NMAX], s_col[2][E_NMAX], s_p[E_NMAX], s_lam[E_NMAX];
   __shared__ float2 s_de[E_NMAX];
@@ -776,9 +775,9 @@ __device__ __forceinline__ int pk(int i, int j) { return ((i * (i + 1)) >> 1) + 
 
 int64_t eig_big_scratch_floats(int N) { return 4ll * N * N + (int64_t)N * (N + 1) / 2 + 64; }
 
-__global__ __launch_bounds__(1024) void eig_big_kernel(const double* __restrict__ Ain, int N,
-                                                       double* __restrict__ Xout, double* __restrict__ lam,
-                                                       float* __restrict__ gscr, float noise_rel, int ap_smem) {
+__device__ __forceinline__ void eig_big_body(const double* __restrict__ Ain, int N, double* __restrict__ Xout,
+                                             double* __restrict__ lam, float* __restrict__ gscr, float noise_rel,
+                                             int ap_smem) {
   extern __shared__ float ebsm[];
   __shared__ float s_d[EB_NMAX], s_e[EB_NMAX], s_beta[EB_NMAX], s_v[EB_NMAX], s_p[EB_NMAX], s_lam[EB_NMAX];
   __shared__ float s_cf[EB_NMAX], s_flag[EB_NMAX];
@@ -1154,6 +1153,43 @@ __global__ __launch_bounds__(1024) void eig_big_kernel(const double* __restrict_
       if (i < N) Xout[(int64_t)i * N + j] = (double)z[r];
     }
   }
+}
+
+__global__ __launch_bounds__(1024) void eig128_kernel(const double* __restrict__ Ain, int N,
+                                                      double* __restrict__ Xout, double* __restrict__ lam,
+                                                      float* __restrict__ Ug, float noise_rel) {
+  eig128_body(Ain, N, Xout, lam, Ug, noise_rel);
+}
+
+__global__ __launch_bounds__(1024) void eig_big_kernel(const double* __restrict__ Ain, int N,
+                                                       double* __restrict__ Xout, double* __restrict__ lam,
+                                                       float* __restrict__ gscr, float noise_rel, int ap_smem) {
+  eig_big_body(Ain, N, Xout, lam, gscr, noise_rel, ap_smem);
+}
+
+// Batched: one CTA per problem (the grouped solve's compressed pairs).
+__global__ __launch_bounds__(1024) void eig128_b_kernel(const EigB* __restrict__ tab) {
+  const EigB& a = tab[blockIdx.x];
+  eig128_body(a.A, a.N, a.X, a.lam, a.scratch, a.noise_rel);
+}
+__global__ __launch_bounds__(1024) void eig_big_b_kernel(const EigB* __restrict__ tab) {
+  const EigB& a = tab[blockIdx.x];
+  eig_big_body(a.A, a.N, a.X, a.lam, a.scratch, a.noise_rel, 1);
+}
+
+cudaError_t launch_eig_f32_b(const EigB* tab, int nprob, int max_N, cudaStream_t st) {
+  if (nprob <= 0) return cudaSuccess;
+  if (max_N < 1 || max_N > EB_SMEM_NMAX) return cudaErrorInvalidValue;
+  if (max_N <= E_NMAX) {
+    const size_t smem = ((size_t)max_N * E_NMAX + 2 * (size_t)max_N * (max_N | 1)) * sizeof(float);
+    cudaFuncSetAttribute(eig128_b_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    eig128_b_kernel<<<nprob, 1024, smem, st>>>(tab);
+    return launched();
+  }
+  const size_t smem = (size_t)max_N * (max_N + 1) / 2 * sizeof(float);
+  cudaFuncSetAttribute(eig_big_b_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 202 * 1024);
+  eig_big_b_kernel<<<nprob, 1024, smem, st>>>(tab);
+  return launched();
 }
 
 cudaError_t launch_eig_f32(const double* A, int N, double* X, double* lam, float* scratch, cudaStream_t st,

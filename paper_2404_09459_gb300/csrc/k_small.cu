@@ -10,6 +10,7 @@
 //     "Iterative refinement for symmetric eigenvalue decomposition", Japan J.
 //     Indust. Appl. Math. 35, 2018), whose work is FP64 GEMMs again.
 #include <algorithm>
+#include <cstring>
 
 #include "kernels.h"
 
@@ -368,11 +369,10 @@ cudaError_t launch_oa_refine(const double* A, int N, double* X, double* lam, dou
 // ============================================================================
 constexpr int CUT_CMAX = 128;
 
-__global__ __launch_bounds__(1024) void oa_cut_cluster_kernel(int N, int r, const double* __restrict__ XtX,
-                                                              const double* __restrict__ S,
-                                                              const double* __restrict__ part, int nparts,
-                                                              const double* __restrict__ lam,
-                                                              double* __restrict__ Vc, int* __restrict__ cinfo) {
+__device__ __forceinline__ void oa_cut_cluster_body(int N, int r, const double* __restrict__ XtX,
+                                                    const double* __restrict__ S, const double* __restrict__ part,
+                                                    int nparts, const double* __restrict__ lam,
+                                                    double* __restrict__ Vc, int* __restrict__ cinfo) {
   extern __shared__ float cut_sm[];
   __shared__ int s_ord[512];
   __shared__ int s_lo, s_c;
@@ -511,13 +511,20 @@ __global__ __launch_bounds__(1024) void oa_cut_cluster_kernel(int N, int r, cons
   for (int e = tid; e < c * c; e += nt) Vc[e] = (double)V[(e / c) * lda + e % c];
 }
 
+__global__ __launch_bounds__(1024) void oa_cut_cluster_kernel(int N, int r, const double* __restrict__ XtX,
+                                                              const double* __restrict__ S,
+                                                              const double* __restrict__ part, int nparts,
+                                                              const double* __restrict__ lam,
+                                                              double* __restrict__ Vc, int* __restrict__ cinfo) {
+  oa_cut_cluster_body(N, r, XtX, S, part, nparts, lam, Vc, cinfo);
+}
+
 // X[:, idx] <- X[:, idx] V_c, one CTA per row of X.
-__global__ __launch_bounds__(128) void cut_rotate_kernel(int N, double* __restrict__ X, const double* __restrict__ Vc,
-                                                         const int* __restrict__ cinfo) {
+__device__ __forceinline__ void cut_rotate_body(int N, double* __restrict__ X, const double* __restrict__ Vc,
+                                                const int* __restrict__ cinfo, int i) {
   __shared__ double row[CUT_CMAX];
   const int c = cinfo[0];
   if (c < 2) return;
-  const int i = blockIdx.x;
   for (int b = threadIdx.x; b < c; b += blockDim.x) row[b] = X[(int64_t)i * N + cinfo[1 + b]];
   __syncthreads();
   for (int a = threadIdx.x; a < c; a += blockDim.x) {
@@ -525,6 +532,11 @@ __global__ __launch_bounds__(128) void cut_rotate_kernel(int N, double* __restri
     for (int b = 0; b < c; ++b) t += row[b] * Vc[(int64_t)b * c + a];
     X[(int64_t)i * N + cinfo[1 + a]] = t;
   }
+}
+
+__global__ __launch_bounds__(128) void cut_rotate_kernel(int N, double* __restrict__ X, const double* __restrict__ Vc,
+                                                         const int* __restrict__ cinfo) {
+  cut_rotate_body(N, X, Vc, cinfo, (int)blockIdx.x);
 }
 
 cudaError_t launch_oa_cut_cluster(int N, int r, double* X, const double* lam, double* work, int64_t work_elems,
@@ -556,8 +568,8 @@ cudaError_t launch_oa_cut_cluster(int N, int r, double* X, const double* lam, do
 // so the ranks below always form a permutation of 0..N-1.
 __device__ __forceinline__ double sort_key(double x) { return isnan(x) ? -INFINITY : x; }
 
-__global__ void select_topr_kernel(const double* __restrict__ X, const double* __restrict__ lam, int N,
-                                   int r, double* __restrict__ Zr, int* __restrict__ order) {
+__device__ __forceinline__ void select_topr_body(const double* __restrict__ X, const double* __restrict__ lam, int N,
+                                                 int r, double* __restrict__ Zr, int* __restrict__ order) {
   extern __shared__ int s_ord[];
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int i = tid; i < N; i += nt) {
@@ -578,6 +590,11 @@ __global__ void select_topr_kernel(const double* __restrict__ X, const double* _
   }
 }
 
+__global__ void select_topr_kernel(const double* __restrict__ X, const double* __restrict__ lam, int N,
+                                   int r, double* __restrict__ Zr, int* __restrict__ order) {
+  select_topr_body(X, lam, N, r, Zr, order);
+}
+
 cudaError_t launch_select_topr(const double* X, const double* lam, int N, int r, double* Zr, int* order,
                                cudaStream_t st) {
   select_topr_kernel<<<1, 512, (size_t)N * sizeof(int), st>>>(X, lam, N, r, Zr, order);
@@ -586,8 +603,8 @@ cudaError_t launch_select_topr(const double* X, const double* lam, int N, int r,
 
 // alpha_i = ||U1[:, i]||, beta_i = ||U2[:, i]|| (U1 = Z1 W, U2 = Z2 W), normalised to
 // alpha^2 + beta^2 = 1, sorted by alpha non-increasing (eq. (ab)).
-__global__ void cs_norms_kernel(const double* __restrict__ U1, int l1, const double* __restrict__ U2, int l2,
-                                int r, double* __restrict__ alpha, double* __restrict__ beta) {
+__device__ __forceinline__ void cs_norms_body(const double* __restrict__ U1, int l1, const double* __restrict__ U2,
+                                              int l2, int r, double* __restrict__ alpha, double* __restrict__ beta) {
   extern __shared__ double sab[];
   double* sa = sab;
   double* sb = sab + r;
@@ -612,6 +629,11 @@ __global__ void cs_norms_kernel(const double* __restrict__ U1, int l1, const dou
     alpha[rank] = sa[i];
     beta[rank] = sb[i];
   }
+}
+
+__global__ void cs_norms_kernel(const double* __restrict__ U1, int l1, const double* __restrict__ U2, int l2,
+                                int r, double* __restrict__ alpha, double* __restrict__ beta) {
+  cs_norms_body(U1, l1, U2, l2, r, alpha, beta);
 }
 
 cudaError_t launch_cs_norms(const double* U1, int l1, const double* U2, int l2, int r, double* alpha,
@@ -733,6 +755,248 @@ __global__ void residual_kernel(const double* gpart, int ng, const double* bpart
 cudaError_t launch_residual(const double* gpart, int ng, const double* bpart, int nb, double* out,
                             cudaStream_t st) {
   residual_kernel<<<1, 32, 0, st>>>(gpart, ng, bpart, nb, out);
+  return launched();
+}
+
+
+// ============================================================================
+// Batched forms for the compressed-pair GSVDs of a grouped solve: one launch
+// per step for all pairs (tables in device memory, see kernels.h).
+// ============================================================================
+template <typename TA, typename TB>
+__global__ __launch_bounds__(256) void dgemm_b_kernel(const DgemmB* __restrict__ tab) {
+  const DgemmB& g = tab[blockIdx.z];
+  const int i0 = blockIdx.x * SG_T, j0 = blockIdx.y * SG_T;
+  if (i0 >= g.Mr || j0 >= g.Nc) return;
+  __shared__ double As[SG_BK][SG_T + 1];
+  __shared__ double Bs[SG_BK][SG_T + 1];
+  const TA* __restrict__ A = static_cast<const TA*>(g.A);
+  const TB* __restrict__ B = static_cast<const TB*>(g.B);
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int K = g.K, ta = g.ta, tb = g.tb;
+  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  for (int k0 = 0; k0 < K; k0 += SG_BK) {
+    for (int e = tid; e < SG_T * SG_BK; e += 256) {
+      const int a = e / 32, b = e % 32;
+      int i, kk;
+      if (!ta) { i = a; kk = b; } else { kk = a; i = b; }
+      int gi = i0 + i, gk = k0 + kk;
+      As[kk][i] = (gi < g.Mr && gk < K) ? (double)(ta ? A[(int64_t)gk * g.lda + gi] : A[(int64_t)gi * g.lda + gk]) : 0.0;
+      int j;
+      if (!tb) { kk = a; j = b; } else { j = a; kk = b; }
+      const int gj = j0 + j;
+      gk = k0 + kk;
+      Bs[kk][j] = (gj < g.Nc && gk < K) ? (double)(tb ? B[(int64_t)gj * g.ldb + gk] : B[(int64_t)gk * g.ldb + gj]) : 0.0;
+    }
+    __syncthreads();
+    const int kk_end = min(SG_BK, K - k0);
+#pragma unroll 8
+    for (int kk = 0; kk < kk_end; ++kk) {
+      const double a0 = As[kk][ty * 2], a1 = As[kk][ty * 2 + 1];
+      const double b0 = Bs[kk][tx * 2], b1 = Bs[kk][tx * 2 + 1];
+      acc[0][0] = fma(a0, b0, acc[0][0]);
+      acc[0][1] = fma(a0, b1, acc[0][1]);
+      acc[1][0] = fma(a1, b0, acc[1][0]);
+      acc[1][1] = fma(a1, b1, acc[1][1]);
+    }
+    __syncthreads();
+  }
+  for (int m = 0; m < 2; ++m)
+    for (int q = 0; q < 2; ++q) {
+      const int i = i0 + ty * 2 + m, j = j0 + tx * 2 + q;
+      if (i < g.Mr && j < g.Nc) {
+        double* c = g.C + (int64_t)i * g.ldc + j;
+        *c = g.beta == 0.0 ? g.alpha * acc[m][q] : g.alpha * acc[m][q] + g.beta * (*c);
+      }
+    }
+}
+
+template <typename TA, typename TB>
+cudaError_t launch_dgemm_b(const DgemmB* tab, int nprob, int max_Mr, int max_Nc, cudaStream_t st) {
+  if (nprob <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)cdiv(max_Mr, SG_T), (unsigned)cdiv(max_Nc, SG_T), (unsigned)nprob);
+  dgemm_b_kernel<TA, TB><<<grid, 256, 0, st>>>(tab);
+  return launched();
+}
+template cudaError_t launch_dgemm_b<float, float>(const DgemmB*, int, int, int, cudaStream_t);
+template cudaError_t launch_dgemm_b<double, double>(const DgemmB*, int, int, int, cudaStream_t);
+
+// Frobenius sums of A, R = I - X^T X and S - diag(lam) (part[0..2]) and lam, one CTA per problem.
+__global__ __launch_bounds__(256) void oa_norms_b_kernel(const OaB* __restrict__ tab) {
+  const OaB& o = tab[blockIdx.x];
+  __shared__ double red[3][8];
+  const int N = o.N;
+  const int64_t nn = (int64_t)N * N;
+  double a2 = 0.0, r2 = 0.0, s2 = 0.0;
+  for (int64_t e = threadIdx.x; e < nn; e += blockDim.x) {
+    const int i = (int)(e / N), j = (int)(e % N);
+    const double a = o.A[e];
+    const double r = (i == j ? 1.0 : 0.0) - o.XtX[e];
+    double sd = o.S[e];
+    if (i == j) sd -= o.S[e] / o.XtX[e];
+    a2 += a * a;
+    r2 += r * r;
+    s2 += sd * sd;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    a2 += __shfl_down_sync(0xffffffffu, a2, off);
+    r2 += __shfl_down_sync(0xffffffffu, r2, off);
+    s2 += __shfl_down_sync(0xffffffffu, s2, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = a2;
+    red[1][threadIdx.x >> 5] = r2;
+    red[2][threadIdx.x >> 5] = s2;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[threadIdx.x][w];
+    o.part[threadIdx.x] = t;
+  }
+  for (int i = threadIdx.x; i < N; i += blockDim.x) o.lam[i] = o.S[(int64_t)i * N + i] / o.XtX[(int64_t)i * N + i];
+}
+
+// F as in oa_form_kernel, delta from the three sums.
+__global__ void oa_form_b_kernel(const OaB* __restrict__ tab) {
+  const OaB& o = tab[blockIdx.z];
+  const int N = o.N;
+  const int64_t nn = (int64_t)N * N;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nn) return;
+  const double delta = 2.0 * (sqrt(o.part[2]) + sqrt(o.part[0]) * sqrt(o.part[1]));
+  const int i = (int)(e / N), j = (int)(e % N);
+  const double r = (i == j ? 1.0 : 0.0) - o.XtX[e];
+  double f;
+  if (i == j) {
+    f = 0.5 * r;
+  } else {
+    const double d = o.lam[j] - o.lam[i];
+    f = (fabs(d) > delta) ? (o.S[e] + o.lam[j] * r) / d : 0.5 * r;
+  }
+  o.F[e] = f;
+}
+
+// X += P (P = X F of the step).
+__global__ void oa_update_b_kernel(const OaB* __restrict__ tab) {
+  const OaB& o = tab[blockIdx.z];
+  const int64_t nn = (int64_t)o.N * o.N;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < nn) o.X[e] += o.P[e];
+}
+
+void oa_b_tables(const OaB* h, int nprob, DgemmB* dg) {
+  for (int i = 0; i < nprob; ++i) {
+    const OaB& o = h[i];
+    const int N = o.N;
+    auto mk = [&](const double* A, int ta, const double* B, int tb, double* C) {
+      DgemmB g;
+      memset(&g, 0, sizeof(g));
+      g.A = A;
+      g.B = B;
+      g.C = C;
+      g.lda = g.ldb = g.ldc = N;
+      g.alpha = 1.0;
+      g.beta = 0.0;
+      g.Mr = g.Nc = g.K = N;
+      g.ta = ta;
+      g.tb = tb;
+      return g;
+    };
+    dg[i] = mk(o.X, 1, o.X, 0, o.XtX);               // X^T X
+    dg[nprob + i] = mk(o.A, 0, o.X, 0, o.P);         // A X
+    dg[2 * nprob + i] = mk(o.X, 1, o.P, 0, o.S);     // X^T (A X)
+    dg[3 * nprob + i] = mk(o.X, 0, o.F, 0, o.P);     // X F
+  }
+}
+
+cudaError_t launch_oa_refine_b(const OaB* tab, const DgemmB* dg, int nprob, int max_N, cudaStream_t st) {
+  if (nprob <= 0) return cudaSuccess;
+  cudaError_t e;
+  for (int k = 0; k < 3; ++k)
+    if ((e = launch_dgemm_b<double, double>(dg + (int64_t)k * nprob, nprob, max_N, max_N, st))) return e;
+  oa_norms_b_kernel<<<nprob, 256, 0, st>>>(tab);
+  if ((e = launched())) return e;
+  const dim3 g2((unsigned)cdiv((int64_t)max_N * max_N, 256), 1, (unsigned)nprob);
+  oa_form_b_kernel<<<g2, 256, 0, st>>>(tab);
+  if ((e = launched())) return e;
+  if ((e = launch_dgemm_b<double, double>(dg + 3ll * nprob, nprob, max_N, max_N, st))) return e;
+  oa_update_b_kernel<<<g2, 256, 0, st>>>(tab);
+  return launched();
+}
+
+// Cut cluster of each problem (XtX and S of the step just taken; V_c in F, the
+// cluster's indices in P), then the rotation of its columns of X.
+__global__ __launch_bounds__(1024) void oa_cut_cluster_b_kernel(const OaB* __restrict__ tab) {
+  const OaB& o = tab[blockIdx.x];
+  oa_cut_cluster_body(o.N, o.r, o.XtX, o.S, o.part, 1, o.lam, o.F, reinterpret_cast<int*>(o.P));
+}
+__global__ __launch_bounds__(128) void cut_rotate_b_kernel(const OaB* __restrict__ tab) {
+  const OaB& o = tab[blockIdx.z];
+  if ((int)blockIdx.x >= o.N) return;
+  cut_rotate_body(o.N, o.X, o.F, reinterpret_cast<const int*>(o.P), (int)blockIdx.x);
+}
+
+cudaError_t launch_oa_cut_cluster_b(const OaB* tab, int nprob, int max_N, cudaStream_t st) {
+  if (nprob <= 0) return cudaSuccess;
+  if (max_N > 512) return cudaErrorInvalidValue;
+  const int cmax = std::min(max_N, CUT_CMAX);
+  const size_t smem = (size_t)2 * cmax * (cmax | 1) * sizeof(float);
+  cudaFuncSetAttribute(oa_cut_cluster_b_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)(2 * CUT_CMAX * (CUT_CMAX | 1) * sizeof(float)));
+  oa_cut_cluster_b_kernel<<<nprob, 1024, smem, st>>>(tab);
+  cudaError_t e = launched();
+  if (e) return e;
+  cut_rotate_b_kernel<<<dim3((unsigned)max_N, 1, (unsigned)nprob), 128, 0, st>>>(tab);
+  return launched();
+}
+
+__global__ void select_topr_b_kernel(const SelB* __restrict__ tab) {
+  const SelB& a = tab[blockIdx.x];
+  select_topr_body(a.X, a.lam, a.N, a.r, a.Zr, a.order);
+}
+
+cudaError_t launch_select_topr_b(const SelB* tab, int nprob, int max_N, cudaStream_t st) {
+  if (nprob <= 0) return cudaSuccess;
+  select_topr_b_kernel<<<nprob, 512, (size_t)max_N * sizeof(int), st>>>(tab);
+  return launched();
+}
+
+__global__ void cs_norms_b_kernel(const CsB* __restrict__ tab) {
+  const CsB& a = tab[blockIdx.x];
+  cs_norms_body(a.U1, a.l1, a.U2, a.l2, a.r, a.alpha, a.beta);
+}
+
+cudaError_t launch_cs_norms_b(const CsB* tab, int nprob, int max_r, cudaStream_t st) {
+  if (nprob <= 0) return cudaSuccess;
+  cs_norms_b_kernel<<<nprob, 256, (size_t)2 * max_r * sizeof(double), st>>>(tab);
+  return launched();
+}
+
+__global__ void residual_b_kernel(const ResidB* __restrict__ tab, int nprob) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nprob) return;
+  const ResidB& a = tab[i];
+  double g = 0.0, b = 0.0;
+  for (int t = 0; t < a.ng; ++t) g += a.gpart[t];
+  for (int t = 0; t < a.nb; ++t) b += a.bpart[t];
+  *a.out = g > 0.0 ? sqrt(fmax(g - b, 0.0) / g) : 0.0;
+}
+
+cudaError_t launch_residual_b(const ResidB* tab, int nprob, cudaStream_t st) {
+  if (nprob <= 0) return cudaSuccess;
+  residual_b_kernel<<<(unsigned)cdiv(nprob, 128), 128, 0, st>>>(tab, nprob);
+  return launched();
+}
+
+__global__ void scatter_b_kernel(const ScatterB* __restrict__ tab) {
+  const ScatterB& a = tab[blockIdx.x];
+  for (int i = threadIdx.x; i < a.count; i += blockDim.x) a.dst[i] = a.src[i];
+}
+
+cudaError_t launch_scatter_b(const ScatterB* tab, int n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  scatter_b_kernel<<<n, 128, 0, st>>>(tab);
   return launched();
 }
 

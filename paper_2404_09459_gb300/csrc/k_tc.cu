@@ -18,11 +18,24 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstring>
+#include <vector>
 
 #include "kernels.h"
 #include "tc.h"
 
 namespace gsvdr {
+
+// One problem of a grouped product, in device memory (the tensor maps must be
+// 64-byte aligned there).
+struct TcGroupProb {  // CUtensorMap members carry their own (>= 64-byte) alignment
+  CUtensorMap mapA;   // G: row tiles (GX) or unswizzled 32 x 32 boxes (GTQ)
+  CUtensorMap mapB;   // K-major B operand: X^T (GX) or Q^T (GTQ)
+  float* out;         // Y (GX) or the split partials (GTQ)
+  int64_t ldo, out_rows, kdim, rows_per_split, split_stride;
+  double* gnorm_part; // GX with the fused norm: 4 partial sums of G^2 per row tile
+  int ncols, nmma, tiles_x, pad;
+};
 
 namespace {
 
@@ -716,6 +729,408 @@ cudaError_t tc_gemm_gtq_bf16(const void* G, int64_t ldg, int64_t M, int64_t n, c
   else
     launch_tc<1, false, false, 2>(grid, smem, st, ma, mb, part, lp, n, l, nmma, M, rps, n * lp, stages, nullptr,
                                   st_dev);
+  return launched();
+}
+
+
+// ---------------------------------------------------------------------------
+// Grouped persistent products: many independent problems (the sides of many
+// pairs) in one launch.  The host writes one TcGroupProb per problem (with its
+// own tensor maps) and a tile list into device memory; CTA b takes tiles
+// b, b + grid, b + 2 grid, ... of the list (sorted longest first), so the
+// roles below walk the same sequence and their pipeline counters agree.
+//
+// Warp roles (10 warps): 0 TMA, 1 MMA (one thread), 2-5 operand preparation
+// (3xTF32 low halves, the G^T transpose, the sum of G^2), 6-9 accumulator
+// drain.  The accumulator is double-buffered in tensor memory, so the drain
+// of one tile overlaps the MMAs of the next.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int TG_THREADS = 320;
+
+template <int MODE, bool NORM, bool SPLIT>
+__global__ __launch_bounds__(TG_THREADS) void tc_group_kernel(const TcGroupProb* __restrict__ probs,
+                                                              const int2* __restrict__ tiles, int ntiles,
+                                                              int nmma_max, int acc_stride, int tmem_cols,
+                                                              int stages, DevStatus* st_glob) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  constexpr int EB = 4, BKE = 32;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const StageLayout L(MODE, SPLIT, nmma_max, EB);
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + (size_t)stages * L.bytes);
+  uint64_t* empty = full + stages;
+  uint64_t* tfull = empty + stages;
+  uint64_t* tmfull = tfull + stages;  // [2] accumulator ready (MMA commit)
+  uint64_t* tmempty = tmfull + 2;     // [2] accumulator drained (4 drain warps)
+  uint64_t* fin = tmempty + 2;        // every MMA of this CTA complete
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
+  constexpr bool TRANSPOSE = MODE == 1;
+  constexpr bool PREP = TRANSPOSE || SPLIT;
+  constexpr bool EPI_STAGE = PREP || NORM;
+  __shared__ int s_abort;
+
+  if (tid == 0) {
+    s_abort = 0;
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], EPI_STAGE ? 5 : 1);
+      mbar_init(&tfull[s], 4);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tmfull[a], 1);
+      mbar_init(&tmempty[a], 4);
+    }
+    mbar_init(fin, 1);
+    fence_barrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, (uint32_t)tmem_cols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  volatile int* abort_flag = &s_abort;
+
+  // the k range of a tile
+  auto krange = [&](const TcGroupProb& P, int t, int64_t& kb, int64_t& ke, int& t0) {
+    if (MODE == 0) {
+      kb = 0;
+      ke = P.kdim;
+      t0 = t * TC_BM;
+    } else {
+      const int z = t / P.tiles_x;
+      t0 = (t - z * P.tiles_x) * TC_BM;
+      kb = (int64_t)z * P.rows_per_split;
+      ke = min(P.kdim, kb + P.rows_per_split);
+    }
+  };
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      uint32_t it = 0, issued = 0;
+      for (int ti = blockIdx.x; ti < ntiles && !*abort_flag; ti += gridDim.x) {
+        const int2 tr = tiles[ti];
+        const TcGroupProb& P = probs[tr.x];
+        int64_t kb, ke;
+        int t0;
+        krange(P, tr.y, kb, ke, t0);
+        const int kt_n = (int)((ke - kb + BKE - 1) / BKE);
+        const uint32_t b_bytes = (uint32_t)P.nmma * 128u;
+        for (int kt = 0; kt < kt_n; ++kt, ++it) {
+          const int s = (int)(it % (uint32_t)stages);
+          const uint32_t ph = (it / (uint32_t)stages) & 1u;
+          if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) break;
+          ++issued;
+          uint8_t* st = base + (size_t)s * L.bytes;
+          mbar_expect_tx(&full[s], (uint32_t)TC_A_BYTES + b_bytes);
+          const int k0 = (int)(kb + (int64_t)kt * BKE);
+          if (MODE == 0) {
+            tma_load_2d(st + L.a, &P.mapA, &full[s], k0, t0);
+          } else {
+#pragma unroll
+            for (int q = 0; q < 128 / BKE; ++q) tma_load_2d(st + L.a + q * (BKE * 128), &P.mapA, &full[s], t0 + BKE * q, k0);
+          }
+          tma_load_2d(st + L.b, &P.mapB, &full[s], k0, 0);
+        }
+      }
+      if (*abort_flag) {
+        // wait (bounded) until the copies this thread issued have landed
+        const uint32_t first = issued > (uint32_t)stages ? issued - (uint32_t)stages : 0u;
+        for (uint32_t j = first; j < issued; ++j) {
+          volatile int none = 0;
+          mbar_wait(&full[j % (uint32_t)stages], (j / (uint32_t)stages) & 1u, &none);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      uint32_t it = 0;
+      int j = 0;
+      for (int ti = blockIdx.x; ti < ntiles && !*abort_flag; ti += gridDim.x, ++j) {
+        const int2 tr = tiles[ti];
+        const TcGroupProb& P = probs[tr.x];
+        int64_t kb, ke;
+        int t0;
+        krange(P, tr.y, kb, ke, t0);
+        const int kt_n = (int)((ke - kb + BKE - 1) / BKE);
+        const int acc = j & 1;
+        if (j >= 2 && !mbar_wait(&tmempty[acc], (uint32_t)((j >> 1) + 1) & 1u, abort_flag)) break;
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(acc * acc_stride);
+        const uint32_t idesc = idesc_tf32(TC_BM, (uint32_t)P.nmma, 0u, 0u);
+        bool ok = true;
+        for (int kt = 0; kt < kt_n; ++kt, ++it) {
+          const int s = (int)(it % (uint32_t)stages);
+          const uint32_t ph = (it / (uint32_t)stages) & 1u;
+          if (!mbar_wait(PREP ? &tfull[s] : &full[s], ph, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t st = smem_u32(base + (size_t)s * L.bytes);
+#pragma unroll
+          for (int ks = 0; ks < 128 / TC_KSTEP_BYTES; ++ks) {
+            const uint64_t adesc = smem_desc(st + L.ak + ks * TC_KSTEP_BYTES, 16, 1024);
+            const uint64_t bdesc = smem_desc(st + L.b + ks * TC_KSTEP_BYTES, 16, 1024);
+            mma_tf32(d, adesc, bdesc, idesc, (kt > 0 || ks > 0) ? 1u : 0u);
+            if (SPLIT) {
+              mma_tf32(d, smem_desc(st + L.alo + ks * TC_KSTEP_BYTES, 16, 1024), bdesc, idesc, 1u);
+              mma_tf32(d, adesc, smem_desc(st + L.blo + ks * TC_KSTEP_BYTES, 16, 1024), idesc, 1u);
+            }
+          }
+          mma_commit(&empty[s]);
+        }
+        if (!ok) break;
+        mma_commit(&tmfull[acc]);
+      }
+      // arrives once every MMA issued above has completed: none is in flight when the
+      // tensor memory is freed
+      mma_commit(fin);
+      volatile int none = 0;
+      mbar_wait(fin, 0, &none);
+    }
+  } else if (warp < 6) {
+    // ---------------- operand preparation (warps 2-5) ----------------
+    if (EPI_STAGE) {
+      const int et = tid - 64;  // 0..127
+      const int q = warp - 2;
+      uint32_t it = 0;
+      for (int ti = blockIdx.x; ti < ntiles && !*abort_flag; ti += gridDim.x) {
+        const int2 tr = tiles[ti];
+        const TcGroupProb& P = probs[tr.x];
+        int64_t kb, ke;
+        int t0;
+        krange(P, tr.y, kb, ke, t0);
+        const int kt_n = (int)((ke - kb + BKE - 1) / BKE);
+        const uint32_t b_bytes = (uint32_t)P.nmma * 128u;
+        SqAccF sq;
+        bool ok = true;
+        for (int kt = 0; kt < kt_n; ++kt, ++it) {
+          const int s = (int)(it % (uint32_t)stages);
+          const uint32_t ph = (it / (uint32_t)stages) & 1u;
+          if (!mbar_wait(&full[s], ph, abort_flag)) {
+            ok = false;
+            break;
+          }
+          uint8_t* st = base + (size_t)s * L.bytes;
+          if (TRANSPOSE) {
+            // thread c owns row c of the K-major tile (see tc_gemm_kernel)
+            const int c = et;
+            const float* stg = reinterpret_cast<const float*>(st + L.a + (c >> 5) * (TC_BK * 128)) + (c & 31);
+            uint8_t* row = st + L.ak + c * 128;
+            uint8_t* rlo = st + L.alo + c * 128;
+#pragma unroll
+            for (int ch = 0; ch < 8; ++ch) {
+              float4 v = make_float4(stg[(4 * ch + 0) * 32], stg[(4 * ch + 1) * 32], stg[(4 * ch + 2) * 32],
+                                     stg[(4 * ch + 3) * 32]);
+              const int off = (ch ^ (c & 7)) << 4;
+              *reinterpret_cast<float4*>(row + off) = v;
+              if (SPLIT)
+                *reinterpret_cast<float4*>(rlo + off) =
+                    make_float4(tf32_lo(v.x), tf32_lo(v.y), tf32_lo(v.z), tf32_lo(v.w));
+            }
+          } else {
+            const float4* a4 = reinterpret_cast<const float4*>(st + L.a);
+            float4* lo4 = reinterpret_cast<float4*>(st + L.alo);
+            for (int i = et; i < TC_A_BYTES / 16; i += 128) {
+              float4 v = a4[i];
+              if (NORM) {
+                sq.add(v.x);
+                sq.add(v.y);
+                sq.add(v.z);
+                sq.add(v.w);
+              }
+              if (SPLIT) lo4[i] = make_float4(tf32_lo(v.x), tf32_lo(v.y), tf32_lo(v.z), tf32_lo(v.w));
+            }
+          }
+          if (SPLIT) {
+            const float4* b4 = reinterpret_cast<const float4*>(st + L.b);
+            float4* blo4 = reinterpret_cast<float4*>(st + L.blo);
+            for (int i = et; i < (int)(b_bytes / 16); i += 128) {
+              float4 v = b4[i];
+              blo4[i] = make_float4(tf32_lo(v.x), tf32_lo(v.y), tf32_lo(v.z), tf32_lo(v.w));
+            }
+          }
+          if (PREP) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) {
+            if (PREP) mbar_arrive(&tfull[s]);
+            mbar_arrive(&empty[s]);
+          }
+        }
+        if (!ok) break;
+        if (NORM && MODE == 0) {
+          // one partial per (row tile, prep warp): summed in order by the residual step
+          double v = (double)sq.hi + (double)sq.lo;
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+          if (lane == 0 && P.gnorm_part) P.gnorm_part[4 * tr.y + q] = v;
+        }
+      }
+    }
+  } else {
+    // ---------------- accumulator drain (warps 6-9) ----------------
+    const int q = warp & 3;  // TMEM sub-partition: lanes 32q .. 32q + 31
+    int j = 0;
+    for (int ti = blockIdx.x; ti < ntiles && !*abort_flag; ti += gridDim.x, ++j) {
+      const int2 tr = tiles[ti];
+      const TcGroupProb& P = probs[tr.x];
+      int64_t kb, ke;
+      int t0;
+      krange(P, tr.y, kb, ke, t0);
+      const int acc = j & 1;
+      if (!mbar_wait(&tmfull[acc], (uint32_t)(j >> 1) & 1u, abort_flag)) break;
+      tc_fence_after();
+      const int row = 32 * q + lane;
+      const int64_t grow = (int64_t)t0 + row;
+      const int z = MODE == 1 ? tr.y / P.tiles_x : 0;
+      float* dst = P.out + (int64_t)z * P.split_stride + grow * P.ldo;
+      const uint32_t src = tmem + (uint32_t)(acc * acc_stride) + ((uint32_t)(32 * q) << 16);
+      for (int c0 = 0; c0 < P.nmma; c0 += 16) {
+        float v[16];
+        tmem_ld16(src + (uint32_t)c0, v);
+        if (grow < P.out_rows) {
+#pragma unroll
+          for (int jj = 0; jj < 16; jj += 4) {
+            const int c = c0 + jj;
+            if (c + 3 < P.ncols) {
+              *reinterpret_cast<float4*>(dst + c) = make_float4(v[jj], v[jj + 1], v[jj + 2], v[jj + 3]);
+            } else {
+              for (int t = 0; t < 4; ++t)
+                if (c + t < P.ncols) dst[c + t] = v[jj + t];
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tmempty[acc]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (tid == 0 && s_abort) set_status(st_glob, -7, 210 + MODE, blockIdx.x);
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, (uint32_t)tmem_cols);
+  }
+}
+
+size_t group_smem_bytes(int mode, bool split, int nmma_max, int stages) {
+  return 1024 + (size_t)stages * StageLayout(mode, split, nmma_max, 4).bytes + (3 * (size_t)stages + 5) * 8 + 16;
+}
+
+}  // namespace
+
+int64_t tc_group_tiles(int mode, const TcGroupSpec* specs, int nprob) {
+  int64_t t = 0;
+  for (int i = 0; i < nprob; ++i) {
+    const TcGroupSpec& s = specs[i];
+    if (mode == 0)
+      t += cdiv(s.M, TC_BM);
+    else
+      t += cdiv(s.n, TC_BM) * (int64_t)s.splits;
+  }
+  return t;
+}
+
+size_t tc_group_table_bytes(int nprob, int64_t ntiles) {
+  return round_up((int64_t)nprob * (int64_t)sizeof(TcGroupProb), 256) + round_up(ntiles * (int64_t)sizeof(int2), 256);
+}
+
+bool tc_group_build(int mode, const TcGroupSpec* specs, int nprob, void* host, int* nmma_max) {
+  TcGroupProb* P = static_cast<TcGroupProb*>(host);
+  int2* T = reinterpret_cast<int2*>(static_cast<unsigned char*>(host) +
+                                    round_up((int64_t)nprob * (int64_t)sizeof(TcGroupProb), 256));
+  std::vector<std::pair<int64_t, int2>> order;
+  int nm = 16;
+  for (int i = 0; i < nprob; ++i) {
+    const TcGroupSpec& s = specs[i];
+    TcGroupProb& p = P[i];
+    memset(&p, 0, sizeof(p));
+    const int nmma = (int)round_up(s.l, 16);
+    if (s.l < 1 || nmma > 256 || !tc_shape_ok(s.G, s.ldg, s.l)) return false;
+    nm = std::max(nm, nmma);
+    p.out = s.out;
+    p.ldo = s.ldo;
+    p.ncols = s.l;
+    p.nmma = nmma;
+    p.gnorm_part = s.gnorm_part;
+    if (mode == 0) {
+      if (!make_map(&p.mapA, s.G, (uint64_t)s.n, (uint64_t)s.M, (uint64_t)s.ldg, TC_BM)) return false;
+      if (!make_map(&p.mapB, s.Bt, (uint64_t)s.n, (uint64_t)nmma, (uint64_t)s.ldb, (uint32_t)nmma)) return false;
+      p.out_rows = s.M;
+      p.kdim = s.n;
+      p.tiles_x = (int)cdiv(s.M, TC_BM);
+      const int64_t kt = cdiv(s.n, TC_BK);
+      for (int t = 0; t < p.tiles_x; ++t) order.push_back({kt, make_int2(i, t)});
+    } else {
+      if (!make_map(&p.mapA, s.G, (uint64_t)s.n, (uint64_t)s.M, (uint64_t)s.ldg, TC_BK, false)) return false;
+      if (!make_map(&p.mapB, s.Bt, (uint64_t)s.M, (uint64_t)nmma, (uint64_t)s.ldb, (uint32_t)nmma)) return false;
+      if (s.splits < 1 || s.rps % TC_BK != 0 || cdiv(s.M, s.rps) != s.splits) return false;
+      p.out_rows = s.n;
+      p.kdim = s.M;
+      p.rows_per_split = s.rps;
+      p.split_stride = s.split_stride;
+      p.tiles_x = (int)cdiv(s.n, TC_BM);
+      for (int z = 0; z < s.splits; ++z) {
+        const int64_t rows = std::min(s.M, (int64_t)(z + 1) * s.rps) - (int64_t)z * s.rps;
+        for (int t = 0; t < p.tiles_x; ++t) order.push_back({cdiv(rows, TC_BK), make_int2(i, t + z * p.tiles_x)});
+      }
+    }
+  }
+  // longest tiles first: the strided assignment then balances the CTAs
+  std::stable_sort(order.begin(), order.end(),
+                   [](const std::pair<int64_t, int2>& a, const std::pair<int64_t, int2>& b) { return a.first > b.first; });
+  for (size_t t = 0; t < order.size(); ++t) T[t] = order[t].second;
+  *nmma_max = nm;
+  return true;
+}
+
+int tc_group_max_stages(int mode, int prec, int nmma_max, int per_sm) {
+  const bool split = prec == 3;
+  const int stage = (int)StageLayout(mode, split, nmma_max, 4).bytes;
+  const int budget = (per_sm >= 2 ? 110 : 214) * 1024 - 2048;
+  return std::min(budget / stage, 8);
+}
+
+cudaError_t tc_group_launch(int mode, int prec, bool norm, const void* dev_table, int nprob, int64_t ntiles,
+                            int nmma_max, int stages, int per_sm, DevStatus* st_dev, cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+  const bool split = prec == 3;
+  const int acc_stride = (int)round_up(nmma_max, 32);
+  const int tmem_cols = tmem_cols_for(2 * acc_stride);
+  if (2 * acc_stride > 512 || (per_sm >= 2 && tmem_cols > 256)) return cudaErrorInvalidValue;
+  if (stages < 2 || stages > tc_group_max_stages(mode, prec, nmma_max, per_sm)) return cudaErrorInvalidValue;
+  const TcGroupProb* probs = static_cast<const TcGroupProb*>(dev_table);
+  const int2* tiles = reinterpret_cast<const int2*>(static_cast<const unsigned char*>(dev_table) +
+                                                    round_up((int64_t)nprob * (int64_t)sizeof(TcGroupProb), 256));
+  // the dynamic shared memory also caps the CTAs per SM at per_sm (TMEM columns stay within 512)
+  size_t smem = group_smem_bytes(mode, split, nmma_max, stages);
+  const size_t floor_smem = per_sm >= 2 ? 80 * 1024 : 120 * 1024;
+  smem = std::max(smem, floor_smem);
+  const int grid = (int)std::min<int64_t>(ntiles, (int64_t)sm_count() * std::max(1, per_sm));
+#define GSVDR_TG(M_, N_, S_)                                                                                  \
+  do {                                                                                                       \
+    cudaFuncSetAttribute(tc_group_kernel<M_, N_, S_>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024); \
+    tc_group_kernel<M_, N_, S_><<<grid, TG_THREADS, smem, st>>>(probs, tiles, (int)ntiles, nmma_max, acc_stride, \
+                                                                tmem_cols, stages, st_dev);                  \
+  } while (0)
+  if (mode == 0) {
+    if (norm && split) GSVDR_TG(0, true, true);
+    else if (norm) GSVDR_TG(0, true, false);
+    else if (split) GSVDR_TG(0, false, true);
+    else GSVDR_TG(0, false, false);
+  } else {
+    if (split) GSVDR_TG(1, false, true);
+    else GSVDR_TG(1, false, false);
+  }
+#undef GSVDR_TG
   return launched();
 }
 

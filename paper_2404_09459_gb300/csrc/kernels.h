@@ -180,4 +180,138 @@ cudaError_t mlp_loss_grad(const float* P, const float* norm, const float* X, con
 cudaError_t mlp_adam(float* P, float* m, float* v, const float* grad, int t, float lr, float b1, float b2, float eps,
                      cudaStream_t st);
 
+// ---- batched forms: one launch for many problems ------------------------------
+// Each launcher takes a table of per-problem arguments in device memory (nprob
+// entries) and the largest extent over the problems, which sizes the grid.
+struct GaussB {  // Omega^T of one side, K-major FP32 (as launch_gaussian_kmajor)
+  float* Xt;
+  int64_t ldx, n;
+  int l, lrows;
+  uint64_t seed;
+  uint32_t pair, side, stream, pad;
+};
+cudaError_t launch_gaussian_kmajor_b(const GaussB* tab, int nprob, int64_t max_ldx, int max_lrows, cudaStream_t st);
+
+struct ReduceB {  // as launch_reduce_splits<float, float>; sq_part gets cdiv(n l, 256) sums
+  const float* part;
+  int splits, l;
+  int64_t n, lp;
+  float* Z;
+  int64_t ldz;
+  int transpose_out, pad;
+  double* sq_part;
+};
+cudaError_t launch_reduce_splits_b(const ReduceB* tab, int nprob, int64_t max_nl, cudaStream_t st);
+
+struct GramB {  // Gram partials of Y (M x l, FP32) over `chunks` chunks of rpc rows
+  const float* Y;
+  int64_t ldy, M, rpc;
+  int l, chunks;
+  double* part;
+};
+cudaError_t launch_gram_partial_b(const GramB* tab, int nprob, int max_chunks, int max_l, cudaStream_t st);
+
+struct GramRedB {  // W = sum of the chunk partials
+  const double* part;
+  int chunks, l;
+  double* W;
+};
+cudaError_t launch_gram_reduce_b(const GramRedB* tab, int nprob, int max_l, cudaStream_t st);
+
+struct CholB {  // shifted Cholesky with the inverse factor (FP32 factor), as launch_chol_shift
+  const double* W;
+  double shift_coef, tau_rel;
+  float* Rinv;
+  DevStatus* st;
+  int l, stage;
+};
+// max_l <= 64: the register-resident elimination; <= 128: the shared-memory one.
+cudaError_t launch_chol_b(const CholB* tab, int nprob, int max_l, cudaStream_t st);
+
+struct ApplyB {  // Q = Y R^{-1} (FP32), as launch_apply_rinv without the fused Gram
+  const float* Y;
+  int64_t ldy, M;
+  const float* Rinv;
+  float* Q;
+  int64_t ldq;
+  int l, transpose_out;
+};
+cudaError_t launch_apply_rinv_b(const ApplyB* tab, int nprob, int64_t max_M, int max_l, cudaStream_t st);
+
+struct ResidB {  // cumulated residual of one side
+  const double* gpart;
+  const double* bpart;
+  double* out;
+  int ng, nb;
+};
+cudaError_t launch_residual_b(const ResidB* tab, int nprob, cudaStream_t st);
+
+// C = alpha op(A) op(B) + beta C in FP64 accumulation (A and B FP32 or FP64), one
+// 32 x 32 tile of C per CTA (no split-K: the batch fills the GPU).  C must not alias
+// A or B.
+struct DgemmB {
+  const void* A;
+  const void* B;
+  double* C;
+  int64_t lda, ldb, ldc;
+  double alpha, beta;
+  int Mr, Nc, K, ta, tb, pad;
+};
+template <typename TA, typename TB>
+cudaError_t launch_dgemm_b(const DgemmB* tab, int nprob, int max_Mr, int max_Nc, cudaStream_t st);
+
+// One Ogita-Aishima step per problem (as launch_oa_refine), and the cut cluster after it.
+struct OaB {
+  const double* A;
+  double* X;
+  double* lam;
+  double* XtX;  // N x N work matrices
+  double* P;
+  double* S;
+  double* F;
+  double* part;  // 3 sums
+  int N, r;
+};
+// The four products of a step use `dg` (4 * nprob DgemmB entries, filled by oa_b_tables).
+void oa_b_tables(const OaB* hostOa, int nprob, DgemmB* dg);
+cudaError_t launch_oa_refine_b(const OaB* tab, const DgemmB* dg, int nprob, int max_N, cudaStream_t st);
+cudaError_t launch_oa_cut_cluster_b(const OaB* tab, int nprob, int max_N, cudaStream_t st);
+
+struct SelB {
+  const double* X;
+  const double* lam;
+  double* Zr;
+  int* order;
+  int N, r;
+};
+cudaError_t launch_select_topr_b(const SelB* tab, int nprob, int max_N, cudaStream_t st);
+
+struct CsB {
+  const double* U1;
+  const double* U2;
+  double* alpha;
+  double* beta;
+  int l1, l2, r, pad;
+};
+cudaError_t launch_cs_norms_b(const CsB* tab, int nprob, int max_r, cudaStream_t st);
+
+struct ScatterB {  // dst[0..count) = src[0..count)
+  const double* src;
+  double* dst;
+  int count, pad;
+};
+cudaError_t launch_scatter_b(const ScatterB* tab, int n, cudaStream_t st);
+
+struct EigB {
+  const double* A;
+  double* X;
+  double* lam;
+  float* scratch;
+  float noise_rel;
+  int N;
+};
+// All problems of the table have N <= 128 (eig128) or 128 < N <= 318 (the packed-triangle
+// solver with the triangle in shared memory).
+cudaError_t launch_eig_f32_b(const EigB* tab, int nprob, int max_N, cudaStream_t st);
+
 }  // namespace gsvdr

@@ -41,4 +41,37 @@ cudaError_t tc_gemm_gtq_bf16(const void* G, int64_t ldg, int64_t M, int64_t n, c
                              DevStatus* st_dev, cudaStream_t st);
 int tc_gtq_splits_bf16(int64_t M, int64_t n, bool split);
 
+// ---- grouped persistent products (many independent problems, one launch) ----
+// One problem: G (M x n, row-major FP32, ld ldg, TMA-aligned) times a K-major B operand
+// Bt with ld ldb: mode 0 (GX) Y = G X with Bt = X^T (round_up(l,16) x n, padding rows
+// zero), out = Y (M x l, ld ldo), gnorm_part (or nullptr) receives 4 partial sums of
+// G^2 per 128-row tile; mode 1 (GTQ) split-K partials of G^T Q with Bt = Q^T
+// (round_up(l,16) x M), `splits` row ranges of rps rows (a multiple of 32), partial z
+// at out + z * split_stride (n x l, ld ldo).
+struct TcGroupSpec {
+  const float* G;
+  int64_t ldg, M, n;
+  const float* Bt;
+  int64_t ldb;
+  int l;
+  float* out;
+  int64_t ldo;
+  int splits;
+  int64_t rps, split_stride;
+  double* gnorm_part;
+};
+// Tiles of a grouped launch (128-row tiles in mode 0; column tiles x splits in mode 1).
+int64_t tc_group_tiles(int mode, const TcGroupSpec* specs, int nprob);
+// Bytes of the device table: the problems, then the tile list.
+size_t tc_group_table_bytes(int nprob, int64_t ntiles);
+// Writes the table into `host` (tc_group_table_bytes bytes; the caller copies it to the
+// device, 256-byte aligned): tensor maps per problem, tiles longest first.
+bool tc_group_build(int mode, const TcGroupSpec* specs, int nprob, void* host, int* nmma_max);
+// Deepest pipeline for per_sm CTAs per SM.
+int tc_group_max_stages(int mode, int prec, int nmma_max, int per_sm);
+// One persistent launch over every tile of the table (prec 3 = 3xTF32, else TF32;
+// norm: mode 0 with the fused sum of G^2).  A timed-out wait sets TIMEOUT in st_dev.
+cudaError_t tc_group_launch(int mode, int prec, bool norm, const void* dev_table, int nprob, int64_t ntiles,
+                            int nmma_max, int stages, int per_sm, DevStatus* st_dev, cudaStream_t st);
+
 }  // namespace gsvdr

@@ -172,3 +172,20 @@ def mlp_init(seed: int = 0) -> np.ndarray:
         parts.append(rng.standard_normal(fin * fout) * np.sqrt(2.0 / fin))
         parts.append(np.zeros(fout))
     return np.concatenate(parts).astype(np.float32)
+
+
+def aligned_rows(G, row_bytes: int = 16):
+    """The same matrix stored with its row stride padded to a multiple of `row_bytes` (a view of
+    a zero-padded torch tensor or numpy array): the layout the tensor-memory-accelerator
+    products need to read G in place."""
+    per = max(1, row_bytes // G.element_size()) if hasattr(G, "element_size") else max(1, row_bytes // G.itemsize)
+    rows, n = G.shape
+    ld = -(-n // per) * per
+    if ld == n:
+        return G
+    if hasattr(G, "new_zeros"):
+        buf = G.new_zeros((rows, ld))
+    else:
+        buf = np.zeros((rows, ld), dtype=G.dtype)
+    buf[:, :n] = G
+    return buf[:, :n]

@@ -1,0 +1,164 @@
+"""Grouped solves (one launch per step for a whole batch, replayed from a CUDA graph)
+against the FP64 oracle, through the C ABI (needs a CUDA GPU).
+
+Tolerance: the mixed-precision target, per-pair GSV error
+e_i = max(|alpha_i - alpha_ref_i|, |beta_i - beta_ref_i|) <= 1e-4 (3xTF32 products,
+FP64 CholeskyQR Grams and FP64 compressed-pair GSVD), 1e-3 for single-pass TF32.
+"""
+import numpy as np
+import pytest
+
+from oracle import gsvd as O
+from paper_2404_09459_gb300.inputs import PairSpec, aligned_rows, planted_pair
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2404_09459_gb300 as P  # noqa: E402
+
+P._build.build()
+
+TOL = {"tf32": 1e-3, "tf32x3": 1e-4}
+
+
+def _dev(a):
+    # rows padded to 16 bytes: the grouped products read G in place through TMA
+    return aligned_rows(torch.from_numpy(np.ascontiguousarray(a)).to("cuda", torch.float32))
+
+
+def _specs(seed, count, wide=False):
+    """Uneven pairs: m, p, n, rank, oversample and q all differ; `wide` adds bases with
+    l = k + oversample > 64 (the second CholeskyQR class) and stacks L = 2 l > 128 (the
+    packed-triangle eigensolver)."""
+    rng = np.random.default_rng(seed)
+    specs = []
+    for i in range(count):
+        m, p = (int(x) for x in rng.integers(300, 2500, 2))
+        n = int(rng.integers(90, 420))
+        r = int(rng.integers(4, 36))
+        os_ = int(rng.choice([4, 8, 10]))
+        if wide and i % 2 == 0:
+            r = int(rng.integers(56, 70))
+            n = max(n, r + 40)
+            os_ = 10
+        specs.append(PairSpec(m=m, p=p, n=n, r=r, alpha="uniform", decay="exp10", sigma=1e-6, k=r,
+                              oversample=os_, q=int(rng.integers(0, 3)), seed=500 + i))
+    return specs
+
+
+def _pairs(specs, mats):
+    return [dict(G1=_dev(G1), G2=_dev(G2), k=s.kk, oversample=s.oversample, q=s.q, seed=s.seed, pair=i)
+            for i, (s, (G1, G2)) in enumerate(zip(specs, mats))]
+
+
+def _check_vs_oracle(prec, specs, mats, outs):
+    for i, (s, (G1, G2), out) in enumerate(zip(specs, mats, outs)):
+        assert out["status"] == 0 and out["r"] == s.kk
+        ref = O.rand_gsvd(G1, G2, s.kk, s.oversample, s.q, s.seed, pair=i)
+        a = np.asarray(out["alpha"].cpu() if hasattr(out["alpha"], "cpu") else out["alpha"])
+        b = np.asarray(out["beta"].cpu() if hasattr(out["beta"], "cpu") else out["beta"])
+        e = O.gsv_error(ref["alpha"], ref["beta"], a, b)
+        assert np.max(e) <= TOL[prec], (i, s, np.max(e))
+        dth = np.abs(np.arctan2(a, b) - np.arctan2(ref["alpha"], ref["beta"]))
+        assert np.max(dth) <= max(1e-4, TOL[prec])
+        assert np.all(np.diff(a) <= 0) and np.all(np.diff(b) >= 0)
+        # cumulated residual sqrt(||G||^2 - ||B||^2) / ||G||: ||B||^2 carries the relative error
+        # of the products (2^-10 for single-pass TF32) and of the FP32 basis' orthogonality, so
+        # the estimate is held on the squared scale
+        rtol = 4e-3 if prec == "tf32" else 1e-4
+        for sd in range(2):
+            assert abs(out["resid"][sd] ** 2 - ref[f"resid{sd + 1}"] ** 2) <= rtol, (i, sd, out["resid"])
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "tf32"])
+def test_grouped_uneven_pairs_match_oracle(prec):
+    # single-pass TF32 truncates G to 10 mantissa bits: planted scales below ~1e-3 of the
+    # largest (ranks above ~60 with the exp(-i/10) law) are beyond it, so it takes the
+    # narrower pairs; 3xTF32 takes the wide ones too
+    specs = _specs(11, 7, wide=prec == "tf32x3")
+    mats = [planted_pair(s)[:2] for s in specs]
+    with P.Context(prec) as ctx:
+        outs = ctx.solve_grouped(_pairs(specs, mats))
+        info = ctx.grouped_info()
+    _check_vs_oracle(prec, specs, mats, outs)
+    assert info["captures"] == 1 and info["replays"] == 1 and info["launches"] > 20
+    for st, ps in info["tuned"]:
+        assert st >= 2 and ps in (1, 2)
+
+
+def test_grouped_replays_graph_bit_identical_and_host_outputs():
+    specs = _specs(12, 6)
+    mats = [planted_pair(s)[:2] for s in specs]
+    pairs = _pairs(specs, mats)
+    with P.Context("tf32x3") as ctx:
+        first = ctx.solve_grouped(pairs)
+        second = ctx.solve_grouped(pairs)           # same inputs, new output buffers: replay
+        host = ctx.solve_grouped(pairs, host_out=True)
+        info = ctx.grouped_info()
+    assert info["captures"] == 1 and info["replays"] == 3
+    for a, b, c in zip(first, second, host):
+        np.testing.assert_array_equal(a["alpha"].cpu().numpy(), b["alpha"].cpu().numpy())
+        np.testing.assert_array_equal(a["beta"].cpu().numpy(), b["beta"].cpu().numpy())
+        np.testing.assert_array_equal(a["alpha"].cpu().numpy(), np.asarray(c["alpha"]))
+        np.testing.assert_array_equal(a["beta"].cpu().numpy(), np.asarray(c["beta"]))
+        assert a["resid"] == c["resid"]
+    _check_vs_oracle("tf32x3", specs, mats, host)
+
+
+def test_grouped_agrees_with_single_and_worker_solves():
+    specs = _specs(13, 5, wide=True)
+    mats = [planted_pair(s)[:2] for s in specs]
+    pairs = _pairs(specs, mats)
+    with P.Context("tf32x3") as ctx:
+        grouped = ctx.solve_grouped(pairs)
+        workers = ctx.solve_batched(pairs, workers=3)
+    for g, w in zip(grouped, workers):
+        # both are within 1e-4 of the oracle; they differ only in rounding (Gram chunking)
+        e = O.gsv_error(w["alpha"].cpu().numpy(), w["beta"].cpu().numpy(), g["alpha"].cpu().numpy(),
+                        g["beta"].cpu().numpy())
+        assert np.max(e) <= 2e-4
+
+
+def test_grouped_new_batch_recaptures_and_bad_pair_is_left_out():
+    specs = _specs(14, 4)
+    mats = [planted_pair(s)[:2] for s in specs]
+    pairs = _pairs(specs, mats)
+    with P.Context("tf32x3") as ctx:
+        good = ctx.solve_grouped(pairs)
+        bad = dict(pairs[1])
+        bad["k"] = 10_000  # k + oversample > n
+        with pytest.raises(P.GsvdRandError) as e:
+            ctx.solve_grouped([pairs[0], bad, pairs[2], pairs[3]])
+        assert e.value.name == "ARG"
+        again = ctx.solve_grouped([pairs[0], pairs[2], pairs[3]])
+        info = ctx.grouped_info()
+    assert info["captures"] == 3
+    np.testing.assert_array_equal(good[0]["alpha"].cpu().numpy(), again[0]["alpha"].cpu().numpy())
+
+
+def test_grouped_refuses_fp64_and_adaptive_contexts():
+    specs = _specs(15, 1)
+    mats = [planted_pair(s)[:2] for s in specs]
+    with P.Context("fp64") as ctx:
+        pairs = [dict(G1=aligned_rows(torch.from_numpy(G1).cuda()), G2=aligned_rows(torch.from_numpy(G2).cuda()), k=s.kk,
+                      oversample=s.oversample, q=s.q, seed=s.seed) for s, (G1, G2) in zip(specs, mats)]
+        with pytest.raises(P.GsvdRandError) as e:
+            ctx.solve_grouped(pairs)
+        assert e.value.name == "UNSUPPORTED"
+
+
+def test_grouped_leaves_out_pairs_with_unaligned_rows():
+    specs = _specs(16, 3)
+    specs[1] = PairSpec(m=500, p=400, n=101, r=8, k=8, oversample=6, q=1, seed=7)
+    mats = [planted_pair(s)[:2] for s in specs]
+    pairs = _pairs(specs, mats)
+    pairs[1]["G1"] = torch.from_numpy(mats[1][0]).to("cuda", torch.float32)  # 404-byte rows
+    with P.Context("tf32x3") as ctx:
+        with pytest.raises(P.GsvdRandError) as e:
+            outs = ctx.solve_grouped(pairs)
+        assert e.value.name == "ARG"
+        outs = ctx.solve_grouped([pairs[0], pairs[2]])
+    _check_vs_oracle("tf32x3", [specs[0]], [mats[0]], outs[:1])
