@@ -260,6 +260,18 @@ def run_batched(args, rank, world):
             times.append(time.perf_counter() - t0)
     launches = (ctx.launch_count() - l0) // args.steps
     info = ctx.grouped_info() if grouped else None
+    stages = None
+    if grouped:
+        # per-step device time of one replay (CUDA events captured into the graph), by stage
+        pctx = P.Context(prec, device=local, flags=P.FLAG_PROFILE)
+        pctx.solve_grouped(pairs)
+        pctx.profile(reset=True)
+        pctx.solve_grouped(pairs)
+        prof = pctx.profile()
+        pctx.close()
+        tot = sum(v[0] for k, v in prof.items() if k != "small")
+        stages = {k: {"ms_per_step": v[0], "steps_per_solve": v[1], "share": v[0] / tot if tot else None}
+                  for k, v in prof.items() if k != "small" and v[1]}
     # the other batched form on the same pairs, for comparison (grouped vs concurrent workers)
     other = None
     if grouped and args.steps > 0:
@@ -312,6 +324,7 @@ def run_batched(args, rank, world):
                                "graph_captures": info["captures"], "graph_replays": info["replays"],
                                "launches_per_replay": info["launches"]}
             line["worker_streams"] = other
+            line["stages"] = stages
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist is not None:

@@ -1074,6 +1074,8 @@ struct GroupState {
   uint64_t launches_per_replay = 0;
   int64_t captures = 0, replays = 0;
   int tuned[3][2] = {{0, 0}, {0, 0}, {0, 0}};  // (stages, CTAs per SM): first sketch, power sketch, G^T Q
+  std::vector<cudaEvent_t> prof_ev;  // GSVD_RAND_FLAG_PROFILE: event pairs around each step in the graph
+  std::vector<int> prof_tag;
   // results
   size_t res_off = 0, res_bytes = 0;  // results block inside the workspace
   std::vector<int> valid;             // pair index of each solved pair
@@ -1097,6 +1099,7 @@ void group_free(GroupState* g) {
   if (g->stream) cudaStreamDestroy(g->stream);
   if (g->ev_in) cudaEventDestroy(g->ev_in);
   if (g->ev_out) cudaEventDestroy(g->ev_out);
+  for (auto e : g->prof_ev) cudaEventDestroy(e);
   if (g->host) cudaFreeHost(g->host);
   if (g->scat_host) cudaFreeHost(g->scat_host);
   if (g->scat_dev) cudaFree(g->scat_dev);
@@ -1202,7 +1205,7 @@ struct GSide {
   int64_t lp, ldx, ldm, lt;
   float *Xt, *Y, *Qt, *tmp, *Z, *part;
   double *gpart, *W, *gnorm, *bnorm;
-  float* R;
+  float* R;  // R^{-1} transposed (lx x lp, padding rows zero): the K-major operand of Q = Y R^{-1}
   int splits;
   int64_t rps;
   int gchunks;
@@ -1226,6 +1229,7 @@ struct GroupBuild {
   Arena arena;
   // launches, replayed in order; each receives the device address of the table arena
   std::vector<std::function<cudaError_t(const unsigned char*, cudaStream_t)>> ops;
+  std::vector<int> tags;  // GSVD_RAND_STAGE_* of each op (timed under GSVD_RAND_FLAG_PROFILE)
   struct Gemm {
     int mode;
     bool norm;
@@ -1234,6 +1238,7 @@ struct GroupBuild {
     int64_t ntiles, kmean;
     int tune_slot;
     int stages, per_sm;  // picked by the autotuner for this launch's own shape
+    int prec;            // 3: 3xTF32; else single-pass TF32
   };
   std::vector<Gemm> gemms;
   size_t ws_bytes = 0;
@@ -1304,7 +1309,7 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
       S.grpc = 0;
       S.gpart = bp.take<double>((int64_t)S.gchunks * P.l * P.l);
       S.W = bp.take<double>((int64_t)P.l * P.l);
-      S.R = bp.take<float>((int64_t)P.l * P.l);
+      S.R = bp.take<float>((int64_t)S.lx * S.lp);
       S.gnorm = bp.take<double>(4 * cdiv(S.M, 128));
       S.bnorm = bp.take<double>(cdiv(S.n * P.l, 256));
     }
@@ -1331,12 +1336,16 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
   // ---- the launch sequence ----
   const int ns = 2 * np;
   Arena& A = gb.arena;
-  auto& ops = gb.ops;
+  int cur_tag = GSVD_RAND_STAGE_SKETCH;
+  auto push = [&](std::function<cudaError_t(const unsigned char*, cudaStream_t)> f) {
+    gb.ops.push_back(std::move(f));
+    gb.tags.push_back(cur_tag);
+  };
   const double u = 5.9604644775390625e-08;  // FP32 unit roundoff
   // statuses to zero on every replay
   {
     DevStatus* st0 = st_all;
-    ops.push_back([st0, np](const unsigned char*, cudaStream_t st) {
+    push([st0, np](const unsigned char*, cudaStream_t st) {
       return cudaMemsetAsync(st0, 0, (size_t)np * sizeof(DevStatus), st);
     });
   }
@@ -1353,7 +1362,7 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
       mlr = std::max(mlr, S.lx);
     }
     const size_t off = A.add(t);
-    ops.push_back([off, ns, mldx, mlr](const unsigned char* d, cudaStream_t st) {
+    push([off, ns, mldx, mlr](const unsigned char* d, cudaStream_t st) {
       return launch_gaussian_kmajor_b(reinterpret_cast<const GaussB*>(d + off), ns, mldx, mlr, st);
     });
   }
@@ -1365,7 +1374,27 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
     for (int j = 0; j < ns; ++j)
       if (it < 0 || gb.prs[j / 2].q > it) act.push_back(j);
   };
+  // one grouped tensor-core launch over the problems of `sp`
+  auto add_gemm_specs = [&](int mode, bool norm, int slot, std::vector<TcGroupSpec>& sp, int64_t kmean, int gprec) {
+    const int na = (int)sp.size();
+    const int64_t ntiles = tc_group_tiles(mode, sp.data(), na);
+    const size_t bytes = tc_group_table_bytes(na, ntiles);
+    size_t off = A.add(nullptr, bytes);
+    int nmma = 16;
+    for (auto& x : sp) nmma = std::max(nmma, (int)round_up(x.l, 16));
+    if (base && !tc_group_build(mode, sp.data(), na, A.buf.data() + off, &nmma)) return false;
+    gb.gemms.push_back(GroupBuild::Gemm{mode, norm, off, na, nmma, ntiles, kmean, slot, 0, 0, gprec});
+    const size_t gi = gb.gemms.size() - 1;
+    DevStatus* sd = st_all;
+    push([gi, &gb, sd](const unsigned char* d, cudaStream_t st) {
+      const GroupBuild::Gemm& G = gb.gemms[gi];
+      return tc_group_launch(G.mode, G.prec, G.norm, d + G.off, G.nprob, G.ntiles, G.nmma, G.stages, G.per_sm, sd,
+                             st);
+    });
+    return true;
+  };
   auto add_gemm = [&](int mode, bool norm, int slot) {
+    cur_tag = mode == 0 ? GSVD_RAND_STAGE_SKETCH : GSVD_RAND_STAGE_GTQ;
     const int na = (int)act.size();
     std::vector<TcGroupSpec> sp(na);
     int64_t ksum = 0;
@@ -1395,23 +1424,11 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
         ksum += S.rps;
       }
     }
-    const int64_t ntiles = tc_group_tiles(mode, sp.data(), na);
-    const size_t bytes = tc_group_table_bytes(na, ntiles);
-    size_t off = A.add(nullptr, bytes);
-    int nmma = 16;
-    for (int a = 0; a < na; ++a) nmma = std::max(nmma, (int)round_up(gb.sides[act[a]].l, 16));
-    if (base && !tc_group_build(mode, sp.data(), na, A.buf.data() + off, &nmma)) return false;
-    gb.gemms.push_back(GroupBuild::Gemm{mode, norm, off, na, nmma, ntiles, ksum / std::max(na, 1), slot, 0, 0});
-    const size_t gi = gb.gemms.size() - 1;
-    DevStatus* sd = st_all;
-    ops.push_back([gi, &gb, sd, prec](const unsigned char* d, cudaStream_t st) {
-      const GroupBuild::Gemm& G = gb.gemms[gi];
-      return tc_group_launch(G.mode, prec, G.norm, d + G.off, G.nprob, G.ntiles, G.nmma, G.stages, G.per_sm, sd, st);
-    });
-    return true;
+    return add_gemm_specs(mode, norm, slot, sp, ksum / std::max(na, 1), prec);
   };
   // split reduction of G^T Q: into Z (power step) or into the rows of S (projection)
   auto add_reduce = [&](bool proj) {
+    cur_tag = GSVD_RAND_STAGE_GTQ;
     const int na = (int)act.size();
     std::vector<ReduceB> t(na);
     int64_t mx = 0;
@@ -1438,82 +1455,77 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
       mx = std::max(mx, S.n * S.l);
     }
     const size_t off = A.add(t);
-    ops.push_back([off, na, mx](const unsigned char* d, cudaStream_t st) {
+    push([off, na, mx](const unsigned char* d, cudaStream_t st) {
       return launch_reduce_splits_b(reinterpret_cast<const ReduceB*>(d + off), na, mx, st);
     });
   };
-  // shifted CholeskyQR3 of every side's basis (as Solver::orth without the fused kernel):
-  // which 0: Y (M x l) -> Q^T; 1: Z (n x l) -> X^T
+  // shifted CholeskyQR3 of every side's basis (the passes of Solver::orth without the fused
+  // kernel).  The Gram Y^T Y stays on the CUDA cores (FP32 FMA over chunks of rows, FP64 across
+  // chunks): the tensor cores' FP32 accumulation in tensor memory loses ~1e-5 relative over
+  // such chunks, which swamps the weak columns of a graded basis.  Q = Y R^{-1} runs as a
+  // grouped 3xTF32 tensor-core product with R^{-1} transposed as its K-major operand; the last
+  // pass stores Q transposed.   which 0: Y (M x l) -> Q^T; 1: Z (n x l) -> X^T
+  bool orth_ok = true;
   auto add_orth = [&](int which, int stage0) {
-    for (int cls = 0; cls < 2; ++cls) {
-      std::vector<int> js;
-      int maxl = 0;
-      for (int j : act)
-        if ((gb.sides[j].l > 64) == (cls == 1)) {
-          js.push_back(j);
-          maxl = std::max(maxl, gb.sides[j].l);
+    const int na = (int)act.size();
+    for (int pass = 0; pass < 3; ++pass) {
+      std::vector<TcGroupSpec> asp(na);
+      std::vector<GramB> gt[2];
+      std::vector<GramRedB> rt[2];
+      std::vector<CholB> ct[2];
+      int maxlc[2] = {1, 1}, maxch[2] = {1, 1};
+      int64_t msum = 0;
+      for (int a = 0; a < na; ++a) {
+        const int j = act[a];
+        const GSide& S = gb.sides[j];
+        const int64_t M = which == 0 ? S.M : S.n;
+        const float* src = pass == 0 ? (which == 0 ? S.Y : S.Z) : (pass == 1 ? S.tmp : S.tmp + M * S.lt);
+        const int64_t lds = pass == 0 ? S.lp : S.lt;
+        const int64_t rpc = round_up(cdiv(M, cdiv(M, GROUP_GRAM_ROWS)), 16);
+        const int chunks = (int)cdiv(M, rpc);
+        const int cls = S.l > 64 ? 1 : 0;
+        gt[cls].push_back(GramB{src, lds, M, rpc, S.l, chunks, S.gpart});
+        rt[cls].push_back(GramRedB{S.gpart, chunks, S.l, S.W});
+        const double shift = pass == 0 ? 11.0 * ((double)rpc + S.l + 1) * u : 0.0;
+        const double tau = 8.0 * (double)std::max<int64_t>(rpc, 128) * u;
+        ct[cls].push_back(CholB{S.W, shift, tau, S.R, gb.prs[j / 2].st, S.l,
+                                10 * (j & 1) + stage0 + (pass > 0 ? 1 : 0), (int)S.lp, 0});
+        maxlc[cls] = std::max(maxlc[cls], S.l);
+        maxch[cls] = std::max(maxch[cls], chunks);
+        TcGroupSpec& x = asp[a];
+        memset(&x, 0, sizeof(x));
+        x.G = src;
+        x.ldg = lds;
+        x.M = M;
+        x.n = S.l;
+        x.l = S.l;
+        x.Bt = S.R;
+        x.ldb = S.lp;
+        if (pass < 2) {
+          x.out = pass == 0 ? S.tmp : S.tmp + M * S.lt;
+          x.ldo = S.lt;
+        } else {
+          x.out = which == 0 ? S.Qt : S.Xt;
+          x.ldo = which == 0 ? S.ldm : S.ldx;
+          x.transpose_out = 1;
         }
-      if (js.empty()) continue;
-      const int nj = (int)js.size();
-      const int64_t arows = cls ? 32 : 128;
-      int maxch = 1;
-      int64_t maxM = 1;
-      std::vector<const float*> in(nj);
-      std::vector<int64_t> ldin(nj), rows(nj);
-      for (int t = 0; t < nj; ++t) {
-        const GSide& S = gb.sides[js[t]];
-        in[t] = which == 0 ? S.Y : S.Z;
-        ldin[t] = S.lp;
-        rows[t] = which == 0 ? S.M : S.n;
-        maxM = std::max(maxM, rows[t]);
+        msum += S.l;
       }
-      for (int pass = 0; pass < 3; ++pass) {
-        std::vector<GramB> gt(nj);
-        std::vector<GramRedB> rt(nj);
-        std::vector<CholB> ct(nj);
-        std::vector<ApplyB> at(nj);
-        for (int t = 0; t < nj; ++t) {
-          const GSide& S = gb.sides[js[t]];
-          const int64_t M = rows[t];
-          const int64_t rpc = round_up(cdiv(M, cdiv(M, GROUP_GRAM_ROWS)), 16);
-          const int chunks = (int)cdiv(M, rpc);
-          maxch = std::max(maxch, chunks);
-          const float* src = pass == 0 ? in[t] : (pass == 1 ? S.tmp : S.tmp + M * S.lt);
-          const int64_t lds = pass == 0 ? ldin[t] : S.lt;
-          gt[t] = GramB{src, lds, M, rpc, S.l, chunks, S.gpart};
-          rt[t] = GramRedB{S.gpart, chunks, S.l, S.W};
-          const double shift = pass == 0 ? 11.0 * ((double)rpc + S.l + 1) * u : 0.0;
-          const double tau = 8.0 * (double)std::max<int64_t>(rpc, arows) * u;
-          ct[t] = CholB{S.W, shift, tau, S.R, gb.prs[js[t] / 2].st, S.l,
-                        10 * (js[t] & 1) + stage0 + (pass > 0 ? 1 : 0)};
-          ApplyB& a = at[t];
-          a.Y = src;
-          a.ldy = lds;
-          a.M = M;
-          a.Rinv = S.R;
-          a.l = S.l;
-          if (pass < 2) {
-            a.Q = pass == 0 ? S.tmp : S.tmp + M * S.lt;
-            a.ldq = S.lt;
-            a.transpose_out = 0;
-          } else {
-            a.Q = which == 0 ? S.Qt : S.Xt;
-            a.ldq = which == 0 ? S.ldm : S.ldx;
-            a.transpose_out = 1;
-          }
-        }
-        const size_t og = A.add(gt), orr = A.add(rt), oc = A.add(ct), oa = A.add(at);
-        const int mch = maxch;
-        const int64_t mM = maxM;
-        const int ml = maxl;
-        ops.push_back([og, orr, oc, oa, nj, mch, ml, mM](const unsigned char* d, cudaStream_t st) {
+      cur_tag = GSVD_RAND_STAGE_ORTH;
+      for (int cls = 0; cls < 2; ++cls) {
+        if (ct[cls].empty()) continue;
+        const size_t og = A.add(gt[cls]), orr = A.add(rt[cls]), oc = A.add(ct[cls]);
+        const int cnt = (int)ct[cls].size(), ml = maxlc[cls], mch = maxch[cls];
+        push([og, orr, oc, cnt, ml, mch](const unsigned char* d, cudaStream_t st) {
           cudaError_t e;
-          if ((e = launch_gram_partial_b(reinterpret_cast<const GramB*>(d + og), nj, mch, ml, st))) return e;
-          if ((e = launch_gram_reduce_b(reinterpret_cast<const GramRedB*>(d + orr), nj, ml, st))) return e;
-          if ((e = launch_chol_b(reinterpret_cast<const CholB*>(d + oc), nj, ml, st))) return e;
-          return launch_apply_rinv_b(reinterpret_cast<const ApplyB*>(d + oa), nj, mM, ml, st);
+          if ((e = launch_gram_partial_b(reinterpret_cast<const GramB*>(d + og), cnt, mch, ml, st))) return e;
+          if ((e = launch_gram_reduce_b(reinterpret_cast<const GramRedB*>(d + orr), cnt, ml, st))) return e;
+          return launch_chol_b(reinterpret_cast<const CholB*>(d + oc), cnt, ml, st);
         });
       }
+      // the re-orthonormalisation wins the accuracy back: its products are 3xTF32 in every mode
+      if (!add_gemm_specs(0, false, -1, asp, msum / std::max(na, 1), GSVD_RAND_TF32X3)) orth_ok = false;
+      cur_tag = GSVD_RAND_STAGE_ORTH;
     }
   };
 
@@ -1532,8 +1544,10 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
   }
   set_active(-1);
   if (!add_gemm(1, false, 2)) return fail(h, GSVD_RAND_ERR_ARG, "tensor map of a grouped product rejected");
+  if (!orth_ok) return fail(h, GSVD_RAND_ERR_ARG, "tensor map of a grouped CholeskyQR product rejected");
   add_reduce(true);
   {
+    cur_tag = GSVD_RAND_STAGE_GTQ;
     std::vector<ResidB> t(ns);
     for (int j = 0; j < ns; ++j) {
       const GSide& S = gb.sides[j];
@@ -1541,12 +1555,13 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
                     (int)cdiv(S.n * S.l, 256)};
     }
     const size_t off = A.add(t);
-    ops.push_back([off, ns](const unsigned char* d, cudaStream_t st) {
+    push([off, ns](const unsigned char* d, cudaStream_t st) {
       return launch_residual_b(reinterpret_cast<const ResidB*>(d + off), ns, st);
     });
   }
 
   // ---- compressed-pair GSVDs ----
+  cur_tag = GSVD_RAND_STAGE_SMALL_GRAM;
   int maxL = 0, maxk = 0, maxl1 = 0;
   for (auto& P : gb.prs) {
     maxL = std::max(maxL, P.L);
@@ -1572,12 +1587,13 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
     }
     const size_t off = A.add(t);
     const int mL = maxL;
-    ops.push_back([off, np, mL](const unsigned char* d, cudaStream_t st) {
+    push([off, np, mL](const unsigned char* d, cudaStream_t st) {
       return launch_dgemm_b<float, float>(reinterpret_cast<const DgemmB*>(d + off), np, mL, mL, st);
     });
   }
   // FP32 eigensolver starts, split by size class
   auto add_eig = [&](bool c1) {
+    cur_tag = c1 ? GSVD_RAND_STAGE_SMALL_CS : GSVD_RAND_STAGE_SMALL_JACOBI;
     for (int cls = 0; cls < 2; ++cls) {
       std::vector<EigB> t;
       int mN = 0;
@@ -1591,13 +1607,14 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
       if (t.empty()) continue;
       const size_t off = A.add(t);
       const int cnt = (int)t.size();
-      ops.push_back([off, cnt, mN](const unsigned char* d, cudaStream_t st) {
+      push([off, cnt, mN](const unsigned char* d, cudaStream_t st) {
         return launch_eig_f32_b(reinterpret_cast<const EigB*>(d + off), cnt, mN, st);
       });
     }
   };
   // Ogita-Aishima steps (three: the mixed-precision count), the cut cluster after the second
   auto add_oa = [&](bool c1) {
+    cur_tag = c1 ? GSVD_RAND_STAGE_SMALL_CS : GSVD_RAND_STAGE_SMALL_REFINE;
     std::vector<OaB> t(np);
     int mN = 0;
     for (int i = 0; i < np; ++i) {
@@ -1610,18 +1627,19 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
     oa_b_tables(t.data(), np, dg.data());
     const size_t ot = A.add(t), od = A.add(dg);
     for (int it = 0; it < 3; ++it) {
-      ops.push_back([ot, od, np, mN](const unsigned char* d, cudaStream_t st) {
+      push([ot, od, np, mN](const unsigned char* d, cudaStream_t st) {
         return launch_oa_refine_b(reinterpret_cast<const OaB*>(d + ot), reinterpret_cast<const DgemmB*>(d + od), np,
                                   mN, st);
       });
       if (!c1 && it == 1)
-        ops.push_back([ot, np, mN](const unsigned char* d, cudaStream_t st) {
+        push([ot, np, mN](const unsigned char* d, cudaStream_t st) {
           return launch_oa_cut_cluster_b(reinterpret_cast<const OaB*>(d + ot), np, mN, st);
         });
     }
   };
   add_eig(false);
   add_oa(false);
+  cur_tag = GSVD_RAND_STAGE_SMALL_CS;
   {
     std::vector<SelB> t(np);
     for (int i = 0; i < np; ++i) {
@@ -1630,7 +1648,7 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
     }
     const size_t off = A.add(t);
     const int mL = maxL;
-    ops.push_back([off, np, mL](const unsigned char* d, cudaStream_t st) {
+    push([off, np, mL](const unsigned char* d, cudaStream_t st) {
       return launch_select_topr_b(reinterpret_cast<const SelB*>(d + off), np, mL, st);
     });
   }
@@ -1653,12 +1671,13 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
     }
     const size_t off = A.add(t);
     const int mk = maxk;
-    ops.push_back([off, np, mk](const unsigned char* d, cudaStream_t st) {
+    push([off, np, mk](const unsigned char* d, cudaStream_t st) {
       return launch_dgemm_b<double, double>(reinterpret_cast<const DgemmB*>(d + off), np, mk, mk, st);
     });
   }
   add_eig(true);
   add_oa(true);
+  cur_tag = GSVD_RAND_STAGE_SMALL_CS;
   {
     std::vector<DgemmB> t(2 * (size_t)np);
     for (int i = 0; i < np; ++i) {
@@ -1678,7 +1697,7 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
     }
     const size_t off = A.add(t);
     const int ml = maxl1, mk = maxk, n2 = 2 * np;
-    ops.push_back([off, n2, ml, mk](const unsigned char* d, cudaStream_t st) {
+    push([off, n2, ml, mk](const unsigned char* d, cudaStream_t st) {
       return launch_dgemm_b<double, double>(reinterpret_cast<const DgemmB*>(d + off), n2, ml, mk, st);
     });
   }
@@ -1690,7 +1709,7 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
     }
     const size_t off = A.add(t);
     const int mk = maxk;
-    ops.push_back([off, np, mk](const unsigned char* d, cudaStream_t st) {
+    push([off, np, mk](const unsigned char* d, cudaStream_t st) {
       return launch_cs_norms_b(reinterpret_cast<const CsB*>(d + off), np, mk, st);
     });
   }
@@ -1808,27 +1827,49 @@ int solve_grouped(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs) {
     CU(cudaMemcpyAsync(dtab, g->host, gb.arena.buf.size(), cudaMemcpyHostToDevice, gs));
     // padding rows of the K-major bases stay zero (nothing writes them)
     for (auto& S : gb.sides)
-      if (S.lx > S.l) CU(cudaMemsetAsync(S.Qt + (int64_t)S.l * S.ldm, 0, (size_t)(S.lx - S.l) * S.ldm * sizeof(float), gs));
+      if (S.lx > S.l) {
+        CU(cudaMemsetAsync(S.Qt + (int64_t)S.l * S.ldm, 0, (size_t)(S.lx - S.l) * S.ldm * sizeof(float), gs));
+        CU(cudaMemsetAsync(S.R + (int64_t)S.l * S.lp, 0, (size_t)(S.lx - S.l) * S.lp * sizeof(float), gs));
+      }
     CU(cudaStreamSynchronize(gs));
     // autotune the products (outside the graph; results do not depend on the choice)
     DevStatus* st0 = reinterpret_cast<DevStatus*>(g->ws);
     for (auto& G : gb.gemms) {
       int s_ = 0, p_ = 0;
-      if ((rc = tune_group(h, gs, G.mode, prec, G.norm, dtab + G.off, G.nprob, G.ntiles, G.nmma, G.kmean, st0, &s_,
+      if ((rc = tune_group(h, gs, G.mode, G.prec, G.norm, dtab + G.off, G.nprob, G.ntiles, G.nmma, G.kmean, st0, &s_,
                            &p_)))
         return rc;
       G.stages = s_;
       G.per_sm = p_;
-      g->tuned[G.tune_slot][0] = s_;  // reported: the last launch of each kind
-      g->tuned[G.tune_slot][1] = p_;
+      if (G.tune_slot >= 0) {
+        g->tuned[G.tune_slot][0] = s_;  // reported: the last launch of each kind
+        g->tuned[G.tune_slot][1] = p_;
+      }
     }
     // capture the launch sequence
     const uint64_t c0 = g_launch_count.load();
     CU(cudaStreamBeginCapture(gs, cudaStreamCaptureModeRelaxed));
+    const bool prof = (h->cfg.flags & GSVD_RAND_FLAG_PROFILE) != 0;
+    for (auto e : g->prof_ev) cudaEventDestroy(e);
+    g->prof_ev.clear();
+    g->prof_tag.clear();
+    if (prof)
+      for (size_t i = 0; i < 2 * gb.ops.size(); ++i) {
+        cudaEvent_t e;
+        CU(cudaEventCreate(&e));
+        g->prof_ev.push_back(e);
+      }
     cudaError_t ce = cudaSuccess;
     size_t bad_op = 0;
-    for (auto& op : gb.ops) {
-      if ((ce = op(dtab, gs)) != cudaSuccess) break;
+    for (size_t i = 0; i < gb.ops.size(); ++i) {
+      // external records: event nodes of the graph (a plain record under capture is only an edge)
+      if (prof && (ce = cudaEventRecordWithFlags(g->prof_ev[2 * i], gs, cudaEventRecordExternal)) != cudaSuccess)
+        break;
+      if ((ce = gb.ops[i](dtab, gs)) != cudaSuccess) break;
+      if (prof) {
+        if ((ce = cudaEventRecordWithFlags(g->prof_ev[2 * i + 1], gs, cudaEventRecordExternal)) != cudaSuccess) break;
+        g->prof_tag.push_back(gb.tags[i]);
+      }
       ++bad_op;
     }
     cudaGraph_t graph = nullptr;
@@ -1851,6 +1892,18 @@ int solve_grouped(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs) {
   CU(cudaGraphLaunch(g->exec, gs));
   g_launch_count.fetch_add(g->launches_per_replay);
   g->replays += 1;
+  if (!g->prof_tag.empty()) {
+    CU(cudaStreamSynchronize(gs));
+    for (size_t i = 0; i < g->prof_tag.size(); ++i) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, g->prof_ev[2 * i], g->prof_ev[2 * i + 1]) == cudaSuccess) {
+        h->prof_ms[g->prof_tag[i]] += ms;
+        h->prof_calls[g->prof_tag[i]] += 1;
+      } else {
+        cudaGetLastError();
+      }
+    }
+  }
   // alpha / beta to device destinations: one scatter launch from a small table; host
   // destinations are filled from the results block below
   const int nv = (int)g->valid.size();
@@ -1915,11 +1968,21 @@ int solve_grouped(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs) {
         *q.r_out = r;
     }
   }
+  int where = 0, index = 0;
+  for (int t = 0; t < nv; ++t)
+    if (sth[t].code && first_bad < 0) {
+      first_bad = g->valid[t];
+      where = sth[t].where;
+      index = sth[t].index;
+    }
   for (int i = 0; i < npairs; ++i)
-    if (pairs[i].status && first_bad < 0) first_bad = i;
+    if (pairs[i].status && (first_bad < 0 || i < first_bad)) {
+      first_bad = i;
+      where = index = 0;
+    }
   if (first_bad >= 0)
-    return fail(h, pairs[first_bad].status, "pair %d (first failing pair): status %d", first_bad,
-                pairs[first_bad].status);
+    return fail(h, pairs[first_bad].status, "pair %d (first failing pair): status %d at stage %d (index %d)",
+                first_bad, pairs[first_bad].status, where, index);
   h->err.clear();
   return GSVD_RAND_OK;
 }

@@ -598,7 +598,7 @@ constexpr int CHOL_THREADS = 1024;
 template <typename TC>
 __device__ __forceinline__ void chol_shift_body(const double* __restrict__ W, int l, double shift_coef,
                                                 double tau_rel, TC* __restrict__ Rinv, DevStatus* st_dev, int stage,
-                                                TC* gscr, int use_smem) {
+                                                TC* gscr, int use_smem, int ldt = 0) {
   extern __shared__ unsigned char smem_raw[];
   const int lda = l | 1;
   TC* M = use_smem ? reinterpret_cast<TC*>(smem_raw) : gscr;
@@ -691,7 +691,10 @@ __device__ __forceinline__ void chol_shift_body(const double* __restrict__ W, in
       TC v = TC(0);
       if (j == c) v = s_scale[j];
       else if (j > c) v = M[(int64_t)j * lda + c] * s_scale[j];
-      Rinv[(int64_t)c * l + j] = v;
+      if (ldt)
+        Rinv[(int64_t)j * ldt + c] = v;  // transposed (K-major operand of Q = Y R^{-1})
+      else
+        Rinv[(int64_t)c * l + j] = v;
     }
 }
 
@@ -713,7 +716,7 @@ constexpr int CHOL64_THREADS = 256;
 
 template <typename TC>
 __device__ __forceinline__ void chol64_body(const double* __restrict__ W, int l, double shift_coef, double tau_rel,
-                                            TC* __restrict__ Rinv, DevStatus* st_dev, int stage) {
+                                            TC* __restrict__ Rinv, DevStatus* st_dev, int stage, int ldt = 0) {
   __shared__ TC s_row[2][128];
   __shared__ TC s_odiag[64], s_scale[64];
   __shared__ double s_tr;
@@ -841,7 +844,13 @@ __device__ __forceinline__ void chol64_body(const double* __restrict__ W, int l,
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       const int cc = t + 32 * c;
-      if (cc < l) Rinv[(int64_t)cc * l + j] = cc <= j ? a[r][2 + c] * sj : TC(0);
+      if (cc < l) {
+        const TC v = cc <= j ? a[r][2 + c] * sj : TC(0);
+        if (ldt)
+          Rinv[(int64_t)j * ldt + cc] = v;  // transposed (K-major operand of Q = Y R^{-1})
+        else
+          Rinv[(int64_t)cc * l + j] = v;
+      }
     }
   }
 }
@@ -1097,12 +1106,12 @@ cudaError_t launch_gram_reduce_b(const GramRedB* tab, int nprob, int max_l, cuda
 
 __global__ __launch_bounds__(CHOL64_THREADS, 1) void chol64_b_kernel(const CholB* __restrict__ tab) {
   const CholB& a = tab[blockIdx.x];
-  chol64_body<float>(a.W, a.l, a.shift_coef, a.tau_rel, a.Rinv, a.st, a.stage);
+  chol64_body<float>(a.W, a.l, a.shift_coef, a.tau_rel, a.Rinv, a.st, a.stage, a.ldt);
 }
 
 __global__ __launch_bounds__(CHOL_THREADS) void chol_shift_b_kernel(const CholB* __restrict__ tab) {
   const CholB& a = tab[blockIdx.x];
-  chol_shift_body<float>(a.W, a.l, a.shift_coef, a.tau_rel, a.Rinv, a.st, a.stage, nullptr, 1);
+  chol_shift_body<float>(a.W, a.l, a.shift_coef, a.tau_rel, a.Rinv, a.st, a.stage, nullptr, 1, a.ldt);
 }
 
 cudaError_t launch_chol_b(const CholB* tab, int nprob, int max_l, cudaStream_t st) {
@@ -1118,31 +1127,6 @@ cudaError_t launch_chol_b(const CholB* tab, int nprob, int max_l, cudaStream_t s
   return launched();
 }
 
-template <int CT, int RT>
-__global__ __launch_bounds__(256) void apply_rinv_b_kernel(const ApplyB* __restrict__ tab) {
-  const ApplyB& a = tab[blockIdx.z];
-  if ((int64_t)blockIdx.x * (16 * RT) >= a.M) return;
-  apply_rinv_body<float, float, CT, RT, true>(a.Y, a.ldy, a.M, a.l, a.Rinv, a.Q, a.ldq, a.transpose_out, nullptr,
-                                              (int)blockIdx.x);
-}
 
-int64_t apply_b_rows(int max_l) { return max_l <= 64 ? 128 : 32; }
-
-cudaError_t launch_apply_rinv_b(const ApplyB* tab, int nprob, int64_t max_M, int max_l, cudaStream_t st) {
-  if (nprob <= 0) return cudaSuccess;
-  if (max_l < 1 || max_l > 128) return cudaErrorInvalidValue;
-  const int ct = max_l <= 64 ? 4 : 8, rt = max_l <= 64 ? 8 : 2;
-  const int lp = 16 * ct, rows = 16 * rt;
-  const size_t smem = 2 * (size_t)rows * (lp + 1) * sizeof(float) + (size_t)lp * lp * sizeof(float);
-  const dim3 grid((unsigned)cdiv(max_M, rows), 1, (unsigned)nprob);
-  if (ct == 4) {
-    cudaFuncSetAttribute(apply_rinv_b_kernel<4, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    apply_rinv_b_kernel<4, 8><<<grid, 256, smem, st>>>(tab);
-  } else {
-    cudaFuncSetAttribute(apply_rinv_b_kernel<8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    apply_rinv_b_kernel<8, 2><<<grid, 256, smem, st>>>(tab);
-  }
-  return launched();
-}
 
 }  // namespace gsvdr

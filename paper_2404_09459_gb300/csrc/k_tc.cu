@@ -34,7 +34,7 @@ struct TcGroupProb {  // CUtensorMap members carry their own (>= 64-byte) alignm
   float* out;         // Y (GX) or the split partials (GTQ)
   int64_t ldo, out_rows, kdim, rows_per_split, split_stride;
   double* gnorm_part; // GX with the fused norm: 4 partial sums of G^2 per row tile
-  int ncols, nmma, tiles_x, pad;
+  int ncols, nmma, tiles_x, transpose_out;  // transpose_out: out[c * ldo + row] (GX)
 };
 
 namespace {
@@ -994,7 +994,15 @@ __global__ __launch_bounds__(TG_THREADS) void tc_group_kernel(const TcGroupProb*
       for (int c0 = 0; c0 < P.nmma; c0 += 16) {
         float v[16];
         tmem_ld16(src + (uint32_t)c0, v);
-        if (grow < P.out_rows) {
+        if (MODE == 0 && P.transpose_out) {
+          // column-major store: the 32 lanes write 32 consecutive rows of each column
+          if (grow < P.out_rows) {
+            float* dc = P.out + grow;
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj)
+              if (c0 + jj < P.ncols) dc[(int64_t)(c0 + jj) * P.ldo] = v[jj];
+          }
+        } else if (grow < P.out_rows) {
 #pragma unroll
           for (int jj = 0; jj < 16; jj += 4) {
             const int c = c0 + jj;
@@ -1061,6 +1069,7 @@ bool tc_group_build(int mode, const TcGroupSpec* specs, int nprob, void* host, i
     p.ncols = s.l;
     p.nmma = nmma;
     p.gnorm_part = s.gnorm_part;
+    p.transpose_out = s.transpose_out;
     if (mode == 0) {
       if (!make_map(&p.mapA, s.G, (uint64_t)s.n, (uint64_t)s.M, (uint64_t)s.ldg, TC_BM)) return false;
       if (!make_map(&p.mapB, s.Bt, (uint64_t)s.n, (uint64_t)nmma, (uint64_t)s.ldb, (uint32_t)nmma)) return false;

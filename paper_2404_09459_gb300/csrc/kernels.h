@@ -221,22 +221,14 @@ cudaError_t launch_gram_reduce_b(const GramRedB* tab, int nprob, int max_l, cuda
 struct CholB {  // shifted Cholesky with the inverse factor (FP32 factor), as launch_chol_shift
   const double* W;
   double shift_coef, tau_rel;
-  float* Rinv;
+  float* Rinv;   // ldt == 0: R^{-1} row-major (l x l); ldt > 0: its transpose, Rinv[j * ldt + c] = R^{-1}[c][j]
   DevStatus* st;
-  int l, stage;
+  int l, stage, ldt, pad;
 };
+
 // max_l <= 64: the register-resident elimination; <= 128: the shared-memory one.
 cudaError_t launch_chol_b(const CholB* tab, int nprob, int max_l, cudaStream_t st);
 
-struct ApplyB {  // Q = Y R^{-1} (FP32), as launch_apply_rinv without the fused Gram
-  const float* Y;
-  int64_t ldy, M;
-  const float* Rinv;
-  float* Q;
-  int64_t ldq;
-  int l, transpose_out;
-};
-cudaError_t launch_apply_rinv_b(const ApplyB* tab, int nprob, int64_t max_M, int max_l, cudaStream_t st);
 
 struct ResidB {  // cumulated residual of one side
   const double* gpart;

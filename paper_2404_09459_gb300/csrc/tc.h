@@ -48,6 +48,7 @@ int tc_gtq_splits_bf16(int64_t M, int64_t n, bool split);
 // G^2 per 128-row tile; mode 1 (GTQ) split-K partials of G^T Q with Bt = Q^T
 // (round_up(l,16) x M), `splits` row ranges of rps rows (a multiple of 32), partial z
 // at out + z * split_stride (n x l, ld ldo).
+// transpose_out (mode 0): Y stored column-major, out[c * ldo + row].
 struct TcGroupSpec {
   const float* G;
   int64_t ldg, M, n;
@@ -59,6 +60,7 @@ struct TcGroupSpec {
   int splits;
   int64_t rps, split_stride;
   double* gnorm_part;
+  int transpose_out;
 };
 // Tiles of a grouped launch (128-row tiles in mode 0; column tiles x splits in mode 1).
 int64_t tc_group_tiles(int mode, const TcGroupSpec* specs, int nprob);
