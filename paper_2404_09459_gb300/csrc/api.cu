@@ -213,12 +213,12 @@ struct Solver {
   DevStatus* st_dev;
   int prec;
   bool use_tc;
-  void* bar;  // grid barrier of the fused CholeskyQR2 (zeroed at solve start)
+  void* bar;  // grid barriers of the fused CholeskyQR2, one per side (zeroed at solve start)
   bool bf16;         // G is BF16: products on kind::f16 tensor cores
   bool split_power;  // BF16: power-step operands as hi + lo (two products)
 
   int orth(SideBufs<T>& b, const T* Yin, int64_t M, int l, int64_t lp, T* out, int64_t ldo,
-           int transpose_out, int stage) {
+           int transpose_out, int stage, int side = 0) {
     ProfScope ps(h, GSVD_RAND_STAGE_ORTH);
     // pass 1: shifted Cholesky of the Gram (Fukaya et al. 2020 shift scaled to the
     // Gram's accumulation precision), pass 2: plain CholeskyQR on the result.
@@ -230,8 +230,9 @@ struct Solver {
       if (ctas > 0 && ctas <= cholqr2_fused_max_ctas()) {
         const double shift_f = 11.0 * ((double)rp + l + 1) * u;
         const double tau_f = 8.0 * (double)rp * u;
-        CU((launch_cholqr2_fused<T, TC>(Yin, lp, M, l, ctas, rp, out, ldo, transpose_out, b.gpart, b.W, bar,
-                                        shift_f, tau_f, st_dev, stage, st)));
+        CU((launch_cholqr2_fused<T, TC>(Yin, lp, M, l, ctas, rp, out, ldo, transpose_out, b.gpart, b.W,
+                                        static_cast<unsigned char*>(bar) + side * cholqr2_fused_bar_bytes(), shift_f,
+                                        tau_f, st_dev, stage, st)));
         return GSVD_RAND_OK;
       }
     }
@@ -271,6 +272,36 @@ struct Solver {
       return rc;
     CU(launch_chol_shift<TC>(b.W, l, 0.0, tau, (TC*)b.R, (TC*)b.cscr, st_dev, stage + 1, st));
     CU((launch_apply_rinv<T, TC>(q2, lt, M, l, (const TC*)b.R, out, ldo, transpose_out, nullptr, st)));
+    return GSVD_RAND_OK;
+  }
+
+  // The same re-orthonormalisation for both sides at once: when both bases fit the fused
+  // kernel together (two CTAs per SM), one cooperative launch runs both sides' passes, so
+  // the latency of the Cholesky chains and grid barriers is paid once; otherwise side by side.
+  int orth2(SideBufs<T>* b, const T* const* Yin, const int64_t* M, int l, int64_t lp, T* const* out,
+            const int64_t* ldo, int transpose_out, const int* stage) {
+    int64_t rp[2] = {0, 0};
+    int ctas[2];
+    for (int s = 0; s < 2; ++s) ctas[s] = cholqr2_fused_plan<T, TC>(M[s], l, &rp[s]);
+    static const int cap = cholqr2_fused_max_total_ctas<T, TC>();
+    if (ctas[0] > 0 && ctas[1] > 0 && ctas[0] <= cholqr2_fused_max_ctas() && ctas[1] <= cholqr2_fused_max_ctas() &&
+        ctas[0] + ctas[1] <= cap) {
+      ProfScope ps(h, GSVD_RAND_STAGE_ORTH);
+      const double u = std::is_same<T, double>::value ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
+      FqBatch fb;
+      memset(&fb, 0, sizeof(fb));
+      fb.nprob = 2;
+      for (int s = 0; s < 2; ++s)
+        fb.p[s] = FqProb{Yin[s], lp, M[s], rp[s], out[s], ldo[s], b[s].gpart, b[s].W,
+                         static_cast<unsigned char*>(bar) + s * cholqr2_fused_bar_bytes(),
+                         11.0 * ((double)rp[s] + l + 1) * u, 8.0 * (double)rp[s] * u, l, ctas[s], transpose_out,
+                         stage[s]};
+      CU((launch_cholqr2_fused_n<T, TC>(fb, st_dev, st)));
+      return GSVD_RAND_OK;
+    }
+    int rc;
+    for (int s = 0; s < 2; ++s)
+      if ((rc = orth(b[s], Yin[s], M[s], l, lp, out[s], ldo[s], transpose_out, stage[s], s))) return rc;
     return GSVD_RAND_OK;
   }
 
@@ -334,6 +365,62 @@ struct Solver {
     return GSVD_RAND_OK;
   }
 
+  // Both sides in lockstep (each step for side 0, then side 1, the re-orthonormalisations
+  // of both in one launch where they fit): the per-side arithmetic of side() unchanged.
+  int sides(const void* const* G, const int64_t* ldg, const Plan& pl, SideBufs<T>* b, int q, uint64_t seed,
+            T* S) {
+    const int qt = use_tc ? 1 : 0;
+    int64_t ldq[2];
+    T* Qo[2];
+    T* Xo[2];
+    const T* Yi[2];
+    const T* Zi[2];
+    int64_t ldx2[2] = {pl.ldx, pl.ldx};
+    int st1[2], st3[2], st5[2];
+    for (int s = 0; s < 2; ++s) {
+      const int64_t M = pl.M[s];
+      if (bf16)
+        CU(launch_gaussian_kmajor_bf16(b[s].Xh, pl.ldx, pl.n, pl.l, (int)pl.lx, seed, h->pair_word, (uint32_t)s,
+                                       GSVD_RAND_STREAM_FIXED, st));
+      else
+        CU(launch_gaussian_kmajor<T>(b[s].Xt, pl.ldx, pl.n, pl.l, (int)pl.lx, seed, h->pair_word, (uint32_t)s,
+                                     GSVD_RAND_STREAM_FIXED, st));
+      ldq[s] = use_tc ? round_up(M, 4) : pl.lp;
+      if (use_tc)
+        CU(cudaMemsetAsync(b[s].Q + (int64_t)pl.l * ldq[s], 0, (size_t)(pl.lx - pl.l) * ldq[s] * sizeof(T), st));
+      Qo[s] = b[s].Q;
+      Xo[s] = b[s].Xt;
+      Yi[s] = b[s].Y;
+      Zi[s] = b[s].Z;
+      st1[s] = 10 * s + 1;
+      st3[s] = 10 * s + 3;
+      st5[s] = 10 * s + 5;
+    }
+    int rc;
+    for (int s = 0; s < 2; ++s)
+      if ((rc = gx(G[s], ldg[s], pl.M[s], pl, b[s], b[s].gnorm))) return rc;
+    if ((rc = orth2(b, Yi, pl.M, pl.l, pl.lp, Qo, ldq, qt, st1))) return rc;
+    const int64_t nn[2] = {pl.n, pl.n};
+    for (int it = 0; it < q; ++it) {
+      for (int s = 0; s < 2; ++s) {
+        if (bf16 && (rc = split_q(b[s], pl.M[s], pl, split_power))) return rc;
+        if ((rc = gtq(G[s], ldg[s], pl.M[s], pl, b[s], b[s].Z, pl.lp, 0, nullptr, split_power))) return rc;
+      }
+      if ((rc = orth2(b, Zi, nn, pl.l, pl.lp, Xo, ldx2, 1, st3))) return rc;
+      for (int s = 0; s < 2; ++s) {
+        if (bf16 && (rc = split_x(b[s], pl, split_power))) return rc;
+        if ((rc = gx(G[s], ldg[s], pl.M[s], pl, b[s], nullptr, split_power))) return rc;
+      }
+      if ((rc = orth2(b, Yi, pl.M, pl.l, pl.lp, Qo, ldq, qt, st5))) return rc;
+    }
+    for (int s = 0; s < 2; ++s) {
+      if (bf16 && (rc = split_q(b[s], pl.M[s], pl, true))) return rc;
+      if ((rc = gtq(G[s], ldg[s], pl.M[s], pl, b[s], S + (int64_t)s * pl.l * pl.ldn, pl.ldn, 1, b[s].bnorm, true)))
+        return rc;
+    }
+    return GSVD_RAND_OK;
+  }
+
   int side(const void* G, int64_t ldg, int s, const Plan& pl, SideBufs<T>& b, int q, uint64_t seed,
            T* Srows) {
     const int64_t M = pl.M[s];
@@ -351,16 +438,16 @@ struct Solver {
       CU(cudaMemsetAsync(b.Q + (int64_t)pl.l * ldq, 0, (size_t)(pl.lx - pl.l) * ldq * sizeof(T), st));
     int rc;
     if ((rc = gx(G, ldg, M, pl, b, b.gnorm))) return rc;
-    if ((rc = orth(b, b.Y, M, pl.l, pl.lp, b.Q, ldq, qt, 10 * s + 1))) return rc;
+    if ((rc = orth(b, b.Y, M, pl.l, pl.lp, b.Q, ldq, qt, 10 * s + 1, s))) return rc;
     // BF16 mode: the power steps take their FP32 operand rounded to BF16 (or as hi + lo
     // with split_power); the projection always takes Q as hi + lo
     for (int it = 0; it < q; ++it) {
       if (bf16 && (rc = split_q(b, M, pl, split_power))) return rc;
       if ((rc = gtq(G, ldg, M, pl, b, b.Z, pl.lp, 0, nullptr, split_power))) return rc;
-      if ((rc = orth(b, b.Z, pl.n, pl.l, pl.lp, b.Xt, pl.ldx, 1, 10 * s + 3))) return rc;
+      if ((rc = orth(b, b.Z, pl.n, pl.l, pl.lp, b.Xt, pl.ldx, 1, 10 * s + 3, s))) return rc;
       if (bf16 && (rc = split_x(b, pl, split_power))) return rc;
       if ((rc = gx(G, ldg, M, pl, b, nullptr, split_power))) return rc;
-      if ((rc = orth(b, b.Y, M, pl.l, pl.lp, b.Q, ldq, qt, 10 * s + 5))) return rc;
+      if ((rc = orth(b, b.Y, M, pl.l, pl.lp, b.Q, ldq, qt, 10 * s + 5, s))) return rc;
     }
     // projection B = Q^T G written as l rows of S
     if (bf16 && (rc = split_q(b, M, pl, true))) return rc;
@@ -551,7 +638,7 @@ int solve_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, const voi
   // host inputs are staged into the workspace
   Bump sizer;
   sizer.take<DevStatus>(1);
-  sizer.take<unsigned char>((int64_t)cholqr2_fused_bar_bytes());
+  sizer.take<unsigned char>(2 * (int64_t)cholqr2_fused_bar_bytes());
   if (!d1) sizer.take<unsigned char>(m * lds * eg);
   if (!d2) sizer.take<unsigned char>(p * lds * eg);
   sizer.take<T>((int64_t)pl.L * pl.ldn);
@@ -566,7 +653,7 @@ int solve_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, const voi
   Bump bp;
   bp.base = h->ws;
   DevStatus* st_dev = bp.take<DevStatus>(1);
-  void* bar = bp.take<unsigned char>((int64_t)cholqr2_fused_bar_bytes());
+  void* bar = bp.take<unsigned char>(2 * (int64_t)cholqr2_fused_bar_bytes());
   const void* G1 = G1v;
   const void* G2 = G2v;
   int64_t l1d = ld1, l2d = ld2;
@@ -589,11 +676,15 @@ int solve_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, const voi
   SideBufs<T> sb1 = side_take<T>(bp, pl, 1, use_tc, bf16);
   SmallBufs small = small_take(bp, pl.L, k, n);
   CU(cudaMemsetAsync(st_dev, 0, sizeof(DevStatus), st));
-  CU(cudaMemsetAsync(bar, 0, cholqr2_fused_bar_bytes(), st));
+  CU(cudaMemsetAsync(bar, 0, 2 * cholqr2_fused_bar_bytes(), st));
 
   Solver<T, TC> sv{h, st, st_dev, prec, use_tc, bar, bf16, (h->cfg.flags & GSVD_RAND_FLAG_BF16_SPLIT_POWER) != 0};
-  if ((rc = sv.side(G1, l1d, 0, pl, sb0, q, seed, S))) return rc;
-  if ((rc = sv.side(G2, l2d, 1, pl, sb1, q, seed, S + (int64_t)pl.l * pl.ldn))) return rc;
+  {
+    const void* Gs[2] = {G1, G2};
+    const int64_t lds2[2] = {l1d, l2d};
+    SideBufs<T> sbs[2] = {sb0, sb1};
+    if ((rc = sv.sides(Gs, lds2, pl, sbs, q, seed, S))) return rc;
+  }
   int gct0 = use_tc ? tc_gx_ctas(m) : gemm_gx_simt_ctas(m);
   int gct1 = use_tc ? tc_gx_ctas(p) : gemm_gx_simt_ctas(p);
   int bblk = (int)cdiv(n * pl.l, 256);
@@ -1584,6 +1675,7 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
       x.K = (int)P.n;
       x.ta = 0;
       x.tb = 1;
+      x.sym = 1;  // K = S S^T
     }
     const size_t off = A.add(t);
     const int mL = maxL;
@@ -1668,6 +1760,7 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
       x.K = P.l;
       x.ta = 1;
       x.tb = 0;
+      x.sym = 1;  // C1 = Z1^T Z1
     }
     const size_t off = A.add(t);
     const int mk = maxk;

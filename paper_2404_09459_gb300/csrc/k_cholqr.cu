@@ -19,6 +19,7 @@
 // releases every other waiting CTA.  The launch is cooperative, so all CTAs
 // are resident.
 #include <algorithm>
+#include <cstring>
 #include <mutex>
 
 #include "kernels.h"
@@ -41,7 +42,8 @@ struct GridBar {
   int pad;
 };
 
-__device__ bool grid_barrier(GridBar* b, DevStatus* st, int stage) {
+// Barrier over the `nctas` CTAs of one problem of the launch.
+__device__ bool grid_barrier(GridBar* b, DevStatus* st, int stage, unsigned nctas) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -51,7 +53,7 @@ __device__ bool grid_barrier(GridBar* b, DevStatus* st, int stage) {
     __threadfence();
     const unsigned arrived = atomicAdd(&b->count, 1u);
     int ok = 1;
-    if (arrived == gridDim.x - 1) {
+    if (arrived == nctas - 1) {
       atomicExch(&b->count, 0u);
       __threadfence();
       atomicAdd(&b->gen, 1u);
@@ -254,15 +256,26 @@ __device__ bool chol_block(const double* W, int l, double shift, double tau_rel,
 }
 
 template <typename T, typename TC>
-__global__ __launch_bounds__(FQ_THREADS, 1) void cholqr2_fused_kernel(
-    const T* __restrict__ Y, int64_t ldy, int64_t M, int l, int64_t rows_per, T* __restrict__ Q, int64_t ldq,
-    int transpose_out, double* part, double* W, GridBar* bar, double shift_coef, double tau_rel,
-    DevStatus* st_dev, int stage) {
+__global__ __launch_bounds__(FQ_THREADS, 2) void cholqr2_fused_kernel(FqBatch bt, DevStatus* st_dev) {
+  // CTAs [0, p[0].ctas) work on problem 0, the next p[1].ctas on problem 1 (the two sides of
+  // a pair share one launch: two CTAs per SM)
+  const int pi = (bt.nprob > 1 && (int)blockIdx.x >= bt.p[0].ctas) ? 1 : 0;
+  const FqProb& pr = bt.p[pi];
+  const unsigned bx = blockIdx.x - (pi ? (unsigned)bt.p[0].ctas : 0u);
+  const unsigned nb = (unsigned)pr.ctas;
+  const T* __restrict__ Y = static_cast<const T*>(pr.Y);
+  T* __restrict__ Q = static_cast<T*>(pr.Q);
+  const int64_t ldy = pr.ldy, M = pr.M, rows_per = pr.rows_per, ldq = pr.ldq;
+  const int l = pr.l, transpose_out = pr.transpose_out, stage = pr.stage;
+  double* part = pr.part;
+  double* W = pr.W;
+  GridBar* bar = static_cast<GridBar*>(pr.bar);
+  const double shift_coef = pr.shift_coef, tau_rel = pr.tau_rel;
   extern __shared__ __align__(16) unsigned char fq_smem[];
   T* Ys = reinterpret_cast<T*>(fq_smem);  // FQ_ROWS x FQ_LS: Y, then Q1
   T* Rs = Ys + FQ_ROWS * FQ_LS;           // FQ_LP x FQ_LP: R^{-1} of the current pass
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int64_t r0 = (int64_t)blockIdx.x * rows_per;
+  const int64_t r0 = (int64_t)bx * rows_per;
   const int64_t left = M - r0;
   const int rows = (int)(left < 0 ? 0 : (left < rows_per ? left : rows_per));
   for (int e = tid; e < FQ_ROWS * FQ_LP; e += FQ_THREADS) {
@@ -309,7 +322,7 @@ __global__ __launch_bounds__(FQ_THREADS, 1) void cholqr2_fused_kernel(
           for (int b = 0; b < 4; ++b) g[a][b] = fma(x[a], y[b], g[a][b]);
       }
       if (tx >= ty) {
-        double* P = part + (int64_t)blockIdx.x * ll;
+        double* P = part + (int64_t)bx * ll;
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -319,17 +332,16 @@ __global__ __launch_bounds__(FQ_THREADS, 1) void cholqr2_fused_kernel(
           }
       }
     }
-    if (!grid_barrier(bar, st_dev, stage + pass)) return;
+    if (!grid_barrier(bar, st_dev, stage + pass, nb)) return;
     // 2. W = sum of the partials (upper entries, mirrored): a warp per entry, lanes over
     //    the partials, a fixed shuffle tree (deterministic)
     {
       const int warp = tid >> 5, lane = tid & 31;
-      for (int64_t e = (int64_t)blockIdx.x * (FQ_THREADS / 32) + warp; e < ll;
-           e += (int64_t)gridDim.x * (FQ_THREADS / 32)) {
+      for (int64_t e = (int64_t)bx * (FQ_THREADS / 32) + warp; e < ll; e += (int64_t)nb * (FQ_THREADS / 32)) {
         const int i = (int)(e / l), j = (int)(e % l);
         if (j < i) continue;
         double s = 0.0;
-        for (unsigned c = lane; c < gridDim.x; c += 32) s += __ldcg(part + (int64_t)c * ll + e);
+        for (unsigned c = lane; c < nb; c += 32) s += __ldcg(part + (int64_t)c * ll + e);
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) {
           W[(int64_t)i * l + j] = s;
@@ -337,7 +349,7 @@ __global__ __launch_bounds__(FQ_THREADS, 1) void cholqr2_fused_kernel(
         }
       }
     }
-    if (!grid_barrier(bar, st_dev, stage + pass)) return;
+    if (!grid_barrier(bar, st_dev, stage + pass, nb)) return;
     // 3. R^{-1} in every CTA (every CTA takes the same decisions).  When the third
     //    pass finds Q2 orthonormal to first order (max |W - I| <= 0.05), one
     //    Newton-Schulz step X = (3 I - W) / 2 (error O(||W - I||^2)) takes the place
@@ -361,7 +373,7 @@ __global__ __launch_bounds__(FQ_THREADS, 1) void cholqr2_fused_kernel(
     if (!newton) {
       float cond2 = 0.f;
       if (!chol_block<T, TC>(W, l, pass == 0 ? shift_coef : 0.0, tau_rel, Rs, st_dev, stage + (pass > 0),
-                             blockIdx.x == 0, &cond2))
+                             bx == 0, &cond2))
         return;
       if (pass == 1) third = cond2 > cond2_max;
     } else {
@@ -462,24 +474,50 @@ int cholqr2_fused_plan(int64_t M, int l, int64_t* rows_per) {
 }
 
 template <typename T, typename TC>
-cudaError_t launch_cholqr2_fused(const T* Y, int64_t ldy, int64_t M, int l, int ctas, int64_t rows_per, T* Q,
-                                 int64_t ldq, int transpose_out, double* part, double* W, void* bar,
-                                 double shift_coef, double tau_rel, DevStatus* st_dev, int stage, cudaStream_t st) {
+cudaError_t launch_cholqr2_fused_n(const FqBatch& bt, DevStatus* st_dev, cudaStream_t st) {
   const size_t smem = fq_smem_bytes<T>();
-  int tr = transpose_out;
-  GridBar* gb = static_cast<GridBar*>(bar);
-  void* args[] = {(void*)&Y, (void*)&ldy, (void*)&M, (void*)&l, (void*)&rows_per, (void*)&Q, (void*)&ldq,
-                  (void*)&tr, (void*)&part, (void*)&W, (void*)&gb, (void*)&shift_coef, (void*)&tau_rel,
-                  (void*)&st_dev, (void*)&stage};
+  FqBatch b = bt;
+  int ctas = 0;
+  for (int i = 0; i < b.nprob; ++i) ctas += b.p[i].ctas;
+  void* args[] = {(void*)&b, (void*)&st_dev};
   cudaError_t e = cudaLaunchCooperativeKernel((const void*)cholqr2_fused_kernel<T, TC>, dim3((unsigned)ctas),
                                               dim3(FQ_THREADS), args, smem, st);
   if (e != cudaSuccess) return e;
   return launched();
 }
 
+template <typename T, typename TC>
+cudaError_t launch_cholqr2_fused(const T* Y, int64_t ldy, int64_t M, int l, int ctas, int64_t rows_per, T* Q,
+                                 int64_t ldq, int transpose_out, double* part, double* W, void* bar,
+                                 double shift_coef, double tau_rel, DevStatus* st_dev, int stage, cudaStream_t st) {
+  FqBatch b;
+  memset(&b, 0, sizeof(b));
+  b.nprob = 1;
+  b.p[0] = FqProb{Y, ldy, M, rows_per, Q, ldq, part, W, bar, shift_coef, tau_rel, l, ctas, transpose_out, stage};
+  return launch_cholqr2_fused_n<T, TC>(b, st_dev, st);
+}
+
+template <typename T, typename TC>
+int cholqr2_fused_max_total_ctas() {
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, cholqr2_fused_kernel<T, TC>, FQ_THREADS, fq_smem_bytes<T>()) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return sms * per;
+}
+
 template int cholqr2_fused_plan<float, float>(int64_t, int, int64_t*);
 template int cholqr2_fused_plan<float, double>(int64_t, int, int64_t*);
 template int cholqr2_fused_plan<double, double>(int64_t, int, int64_t*);
+template cudaError_t launch_cholqr2_fused_n<float, float>(const FqBatch&, DevStatus*, cudaStream_t);
+template cudaError_t launch_cholqr2_fused_n<float, double>(const FqBatch&, DevStatus*, cudaStream_t);
+template cudaError_t launch_cholqr2_fused_n<double, double>(const FqBatch&, DevStatus*, cudaStream_t);
+template int cholqr2_fused_max_total_ctas<float, float>();
+template int cholqr2_fused_max_total_ctas<float, double>();
+template int cholqr2_fused_max_total_ctas<double, double>();
 template cudaError_t launch_cholqr2_fused<float, float>(const float*, int64_t, int64_t, int, int, int64_t, float*,
                                                         int64_t, int, double*, double*, void*, double, double,
                                                         DevStatus*, int, cudaStream_t);

@@ -768,6 +768,8 @@ __global__ __launch_bounds__(256) void dgemm_b_kernel(const DgemmB* __restrict__
   const DgemmB& g = tab[blockIdx.z];
   const int i0 = blockIdx.x * SG_T, j0 = blockIdx.y * SG_T;
   if (i0 >= g.Mr || j0 >= g.Nc) return;
+  // symmetric result: the upper tiles only, mirrored on the way out
+  if (g.sym && blockIdx.x > blockIdx.y) return;
   __shared__ double As[SG_BK][SG_T + 1];
   __shared__ double Bs[SG_BK][SG_T + 1];
   const TA* __restrict__ A = static_cast<const TA*>(g.A);
@@ -789,15 +791,19 @@ __global__ __launch_bounds__(256) void dgemm_b_kernel(const DgemmB* __restrict__
       Bs[kk][j] = (gj < g.Nc && gk < K) ? (double)(tb ? B[(int64_t)gj * g.ldb + gk] : B[(int64_t)gk * g.ldb + gj]) : 0.0;
     }
     __syncthreads();
-    const int kk_end = min(SG_BK, K - k0);
+    // threads whose rows and columns all lie past the edge skip the FP64 work (the SM's
+    // FP64 units, ~1/64 of its FP32 rate, then go to the threads with real outputs)
+    if (i0 + ty * 2 < g.Mr && j0 + tx * 2 < g.Nc) {
+      const int kk_end = min(SG_BK, K - k0);
 #pragma unroll 8
-    for (int kk = 0; kk < kk_end; ++kk) {
-      const double a0 = As[kk][ty * 2], a1 = As[kk][ty * 2 + 1];
-      const double b0 = Bs[kk][tx * 2], b1 = Bs[kk][tx * 2 + 1];
-      acc[0][0] = fma(a0, b0, acc[0][0]);
-      acc[0][1] = fma(a0, b1, acc[0][1]);
-      acc[1][0] = fma(a1, b0, acc[1][0]);
-      acc[1][1] = fma(a1, b1, acc[1][1]);
+      for (int kk = 0; kk < kk_end; ++kk) {
+        const double a0 = As[kk][ty * 2], a1 = As[kk][ty * 2 + 1];
+        const double b0 = Bs[kk][tx * 2], b1 = Bs[kk][tx * 2 + 1];
+        acc[0][0] = fma(a0, b0, acc[0][0]);
+        acc[0][1] = fma(a0, b1, acc[0][1]);
+        acc[1][0] = fma(a1, b0, acc[1][0]);
+        acc[1][1] = fma(a1, b1, acc[1][1]);
+      }
     }
     __syncthreads();
   }
@@ -806,7 +812,9 @@ __global__ __launch_bounds__(256) void dgemm_b_kernel(const DgemmB* __restrict__
       const int i = i0 + ty * 2 + m, j = j0 + tx * 2 + q;
       if (i < g.Mr && j < g.Nc) {
         double* c = g.C + (int64_t)i * g.ldc + j;
-        *c = g.beta == 0.0 ? g.alpha * acc[m][q] : g.alpha * acc[m][q] + g.beta * (*c);
+        const double v = g.beta == 0.0 ? g.alpha * acc[m][q] : g.alpha * acc[m][q] + g.beta * (*c);
+        *c = v;
+        if (g.sym && blockIdx.x < blockIdx.y) g.C[(int64_t)j * g.ldc + i] = v;
       }
     }
 }
@@ -903,9 +911,11 @@ void oa_b_tables(const OaB* h, int nprob, DgemmB* dg) {
       g.tb = tb;
       return g;
     };
-    dg[i] = mk(o.X, 1, o.X, 0, o.XtX);               // X^T X
+    dg[i] = mk(o.X, 1, o.X, 0, o.XtX);               // X^T X (symmetric)
+    dg[i].sym = 1;
     dg[nprob + i] = mk(o.A, 0, o.X, 0, o.P);         // A X
-    dg[2 * nprob + i] = mk(o.X, 1, o.P, 0, o.S);     // X^T (A X)
+    dg[2 * nprob + i] = mk(o.X, 1, o.P, 0, o.S);     // X^T (A X) (symmetric: A is)
+    dg[2 * nprob + i].sym = 1;
     dg[3 * nprob + i] = mk(o.X, 0, o.F, 0, o.P);     // X F
   }
 }

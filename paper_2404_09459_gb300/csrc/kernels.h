@@ -140,6 +140,29 @@ cudaError_t launch_cholqr2_fused(const T* Y, int64_t ldy, int64_t M, int l, int 
                                  int64_t ldq, int transpose_out, double* part, double* W, void* bar,
                                  double shift_coef, double tau_rel, DevStatus* st_dev, int stage, cudaStream_t st);
 
+// Up to two problems (the two sides of a pair) in one cooperative launch: the CTAs of
+// problem i follow those of problem i - 1; each problem has its own barrier word, partials
+// and W.  The total CTA count must not exceed cholqr2_fused_max_total_ctas().
+struct FqProb {
+  const void* Y;
+  int64_t ldy, M, rows_per;
+  void* Q;
+  int64_t ldq;
+  double* part;
+  double* W;
+  void* bar;
+  double shift_coef, tau_rel;
+  int l, ctas, transpose_out, stage;
+};
+struct FqBatch {
+  FqProb p[2];
+  int nprob, pad;
+};
+template <typename T, typename TC>
+cudaError_t launch_cholqr2_fused_n(const FqBatch& b, DevStatus* st_dev, cudaStream_t st);
+template <typename T, typename TC>
+int cholqr2_fused_max_total_ctas();
+
 // The cluster of eigenvalues (within the last refinement step's delta) that
 // straddles the cut between the r-th and (r+1)-th largest: its block of
 // X^T A X is diagonalised (FP32 Jacobi, shifted and scaled) and its columns of
@@ -247,7 +270,8 @@ struct DgemmB {
   double* C;
   int64_t lda, ldb, ldc;
   double alpha, beta;
-  int Mr, Nc, K, ta, tb, pad;
+  int Mr, Nc, K, ta, tb;
+  int sym;  // the result is symmetric (Mr == Nc): upper tiles computed and mirrored
 };
 template <typename TA, typename TB>
 cudaError_t launch_dgemm_b(const DgemmB* tab, int nprob, int max_Mr, int max_Nc, cudaStream_t st);
