@@ -1609,8 +1609,8 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
         const int cnt = (int)ct[cls].size(), ml = maxlc[cls], mch = maxch[cls];
         push([og, orr, oc, cnt, ml, mch](const unsigned char* d, cudaStream_t st) {
           cudaError_t e;
-          if ((e = launch_gram_partial_b(reinterpret_cast<const GramB*>(d + og), cnt, mch, ml, st))) return e;
-          if ((e = launch_gram_reduce_b(reinterpret_cast<const GramRedB*>(d + orr), cnt, ml, st))) return e;
+          if ((e = launch_gram_blocks_b(reinterpret_cast<const GramB*>(d + og), cnt, mch, ml, st))) return e;
+          if ((e = launch_gram_sum_b(reinterpret_cast<const GramRedB*>(d + orr), cnt, ml, st))) return e;
           return launch_chol_b(reinterpret_cast<const CholB*>(d + oc), cnt, ml, st);
         });
       }

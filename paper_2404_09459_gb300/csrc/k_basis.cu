@@ -475,6 +475,7 @@ __device__ __forceinline__ void gram_partial_body(const T* __restrict__ Y, int64
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int64_t rbeg = (int64_t)c * rows_per_chunk, rend = min(M, rbeg + rows_per_chunk);
   const int i0 = ti * GR_T, j0 = tj * GR_T;
+  const bool active = i0 + ty * 4 < l && j0 + tx * 4 < l && (ti != tj || tx >= ty);
   T acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -490,17 +491,21 @@ __device__ __forceinline__ void gram_partial_body(const T* __restrict__ Y, int64
       Bs[rr][cc] = (rok && j0 + cc < l) ? Y[gr * ldy + j0 + cc] : T(0);
     }
     __syncthreads();
+    // only threads with a stored output (inside l, on or above the diagonal) do the FMAs:
+    // for narrow bases most of the 64 x 64 tile is padding
+    if (active) {
 #pragma unroll
-    for (int kk = 0; kk < GR_BK; ++kk) {
-      T a[4], b[4];
+      for (int kk = 0; kk < GR_BK; ++kk) {
+        T a[4], b[4];
 #pragma unroll
-      for (int m = 0; m < 4; ++m) a[m] = As[kk][ty * 4 + m];
+        for (int m = 0; m < 4; ++m) a[m] = As[kk][ty * 4 + m];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) b[q] = Bs[kk][tx * 4 + q];
+        for (int q = 0; q < 4; ++q) b[q] = Bs[kk][tx * 4 + q];
 #pragma unroll
-      for (int m = 0; m < 4; ++m)
+        for (int m = 0; m < 4; ++m)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[m][q] = fma(a[m], b[q], acc[m][q]);
+          for (int q = 0; q < 4; ++q) acc[m][q] = fma(a[m], b[q], acc[m][q]);
+      }
     }
     __syncthreads();
   }
@@ -1076,33 +1081,7 @@ cudaError_t launch_reduce_splits_b(const ReduceB* tab, int nprob, int64_t max_nl
   return launched();
 }
 
-__global__ __launch_bounds__(256) void gram_partial_b_kernel(const GramB* __restrict__ tab, int tdim) {
-  const GramB& a = tab[blockIdx.z];
-  const int ti = (int)blockIdx.y / tdim, tj = (int)blockIdx.y % tdim;
-  const int t = (a.l + GR_T - 1) / GR_T;
-  if ((int)blockIdx.x >= a.chunks || ti >= t || tj >= t || ti > tj) return;
-  gram_partial_body<float>(a.Y, a.ldy, a.M, a.l, a.part, a.rpc, (int)blockIdx.x, ti, tj);
-}
 
-cudaError_t launch_gram_partial_b(const GramB* tab, int nprob, int max_chunks, int max_l, cudaStream_t st) {
-  if (nprob <= 0) return cudaSuccess;
-  const int t = (int)cdiv(max_l, GR_T);
-  gram_partial_b_kernel<<<dim3((unsigned)max_chunks, (unsigned)(t * t), (unsigned)nprob), 256, 0, st>>>(tab, t);
-  return launched();
-}
-
-__global__ void gram_reduce_b_kernel(const GramRedB* __restrict__ tab) {
-  const GramRedB& a = tab[blockIdx.z];
-  if ((((int64_t)blockIdx.x * blockDim.x) >> 5) >= (int64_t)a.l * a.l) return;
-  gram_reduce_body(a.part, a.chunks, a.l, a.W, (int)blockIdx.x);
-}
-
-cudaError_t launch_gram_reduce_b(const GramRedB* tab, int nprob, int max_l, cudaStream_t st) {
-  if (nprob <= 0) return cudaSuccess;
-  const int64_t threads = (int64_t)max_l * max_l * 32;
-  gram_reduce_b_kernel<<<dim3((unsigned)cdiv(threads, 256), 1, (unsigned)nprob), 256, 0, st>>>(tab);
-  return launched();
-}
 
 __global__ __launch_bounds__(CHOL64_THREADS, 1) void chol64_b_kernel(const CholB* __restrict__ tab) {
   const CholB& a = tab[blockIdx.x];
@@ -1128,5 +1107,154 @@ cudaError_t launch_chol_b(const CholB* tab, int nprob, int max_l, cudaStream_t s
 }
 
 
+
+// ---------------------------------------------------------------------------
+// Batched Gram partials for bases of up to 128 columns (the grouped solve's
+// CholeskyQR): one CTA per (chunk of rows, problem) holds the whole upper
+// triangle of the chunk's Y^T Y in 8 x 8 register blocks, one block per thread;
+// for narrow bases the threads form up to 8 groups that take interleaved rows
+// of each 32-row slab, and the groups' sums are added in group order at the end
+// (deterministic).  The slabs are double-buffered: the next one is loaded into
+// registers while the current one is multiplied.
+// ---------------------------------------------------------------------------
+constexpr int GB_SLAB = 32, GB_LP = 128, GB_LS = GB_LP + 4;
+
+__global__ __launch_bounds__(256, 2) void gram_blocks_b_kernel(const GramB* __restrict__ tab) {
+  const GramB& g = tab[blockIdx.z];
+  const int c = blockIdx.x;
+  if (c >= g.chunks) return;
+  __shared__ __align__(16) float Ys[2][GB_SLAB * GB_LS];
+  const int tid = threadIdx.x, l = g.l;
+  const int LB = (l + 7) >> 3, nblk = LB * (LB + 1) / 2;
+  const int G = max(1, min(8, 256 / nblk));
+  const int grp = tid / nblk, bp = tid - grp * nblk;
+  const bool active = grp < G;
+  // block pair bp -> (bi, bj), bi <= bj, row by row of the upper triangle
+  int bi = 0, rem = bp;
+  while (active && rem >= LB - bi) {
+    rem -= LB - bi;
+    ++bi;
+  }
+  const int bj = bi + rem;
+  const int64_t rbeg = (int64_t)c * g.rpc, rend = min(g.M, rbeg + g.rpc);
+  const int nslab = (int)((rend - rbeg + GB_SLAB - 1) / GB_SLAB);
+  const int lq = (l + 3) >> 2;  // float4 per row
+  // slab loader: element e of the slab (row e / 32, float4 e % 32), four per thread, as
+  // asynchronous 16-byte copies that zero-fill past the rows of the chunk and column l
+  auto issue = [&](int sidx, int buf) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + 256 * q, r = e >> 5, c4 = e & 31;
+      const int64_t row = rbeg + (int64_t)sidx * GB_SLAB + r;
+      const float* src = g.Y;
+      int bytes = 0;
+      if (row < rend && c4 < lq) {
+        src = g.Y + row * g.ldy + 4 * c4;
+        bytes = 4 * min(4, l - 4 * c4);
+      }
+      const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&Ys[buf][r * GB_LS + 4 * c4]);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  float acc[8][8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+  if (nslab > 0) issue(0, 0);
+  for (int si = 0; si < nslab; ++si) {
+    const int buf = si & 1;
+    if (si + 1 < nslab) {
+      issue(si + 1, buf ^ 1);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    __syncthreads();
+    if (active) {
+      const float* base = Ys[buf];
+      for (int r = grp; r < GB_SLAB; r += G) {
+        const float* row = base + r * GB_LS;
+        const float4 a0 = *reinterpret_cast<const float4*>(row + 8 * bi);
+        const float4 a1 = *reinterpret_cast<const float4*>(row + 8 * bi + 4);
+        const float4 b0 = *reinterpret_cast<const float4*>(row + 8 * bj);
+        const float4 b1 = *reinterpret_cast<const float4*>(row + 8 * bj + 4);
+        const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+          for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+      }
+    }
+    __syncthreads();
+  }
+  // groups 1..G-1 hand their sums to group 0 through shared memory: the two slab buffers
+  // (2 x 32 x 132 floats) take `cap` blocks of 64 values, so as many groups per round
+  float* red = &Ys[0][0];
+  const int cap = (2 * GB_SLAB * GB_LS) / 64;  // blocks of 64 values that fit
+  for (int g0 = 1; g0 < G; g0 += max(1, cap / nblk)) {
+    const int g1 = min(G, g0 + max(1, cap / nblk));
+    if (active && grp >= g0 && grp < g1) {
+      float* dst = red + ((size_t)(grp - g0) * nblk + bp) * 64;
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) dst[a * 8 + b] = acc[a][b];
+    }
+    __syncthreads();
+    if (active && grp == 0)
+      for (int gg = g0; gg < g1; ++gg) {
+        const float* srcp = red + ((size_t)(gg - g0) * nblk + bp) * 64;
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+          for (int b = 0; b < 8; ++b) acc[a][b] += srcp[a * 8 + b];
+      }
+    __syncthreads();
+  }
+  if (active && grp == 0) {
+    double* P = g.part + (int64_t)c * l * l;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int i = 8 * bi + a;
+      if (i >= l) continue;
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        const int j = 8 * bj + b;
+        if (j < l && j >= i) P[(int64_t)i * l + j] = (double)acc[a][b];
+      }
+    }
+  }
+}
+
+cudaError_t launch_gram_blocks_b(const GramB* tab, int nprob, int max_chunks, int max_l, cudaStream_t st) {
+  if (nprob <= 0) return cudaSuccess;
+  if (max_l < 1 || max_l > GB_LP) return cudaErrorInvalidValue;
+  gram_blocks_b_kernel<<<dim3((unsigned)max_chunks, 1, (unsigned)nprob), 256, 0, st>>>(tab);
+  return launched();
+}
+
+// W = sum of the chunk partials in chunk order, a thread per upper entry (coalesced
+// across the entries of each partial), mirrored.
+__global__ void gram_sum_b_kernel(const GramRedB* __restrict__ tab) {
+  const GramRedB& a = tab[blockIdx.z];
+  const int64_t ll = (int64_t)a.l * a.l;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ll) return;
+  const int i = (int)(e / a.l), j = (int)(e % a.l);
+  if (j < i) return;
+  double s = 0.0;
+  for (int c = 0; c < a.chunks; ++c) s += a.part[(int64_t)c * ll + e];
+  a.W[e] = s;
+  a.W[(int64_t)j * a.l + i] = s;
+}
+
+cudaError_t launch_gram_sum_b(const GramRedB* tab, int nprob, int max_l, cudaStream_t st) {
+  if (nprob <= 0) return cudaSuccess;
+  gram_sum_b_kernel<<<dim3((unsigned)cdiv((int64_t)max_l * max_l, 256), 1, (unsigned)nprob), 256, 0, st>>>(tab);
+  return launched();
+}
 
 }  // namespace gsvdr

@@ -728,17 +728,25 @@ __device__ __forceinline__ void eig128_body(const double* __restrict__ Ain, int 
     float v[4];
 #pragma unroll
     for (int r = 0; r < 4; ++r) v[r] = Vref[(size_t)k * E_NMAX + t + 32 * r];
+    // the four column sums reduced together (independent shuffle chains)
+    float sc[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      float s = 0.f;
+      sc[c] = 0.f;
 #pragma unroll
       for (int r = 0; r < 4; ++r)
-        if (32 * r + 31 > k) s = fmaf(v[r], z[r][c], s);
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      s *= bk;
+        if (32 * r + 31 > k) sc[c] = fmaf(v[r], z[r][c], sc[c]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) sc[c] += __shfl_xor_sync(0xffffffffu, sc[c], o);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const float sb = sc[c] * bk;
 #pragma unroll
       for (int r = 0; r < 4; ++r)
-        if (32 * r + 31 > k) z[r][c] -= s * v[r];
+        if (32 * r + 31 > k) z[r][c] -= sb * v[r];
     }
   }
   __syncthreads();

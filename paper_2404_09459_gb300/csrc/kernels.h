@@ -226,20 +226,21 @@ struct ReduceB {  // as launch_reduce_splits<float, float>; sq_part gets cdiv(n 
 };
 cudaError_t launch_reduce_splits_b(const ReduceB* tab, int nprob, int64_t max_nl, cudaStream_t st);
 
-struct GramB {  // Gram partials of Y (M x l, FP32) over `chunks` chunks of rpc rows
+struct GramB {  // Gram partials of Y (M x l, FP32, l <= 128) over `chunks` chunks of rpc rows
   const float* Y;
   int64_t ldy, M, rpc;
   int l, chunks;
   double* part;
 };
-cudaError_t launch_gram_partial_b(const GramB* tab, int nprob, int max_chunks, int max_l, cudaStream_t st);
-
 struct GramRedB {  // W = sum of the chunk partials
   const double* part;
   int chunks, l;
   double* W;
 };
-cudaError_t launch_gram_reduce_b(const GramRedB* tab, int nprob, int max_l, cudaStream_t st);
+// The whole upper triangle of a chunk's Y^T Y in one CTA (register blocks, FP32 FMA over
+// the chunk's rows), then the chunk sums in FP64 a thread per entry (both deterministic).
+cudaError_t launch_gram_blocks_b(const GramB* tab, int nprob, int max_chunks, int max_l, cudaStream_t st);
+cudaError_t launch_gram_sum_b(const GramRedB* tab, int nprob, int max_l, cudaStream_t st);
 
 struct CholB {  // shifted Cholesky with the inverse factor (FP32 factor), as launch_chol_shift
   const double* W;
