@@ -1401,7 +1401,7 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
       S.gpart = bp.take<double>((int64_t)S.gchunks * P.l * P.l);
       S.W = bp.take<double>((int64_t)P.l * P.l);
       S.R = bp.take<float>((int64_t)S.lx * S.lp);
-      S.gnorm = bp.take<double>(4 * cdiv(S.M, 128));
+      S.gnorm = bp.take<double>(tc_group_norm_parts() * cdiv(S.M, 128));
       S.bnorm = bp.take<double>(cdiv(S.n * P.l, 256));
     }
   const int L = P.L;
@@ -1642,7 +1642,7 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
     std::vector<ResidB> t(ns);
     for (int j = 0; j < ns; ++j) {
       const GSide& S = gb.sides[j];
-      t[j] = ResidB{S.gnorm, S.bnorm, gb.prs[j / 2].resid + (j & 1), (int)(4 * cdiv(S.M, 128)),
+      t[j] = ResidB{S.gnorm, S.bnorm, gb.prs[j / 2].resid + (j & 1), (int)(tc_group_norm_parts() * cdiv(S.M, 128)),
                     (int)cdiv(S.n * S.l, 256)};
     }
     const size_t off = A.add(t);

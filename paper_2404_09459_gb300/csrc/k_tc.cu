@@ -747,7 +747,9 @@ cudaError_t tc_gemm_gtq_bf16(const void* G, int64_t ldg, int64_t M, int64_t n, c
 // ---------------------------------------------------------------------------
 namespace {
 
-constexpr int TG_THREADS = 320;
+constexpr int TG_PREP_WARPS = 8;                   // operand preparation warps
+constexpr int TG_THREADS = 32 * (6 + TG_PREP_WARPS);  // + TMA, MMA and four drain warps
+constexpr int TG_LO_STAGES = 2;  // depth of the low-half ring of the 3xTF32 Y = G X product
 
 template <int MODE, bool NORM, bool SPLIT>
 __global__ __launch_bounds__(TG_THREADS) void tc_group_kernel(const TcGroupProb* __restrict__ probs,
@@ -758,11 +760,21 @@ __global__ __launch_bounds__(TG_THREADS) void tc_group_kernel(const TcGroupProb*
   constexpr int EB = 4, BKE = 32;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  // RING2 (Y = G X with 3xTF32): the TMA ring holds {A, B} only (`stages` deep) and a
+  // second, shallow ring (TG_LO_STAGES) holds the low halves {A_lo, B_lo} that the prep
+  // warps write; the MMA reads both.  More of G is in flight for the same shared memory.
+  constexpr bool RING2 = MODE == 0 && SPLIT;
   const StageLayout L(MODE, SPLIT, nmma_max, EB);
-  uint64_t* full = reinterpret_cast<uint64_t*>(base + (size_t)stages * L.bytes);
+  const uint32_t nb = ((uint32_t)nmma_max * 128u + 1023u) & ~1023u;
+  const uint32_t sa_bytes = RING2 ? (uint32_t)TC_A_BYTES + nb : L.bytes;  // one stage of the TMA ring
+  const uint32_t sp_bytes = RING2 ? (uint32_t)TC_A_BYTES + nb : 0u;      // one stage of the low ring
+  constexpr int SP = RING2 ? TG_LO_STAGES : 1;
+  uint8_t* pbase = base + (size_t)stages * sa_bytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(pbase + (size_t)(RING2 ? SP : 0) * sp_bytes);
   uint64_t* empty = full + stages;
-  uint64_t* tfull = empty + stages;
-  uint64_t* tmfull = tfull + stages;  // [2] accumulator ready (MMA commit)
+  uint64_t* tfull = empty + stages;   // prep done: per TMA stage, or per low-ring stage (RING2)
+  uint64_t* lempty = tfull + stages;  // RING2: low-ring stage free (MMA commit)
+  uint64_t* tmfull = lempty + SP;     // [2] accumulator ready (MMA commit)
   uint64_t* tmempty = tmfull + 2;     // [2] accumulator drained (4 drain warps)
   uint64_t* fin = tmempty + 2;        // every MMA of this CTA complete
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
@@ -775,9 +787,11 @@ __global__ __launch_bounds__(TG_THREADS) void tc_group_kernel(const TcGroupProb*
     s_abort = 0;
     for (int s = 0; s < stages; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], EPI_STAGE ? 5 : 1);
-      mbar_init(&tfull[s], 4);
+      // RING2: the MMA (which waits for the prep) alone releases a TMA stage
+      mbar_init(&empty[s], (EPI_STAGE && !RING2) ? 1 + TG_PREP_WARPS : 1);
+      mbar_init(&tfull[s], TG_PREP_WARPS);
     }
+    for (int s = 0; s < SP; ++s) mbar_init(&lempty[s], 1);
     for (int a = 0; a < 2; ++a) {
       mbar_init(&tmfull[a], 1);
       mbar_init(&tmempty[a], 4);
@@ -826,7 +840,7 @@ __global__ __launch_bounds__(TG_THREADS) void tc_group_kernel(const TcGroupProb*
           const uint32_t ph = (it / (uint32_t)stages) & 1u;
           if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) break;
           ++issued;
-          uint8_t* st = base + (size_t)s * L.bytes;
+          uint8_t* st = base + (size_t)s * sa_bytes;
           mbar_expect_tx(&full[s], (uint32_t)TC_A_BYTES + b_bytes);
           const int k0 = (int)(kb + (int64_t)kt * BKE);
           if (MODE == 0) {
@@ -868,23 +882,30 @@ __global__ __launch_bounds__(TG_THREADS) void tc_group_kernel(const TcGroupProb*
         for (int kt = 0; kt < kt_n; ++kt, ++it) {
           const int s = (int)(it % (uint32_t)stages);
           const uint32_t ph = (it / (uint32_t)stages) & 1u;
-          if (!mbar_wait(PREP ? &tfull[s] : &full[s], ph, abort_flag)) {
+          const int sl = (int)(it % (uint32_t)SP);
+          const uint32_t phl = (it / (uint32_t)SP) & 1u;
+          if (!mbar_wait(RING2 ? &tfull[sl] : (PREP ? &tfull[s] : &full[s]), RING2 ? phl : ph, abort_flag)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t st = smem_u32(base + (size_t)s * L.bytes);
+          const uint32_t st = smem_u32(base + (size_t)s * sa_bytes);
+          // low halves: in the stage itself, or in the low ring (RING2: A_lo at 0, B_lo after it)
+          const uint32_t alo = RING2 ? smem_u32(pbase + (size_t)sl * sp_bytes) : st + L.alo;
+          const uint32_t blo = RING2 ? alo + (uint32_t)TC_A_BYTES : st + L.blo;
+          const uint32_t bst = RING2 ? st + (uint32_t)TC_A_BYTES : st + L.b;
 #pragma unroll
           for (int ks = 0; ks < 128 / TC_KSTEP_BYTES; ++ks) {
             const uint64_t adesc = smem_desc(st + L.ak + ks * TC_KSTEP_BYTES, 16, 1024);
-            const uint64_t bdesc = smem_desc(st + L.b + ks * TC_KSTEP_BYTES, 16, 1024);
+            const uint64_t bdesc = smem_desc(bst + ks * TC_KSTEP_BYTES, 16, 1024);
             mma_tf32(d, adesc, bdesc, idesc, (kt > 0 || ks > 0) ? 1u : 0u);
             if (SPLIT) {
-              mma_tf32(d, smem_desc(st + L.alo + ks * TC_KSTEP_BYTES, 16, 1024), bdesc, idesc, 1u);
-              mma_tf32(d, adesc, smem_desc(st + L.blo + ks * TC_KSTEP_BYTES, 16, 1024), idesc, 1u);
+              mma_tf32(d, smem_desc(alo + ks * TC_KSTEP_BYTES, 16, 1024), bdesc, idesc, 1u);
+              mma_tf32(d, adesc, smem_desc(blo + ks * TC_KSTEP_BYTES, 16, 1024), idesc, 1u);
             }
           }
           mma_commit(&empty[s]);
+          if (RING2) mma_commit(&lempty[sl]);
         }
         if (!ok) break;
         mma_commit(&tmfull[acc]);
@@ -895,10 +916,11 @@ __global__ __launch_bounds__(TG_THREADS) void tc_group_kernel(const TcGroupProb*
       volatile int none = 0;
       mbar_wait(fin, 0, &none);
     }
-  } else if (warp < 6) {
-    // ---------------- operand preparation (warps 2-5) ----------------
+  } else if (warp < 2 + TG_PREP_WARPS) {
+    // ---------------- operand preparation (warps 2 .. 2 + TG_PREP_WARPS - 1) ----------------
     if (EPI_STAGE) {
-      const int et = tid - 64;  // 0..127
+      constexpr int PT = 32 * TG_PREP_WARPS;  // preparation threads
+      const int et = tid - 64;                // 0 .. PT - 1
       const int q = warp - 2;
       uint32_t it = 0;
       for (int ti = blockIdx.x; ti < ntiles && !*abort_flag; ti += gridDim.x) {
@@ -914,19 +936,31 @@ __global__ __launch_bounds__(TG_THREADS) void tc_group_kernel(const TcGroupProb*
         for (int kt = 0; kt < kt_n; ++kt, ++it) {
           const int s = (int)(it % (uint32_t)stages);
           const uint32_t ph = (it / (uint32_t)stages) & 1u;
+          const int sl = (int)(it % (uint32_t)SP);
+          const uint32_t phl = (it / (uint32_t)SP) & 1u;
           if (!mbar_wait(&full[s], ph, abort_flag)) {
             ok = false;
             break;
           }
-          uint8_t* st = base + (size_t)s * L.bytes;
+          // RING2: the low-ring stage must be free (its last MMA done) before it is rewritten
+          if (RING2 && !mbar_wait(&lempty[sl], phl ^ 1u, abort_flag)) {
+            ok = false;
+            break;
+          }
+          uint8_t* st = base + (size_t)s * sa_bytes;
+          uint8_t* lo_a = RING2 ? pbase + (size_t)sl * sp_bytes : st + L.alo;
+          uint8_t* lo_b = RING2 ? lo_a + TC_A_BYTES : st + L.blo;
+          uint8_t* b_src = RING2 ? st + TC_A_BYTES : st + L.b;
           if (TRANSPOSE) {
-            // thread c owns row c of the K-major tile (see tc_gemm_kernel)
-            const int c = et;
+            // row c of the K-major tile (see tc_gemm_kernel), its 16-byte chunks shared by the
+            // PT / 128 threads with the same c
+            const int c = et & 127, part = et >> 7;
+            constexpr int NCH = 8 / (PT / 128);
             const float* stg = reinterpret_cast<const float*>(st + L.a + (c >> 5) * (TC_BK * 128)) + (c & 31);
             uint8_t* row = st + L.ak + c * 128;
             uint8_t* rlo = st + L.alo + c * 128;
 #pragma unroll
-            for (int ch = 0; ch < 8; ++ch) {
+            for (int ch = part * NCH; ch < (part + 1) * NCH; ++ch) {
               float4 v = make_float4(stg[(4 * ch + 0) * 32], stg[(4 * ch + 1) * 32], stg[(4 * ch + 2) * 32],
                                      stg[(4 * ch + 3) * 32]);
               const int off = (ch ^ (c & 7)) << 4;
@@ -937,8 +971,8 @@ __global__ __launch_bounds__(TG_THREADS) void tc_group_kernel(const TcGroupProb*
             }
           } else {
             const float4* a4 = reinterpret_cast<const float4*>(st + L.a);
-            float4* lo4 = reinterpret_cast<float4*>(st + L.alo);
-            for (int i = et; i < TC_A_BYTES / 16; i += 128) {
+            float4* lo4 = reinterpret_cast<float4*>(lo_a);
+            for (int i = et; i < TC_A_BYTES / 16; i += PT) {
               float4 v = a4[i];
               if (NORM) {
                 sq.add(v.x);
@@ -950,9 +984,9 @@ __global__ __launch_bounds__(TG_THREADS) void tc_group_kernel(const TcGroupProb*
             }
           }
           if (SPLIT) {
-            const float4* b4 = reinterpret_cast<const float4*>(st + L.b);
-            float4* blo4 = reinterpret_cast<float4*>(st + L.blo);
-            for (int i = et; i < (int)(b_bytes / 16); i += 128) {
+            const float4* b4 = reinterpret_cast<const float4*>(b_src);
+            float4* blo4 = reinterpret_cast<float4*>(lo_b);
+            for (int i = et; i < (int)(b_bytes / 16); i += PT) {
               float4 v = b4[i];
               blo4[i] = make_float4(tf32_lo(v.x), tf32_lo(v.y), tf32_lo(v.z), tf32_lo(v.w));
             }
@@ -960,8 +994,8 @@ __global__ __launch_bounds__(TG_THREADS) void tc_group_kernel(const TcGroupProb*
           if (PREP) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           __syncwarp();
           if (lane == 0) {
-            if (PREP) mbar_arrive(&tfull[s]);
-            mbar_arrive(&empty[s]);
+            if (PREP) mbar_arrive(&tfull[RING2 ? sl : s]);
+            if (!RING2) mbar_arrive(&empty[s]);
           }
         }
         if (!ok) break;
@@ -969,12 +1003,12 @@ __global__ __launch_bounds__(TG_THREADS) void tc_group_kernel(const TcGroupProb*
           // one partial per (row tile, prep warp): summed in order by the residual step
           double v = (double)sq.hi + (double)sq.lo;
           for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-          if (lane == 0 && P.gnorm_part) P.gnorm_part[4 * tr.y + q] = v;
+          if (lane == 0 && P.gnorm_part) P.gnorm_part[TG_PREP_WARPS * tr.y + q] = v;
         }
       }
     }
   } else {
-    // ---------------- accumulator drain (warps 6-9) ----------------
+    // ---------------- accumulator drain (the last four warps) ----------------
     const int q = warp & 3;  // TMEM sub-partition: lanes 32q .. 32q + 31
     int j = 0;
     for (int ti = blockIdx.x; ti < ntiles && !*abort_flag; ti += gridDim.x, ++j) {
@@ -1030,10 +1064,16 @@ __global__ __launch_bounds__(TG_THREADS) void tc_group_kernel(const TcGroupProb*
 }
 
 size_t group_smem_bytes(int mode, bool split, int nmma_max, int stages) {
-  return 1024 + (size_t)stages * StageLayout(mode, split, nmma_max, 4).bytes + (3 * (size_t)stages + 5) * 8 + 16;
+  if (mode == 0 && split) {  // two rings: {A, B} x stages and {A_lo, B_lo} x TG_LO_STAGES
+    const size_t nb = ((size_t)nmma_max * 128 + 1023) & ~size_t(1023);
+    return 1024 + (size_t)(stages + TG_LO_STAGES) * (TC_A_BYTES + nb) + (3 * (size_t)stages + TG_LO_STAGES + 5) * 8 + 16;
+  }
+  return 1024 + (size_t)stages * StageLayout(mode, split, nmma_max, 4).bytes + (3 * (size_t)stages + 6) * 8 + 16;
 }
 
 }  // namespace
+
+int tc_group_norm_parts() { return TG_PREP_WARPS; }
 
 int64_t tc_group_tiles(int mode, const TcGroupSpec* specs, int nprob) {
   int64_t t = 0;
@@ -1103,8 +1143,12 @@ bool tc_group_build(int mode, const TcGroupSpec* specs, int nprob, void* host, i
 
 int tc_group_max_stages(int mode, int prec, int nmma_max, int per_sm) {
   const bool split = prec == 3;
-  const int stage = (int)StageLayout(mode, split, nmma_max, 4).bytes;
   const int budget = (per_sm >= 2 ? 110 : 214) * 1024 - 2048;
+  if (mode == 0 && split) {
+    const int stage = TC_A_BYTES + (int)(((size_t)nmma_max * 128 + 1023) & ~size_t(1023));
+    return std::min((budget - TG_LO_STAGES * stage) / stage, 12);
+  }
+  const int stage = (int)StageLayout(mode, split, nmma_max, 4).bytes;
   return std::min(budget / stage, 8);
 }
 

@@ -44,8 +44,8 @@ int tc_gtq_splits_bf16(int64_t M, int64_t n, bool split);
 // ---- grouped persistent products (many independent problems, one launch) ----
 // One problem: G (M x n, row-major FP32, ld ldg, TMA-aligned) times a K-major B operand
 // Bt with ld ldb: mode 0 (GX) Y = G X with Bt = X^T (round_up(l,16) x n, padding rows
-// zero), out = Y (M x l, ld ldo), gnorm_part (or nullptr) receives 4 partial sums of
-// G^2 per 128-row tile; mode 1 (GTQ) split-K partials of G^T Q with Bt = Q^T
+// zero), out = Y (M x l, ld ldo), gnorm_part (or nullptr) receives tc_group_norm_parts()
+// partial sums of G^2 per 128-row tile; mode 1 (GTQ) split-K partials of G^T Q with Bt = Q^T
 // (round_up(l,16) x M), `splits` row ranges of rps rows (a multiple of 32), partial z
 // at out + z * split_stride (n x l, ld ldo).
 // transpose_out (mode 0): Y stored column-major, out[c * ldo + row].
@@ -62,6 +62,7 @@ struct TcGroupSpec {
   double* gnorm_part;
   int transpose_out;
 };
+int tc_group_norm_parts();
 // Tiles of a grouped launch (128-row tiles in mode 0; column tiles x splits in mode 1).
 int64_t tc_group_tiles(int mode, const TcGroupSpec* specs, int nprob);
 // Bytes of the device table: the problems, then the tile list.
