@@ -744,12 +744,17 @@ cudaError_t launch_metrics(const double* alpha, const double* beta, int r, int N
   return launched();
 }
 
+// One warp: lane-strided partial sums, then a fixed shuffle tree (deterministic).
 __global__ void residual_kernel(const double* gpart, int ng, const double* bpart, int nb, double* out) {
-  if (threadIdx.x != 0) return;
+  const int lane = threadIdx.x;
   double g = 0.0, b = 0.0;
-  for (int i = 0; i < ng; ++i) g += gpart[i];
-  for (int i = 0; i < nb; ++i) b += bpart[i];
-  *out = g > 0.0 ? sqrt(fmax(g - b, 0.0) / g) : 0.0;
+  for (int i = lane; i < ng; i += 32) g += gpart[i];
+  for (int i = lane; i < nb; i += 32) b += bpart[i];
+  for (int o = 16; o > 0; o >>= 1) {
+    g += __shfl_xor_sync(0xffffffffu, g, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if (lane == 0) *out = g > 0.0 ? sqrt(fmax(g - b, 0.0) / g) : 0.0;
 }
 
 cudaError_t launch_residual(const double* gpart, int ng, const double* bpart, int nb, double* out,

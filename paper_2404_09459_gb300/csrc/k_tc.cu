@@ -120,6 +120,30 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+// The same with A read from tensor memory (M rows in lanes, one 32-bit column per K element).
+__device__ __forceinline__ void mma_tf32_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// Sixteen consecutive 32-bit columns of this thread's lane (warp-wide, its own 32-lane quarter).
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+      "r"(__float_as_uint(v[15]))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 // Arrive on `bar` once all previously issued MMAs of this thread have completed.
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -740,16 +764,49 @@ cudaError_t tc_gemm_gtq_bf16(const void* G, int64_t ldg, int64_t M, int64_t n, c
 // b, b + grid, b + 2 grid, ... of the list (sorted longest first), so the
 // roles below walk the same sequence and their pipeline counters agree.
 //
-// Warp roles (10 warps): 0 TMA, 1 MMA (one thread), 2-5 operand preparation
-// (3xTF32 low halves, the G^T transpose, the sum of G^2), 6-9 accumulator
-// drain.  The accumulator is double-buffered in tensor memory, so the drain
-// of one tile overlaps the MMAs of the next.
+// Warp roles (14 warps): 0 TMA, 1 MMA (one thread), 2-9 operand preparation,
+// 10-13 accumulator drain.  The accumulator is double-buffered in tensor
+// memory, so the drain of one tile overlaps the MMAs of the next.
+//
+// 3xTF32 (SPLIT): the A operand (the G tile, or its transpose for G^T Q) goes
+// to the MMA from tensor memory: the preparation warps read it from the staged
+// tile and write A and A - tf32(A) into a tensor-memory ring (one 64-column
+// stage per pipeline stage, after the two accumulators), so shared memory holds
+// only the staged tile, B and B - tf32(B).  Shared-memory traffic per stage is
+// then about 2/3 of what A and its low half in shared memory would need, and the
+// G^T Q stage no longer holds the transposed copies.
 // ---------------------------------------------------------------------------
 namespace {
 
 constexpr int TG_PREP_WARPS = 8;                   // operand preparation warps
 constexpr int TG_THREADS = 32 * (6 + TG_PREP_WARPS);  // + TMA, MMA and four drain warps
-constexpr int TG_LO_STAGES = 2;  // depth of the low-half ring of the 3xTF32 Y = G X product
+constexpr int TG_TA_COL0 = 256;                    // first tensor-memory column of the A ring
+constexpr int TG_TA_STAGES = 4;                    // A-ring stages (64 columns each: A, then A_lo)
+
+// Shared-memory stage of the grouped kernel: with SPLIT, the staged A tile (16 KB), B and
+// B_lo (each nmma x 128 bytes, 1024-aligned); otherwise the StageLayout of tc_gemm_kernel.
+struct GroupLayout {
+  uint32_t a, b, blo, ak, alo, bytes;
+  __host__ __device__ GroupLayout(int mode, bool split, int nmma) {
+    if (split) {
+      const uint32_t nb = ((uint32_t)nmma * 128u + 1023u) & ~1023u;
+      a = 0;
+      ak = 0;
+      alo = 0;
+      b = TC_A_BYTES;
+      blo = b + nb;
+      bytes = blo + nb;
+    } else {
+      const StageLayout L(mode, false, nmma, 4);
+      a = L.a;
+      b = L.b;
+      ak = L.ak;
+      alo = L.alo;
+      blo = L.blo;
+      bytes = L.bytes;
+    }
+  }
+};
 
 template <int MODE, bool NORM, bool SPLIT>
 __global__ __launch_bounds__(TG_THREADS) void tc_group_kernel(const TcGroupProb* __restrict__ probs,
@@ -757,24 +814,14 @@ __global__ __launch_bounds__(TG_THREADS) void tc_group_kernel(const TcGroupProb*
                                                               int nmma_max, int acc_stride, int tmem_cols,
                                                               int stages, DevStatus* st_glob) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  constexpr int EB = 4, BKE = 32;
+  constexpr int BKE = 32;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  // RING2 (Y = G X with 3xTF32): the TMA ring holds {A, B} only (`stages` deep) and a
-  // second, shallow ring (TG_LO_STAGES) holds the low halves {A_lo, B_lo} that the prep
-  // warps write; the MMA reads both.  More of G is in flight for the same shared memory.
-  constexpr bool RING2 = MODE == 0 && SPLIT;
-  const StageLayout L(MODE, SPLIT, nmma_max, EB);
-  const uint32_t nb = ((uint32_t)nmma_max * 128u + 1023u) & ~1023u;
-  const uint32_t sa_bytes = RING2 ? (uint32_t)TC_A_BYTES + nb : L.bytes;  // one stage of the TMA ring
-  const uint32_t sp_bytes = RING2 ? (uint32_t)TC_A_BYTES + nb : 0u;      // one stage of the low ring
-  constexpr int SP = RING2 ? TG_LO_STAGES : 1;
-  uint8_t* pbase = base + (size_t)stages * sa_bytes;
-  uint64_t* full = reinterpret_cast<uint64_t*>(pbase + (size_t)(RING2 ? SP : 0) * sp_bytes);
+  const GroupLayout L(MODE, SPLIT, nmma_max);
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + (size_t)stages * L.bytes);
   uint64_t* empty = full + stages;
-  uint64_t* tfull = empty + stages;   // prep done: per TMA stage, or per low-ring stage (RING2)
-  uint64_t* lempty = tfull + stages;  // RING2: low-ring stage free (MMA commit)
-  uint64_t* tmfull = lempty + SP;     // [2] accumulator ready (MMA commit)
+  uint64_t* tfull = empty + stages;   // operands prepared (preparation warps)
+  uint64_t* tmfull = tfull + stages;  // [2] accumulator ready (MMA commit)
   uint64_t* tmempty = tmfull + 2;     // [2] accumulator drained (4 drain warps)
   uint64_t* fin = tmempty + 2;        // every MMA of this CTA complete
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
@@ -787,11 +834,10 @@ __global__ __launch_bounds__(TG_THREADS) void tc_group_kernel(const TcGroupProb*
     s_abort = 0;
     for (int s = 0; s < stages; ++s) {
       mbar_init(&full[s], 1);
-      // RING2: the MMA (which waits for the prep) alone releases a TMA stage
-      mbar_init(&empty[s], (EPI_STAGE && !RING2) ? 1 + TG_PREP_WARPS : 1);
+      // with PREP the MMA waits for the preparation, so its commit alone releases a stage
+      mbar_init(&empty[s], (EPI_STAGE && !PREP) ? 1 + TG_PREP_WARPS : 1);
       mbar_init(&tfull[s], TG_PREP_WARPS);
     }
-    for (int s = 0; s < SP; ++s) mbar_init(&lempty[s], 1);
     for (int a = 0; a < 2; ++a) {
       mbar_init(&tmfull[a], 1);
       mbar_init(&tmempty[a], 4);
@@ -840,7 +886,7 @@ __global__ __launch_bounds__(TG_THREADS) void tc_group_kernel(const TcGroupProb*
           const uint32_t ph = (it / (uint32_t)stages) & 1u;
           if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) break;
           ++issued;
-          uint8_t* st = base + (size_t)s * sa_bytes;
+          uint8_t* st = base + (size_t)s * L.bytes;
           mbar_expect_tx(&full[s], (uint32_t)TC_A_BYTES + b_bytes);
           const int k0 = (int)(kb + (int64_t)kt * BKE);
           if (MODE == 0) {
@@ -882,30 +928,27 @@ __global__ __launch_bounds__(TG_THREADS) void tc_group_kernel(const TcGroupProb*
         for (int kt = 0; kt < kt_n; ++kt, ++it) {
           const int s = (int)(it % (uint32_t)stages);
           const uint32_t ph = (it / (uint32_t)stages) & 1u;
-          const int sl = (int)(it % (uint32_t)SP);
-          const uint32_t phl = (it / (uint32_t)SP) & 1u;
-          if (!mbar_wait(RING2 ? &tfull[sl] : (PREP ? &tfull[s] : &full[s]), RING2 ? phl : ph, abort_flag)) {
+          if (!mbar_wait(PREP ? &tfull[s] : &full[s], ph, abort_flag)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t st = smem_u32(base + (size_t)s * sa_bytes);
-          // low halves: in the stage itself, or in the low ring (RING2: A_lo at 0, B_lo after it)
-          const uint32_t alo = RING2 ? smem_u32(pbase + (size_t)sl * sp_bytes) : st + L.alo;
-          const uint32_t blo = RING2 ? alo + (uint32_t)TC_A_BYTES : st + L.blo;
-          const uint32_t bst = RING2 ? st + (uint32_t)TC_A_BYTES : st + L.b;
+          const uint32_t st = smem_u32(base + (size_t)s * L.bytes);
+          const uint32_t ta = tmem + (uint32_t)(TG_TA_COL0 + 64 * s);  // A (3xTF32): columns 0-31 A, 32-63 A_lo
 #pragma unroll
           for (int ks = 0; ks < 128 / TC_KSTEP_BYTES; ++ks) {
-            const uint64_t adesc = smem_desc(st + L.ak + ks * TC_KSTEP_BYTES, 16, 1024);
-            const uint64_t bdesc = smem_desc(bst + ks * TC_KSTEP_BYTES, 16, 1024);
-            mma_tf32(d, adesc, bdesc, idesc, (kt > 0 || ks > 0) ? 1u : 0u);
+            const uint64_t bdesc = smem_desc(st + L.b + ks * TC_KSTEP_BYTES, 16, 1024);
             if (SPLIT) {
-              mma_tf32(d, smem_desc(alo + ks * TC_KSTEP_BYTES, 16, 1024), bdesc, idesc, 1u);
-              mma_tf32(d, adesc, smem_desc(blo + ks * TC_KSTEP_BYTES, 16, 1024), idesc, 1u);
+              const uint32_t ahi = ta + (uint32_t)(8 * ks), alo = ahi + 32u;
+              mma_tf32_ta(d, ahi, bdesc, idesc, (kt > 0 || ks > 0) ? 1u : 0u);
+              mma_tf32_ta(d, alo, bdesc, idesc, 1u);
+              mma_tf32_ta(d, ahi, smem_desc(st + L.blo + ks * TC_KSTEP_BYTES, 16, 1024), idesc, 1u);
+            } else {
+              const uint64_t adesc = smem_desc(st + L.ak + ks * TC_KSTEP_BYTES, 16, 1024);
+              mma_tf32(d, adesc, bdesc, idesc, (kt > 0 || ks > 0) ? 1u : 0u);
             }
           }
           mma_commit(&empty[s]);
-          if (RING2) mma_commit(&lempty[sl]);
         }
         if (!ok) break;
         mma_commit(&tmfull[acc]);
@@ -917,11 +960,14 @@ __global__ __launch_bounds__(TG_THREADS) void tc_group_kernel(const TcGroupProb*
       mbar_wait(fin, 0, &none);
     }
   } else if (warp < 2 + TG_PREP_WARPS) {
-    // ---------------- operand preparation (warps 2 .. 2 + TG_PREP_WARPS - 1) ----------------
+    // ---------------- operand preparation (warps 2 .. 9) ----------------
     if (EPI_STAGE) {
       constexpr int PT = 32 * TG_PREP_WARPS;  // preparation threads
       const int et = tid - 64;                // 0 .. PT - 1
-      const int q = warp - 2;
+      const int q = warp - 2;                 // partial index of the fused norm
+      const int sub = warp & 3;               // tensor-memory lane quarter of this warp
+      const int half = (warp - 2) >> 2;       // which 16 of the stage's 32 K columns (SPLIT)
+      const int arow = 32 * sub + lane;       // the A row (tensor-memory lane) this thread writes
       uint32_t it = 0;
       for (int ti = blockIdx.x; ti < ntiles && !*abort_flag; ti += gridDim.x) {
         const int2 tr = tiles[ti];
@@ -936,74 +982,87 @@ __global__ __launch_bounds__(TG_THREADS) void tc_group_kernel(const TcGroupProb*
         for (int kt = 0; kt < kt_n; ++kt, ++it) {
           const int s = (int)(it % (uint32_t)stages);
           const uint32_t ph = (it / (uint32_t)stages) & 1u;
-          const int sl = (int)(it % (uint32_t)SP);
-          const uint32_t phl = (it / (uint32_t)SP) & 1u;
           if (!mbar_wait(&full[s], ph, abort_flag)) {
             ok = false;
             break;
           }
-          // RING2: the low-ring stage must be free (its last MMA done) before it is rewritten
-          if (RING2 && !mbar_wait(&lempty[sl], phl ^ 1u, abort_flag)) {
-            ok = false;
-            break;
-          }
-          uint8_t* st = base + (size_t)s * sa_bytes;
-          uint8_t* lo_a = RING2 ? pbase + (size_t)sl * sp_bytes : st + L.alo;
-          uint8_t* lo_b = RING2 ? lo_a + TC_A_BYTES : st + L.blo;
-          uint8_t* b_src = RING2 ? st + TC_A_BYTES : st + L.b;
-          if (TRANSPOSE) {
+          uint8_t* st = base + (size_t)s * L.bytes;
+          if (SPLIT) {
+            // the A-ring stage was last read by the MMAs whose commit released this stage
+            tc_fence_after();
+            // this thread's row of A, K columns 16 half .. 16 half + 15, into the A ring
+            float v[16], lo[16];
+            if (MODE == 0) {
+              // staged K-major with the 128-byte swizzle: 16-byte chunk c of row r at c ^ (r & 7)
+              const uint8_t* row = st + L.a + arow * 128;
+#pragma unroll
+              for (int c = 0; c < 4; ++c) {
+                const float4 x = *reinterpret_cast<const float4*>(row + (((4 * half + c) ^ (arow & 7)) << 4));
+                v[4 * c + 0] = x.x;
+                v[4 * c + 1] = x.y;
+                v[4 * c + 2] = x.z;
+                v[4 * c + 3] = x.w;
+              }
+            } else {
+              // staged G[k][c] (unswizzled 32 x 32 boxes): A row c = column c of G
+              const float* stg = reinterpret_cast<const float*>(st + L.a + (arow >> 5) * (TC_BK * 128)) + (arow & 31);
+#pragma unroll
+              for (int k = 0; k < 16; ++k) v[k] = stg[(16 * half + k) * 32];
+            }
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+              if (NORM) sq.add(v[k]);
+              lo[k] = tf32_lo(v[k]);
+            }
+            const uint32_t ta = tmem + ((uint32_t)(32 * sub) << 16) + (uint32_t)(TG_TA_COL0 + 64 * s + 16 * half);
+            tmem_st16(ta, v);
+            tmem_st16(ta + 32u, lo);
+            // B_lo in shared memory
+            const float4* b4 = reinterpret_cast<const float4*>(st + L.b);
+            float4* blo4 = reinterpret_cast<float4*>(st + L.blo);
+            for (int i = et; i < (int)(b_bytes / 16); i += PT) {
+              float4 x = b4[i];
+              blo4[i] = make_float4(tf32_lo(x.x), tf32_lo(x.y), tf32_lo(x.z), tf32_lo(x.w));
+            }
+            tmem_wait_st();
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tc_fence_before();
+          } else if (TRANSPOSE) {
             // row c of the K-major tile (see tc_gemm_kernel), its 16-byte chunks shared by the
             // PT / 128 threads with the same c
             const int c = et & 127, part = et >> 7;
             constexpr int NCH = 8 / (PT / 128);
             const float* stg = reinterpret_cast<const float*>(st + L.a + (c >> 5) * (TC_BK * 128)) + (c & 31);
             uint8_t* row = st + L.ak + c * 128;
-            uint8_t* rlo = st + L.alo + c * 128;
 #pragma unroll
             for (int ch = part * NCH; ch < (part + 1) * NCH; ++ch) {
-              float4 v = make_float4(stg[(4 * ch + 0) * 32], stg[(4 * ch + 1) * 32], stg[(4 * ch + 2) * 32],
+              float4 x = make_float4(stg[(4 * ch + 0) * 32], stg[(4 * ch + 1) * 32], stg[(4 * ch + 2) * 32],
                                      stg[(4 * ch + 3) * 32]);
-              const int off = (ch ^ (c & 7)) << 4;
-              *reinterpret_cast<float4*>(row + off) = v;
-              if (SPLIT)
-                *reinterpret_cast<float4*>(rlo + off) =
-                    make_float4(tf32_lo(v.x), tf32_lo(v.y), tf32_lo(v.z), tf32_lo(v.w));
+              *reinterpret_cast<float4*>(row + ((ch ^ (c & 7)) << 4)) = x;
             }
-          } else {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          } else if (NORM) {
             const float4* a4 = reinterpret_cast<const float4*>(st + L.a);
-            float4* lo4 = reinterpret_cast<float4*>(lo_a);
             for (int i = et; i < TC_A_BYTES / 16; i += PT) {
-              float4 v = a4[i];
-              if (NORM) {
-                sq.add(v.x);
-                sq.add(v.y);
-                sq.add(v.z);
-                sq.add(v.w);
-              }
-              if (SPLIT) lo4[i] = make_float4(tf32_lo(v.x), tf32_lo(v.y), tf32_lo(v.z), tf32_lo(v.w));
+              float4 x = a4[i];
+              sq.add(x.x);
+              sq.add(x.y);
+              sq.add(x.z);
+              sq.add(x.w);
             }
           }
-          if (SPLIT) {
-            const float4* b4 = reinterpret_cast<const float4*>(b_src);
-            float4* blo4 = reinterpret_cast<float4*>(lo_b);
-            for (int i = et; i < (int)(b_bytes / 16); i += PT) {
-              float4 v = b4[i];
-              blo4[i] = make_float4(tf32_lo(v.x), tf32_lo(v.y), tf32_lo(v.z), tf32_lo(v.w));
-            }
-          }
-          if (PREP) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           __syncwarp();
           if (lane == 0) {
-            if (PREP) mbar_arrive(&tfull[RING2 ? sl : s]);
-            if (!RING2) mbar_arrive(&empty[s]);
+            if (PREP) mbar_arrive(&tfull[s]);
+            else mbar_arrive(&empty[s]);
           }
         }
         if (!ok) break;
         if (NORM && MODE == 0) {
           // one partial per (row tile, prep warp): summed in order by the residual step
-          double v = (double)sq.hi + (double)sq.lo;
-          for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-          if (lane == 0 && P.gnorm_part) P.gnorm_part[TG_PREP_WARPS * tr.y + q] = v;
+          double x = (double)sq.hi + (double)sq.lo;
+          for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+          if (lane == 0 && P.gnorm_part) P.gnorm_part[TG_PREP_WARPS * tr.y + q] = x;
         }
       }
     }
@@ -1064,11 +1123,7 @@ __global__ __launch_bounds__(TG_THREADS) void tc_group_kernel(const TcGroupProb*
 }
 
 size_t group_smem_bytes(int mode, bool split, int nmma_max, int stages) {
-  if (mode == 0 && split) {  // two rings: {A, B} x stages and {A_lo, B_lo} x TG_LO_STAGES
-    const size_t nb = ((size_t)nmma_max * 128 + 1023) & ~size_t(1023);
-    return 1024 + (size_t)(stages + TG_LO_STAGES) * (TC_A_BYTES + nb) + (3 * (size_t)stages + TG_LO_STAGES + 5) * 8 + 16;
-  }
-  return 1024 + (size_t)stages * StageLayout(mode, split, nmma_max, 4).bytes + (3 * (size_t)stages + 6) * 8 + 16;
+  return 1024 + (size_t)stages * GroupLayout(mode, split, nmma_max).bytes + (3 * (size_t)stages + 5) * 8 + 16;
 }
 
 }  // namespace
@@ -1143,13 +1198,11 @@ bool tc_group_build(int mode, const TcGroupSpec* specs, int nprob, void* host, i
 
 int tc_group_max_stages(int mode, int prec, int nmma_max, int per_sm) {
   const bool split = prec == 3;
+  // 3xTF32 keeps A in tensor memory: all 512 columns (two accumulators, the A ring), one CTA per SM
+  if (split && per_sm >= 2) return 0;
   const int budget = (per_sm >= 2 ? 110 : 214) * 1024 - 2048;
-  if (mode == 0 && split) {
-    const int stage = TC_A_BYTES + (int)(((size_t)nmma_max * 128 + 1023) & ~size_t(1023));
-    return std::min((budget - TG_LO_STAGES * stage) / stage, 12);
-  }
-  const int stage = (int)StageLayout(mode, split, nmma_max, 4).bytes;
-  return std::min(budget / stage, 8);
+  const int stage = (int)GroupLayout(mode, split, nmma_max).bytes;
+  return std::min(budget / stage, split ? TG_TA_STAGES : 8);
 }
 
 cudaError_t tc_group_launch(int mode, int prec, bool norm, const void* dev_table, int nprob, int64_t ntiles,
@@ -1157,8 +1210,9 @@ cudaError_t tc_group_launch(int mode, int prec, bool norm, const void* dev_table
   if (ntiles <= 0) return cudaSuccess;
   const bool split = prec == 3;
   const int acc_stride = (int)round_up(nmma_max, 32);
-  const int tmem_cols = tmem_cols_for(2 * acc_stride);
-  if (2 * acc_stride > 512 || (per_sm >= 2 && tmem_cols > 256)) return cudaErrorInvalidValue;
+  // 3xTF32: the two accumulators in columns [0, 256), the A ring in [256, 512)
+  const int tmem_cols = split ? 512 : tmem_cols_for(2 * acc_stride);
+  if (2 * acc_stride > (split ? TG_TA_COL0 : 512) || (per_sm >= 2 && tmem_cols > 256)) return cudaErrorInvalidValue;
   if (stages < 2 || stages > tc_group_max_stages(mode, prec, nmma_max, per_sm)) return cudaErrorInvalidValue;
   const TcGroupProb* probs = static_cast<const TcGroupProb*>(dev_table);
   const int2* tiles = reinterpret_cast<const int2*>(static_cast<const unsigned char*>(dev_table) +
