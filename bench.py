@@ -81,7 +81,7 @@ def sketch_traffic(prec, workload):
         return None
     if hashlib.sha256(src).hexdigest() != rec["source_sha256"]:
         return None
-    return rec["traffic_per_launch_both_sides_avg"]
+    return rec.get("traffic_per_launch", rec.get("traffic_per_launch_both_sides_avg"))
 
 
 def sketch_flops(spec):
@@ -546,9 +546,14 @@ def main():
     pk = peaks()
     sk_ms, sk_calls = prof["sketch"]
     el = 8 if prec == "fp64" else (2 if prec == "bf16" else 4)
-    # algorithmic bytes per launch averaged over both sides: G (el bytes) + X (el) + Y (FP32 / FP64)
+    # algorithmic bytes of the Y = G X products of one solve ((1 + q) passes over both sides: G (el
+    # bytes) + X (el) + Y (FP32 / FP64)), over their device time; a launch covers one side, or both
+    # sides when the library groups them
     ey = 8 if prec == "fp64" else 4
-    bytes_per_launch = sum(M * spec.n * el + spec.l * spec.n * el + M * spec.l * ey for M in (spec.m, spec.p)) / 2
+    bytes_per_step = (1 + spec.q) * sum(M * spec.n * el + spec.l * spec.n * el + M * spec.l * ey
+                                        for M in (spec.m, spec.p))
+    calls_step = sk_calls / args.steps if sk_calls else 0
+    bytes_per_launch = bytes_per_step / calls_step if calls_step else None
     launch_s = sk_ms / sk_calls / 1e3 if sk_calls else None
     achieved = bytes_per_launch / launch_s / 1e9 if sk_calls else None
     roof = {"kernel": "sketch product Y = G X", "bound": "hbm", "achieved": achieved,
@@ -558,7 +563,7 @@ def main():
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if not pk.get("fallback") else "fallback"}
     if prec in ("bf16", "tf32", "tf32x3") and sk_calls:
         # the same launches against the tensor peak: BF16 measured; TF32 at half of it (nominal ratio)
-        flops_per_launch = sum(2.0 * M * spec.n * spec.l for M in (spec.m, spec.p)) / 2
+        flops_per_launch = (1 + spec.q) * sum(2.0 * M * spec.n * spec.l for M in (spec.m, spec.p)) / calls_step
         tpk = pk.get("bf16_tflops", 1900.0) * (1.0 if prec == "bf16" else 0.5)
         roof["tensor"] = {"achieved_tflops": flops_per_launch / launch_s / 1e12, "peak_tflops": tpk,
                           "frac": flops_per_launch / launch_s / 1e12 / tpk,

@@ -45,6 +45,8 @@ struct gsvd_rand_ctx {
   bool owns_stream = false;      // stream created by the library (batched workers)
   std::vector<gsvd_rand_ctx*> workers;  // sub-contexts of gsvd_rand_solve_batched
   struct GroupState* grp = nullptr;     // gsvd_rand_solve_grouped: plan, tables and captured graph
+  unsigned char* tab_host = nullptr;    // pinned staging of the two-side product tables of a solve
+  size_t tab_host_bytes = 0;
   // learned proposal: network (params | norm), then features, logits and scratch of one pair
   float* mlp_dev = nullptr;
   bool mlp_ready = false;
@@ -216,6 +218,88 @@ struct Solver {
   void* bar;  // grid barriers of the fused CholeskyQR2, one per side (zeroed at solve start)
   bool bf16;         // G is BF16: products on kind::f16 tensor cores
   bool split_power;  // BF16: power-step operands as hi + lo (two products)
+  // both sides' products as one grouped launch (TF32 / 3xTF32, l <= 128): device table slots
+  // (one per launch of the solve) and their pinned host staging
+  unsigned char* tab_dev = nullptr;
+  size_t tab_bytes = 0;  // bytes of one slot
+  int tab_slots = 0, tab_next = 0;
+
+  bool grouped_products() const { return tab_dev != nullptr; }
+
+  // One grouped launch over the two sides: the table goes through its own pinned and device
+  // slot (the solve synchronises before the slots are reused).
+  int group2(int mode, bool norm, TcGroupSpec* sp) {
+    if (tab_next >= tab_slots) return fail(h, GSVD_RAND_ERR_CUDA, "grouped product table slots exhausted");
+    const int slot = tab_next++;
+    unsigned char* hs = h->tab_host + (size_t)slot * tab_bytes;
+    unsigned char* ds = tab_dev + (size_t)slot * tab_bytes;
+    const int64_t ntiles = tc_group_tiles(mode, sp, 2);
+    if (tc_group_table_bytes(2, ntiles) > tab_bytes) return fail(h, GSVD_RAND_ERR_CUDA, "grouped product table too large");
+    int nmma = 0;
+    if (!tc_group_build(mode, sp, 2, hs, &nmma)) return fail(h, GSVD_RAND_ERR_ARG, "tensor map of a product rejected");
+    CU(cudaMemcpyAsync(ds, hs, tc_group_table_bytes(2, ntiles), cudaMemcpyHostToDevice, st));
+    const int per_sm = prec == GSVD_RAND_TF32X3 ? 1 : (2 * round_up(nmma, 32) <= 256 ? 2 : 1);
+    const int stages = tc_group_max_stages(mode, prec, nmma, per_sm);
+    CU(tc_group_launch(mode, prec, norm, ds, 2, ntiles, nmma, stages, per_sm, st_dev, st));
+    return GSVD_RAND_OK;
+  }
+
+  // Y = G X for both sides in one launch
+  int gx2(const void* const* G, const int64_t* ldg, const Plan& pl, SideBufs<T>* b, bool norm) {
+    ProfScope ps(h, GSVD_RAND_STAGE_SKETCH);
+    TcGroupSpec sp[2];
+    for (int s = 0; s < 2; ++s) {
+      memset(&sp[s], 0, sizeof(TcGroupSpec));
+      sp[s].G = static_cast<const float*>(G[s]);
+      sp[s].ldg = ldg[s];
+      sp[s].M = pl.M[s];
+      sp[s].n = pl.n;
+      sp[s].Bt = reinterpret_cast<const float*>(b[s].Xt);
+      sp[s].ldb = pl.ldx;
+      sp[s].l = pl.l;
+      sp[s].out = reinterpret_cast<float*>(b[s].Y);
+      sp[s].ldo = pl.lp;
+      sp[s].gnorm_part = norm ? b[s].gnorm : nullptr;
+    }
+    return group2(0, norm, sp);
+  }
+
+  // G^T Q for both sides in one launch (split-K partials), then each side's split reduction
+  int gtq2(const void* const* G, const int64_t* ldg, const Plan& pl, SideBufs<T>* b, T* const* out,
+           const int64_t* ldo, int transpose_out, double* const* sq) {
+    ProfScope ps(h, GSVD_RAND_STAGE_GTQ);
+    TcGroupSpec sp[2];
+    const int64_t ctiles = cdiv(pl.n, 128);
+    for (int s = 0; s < 2; ++s) {
+      const int64_t M = pl.M[s];
+      // about two tiles per SM over both sides, within the partial buffer
+      int64_t splits = std::max<int64_t>(1, 2 * 152 / (2 * ctiles));
+      splits = std::min<int64_t>(splits, std::max<int64_t>(1, pl.part_elems / (pl.n * pl.lp)));
+      splits = std::min<int64_t>(splits, cdiv(M, 32));
+      const int64_t rps = round_up(cdiv(M, splits), 32);
+      memset(&sp[s], 0, sizeof(TcGroupSpec));
+      sp[s].G = static_cast<const float*>(G[s]);
+      sp[s].ldg = ldg[s];
+      sp[s].M = M;
+      sp[s].n = pl.n;
+      sp[s].Bt = reinterpret_cast<const float*>(b[s].Q);
+      sp[s].ldb = round_up(M, 4);
+      sp[s].l = pl.l;
+      sp[s].out = reinterpret_cast<float*>(b[s].part);
+      sp[s].ldo = pl.lp;
+      sp[s].rps = rps;
+      sp[s].splits = (int)cdiv(M, rps);
+      sp[s].split_stride = pl.n * pl.lp;
+    }
+    int rc;
+    if ((rc = group2(1, false, sp))) return rc;
+    for (int s = 0; s < 2; ++s) {
+      int blocks = 0;
+      CU((launch_reduce_splits<T, T>(b[s].part, sp[s].splits, pl.n, pl.l, pl.lp, out[s], ldo[s], transpose_out,
+                                     sq ? sq[s] : nullptr, &blocks, st)));
+    }
+    return GSVD_RAND_OK;
+  }
 
   int orth(SideBufs<T>& b, const T* Yin, int64_t M, int l, int64_t lp, T* out, int64_t ldo,
            int transpose_out, int stage, int side = 0) {
@@ -397,26 +481,47 @@ struct Solver {
       st5[s] = 10 * s + 5;
     }
     int rc;
-    for (int s = 0; s < 2; ++s)
-      if ((rc = gx(G[s], ldg[s], pl.M[s], pl, b[s], b[s].gnorm))) return rc;
+    const bool g2 = grouped_products();
+    T* Zo[2] = {b[0].Z, b[1].Z};
+    const int64_t ldz[2] = {pl.lp, pl.lp};
+    T* So[2] = {S, S + (int64_t)pl.l * pl.ldn};
+    const int64_t lds[2] = {pl.ldn, pl.ldn};
+    double* sqp[2] = {b[0].bnorm, b[1].bnorm};
+    if (g2) {
+      if ((rc = gx2(G, ldg, pl, b, true))) return rc;
+    } else {
+      for (int s = 0; s < 2; ++s)
+        if ((rc = gx(G[s], ldg[s], pl.M[s], pl, b[s], b[s].gnorm))) return rc;
+    }
     if ((rc = orth2(b, Yi, pl.M, pl.l, pl.lp, Qo, ldq, qt, st1))) return rc;
     const int64_t nn[2] = {pl.n, pl.n};
     for (int it = 0; it < q; ++it) {
-      for (int s = 0; s < 2; ++s) {
-        if (bf16 && (rc = split_q(b[s], pl.M[s], pl, split_power))) return rc;
-        if ((rc = gtq(G[s], ldg[s], pl.M[s], pl, b[s], b[s].Z, pl.lp, 0, nullptr, split_power))) return rc;
+      if (g2) {
+        if ((rc = gtq2(G, ldg, pl, b, Zo, ldz, 0, nullptr))) return rc;
+      } else {
+        for (int s = 0; s < 2; ++s) {
+          if (bf16 && (rc = split_q(b[s], pl.M[s], pl, split_power))) return rc;
+          if ((rc = gtq(G[s], ldg[s], pl.M[s], pl, b[s], b[s].Z, pl.lp, 0, nullptr, split_power))) return rc;
+        }
       }
       if ((rc = orth2(b, Zi, nn, pl.l, pl.lp, Xo, ldx2, 1, st3))) return rc;
-      for (int s = 0; s < 2; ++s) {
-        if (bf16 && (rc = split_x(b[s], pl, split_power))) return rc;
-        if ((rc = gx(G[s], ldg[s], pl.M[s], pl, b[s], nullptr, split_power))) return rc;
+      if (g2) {
+        if ((rc = gx2(G, ldg, pl, b, false))) return rc;
+      } else {
+        for (int s = 0; s < 2; ++s) {
+          if (bf16 && (rc = split_x(b[s], pl, split_power))) return rc;
+          if ((rc = gx(G[s], ldg[s], pl.M[s], pl, b[s], nullptr, split_power))) return rc;
+        }
       }
       if ((rc = orth2(b, Yi, pl.M, pl.l, pl.lp, Qo, ldq, qt, st5))) return rc;
     }
-    for (int s = 0; s < 2; ++s) {
-      if (bf16 && (rc = split_q(b[s], pl.M[s], pl, true))) return rc;
-      if ((rc = gtq(G[s], ldg[s], pl.M[s], pl, b[s], S + (int64_t)s * pl.l * pl.ldn, pl.ldn, 1, b[s].bnorm, true)))
-        return rc;
+    if (g2) {
+      if ((rc = gtq2(G, ldg, pl, b, So, lds, 1, sqp))) return rc;
+    } else {
+      for (int s = 0; s < 2; ++s) {
+        if (bf16 && (rc = split_q(b[s], pl.M[s], pl, true))) return rc;
+        if ((rc = gtq(G[s], ldg[s], pl.M[s], pl, b[s], So[s], pl.ldn, 1, b[s].bnorm, true))) return rc;
+      }
     }
     return GSVD_RAND_OK;
   }
@@ -481,7 +586,8 @@ SideBufs<T> side_take(Bump& bp, const Plan& pl, int s, bool tc, bool bf16) {
   b.W = bp.take<double>((int64_t)pl.l * pl.l);
   b.R = bp.take<double>((int64_t)pl.l * pl.l);
   b.cscr = bp.take<double>(chol_scratch_elems(pl.l));
-  b.gnorm = bp.take<double>(std::max<int64_t>(gemm_gx_simt_ctas(M), tc ? tc_gx_ctas(M) : 1) + 8);
+  b.gnorm = bp.take<double>(std::max<int64_t>(std::max<int64_t>(gemm_gx_simt_ctas(M), tc ? tc_gx_ctas(M) : 1),
+                                               tc ? tc_group_norm_parts() * cdiv(M, 128) : 1) + 8);
   b.bnorm = bp.take<double>(cdiv(pl.n * pl.l, 256) + 8);
   b.Xh = b.Xl = b.Qh = b.Ql = nullptr;
   if (bf16) {
@@ -647,8 +753,23 @@ int solve_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, const voi
   Bump sb_sizer;
   small_take(sb_sizer, pl.L, k, n);
   need += sb_sizer.off + 4096;
+  // both sides' products as grouped launches: TF32 / 3xTF32 with l <= 128 (tensor memory)
+  const bool g2 = use_tc && !bf16 && pl.l <= 128;
+  const int tab_slots = 2 * (q + 1);
+  // a slot holds the larger of the two tables: G X (128-row tiles of both sides) and G^T Q
+  // (at most 152 tiles per side, see gtq2)
+  const size_t tab_bytes =
+      tc_group_table_bytes(2, std::max<int64_t>(cdiv(m, 128) + cdiv(p, 128), 2 * 152 + 2 * cdiv(n, 128))) + 256;
+  if (g2) need += (size_t)tab_slots * tab_bytes + 256;
   int rc = ensure_ws(h, need);
   if (rc) return rc;
+  if (g2 && h->tab_host_bytes < (size_t)tab_slots * tab_bytes) {
+    if (h->tab_host) cudaFreeHost(h->tab_host);
+    h->tab_host = nullptr;
+    h->tab_host_bytes = 0;
+    CU(cudaMallocHost(&h->tab_host, (size_t)tab_slots * tab_bytes));
+    h->tab_host_bytes = (size_t)tab_slots * tab_bytes;
+  }
 
   Bump bp;
   bp.base = h->ws;
@@ -679,14 +800,19 @@ int solve_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, const voi
   CU(cudaMemsetAsync(bar, 0, 2 * cholqr2_fused_bar_bytes(), st));
 
   Solver<T, TC> sv{h, st, st_dev, prec, use_tc, bar, bf16, (h->cfg.flags & GSVD_RAND_FLAG_BF16_SPLIT_POWER) != 0};
+  if (g2) {
+    sv.tab_dev = reinterpret_cast<unsigned char*>(bp.take<unsigned char>((int64_t)tab_slots * tab_bytes));
+    sv.tab_bytes = tab_bytes;
+    sv.tab_slots = tab_slots;
+  }
   {
     const void* Gs[2] = {G1, G2};
     const int64_t lds2[2] = {l1d, l2d};
     SideBufs<T> sbs[2] = {sb0, sb1};
     if ((rc = sv.sides(Gs, lds2, pl, sbs, q, seed, S))) return rc;
   }
-  int gct0 = use_tc ? tc_gx_ctas(m) : gemm_gx_simt_ctas(m);
-  int gct1 = use_tc ? tc_gx_ctas(p) : gemm_gx_simt_ctas(p);
+  int gct0 = g2 ? (int)(tc_group_norm_parts() * cdiv(m, 128)) : (use_tc ? tc_gx_ctas(m) : gemm_gx_simt_ctas(m));
+  int gct1 = g2 ? (int)(tc_group_norm_parts() * cdiv(p, 128)) : (use_tc ? tc_gx_ctas(p) : gemm_gx_simt_ctas(p));
   int bblk = (int)cdiv(n * pl.l, 256);
   CU(launch_residual(sb0.gnorm, gct0, sb0.bnorm, bblk, small.resid, st));
   CU(launch_residual(sb1.gnorm, gct1, sb1.bnorm, bblk, small.resid + 1, st));
@@ -2114,6 +2240,7 @@ int gsvd_rand_create(gsvd_rand_t* out, const gsvd_rand_config* cfg) {
       cudaMallocHost(&h->res_host, 4 * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     if (h->st_host) cudaFreeHost(h->st_host);
+  if (h->tab_host) cudaFreeHost(h->tab_host);
     delete h;
     return GSVD_RAND_ERR_OOM;
   }
