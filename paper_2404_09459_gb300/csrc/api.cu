@@ -132,6 +132,14 @@ void prof_collect(gsvd_rand_ctx* h) {
   h->evused = 0;
 }
 
+// Rows of `bytes` each from a source with row pitch spitch into a destination with pitch dpitch:
+// one plain copy when both pitches equal the row (contiguous), else a pitched copy.
+cudaError_t copy_rows(void* dst, size_t dpitch, const void* src, size_t spitch, size_t bytes, size_t rows,
+                      cudaMemcpyKind kind, cudaStream_t st) {
+  if (dpitch == bytes && spitch == bytes) return cudaMemcpyAsync(dst, src, bytes * rows, kind, st);
+  return cudaMemcpy2DAsync(dst, dpitch, src, spitch, bytes, rows, kind, st);
+}
+
 bool is_device_ptr(const void* p) {
   if (!p) return false;
   cudaPointerAttributes a;
@@ -780,14 +788,14 @@ int solve_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, const voi
   int64_t l1d = ld1, l2d = ld2;
   if (!d1) {
     unsigned char* g = bp.take<unsigned char>(m * lds * eg);
-    CU(cudaMemcpy2DAsync(g, lds * eg, G1v, ld1 * eg, n * eg, m, dev1 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+    CU(copy_rows(g, lds * eg, G1v, ld1 * eg, n * eg, m, dev1 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                          st));
     G1 = g;
     l1d = lds;
   }
   if (!d2) {
     unsigned char* g = bp.take<unsigned char>(p * lds * eg);
-    CU(cudaMemcpy2DAsync(g, lds * eg, G2v, ld2 * eg, n * eg, p, dev2 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+    CU(copy_rows(g, lds * eg, G2v, ld2 * eg, n * eg, p, dev2 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                          st));
     G2 = g;
     l2d = lds;
@@ -953,7 +961,7 @@ int solve_adaptive_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, 
   const bool dev[2] = {d1, d2};
   for (int s = 0; s < 2; ++s)
     if (!dev[s]) {
-      CU(cudaMemcpy2DAsync(w.g[s], lds * sizeof(T), src[s], ldg[s] * sizeof(T), n * sizeof(T), Ms[s],
+      CU(copy_rows(w.g[s], lds * sizeof(T), src[s], ldg[s] * sizeof(T), n * sizeof(T), Ms[s],
                            cudaMemcpyHostToDevice, st));
       Gs[s] = w.g[s];
       ldg[s] = lds;
@@ -1137,7 +1145,7 @@ int probe_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, const voi
   for (int s = 0; s < 2; ++s)
     if (!inplace[s]) {
       unsigned char* g = bp.take<unsigned char>(Ms[s] * lds * eg);
-      CU(cudaMemcpy2DAsync(g, lds * eg, Gs[s], ldg[s] * eg, n * eg, Ms[s],
+      CU(copy_rows(g, lds * eg, Gs[s], ldg[s] * eg, n * eg, Ms[s],
                            dv[s] ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
       Gs[s] = g;
       ldg[s] = lds;
