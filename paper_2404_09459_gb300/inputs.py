@@ -138,9 +138,12 @@ def planted_pair_torch(spec: PairSpec, device="cuda", dtype=None):
 
 
 def uneven_batch(npairs: int = 256, seed: int = 0, m_range=(2000, 30000), n_range=(100, 1000),
-                 r_range=(10, 100), oversample: int = 10, q: int = 1, sigma: float = 1e-6):
+                 r_range=(10, 100), oversample: int = 10, q: int = 1, sigma: float = 1e-9):
     """Specs of a batch of uneven pairs: m, p ~ U[m_range], n ~ U[n_range],
-    r ~ U[r_range] (clipped so that k + oversample <= min(m, p, n)), seed per pair."""
+    r ~ U[r_range] (clipped so that k + oversample <= min(m, p, n)), seed per pair.
+    sigma = 1e-9 keeps every planted scale exp(-i/10), i <= 100, far above the noise floor
+    sigma (sqrt(M) + sqrt(n)); at 1e-6 the tail of ranks above ~70 would sit in the noise and its
+    GSVs would be noise-determined."""
     rng = np.random.default_rng(np.random.SeedSequence([seed, npairs, 4242]))
     specs = []
     for i in range(npairs):
@@ -157,7 +160,7 @@ def uneven_batch(npairs: int = 256, seed: int = 0, m_range=(2000, 30000), n_rang
 def learned_pairs(npairs: int, seed: int = 0, sigma: float = 1e-9, m_range=(2000, 30000), n_range=(100, 1000),
                   r_range=(10, 100), oversample: int = 10):
     """Pairs of the learned-proposal workload: the uneven-batch laws (m, p, n, r, alpha, exp(-i/10)
-    scale) with noise sigma; at the batch's sigma = 1e-6 the noise alone is ~2e-3 of ||G||_F, above
+    scale) with noise sigma; at sigma = 1e-6 the noise alone would be ~2e-3 of ||G||_F, above
     the 1e-4 residual tolerance the labels are taken at, so every basis narrower than n would miss."""
     return uneven_batch(npairs, seed, m_range=m_range, n_range=n_range, r_range=r_range, oversample=oversample,
                         q=1, sigma=sigma)

@@ -162,3 +162,33 @@ def test_grouped_leaves_out_pairs_with_unaligned_rows():
         assert e.value.name == "ARG"
         outs = ctx.solve_grouped([pairs[0], pairs[2]])
     _check_vs_oracle("tf32x3", [specs[0]], [mats[0]], outs[:1])
+
+
+def test_grouped_limits_widest_basis_small_tiles_and_q0():
+    # l = 128 (the widest grouped basis: two 128-column accumulators and the A ring fill the
+    # tensor memory; a 256-row stack), pairs shorter than one 128-row tile, q = 0 everywhere
+    specs = [PairSpec(m=900, p=700, n=300, r=60, alpha="uniform", decay="exp10", sigma=1e-10, k=60,
+                      oversample=68, q=0, seed=31),
+             PairSpec(m=100, p=90, n=64, r=6, alpha="uniform", decay="exp10", sigma=1e-6, k=6,
+                      oversample=4, q=0, seed=32),
+             PairSpec(m=130, p=257, n=41, r=9, alpha="uniform", decay="exp10", sigma=1e-6, k=9,
+                      oversample=7, q=0, seed=33)]
+    mats = [planted_pair(s)[:2] for s in specs]
+    with P.Context("tf32x3") as ctx:
+        outs = ctx.solve_grouped(_pairs(specs, mats))
+        single = _pairs(specs, mats)[1:2]  # keeps its pair word (1)
+        one = ctx.solve_grouped(single)
+    _check_vs_oracle("tf32x3", specs, mats, outs)
+    # a group of one pair: the same arithmetic as inside the larger group
+    np.testing.assert_array_equal(one[0]["alpha"].cpu().numpy(), outs[1]["alpha"].cpu().numpy())
+
+
+def test_grouped_batch_laws_at_the_largest_ranks():
+    # the uneven-batch laws at their largest ranks (exp(-i/10) scales down to ~5e-5 of the first,
+    # a compressed-pair Gram spanning ~1e-9), noise sigma 1e-9 well below the smallest planted scale
+    from paper_2404_09459_gb300.inputs import uneven_batch
+    specs = [s for s in uneven_batch(64, seed=9, m_range=(1500, 4000), n_range=(200, 600), r_range=(92, 100))][:3]
+    mats = [planted_pair(s)[:2] for s in specs]
+    with P.Context("tf32x3") as ctx:
+        outs = ctx.solve_grouped(_pairs(specs, mats))
+    _check_vs_oracle("tf32x3", specs, mats, outs)
