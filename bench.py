@@ -281,7 +281,8 @@ def run_batched(args, rank, world):
         ctx.solve_batched(pairs, workers=args.workers)
         torch.cuda.synchronize()
         other = {"value": npairs / (time.perf_counter() - t0), "unit": "pairs/s",
-                 "form": f"{args.workers} concurrent worker streams, per-pair launches"}
+                 "form": f"{args.workers} concurrent worker streams, per-pair launches",
+                 "chol64_retries": ctx.chol64_retries() // 2}  # per call (two calls above)
     sec = sum(times)
     if dist is not None:
         t = torch.tensor([sec], device=f"cuda:{local}")

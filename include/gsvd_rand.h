@@ -105,7 +105,9 @@ typedef struct {
 } gsvd_rand_config;
 
 /* flags */
-#define GSVD_RAND_FLAG_CHOL_FP64 1 /* mixed precisions: run the CholeskyQR factorisations in FP64 */
+#define GSVD_RAND_FLAG_CHOL_FP64 1 /* mixed precisions: run the CholeskyQR factorisations in FP64
+                                      (without it, a solve whose FP32 factors break down is repeated
+                                      in this form: gsvd_rand_chol64_retries) */
 #define GSVD_RAND_FLAG_PROFILE 2   /* time each stage with CUDA events on the solve stream */
 #define GSVD_RAND_FLAG_BF16_SPLIT_POWER 4 /* BF16: power-step operands as hi + lo (two products) */
 #define GSVD_RAND_FLAG_BASIS_ONLY 8 /* bases and residuals only: no compressed-pair GSVD, alpha and
@@ -289,6 +291,13 @@ int gsvd_rand_profile_reset(gsvd_rand_t h);
  * the fixed path, the Algorithm 1 block counts times block_b (or the cap) on the adaptive
  * path.  Errors: ARG (NULL handle). */
 int gsvd_rand_basis_cols(gsvd_rand_t h, int *l1, int *l2);
+
+/* Number of solves on h and its gsvd_rand_solve_batched workers that were repeated with FP64
+ * Cholesky factors (the GSVD_RAND_FLAG_CHOL_FP64 form) because the FP32 factors of their
+ * CholeskyQR broke down (NONFINITE or BREAKDOWN): FP32 data whose sketch is conditioned
+ * beyond about 1e6, where the first shifted pass leaves Q1 too ill-conditioned for an FP32
+ * Gram.  The repeated solve's result is the one returned.  Errors: ARG (NULL handle). */
+int gsvd_rand_chol64_retries(gsvd_rand_t h, int64_t *count);
 
 /* Total number of CUDA kernels this library has launched in this process. */
 uint64_t gsvd_rand_launch_count(void);

@@ -26,7 +26,7 @@ EXPORTS = ("gsvd_rand_config_init", "gsvd_rand_create", "gsvd_rand_destroy", "gs
            "gsvd_rand_metrics_noalloc", "gsvd_rand_basis_cols", "gsvd_rand_solve_batched",
            "gsvd_rand_probe_features", "gsvd_rand_mlp_forward", "gsvd_rand_mlp_loss_grad", "gsvd_rand_mlp_adam",
            "gsvd_rand_mlp_train", "gsvd_rand_mlp_set", "gsvd_rand_mlp_load", "gsvd_rand_last_plan",
-           "gsvd_rand_solve_grouped", "gsvd_rand_grouped_info")
+           "gsvd_rand_solve_grouped", "gsvd_rand_grouped_info", "gsvd_rand_chol64_retries")
 NOALLOC_MAX_N = 32768
 FLAG_PROFILE = 2
 FLAG_BF16_SPLIT_POWER = 4
@@ -98,6 +98,7 @@ def load_library(path: str | None = None):
     lib.gsvd_rand_mlp_set.argtypes = [vp, vp, vp]
     lib.gsvd_rand_mlp_load.argtypes = [vp, C.c_char_p]
     lib.gsvd_rand_last_plan.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    lib.gsvd_rand_chol64_retries.argtypes = [vp, C.POINTER(C.c_int64)]
     for name in EXPORTS:
         if name not in ("gsvd_rand_last_error", "gsvd_rand_launch_count"):
             getattr(lib, name).restype = C.c_int
@@ -383,6 +384,13 @@ class Context:
         a, b = C.c_int(0), C.c_int(0)
         self._check(self.lib.gsvd_rand_basis_cols(self.h, C.byref(a), C.byref(b)))
         return a.value, b.value
+
+    def chol64_retries(self) -> int:
+        """Solves (on this context and its batched workers) repeated with FP64 Cholesky
+        factors after their FP32 CholeskyQR broke down."""
+        c = C.c_int64(0)
+        self._check(self.lib.gsvd_rand_chol64_retries(self.h, C.byref(c)))
+        return c.value
 
     def metrics(self, alpha, beta, pad_to_n: int = 0, pad_mode: int = 0):
         """Section 1 quantities: dict(theta, rho, P1, P2, D1, D2)."""

@@ -47,6 +47,7 @@ struct gsvd_rand_ctx {
   struct GroupState* grp = nullptr;     // gsvd_rand_solve_grouped: plan, tables and captured graph
   unsigned char* tab_host = nullptr;    // pinned staging of the two-side product tables of a solve
   size_t tab_host_bytes = 0;
+  int64_t chol64_retries = 0;  // solves repeated with FP64 Cholesky factors
   // learned proposal: network (params | norm), then features, logits and scratch of one pair
   float* mlp_dev = nullptr;
   bool mlp_ready = false;
@@ -457,8 +458,11 @@ struct Solver {
     return GSVD_RAND_OK;
   }
 
-  // Both sides in lockstep (each step for side 0, then side 1, the re-orthonormalisations
-  // of both in one launch where they fit): the per-side arithmetic of side() unchanged.
+  // Both sides in lockstep (each step for side 0, then side 1, the products and the
+  // re-orthonormalisations of both in one launch where they fit).  Per side: Y = G Omega,
+  // Q = orth(Y), q times (Z = orth(G^T Q), Q = orth(G Z)), then B = Q^T G as l rows of S.
+  // BF16 mode: the power steps take their FP32 operand rounded to BF16 (or as hi + lo with
+  // split_power); the projection always takes Q as hi + lo.
   int sides(const void* const* G, const int64_t* ldg, const Plan& pl, SideBufs<T>* b, int q, uint64_t seed,
             T* S) {
     const int qt = use_tc ? 1 : 0;
@@ -531,40 +535,6 @@ struct Solver {
         if ((rc = gtq(G[s], ldg[s], pl.M[s], pl, b[s], So[s], pl.ldn, 1, b[s].bnorm, true))) return rc;
       }
     }
-    return GSVD_RAND_OK;
-  }
-
-  int side(const void* G, int64_t ldg, int s, const Plan& pl, SideBufs<T>& b, int q, uint64_t seed,
-           T* Srows) {
-    const int64_t M = pl.M[s];
-    if (bf16)
-      CU(launch_gaussian_kmajor_bf16(b.Xh, pl.ldx, pl.n, pl.l, (int)pl.lx, seed, h->pair_word, (uint32_t)s,
-                                     GSVD_RAND_STREAM_FIXED, st));
-    else
-      CU(launch_gaussian_kmajor<T>(b.Xt, pl.ldx, pl.n, pl.l, (int)pl.lx, seed, h->pair_word, (uint32_t)s,
-                                   GSVD_RAND_STREAM_FIXED, st));
-    // Q layout: row-major M x lp for the CUDA-core product, transposed Q^T
-    // (lx x ldm, padding rows zero) as the K-major operand of the tensor-core one
-    const int qt = use_tc ? 1 : 0;
-    const int64_t ldq = use_tc ? round_up(M, 4) : pl.lp;
-    if (use_tc)
-      CU(cudaMemsetAsync(b.Q + (int64_t)pl.l * ldq, 0, (size_t)(pl.lx - pl.l) * ldq * sizeof(T), st));
-    int rc;
-    if ((rc = gx(G, ldg, M, pl, b, b.gnorm))) return rc;
-    if ((rc = orth(b, b.Y, M, pl.l, pl.lp, b.Q, ldq, qt, 10 * s + 1, s))) return rc;
-    // BF16 mode: the power steps take their FP32 operand rounded to BF16 (or as hi + lo
-    // with split_power); the projection always takes Q as hi + lo
-    for (int it = 0; it < q; ++it) {
-      if (bf16 && (rc = split_q(b, M, pl, split_power))) return rc;
-      if ((rc = gtq(G, ldg, M, pl, b, b.Z, pl.lp, 0, nullptr, split_power))) return rc;
-      if ((rc = orth(b, b.Z, pl.n, pl.l, pl.lp, b.Xt, pl.ldx, 1, 10 * s + 3, s))) return rc;
-      if (bf16 && (rc = split_x(b, pl, split_power))) return rc;
-      if ((rc = gx(G, ldg, M, pl, b, nullptr, split_power))) return rc;
-      if ((rc = orth(b, b.Y, M, pl.l, pl.lp, b.Q, ldq, qt, 10 * s + 5, s))) return rc;
-    }
-    // projection B = Q^T G written as l rows of S
-    if (bf16 && (rc = split_q(b, M, pl, true))) return rc;
-    if ((rc = gtq(G, ldg, M, pl, b, Srows, pl.ldn, 1, b.bnorm, true))) return rc;
     return GSVD_RAND_OK;
   }
 };
@@ -1199,14 +1169,30 @@ int solve_dispatch(gsvd_rand_ctx* h, bool adaptive, const void* G1, int64_t m, i
                    int* r_out, double* resid_out) {
   const bool f64 = h->cfg.prec == GSVD_RAND_FP64;
   const bool c64 = (h->cfg.flags & GSVD_RAND_FLAG_CHOL_FP64) != 0;
+  // FP32 data with FP32 Cholesky factors: the first (shifted) CholeskyQR pass leaves
+  // kappa(Q1) ~ sqrt(s) kappa(Y), s ~ 11 (rpc + l + 1) u tr(Y^T Y).  For sketches with
+  // kappa(Y) above ~1e6 (a rank well below l with the noise under FP32 resolution) that is
+  // beyond u^(-1/2) of FP32, the FP32 Gram of the next pass no longer resolves Q1's weak
+  // columns, and its pivots can overflow (NONFINITE) or vanish (BREAKDOWN).  Such a solve is
+  // repeated with the Cholesky factors in FP64 (the GSVD_RAND_FLAG_CHOL_FP64 form).
+  auto retry = [](int rc) { return rc == GSVD_RAND_ERR_NONFINITE || rc == GSVD_RAND_ERR_BREAKDOWN; };
   if (adaptive) {
     if (f64) return solve_adaptive_t<double, double>(h, G1, m, ld1, G2, p, ld2, n, k, seed, alpha, beta, r_out, resid_out);
-    if (c64) return solve_adaptive_t<float, double>(h, G1, m, ld1, G2, p, ld2, n, k, seed, alpha, beta, r_out, resid_out);
-    return solve_adaptive_t<float, float>(h, G1, m, ld1, G2, p, ld2, n, k, seed, alpha, beta, r_out, resid_out);
+    if (!c64) {
+      const int rc = solve_adaptive_t<float, float>(h, G1, m, ld1, G2, p, ld2, n, k, seed, alpha, beta, r_out, resid_out);
+      if (!retry(rc)) return rc;
+      ++h->chol64_retries;
+    }
+    return solve_adaptive_t<float, double>(h, G1, m, ld1, G2, p, ld2, n, k, seed, alpha, beta, r_out, resid_out);
   }
   if (f64) return solve_t<double, double>(h, G1, m, ld1, G2, p, ld2, n, k, oversample, q, seed, alpha, beta, r_out, resid_out);
-  if (c64) return solve_t<float, double>(h, G1, m, ld1, G2, p, ld2, n, k, oversample, q, seed, alpha, beta, r_out, resid_out);
-  return solve_t<float, float>(h, G1, m, ld1, G2, p, ld2, n, k, oversample, q, seed, alpha, beta, r_out, resid_out);
+  if (!c64) {
+    const int rc = solve_t<float, float>(h, G1, m, ld1, G2, p, ld2, n, k, oversample, q, seed, alpha, beta, r_out,
+                                         resid_out);
+    if (!retry(rc)) return rc;
+    ++h->chol64_retries;
+  }
+  return solve_t<float, double>(h, G1, m, ld1, G2, p, ld2, n, k, oversample, q, seed, alpha, beta, r_out, resid_out);
 }
 
 constexpr int MLP_IN = GSVD_RAND_MLP_IN, MLP_OUT = GSVD_RAND_MLP_KCLS + GSVD_RAND_MLP_QCLS;
@@ -2304,6 +2290,14 @@ int gsvd_rand_profile_reset(gsvd_rand_t h) {
 }
 
 uint64_t gsvd_rand_launch_count(void) { return gsvdr::g_launch_count.load(); }
+
+int gsvd_rand_chol64_retries(gsvd_rand_t h, int64_t* count) {
+  if (!h || !count) return GSVD_RAND_ERR_ARG;
+  int64_t c = h->chol64_retries;
+  for (gsvd_rand_ctx* w : h->workers) c += w->chol64_retries;
+  *count = c;
+  return GSVD_RAND_OK;
+}
 
 int gsvd_rand_basis_cols(gsvd_rand_t h, int* l1, int* l2) {
   if (!h) return GSVD_RAND_ERR_ARG;

@@ -10,7 +10,8 @@ import pytest
 
 from oracle import gsvd as O
 from oracle.philox import gaussian, philox_words
-from paper_2404_09459_gb300.inputs import PAIR_FP64_SMALL, PAIR_TF32_LARGE, PairSpec, planted_pair
+from paper_2404_09459_gb300.inputs import (PAIR_FP64_SMALL, PAIR_TF32_LARGE, PairSpec, aligned_rows, planted_pair,
+                                          planted_pair_torch)
 
 pytestmark = pytest.mark.gpu
 
@@ -235,6 +236,39 @@ def test_batched_equals_single_solves_and_reports_per_pair_status():
         with pytest.raises(P.GsvdRandError) as e:
             ctx.solve_batched([pairs[0], bad, pairs[2]], workers=2)
         assert e.value.name == "ARG"
+
+
+def test_fp32_cholesky_breakdown_repeated_with_fp64_factors():
+    # rank 19 in a basis of 29 with the noise (1e-9) under FP32 resolution: kappa(Y) ~ 1e6, so
+    # the first shifted CholeskyQR pass can leave Q1 beyond what an FP32 Gram resolves; the FP32
+    # factors of the next pass then break down and the solve is repeated with FP64 factors.
+    # This draw (built on the device, as the batch bench builds it) broke down in FP32 on GB300.
+    spec = PairSpec(m=6845, p=19105, n=267, r=19, alpha="uniform", decay="exp10", sigma=1e-9, k=19,
+                    oversample=10, q=1, seed=100018)
+    G1, G2 = (aligned_rows(G) for G in planted_pair_torch(spec, device="cuda", dtype=torch.float32)[:2])
+    pair = dict(G1=G1, G2=G2, k=19, oversample=10, q=1, seed=spec.seed, pair=15)
+    with P.Context("tf32x3") as ctx:
+        out = ctx.solve_batched([pair], workers=1)[0]
+        retries = ctx.chol64_retries()
+    with P.Context("tf32x3", flags=P.FLAG_CHOL_FP64) as ctx:
+        f64 = ctx.solve_batched([pair], workers=1)[0]
+        assert ctx.chol64_retries() == 0
+    assert retries in (0, 1)
+    if retries:
+        # the repeated solve is the FP64-factor solve
+        np.testing.assert_array_equal(out["alpha"].cpu().numpy(), f64["alpha"].cpu().numpy())
+    ref = O.rand_gsvd(G1.double().cpu().numpy(), G2.double().cpu().numpy(), 19, 10, 1, spec.seed, pair=15)
+    for o in (out, f64):
+        e = O.gsv_error(ref["alpha"], ref["beta"], o["alpha"].cpu().numpy(), o["beta"].cpu().numpy())
+        assert np.max(e) <= TOL["tf32x3"], np.max(e)
+    # an input NaN breaks both factorisations: repeated once, then reported
+    bad = G1.clone()
+    bad[3, 7] = float("nan")
+    with P.Context("tf32x3") as ctx:
+        with pytest.raises(P.GsvdRandError) as e:
+            ctx.solve(bad, G2, 19, 10, 1, spec.seed)
+        assert e.value.name == "NONFINITE"
+        assert ctx.chol64_retries() == 1
 
 
 def test_adaptive_cap_reached_reports_tol_miss():
