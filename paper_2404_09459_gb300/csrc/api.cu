@@ -217,6 +217,9 @@ int64_t part_cap(const Plan& pl) {
   return pl.part_elems;
 }
 
+int tune_group(gsvd_rand_ctx* h, cudaStream_t st, int mode, int prec, bool norm, const void* table, int nprob,
+               int64_t ntiles, int nmma_max, int64_t kmean, DevStatus* st_dev, int* stages_out, int* per_sm_out);
+
 template <typename T, typename TC>
 struct Solver {
   gsvd_rand_ctx* h;
@@ -237,7 +240,7 @@ struct Solver {
 
   // One grouped launch over the two sides: the table goes through its own pinned and device
   // slot (the solve synchronises before the slots are reused).
-  int group2(int mode, bool norm, TcGroupSpec* sp) {
+  int group2(int mode, bool norm, TcGroupSpec* sp, int64_t kmean) {
     if (tab_next >= tab_slots) return fail(h, GSVD_RAND_ERR_CUDA, "grouped product table slots exhausted");
     const int slot = tab_next++;
     unsigned char* hs = h->tab_host + (size_t)slot * tab_bytes;
@@ -247,8 +250,10 @@ struct Solver {
     int nmma = 0;
     if (!tc_group_build(mode, sp, 2, hs, &nmma)) return fail(h, GSVD_RAND_ERR_ARG, "tensor map of a product rejected");
     CU(cudaMemcpyAsync(ds, hs, tc_group_table_bytes(2, ntiles), cudaMemcpyHostToDevice, st));
-    const int per_sm = prec == GSVD_RAND_TF32X3 ? 1 : (2 * round_up(nmma, 32) <= 256 ? 2 : 1);
-    const int stages = tc_group_max_stages(mode, prec, nmma, per_sm);
+    // pipeline depth and CTAs per SM: the built-in tuner, timed on the first product of each
+    // shape bucket (on this table; the launch below rewrites its outputs)
+    int stages = 0, per_sm = 0, rc;
+    if ((rc = tune_group(h, st, mode, prec, norm, ds, 2, ntiles, nmma, kmean, st_dev, &stages, &per_sm))) return rc;
     CU(tc_group_launch(mode, prec, norm, ds, 2, ntiles, nmma, stages, per_sm, st_dev, st));
     return GSVD_RAND_OK;
   }
@@ -270,7 +275,7 @@ struct Solver {
       sp[s].ldo = pl.lp;
       sp[s].gnorm_part = norm ? b[s].gnorm : nullptr;
     }
-    return group2(0, norm, sp);
+    return group2(0, norm, sp, pl.n);
   }
 
   // G^T Q for both sides in one launch (split-K partials), then each side's split reduction
@@ -301,7 +306,7 @@ struct Solver {
       sp[s].split_stride = pl.n * pl.lp;
     }
     int rc;
-    if ((rc = group2(1, false, sp))) return rc;
+    if ((rc = group2(1, false, sp, (sp[0].rps + sp[1].rps) / 2))) return rc;
     for (int s = 0; s < 2; ++s) {
       int blocks = 0;
       CU((launch_reduce_splits<T, T>(b[s].part, sp[s].splits, pl.n, pl.l, pl.lp, out[s], ldo[s], transpose_out,

@@ -780,8 +780,20 @@ namespace {
 
 constexpr int TG_PREP_WARPS = 8;                   // operand preparation warps
 constexpr int TG_THREADS = 32 * (6 + TG_PREP_WARPS);  // + TMA, MMA and four drain warps
-constexpr int TG_TA_COL0 = 256;                    // first tensor-memory column of the A ring
-constexpr int TG_TA_STAGES = 4;                    // A-ring stages (64 columns each: A, then A_lo)
+constexpr int TG_TA_STAGE_COLS = 64;              // A-ring stage: 32 columns A, then 32 A_lo
+
+// 3xTF32 tensor-memory plan: one CTA per SM takes all 512 columns (the two accumulators in
+// [0, 256), a 4-stage A ring in [256, 512)); two CTAs per SM take 256 columns each (the
+// accumulators, then as many ring stages as fit: 2 for bases up to 64 columns, 3 up to 32).
+struct TaPlan {
+  int cols, col0, stages;
+};
+__host__ __device__ inline TaPlan ta_plan(int acc_stride, int per_sm) {
+  const int cols = per_sm >= 2 ? 256 : 512;
+  const int col0 = per_sm >= 2 ? 2 * acc_stride : 256;
+  const int st = col0 < cols ? (cols - col0) / TG_TA_STAGE_COLS : 0;
+  return TaPlan{cols, col0, 2 * acc_stride <= col0 ? st : 0};
+}
 
 // Shared-memory stage of the grouped kernel: with SPLIT, the staged A tile (16 KB), B and
 // B_lo (each nmma x 128 bytes, 1024-aligned); otherwise the StageLayout of tc_gemm_kernel.
@@ -809,10 +821,10 @@ struct GroupLayout {
 };
 
 template <int MODE, bool NORM, bool SPLIT>
-__global__ __launch_bounds__(TG_THREADS) void tc_group_kernel(const TcGroupProb* __restrict__ probs,
+__global__ __launch_bounds__(TG_THREADS, 2) void tc_group_kernel(const TcGroupProb* __restrict__ probs,
                                                               const int2* __restrict__ tiles, int ntiles,
                                                               int nmma_max, int acc_stride, int tmem_cols,
-                                                              int stages, DevStatus* st_glob) {
+                                                              int ta_col0, int stages, DevStatus* st_glob) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   constexpr int BKE = 32;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -934,7 +946,7 @@ __global__ __launch_bounds__(TG_THREADS) void tc_group_kernel(const TcGroupProb*
           }
           tc_fence_after();
           const uint32_t st = smem_u32(base + (size_t)s * L.bytes);
-          const uint32_t ta = tmem + (uint32_t)(TG_TA_COL0 + 64 * s);  // A (3xTF32): columns 0-31 A, 32-63 A_lo
+          const uint32_t ta = tmem + (uint32_t)(ta_col0 + TG_TA_STAGE_COLS * s);  // 0-31 A, 32-63 A_lo
 #pragma unroll
           for (int ks = 0; ks < 128 / TC_KSTEP_BYTES; ++ks) {
             const uint64_t bdesc = smem_desc(st + L.b + ks * TC_KSTEP_BYTES, 16, 1024);
@@ -1014,7 +1026,8 @@ __global__ __launch_bounds__(TG_THREADS) void tc_group_kernel(const TcGroupProb*
               if (NORM) sq.add(v[k]);
               lo[k] = tf32_lo(v[k]);
             }
-            const uint32_t ta = tmem + ((uint32_t)(32 * sub) << 16) + (uint32_t)(TG_TA_COL0 + 64 * s + 16 * half);
+            const uint32_t ta =
+                tmem + ((uint32_t)(32 * sub) << 16) + (uint32_t)(ta_col0 + TG_TA_STAGE_COLS * s + 16 * half);
             tmem_st16(ta, v);
             tmem_st16(ta + 32u, lo);
             // B_lo in shared memory
@@ -1198,11 +1211,11 @@ bool tc_group_build(int mode, const TcGroupSpec* specs, int nprob, void* host, i
 
 int tc_group_max_stages(int mode, int prec, int nmma_max, int per_sm) {
   const bool split = prec == 3;
-  // 3xTF32 keeps A in tensor memory: all 512 columns (two accumulators, the A ring), one CTA per SM
-  if (split && per_sm >= 2) return 0;
   const int budget = (per_sm >= 2 ? 110 : 214) * 1024 - 2048;
   const int stage = (int)GroupLayout(mode, split, nmma_max).bytes;
-  return std::min(budget / stage, split ? TG_TA_STAGES : 8);
+  // 3xTF32: each pipeline stage owns a stage of the A ring in tensor memory
+  const int cap = split ? ta_plan((int)round_up(nmma_max, 32), per_sm).stages : 8;
+  return std::min(budget / stage, cap);
 }
 
 cudaError_t tc_group_launch(int mode, int prec, bool norm, const void* dev_table, int nprob, int64_t ntiles,
@@ -1210,9 +1223,11 @@ cudaError_t tc_group_launch(int mode, int prec, bool norm, const void* dev_table
   if (ntiles <= 0) return cudaSuccess;
   const bool split = prec == 3;
   const int acc_stride = (int)round_up(nmma_max, 32);
-  // 3xTF32: the two accumulators in columns [0, 256), the A ring in [256, 512)
-  const int tmem_cols = split ? 512 : tmem_cols_for(2 * acc_stride);
-  if (2 * acc_stride > (split ? TG_TA_COL0 : 512) || (per_sm >= 2 && tmem_cols > 256)) return cudaErrorInvalidValue;
+  // 3xTF32: the two accumulators, then the A ring (ta_plan)
+  const TaPlan tp = ta_plan(acc_stride, per_sm);
+  const int tmem_cols = split ? tp.cols : tmem_cols_for(2 * acc_stride);
+  const int ta_col0 = split ? tp.col0 : 0;
+  if (2 * acc_stride > (split ? ta_col0 : 512) || (per_sm >= 2 && tmem_cols > 256)) return cudaErrorInvalidValue;
   if (stages < 2 || stages > tc_group_max_stages(mode, prec, nmma_max, per_sm)) return cudaErrorInvalidValue;
   const TcGroupProb* probs = static_cast<const TcGroupProb*>(dev_table);
   const int2* tiles = reinterpret_cast<const int2*>(static_cast<const unsigned char*>(dev_table) +
@@ -1226,7 +1241,7 @@ cudaError_t tc_group_launch(int mode, int prec, bool norm, const void* dev_table
   do {                                                                                                       \
     cudaFuncSetAttribute(tc_group_kernel<M_, N_, S_>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024); \
     tc_group_kernel<M_, N_, S_><<<grid, TG_THREADS, smem, st>>>(probs, tiles, (int)ntiles, nmma_max, acc_stride, \
-                                                                tmem_cols, stages, st_dev);                  \
+                                                                tmem_cols, ta_col0, stages, st_dev);         \
   } while (0)
   if (mode == 0) {
     if (norm && split) GSVDR_TG(0, true, true);
