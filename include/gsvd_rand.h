@@ -195,9 +195,10 @@ int gsvd_rand_solve_batched(gsvd_rand_t h, int npairs, gsvd_rand_pair *pairs, in
  * whole batch (Algorithms 1 and 2 of Section 2 per pair, as gsvd_rand_solve):
  *   - the products Y = G X, G^T Q and Q^T G of all sides are persistent grouped
  *     tcgen05 launches over one tile table (per-problem tensor maps, tiles longest
- *     first, double-buffered tensor-memory accumulators); their pipeline depth and
- *     CTAs per SM are picked by a built-in autotuner (timed on the first batch of
- *     each size bucket; the choice does not change the results);
+ *     first, tensor-memory accumulators); their pipeline depth and CTAs per SM are
+ *     picked by a built-in autotuner (timed on the first batch of each size bucket;
+ *     the choice does not change the results; the environment variable
+ *     GSVD_RAND_GROUP_PIPELINE="stages,ctas_per_sm" pins it where that shape fits);
  *   - the shifted CholeskyQR3 passes, the split reductions, the residuals and the
  *     compressed-pair GSVDs run as batched kernels (one table entry per problem).
  * The whole launch sequence is captured into a CUDA graph and replayed while the

@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <map>
@@ -1348,6 +1349,17 @@ int ilog2_bucket(int64_t v) {
 
 int tune_group(gsvd_rand_ctx* h, cudaStream_t st, int mode, int prec, bool norm, const void* table, int nprob,
                int64_t ntiles, int nmma_max, int64_t kmean, DevStatus* st_dev, int* stages_out, int* per_sm_out) {
+  // GSVD_RAND_GROUP_PIPELINE="stages,ctas_per_sm" pins the shape where it fits this launch
+  if (const char* env = getenv("GSVD_RAND_GROUP_PIPELINE")) {
+    int s = 0, p = 0;
+    if (sscanf(env, "%d,%d", &s, &p) == 2 && (p == 1 || p == 2) && s >= 2 &&
+        s <= tc_group_max_stages(mode, prec, nmma_max, p) &&
+        (p == 1 || prec == GSVD_RAND_TF32X3 || 2 * round_up(nmma_max, 32) <= 256)) {
+      *stages_out = s;
+      *per_sm_out = p;
+      return GSVD_RAND_OK;
+    }
+  }
   const TuneKey key{mode, prec, norm ? 1 : 0, nmma_max, ilog2_bucket(ntiles), ilog2_bucket(kmean)};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -1360,7 +1372,8 @@ int tune_group(gsvd_rand_ctx* h, cudaStream_t st, int mode, int prec, bool norm,
   }
   std::vector<std::pair<int, int>> cand;
   for (int per_sm = 2; per_sm >= 1; --per_sm) {
-    if (per_sm == 2 && 2 * round_up(nmma_max, 32) > 256) continue;
+    // two CTAs per SM: 256 tensor-memory columns each (3xTF32 plans them in tc_group_max_stages)
+    if (per_sm == 2 && prec != GSVD_RAND_TF32X3 && 2 * round_up(nmma_max, 32) > 256) continue;
     const int ms = tc_group_max_stages(mode, prec, nmma_max, per_sm);
     for (int s : {2, 3, 4, 6, 8})
       if (s <= ms) cand.push_back({s, per_sm});

@@ -782,17 +782,23 @@ constexpr int TG_PREP_WARPS = 8;                   // operand preparation warps
 constexpr int TG_THREADS = 32 * (6 + TG_PREP_WARPS);  // + TMA, MMA and four drain warps
 constexpr int TG_TA_STAGE_COLS = 64;              // A-ring stage: 32 columns A, then 32 A_lo
 
-// 3xTF32 tensor-memory plan: one CTA per SM takes all 512 columns (the two accumulators in
-// [0, 256), a 4-stage A ring in [256, 512)); two CTAs per SM take 256 columns each (the
-// accumulators, then as many ring stages as fit: 2 for bases up to 64 columns, 3 up to 32).
+// 3xTF32 tensor-memory plan: one CTA per SM takes all 512 columns (two accumulators in
+// [0, 256), a 4-stage A ring in [256, 512)).  Two CTAs per SM take 256 columns each: two
+// accumulators and the ring stages that fit after them (3 for bases up to 32 columns, 2 up
+// to 64), or, for wider bases, a single accumulator (its drain then overlaps the other CTA's
+// work, not the next tile's MMAs) and a 2-stage ring.
 struct TaPlan {
-  int cols, col0, stages;
+  int cols, col0, stages, nacc;
 };
 __host__ __device__ inline TaPlan ta_plan(int acc_stride, int per_sm) {
-  const int cols = per_sm >= 2 ? 256 : 512;
-  const int col0 = per_sm >= 2 ? 2 * acc_stride : 256;
-  const int st = col0 < cols ? (cols - col0) / TG_TA_STAGE_COLS : 0;
-  return TaPlan{cols, col0, 2 * acc_stride <= col0 ? st : 0};
+  if (per_sm < 2) return TaPlan{512, 256, 2 * acc_stride <= 256 ? 4 : 0, 2};
+  int nacc = 2, col0 = 2 * acc_stride;
+  if (256 - col0 < 2 * TG_TA_STAGE_COLS) {
+    nacc = 1;
+    col0 = (acc_stride + TG_TA_STAGE_COLS - 1) / TG_TA_STAGE_COLS * TG_TA_STAGE_COLS;
+  }
+  const int st = col0 < 256 ? (256 - col0) / TG_TA_STAGE_COLS : 0;
+  return TaPlan{256, col0, st, nacc};
 }
 
 // Shared-memory stage of the grouped kernel: with SPLIT, the staged A tile (16 KB), B and
@@ -824,7 +830,8 @@ template <int MODE, bool NORM, bool SPLIT>
 __global__ __launch_bounds__(TG_THREADS, 2) void tc_group_kernel(const TcGroupProb* __restrict__ probs,
                                                               const int2* __restrict__ tiles, int ntiles,
                                                               int nmma_max, int acc_stride, int tmem_cols,
-                                                              int ta_col0, int stages, DevStatus* st_glob) {
+                                                              int ta_col0, int nacc, int stages,
+                                                              DevStatus* st_glob) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   constexpr int BKE = 32;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -931,8 +938,9 @@ __global__ __launch_bounds__(TG_THREADS, 2) void tc_group_kernel(const TcGroupPr
         int t0;
         krange(P, tr.y, kb, ke, t0);
         const int kt_n = (int)((ke - kb + BKE - 1) / BKE);
-        const int acc = j & 1;
-        if (j >= 2 && !mbar_wait(&tmempty[acc], (uint32_t)((j >> 1) + 1) & 1u, abort_flag)) break;
+        // accumulator acc, its use jj: waits for the drain of its previous use
+        const int acc = nacc == 2 ? (j & 1) : 0, jj = nacc == 2 ? (j >> 1) : j;
+        if (j >= nacc && !mbar_wait(&tmempty[acc], (uint32_t)(jj + 1) & 1u, abort_flag)) break;
         tc_fence_after();
         const uint32_t d = tmem + (uint32_t)(acc * acc_stride);
         const uint32_t idesc = idesc_tf32(TC_BM, (uint32_t)P.nmma, 0u, 0u);
@@ -1089,8 +1097,8 @@ __global__ __launch_bounds__(TG_THREADS, 2) void tc_group_kernel(const TcGroupPr
       int64_t kb, ke;
       int t0;
       krange(P, tr.y, kb, ke, t0);
-      const int acc = j & 1;
-      if (!mbar_wait(&tmfull[acc], (uint32_t)(j >> 1) & 1u, abort_flag)) break;
+      const int acc = nacc == 2 ? (j & 1) : 0, jj = nacc == 2 ? (j >> 1) : j;
+      if (!mbar_wait(&tmfull[acc], (uint32_t)jj & 1u, abort_flag)) break;
       tc_fence_after();
       const int row = 32 * q + lane;
       const int64_t grow = (int64_t)t0 + row;
@@ -1226,8 +1234,8 @@ cudaError_t tc_group_launch(int mode, int prec, bool norm, const void* dev_table
   // 3xTF32: the two accumulators, then the A ring (ta_plan)
   const TaPlan tp = ta_plan(acc_stride, per_sm);
   const int tmem_cols = split ? tp.cols : tmem_cols_for(2 * acc_stride);
-  const int ta_col0 = split ? tp.col0 : 0;
-  if (2 * acc_stride > (split ? ta_col0 : 512) || (per_sm >= 2 && tmem_cols > 256)) return cudaErrorInvalidValue;
+  const int ta_col0 = split ? tp.col0 : 0, nacc = split ? tp.nacc : 2;
+  if (nacc * acc_stride > (split ? ta_col0 : 512) || (per_sm >= 2 && tmem_cols > 256)) return cudaErrorInvalidValue;
   if (stages < 2 || stages > tc_group_max_stages(mode, prec, nmma_max, per_sm)) return cudaErrorInvalidValue;
   const TcGroupProb* probs = static_cast<const TcGroupProb*>(dev_table);
   const int2* tiles = reinterpret_cast<const int2*>(static_cast<const unsigned char*>(dev_table) +
@@ -1241,7 +1249,7 @@ cudaError_t tc_group_launch(int mode, int prec, bool norm, const void* dev_table
   do {                                                                                                       \
     cudaFuncSetAttribute(tc_group_kernel<M_, N_, S_>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024); \
     tc_group_kernel<M_, N_, S_><<<grid, TG_THREADS, smem, st>>>(probs, tiles, (int)ntiles, nmma_max, acc_stride, \
-                                                                tmem_cols, ta_col0, stages, st_dev);         \
+                                                                tmem_cols, ta_col0, nacc, stages, st_dev);   \
   } while (0)
   if (mode == 0) {
     if (norm && split) GSVDR_TG(0, true, true);

@@ -183,6 +183,27 @@ def test_grouped_limits_widest_basis_small_tiles_and_q0():
     np.testing.assert_array_equal(one[0]["alpha"].cpu().numpy(), outs[1]["alpha"].cpu().numpy())
 
 
+def test_grouped_pipeline_shapes_agree_bit_for_bit(monkeypatch):
+    # every pipeline shape the tuner may pick runs each tile's MMAs in the same order, so the
+    # results are the same: two CTAs per SM (bases wider than 64 columns: one accumulator each),
+    # one CTA per SM with 2 or 4 ring stages
+    specs = _specs(17, 6, wide=True)
+    mats = [planted_pair(s)[:2] for s in specs]
+    pairs = _pairs(specs, mats)
+    res = {}
+    for shape in ("2,2", "2,1", "4,1"):
+        monkeypatch.setenv("GSVD_RAND_GROUP_PIPELINE", shape)
+        with P.Context("tf32x3") as ctx:
+            res[shape] = ctx.solve_grouped(pairs)
+            tuned = ctx.grouped_info()["tuned"]
+        assert all(t == tuple(int(x) for x in shape.split(",")) for t in tuned), (shape, tuned)
+    for shape in ("2,1", "4,1"):
+        for a, b in zip(res["2,2"], res[shape]):
+            np.testing.assert_array_equal(a["alpha"].cpu().numpy(), b["alpha"].cpu().numpy())
+            np.testing.assert_array_equal(a["beta"].cpu().numpy(), b["beta"].cpu().numpy())
+    _check_vs_oracle("tf32x3", specs, mats, res["2,2"])
+
+
 def test_grouped_batch_laws_at_the_largest_ranks():
     # the uneven-batch laws at their largest ranks (exp(-i/10) scales down to ~5e-5 of the first,
     # a compressed-pair Gram spanning ~1e-9), noise sigma 1e-9 well below the smallest planted scale
