@@ -620,6 +620,11 @@ def main():
                            "parallelism": f"independent pairs, {world} rank(s)"},
                 "sketch_tflops": tflops, "roofline": roof, "stages": stages, "fp64_plain": fp64,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary()}
+        shapes = ctx.product_shapes()
+        if any(s for sh in shapes for s in sh):
+            # the timed solves' grouped two-side products: (stages, CTAs per SM) the tuner picked
+            line["product_pipeline"] = {"first_sketch": shapes[0], "power_sketch": shapes[1],
+                                        "gtq_projection": shapes[2]}
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist is not None:

@@ -223,6 +223,13 @@ int gsvd_rand_solve_grouped(gsvd_rand_t h, int npairs, gsvd_rand_pair *pairs);
  * replays so far and the kernel launches per replay.  Any pointer may be NULL. */
 int gsvd_rand_grouped_info(gsvd_rand_t h, int *tuned, int64_t *captures, int64_t *replays, int64_t *launches);
 
+/* The pipeline shapes of the last gsvd_rand_solve on h whose products of both sides ran as
+ * grouped tensor-core launches (fixed rank, TF32 / TF32X3, k + oversample <= 128):
+ * shapes[6] = (stages, CTAs per SM) of the first sketch, the power-step sketch and the
+ * G^T Q / projection products, as the built-in tuner picked them (zeros before such a
+ * solve).  Errors: ARG (NULL handle or shapes). */
+int gsvd_rand_product_shapes(gsvd_rand_t h, int *shapes);
+
 /* Comparative quantities of Section 1 for r GSV pairs (alpha non-increasing,
  * beta non-decreasing):
  *   theta[i] = atan2(alpha_i, beta_i) - pi/4      (antisymmetric angular distance)

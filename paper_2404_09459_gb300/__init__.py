@@ -26,7 +26,8 @@ EXPORTS = ("gsvd_rand_config_init", "gsvd_rand_create", "gsvd_rand_destroy", "gs
            "gsvd_rand_metrics_noalloc", "gsvd_rand_basis_cols", "gsvd_rand_solve_batched",
            "gsvd_rand_probe_features", "gsvd_rand_mlp_forward", "gsvd_rand_mlp_loss_grad", "gsvd_rand_mlp_adam",
            "gsvd_rand_mlp_train", "gsvd_rand_mlp_set", "gsvd_rand_mlp_load", "gsvd_rand_last_plan",
-           "gsvd_rand_solve_grouped", "gsvd_rand_grouped_info", "gsvd_rand_chol64_retries")
+           "gsvd_rand_solve_grouped", "gsvd_rand_grouped_info", "gsvd_rand_chol64_retries",
+           "gsvd_rand_product_shapes")
 NOALLOC_MAX_N = 32768
 FLAG_PROFILE = 2
 FLAG_BF16_SPLIT_POWER = 4
@@ -99,6 +100,7 @@ def load_library(path: str | None = None):
     lib.gsvd_rand_mlp_load.argtypes = [vp, C.c_char_p]
     lib.gsvd_rand_last_plan.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
     lib.gsvd_rand_chol64_retries.argtypes = [vp, C.POINTER(C.c_int64)]
+    lib.gsvd_rand_product_shapes.argtypes = [vp, C.POINTER(C.c_int)]
     for name in EXPORTS:
         if name not in ("gsvd_rand_last_error", "gsvd_rand_launch_count"):
             getattr(lib, name).restype = C.c_int
@@ -384,6 +386,13 @@ class Context:
         a, b = C.c_int(0), C.c_int(0)
         self._check(self.lib.gsvd_rand_basis_cols(self.h, C.byref(a), C.byref(b)))
         return a.value, b.value
+
+    def product_shapes(self):
+        """[(stages, ctas_per_sm)] x 3 (first sketch, power sketch, G^T Q) of the last solve whose
+        two-side products ran as grouped launches, as the built-in tuner picked them."""
+        t = (C.c_int * 6)()
+        self._check(self.lib.gsvd_rand_product_shapes(self.h, t))
+        return [(t[0], t[1]), (t[2], t[3]), (t[4], t[5])]
 
     def chol64_retries(self) -> int:
         """Solves (on this context and its batched workers) repeated with FP64 Cholesky

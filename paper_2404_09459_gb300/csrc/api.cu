@@ -49,6 +49,7 @@ struct gsvd_rand_ctx {
   unsigned char* tab_host = nullptr;    // pinned staging of the two-side product tables of a solve
   size_t tab_host_bytes = 0;
   int64_t chol64_retries = 0;  // solves repeated with FP64 Cholesky factors
+  int product_shapes[6] = {0, 0, 0, 0, 0, 0};  // tuned (stages, CTAs per SM) of the two-side products
   // learned proposal: network (params | norm), then features, logits and scratch of one pair
   float* mlp_dev = nullptr;
   bool mlp_ready = false;
@@ -255,6 +256,9 @@ struct Solver {
     // shape bucket (on this table; the launch below rewrites its outputs)
     int stages = 0, per_sm = 0, rc;
     if ((rc = tune_group(h, st, mode, prec, norm, ds, 2, ntiles, nmma, kmean, st_dev, &stages, &per_sm))) return rc;
+    const int kind = mode == 1 ? 2 : (norm ? 0 : 1);  // first sketch, power sketch, G^T Q
+    h->product_shapes[2 * kind] = stages;
+    h->product_shapes[2 * kind + 1] = per_sm;
     CU(tc_group_launch(mode, prec, norm, ds, 2, ntiles, nmma, stages, per_sm, st_dev, st));
     return GSVD_RAND_OK;
   }
@@ -2435,6 +2439,12 @@ int gsvd_rand_grouped_info(gsvd_rand_t h, int* tuned, int64_t* captures, int64_t
   if (captures) *captures = g ? g->captures : 0;
   if (replays) *replays = g ? g->replays : 0;
   if (launches) *launches = g ? (int64_t)g->launches_per_replay : 0;
+  return GSVD_RAND_OK;
+}
+
+int gsvd_rand_product_shapes(gsvd_rand_t h, int* shapes) {
+  if (!h || !shapes) return GSVD_RAND_ERR_ARG;
+  for (int i = 0; i < 6; ++i) shapes[i] = h->product_shapes[i];
   return GSVD_RAND_OK;
 }
 
