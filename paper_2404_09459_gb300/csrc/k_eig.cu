@@ -62,6 +62,42 @@ __device__ __forceinline__ float hash_unit(uint32_t a, uint32_t b) {
   return (float)(h >> 8) * 5.9604645e-08f - 0.5f;
 }
 
+// A replacement for set-aside vector j of eigenvalue lambda_j: one step of inverse iteration
+// on T - lambda_j I from a pseudo-random start (one thread).  T - lambda I = U D U^T with the
+// backward pivots dm (dm_{N-1} = d_{N-1} - lambda, dm_i = d_i - lambda - e_i^2 / dm_{i+1}),
+// U unit upper bidiagonal with U_{i,i+1} = e_i / dm_{i+1}: U y = b from the bottom, then
+// x_0 = y_0 / dm_0, x_{i+1} = (y_{i+1} - e_i x_i) / dm_{i+1}.  The result lies, to the gap
+// ratio, in T's eigenspace at lambda_j, so the vectors set aside from an exactly multiple
+// eigenvalue are replaced within their own eigenspace.  Values growing past 2^60 rescale the
+// whole vector (the same system with a scaled right-hand side).  A non-finite result falls
+// back to the pseudo-random start itself.  x has stride xs.
+__device__ void inverse_iteration_start(const float* __restrict__ e, const float* __restrict__ dm, int N,
+                                        uint32_t j, float* x, int64_t xs) {
+  x[(int64_t)(N - 1) * xs] = hash_unit(j, (uint32_t)(N - 1));
+  for (int i = N - 2; i >= 0; --i) {
+    float y = hash_unit(j, (uint32_t)i) - (e[i] / dm[i + 1]) * x[(int64_t)(i + 1) * xs];
+    if (fabsf(y) > 1.15e18f) {
+      for (int u = i + 1; u < N; ++u) x[(int64_t)u * xs] *= 8.67e-19f;
+      y *= 8.67e-19f;
+    }
+    x[(int64_t)i * xs] = y;
+  }
+  float xv = x[0] / dm[0];
+  x[0] = xv;
+  bool ok = isfinite(xv);
+  for (int i = 0; i + 1 < N; ++i) {
+    xv = (x[(int64_t)(i + 1) * xs] - e[i] * xv) / dm[i + 1];
+    if (fabsf(xv) > 1.15e18f) {
+      for (int u = 0; u < N; ++u) x[(int64_t)u * xs] *= 8.67e-19f;
+      xv *= 8.67e-19f;
+    }
+    x[(int64_t)(i + 1) * xs] = xv;
+    ok = ok && isfinite(xv);
+  }
+  if (!ok)
+    for (int i = 0; i < N; ++i) x[(int64_t)i * xs] = hash_unit(j, (uint32_t)i);
+}
+
 }  // namespace
 
 int64_t eig_big_scratch_floats(int N);
@@ -325,8 +361,10 @@ __global__ __launch_bounds__(1024) void eig_f32_kernel(const double* __restrict_
 //   3. within each cluster of eigenvalues (gap below 1e-3 of ||T||) the
 //      vectors are orthogonalised by classical Gram-Schmidt applied twice,
 //      column by column with the whole CTA; a column with less than 1e-3 of
-//      its length left is set aside and replaced at the end by a pseudo-random
-//      vector orthogonalised against every accepted column;
+//      its length left is set aside and replaced at the end by one step of
+//      inverse iteration at its eigenvalue from a pseudo-random start (so it
+//      stays in that eigenspace even when several multiple eigenvalues lose
+//      vectors), orthogonalised against every accepted column;
 //   4. X = H_0 ... H_{N-3} Z, reflector by reflector, no block barriers.
 // ============================================================================
 namespace {
@@ -352,7 +390,7 @@ __device__ __forceinline__ void eig128_body(const double* __restrict__ Ain, int 
   __shared__ float2 s_de[E_NMAX];
   __shared__ float s_cf[E_NMAX], s_flag[E_NMAX];
   __shared__ int s_cstart[E_NMAX], s_prev[E_NMAX], s_np, s_npan;
-  __shared__ float s_scale, s_bound[2], s_nrm;
+  __shared__ float s_scale, s_bound[2], s_nrm, s_before;
   const int tid = threadIdx.x, w = tid >> 5, t = tid & 31;
   const int lda = N | 1;
   float* Vref = esm;                       // N x 128: reflector k in row k (zero up to row k)
@@ -597,7 +635,15 @@ __device__ __forceinline__ void eig128_body(const double* __restrict__ Ain, int 
       if (pass == 0 && cs == j) continue;  // first of its cluster (or a singleton)
       if (pass == 1) {
         if (s_flag[j] >= 0.f) continue;
-        for (int i = tid; i < N; i += 1024) Zs[(size_t)i * lda + j] = hash_unit((uint32_t)j, (uint32_t)i);
+        // U pivots of the twisted factorisation at lambda_j are still in row j of Us
+        if (tid == 0) inverse_iteration_start(s_e, Us + (size_t)j * lda, N, (uint32_t)j, Zs + j, lda);
+        __syncthreads();
+        if (w == 0) {  // the length before the projection
+          float s2 = 0.f;
+          for (int i = t; i < N; i += 32) s2 = fmaf(Zs[(size_t)i * lda + j], Zs[(size_t)i * lda + j], s2);
+          for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+          if (t == 0) s_before = s2;
+        }
         __syncthreads();
       }
       const int ce = pass == 0 ? j : N;
@@ -628,8 +674,8 @@ __device__ __forceinline__ void eig128_body(const double* __restrict__ Ain, int 
         float s2 = 0.f;
         for (int i = t; i < N; i += 32) s2 = fmaf(Zs[(size_t)i * lda + j], Zs[(size_t)i * lda + j], s2);
         for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-        // the column was unit length (pass 0) or ~N/12 (pass 1) before the projection
-        const float before = pass == 0 ? 1.f : (float)N / 12.f;
+        // the column was unit length (pass 0) or of length^2 s_before (pass 1) before the projection
+        const float before = pass == 0 ? 1.f : s_before;
         const bool dep = !(s2 > 1e-6f * before) || !(s2 > 0.f);
         if (t == 0) {
           s_nrm = dep && pass == 0 ? 0.f : rsqrtf(s2 > 0.f ? s2 : 1.f);
@@ -791,7 +837,7 @@ __device__ __forceinline__ void eig_big_body(const double* __restrict__ Ain, int
   __shared__ float s_cf[EB_NMAX], s_flag[EB_NMAX];
   __shared__ float2 s_de[EB_NMAX];
   __shared__ int s_cstart[EB_NMAX], s_prev[EB_NMAX], s_np, s_npan;
-  __shared__ float s_red[32], s_scale, s_bound[2], s_nrm;
+  __shared__ float s_red[32], s_scale, s_bound[2], s_nrm, s_before;
   const int tid = threadIdx.x, w = tid >> 5, t = tid & 31;
   const size_t NN = (size_t)N * N;
   float* ZT = gscr;        // N x N column-major: eigenvectors of T, then of A
@@ -1014,7 +1060,15 @@ __device__ __forceinline__ void eig_big_body(const double* __restrict__ Ain, int
       float* Zj = ZT + (size_t)j * N;
       if (pass == 1) {
         if (s_flag[j] >= 0.f) continue;
-        for (int i = tid; i < N; i += 1024) Zj[i] = hash_unit((uint32_t)j, (uint32_t)i);
+        // U pivots of the twisted factorisation at lambda_j are still in column j of UT
+        if (tid == 0) inverse_iteration_start(s_e, UT + (size_t)j * N, N, (uint32_t)j, Zj, 1);
+        __syncthreads();
+        if (w == 0) {  // the length before the projection
+          float s2 = 0.f;
+          for (int i = t; i < N; i += 32) s2 = fmaf(Zj[i], Zj[i], s2);
+          for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+          if (t == 0) s_before = s2;
+        }
         __syncthreads();
       }
       const int ce = pass == 0 ? j : N;
@@ -1046,7 +1100,7 @@ __device__ __forceinline__ void eig_big_body(const double* __restrict__ Ain, int
         float s2 = 0.f;
         for (int i = t; i < N; i += 32) s2 = fmaf(Zj[i], Zj[i], s2);
         for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-        const float before = pass == 0 ? 1.f : (float)N / 12.f;
+        const float before = pass == 0 ? 1.f : s_before;
         const bool dep = !(s2 > 1e-6f * before) || !(s2 > 0.f);
         if (t == 0) {
           s_nrm = dep && pass == 0 ? 0.f : rsqrtf(s2 > 0.f ? s2 : 1.f);

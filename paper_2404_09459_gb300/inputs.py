@@ -137,6 +137,33 @@ def planted_pair_torch(spec: PairSpec, device="cuda", dtype=None):
     return out[0], out[1], alpha, beta
 
 
+def full_gmp_pair(m: int, p: int, n: int, seed: int = 0, rank_frac: float = 0.6, dtype=np.float64):
+    """The paper's own synthetic pair (Section 4.1), real-valued: G1 = U diag(alpha) R and
+    G2 = V diag(beta) R with U (m x n), V (p x n) orthonormalised Gaussian, R (n x n) Gaussian
+    and rank(G1) = rank(G2) = round(rank_frac min(m, p, n)).  So n - rank(G2) pairs have
+    alpha = 1 (beta = 0), n - rank(G1) have alpha = 0 (beta = 1), and the rest take sorted
+    U(0, 1) values, with beta = sqrt(1 - alpha^2).  The stack [G1; G2] has full rank n: every
+    one of the n pairs is resolved (r = n), and each side needs a basis of its full rank.
+    Returns (G1, G2, alpha, beta), alpha descending."""
+    if m < n or p < n:
+        raise ValueError("the construction needs m >= n and p >= n")
+    rng = np.random.default_rng(np.random.SeedSequence([seed, m, p, n, 4101]))
+    r = int(round(rank_frac * min(m, p, n)))
+    n_one, n_zero = n - r, n - r
+    n_mid = n - n_one - n_zero
+    if n_mid < 0:
+        raise ValueError("rank_frac must be at least 0.5")
+    mid = np.sort(rng.uniform(0.0, 1.0, n_mid))[::-1]
+    alpha = np.concatenate([np.ones(n_one), mid, np.zeros(n_zero)])
+    beta = np.sqrt((1.0 - alpha) * (1.0 + alpha))
+    U = _haar_columns(rng, m, n)
+    V = _haar_columns(rng, p, n)
+    R = rng.standard_normal((n, n))
+    G1 = (U * alpha[None, :]) @ R
+    G2 = (V * beta[None, :]) @ R
+    return G1.astype(dtype), G2.astype(dtype), alpha, beta
+
+
 def uneven_batch(npairs: int = 256, seed: int = 0, m_range=(2000, 30000), n_range=(100, 1000),
                  r_range=(10, 100), oversample: int = 10, q: int = 1, sigma: float = 1e-9):
     """Specs of a batch of uneven pairs: m, p ~ U[m_range], n ~ U[n_range],

