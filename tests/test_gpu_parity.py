@@ -53,7 +53,9 @@ def _check(prec, G1, G2, spec, ref=None, **kw):
     dth = np.abs(np.arctan2(a, b) - np.arctan2(ref["alpha"], ref["beta"]))
     assert np.max(e) <= TOL[prec], (prec, np.max(e), e)
     assert np.max(dth) <= max(1e-4, TOL[prec])
-    assert np.all(np.diff(a) <= 0) and np.all(np.diff(b) >= 0)
+    # alpha non-increasing, beta non-decreasing; within exact ties (a multiple GSV) the pairs are
+    # values only and may swap at rounding level
+    assert np.all(np.diff(a) <= 1e-14) and np.all(np.diff(b) >= -1e-14)
     return a, b, out, ref
 
 
