@@ -54,8 +54,8 @@ def _check(prec, G1, G2, spec, ref=None, **kw):
     assert np.max(e) <= TOL[prec], (prec, np.max(e), e)
     assert np.max(dth) <= max(1e-4, TOL[prec])
     # alpha non-increasing, beta non-decreasing; within exact ties (a multiple GSV) the pairs are
-    # values only and may swap at rounding level
-    assert np.all(np.diff(a) <= 1e-14) and np.all(np.diff(b) >= -1e-14)
+    # values only, each within the mode's tolerance, so neighbours may swap by up to that much
+    assert np.all(np.diff(a) <= TOL[prec]) and np.all(np.diff(b) >= -TOL[prec])
     return a, b, out, ref
 
 
