@@ -743,6 +743,7 @@ int solve_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, const voi
   need += sb_sizer.off + 4096;
   // both sides' products as grouped launches: TF32 / 3xTF32 with l <= 128 (tensor memory)
   const bool g2 = use_tc && !bf16 && pl.l <= 128;
+  std::fill(h->product_shapes, h->product_shapes + 6, 0);  // set again by this solve's grouped products
   const int tab_slots = 2 * (q + 1);
   // a slot holds the larger of the two tables: G X (128-row tiles of both sides) and G^T Q
   // (at most 152 tiles per side, see gtq2)
