@@ -53,6 +53,21 @@ METRIC = "pairs/sec and sketch TFLOP/s at GSV rel-err <=1e-4, chosen form vs pla
 DTYPE = {"tf32": "tf32", "tf32x3": "tf32x3", "bf16": "bf16", "fp32": "f32", "fp64": "f64"}
 
 
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """The largest x over the ranks (a weak-scaling job takes as long as its slowest rank)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_seed(seed: int, rank: int) -> int:
+    """Seed of rank `rank`'s own pair (the ranks solve independent pairs)."""
+    return seed + 1000 * rank
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -283,11 +298,7 @@ def run_batched(args, rank, world):
         other = {"value": npairs / (time.perf_counter() - t0), "unit": "pairs/s",
                  "form": f"{args.workers} concurrent worker streams, per-pair launches",
                  "chol64_retries": ctx.chol64_retries() // 2}  # per call (two calls above)
-    sec = sum(times)
-    if dist is not None:
-        t = torch.tensor([sec], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        sec = float(t.item())
+    sec = max_over_ranks(sum(times), dist, f"cuda:{local}")
     value = world * npairs * args.steps / sec
     ms_step = 1e3 * sec / args.steps
     flops = sum(sketch_flops(s) for s in specs)
@@ -399,9 +410,7 @@ def run_learned(args, rank, world):
                      plans=[(max(1, min(learn.k_of_bucket(b), lm)), int(q)) for b, q, lm in zip(ykh, yqh, lmax)])
     value = learned["value"]
     if dist is not None:
-        t = torch.tensor([len(rows) / value], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        value = world * len(rows) / float(t.item())
+        value = world * len(rows) / max_over_ranks(len(rows) / value, dist, f"cuda:{local}")
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = oracle_learned_sample(ho)
@@ -490,7 +499,7 @@ def main():
     prec = args.prec or default_prec
     # each rank draws its own pair (independent units)
     from dataclasses import replace
-    rspec = replace(spec, seed=spec.seed + 1000 * rank)
+    rspec = replace(spec, seed=rank_seed(spec.seed, rank))
     dt = torch.float64 if prec == "fp64" else torch.float32
     G1, G2, _, _ = planted_pair_torch(rspec, device=f"cuda:{local}", dtype=dt)
     if prec == "bf16":
@@ -521,11 +530,7 @@ def main():
             evs[i][1].record(st)
         barrier()
     launches = (ctx.launch_count() - l0) // args.steps
-    ms = sum(a.elapsed_time(b) for a, b in evs)
-    if dist is not None:
-        t = torch.tensor([ms], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), dist, f"cuda:{local}")
     ms_step = ms / args.steps
     value = world * args.steps / (ms / 1e3)
     tflops = sketch_flops(spec) / (ms_step / 1e3) / 1e12
