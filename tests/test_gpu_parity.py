@@ -137,6 +137,28 @@ def test_tensor_core_ragged(prec, m, p, n, k, os_, q):
     _check(prec, G1, G2, spec)
 
 
+def test_single_solve_product_shapes_tuned_and_pinned_agree(monkeypatch):
+    # a single solve's two-side products are tuned like the grouped ones (pipeline depth, one or
+    # two CTAs per SM); every shape runs each tile's MMAs in the same order: the same bits
+    spec = PairSpec(m=4000, p=3000, n=400, r=30, alpha="uniform", decay="exp10", sigma=1e-6, k=30,
+                    oversample=10, q=1, seed=21)
+    G1, G2, _, _ = planted_pair(spec)
+    res = {}
+    for shape in (None, "2,2", "4,1"):
+        if shape:
+            monkeypatch.setenv("GSVD_RAND_GROUP_PIPELINE", shape)
+        with P.Context("tf32x3") as ctx:
+            out = ctx.solve(_dev(G1, "tf32x3"), _dev(G2, "tf32x3"), 30, 10, 1, 21)
+            shapes = ctx.product_shapes()
+        if shape:
+            assert all(sh == tuple(int(x) for x in shape.split(",")) for sh in shapes), shapes
+        else:
+            assert all(sh[0] >= 2 and sh[1] in (1, 2) for sh in shapes), shapes
+        res[shape] = out["alpha"].cpu().numpy()
+    np.testing.assert_array_equal(res[None], res["2,2"])
+    np.testing.assert_array_equal(res[None], res["4,1"])
+
+
 def test_tf32x3_unaligned_rows_use_cuda_cores():
     # n = 97: a row stride TMA cannot address; device inputs then run the FP32 CUDA-core products
     spec = PairSpec(m=500, p=400, n=97, r=12, sigma=1e-6, k=12, oversample=6, q=1, seed=4)
