@@ -223,6 +223,21 @@ int gsvd_rand_solve_grouped(gsvd_rand_t h, int npairs, gsvd_rand_pair *pairs);
  * replays so far and the kernel launches per replay.  Any pointer may be NULL. */
 int gsvd_rand_grouped_info(gsvd_rand_t h, int *tuned, int64_t *captures, int64_t *replays, int64_t *launches);
 
+/* The GSVD factors of the last fixed-rank gsvd_rand_solve on h (not basis-only), as the
+ * recovery that follows Algorithm 2 in Section 2 gives them, in the rank-revealing reading:
+ * with S = [Q1^T G1; Q2^T G2] = Zr Sigma Wr^T truncated to r = k and W the eigenvectors of
+ * Z1^T Z1 (Z1, Z2 the two blocks of Zr),
+ *     U = Q1 Z1 W diag(1 / ||Z1 w_i||)   (m x r),    V = Q2 Z2 W diag(1 / ||Z2 w_i||)   (p x r),
+ *     R = diag(||Zr w_i||) W^T Zr^T S   (r x n),
+ * so that G1 ~ U diag(alpha) R and G2 ~ V diag(beta) R with the solve's alpha, beta (column and
+ * row i pair with alpha_i, beta_i; U and V have orthonormal columns where alpha, beta > 0; a
+ * column whose alpha (beta) is zero is zero).  The product U diag(alpha) R does not depend on
+ * the rotations of the bases.  U, V, R: device FP64 row-major with ldu, ldv >= r and ldr >= n;
+ * any may be NULL.  The factors are taken from the solve's workspace: any later call on h that
+ * uses it (a solve, gsvd_rand_metrics, ...) makes them unavailable.  Synchronises cfg->stream.
+ * Errors: ARG (NULL handle, no such solve, host pointers or short leading dimensions), CUDA. */
+int gsvd_rand_factors(gsvd_rand_t h, double *U, int64_t ldu, double *V, int64_t ldv, double *R, int64_t ldr);
+
 /* The pipeline shapes of the last gsvd_rand_solve on h whose products of both sides ran as
  * grouped tensor-core launches (fixed rank, TF32 / TF32X3, k + oversample <= 128):
  * shapes[6] = (stages, CTAs per SM) of the first sketch, the power-step sketch and the

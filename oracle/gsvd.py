@@ -163,6 +163,31 @@ def rand_gsvd(G1, G2, k: int, oversample: int, q: int, seed: int, pair: int = 0,
     return out
 
 
+def rand_gsvd_factors(G1, G2, k: int, oversample: int, q: int, seed: int, pair: int = 0):
+    """The GSVD factors of the randomized method (the recovery that follows Algorithm 2 in
+    Section 2, in the rank-revealing reading): with S = [B1; B2] = Zr Sigma_r Wr^T (thin SVD
+    truncated to r = k) and the SVD Z1 = U1 C Vh of its first block, U = Q1 U1, R = Vh Zr^T S
+    and V = Q2 Z2 Vh^T diag(1 / beta), so that G1 ~ U diag(alpha) R and G2 ~ V diag(beta) R
+    (G_s ~ Q_s B_s).  A column whose alpha (beta) is zero is left zero in U (V).  Columns and
+    rows are ordered by alpha non-increasing.  Returns dict(U, V, R, alpha, beta)."""
+    out = rand_gsvd(G1, G2, k, oversample, q, seed, pair)
+    Q1, Q2, B1, B2 = out["Q1"], out["Q2"], out["B1"], out["B2"]
+    S = np.vstack([B1, B2])
+    l1 = B1.shape[0]
+    Z, _, _ = np.linalg.svd(S, full_matrices=False)
+    Zr = Z[:, :k]
+    _, _, Vh = np.linalg.svd(Zr[:l1], full_matrices=False)
+    ZW = Zr @ Vh.T                  # [Z1; Z2] W: column norms alpha_i, beta_i
+    a = np.linalg.norm(ZW[:l1], axis=0)
+    b = np.linalg.norm(ZW[l1:], axis=0)
+    order = np.argsort(-a, kind="stable")
+    ZW, a, b = ZW[:, order], a[order], b[order]
+    U = Q1 @ (ZW[:l1] / np.where(a > 0, a, np.inf))
+    V = Q2 @ (ZW[l1:] / np.where(b > 0, b, np.inf))
+    R = ZW.T @ S
+    return dict(U=U, V=V, R=R, alpha=a, beta=b)
+
+
 def adaptive_basis(G, tol: float, b: int, seed: int, pair: int = 0, side: int = 0,
                    max_cols: int | None = None):
     """Algorithm 1 (BasisExt), blocked adaptive range finder.

@@ -27,7 +27,7 @@ EXPORTS = ("gsvd_rand_config_init", "gsvd_rand_create", "gsvd_rand_destroy", "gs
            "gsvd_rand_probe_features", "gsvd_rand_mlp_forward", "gsvd_rand_mlp_loss_grad", "gsvd_rand_mlp_adam",
            "gsvd_rand_mlp_train", "gsvd_rand_mlp_set", "gsvd_rand_mlp_load", "gsvd_rand_last_plan",
            "gsvd_rand_solve_grouped", "gsvd_rand_grouped_info", "gsvd_rand_chol64_retries",
-           "gsvd_rand_product_shapes")
+           "gsvd_rand_product_shapes", "gsvd_rand_factors")
 NOALLOC_MAX_N = 32768
 FLAG_PROFILE = 2
 FLAG_BF16_SPLIT_POWER = 4
@@ -101,6 +101,7 @@ def load_library(path: str | None = None):
     lib.gsvd_rand_last_plan.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
     lib.gsvd_rand_chol64_retries.argtypes = [vp, C.POINTER(C.c_int64)]
     lib.gsvd_rand_product_shapes.argtypes = [vp, C.POINTER(C.c_int)]
+    lib.gsvd_rand_factors.argtypes = [vp, vp, i64, vp, i64, vp, i64]
     for name in EXPORTS:
         if name not in ("gsvd_rand_last_error", "gsvd_rand_launch_count"):
             getattr(lib, name).restype = C.c_int
@@ -229,7 +230,22 @@ class Context:
                                       C.addressof(r), C.addressof(resid))
         self._check(rc)
         rr = r.value
+        self._last_shape = (m, p, n1, rr)
         return dict(alpha=alpha[:rr], beta=beta[:rr], r=rr, resid=(resid[0], resid[1]))
+
+    def factors(self):
+        """GSVD factors of the last solve(): dict(U (m x r), V (p x r), R (r x n)), FP64 CUDA tensors,
+        with G1 ~ U diag(alpha) R and G2 ~ V diag(beta) R (gsvd_rand_factors)."""
+        import torch
+        m, p, n, r = getattr(self, "_last_shape", (0, 0, 0, 0))
+        dev = torch.device("cuda", self.device)
+        U = torch.empty((m, r), dtype=torch.float64, device=dev)
+        V = torch.empty((p, r), dtype=torch.float64, device=dev)
+        R = torch.empty((r, n), dtype=torch.float64, device=dev)
+        self._check(self.lib.gsvd_rand_factors(self.h, U.data_ptr() if U.numel() else None, max(r, 1),
+                                               V.data_ptr() if V.numel() else None, max(r, 1),
+                                               R.data_ptr() if R.numel() else None, max(n, 1)))
+        return dict(U=U, V=V, R=R)
 
     def solve_batched(self, pairs, workers: int = 8):
         """Many independent pairs at once.  pairs: sequence of dicts with G1, G2, k and optional

@@ -50,6 +50,19 @@ struct gsvd_rand_ctx {
   size_t tab_host_bytes = 0;
   int64_t chol64_retries = 0;  // solves repeated with FP64 Cholesky factors
   int product_shapes[6] = {0, 0, 0, 0, 0, 0};  // tuned (stages, CTAs per SM) of the two-side products
+  // where the last fixed-rank solve left its bases, compressed stack and CS factor in the
+  // workspace (for gsvd_rand_factors); cleared whenever the workspace is next taken
+  struct Fact {
+    bool valid = false;
+    int tsize = 0;                  // bytes per element of Q and S (4 or 8)
+    const void* Q[2] = {nullptr, nullptr};
+    int64_t rs[2] = {0, 0}, cs[2] = {0, 0}, M[2] = {0, 0};  // Q_s(i, j) = Q_s[i rs + j cs], M_s x l
+    const void* S = nullptr;        // [B1; B2], 2 l x n, row stride ldn
+    int64_t n = 0, ldn = 0;
+    int l = 0, r = 0;
+    const double* U1 = nullptr;     // [Z1; Z2] W, 2 l x r
+  } fact;
+  double* fact_scr = nullptr;  // device scratch of gsvd_rand_factors (4 x 512 doubles)
   // learned proposal: network (params | norm), then features, logits and scratch of one pair
   float* mlp_dev = nullptr;
   bool mlp_ready = false;
@@ -168,6 +181,7 @@ struct Bump {
 };
 
 int ensure_ws(gsvd_rand_ctx* h, size_t bytes) {
+  h->fact.valid = false;  // every user of the workspace overwrites it
   if (bytes <= h->ws_bytes) return GSVD_RAND_OK;
   if (h->ws) {
     cudaStreamSynchronize(h->stream);
@@ -830,6 +844,25 @@ int solve_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, const voi
                                              : (c == GSVD_RAND_ERR_NONFINITE ? ": non-finite values" : ""));
   }
   h->last_cols[0] = h->last_cols[1] = pl.l;
+  if (!basis_only) {
+    gsvd_rand_ctx::Fact& f = h->fact;
+    const SideBufs<T>* sbs[2] = {&sb0, &sb1};
+    for (int s = 0; s < 2; ++s) {
+      f.Q[s] = sbs[s]->Q;
+      f.M[s] = pl.M[s];
+      // tensor-core paths keep Q transposed (l x round_up(M, 4)), the others row-major (M x lp)
+      f.rs[s] = use_tc ? 1 : pl.lp;
+      f.cs[s] = use_tc ? round_up(pl.M[s], 4) : 1;
+    }
+    f.tsize = (int)sizeof(T);
+    f.S = S;
+    f.n = n;
+    f.ldn = pl.ldn;
+    f.l = (int)pl.l;
+    f.r = k;
+    f.U1 = small.U1;
+    f.valid = true;
+  }
   if (r_out) {
     const int r = basis_only ? 0 : k;
     if (is_device_ptr(r_out))
@@ -2257,7 +2290,7 @@ int gsvd_rand_create(gsvd_rand_t* out, const gsvd_rand_config* cfg) {
       cudaMallocHost(&h->res_host, 4 * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     if (h->st_host) cudaFreeHost(h->st_host);
-  if (h->tab_host) cudaFreeHost(h->tab_host);
+    if (h->res_host) cudaFreeHost(h->res_host);
     delete h;
     return GSVD_RAND_ERR_OOM;
   }
@@ -2288,8 +2321,10 @@ int gsvd_rand_destroy(gsvd_rand_t h) {
   for (auto e : h->evpool) cudaEventDestroy(e);
   if (h->ws) cudaFree(h->ws);
   if (h->mlp_dev) cudaFree(h->mlp_dev);
+  if (h->fact_scr) cudaFree(h->fact_scr);
   if (h->st_host) cudaFreeHost(h->st_host);
   if (h->res_host) cudaFreeHost(h->res_host);
+  if (h->tab_host) cudaFreeHost(h->tab_host);
   delete h;
   return GSVD_RAND_OK;
 }
@@ -2440,6 +2475,24 @@ int gsvd_rand_grouped_info(gsvd_rand_t h, int* tuned, int64_t* captures, int64_t
   if (captures) *captures = g ? g->captures : 0;
   if (replays) *replays = g ? g->replays : 0;
   if (launches) *launches = g ? (int64_t)g->launches_per_replay : 0;
+  return GSVD_RAND_OK;
+}
+
+int gsvd_rand_factors(gsvd_rand_t h, double* U, int64_t ldu, double* V, int64_t ldv, double* R, int64_t ldr) {
+  if (!h) return GSVD_RAND_ERR_ARG;
+  const gsvd_rand_ctx::Fact& f = h->fact;
+  if (!f.valid)
+    return fail(h, GSVD_RAND_ERR_ARG, "no fixed-rank solve on this context to take the factors from "
+                                      "(or its workspace was used since)");
+  if ((U && (ldu < f.r || !is_device_ptr(U))) || (V && (ldv < f.r || !is_device_ptr(V))) ||
+      (R && (ldr < f.n || !is_device_ptr(R))))
+    return fail(h, GSVD_RAND_ERR_ARG, "U, V and R must be device FP64 with ldu, ldv >= r = %d and ldr >= n = %lld",
+                f.r, (long long)f.n);
+  CU(cudaSetDevice(h->cfg.device));
+  if (!h->fact_scr) CU(cudaMalloc(&h->fact_scr, 4 * 512 * sizeof(double)));
+  CU(launch_gsvd_factors(f.tsize, f.Q[0], f.rs[0], f.cs[0], f.M[0], f.Q[1], f.rs[1], f.cs[1], f.M[1], f.l, f.r, f.U1,
+                         f.S, f.ldn, f.n, h->fact_scr, U, ldu, V, ldv, R, ldr, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
   return GSVD_RAND_OK;
 }
 

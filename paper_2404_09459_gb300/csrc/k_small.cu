@@ -643,6 +643,113 @@ cudaError_t launch_cs_norms(const double* U1, int l1, const double* U2, int l2, 
 }
 
 
+// ---------------------------------------------------------------------------
+// GSVD factors (the recovery that follows Algorithm 2): the column order and scales first,
+// with the same arithmetic and ranking as cs_norms_body, so that factor column c pairs with
+// alpha[c], beta[c] of the solve.
+// ---------------------------------------------------------------------------
+__global__ void factor_prep_kernel(const double* __restrict__ U1, int l, int r, double* __restrict__ scr) {
+  extern __shared__ double fsm[];
+  double* sa = fsm;       // alpha of column i
+  double* ua = fsm + r;   // 1 / ||Z1 w_i||
+  double* ub = ua + r;    // 1 / ||Z2 w_i||
+  double* un = ub + r;    // ||[Z1; Z2] w_i||
+  const double* U2 = U1 + (int64_t)l * r;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < r; i += nt) {
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < l; ++k) a = fma(U1[(int64_t)k * r + i], U1[(int64_t)k * r + i], a);
+    for (int k = 0; k < l; ++k) b = fma(U2[(int64_t)k * r + i], U2[(int64_t)k * r + i], b);
+    const double nn = sqrt(a + b);
+    sa[i] = nn > 0.0 ? sqrt(a) / nn : 0.0;
+    ua[i] = a > 0.0 ? 1.0 / sqrt(a) : 0.0;
+    ub[i] = b > 0.0 ? 1.0 / sqrt(b) : 0.0;
+    un[i] = nn;
+  }
+  __syncthreads();
+  // scr: perm (as doubles) | 1 / ||Z1 w|| | 1 / ||Z2 w|| | ||[Z1; Z2] w||, by rank
+  for (int i = tid; i < r; i += nt) {
+    const double ai = isnan(sa[i]) ? -1.0 : sa[i];
+    int rank = 0;
+    for (int j = 0; j < r; ++j) {
+      const double aj = isnan(sa[j]) ? -1.0 : sa[j];
+      rank += (aj > ai) || (aj == ai && j < i);
+    }
+    rank = min(max(rank, 0), r - 1);
+    scr[rank] = (double)i;
+    scr[r + rank] = ua[i];
+    scr[2 * r + rank] = ub[i];
+    scr[3 * r + rank] = un[i];
+  }
+}
+
+// out[i][c] = sc[c] sum_j Q(i, j) Uh[j][perm[c]]: a thread per row, a grid row per column
+template <typename T>
+__global__ void factor_side_kernel(const T* __restrict__ Q, int64_t rs, int64_t cs, int64_t M, int l,
+                                   const double* __restrict__ Uh, int r, const double* __restrict__ scr, int which,
+                                   double* __restrict__ out, int64_t ldo) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.y;
+  if (i >= M) return;
+  const int src = (int)scr[c];
+  const double sc = scr[(1 + which) * r + c];
+  double s = 0.0;
+  for (int j = 0; j < l; ++j) s = fma((double)Q[i * rs + (int64_t)j * cs], Uh[(int64_t)j * r + src], s);
+  out[i * ldo + c] = sc * s;
+}
+
+// R[c][j] = nn[c] sum_k U1[k][perm[c]] S[k][j]: a thread per column of S, a grid row per row of R
+template <typename T>
+__global__ void factor_r_kernel(const double* __restrict__ U1, int L, int r, const double* __restrict__ scr,
+                                const T* __restrict__ S, int64_t ldn, int64_t n, double* __restrict__ R, int64_t ldr) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.y;
+  if (j >= n) return;
+  const int src = (int)scr[c];
+  double s = 0.0;
+  for (int k = 0; k < L; ++k) s = fma(U1[(int64_t)k * r + src], (double)S[(int64_t)k * ldn + j], s);
+  R[(int64_t)c * ldr + j] = scr[3 * r + c] * s;
+}
+
+template <typename T>
+cudaError_t gsvd_factors_t(const T* Q1, int64_t rs1, int64_t cs1, int64_t M1, const T* Q2, int64_t rs2, int64_t cs2,
+                           int64_t M2, int l, int r, const double* U1, const T* S, int64_t ldn, int64_t n, double* scr,
+                           double* U, int64_t ldu, double* V, int64_t ldv, double* R, int64_t ldr, cudaStream_t st) {
+  if (r < 1 || r > 65535 || l < 1) return cudaErrorInvalidValue;
+  factor_prep_kernel<<<1, 256, (size_t)4 * r * sizeof(double), st>>>(U1, l, r, scr);
+  int nl = 1;
+  if (U) {
+    factor_side_kernel<T><<<dim3((unsigned)cdiv(M1, 128), (unsigned)r), 128, 0, st>>>(Q1, rs1, cs1, M1, l, U1, r,
+                                                                                      scr, 0, U, ldu);
+    ++nl;
+  }
+  if (V) {
+    factor_side_kernel<T><<<dim3((unsigned)cdiv(M2, 128), (unsigned)r), 128, 0, st>>>(
+        Q2, rs2, cs2, M2, l, U1 + (int64_t)l * r, r, scr, 1, V, ldv);
+    ++nl;
+  }
+  if (R) {
+    factor_r_kernel<T><<<dim3((unsigned)cdiv(n, 128), (unsigned)r), 128, 0, st>>>(U1, 2 * l, r, scr, S, ldn, n, R,
+                                                                                  ldr);
+    ++nl;
+  }
+  return launched(nl);
+}
+
+cudaError_t launch_gsvd_factors(int tsize, const void* Q1, int64_t rs1, int64_t cs1, int64_t M1, const void* Q2,
+                                int64_t rs2, int64_t cs2, int64_t M2, int l, int r, const double* U1,
+                                const void* S, int64_t ldn, int64_t n, double* scr, double* U, int64_t ldu,
+                                double* V, int64_t ldv, double* R, int64_t ldr, cudaStream_t st) {
+  if (tsize == 8)
+    return gsvd_factors_t<double>(static_cast<const double*>(Q1), rs1, cs1, M1, static_cast<const double*>(Q2), rs2,
+                                  cs2, M2, l, r, U1, static_cast<const double*>(S), ldn, n, scr, U, ldu, V, ldv, R,
+                                  ldr, st);
+  if (tsize == 4)
+    return gsvd_factors_t<float>(static_cast<const float*>(Q1), rs1, cs1, M1, static_cast<const float*>(Q2), rs2, cs2,
+                                 M2, l, r, U1, static_cast<const float*>(S), ldn, n, scr, U, ldu, V, ldv, R, ldr, st);
+  return cudaErrorInvalidValue;
+}
+
 // ============================================================================
 // Comparative quantities (Section 1): theta, rho, P1, P2, D1, D2.
 // ============================================================================

@@ -182,6 +182,18 @@ cudaError_t launch_metrics(const double* alpha, const double* beta, int r, int N
 cudaError_t launch_cs_norms(const double* U1, int l1, const double* U2, int l2, int r, double* alpha,
                             double* beta, cudaStream_t st);
 
+// GSVD factors of a solve (the recovery after Algorithm 2, rank-revealing reading): from
+// U1 = [Z1; Z2] W (2 l x r, FP64), the bases Q_s (M_s x l, Q_s(i, j) = Q_s[i rs_s + j cs_s],
+// element type float or double as tsize) and the stack S = [B1; B2] (2 l x n, row stride ldn,
+// same type): column c of U (V) is Q_1 Z1 w_i / ||Z1 w_i|| (Q_2 Z2 w_i / ||Z2 w_i||, zero for a
+// zero norm) and row c of R is ||[Z1; Z2] w_i|| w_i^T [Z1; Z2]^T S, where i is the column of
+// descending-alpha rank c (the order of launch_cs_norms).  scr: 4 r doubles of device scratch.
+// U (M_1 x r, ldu), V (M_2 x r, ldv), R (r x n, ldr): FP64 device, any of them may be null.
+cudaError_t launch_gsvd_factors(int tsize, const void* Q1, int64_t rs1, int64_t cs1, int64_t M1, const void* Q2,
+                                int64_t rs2, int64_t cs2, int64_t M2, int l, int r, const double* U1,
+                                const void* S, int64_t ldn, int64_t n, double* scr, double* U, int64_t ldu,
+                                double* V, int64_t ldv, double* R, int64_t ldr, cudaStream_t st);
+
 // Residual (cumulated form): resid[s] = sqrt(max(g2 - b2, 0) / g2).
 cudaError_t launch_residual(const double* gpart, int ng, const double* bpart, int nb, double* out,
                             cudaStream_t st);

@@ -137,6 +137,34 @@ def test_tensor_core_ragged(prec, m, p, n, k, os_, q):
     _check(prec, G1, G2, spec)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "tf32x3"])
+def test_gsvd_factors_match_oracle(prec):
+    # U, V, R of the recovery after Algorithm 2: the products U diag(alpha) R and V diag(beta) R
+    # do not depend on the bases' rotations, so they are compared with the oracle's element by
+    # element; U and V have orthonormal columns
+    spec = PairSpec(m=3000, p=2500, n=300, r=20, alpha="uniform", decay="exp10", sigma=1e-8, k=20,
+                    oversample=8, q=1, seed=41)
+    G1, G2, _, _ = planted_pair(spec)
+    ref = O.rand_gsvd_factors(G1, G2, 20, 8, 1, spec.seed)
+    with P.Context(prec) as ctx:
+        out = ctx.solve(_dev(G1, prec), _dev(G2, prec), 20, 8, 1, spec.seed)
+        f = ctx.factors()
+        U, V, R = (f[x].cpu().numpy() for x in "UVR")
+        a, b = out["alpha"].cpu().numpy(), out["beta"].cpu().numpy()
+        ctx.metrics(out["alpha"], out["beta"])  # takes the workspace: the factors are gone
+        with pytest.raises(P.GsvdRandError) as e:
+            ctx.factors()
+        assert e.value.name == "ARG"
+    assert U.shape == (3000, 20) and V.shape == (2500, 20) and R.shape == (20, 300)
+    tol = TOL[prec]
+    for F, s, Fr, sr, G in ((U, a, ref["U"], ref["alpha"], G1), (V, b, ref["V"], ref["beta"], G2)):
+        rec, rec_ref = (F * s) @ R, (Fr * sr) @ ref["R"]
+        assert np.linalg.norm(rec - rec_ref) <= tol * np.linalg.norm(G), np.linalg.norm(rec - rec_ref)
+        keep = s > 1e-3
+        otol = 1e-9 if prec == "fp64" else 1e-4  # the bases' orthonormality: FP64 or FP32 Q
+        assert np.max(np.abs(F[:, keep].T @ F[:, keep] - np.eye(keep.sum()))) <= otol
+
+
 def test_single_solve_product_shapes_tuned_and_pinned_agree(monkeypatch):
     # a single solve's two-side products are tuned like the grouped ones (pipeline depth, one or
     # two CTAs per SM); every shape runs each tile's MMAs in the same order: the same bits

@@ -12,7 +12,7 @@ from scipy import stats
 
 from oracle import gsvd as O
 from oracle.philox import gaussian, philox4x32_10, philox_words
-from paper_2404_09459_gb300.inputs import PairSpec, full_gmp_pair, planted_pair
+from paper_2404_09459_gb300.inputs import PairSpec, full_gmp_pair, planted_pair, planted_scale
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -182,6 +182,24 @@ def test_paper_full_pair_workload_recovers_planted():
         out = O.rand_gsvd(G1, G2, 40, 0, q, seed=7)
         assert np.max(O.gsv_error(a, b, out["alpha"], out["beta"])) < 1e-12
         assert out["resid1"] < 1e-13 and out["resid2"] < 1e-13
+
+
+def test_gsvd_factors_reconstruct_and_match_the_planted_R():
+    # the recovery after Algorithm 2 (Section 2): G1 = U diag(alpha) R, G2 = V diag(beta) R with
+    # orthonormal U, V.  On a planted noise-free pair G1 = U_r diag(alpha) D O_r the shared factor
+    # is R = D O_r up to row signs (the GSVs are distinct), so R R^T = D^2 with the planted scales
+    spec = PairSpec(m=200, p=150, n=60, r=10, alpha="uniform", decay="exp10", sigma=0.0, k=10,
+                    oversample=5, q=1, seed=4)
+    G1, G2, a, b = planted_pair(spec)
+    f = O.rand_gsvd_factors(G1, G2, 10, 5, 1, seed=3)
+    np.testing.assert_allclose(f["alpha"], a, atol=1e-12)
+    np.testing.assert_allclose(f["beta"], b, atol=1e-12)
+    assert np.linalg.norm(G1 - (f["U"] * f["alpha"]) @ f["R"]) <= 1e-12 * np.linalg.norm(G1)
+    assert np.linalg.norm(G2 - (f["V"] * f["beta"]) @ f["R"]) <= 1e-12 * np.linalg.norm(G2)
+    np.testing.assert_allclose(f["U"].T @ f["U"], np.eye(10), atol=1e-12)
+    np.testing.assert_allclose(f["V"].T @ f["V"], np.eye(10), atol=1e-12)
+    d = planted_scale(spec)
+    np.testing.assert_allclose(f["R"] @ f["R"].T, np.diag(d ** 2), atol=1e-12)
 
 
 def test_alg2_literal_matches_rank_revealing_reading():
