@@ -1,13 +1,13 @@
 """Benchmark of the randomized GSV solve on GB300.
 
-One step = one full solve of the workload pair (both basis extractions with q
-power iterations, the projections, the FP64 compressed-pair GSVD), inputs
+One step = one full solve of the workload (every pair's two basis extractions
+with q power iterations, the projections, the FP64 compressed-pair GSVD), inputs
 resident in HBM.  Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload tf32_large|fp64_small|bf16_stress|batched|learned] [--prec tf32|fp32|...]
+                  [--workload batched|tf32_large|fp64_small|bf16_stress|learned] [--prec tf32|fp32|...]
 
---workload batched: 256 uneven pairs (m, p ~ U[2000, 30000], n ~ U[100, 1000],
+--workload batched (the default): 256 uneven pairs (m, p ~ U[2000, 30000], n ~ U[100, 1000],
 k = rank ~ U[10, 100], oversample 10, q = 1) per step, solved by one
 gsvd_rand_solve_grouped call (every step one launch for all pairs, the launch
 sequence replayed from a CUDA graph); --batched-mode workers runs
@@ -173,19 +173,50 @@ def run_reference(args, rank, world):
     spec, prec = WORKLOADS[args.workload]
     if rank != 0:
         return
-    if spec is None:  # batched / learned: the oracle on a bounded sample of the pairs, per step
-        if args.workload == "learned":
-            from paper_2404_09459_gb300.inputs import learned_pairs
-            s = oracle_learned_sample(learned_pairs(args.holdout, seed=2), seconds=10.0)
-        else:
-            s = oracle_batch_sample(uneven_batch(args.pairs, seed=1), seconds=10.0, max_pairs=4)
+    if spec is None and args.workload == "learned":
+        from paper_2404_09459_gb300.inputs import learned_pairs
+        s = oracle_learned_sample(learned_pairs(args.holdout, seed=2), seconds=10.0)
         line = {"impl": "reference", "metric": METRIC, "value": s["value"], "unit": "pairs/s", "n_gpus": world,
                 "steps": 1, "warmup": 0, "ms_per_step": 1e3 / s["value"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": (f"batch of {args.pairs} uneven pairs" if args.workload == "batched" else
-                                        f"learned-proposal held-out pairs ({args.holdout})") + " (oracle on a sample)"},
+                "config": {"workload": f"learned-proposal held-out pairs ({args.holdout}) (oracle on a sample)"},
                 "cpu_baseline": s,
                 "e2e": {"value": s["value"], "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+    if spec is None:
+        # batched: each step is the oracle's solve of one pair of the same 256-pair batch (pairs taken
+        # in turn from the first few), so that --steps K --warmup W stays within minutes on host cores
+        from oracle import gsvd as O
+        specs = uneven_batch(args.pairs, seed=1)
+        distinct = min(len(specs), 6)
+        cache = {}
+
+        def one(i):
+            j = i % distinct
+            if j not in cache:
+                cache[j] = planted_pair(specs[j])[:2]
+            G1, G2 = cache[j]
+            s = specs[j]
+            t0 = time.perf_counter()
+            O.rand_gsvd(G1, G2, s.kk, s.oversample, s.q, s.seed, pair=j)
+            return time.perf_counter() - t0
+
+        for i in range(args.warmup):
+            one(i)
+        secs = sum(one(args.warmup + i) for i in range(args.steps))
+        v = args.steps / secs
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "pairs/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": f"batch of {args.pairs} uneven pairs: m, p ~ U[2000, 30000], n ~ U[100, 1000], "
+                                       "k = rank ~ U[10, 100], oversample 10, q 1; FP64 oracle, one pair per step "
+                                       f"(the first {distinct} pairs in turn)"},
+                "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": os.cpu_count(), "kind": "oracle",
+                                 "sample": f"{args.steps} oracle solves of pairs 0..{distinct - 1} of the batch "
+                                           f"(OpenBLAS, {os.cpu_count()} threads); input generation not timed"},
+                "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return
     from oracle import gsvd as O
@@ -224,12 +255,39 @@ def oracle_batch_sample(specs, seconds=20.0, max_pairs=16):
                       "input generation not timed"}
 
 
+def gsv_error_summary(pairs_out, refs):
+    """Per-GSV error e_i = max(|alpha_i - alpha_ref_i|, |beta_i - beta_ref_i|) and the angular-distance
+    error |theta_i - theta_ref_i| (theta = atan2(alpha, beta) - pi/4) over the compared pairs."""
+    es, ts = [], []
+    for (a, b), (ar, br) in zip(pairs_out, refs):
+        a, b, ar, br = (np.asarray(x, dtype=np.float64) for x in (a, b, ar, br))
+        es.append(np.maximum(np.abs(a - ar), np.abs(b - br)))
+        ts.append(np.abs(np.arctan2(a, b) - np.arctan2(ar, br)))
+    e, t = np.concatenate(es), np.concatenate(ts)
+    return {"max": float(e.max()), "median": float(np.median(e)), "theta_abs_max": float(t.max()),
+            "pairs": len(refs), "gsvs": int(e.size)}
+
+
+def tensor_peak(prec, pk):
+    """Tensor-core peak (TFLOP/s) for the products of `prec`: BF16 from MEASURED_PEAKS.json; TF32
+    from the committed cuBLAS measurement in profiles/ (else half the BF16 peak, the nominal ratio)."""
+    bf = pk.get("bf16_tflops", 1900.0)
+    if prec == "bf16":
+        return bf, "measured bf16_tflops (MEASURED_PEAKS.json)"
+    try:
+        rates = json.load(open(os.path.join(ROOT, "profiles", "measured_rates.json")))
+        return float(rates["tf32_tflops"]), "measured TF32 cuBLAS GEMM (profiles/measured_rates.json)"
+    except Exception:
+        return 0.5 * bf, "measured bf16_tflops x 0.5 (TF32 nominal ratio)"
+
+
 def run_batched(args, rank, world):
-    """--workload batched: one step = one batched solve of 256 uneven pairs."""
+    """--workload batched (the default): one step = one grouped solve of 256 uneven pairs."""
     import torch
     import paper_2404_09459_gb300 as P
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -240,19 +298,18 @@ def run_batched(args, rank, world):
     specs = uneven_batch(npairs, seed=1 + rank)
     dt = torch.float64 if prec == "fp64" else torch.float32
     # rows stored with a 16-byte-multiple stride, so that the tensor-core products read G in place
-    mats = [tuple(aligned_rows(G) for G in planted_pair_torch(s, device=f"cuda:{local}", dtype=dt)[:2])
-            for s in specs]
+    mats = [tuple(aligned_rows(G) for G in planted_pair_torch(s, device=dev, dtype=dt)[:2]) for s in specs]
     pairs = [dict(G1=G1, G2=G2, k=s.kk, oversample=s.oversample, q=s.q, seed=s.seed, pair=i)
              for i, (s, (G1, G2)) in enumerate(zip(specs, mats))]
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
     ctx = P.Context(prec, device=local)
     grouped = args.batched_mode == "grouped"
+    st = torch.cuda.current_stream()
 
-    def step():
+    def step(c=ctx, pl=pairs):
         if grouped:
-            ctx.solve_grouped(pairs)  # one launch per step for all pairs, replayed from a CUDA graph
-        else:
-            ctx.solve_batched(pairs, workers=args.workers)  # synchronous: returns after the worker streams
+            return c.solve_grouped(pl)  # one launch per step for all pairs, replayed from a CUDA graph
+        return c.solve_batched(pl, workers=args.workers)  # synchronous: returns after the worker streams
 
     for _ in range(args.warmup):
         step()
@@ -264,30 +321,81 @@ def run_batched(args, rank, world):
             dist.barrier()
         torch.cuda.synchronize()
 
-    times = []
+    # timed region: CUDA events on the stream the library orders its work after and before
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
     with ClockSampler(local) as clk:
         for i in range(args.steps):
-            flush.fill_(i & 0xFF)
-            barrier()
-            t0 = time.perf_counter()
-            step()
-            torch.cuda.synchronize()
-            times.append(time.perf_counter() - t0)
-    launches = (ctx.launch_count() - l0) // args.steps
+            flush.fill_(i & 0xFF)  # L2 flush between timed steps (outside the events)
+            evs[i][0].record(st)
+            outs = step()
+            evs[i][1].record(st)
+        barrier()
+    launches = (ctx.launch_count() - l0) // max(args.steps, 1)
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), dist, dev)
+    ms_step = ms / args.steps
+    value = world * npairs * args.steps / (ms / 1e3)
     info = ctx.grouped_info() if grouped else None
-    stages = None
+    flops = sum(sketch_flops(s) for s in specs)
+
+    # per-step device time of the replays by stage (CUDA events captured into the graph, on the
+    # stream the kernels run on), for the stage split and the roofline of the Y = G X products
+    stages, roof = None, None
+    pk = peaks()
     if grouped:
-        # per-step device time of one replay (CUDA events captured into the graph), by stage
         pctx = P.Context(prec, device=local, flags=P.FLAG_PROFILE)
         pctx.solve_grouped(pairs)
         pctx.profile(reset=True)
-        pctx.solve_grouped(pairs)
+        reps = max(1, min(args.steps, 5))
+        for i in range(reps):
+            flush.fill_(i & 0xFF)
+            pctx.solve_grouped(pairs)
         prof = pctx.profile()
         pctx.close()
-        tot = sum(v[0] for k, v in prof.items() if k != "small")
-        stages = {k: {"ms_per_step": v[0], "steps_per_solve": v[1], "share": v[0] / tot if tot else None}
-                  for k, v in prof.items() if k != "small" and v[1]}
-    # the other batched form on the same pairs, for comparison (grouped vs concurrent workers)
+        tot = sum(v[0] for k, v in prof.items() if k != "small")  # grouped steps carry the sub-stage tags
+        stages = {k: {"ms_per_step": v[0] / reps, "launches_per_step": v[1] / reps,
+                      "share": v[0] / tot if tot else None}
+                  for k, v in prof.items() if v[1] and k != "small"}
+        sk_ms, sk_calls = prof["sketch"]
+        if sk_calls:
+            # algorithmic bytes of the Y = G X launches of one solve: (1 + q) passes per side over G
+            # (FP32), X (FP32, once) and Y (FP32 written); a launch covers every side still iterating
+            passes = [(1 + s.q, M, s.n, s.l) for s in specs for M in (s.m, s.p)]
+            bytes_step = sum(c * (M * n + n * l + M * l) * 4 for c, M, n, l in passes)
+            flops_step = sum(c * 2.0 * M * n * l for c, M, n, l in passes)
+            calls_step = sk_calls / reps
+            launch_s = sk_ms / sk_calls / 1e3
+            achieved = bytes_step / calls_step / launch_s / 1e9
+            roof = {"kernel": "tc_group_kernel, Y = G X (all sides of the batch per launch)", "bound": "hbm",
+                    "achieved": achieved, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
+                    "frac": achieved / pk["hbm_gbs"], "traffic": sketch_traffic(prec, "batched"),
+                    "bytes_per_launch": bytes_step / calls_step, "launch_ms": launch_s * 1e3,
+                    "launches_per_step": calls_step,
+                    "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if not pk.get("fallback") else "fallback"}
+            tpk, src = tensor_peak(prec, pk)
+            tach = flops_step / calls_step / launch_s / 1e12
+            roof["tensor"] = {"achieved_tflops": tach, "peak_tflops": tpk, "frac": tach / tpk, "peak_source": src}
+
+    # accuracy of the timed step's results: per-GSV error against the FP64 oracle on a sample of the
+    # pairs (the oracle runs on host copies of the same FP32 matrices, same Philox streams)
+    gsv = None
+    sample = list(range(0, npairs, max(1, npairs // args.error_pairs)))[:args.error_pairs] if args.error_pairs else []
+    refs, got = [], []
+    if rank == 0 and sample:
+        from oracle import gsvd as O
+        for i in sample:
+            s = specs[i]
+            G1h = mats[i][0].double().cpu().numpy()
+            G2h = mats[i][1].double().cpu().numpy()
+            ref = O.rand_gsvd(G1h, G2h, s.kk, s.oversample, s.q, s.seed, pair=i)
+            refs.append((ref["alpha"], ref["beta"]))
+            got.append((outs[i]["alpha"].cpu().numpy(), outs[i]["beta"].cpu().numpy()))
+        gsv = gsv_error_summary(got, refs)
+        gsv.update({"tol": 1e-4 if prec != "tf32" else 1e-3, "against": "FP64 oracle, same FP32 inputs and Omega",
+                    "sample": f"pairs {sample[0]}..{sample[-1]} step {max(1, npairs // args.error_pairs)}"})
+        gsv["pass"] = gsv["max"] <= gsv["tol"] and gsv["theta_abs_max"] <= 1e-4
+
+    # the other batched form on the same pairs (grouped vs concurrent per-pair workers)
     other = None
     if grouped and args.steps > 0:
         ctx.solve_batched(pairs, workers=args.workers)
@@ -298,19 +406,72 @@ def run_batched(args, rank, world):
         other = {"value": npairs / (time.perf_counter() - t0), "unit": "pairs/s",
                  "form": f"{args.workers} concurrent worker streams, per-pair launches",
                  "chol64_retries": ctx.chol64_retries() // 2}  # per call (two calls above)
-    sec = max_over_ranks(sum(times), dist, f"cuda:{local}")
-    value = world * npairs * args.steps / sec
-    ms_step = 1e3 * sec / args.steps
-    flops = sum(sketch_flops(s) for s in specs)
+
+    # plain FP64 GPU path on the same pairs (FP64 copies; the concurrent worker-stream form)
+    fp64 = None
+    if not args.no_fp64 and prec != "fp64":
+        fpairs = [dict(d, G1=d["G1"].double(), G2=d["G2"].double()) for d in pairs]
+        fctx = P.Context("fp64", device=local)
+        fctx.solve_batched(fpairs[:args.workers], workers=args.workers)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        fouts = fctx.solve_batched(fpairs, workers=args.workers)
+        e1.record(st)
+        torch.cuda.synchronize()
+        fms = e0.elapsed_time(e1)
+        fctx.close()
+        fp64 = {"value": npairs / (fms / 1e3), "unit": "pairs/s", "ms_per_step": fms,
+                "form": f"plain FP64 path, {args.workers} concurrent worker streams",
+                "speedup_of_chosen_form": (value / world) / (npairs / (fms / 1e3))}
+        if refs:
+            fgot = [(fouts[i]["alpha"].cpu().numpy(), fouts[i]["beta"].cpu().numpy()) for i in sample]
+            fp64["gsv_error"] = gsv_error_summary(fgot, refs)
+        del fpairs, fouts
+        torch.cuda.empty_cache()
+
+    # end to end through the public API with host (pinned) buffers: every step copies the whole
+    # batch into HBM inside the call (gsvd_rand_solve_grouped stages host inputs) and returns
+    # alpha / beta in host memory
+    e2e = None
+    if not args.no_e2e:
+        hpairs = []
+        for d in pairs:
+            h1 = torch.empty((d["G1"].shape[0], d["G1"].shape[1]), dtype=dt, pin_memory=True)
+            h2 = torch.empty((d["G2"].shape[0], d["G2"].shape[1]), dtype=dt, pin_memory=True)
+            h1.copy_(d["G1"])
+            h2.copy_(d["G2"])
+            hpairs.append(dict(d, G1=h1, G2=h2))
+        ectx = P.Context(prec, device=local)
+        for _ in range(2):
+            step(ectx, hpairs)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step(ectx, hpairs)
+        barrier()
+        e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
+        ectx.close()
+        h2d = sum((d["G1"].shape[0] + d["G2"].shape[0]) * d["G1"].shape[1] for d in hpairs) * (8 if prec == "fp64" else 4)
+        d2h = sum(2 * d["k"] * 8 + 2 * 8 + 4 for d in hpairs)
+        e2e = {"value": world * npairs * args.steps / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h),
+               "form": "gsvd_rand_solve_grouped on pinned host inputs (copied inside the call), host outputs; "
+                       "host clock, device synchronised on both sides"}
+        del hpairs
+
     # the same batch one pair after another (one stream), for the batching gain
-    seq_ctx = P.Context(prec, device=local)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for s, (G1, G2) in zip(specs, mats):
-        seq_ctx.solve(G1, G2, s.kk, s.oversample, s.q, s.seed)
-    torch.cuda.synchronize()
-    seq_s = time.perf_counter() - t0
-    seq_ctx.close()
+    seq = None
+    if grouped and not args.no_sequential:
+        seq_ctx = P.Context(prec, device=local)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for s, (G1, G2) in zip(specs, mats):
+            seq_ctx.solve(G1, G2, s.kk, s.oversample, s.q, s.seed)
+        torch.cuda.synchronize()
+        seq_s = time.perf_counter() - t0
+        seq_ctx.close()
+        seq = {"value": npairs / seq_s, "unit": "pairs/s", "batching_speedup": value / world / (npairs / seq_s)}
     cpu = oracle_batch_sample(specs) if rank == 0 and not args.no_cpu_baseline else None
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
@@ -322,13 +483,12 @@ def run_batched(args, rank, world):
                                           "products, batched CholeskyQR and compressed-pair kernels), replayed from "
                                           "a captured CUDA graph" if grouped else
                                           f"{args.workers} concurrent worker streams"),
-                           "l2": "flushed between timed steps (256 MiB write)",
-                           "timing": "host clock around the synchronous batched call, device synchronised on both sides",
+                           "l2": "flushed between timed steps (256 MiB write); the batch's G (17.6 GB) exceeds L2",
+                           "timing": "CUDA events on the library's stream around each grouped call",
                            "parallelism": f"independent batches, {world} rank(s)"},
-                "sketch_tflops": flops / (ms_step / 1e3) / 1e12,
-                "sequential": {"value": npairs / seq_s, "unit": "pairs/s",
-                               "batching_speedup": value / world / (npairs / seq_s)},
-                "cpu_baseline": cpu, "gpu_launches": int(launches), "clocks": clk.summary()}
+                "sketch_tflops": flops / (ms_step / 1e3) / 1e12, "roofline": roof, "gsv_error": gsv,
+                "fp64_plain": fp64, "e2e": e2e, "sequential": seq, "cpu_baseline": cpu,
+                "gpu_launches": int(launches), "clocks": clk.summary()}
         if info is not None:
             line["grouped"] = {"tuned_stages_ctas_per_sm": {"first_sketch": info["tuned"][0],
                                                             "power_sketch": info["tuned"][1],
@@ -455,16 +615,53 @@ def oracle_learned_sample(specs, seconds=20.0, max_pairs=4):
             "sample": f"{done} held-out pairs solved by the oracle's Algorithm 1 (b = 16, tol 1e-4)"}
 
 
+def measure_rates(device=0):
+    """Dense GEMM rates of this GPU through cuBLAS (torch.matmul): TF32, FP32 and FP64, best of 10
+    with CUDA events after warm-up (2 N^3 flops each).  The denominators of the TF32 tensor
+    fraction and of the FP64 stages; printed as one JSON line."""
+    import torch
+    dev = torch.device("cuda", device)
+    out = {}
+    for name, dt, n, tf32 in (("tf32", torch.float32, 8192, True), ("fp32", torch.float32, 8192, False),
+                              ("fp64", torch.float64, 4096, False)):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn(n, n, device=dev, dtype=dt)
+        b = torch.randn(n, n, device=dev, dtype=dt)
+        for _ in range(3):
+            torch.matmul(a, b)
+        best = None
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1e3
+            best = t if best is None else min(best, t)
+        out[f"{name}_tflops"] = 2.0 * n ** 3 / best / 1e12
+        out[f"{name}_n"] = n
+    torch.backends.cuda.matmul.allow_tf32 = False
+    out["gpu_name"] = torch.cuda.get_device_name(dev)
+    out["torch"] = torch.__version__
+    out["how"] = "torch.matmul (cuBLAS) on N x N random operands, best of 10 with CUDA events after 3 warm-up calls"
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="tf32_large", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="batched", choices=sorted(WORKLOADS))
     ap.add_argument("--prec", default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison leg")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg with host buffers")
+    ap.add_argument("--no-error", action="store_true", help="single pair: skip the GSV error against the oracle")
+    ap.add_argument("--no-sequential", action="store_true", help="batched: skip the one-pair-at-a-time leg")
+    ap.add_argument("--error-pairs", type=int, default=8,
+                    help="batched: pairs whose GSVs are checked against the FP64 oracle (0: none)")
     ap.add_argument("--pairs", type=int, default=256, help="batched workload: pairs per step")
     ap.add_argument("--workers", type=int, default=16, help="batched workload: concurrent worker streams")
     ap.add_argument("--batched-mode", default="grouped", choices=["grouped", "workers"],
@@ -472,8 +669,12 @@ def main():
     ap.add_argument("--train", type=int, default=1024, help="learned workload: training pairs")
     ap.add_argument("--holdout", type=int, default=128, help="learned workload: held-out pairs")
     ap.add_argument("--epochs", type=int, default=60, help="learned workload: training epochs")
+    ap.add_argument("--measure-rates", action="store_true",
+                    help="print the cuBLAS TF32 / FP32 / FP64 GEMM rates of this GPU and exit")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.measure_rates:
+        return measure_rates(int(os.environ.get("LOCAL_RANK", "0")))
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -501,7 +702,8 @@ def main():
     from dataclasses import replace
     rspec = replace(spec, seed=rank_seed(spec.seed, rank))
     dt = torch.float64 if prec == "fp64" else torch.float32
-    G1, G2, _, _ = planted_pair_torch(rspec, device=f"cuda:{local}", dtype=dt)
+    G1, G2, a_true, b_true = planted_pair_torch(rspec, device=f"cuda:{local}", dtype=dt)
+    G1u, G2u = G1, G2  # before BF16 storage rounding
     if prec == "bf16":
         dt = torch.bfloat16
         G1, G2 = G1.to(dt), G2.to(dt)
@@ -526,7 +728,7 @@ def main():
         for i in range(args.steps):
             flush.fill_(i & 0xFF)  # L2 flush between timed steps (outside the events)
             evs[i][0].record(st)
-            ctx.solve(G1, G2, spec.kk, spec.oversample, spec.q, rspec.seed)
+            out = ctx.solve(G1, G2, spec.kk, spec.oversample, spec.q, rspec.seed)
             evs[i][1].record(st)
         barrier()
     launches = (ctx.launch_count() - l0) // args.steps
@@ -570,10 +772,9 @@ def main():
     if prec in ("bf16", "tf32", "tf32x3") and sk_calls:
         # the same launches against the tensor peak: BF16 measured; TF32 at half of it (nominal ratio)
         flops_per_launch = (1 + spec.q) * sum(2.0 * M * spec.n * spec.l for M in (spec.m, spec.p)) / calls_step
-        tpk = pk.get("bf16_tflops", 1900.0) * (1.0 if prec == "bf16" else 0.5)
+        tpk, src = tensor_peak(prec, pk)
         roof["tensor"] = {"achieved_tflops": flops_per_launch / launch_s / 1e12, "peak_tflops": tpk,
-                          "frac": flops_per_launch / launch_s / 1e12 / tpk,
-                          "peak_source": "measured bf16_tflops" + ("" if prec == "bf16" else " x 0.5 (TF32 nominal)")}
+                          "frac": flops_per_launch / launch_s / 1e12 / tpk, "peak_source": src}
 
     # end to end through the public API with host (pinned) buffers
     h1 = torch.empty(G1.shape, dtype=dt, pin_memory=True)
@@ -613,6 +814,30 @@ def main():
         del g1d, g2d
         fp64 = {"value": 1e3 / fms, "unit": "pairs/s", "ms_per_step": fms, "speedup_of_chosen_form": (1e3 / ms_step) / (1e3 / fms)}
 
+    # accuracy of the timed solve's result against the FP64 oracle on the same stored input (same
+    # Philox Omega; BF16: Omega rounded as the BF16 mode rounds it); in BF16 also against the oracle
+    # on the unrounded pair (the error of BF16 storage itself) and against the planted pairs
+    gsv = None
+    if rank == 0 and not args.no_error:
+        from oracle import gsvd as O
+        got = [(out["alpha"].cpu().numpy(), out["beta"].cpu().numpy())]
+        h1, h2 = G1.double().cpu().numpy(), G2.double().cpu().numpy()
+        ref = O.rand_gsvd(h1, h2, spec.kk, spec.oversample, spec.q, rspec.seed,
+                          omega_round="bf16" if prec == "bf16" else None)
+        del h1, h2
+        gsv = gsv_error_summary(got, [(ref["alpha"], ref["beta"])])
+        tol = 1e-10 if prec == "fp64" else (1e-3 if prec == "tf32" else 1e-4)
+        gsv.update({"tol": tol, "against": "FP64 oracle, same stored input and Omega"})
+        if prec == "bf16":
+            u1, u2 = G1u.double().cpu().numpy(), G2u.double().cpu().numpy()
+            refu = O.rand_gsvd(u1, u2, spec.kk, spec.oversample, spec.q, rspec.seed)
+            del u1, u2
+            gsv["storage_error_vs_unrounded_fp64"] = gsv_error_summary(got, [(refu["alpha"], refu["beta"])])
+            gsv["oracle_unrounded_vs_rounded"] = gsv_error_summary([(ref["alpha"], ref["beta"])],
+                                                                   [(refu["alpha"], refu["beta"])])
+        gsv["vs_planted"] = gsv_error_summary(got, [(np.asarray(a_true), np.asarray(b_true))])
+        gsv["pass"] = gsv["max"] <= tol and gsv["theta_abs_max"] <= 1e-4
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(spec)
@@ -623,7 +848,7 @@ def main():
                 "vs_baseline": None, "dtype": DTYPE.get(prec, prec), "data": "synthetic",
                 "config": {"workload": workload_desc(spec, prec), "l2": "flushed between timed steps (256 MiB write)",
                            "parallelism": f"independent pairs, {world} rank(s)"},
-                "sketch_tflops": tflops, "roofline": roof, "stages": stages, "fp64_plain": fp64,
+                "sketch_tflops": tflops, "roofline": roof, "stages": stages, "gsv_error": gsv, "fp64_plain": fp64,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary()}
         shapes = ctx.product_shapes()
         if any(s for sh in shapes for s in sh):

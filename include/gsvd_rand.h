@@ -122,7 +122,8 @@ typedef struct {
 #define GSVD_RAND_STAGE_SMALL_JACOBI 5 /* ... the FP32 Jacobi eigensolve of K */
 #define GSVD_RAND_STAGE_SMALL_REFINE 6 /* ... the FP64 eigenvector refinement of K */
 #define GSVD_RAND_STAGE_SMALL_CS 7     /* ... the CS step (C1, C2 and their eigensolve) */
-#define GSVD_RAND_NUM_STAGES 8
+#define GSVD_RAND_STAGE_SETUP 8        /* grouped solves: status resets and the Gaussian test matrices */
+#define GSVD_RAND_NUM_STAGES 9
 
 /* Fill *cfg with defaults: device 0, default stream, TF32, fixed rank, b = 100, tol = 1e-4. */
 int gsvd_rand_config_init(gsvd_rand_config *cfg);
@@ -206,8 +207,11 @@ int gsvd_rand_solve_batched(gsvd_rand_t h, int npairs, gsvd_rand_pair *pairs, in
  * the first call of a new batch builds the plan, uploads the tables, tunes and
  * captures (it costs several solves).  Results go to each pair's alpha / beta
  * (device or host; resid_out and r_out as in gsvd_rand_solve).  Per pair:
- * l = k + oversample <= min(m, p, n) and <= 128, q <= 16, G1 and G2 device FP32 with
- * 16-byte aligned rows; pairs may differ in every size and in q.  A pair that breaks
+ * l = k + oversample <= min(m, p, n) and <= 128, q <= 16, G1 and G2 FP32: device matrices
+ * with 16-byte aligned rows are read in place; host matrices (any ld >= n) are copied on
+ * cfg->stream, every call, into device memory owned by h (rows padded to 16 bytes, kept
+ * for later calls, freed by gsvd_rand_destroy) and solved from there; pairs may differ in
+ * every size and in q.  A pair that breaks
  * these rules gets status ARG and is left out; the others are solved.  The grouped
  * path chunks its Gram sums differently from gsvd_rand_solve, so results agree with it
  * to rounding (not bit for bit); repeated calls are bit-identical.  The plan, tables
@@ -235,7 +239,8 @@ int gsvd_rand_grouped_info(gsvd_rand_t h, int *tuned, int64_t *captures, int64_t
  * the rotations of the bases.  U, V, R: device FP64 row-major with ldu, ldv >= r and ldr >= n;
  * any may be NULL.  The factors are taken from the solve's workspace: any later call on h that
  * uses it (a solve, gsvd_rand_metrics, ...) makes them unavailable.  Synchronises cfg->stream.
- * Errors: ARG (NULL handle, no such solve, host pointers or short leading dimensions), CUDA. */
+ * Errors: ARG (NULL handle, no such solve, host pointers, memory of another GPU or short leading
+ * dimensions), CUDA. */
 int gsvd_rand_factors(gsvd_rand_t h, double *U, int64_t ldu, double *V, int64_t ldv, double *R, int64_t ldr);
 
 /* The pipeline shapes of the last gsvd_rand_solve on h whose products of both sides ran as
@@ -277,9 +282,10 @@ int gsvd_rand_metrics(gsvd_rand_t h, const double *alpha, const double *beta, in
  *     that scratch.  Its block counter is cleared on the stream at each call.
  *   - N = max(r, pad_to_n) <= GSVD_RAND_NOALLOC_MAX_N, else
  *     GSVD_RAND_ERR_TOO_LARGE and nothing is enqueued.
- *   - The first call on each device looks up the scratch address there (and so
- *     loads the library's device code on that device); make that first call
- *     before any stream capture.
+ *   - Every call looks up the scratch address on `device` (cudaGetSymbolAddress,
+ *     which allocates nothing), so the entry point stays valid after the
+ *     device's context is reset; the first call on a device also loads the
+ *     library's device code there: make that first call before any stream capture.
  *   - All calls on one device share the one scratch array: calls that overlap
  *     in time (from several host threads, or on several streams) race and can
  *     return wrong results.  Each call synchronises `stream` before it returns.

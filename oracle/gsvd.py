@@ -163,14 +163,16 @@ def rand_gsvd(G1, G2, k: int, oversample: int, q: int, seed: int, pair: int = 0,
     return out
 
 
-def rand_gsvd_factors(G1, G2, k: int, oversample: int, q: int, seed: int, pair: int = 0):
+def rand_gsvd_factors(G1, G2, k: int, oversample: int, q: int, seed: int, pair: int = 0,
+                      omega_round: str | None = None):
     """The GSVD factors of the randomized method (the recovery that follows Algorithm 2 in
     Section 2, in the rank-revealing reading): with S = [B1; B2] = Zr Sigma_r Wr^T (thin SVD
     truncated to r = k) and the SVD Z1 = U1 C Vh of its first block, U = Q1 U1, R = Vh Zr^T S
     and V = Q2 Z2 Vh^T diag(1 / beta), so that G1 ~ U diag(alpha) R and G2 ~ V diag(beta) R
     (G_s ~ Q_s B_s).  A column whose alpha (beta) is zero is left zero in U (V).  Columns and
-    rows are ordered by alpha non-increasing.  Returns dict(U, V, R, alpha, beta)."""
-    out = rand_gsvd(G1, G2, k, oversample, q, seed, pair)
+    rows are ordered by alpha non-increasing.  omega_round as in basis_fixed.
+    Returns dict(U, V, R, alpha, beta)."""
+    out = rand_gsvd(G1, G2, k, oversample, q, seed, pair, omega_round)
     Q1, Q2, B1, B2 = out["Q1"], out["Q2"], out["B1"], out["B2"]
     S = np.vstack([B1, B2])
     l1 = B1.shape[0]

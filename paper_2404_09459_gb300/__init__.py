@@ -34,7 +34,7 @@ FLAG_BF16_SPLIT_POWER = 4
 FLAG_BASIS_ONLY = 8
 MLP_IN, MLP_HID, MLP_KCLS, MLP_QCLS, MLP_KBUCKET = 64, 128, 32, 5, 4
 MLP_PARAMS = 64 * 128 + 128 + 128 * 128 + 128 + 128 * 37 + 37
-STAGES = ("sketch", "gtq", "orth", "small", "small_gram", "small_jacobi", "small_refine", "small_cs")
+STAGES = ("sketch", "gtq", "orth", "small", "small_gram", "small_jacobi", "small_refine", "small_cs", "setup")
 
 
 class GsvdRandError(RuntimeError):

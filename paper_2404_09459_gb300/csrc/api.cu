@@ -63,6 +63,8 @@ struct gsvd_rand_ctx {
     const double* U1 = nullptr;     // [Z1; Z2] W, 2 l x r
   } fact;
   double* fact_scr = nullptr;  // device scratch of gsvd_rand_factors (4 x 512 doubles)
+  char* gstage = nullptr;      // device copies of a grouped solve's host inputs
+  size_t gstage_bytes = 0;
   // learned proposal: network (params | norm), then features, logits and scratch of one pair
   float* mlp_dev = nullptr;
   bool mlp_ready = false;
@@ -75,8 +77,8 @@ struct gsvd_rand_ctx {
   std::vector<cudaEvent_t> evpool;
   size_t evused = 0;
   std::vector<Rec> recs;
-  double prof_ms[8] = {};
-  int64_t prof_calls[8] = {};
+  double prof_ms[GSVD_RAND_NUM_STAGES] = {};
+  int64_t prof_calls[GSVD_RAND_NUM_STAGES] = {};
 };
 
 namespace gsvdr {
@@ -165,6 +167,17 @@ bool is_device_ptr(const void* p) {
     return false;
   }
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Device memory that lives on GPU `device` (managed memory counts as anywhere).
+bool is_device_ptr_on(const void* p, int device) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeManaged || (a.type == cudaMemoryTypeDevice && a.device == device);
 }
 
 // Bump allocator over the context workspace (256-byte aligned slices).
@@ -1603,7 +1616,7 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
   // ---- the launch sequence ----
   const int ns = 2 * np;
   Arena& A = gb.arena;
-  int cur_tag = GSVD_RAND_STAGE_SKETCH;
+  int cur_tag = GSVD_RAND_STAGE_SETUP;
   auto push = [&](std::function<cudaError_t(const unsigned char*, cudaStream_t)> f) {
     gb.ops.push_back(std::move(f));
     gb.tags.push_back(cur_tag);
@@ -2256,6 +2269,70 @@ int solve_grouped(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs) {
   return GSVD_RAND_OK;
 }
 
+// Host inputs of a grouped solve.  Each host matrix is copied, on h's stream ahead of the
+// grouped launch, into device memory owned by h with its rows padded to a 16-byte multiple
+// (the row stride the tensor-core products need); the grouped solve then runs on the copies.
+// The copies keep their addresses while the batch's shapes stay the same, so a repeated call
+// copies the inputs again and replays the captured graph.  Matrices whose shape arguments are
+// invalid are left as they are (the grouped solve gives their pair ARG).
+int solve_grouped_staged(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs) {
+  CU(cudaSetDevice(h->cfg.device));
+  const int prec = h->cfg.prec;
+  const bool f32 = prec == GSVD_RAND_TF32 || prec == GSVD_RAND_TF32X3;
+  std::vector<int> host(npairs, 0);  // bit 0: G1 on the host, bit 1: G2
+  size_t need = 0;
+  for (int i = 0; i < npairs; ++i) {
+    const gsvd_rand_pair& q = pairs[i];
+    if (!f32 || !(q.m >= 1 && q.p >= 1 && q.n >= 1 && q.ld1 >= q.n && q.ld2 >= q.n)) continue;
+    const size_t row = (size_t)round_up(q.n, 4) * sizeof(float);
+    if (q.G1 && !is_device_ptr(q.G1)) {
+      host[i] |= 1;
+      need += ((size_t)q.m * row + 255) & ~size_t(255);
+    }
+    if (q.G2 && !is_device_ptr(q.G2)) {
+      host[i] |= 2;
+      need += ((size_t)q.p * row + 255) & ~size_t(255);
+    }
+  }
+  if (need == 0) return solve_grouped(h, npairs, pairs);
+  if (need > h->gstage_bytes) {
+    // nothing of an earlier call is in flight: every grouped solve synchronises before it returns
+    if (h->gstage) cudaFree(h->gstage);
+    h->gstage = nullptr;
+    h->gstage_bytes = 0;
+    if (cudaMalloc(&h->gstage, need) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, GSVD_RAND_ERR_OOM, "staging of the grouped solve's host inputs (%zu bytes) failed", need);
+    }
+    h->gstage_bytes = need;
+  }
+  std::vector<gsvd_rand_pair> sp(pairs, pairs + npairs);
+  size_t off = 0;
+  for (int i = 0; i < npairs; ++i) {
+    gsvd_rand_pair& q = sp[i];
+    const int64_t ldn = round_up(q.n, 4);
+    for (int s = 0; s < 2; ++s) {
+      if (!(host[i] & (1 << s))) continue;
+      const void* src = s ? q.G2 : q.G1;
+      const int64_t M = s ? q.p : q.m, ld = s ? q.ld2 : q.ld1;
+      char* dst = h->gstage + off;
+      CU(copy_rows(dst, (size_t)ldn * sizeof(float), src, (size_t)ld * sizeof(float), (size_t)q.n * sizeof(float),
+                   (size_t)M, cudaMemcpyHostToDevice, h->stream));
+      if (s) {
+        q.G2 = dst;
+        q.ld2 = ldn;
+      } else {
+        q.G1 = dst;
+        q.ld1 = ldn;
+      }
+      off += ((size_t)M * ldn * sizeof(float) + 255) & ~size_t(255);
+    }
+  }
+  const int rc = solve_grouped(h, npairs, sp.data());
+  for (int i = 0; i < npairs; ++i) pairs[i].status = sp[i].status;
+  return rc;
+}
+
 }  // namespace
 
 extern "C" {
@@ -2325,6 +2402,7 @@ int gsvd_rand_destroy(gsvd_rand_t h) {
   if (h->st_host) cudaFreeHost(h->st_host);
   if (h->res_host) cudaFreeHost(h->res_host);
   if (h->tab_host) cudaFreeHost(h->tab_host);
+  if (h->gstage) cudaFree(h->gstage);
   delete h;
   return GSVD_RAND_OK;
 }
@@ -2340,7 +2418,7 @@ int gsvd_rand_profile_get(gsvd_rand_t h, int stage, double* total_ms, int64_t* c
 
 int gsvd_rand_profile_reset(gsvd_rand_t h) {
   if (!h) return GSVD_RAND_ERR_ARG;
-  for (int i = 0; i < 8; ++i) {
+  for (int i = 0; i < GSVD_RAND_NUM_STAGES; ++i) {
     h->prof_ms[i] = 0.0;
     h->prof_calls[i] = 0;
   }
@@ -2464,7 +2542,7 @@ int gsvd_rand_solve_batched(gsvd_rand_t h, int npairs, gsvd_rand_pair* pairs, in
 int gsvd_rand_solve_grouped(gsvd_rand_t h, int npairs, gsvd_rand_pair* pairs) {
   if (!h || npairs < 0 || (npairs > 0 && !pairs)) return GSVD_RAND_ERR_ARG;
   if (npairs == 0) return GSVD_RAND_OK;
-  return solve_grouped(h, npairs, pairs);
+  return solve_grouped_staged(h, npairs, pairs);
 }
 
 int gsvd_rand_grouped_info(gsvd_rand_t h, int* tuned, int64_t* captures, int64_t* replays, int64_t* launches) {
@@ -2484,10 +2562,12 @@ int gsvd_rand_factors(gsvd_rand_t h, double* U, int64_t ldu, double* V, int64_t 
   if (!f.valid)
     return fail(h, GSVD_RAND_ERR_ARG, "no fixed-rank solve on this context to take the factors from "
                                       "(or its workspace was used since)");
-  if ((U && (ldu < f.r || !is_device_ptr(U))) || (V && (ldv < f.r || !is_device_ptr(V))) ||
-      (R && (ldr < f.n || !is_device_ptr(R))))
-    return fail(h, GSVD_RAND_ERR_ARG, "U, V and R must be device FP64 with ldu, ldv >= r = %d and ldr >= n = %lld",
-                f.r, (long long)f.n);
+  const int dv = h->cfg.device;
+  if ((U && (ldu < f.r || !is_device_ptr_on(U, dv))) || (V && (ldv < f.r || !is_device_ptr_on(V, dv))) ||
+      (R && (ldr < f.n || !is_device_ptr_on(R, dv))))
+    return fail(h, GSVD_RAND_ERR_ARG,
+                "U, V and R must be FP64 memory on the context's device %d with ldu, ldv >= r = %d and "
+                "ldr >= n = %lld", dv, f.r, (long long)f.n);
   CU(cudaSetDevice(h->cfg.device));
   if (!h->fact_scr) CU(cudaMalloc(&h->fact_scr, 4 * 512 * sizeof(double)));
   CU(launch_gsvd_factors(f.tsize, f.Q[0], f.rs[0], f.cs[0], f.M[0], f.Q[1], f.rs[1], f.cs[1], f.M[1], f.l, f.r, f.U1,

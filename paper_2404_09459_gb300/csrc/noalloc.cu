@@ -37,8 +37,6 @@ static_assert(NA_VEC % 256 == 0 && NA_OFF_CNT % 256 == 0, "scratch regions must 
 // The scratch itself: about 1.5 MiB of static device memory per GPU.
 static __device__ __align__(256) unsigned char g_metrics_scratch[NA_BYTES];
 
-std::mutex g_na_mutex;
-void* g_na_base[NA_MAX_DEVICES] = {};
 
 // Pair i of the (padded) list: pad_mode 0 appends (0, 1), pad_mode 1 prepends (1, 0).
 __device__ __forceinline__ void padded_pair(const double* alpha, const double* beta, int r, int N, int pad_mode,
@@ -141,20 +139,20 @@ bool on_device(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-// Address of the scratch array on `device` (current): looked up once per
-// device with cudaGetSymbolAddress, which also loads the module there.
+// Address of the scratch array on `device` (current), looked up with
+// cudaGetSymbolAddress at every call: the lookup allocates nothing, and a fresh
+// lookup stays right after the device's context was torn down and recreated
+// (cudaDeviceReset), where the module can load at another address.  The first
+// lookup on a device also loads the module there.
 int scratch_base(int device, unsigned char** out) {
-  std::lock_guard<std::mutex> lock(g_na_mutex);
-  if (!g_na_base[device]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_metrics_scratch);
-    if (e != cudaSuccess || !p) {
-      cudaGetLastError();
-      return GSVD_RAND_ERR_CUDA;
-    }
-    g_na_base[device] = p;
+  (void)device;
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_metrics_scratch);
+  if (e != cudaSuccess || !p) {
+    cudaGetLastError();
+    return GSVD_RAND_ERR_CUDA;
   }
-  *out = static_cast<unsigned char*>(g_na_base[device]);
+  *out = static_cast<unsigned char*>(p);
   return GSVD_RAND_OK;
 }
 

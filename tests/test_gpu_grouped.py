@@ -213,3 +213,41 @@ def test_grouped_batch_laws_at_the_largest_ranks():
     with P.Context("tf32x3") as ctx:
         outs = ctx.solve_grouped(_pairs(specs, mats))
     _check_vs_oracle("tf32x3", specs, mats, outs)
+
+
+def test_grouped_dense_tail_across_the_cut():
+    # the single-solve dense-tail case (d_i = i^-1.5 at full rank, l = 96 .. 128, stacks of 192 .. 256
+    # rows whose eigenvalues around the cut lie below FP32 resolution) as one group
+    specs = [PairSpec(m=900, p=700, n=300, r=300, alpha="uniform", decay="pow15", sigma=0.0, k=l - 10,
+                      oversample=10, q=0, seed=5) for l in (96, 112, 128)]
+    mats = [tuple(G.astype(np.float32).astype(np.float64) for G in planted_pair(s)[:2]) for s in specs]
+    with P.Context("tf32x3") as ctx:
+        outs = ctx.solve_grouped(_pairs(specs, mats))
+    _check_vs_oracle("tf32x3", specs, mats, outs)
+
+
+def test_grouped_host_inputs_staged_and_replayed():
+    # host matrices (pinned and pageable, unpadded rows) are copied into the context's device memory
+    # inside each call; the group runs on those copies: the same bits as device inputs, and a second
+    # call with the same host matrices replays the captured graph
+    specs = _specs(18, 4)
+    mats = [planted_pair(s)[:2] for s in specs]
+    dev_pairs = _pairs(specs, mats)
+    host_pairs = []
+    for i, (d, (G1, G2)) in enumerate(zip(dev_pairs, mats)):
+        h1 = torch.from_numpy(np.ascontiguousarray(G1, dtype=np.float32))
+        h2 = torch.from_numpy(np.ascontiguousarray(G2, dtype=np.float32))
+        if i % 2 == 0:
+            h1, h2 = h1.pin_memory(), h2.pin_memory()
+        host_pairs.append(dict(d, G1=h1, G2=h2))
+    with P.Context("tf32x3") as ctx:
+        ref = ctx.solve_grouped(dev_pairs)
+    with P.Context("tf32x3") as ctx:
+        first = ctx.solve_grouped(host_pairs)
+        second = ctx.solve_grouped(host_pairs)
+        info = ctx.grouped_info()
+    assert info["captures"] == 1 and info["replays"] == 2
+    for r, a, b in zip(ref, first, second):
+        for key in ("alpha", "beta"):
+            np.testing.assert_array_equal(r[key].cpu().numpy(), np.asarray(a[key]))
+            np.testing.assert_array_equal(np.asarray(a[key]), np.asarray(b[key]))

@@ -137,17 +137,38 @@ def test_tensor_core_ragged(prec, m, p, n, k, os_, q):
     _check(prec, G1, G2, spec)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "tf32x3"])
-def test_gsvd_factors_match_oracle(prec):
+def _odd_ld(a):
+    """FP32 device matrix whose row stride (n + 1 floats) is not a multiple of 16 bytes: the
+    tensor-core products cannot read it through TMA, so the solve takes the CUDA-core products."""
+    t = torch.empty((a.shape[0], a.shape[1] + 1), dtype=torch.float32, device="cuda")
+    t[:, :a.shape[1]] = torch.from_numpy(np.ascontiguousarray(a)).to("cuda", torch.float32)
+    return t[:, :a.shape[1]]
+
+
+# every layout the solve records its bases in: FP64 row-major Q (fp64), FP32 row-major Q (fp32,
+# and tf32 on an unaligned input, which takes the CUDA-core products), FP32 transposed Q (tf32x3,
+# bf16 with BF16 storage of G)
+@pytest.mark.parametrize("prec,layout", [("fp64", "plain"), ("tf32x3", "plain"), ("fp32", "plain"),
+                                         ("tf32", "odd_ld"), ("bf16", "plain")])
+def test_gsvd_factors_match_oracle(prec, layout):
     # U, V, R of the recovery after Algorithm 2: the products U diag(alpha) R and V diag(beta) R
     # do not depend on the bases' rotations, so they are compared with the oracle's element by
     # element; U and V have orthonormal columns
     spec = PairSpec(m=3000, p=2500, n=300, r=20, alpha="uniform", decay="exp10", sigma=1e-8, k=20,
                     oversample=8, q=1, seed=41)
     G1, G2, _, _ = planted_pair(spec)
-    ref = O.rand_gsvd_factors(G1, G2, 20, 8, 1, spec.seed)
-    with P.Context(prec) as ctx:
-        out = ctx.solve(_dev(G1, prec), _dev(G2, prec), 20, 8, 1, spec.seed)
+    if prec == "bf16":
+        # parity on the BF16-rounded pair with the BF16-rounded Omega (the mode's own inputs)
+        G1, G2 = (O.round_bf16(G).astype(np.float64) for G in (G1, G2))
+        ref = O.rand_gsvd_factors(G1, G2, 20, 8, 1, spec.seed, omega_round="bf16")
+        g1, g2 = (torch.from_numpy(np.ascontiguousarray(G)).to("cuda", torch.float32).to(torch.bfloat16)
+                  for G in (G1, G2))
+    else:
+        ref = O.rand_gsvd_factors(G1, G2, 20, 8, 1, spec.seed)
+        g1, g2 = ((_odd_ld(G) if layout == "odd_ld" else _dev(G, prec)) for G in (G1, G2))
+    flags = P.FLAG_BF16_SPLIT_POWER if prec == "bf16" else 0
+    with P.Context(prec, flags=flags) as ctx:
+        out = ctx.solve(g1, g2, 20, 8, 1, spec.seed)
         f = ctx.factors()
         U, V, R = (f[x].cpu().numpy() for x in "UVR")
         a, b = out["alpha"].cpu().numpy(), out["beta"].cpu().numpy()
@@ -156,6 +177,7 @@ def test_gsvd_factors_match_oracle(prec):
             ctx.factors()
         assert e.value.name == "ARG"
     assert U.shape == (3000, 20) and V.shape == (2500, 20) and R.shape == (20, 300)
+    assert np.max(O.gsv_error(ref["alpha"], ref["beta"], a, b)) <= TOL[prec]
     tol = TOL[prec]
     for F, s, Fr, sr, G in ((U, a, ref["U"], ref["alpha"], G1), (V, b, ref["V"], ref["beta"], G2)):
         rec, rec_ref = (F * s) @ R, (Fr * sr) @ ref["R"]
@@ -301,21 +323,27 @@ def test_paper_full_pair_workload(prec, q):
     if prec != "fp64":  # the oracle takes the FP32-stored pair the GPU reads
         G1, G2 = G1.astype(np.float32).astype(np.float64), G2.astype(np.float32).astype(np.float64)
     spec = PairSpec(m=300, p=260, n=100, r=100, k=100, oversample=0, q=q, seed=11)
-    if prec == "fp64" and q == 1:
-        # a known limit of the FP64 path (the compressed-pair refinement with L = 200 > 128 after a
-        # power step on these exactly rank-deficient sketches): measured 1e-5 on the (0, 1) block and
-        # 2.5e-7 on the uniform block, above the 1e-10 target; q = 0, L <= 128 and rank 80% are exact
-        ref = O.rand_gsvd(G1, G2, 100, 0, q, spec.seed)
-        al, be, out = _solve(prec, G1, G2, spec)
-        e = O.gsv_error(ref["alpha"], ref["beta"], al, be)
-        assert np.max(e[:40]) <= 1e-10 and np.max(e) <= 2e-5, np.max(e)
-        return
     al, be, out, ref = _check(prec, G1, G2, spec)
     assert out["r"] == 100
     # the exact blocks: within the mode's tolerance of the planted 1s and 0s
     tol = 1e-10 if prec == "fp64" else 1e-4
     assert np.max(np.abs(al[:40] - 1.0)) <= tol and np.max(np.abs(be[:40])) <= tol
     assert np.max(np.abs(al[60:])) <= tol and np.max(np.abs(be[60:] - 1.0)) <= tol
+
+
+@pytest.mark.parametrize("l", [80, 96, 112, 128])
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
+def test_dense_tail_across_the_cut(prec, l):
+    # slow decay d_i = i^-1.5 at full rank: the k-th singular value of the stack is 1e-3 .. 8e-4 of
+    # the first, so the eigenvalues of K = S S^T around the cut (k-th and (k+1)-th) lie near 1e-6 of
+    # the largest, below what the FP32 eigensolver start resolves, and a dense run of them (the
+    # whole tail of K, L - k + a few tens of columns, more than 128 for l >= 96) has to be split
+    # across the cut in the refinement
+    spec = PairSpec(m=900, p=700, n=300, r=300, alpha="uniform", decay="pow15", sigma=0.0, k=l - 10,
+                    oversample=10, q=0, seed=5)
+    G1, G2, _, _ = planted_pair(spec)
+    G1, G2 = G1.astype(np.float32).astype(np.float64), G2.astype(np.float32).astype(np.float64)
+    _check(prec, G1, G2, spec)
 
 
 def test_fp32_cholesky_breakdown_repeated_with_fp64_factors():
@@ -545,3 +573,30 @@ def test_error_codes():
         with pytest.raises(P.GsvdRandError) as e:
             ctx.metrics(np.array([1.0]), np.array([0.0]))
         assert e.value.name == "ARG"
+
+
+def test_bf16_low_noise_config3_shape():
+    """The precision-stress shape (m = 120000, p = 80000, n = 4000, r = 200, d_i = i^-1.5, k = 200,
+    os = 20, q = 3; L = 440) at low noise, sigma = 1e-7: the noise floor sigma (sqrt(m) + sqrt(n))
+    = 4.1e-5 lies below the planted tail (d_200 = 3.5e-4), so most pairs are resolved and gated, and
+    the cut between the 200th and 201st eigenvalue of K (about 1e-7 of the largest apart from the
+    noise) lies below FP32 resolution."""
+    from paper_2404_09459_gb300.inputs import PAIR_BF16_STRESS
+    from dataclasses import replace
+    S = replace(PAIR_BF16_STRESS, sigma=1e-7, seed=7)
+    G1, G2, _, _ = planted_pair_torch(S)
+    b1, b2 = G1.to(torch.bfloat16), G2.to(torch.bfloat16)
+    del G1, G2
+    with P.Context("bf16", flags=P.FLAG_BF16_SPLIT_POWER) as ctx:
+        out = ctx.solve(b1, b2, S.kk, S.oversample, S.q, S.seed)
+    a, b = out["alpha"].cpu().numpy(), out["beta"].cpu().numpy()
+    ref = O.rand_gsvd(b1.double().cpu().numpy(), b2.double().cpu().numpy(), S.kk, S.oversample, S.q, S.seed,
+                      omega_round="bf16")
+    floor = S.sigma * (np.sqrt(S.m) + np.sqrt(S.n))
+    gate = int(np.sum(np.arange(1, S.r + 1) ** -1.5 >= 10 * floor))
+    e = O.gsv_error(ref["alpha"], ref["beta"], a, b)
+    print("gate", gate, "max", e[:gate].max(), "per decile", [float(e[i:i + 20].max()) for i in range(0, 200, 20)])
+    assert gate >= 20
+    assert np.max(e[:gate]) <= TOL["bf16"], (gate, np.max(e[:gate]), np.argmax(e[:gate]))
+    dth = np.abs(np.arctan2(a, b) - np.arctan2(ref["alpha"], ref["beta"]))[:gate]
+    assert np.max(dth) <= 1e-4

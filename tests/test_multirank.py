@@ -61,12 +61,15 @@ def test_reference_arm_prints_on_rank_zero_only(capsys):
     assert capsys.readouterr().out == ""
 
 
-def test_reference_arm_json_line_contract():
-    # bench.py --impl reference on the host cores (the oracle): one JSON line with the contract's keys
+@pytest.mark.parametrize("workload", ["fp64_small", "batched"])
+def test_reference_arm_json_line_contract(workload):
+    # bench.py --impl reference on the host cores (the oracle): one JSON line with the contract's keys;
+    # the batched workload (the default) solves one pair of the batch per step
     import subprocess
+    extra = ["--pairs", "2"] if workload == "batched" else []
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
-                          "fp64_small", "--steps", "1", "--warmup", "0"], capture_output=True, text=True, timeout=300,
-                         cwd=ROOT)
+                          workload, "--steps", "1", "--warmup", "0", *extra], capture_output=True, text=True,
+                         timeout=300, cwd=ROOT)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
     assert len(lines) == 1
@@ -76,3 +79,4 @@ def test_reference_arm_json_line_contract():
         assert key in d, key
     assert d["impl"] == "reference" and d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    assert d["steps"] == 1 and d["warmup"] == 3

@@ -398,6 +398,33 @@ def test_perturbation_bounds_lemma_per_and_theorem_exp():
         assert np.max(np.abs(th - tht)) <= np.arcsin(min(1.0, 2 * E))
 
 
+def test_perturbation_E_closed_form_on_a_diagonal_pair():
+    # G1 = diag(a1 d1, a2 d2), G2 = diag(b1 d1, b2 d2) (a_i^2 + b_i^2 = 1): the stack [G1; G2] has
+    # orthogonal columns of norms d1, d2, so ||G^+||_2 = 1 / d2 for d1 > d2.  Adding eps to entry
+    # (2, 2) of G1 gives ||Delta G||_F = eps and a second column of norm
+    # sqrt((a2 d2 + eps)^2 + (b2 d2)^2) > d2, whose inverse is the smaller of the two pseudo-inverse
+    # norms: E = sqrt(2) eps / sqrt((a2 d2 + eps)^2 + (b2 d2)^2), written out by hand.
+    a1, a2, d1, d2, eps = 0.8, 0.6, 2.0, 0.5, 1e-3
+    b1, b2 = 0.6, 0.8
+    G1 = np.diag([a1 * d1, a2 * d2])
+    G2 = np.diag([b1 * d1, b2 * d2])
+    G1t = G1.copy()
+    G1t[1, 1] += eps
+    # (a2 d2 + eps)^2 + (b2 d2)^2 = 0.301^2 + 0.4^2 = 0.250601
+    E_hand = np.sqrt(2.0) * 1e-3 / np.sqrt(0.250601)
+    assert abs(O.perturbation_E(G1, G2, G1t, G2) - E_hand) <= 1e-15 * E_hand
+    # symmetric in which pair is taken as the reference
+    assert abs(O.perturbation_E(G1t, G2, G1, G2) - E_hand) <= 1e-15 * E_hand
+    # and the Lemma's bound holds on it: the perturbed pair of the second column is
+    # ((a2 d2 + eps), b2 d2) / its norm, the first pair is unchanged
+    nrm = np.sqrt(0.250601)
+    at, bt = np.array([a1, 0.301 / nrm]), np.array([b1, 0.4 / nrm])
+    got_a, got_b = O.direct_gsvd(G1t, G2)
+    np.testing.assert_allclose(got_a, at, atol=1e-15)
+    np.testing.assert_allclose(got_b, bt, atol=1e-15)
+    assert np.sqrt(np.sum((at - [a1, a2]) ** 2 + (bt - [b1, b2]) ** 2)) <= E_hand
+
+
 def test_power_iterations_keep_small_directions():
     # Subspace iteration must re-orthonormalise after every product: with a
     # spectrum spanning 1 .. 1e-8 and q = 4 the plain powered sketch

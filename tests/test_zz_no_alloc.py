@@ -1,9 +1,15 @@
-"""gsvd_rand_metrics_noalloc against gsvd_rand_metrics (needs a CUDA GPU).
+"""gsvd_rand_metrics_noalloc against gsvd_rand_metrics and the FP64 oracle (needs a CUDA GPU).
 
 The no-allocation entry point keeps its scratch in a fixed static device array;
 here two calls in a row must each agree with the allocating entry point to
-rounding (the entropy sums are added in another order), leave the device's free
-memory unchanged, and refuse sizes above the fixed limit.
+rounding (the entropy sums are added in another order) and with the oracle's
+Section 1 formulas, leave the device's free memory unchanged, and refuse sizes
+above the fixed limit.
+
+Tolerances against the oracle: theta and P to 1e-14 absolute, rho to 1e-14
+relative (one division or atan2 per entry, a few ulps); D_1, D_2 to 4e-12: each
+is a sum of N <= 32768 terms P log P of magnitude <= 1/e, summed in another
+order, so the rounding differences stay below N u = 3.6e-12.
 """
 import numpy as np
 import pytest
@@ -15,6 +21,7 @@ if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
 import paper_2404_09459_gb300 as P  # noqa: E402
+from oracle import gsvd as O  # noqa: E402
 
 P._build.build()
 
@@ -39,6 +46,20 @@ def _close(got, ref):
         assert abs(float(got[key]) - float(ref[key])) <= 1e-13, key
 
 
+def _close_oracle(got, a, b, pad_to_n, pad_mode):
+    ref = O.metrics(a, b, pad_to_n, pad_mode)
+    for key in KEYS:
+        g = np.asarray(got[key].cpu() if hasattr(got[key], "cpu") else got[key])
+        fin = np.isfinite(ref[key])
+        if key == "rho":
+            np.testing.assert_allclose(g[fin], ref[key][fin], rtol=1e-14, atol=0)
+        else:
+            np.testing.assert_allclose(g[fin], ref[key][fin], rtol=0, atol=1e-14)
+        assert np.all(np.isinf(g[~fin]))
+    for key in ("D1", "D2"):
+        assert abs(float(got[key]) - float(ref[key])) <= 4e-12, key
+
+
 @pytest.mark.parametrize("r,pad_to_n,pad_mode", [(17, 0, 0), (17, 40, 0), (17, 40, 1), (3000, 5000, 1),
                                                  (20000, P.NOALLOC_MAX_N, 0)])
 def test_host_buffers_two_calls_match_allocating_entry_point(r, pad_to_n, pad_mode):
@@ -49,6 +70,8 @@ def test_host_buffers_two_calls_match_allocating_entry_point(r, pad_to_n, pad_mo
     second = P.metrics_noalloc(a, b, pad_to_n, pad_mode)
     _close(first, ref)
     _close(second, ref)
+    _close_oracle(first, a, b, pad_to_n, pad_mode)
+    _close_oracle(second, a, b, pad_to_n, pad_mode)
     for key in KEYS:
         np.testing.assert_array_equal(first[key], second[key])
 
@@ -71,6 +94,7 @@ def test_device_buffers_two_calls_allocate_nothing():
     assert torch.cuda.mem_get_info()[0] == free_before
     for g in got:
         _close(g, ref)
+        _close_oracle(g, a, b, N, 0)
 
 
 def test_size_above_limit_is_refused():
