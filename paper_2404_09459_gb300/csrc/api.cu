@@ -65,6 +65,8 @@ struct gsvd_rand_ctx {
   double* fact_scr = nullptr;  // device scratch of gsvd_rand_factors (4 x 512 doubles)
   char* gstage = nullptr;      // device copies of a grouped solve's host inputs
   size_t gstage_bytes = 0;
+  char* gbounce = nullptr;     // contiguous landing area of one host matrix before its rows are padded
+  size_t gbounce_bytes = 0;
   // learned proposal: network (params | norm), then features, logits and scratch of one pair
   float* mlp_dev = nullptr;
   bool mlp_ready = false;
@@ -695,11 +697,10 @@ int small_gsvd(gsvd_rand_ctx* h, cudaStream_t st, DevStatus* st_dev, const T* S,
     ProfScope ps(h, GSVD_RAND_STAGE_SMALL_REFINE);
     for (int it = 0; it < oa_iters<T>(); ++it) {
       CU(launch_oa_refine(sb.K, L, sb.X, sb.lam, sb.work, sb.work_elems, st));
-      // after two steps the start's error is gone but a cluster across the cut is not split;
-      // on the FP64 path the split is repeated after the third step, whose delta (set by
-      // the second step's Newton correction) takes in the whole unresolved group
-      if (it == 1 || (it == 2 && oa_iters<T>() > 3))
-        CU(launch_oa_cut_cluster(L, r, sb.X, sb.lam, sb.work, sb.work_elems, st));
+      // after the first step every eigenvector outside the clusters has squared its start
+      // error, so the cluster that straddles the cut (of any size up to L) is split then,
+      // and the remaining steps (two on the mixed paths) refine the split columns
+      if (it == 0) CU(launch_oa_cut_cluster(L, r, sb.X, sb.lam, sb.work, sb.work_elems, sb.jscratch, st));
     }
   }
   ProfScope ps_cs(h, GSVD_RAND_STAGE_SMALL_CS);
@@ -1893,7 +1894,7 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
       });
     }
   };
-  // Ogita-Aishima steps (three: the mixed-precision count), the cut cluster after the second
+  // Ogita-Aishima steps (three: the mixed-precision count), the cut cluster after the first
   auto add_oa = [&](bool c1) {
     cur_tag = c1 ? GSVD_RAND_STAGE_SMALL_CS : GSVD_RAND_STAGE_SMALL_REFINE;
     std::vector<OaB> t(np);
@@ -1901,7 +1902,8 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
     for (int i = 0; i < np; ++i) {
       const GPair& P = gb.prs[i];
       const int N = c1 ? P.k : P.L;
-      t[i] = OaB{c1 ? P.C1 : P.K, c1 ? P.Wv : P.X, c1 ? P.mu : P.lam, P.XtX, P.P, P.S2, P.F, P.opart, N, P.k};
+      t[i] = OaB{c1 ? P.C1 : P.K, c1 ? P.Wv : P.X, c1 ? P.mu : P.lam, P.XtX, P.P, P.S2, P.F, P.opart, N, P.k,
+                 c1 ? nullptr : P.jscr};
       mN = std::max(mN, N);
     }
     std::vector<DgemmB> dg(4 * (size_t)np);
@@ -1912,7 +1914,7 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
         return launch_oa_refine_b(reinterpret_cast<const OaB*>(d + ot), reinterpret_cast<const DgemmB*>(d + od), np,
                                   mN, st);
       });
-      if (!c1 && it == 1)
+      if (!c1 && it == 0)  // the cut cluster split after the first step, as in the single solve
         push([ot, np, mN](const unsigned char* d, cudaStream_t st) {
           return launch_oa_cut_cluster_b(reinterpret_cast<const OaB*>(d + ot), np, mN, st);
         });
@@ -2272,6 +2274,10 @@ int solve_grouped(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs) {
 // Host inputs of a grouped solve.  Each host matrix is copied, on h's stream ahead of the
 // grouped launch, into device memory owned by h with its rows padded to a 16-byte multiple
 // (the row stride the tensor-core products need); the grouped solve then runs on the copies.
+// A host matrix whose rows are contiguous and already 16-byte multiples lands in place with one
+// copy; any other lands contiguously (one copy of its M n elements, or a pitched copy when its
+// host rows are not contiguous) in a bounce buffer and is re-pitched by a device-to-device copy,
+// because pitched host copies of rows a few KB long run far below the link's bandwidth.
 // The copies keep their addresses while the batch's shapes stay the same, so a repeated call
 // copies the inputs again and replays the captured graph.  Matrices whose shape arguments are
 // invalid are left as they are (the grouped solve gives their pair ARG).
@@ -2306,6 +2312,23 @@ int solve_grouped_staged(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs) {
     }
     h->gstage_bytes = need;
   }
+  size_t bounce = 0;  // the largest matrix that needs re-pitching
+  for (int i = 0; i < npairs; ++i)
+    for (int s = 0; s < 2; ++s)
+      if ((host[i] & (1 << s)) && pairs[i].n % 4)
+        bounce = std::max(bounce, (size_t)(s ? pairs[i].p : pairs[i].m) * pairs[i].n * sizeof(float));
+  if (bounce > h->gbounce_bytes) {
+    CU(cudaStreamSynchronize(h->stream));
+    if (h->gbounce) cudaFree(h->gbounce);
+    h->gbounce = nullptr;
+    h->gbounce_bytes = 0;
+    if (cudaMalloc(&h->gbounce, bounce) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, GSVD_RAND_ERR_OOM, "bounce buffer of the grouped solve's host inputs (%zu bytes) failed",
+                  bounce);
+    }
+    h->gbounce_bytes = bounce;
+  }
   std::vector<gsvd_rand_pair> sp(pairs, pairs + npairs);
   size_t off = 0;
   for (int i = 0; i < npairs; ++i) {
@@ -2316,8 +2339,15 @@ int solve_grouped_staged(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs) {
       const void* src = s ? q.G2 : q.G1;
       const int64_t M = s ? q.p : q.m, ld = s ? q.ld2 : q.ld1;
       char* dst = h->gstage + off;
-      CU(copy_rows(dst, (size_t)ldn * sizeof(float), src, (size_t)ld * sizeof(float), (size_t)q.n * sizeof(float),
-                   (size_t)M, cudaMemcpyHostToDevice, h->stream));
+      const size_t row = (size_t)q.n * sizeof(float);
+      if (ldn == q.n) {
+        CU(copy_rows(dst, row, src, (size_t)ld * sizeof(float), row, (size_t)M, cudaMemcpyHostToDevice, h->stream));
+      } else {
+        CU(copy_rows(h->gbounce, row, src, (size_t)ld * sizeof(float), row, (size_t)M, cudaMemcpyHostToDevice,
+                     h->stream));
+        CU(cudaMemcpy2DAsync(dst, (size_t)ldn * sizeof(float), h->gbounce, row, row, (size_t)M,
+                             cudaMemcpyDeviceToDevice, h->stream));
+      }
       if (s) {
         q.G2 = dst;
         q.ld2 = ldn;
@@ -2403,6 +2433,7 @@ int gsvd_rand_destroy(gsvd_rand_t h) {
   if (h->res_host) cudaFreeHost(h->res_host);
   if (h->tab_host) cudaFreeHost(h->tab_host);
   if (h->gstage) cudaFree(h->gstage);
+  if (h->gbounce) cudaFree(h->gbounce);
   delete h;
   return GSVD_RAND_OK;
 }

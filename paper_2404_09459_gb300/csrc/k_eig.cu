@@ -38,6 +38,50 @@ __device__ float block_sum_f(float v, float* red) {
   return s;
 }
 
+// Block max; every thread receives the result.
+__device__ float block_max_f(float v, float* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, ln = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (ln == 0) red[w] = v;
+  __syncthreads();
+  float m = 0.f;
+  for (int i = 0; i < nw; ++i) m = fmaxf(m, red[i]);
+  return m;
+}
+
+// Columns whose largest entry is below this (in a matrix scaled to unit size) are taken as
+// zero by the reflectors: their squares would fall into the denormal range.
+constexpr float NRM_TINY = 1e-36f;
+
+// sqrt(sum_i x(i)^2) for i = i0, i0 + 1, .. N - 1 over one warp (lane t), scaled by the largest
+// |x(i)| before squaring (as the reference BLAS nrm2 scales), so that a column of tiny entries
+// (the rounding-level rows of a nearly singular matrix) keeps the relative accuracy of its
+// norm: unscaled, squares below 1e-38 turn denormal or vanish, the norm no longer matches the
+// entries, and a reflector built from it is not orthogonal.  Returns 0 for a column whose
+// largest entry is below NRM_TINY, NaN or inf when an entry is.
+template <typename F>
+__device__ __forceinline__ float warp_nrm2(int i0, int N, int t, F x) {
+  float mx = 0.f;
+  bool bad = false;
+  for (int i = i0 + t; i < N; i += 32) {
+    const float a = fabsf(x(i));
+    bad = bad || !(a <= 3.0e38f);
+    mx = fmaxf(mx, a);
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (__any_sync(0xffffffffu, bad)) return __int_as_float(0x7fc00000);
+  if (!(mx >= NRM_TINY)) return 0.f;
+  const float sc = 1.f / mx;
+  float sg = 0.f;
+  for (int i = i0 + t; i < N; i += 32) {
+    const float y = x(i) * sc;
+    sg = fmaf(y, y, sg);
+  }
+  for (int o = 16; o > 0; o >>= 1) sg += __shfl_xor_sync(0xffffffffu, sg, o);
+  return mx * sqrtf(sg);
+}
+
 // Number of eigenvalues of T (d, e2 = e^2) smaller than x.
 __device__ int sturm_count(const float* d, const float* e2, int N, float x, float pivmin) {
   int c = 0;
@@ -143,13 +187,17 @@ __global__ __launch_bounds__(1024) void eig_f32_kernel(const double* __restrict_
   for (int k = 0; k + 2 < N; ++k) {
     const int m = N - k - 1;
     const float x0 = A[(int64_t)(k + 1) * lda + k];
+    float amax = 0.f;
+    for (int i = tid; i < m; i += nt) amax = fmaxf(amax, fabsf(A[(int64_t)(k + 1 + i) * lda + k]));
+    const float mx = block_max_f(amax, red);  // scaled sum of squares (see warp_nrm2)
+    const float isc = mx >= NRM_TINY ? 1.f / mx : 0.f;
     float part = 0.f;
     for (int i = tid; i < m; i += nt) {
-      float xi = A[(int64_t)(k + 1 + i) * lda + k];
+      const float xi = A[(int64_t)(k + 1 + i) * lda + k] * isc;
       part += xi * xi;
     }
     const float sig2 = block_sum_f(part, red);
-    const float sig = sqrtf(sig2);
+    const float sig = mx >= NRM_TINY ? mx * sqrtf(sig2) : (isfinite(sig2) ? 0.f : sig2);
     const float alpha = x0 >= 0.f ? -sig : sig;  // H x = alpha e1
     // normalised reflector (v_0 = 1, tau in [1, 2]): bounded for any scale of the column
     const bool refl = sig > 0.f && isfinite(sig);
@@ -391,6 +439,7 @@ __device__ __forceinline__ void eig128_body(const double* __restrict__ Ain, int 
   __shared__ float s_cf[E_NMAX], s_flag[E_NMAX];
   __shared__ int s_cstart[E_NMAX], s_prev[E_NMAX], s_np, s_npan;
   __shared__ float s_scale, s_bound[2], s_nrm, s_before;
+  __shared__ int s_retry;
   const int tid = threadIdx.x, w = tid >> 5, t = tid & 31;
   const int lda = N | 1;
   float* Vref = esm;                       // N x 128: reflector k in row k (zero up to row k)
@@ -433,10 +482,7 @@ __device__ __forceinline__ void eig128_body(const double* __restrict__ Ain, int 
       // normalised form v_0 = 1, v_i = x_i / (x0 - alpha), tau = (alpha - x0) / alpha in
       // [1, 2]: bounded for any scale of x (an unnormalised 2 / v^T v overflows on tiny columns)
       const float x0 = col[k + 1];
-      float sg = 0.f;
-      for (int i = k + 1 + t; i < N; i += 32) sg = fmaf(col[i], col[i], sg);
-      for (int o = 16; o > 0; o >>= 1) sg += __shfl_xor_sync(0xffffffffu, sg, o);
-      const float sig = sqrtf(sg);
+      const float sig = warp_nrm2(k + 1, N, t, [&](int i) { return col[i]; });
       const float alpha = x0 >= 0.f ? -sig : sig;
       const bool refl = sig > 0.f && isfinite(sig);
       const float bk = refl ? (alpha - x0) / alpha : 0.f;
@@ -633,10 +679,19 @@ __device__ __forceinline__ void eig128_body(const double* __restrict__ Ain, int 
       const int cs = pass == 0 ? s_cstart[j] : 0;
       if (s_flag[j] == 2.f) continue;      // noise column: filled by the complement below
       if (pass == 0 && cs == j) continue;  // first of its cluster (or a singleton)
+      if (pass == 1 && s_flag[j] >= 0.f) continue;
+      // pass 1: the replacement by inverse iteration; when it falls (nearly) inside the span of
+      // the accepted columns (an eigenvalue of T closer to accepted ones than to the missing
+      // one), a second attempt from a plain pseudo-random start, which keeps the basis orthonormal
+      for (int att = 0; att < (pass == 1 ? 2 : 1); ++att) {
       if (pass == 1) {
-        if (s_flag[j] >= 0.f) continue;
         // U pivots of the twisted factorisation at lambda_j are still in row j of Us
-        if (tid == 0) inverse_iteration_start(s_e, Us + (size_t)j * lda, N, (uint32_t)j, Zs + j, lda);
+        if (tid == 0) {
+          if (att == 0)
+            inverse_iteration_start(s_e, Us + (size_t)j * lda, N, (uint32_t)j, Zs + j, lda);
+          else
+            for (int i = 0; i < N; ++i) Zs[(size_t)i * lda + j] = hash_unit((uint32_t)j ^ 0x5bd1e995u, (uint32_t)i);
+        }
         __syncthreads();
         if (w == 0) {  // the length before the projection
           float s2 = 0.f;
@@ -680,12 +735,16 @@ __device__ __forceinline__ void eig128_body(const double* __restrict__ Ain, int 
         if (t == 0) {
           s_nrm = dep && pass == 0 ? 0.f : rsqrtf(s2 > 0.f ? s2 : 1.f);
           s_flag[j] = dep && pass == 0 ? -1.f : 1.f;
+          s_retry = (pass == 1 && att == 0 && dep) ? 1 : 0;
         }
       }
       __syncthreads();
+      if (s_retry) continue;
       const float sc = s_nrm;
       for (int i = tid; i < N; i += 1024) Zs[(size_t)i * lda + j] *= sc;
       __syncthreads();
+      break;
+      }
     }
   }
 
@@ -715,14 +774,11 @@ __device__ __forceinline__ void eig128_body(const double* __restrict__ Ain, int 
     __syncthreads();
     for (int k = 0; k < nn; ++k) {
       if (w == 0) {
-        float sg = 0.f;
-        for (int i = k + t; i < N; i += 32) sg = fmaf(V[(size_t)i * lda + k], V[(size_t)i * lda + k], sg);
-        for (int o = 16; o > 0; o >>= 1) sg += __shfl_xor_sync(0xffffffffu, sg, o);
+        const float sig = warp_nrm2(k, N, t, [&](int i) { return V[(size_t)i * lda + k]; });
         const float x0 = V[(size_t)k * lda + k];
-        const float sig = sqrtf(sg);
         const float alpha = x0 >= 0.f ? -sig : sig;
-        const float den = sg - x0 * alpha;
-        const float bk = (sig > 0.f && den > 0.f) ? 1.f / den : 0.f;
+        const float den = sig * (sig + fabsf(x0));  // v^T v / 2 for v = x - alpha e_k
+        const float bk = (den >= NRM_TINY && isfinite(den)) ? 1.f / den : 0.f;
         __syncwarp();
         if (t == 0) {
           V[(size_t)k * lda + k] = x0 - alpha;  // v_k in place (rows k..N-1)
@@ -838,6 +894,7 @@ __device__ __forceinline__ void eig_big_body(const double* __restrict__ Ain, int
   __shared__ float2 s_de[EB_NMAX];
   __shared__ int s_cstart[EB_NMAX], s_prev[EB_NMAX], s_np, s_npan;
   __shared__ float s_red[32], s_scale, s_bound[2], s_nrm, s_before;
+  __shared__ int s_retry;
   const int tid = threadIdx.x, w = tid >> 5, t = tid & 31;
   const size_t NN = (size_t)N * N;
   float* ZT = gscr;        // N x N column-major: eigenvectors of T, then of A
@@ -863,13 +920,7 @@ __device__ __forceinline__ void eig_big_body(const double* __restrict__ Ain, int
   for (int k = 0; k + 2 < N; ++k) {
     if (w == 0) {
       const float x0 = Ap[pk(k + 1, k)];
-      float sg = 0.f;
-      for (int i = k + 1 + t; i < N; i += 32) {
-        const float x = Ap[pk(i, k)];
-        sg = fmaf(x, x, sg);
-      }
-      for (int o = 16; o > 0; o >>= 1) sg += __shfl_xor_sync(0xffffffffu, sg, o);
-      const float sig = sqrtf(sg);
+      const float sig = warp_nrm2(k + 1, N, t, [&](int i) { return Ap[pk(i, k)]; });
       const float alpha = x0 >= 0.f ? -sig : sig;
       const bool refl = sig > 0.f && isfinite(sig);
       const float bk = refl ? (alpha - x0) / alpha : 0.f;  // normalised reflector, v_0 = 1, bk in [1, 2]
@@ -1058,10 +1109,18 @@ __device__ __forceinline__ void eig_big_body(const double* __restrict__ Ain, int
       if (s_flag[j] == 2.f) continue;
       if (pass == 0 && cs == j) continue;
       float* Zj = ZT + (size_t)j * N;
+      if (pass == 1 && s_flag[j] >= 0.f) continue;
+      // pass 1: inverse iteration, then (when that falls inside the accepted span) a plain
+      // pseudo-random start, as in eig128
+      for (int att = 0; att < (pass == 1 ? 2 : 1); ++att) {
       if (pass == 1) {
-        if (s_flag[j] >= 0.f) continue;
         // U pivots of the twisted factorisation at lambda_j are still in column j of UT
-        if (tid == 0) inverse_iteration_start(s_e, UT + (size_t)j * N, N, (uint32_t)j, Zj, 1);
+        if (tid == 0) {
+          if (att == 0)
+            inverse_iteration_start(s_e, UT + (size_t)j * N, N, (uint32_t)j, Zj, 1);
+          else
+            for (int i = 0; i < N; ++i) Zj[i] = hash_unit((uint32_t)j ^ 0x5bd1e995u, (uint32_t)i);
+        }
         __syncthreads();
         if (w == 0) {  // the length before the projection
           float s2 = 0.f;
@@ -1105,12 +1164,16 @@ __device__ __forceinline__ void eig_big_body(const double* __restrict__ Ain, int
         if (t == 0) {
           s_nrm = dep && pass == 0 ? 0.f : rsqrtf(s2 > 0.f ? s2 : 1.f);
           s_flag[j] = dep && pass == 0 ? -1.f : 1.f;
+          s_retry = (pass == 1 && att == 0 && dep) ? 1 : 0;
         }
       }
       __syncthreads();
+      if (s_retry) continue;
       const float sc = s_nrm;
       for (int i = tid; i < N; i += 1024) Zj[i] *= sc;
       __syncthreads();
+      break;
+      }
     }
   }
 
@@ -1138,14 +1201,11 @@ __device__ __forceinline__ void eig_big_body(const double* __restrict__ Ain, int
     for (int k = 0; k < nn; ++k) {
       float* Vk = VT + (size_t)k * N;
       if (w == 0) {
-        float sg = 0.f;
-        for (int i = k + t; i < N; i += 32) sg = fmaf(Vk[i], Vk[i], sg);
-        for (int o = 16; o > 0; o >>= 1) sg += __shfl_xor_sync(0xffffffffu, sg, o);
+        const float sig = warp_nrm2(k, N, t, [&](int i) { return Vk[i]; });
         const float x0 = Vk[k];
-        const float sig = sqrtf(sg);
         const float alpha = x0 >= 0.f ? -sig : sig;
-        const float den = sg - x0 * alpha;
-        const float bk = (sig > 0.f && den > 0.f) ? 1.f / den : 0.f;
+        const float den = sig * (sig + fabsf(x0));  // v^T v / 2 for v = x - alpha e_k
+        const float bk = (den >= NRM_TINY && isfinite(den)) ? 1.f / den : 0.f;
         __syncwarp();
         if (t == 0) {
           Vk[k] = x0 - alpha;
@@ -1237,6 +1297,44 @@ __global__ __launch_bounds__(1024) void eig128_b_kernel(const EigB* __restrict__
 __global__ __launch_bounds__(1024) void eig_big_b_kernel(const EigB* __restrict__ tab) {
   const EigB& a = tab[blockIdx.x];
   eig_big_body(a.A, a.N, a.X, a.lam, a.scratch, a.noise_rel, 1);
+}
+
+// A cut cluster of more than CUT_CMAX columns (the descriptor written by the cut-cluster
+// detection kernel into the P block of the refinement work; N = 0: nothing to solve).  The
+// packed triangle stays in shared memory when N <= ap_cap (the launch's allocation).
+__device__ __forceinline__ void eig_cut_big_body(const double* __restrict__ pblock, int ap_cap) {
+  const EigB* e = reinterpret_cast<const EigB*>(pblock + CUT_EIGB_OFF);
+  const int c = e->N;
+  if (c <= CUT_CMAX || c > EB_NMAX) return;
+  eig_big_body(e->A, c, e->X, e->lam, e->scratch, 0.f, c <= ap_cap);
+}
+
+__global__ __launch_bounds__(1024) void eig_cut_big_kernel(const double* __restrict__ pblock, int ap_cap) {
+  eig_cut_big_body(pblock, ap_cap);
+}
+
+__global__ __launch_bounds__(1024) void eig_cut_big_b_kernel(const OaB* __restrict__ tab, int ap_cap) {
+  const OaB& o = tab[blockIdx.x];
+  if (o.N <= CUT_CMAX || !o.jscr) return;  // no room for a descriptor, or no scratch: clipped clusters only
+  eig_cut_big_body(o.P, ap_cap);
+}
+
+cudaError_t launch_eig_cut_big(const double* pblock, int max_N, cudaStream_t st) {
+  if (max_N <= CUT_CMAX) return cudaSuccess;
+  const int cap = std::min(max_N, EB_SMEM_NMAX);
+  const size_t smem = (size_t)cap * (cap + 1) / 2 * sizeof(float);
+  cudaFuncSetAttribute(eig_cut_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 202 * 1024);
+  eig_cut_big_kernel<<<1, 1024, smem, st>>>(pblock, cap);
+  return launched();
+}
+
+cudaError_t launch_eig_cut_big_b(const OaB* tab, int nprob, int max_N, cudaStream_t st) {
+  if (nprob <= 0 || max_N <= CUT_CMAX) return cudaSuccess;
+  const int cap = std::min(max_N, EB_SMEM_NMAX);
+  const size_t smem = (size_t)cap * (cap + 1) / 2 * sizeof(float);
+  cudaFuncSetAttribute(eig_cut_big_b_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 202 * 1024);
+  eig_cut_big_b_kernel<<<nprob, 1024, smem, st>>>(tab, cap);
+  return launched();
 }
 
 cudaError_t launch_eig_f32_b(const EigB* tab, int nprob, int max_N, cudaStream_t st) {

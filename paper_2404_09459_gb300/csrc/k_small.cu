@@ -363,24 +363,36 @@ cudaError_t launch_oa_refine(const double* A, int N, double* X, double* lam, dou
 // by its mean and scaled to unit size, which resolves the block's own
 // spread, by parallel cyclic Jacobi in FP32 (round-robin pairs).  Its columns
 // of X are then rotated, X_c <- X_c V_c, and the following refinement steps
-// re-orthogonalise in FP64 and separate them.
+// re-orthogonalise in FP64 and separate them.  A cluster of more than
+// CUT_CMAX columns (a dense run of eigenvalues below FP32 resolution, e.g. a
+// slowly decaying tail) is not clipped: its shifted and scaled block is left
+// in XtX (no longer needed by then) for the packed-triangle FP32 eigensolver,
+// a second launch that reads the block's size from the descriptor this
+// kernel writes (launch_eig_cut_big).
 // Work layout (as launch_oa_refine): XtX, P, S, F (N x N each), part (3 nb).
-// V_c goes to F, the cluster's column indices and size to P.
+// V_c goes to F, the cluster's column indices and size to P (ints 0 .. c);
+// for a large cluster P also holds the eigensolver's descriptor (EigB at double
+// offset CUT_EIGB_OFF) and the block's eigenvalues (from CUT_LAM_OFF).
 // ============================================================================
-constexpr int CUT_CMAX = 128;
 
-__device__ __forceinline__ void oa_cut_cluster_body(int N, int r, const double* __restrict__ XtX,
-                                                    const double* __restrict__ S, const double* __restrict__ part,
-                                                    int nparts, const double* __restrict__ lam,
-                                                    double* __restrict__ Vc, int* __restrict__ cinfo) {
+__device__ __forceinline__ void oa_cut_cluster_body(int N, int r, double* XtX, const double* __restrict__ S,
+                                                    const double* __restrict__ part, int nparts,
+                                                    const double* __restrict__ lam, double* __restrict__ Vc,
+                                                    int* __restrict__ cinfo, float* jscr) {
   extern __shared__ float cut_sm[];
   __shared__ int s_ord[512];
+  __shared__ double s_dg[CUT_BIG_NMAX];  // Rayleigh quotients s_ii / x_i^T x_i of the cluster
+  __shared__ double s_wmax[32];
   __shared__ int s_lo, s_c;
   __shared__ double s_delta, s_mu, s_scale;
   __shared__ int s_p[CUT_CMAX / 2], s_q[CUT_CMAX / 2];
   __shared__ float s_cs[CUT_CMAX / 2], s_sn[CUT_CMAX / 2];
   __shared__ unsigned s_off;
   const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nwarp = nt >> 5;
+  // clusters beyond CUT_CMAX columns go to the second launch when its scratch is given
+  const bool big_ok = jscr != nullptr && N > CUT_CMAX;
+  const int cap = big_ok ? CUT_BIG_NMAX : CUT_CMAX;
+  EigB* eb = big_ok ? reinterpret_cast<EigB*>(reinterpret_cast<double*>(cinfo) + CUT_EIGB_OFF) : nullptr;
   if (tid == 0) {
     double A2 = 0, R2 = 0, S2 = 0;
     for (int b = 0; b < nparts; ++b) {
@@ -409,44 +421,70 @@ __device__ __forceinline__ void oa_cut_cluster_body(int N, int r, const double* 
       lo = 0;
       hi = 0;
     } else {
-      while (lo > 0 && lm(lo - 1) - lm(lo) <= d && hi - lo < CUT_CMAX) --lo;
-      while (hi < N && lm(hi - 1) - lm(hi) <= d && hi - lo < CUT_CMAX) ++hi;
+      while (lo > 0 && lm(lo - 1) - lm(lo) <= d && hi - lo < cap) --lo;
+      while (hi < N && lm(hi - 1) - lm(hi) <= d && hi - lo < cap) ++hi;
     }
     s_lo = lo;
     s_c = hi - lo;
     cinfo[0] = hi - lo;
+    if (eb) eb->N = 0;  // no second eigensolve unless the cluster is large (below)
   }
   __syncthreads();
   const int c = s_c, lo = s_lo;
   if (c < 2) return;
-  const int lda = c | 1;
-  float* T = cut_sm;
-  float* V = cut_sm + c * lda;
-  for (int a = tid; a < c; a += nt) cinfo[1 + a] = s_ord[lo + a];
+  for (int a = tid; a < c; a += nt) {
+    const int ia = s_ord[lo + a];
+    cinfo[1 + a] = ia;
+    s_dg[a] = S[(int64_t)ia * N + ia] / XtX[(int64_t)ia * N + ia];
+  }
+  __syncthreads();
   if (tid == 0) {
     double mu = 0.0;
-    for (int a = 0; a < c; ++a) {
-      const int ia = s_ord[lo + a];
-      mu += S[(int64_t)ia * N + ia] / XtX[(int64_t)ia * N + ia];
-    }
+    for (int a = 0; a < c; ++a) mu += s_dg[a];
     s_mu = mu / c;
   }
   __syncthreads();
-  if (tid == 0) {
+  {  // scale: the largest |entry| of the shifted block (parallel max)
     double mx = 0.0;
-    for (int a = 0; a < c; ++a) {
-      const int ia = s_ord[lo + a];
-      mx = fmax(mx, fabs(S[(int64_t)ia * N + ia] / XtX[(int64_t)ia * N + ia] - s_mu));
-      for (int b = 0; b < c; ++b) mx = fmax(mx, fabs(S[(int64_t)ia * N + s_ord[lo + b]]) * (a != b));
+    for (int e = tid; e < c * c; e += nt) {
+      const int a = e / c, b = e % c;
+      mx = fmax(mx, a == b ? fabs(s_dg[a] - s_mu) : fabs(S[(int64_t)s_ord[lo + a] * N + s_ord[lo + b]]));
     }
-    s_scale = (mx > 0.0 && isfinite(mx)) ? mx : 1.0;
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) s_wmax[warp] = mx;
+    __syncthreads();
+    if (tid == 0) {
+      double m = 0.0;
+      for (int w = 0; w < nwarp; ++w) m = fmax(m, s_wmax[w]);
+      s_scale = (m > 0.0 && isfinite(m)) ? m : 1.0;
+    }
+    __syncthreads();
   }
-  __syncthreads();
   const double inv = 1.0 / s_scale, mu = s_mu;
+  if (c > CUT_CMAX) {
+    // the block (FP64, c x c) into XtX, read by nothing else from here on; the eigensolver
+    // writes its eigenvectors (V_c) into Vc and its eigenvalues after the descriptor
+    for (int e = tid; e < c * c; e += nt) {
+      const int a = e / c, b = e % c, ia = s_ord[lo + a], ib = s_ord[lo + b];
+      XtX[e] = (a == b ? s_dg[a] - mu : 0.5 * (S[(int64_t)ia * N + ib] + S[(int64_t)ib * N + ia])) * inv;
+    }
+    if (tid == 0) {
+      eb->A = XtX;
+      eb->X = Vc;
+      eb->lam = reinterpret_cast<double*>(cinfo) + CUT_LAM_OFF;
+      eb->scratch = jscr;
+      eb->noise_rel = 0.f;
+      eb->N = c;
+    }
+    return;
+  }
+  const int lda = c | 1;
+  float* T = cut_sm;
+  float* V = cut_sm + c * lda;
   for (int e = tid; e < c * c; e += nt) {
     const int a = e / c, b = e % c, ia = s_ord[lo + a], ib = s_ord[lo + b];
     double t = 0.5 * (S[(int64_t)ia * N + ib] + S[(int64_t)ib * N + ia]);
-    if (a == b) t = t / XtX[(int64_t)ia * N + ia] - mu;
+    if (a == b) t = s_dg[a] - mu;
     T[a * lda + b] = (float)(t * inv);
     V[a * lda + b] = a == b ? 1.f : 0.f;
   }
@@ -511,18 +549,19 @@ __device__ __forceinline__ void oa_cut_cluster_body(int N, int r, const double* 
   for (int e = tid; e < c * c; e += nt) Vc[e] = (double)V[(e / c) * lda + e % c];
 }
 
-__global__ __launch_bounds__(1024) void oa_cut_cluster_kernel(int N, int r, const double* __restrict__ XtX,
+__global__ __launch_bounds__(1024) void oa_cut_cluster_kernel(int N, int r, double* XtX,
                                                               const double* __restrict__ S,
                                                               const double* __restrict__ part, int nparts,
                                                               const double* __restrict__ lam,
-                                                              double* __restrict__ Vc, int* __restrict__ cinfo) {
-  oa_cut_cluster_body(N, r, XtX, S, part, nparts, lam, Vc, cinfo);
+                                                              double* __restrict__ Vc, int* __restrict__ cinfo,
+                                                              float* jscr) {
+  oa_cut_cluster_body(N, r, XtX, S, part, nparts, lam, Vc, cinfo, jscr);
 }
 
 // X[:, idx] <- X[:, idx] V_c, one CTA per row of X.
 __device__ __forceinline__ void cut_rotate_body(int N, double* __restrict__ X, const double* __restrict__ Vc,
                                                 const int* __restrict__ cinfo, int i) {
-  __shared__ double row[CUT_CMAX];
+  __shared__ double row[CUT_BIG_NMAX];
   const int c = cinfo[0];
   if (c < 2) return;
   for (int b = threadIdx.x; b < c; b += blockDim.x) row[b] = X[(int64_t)i * N + cinfo[1 + b]];
@@ -540,11 +579,11 @@ __global__ __launch_bounds__(128) void cut_rotate_kernel(int N, double* __restri
 }
 
 cudaError_t launch_oa_cut_cluster(int N, int r, double* X, const double* lam, double* work, int64_t work_elems,
-                                  cudaStream_t st) {
+                                  float* jscr, cudaStream_t st) {
   const int64_t nn = (int64_t)N * N;
   const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(128, cdiv(nn, 1024)));
-  if (N > 512 || work_elems < 4 * nn + 3 * nb + nn) return cudaErrorInvalidValue;
-  const double* XtX = work;
+  if (N > CUT_BIG_NMAX || work_elems < 4 * nn + 3 * nb + nn) return cudaErrorInvalidValue;
+  double* XtX = work;
   int* cinfo = reinterpret_cast<int*>(work + nn);
   const double* S = work + 2 * nn;
   double* Vc = work + 3 * nn;
@@ -554,9 +593,10 @@ cudaError_t launch_oa_cut_cluster(int N, int r, double* X, const double* lam, do
   // a fixed cap (the largest cluster block): concurrent launches must not lower it
   cudaFuncSetAttribute(oa_cut_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)(2 * CUT_CMAX * (CUT_CMAX | 1) * sizeof(float)));
-  oa_cut_cluster_kernel<<<1, 1024, smem, st>>>(N, r, XtX, S, part, nb, lam, Vc, cinfo);
+  oa_cut_cluster_kernel<<<1, 1024, smem, st>>>(N, r, XtX, S, part, nb, lam, Vc, cinfo, jscr);
   cudaError_t e = launched();
   if (e) return e;
+  if (jscr && N > CUT_CMAX && (e = launch_eig_cut_big(work + nn, N, st))) return e;
   cut_rotate_kernel<<<N, 128, 0, st>>>(N, X, Vc, cinfo);
   return launched();
 }
@@ -1051,7 +1091,7 @@ cudaError_t launch_oa_refine_b(const OaB* tab, const DgemmB* dg, int nprob, int 
 // cluster's indices in P), then the rotation of its columns of X.
 __global__ __launch_bounds__(1024) void oa_cut_cluster_b_kernel(const OaB* __restrict__ tab) {
   const OaB& o = tab[blockIdx.x];
-  oa_cut_cluster_body(o.N, o.r, o.XtX, o.S, o.part, 1, o.lam, o.F, reinterpret_cast<int*>(o.P));
+  oa_cut_cluster_body(o.N, o.r, o.XtX, o.S, o.part, 1, o.lam, o.F, reinterpret_cast<int*>(o.P), o.jscr);
 }
 __global__ __launch_bounds__(128) void cut_rotate_b_kernel(const OaB* __restrict__ tab) {
   const OaB& o = tab[blockIdx.z];
@@ -1069,6 +1109,7 @@ cudaError_t launch_oa_cut_cluster_b(const OaB* tab, int nprob, int max_N, cudaSt
   oa_cut_cluster_b_kernel<<<nprob, 1024, smem, st>>>(tab);
   cudaError_t e = launched();
   if (e) return e;
+  if (max_N > CUT_CMAX && (e = launch_eig_cut_big_b(tab, nprob, max_N, st))) return e;
   cut_rotate_b_kernel<<<dim3((unsigned)max_N, 1, (unsigned)nprob), 128, 0, st>>>(tab);
   return launched();
 }

@@ -167,8 +167,21 @@ int cholqr2_fused_max_total_ctas();
 // straddles the cut between the r-th and (r+1)-th largest: its block of
 // X^T A X is diagonalised (FP32 Jacobi, shifted and scaled) and its columns of
 // X rotated.  Uses the work buffer of the preceding launch_oa_refine call.
+// jscr: FP32 scratch of eig_scratch_floats(N) floats for clusters of more than CUT_CMAX columns
+// (solved by the packed-triangle eigensolver in a second launch), or null to clip clusters there.
 cudaError_t launch_oa_cut_cluster(int N, int r, double* X, const double* lam, double* work, int64_t work_elems,
-                                  cudaStream_t st);
+                                  float* jscr, cudaStream_t st);
+// Cut clusters: up to CUT_CMAX columns by FP32 Jacobi inside the detection kernel, larger ones
+// (up to CUT_BIG_NMAX) by the packed-triangle FP32 eigensolver, whose descriptor the detection
+// kernel leaves in the P block of the refinement work: an EigB at double offset CUT_EIGB_OFF
+// (N = 0 when there is nothing to solve) and the block's eigenvalues from CUT_LAM_OFF.
+constexpr int CUT_CMAX = 128;
+constexpr int CUT_BIG_NMAX = 512;
+constexpr int CUT_EIGB_OFF = 260;
+constexpr int CUT_LAM_OFF = 512;
+// The second launch: pblock is the P block of one problem (max_N its N), or the batched table.
+cudaError_t launch_eig_cut_big(const double* pblock, int max_N, cudaStream_t st);
+cudaError_t launch_eig_cut_big_b(const struct OaB* tab, int nprob, int max_N, cudaStream_t st);
 cudaError_t launch_select_topr(const double* X, const double* lam, int N, int r, double* Zr,
                                int* order, cudaStream_t st);
 
@@ -300,6 +313,7 @@ struct OaB {
   double* F;
   double* part;  // 3 sums
   int N, r;
+  float* jscr;   // FP32 eigensolver scratch for a large cut cluster (eig_scratch_floats(N)), or null
 };
 // The four products of a step use `dg` (4 * nprob DgemmB entries, filled by oa_b_tables).
 void oa_b_tables(const OaB* hostOa, int nprob, DgemmB* dg);
