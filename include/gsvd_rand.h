@@ -163,6 +163,30 @@ int gsvd_rand_solve(gsvd_rand_t h, const void *G1, int64_t m, int64_t ld1, const
                     int64_t p, int64_t ld2, int64_t n, int k, int oversample, int q,
                     uint64_t seed, double *alpha, double *beta, int *r_out, double *resid_out);
 
+/* Randomized GSVs of a complex pair.  Section 1 states the GSVD over C (eq. (gsvd1):
+ * G1 = U Sigma1 R, G2 = V Sigma2 R with unitary U, V) and the synthetic experiments of
+ * Section 4.1 are complex; the method is Algorithm 2 with the fixed-rank bases as in
+ * gsvd_rand_solve, with conjugate transposes and a complex Gaussian test matrix
+ *     Omega[j][c] = g(2 (j l + c)) + i g(2 (j l + c) + 1),  l = k + oversample,
+ * g the real stream of gsvd_rand_gaussian for an n x 2l matrix (the real and imaginary parts
+ * are the two normals of one Box-Muller pair), per side s counter words (t, 0, s, 0).
+ *   G1, G2 : complex m x n and p x n, row-major, each entry an interleaved (re, im) pair:
+ *            complex128 (two doubles) for FP64, complex64 (two floats) for TF32, TF32X3 and
+ *            FP32; ld1, ld2 >= n in complex entries; device or host (read only).
+ *   alpha, beta, r_out, resid_out : as gsvd_rand_solve (the GSVs of a complex pair are real).
+ * The library solves the realified pair: each entry a + ib becomes the real 2 x 2 block
+ * [[a, -b], [b, a]], a map that carries products and conjugate transposes over, so the real
+ * method on the realified pair with the realified Omega (and k, oversample doubled) runs the
+ * complex method's arithmetic and returns each complex GSV twice; one of each two is returned.
+ * The realified matrices (4 m n and 4 p n reals) live in device memory owned by h, grown on
+ * demand and freed by gsvd_rand_destroy.  k + oversample <= min(m, p, n) and <= 112 (FP64) or
+ * 128 (the others).  gsvd_rand_factors is not available after a complex solve.
+ * Errors: ARG, OOM, CUDA, UNSUPPORTED (BF16, adaptive, learned or basis-only contexts),
+ * NONFINITE, BREAKDOWN.  Synchronises cfg->stream. */
+int gsvd_rand_solve_complex(gsvd_rand_t h, const void *G1, int64_t m, int64_t ld1, const void *G2,
+                            int64_t p, int64_t ld2, int64_t n, int k, int oversample, int q,
+                            uint64_t seed, double *alpha, double *beta, int *r_out, double *resid_out);
+
 /* One pair of a batched solve: the arguments of gsvd_rand_solve, the Philox counter word
  * 'pair' (side s of this pair uses counter words (t, pair, s, stream)), and the
  * per-pair return code written by gsvd_rand_solve_batched. */

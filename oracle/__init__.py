@@ -15,6 +15,9 @@ algorithms for GSVs", arXiv:2404.09459):
   gsvd.rand_gsvd_adaptive  Algorithm 2 on the Algorithm 1 bases
   gsvd.metrics         theta, rho, P1, P2, D1, D2 of Section 1
   gsvd.perturbation_E  the E of Lemma "per" / Theorem "exp" (Section 3)
+  gsvd.rand_gsvd_complex, direct_gsvd_complex, pencil_gsvd_complex, gaussian_complex
+                       the same over C (eq. (gsvd1) is stated over C; Section 4.1 is complex)
+  gsvd.realify         the real 2 x 2-block form of a complex matrix (a pin of the complex path)
 
 Every function is pinned by a `-m "not gpu"` test against values fixed by the
 paper or by mathematics (known-answer vectors, closed forms, invariants,

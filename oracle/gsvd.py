@@ -334,3 +334,83 @@ def alg2_literal(B1: np.ndarray, B2: np.ndarray):
         beta = np.concatenate([np.zeros(n - b.size), b])
         alpha = np.sqrt(np.clip(1.0 - beta ** 2, 0.0, None))
     return alpha, beta
+
+
+# ----------------------------------------------------------------------------------------------
+# Complex pairs.  Section 1 states the GSVD over C (eq. (gsvd1): G1 = U Sigma1 R, G2 = V Sigma2 R
+# with unitary U, V) and the synthetic experiments of Section 4.1 are complex; the randomized
+# method is the same with conjugate transposes and a complex Gaussian test matrix.
+# ----------------------------------------------------------------------------------------------
+def gaussian_complex(n: int, l: int, seed: int, pair: int = 0, side: int = 0, stream: int = STREAM_FIXED):
+    """Complex Gaussian test matrix (n x l): Omega[j, c] = g[j, 2c] + i g[j, 2c + 1], g the real
+    Philox/Box-Muller stream of an n x 2l matrix, so that the real and imaginary parts of each
+    entry are the two normals of one Box-Muller pair (independent, circularly symmetric)."""
+    g = gaussian(n, 2 * l, seed, pair, side, stream)
+    return g[:, 0::2] + 1j * g[:, 1::2]
+
+
+def basis_fixed_complex(G, l: int, q: int, seed: int, pair: int = 0, side: int = 0):
+    """The fixed-rank range finder over C: Y = G Omega, Q = orth(Y); q times Z = orth(G^H Q),
+    Q = orth(G Z) (complex Householder QR)."""
+    n = G.shape[1]
+    Q = orth(G @ gaussian_complex(n, l, seed, pair, side, STREAM_FIXED))
+    for _ in range(q):
+        Z = orth(G.conj().T @ Q)
+        Q = orth(G @ Z)
+    return Q
+
+
+def rand_gsvd_complex(G1, G2, k: int, oversample: int, q: int, seed: int, pair: int = 0):
+    """Algorithm 2 over C with the fixed-rank bases: B_s = Q_s^H G_s, then the GSVs of the
+    stack [B1; B2] truncated to r = k (thin SVD and CS split, as gsv_from_stack; the singular
+    values of complex blocks are real).  Returns alpha, beta (k each), the relative residuals
+    ||G_s - Q_s B_s||_F / ||G_s||_F, Q_s and B_s."""
+    G1 = np.asarray(G1, dtype=np.complex128)
+    G2 = np.asarray(G2, dtype=np.complex128)
+    l = k + oversample
+    out, Bs = {}, []
+    for s, G in enumerate((G1, G2)):
+        Q = basis_fixed_complex(G, l, q, seed, pair, s)
+        B = Q.conj().T @ G
+        out[f"Q{s + 1}"] = Q
+        out[f"B{s + 1}"] = B
+        out[f"resid{s + 1}"] = np.linalg.norm(G - Q @ B) / max(np.linalg.norm(G), 1e-300)
+        Bs.append(B)
+    alpha, beta, svals = gsv_from_stack(np.vstack(Bs), Bs[0].shape[0], k)
+    out.update(alpha=alpha, beta=beta, stack_svals=svals)
+    return out
+
+
+def direct_gsvd_complex(G1, G2, r: int | None = None):
+    """The direct dense GSVD of a complex pair (thin SVD of the stack, CS split)."""
+    G1 = np.asarray(G1, dtype=np.complex128)
+    G2 = np.asarray(G2, dtype=np.complex128)
+    r = G1.shape[1] if r is None else r
+    alpha, beta, _ = gsv_from_stack(np.vstack([G1, G2]), G1.shape[0], r)
+    return alpha, beta
+
+
+def pencil_gsvd_complex(G1, G2):
+    """Brute force for tiny full-rank complex pairs: alpha^2 are the eigenvalues of the
+    Hermitian-definite pencil (G1^H G1, G1^H G1 + G2^H G2), beta^2 those of (G2^H G2, same)."""
+    A1 = G1.conj().T @ G1
+    A2 = G2.conj().T @ G2
+    Bm = A1 + A2
+    a2 = sla.eigh(A1, Bm, eigvals_only=True)
+    b2 = sla.eigh(A2, Bm, eigvals_only=True)
+    return np.sqrt(np.clip(a2, 0.0, None))[::-1].copy(), np.sqrt(np.clip(b2, 0.0, None))
+
+
+def realify(G) -> np.ndarray:
+    """The real 2m x 2n matrix of a complex m x n one, each entry a + ib as the 2 x 2 block
+    [[a, -b], [b, a]]: the representation of C as real 2 x 2 matrices, a ring homomorphism
+    (products and conjugate transposes carry over), so every singular value of G appears twice
+    in it and every GSV of a complex pair twice in the real pair."""
+    G = np.asarray(G, dtype=np.complex128)
+    m, n = G.shape
+    R = np.empty((2 * m, 2 * n))
+    R[0::2, 0::2] = G.real
+    R[0::2, 1::2] = -G.imag
+    R[1::2, 0::2] = G.imag
+    R[1::2, 1::2] = G.real
+    return R

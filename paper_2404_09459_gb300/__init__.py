@@ -27,7 +27,7 @@ EXPORTS = ("gsvd_rand_config_init", "gsvd_rand_create", "gsvd_rand_destroy", "gs
            "gsvd_rand_probe_features", "gsvd_rand_mlp_forward", "gsvd_rand_mlp_loss_grad", "gsvd_rand_mlp_adam",
            "gsvd_rand_mlp_train", "gsvd_rand_mlp_set", "gsvd_rand_mlp_load", "gsvd_rand_last_plan",
            "gsvd_rand_solve_grouped", "gsvd_rand_grouped_info", "gsvd_rand_chol64_retries",
-           "gsvd_rand_product_shapes", "gsvd_rand_factors")
+           "gsvd_rand_product_shapes", "gsvd_rand_factors", "gsvd_rand_solve_complex")
 NOALLOC_MAX_N = 32768
 FLAG_PROFILE = 2
 FLAG_BF16_SPLIT_POWER = 4
@@ -77,6 +77,7 @@ def load_library(path: str | None = None):
     lib.gsvd_rand_last_error.argtypes = [vp]
     lib.gsvd_rand_last_error.restype = C.c_char_p
     lib.gsvd_rand_solve.argtypes = [vp, vp, i64, i64, vp, i64, i64, i64, i32, i32, i32, u64, vp, vp, vp, vp]
+    lib.gsvd_rand_solve_complex.argtypes = [vp, vp, i64, i64, vp, i64, i64, i64, i32, i32, i32, u64, vp, vp, vp, vp]
     lib.gsvd_rand_metrics.argtypes = [vp, vp, vp, i32, i32, i32, vp, vp, vp, vp, vp]
     lib.gsvd_rand_gaussian.argtypes = [vp, i64, i64, u64, u32, u32, u32, vp]
     lib.gsvd_rand_philox.argtypes = [vp, u64, u64, u32, u32, u32, vp]
@@ -108,6 +109,27 @@ def load_library(path: str | None = None):
     if path == LIB:
         _lib = lib
     return lib
+
+
+def _cmat_ptr(x, want_dtype: str):
+    """(pointer, rows, cols, ld in complex entries, on_device, keepalive) of a row-major complex
+    matrix: complex128 for "c128", complex64 for "c64" (interleaved (re, im) pairs)."""
+    if _is_torch(x):
+        import torch
+        dt = {"c128": torch.complex128, "c64": torch.complex64}[want_dtype]
+        if x.dtype != dt:
+            raise TypeError(f"expected {dt}, got {x.dtype}")
+        if x.dim() != 2 or x.stride(1) != 1:
+            raise ValueError("matrix must be 2-D with unit column stride (row-major)")
+        return x.data_ptr(), x.shape[0], x.shape[1], max(x.stride(0), x.shape[1]), x.is_cuda, x
+    import numpy as np
+    dt = {"c128": np.complex128, "c64": np.complex64}[want_dtype]
+    a = np.asarray(x)
+    if a.dtype != dt:
+        raise TypeError(f"expected {np.dtype(dt)}, got {a.dtype}")
+    if a.ndim != 2 or a.strides[1] != a.itemsize or a.strides[0] % a.itemsize:
+        raise ValueError("matrix must be 2-D row-major")
+    return a.ctypes.data, a.shape[0], a.shape[1], max(a.strides[0] // a.itemsize, a.shape[1]), False, a
 
 
 def _is_torch(x):
@@ -232,6 +254,24 @@ class Context:
         rr = r.value
         self._last_shape = (m, p, n1, rr)
         return dict(alpha=alpha[:rr], beta=beta[:rr], r=rr, resid=(resid[0], resid[1]))
+
+    def solve_complex(self, G1, G2, k: int, oversample: int = 10, q: int = 1, seed: int = 0):
+        """Randomized GSVs of a complex pair (gsvd_rand_solve_complex): complex128 matrices on
+        the FP64 path, complex64 otherwise.  dict(alpha, beta, r, resid); outputs live where G1
+        lives."""
+        want = "c128" if self.prec == "fp64" else "c64"
+        p1, m, n1, ld1, dev1, k1 = _cmat_ptr(G1, want)
+        p2, p, n2, ld2, dev2, k2 = _cmat_ptr(G2, want)
+        if n1 != n2:
+            raise ValueError("G1 and G2 must have the same number of columns")
+        alpha, pa = self._out_vec(dev1, k)
+        beta, pb = self._out_vec(dev1, k)
+        r = C.c_int(0)
+        resid = (C.c_double * 2)()
+        rc = self.lib.gsvd_rand_solve_complex(self.h, p1, m, ld1, p2, p, ld2, n1, k, oversample, q, seed, pa, pb,
+                                              C.addressof(r), C.addressof(resid))
+        self._check(rc)
+        return dict(alpha=alpha[:r.value], beta=beta[:r.value], r=r.value, resid=(resid[0], resid[1]))
 
     def factors(self):
         """GSVD factors of the last solve(): dict(U (m x r), V (p x r), R (r x n)), FP64 CUDA tensors,

@@ -67,6 +67,10 @@ struct gsvd_rand_ctx {
   size_t gstage_bytes = 0;
   char* gbounce = nullptr;     // contiguous landing area of one host matrix before its rows are padded
   size_t gbounce_bytes = 0;
+  // complex pairs: the realified matrices, staged host inputs and the doubled GSVs
+  char* cplx = nullptr;
+  size_t cplx_bytes = 0;
+  bool cplx_sketch = false;    // the solve in progress draws rho(Omega) of a complex Omega
   // learned proposal: network (params | norm), then features, logits and scratch of one pair
   float* mlp_dev = nullptr;
   bool mlp_ready = false;
@@ -517,6 +521,9 @@ struct Solver {
       if (bf16)
         CU(launch_gaussian_kmajor_bf16(b[s].Xh, pl.ldx, pl.n, pl.l, (int)pl.lx, seed, h->pair_word, (uint32_t)s,
                                        GSVD_RAND_STREAM_FIXED, st));
+      else if (h->cplx_sketch)  // a complex pair solved as its realified form
+        CU(launch_gaussian_kmajor_cplx<T>(b[s].Xt, pl.ldx, pl.n, pl.l, (int)pl.lx, seed, h->pair_word, (uint32_t)s,
+                                          GSVD_RAND_STREAM_FIXED, st));
       else
         CU(launch_gaussian_kmajor<T>(b[s].Xt, pl.ldx, pl.n, pl.l, (int)pl.lx, seed, h->pair_word, (uint32_t)s,
                                      GSVD_RAND_STREAM_FIXED, st));
@@ -679,13 +686,18 @@ constexpr int oa_iters() {
 // of K = S S^T (FP64 Gram; FP32 tridiagonal start; FP64 Ogita-Aishima
 // refinement of the full eigenbasis), then the CS split: W = eigenvectors of
 // Z1^T Z1 (the same two stages), alpha_i = ||Z1 w_i||, beta_i = ||Z2 w_i||.
+// The mixed paths (T = float) run the products in double-float arithmetic (about 2^-48
+// relative, several times GB300's FP64 rate), with K scaled by a power of two into FP32's
+// exponent range; the plain path keeps FP64.
 template <typename T>
 int small_gsvd(gsvd_rand_ctx* h, cudaStream_t st, DevStatus* st_dev, const T* S, int64_t ldn, int l1,
                int L, int64_t n, int r, SmallBufs& sb) {
+  const bool df = !std::is_same<T, double>::value;
   {
     ProfScope ps(h, GSVD_RAND_STAGE_SMALL_GRAM);
     CU((launch_dgemm_small<T, T>(L, L, (int)n, S, ldn, 0, S, ldn, 1, sb.K, L, 1.0, 0.0, sb.work,
-                                 sb.work_elems, st)));
+                                 sb.work_elems, st, df)));
+    if (df) CU(launch_pow2_scale(sb.K, L, st));
   }
   {
     ProfScope ps(h, GSVD_RAND_STAGE_SMALL_JACOBI);
@@ -696,7 +708,7 @@ int small_gsvd(gsvd_rand_ctx* h, cudaStream_t st, DevStatus* st_dev, const T* S,
   {
     ProfScope ps(h, GSVD_RAND_STAGE_SMALL_REFINE);
     for (int it = 0; it < oa_iters<T>(); ++it) {
-      CU(launch_oa_refine(sb.K, L, sb.X, sb.lam, sb.work, sb.work_elems, st));
+      CU(launch_oa_refine(sb.K, L, sb.X, sb.lam, sb.work, sb.work_elems, st, df));
       // after the first step every eigenvector outside the clusters has squared its start
       // error, so the cluster that straddles the cut (of any size up to L) is split then,
       // and the remaining steps (two on the mixed paths) refine the split columns
@@ -708,13 +720,14 @@ int small_gsvd(gsvd_rand_ctx* h, cudaStream_t st, DevStatus* st_dev, const T* S,
   const int l2 = L - l1;
   const double* Z2 = sb.Zr + (int64_t)l1 * r;
   CU((launch_dgemm_small<double, double>(r, r, l1, sb.Zr, r, 1, sb.Zr, r, 0, sb.C1, r, 1.0, 0.0, sb.work,
-                                         sb.work_elems, st)));
+                                         sb.work_elems, st, df)));
   CU(launch_eig_f32(sb.C1, r, sb.Wv, sb.mu, sb.jscratch, st));
-  for (int it = 0; it < oa_iters<T>(); ++it) CU(launch_oa_refine(sb.C1, r, sb.Wv, sb.mu, sb.work, sb.work_elems, st));
+  for (int it = 0; it < oa_iters<T>(); ++it)
+    CU(launch_oa_refine(sb.C1, r, sb.Wv, sb.mu, sb.work, sb.work_elems, st, df));
   CU((launch_dgemm_small<double, double>(l1, r, r, sb.Zr, r, 0, sb.Wv, r, 0, sb.U1, r, 1.0, 0.0, sb.work,
-                                         sb.work_elems, st)));
+                                         sb.work_elems, st, df)));
   CU((launch_dgemm_small<double, double>(l2, r, r, Z2, r, 0, sb.Wv, r, 0, sb.U1 + (int64_t)l1 * r, r, 1.0, 0.0,
-                                         sb.work, sb.work_elems, st)));
+                                         sb.work, sb.work_elems, st, df)));
   CU(launch_cs_norms(sb.U1, l1, sb.U1 + (int64_t)l1 * r, l2, r, sb.alpha, sb.beta, st));
   return GSVD_RAND_OK;
 }
@@ -1870,7 +1883,14 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
     const size_t off = A.add(t);
     const int mL = maxL;
     push([off, np, mL](const unsigned char* d, cudaStream_t st) {
-      return launch_dgemm_b<float, float>(reinterpret_cast<const DgemmB*>(d + off), np, mL, mL, st);
+      return launch_dgemm_b<float, float>(reinterpret_cast<const DgemmB*>(d + off), np, mL, mL, st, true);
+    });
+    // each K by a power of two into FP32's exponent range (the double-float refinement)
+    std::vector<EigB> ks(np);
+    for (int i = 0; i < np; ++i) ks[i] = EigB{gb.prs[i].K, nullptr, nullptr, nullptr, 0.f, gb.prs[i].L};
+    const size_t koff = A.add(ks);
+    push([koff, np](const unsigned char* d, cudaStream_t st) {
+      return launch_pow2_scale_b(reinterpret_cast<const EigB*>(d + koff), np, st);
     });
   }
   // FP32 eigensolver starts, split by size class
@@ -1912,7 +1932,7 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
     for (int it = 0; it < 3; ++it) {
       push([ot, od, np, mN](const unsigned char* d, cudaStream_t st) {
         return launch_oa_refine_b(reinterpret_cast<const OaB*>(d + ot), reinterpret_cast<const DgemmB*>(d + od), np,
-                                  mN, st);
+                                  mN, st, true);
       });
       if (!c1 && it == 0)  // the cut cluster split after the first step, as in the single solve
         push([ot, np, mN](const unsigned char* d, cudaStream_t st) {
@@ -1956,7 +1976,7 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
     const size_t off = A.add(t);
     const int mk = maxk;
     push([off, np, mk](const unsigned char* d, cudaStream_t st) {
-      return launch_dgemm_b<double, double>(reinterpret_cast<const DgemmB*>(d + off), np, mk, mk, st);
+      return launch_dgemm_b<double, double>(reinterpret_cast<const DgemmB*>(d + off), np, mk, mk, st, true);
     });
   }
   add_eig(true);
@@ -1982,7 +2002,7 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
     const size_t off = A.add(t);
     const int ml = maxl1, mk = maxk, n2 = 2 * np;
     push([off, n2, ml, mk](const unsigned char* d, cudaStream_t st) {
-      return launch_dgemm_b<double, double>(reinterpret_cast<const DgemmB*>(d + off), n2, ml, mk, st);
+      return launch_dgemm_b<double, double>(reinterpret_cast<const DgemmB*>(d + off), n2, ml, mk, st, true);
     });
   }
   {
@@ -2363,6 +2383,93 @@ int solve_grouped_staged(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs) {
   return rc;
 }
 
+// A complex pair {G1, G2} through its realified form: rho maps each entry a + ib to the real
+// 2 x 2 block [[a, -b], [b, a]], a ring homomorphism that carries products and conjugate
+// transposes over, so the randomized method on (rho(G1), rho(G2)) with the sketch rho(Omega)
+// of a complex Gaussian Omega, k and oversample doubled, computes exactly the complex method's
+// bases (realified) and returns every complex GSV twice; the pairs are taken one of each two.
+// The realified matrices (2M x 2n, rows padded to 16 bytes) live in device memory owned by h.
+int solve_complex(gsvd_rand_ctx* h, const void* G1, int64_t m, int64_t ld1, const void* G2, int64_t p, int64_t ld2,
+                  int64_t n, int k, int os, int q, uint64_t seed, double* alpha, double* beta, int* r_out,
+                  double* resid_out) {
+  const int prec = h->cfg.prec;
+  if (prec == GSVD_RAND_BF16)
+    return fail(h, GSVD_RAND_ERR_UNSUPPORTED, "complex pairs run in FP64, FP32, TF32 or 3xTF32, not BF16");
+  if (h->cfg.adaptive || h->cfg.use_learned || (h->cfg.flags & GSVD_RAND_FLAG_BASIS_ONLY))
+    return fail(h, GSVD_RAND_ERR_UNSUPPORTED, "complex pairs take fixed-rank solves with the compressed-pair GSVD");
+  const bool f64 = prec == GSVD_RAND_FP64;
+  const size_t es = f64 ? sizeof(double) : sizeof(float);  // bytes of one real part
+  const int64_t l = (int64_t)k + os;
+  if (l > std::min(std::min(m, p), n))
+    return fail(h, GSVD_RAND_ERR_ARG, "k + oversample = %lld exceeds min(m, p, n)", (long long)l);
+  if (2 * l > (f64 ? 224 : 256))
+    return fail(h, GSVD_RAND_ERR_ARG, "k + oversample = %lld exceeds the complex limit %d", (long long)l,
+                f64 ? 112 : 128);
+  CU(cudaSetDevice(h->cfg.device));
+  const int64_t ldr = round_up(2 * n, (int64_t)(16 / es));
+  const bool dv1 = is_device_ptr(G1), dv2 = is_device_ptr(G2);
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t r1 = al((size_t)2 * m * ldr * es), r2 = al((size_t)2 * p * ldr * es);
+  const size_t stage = al((size_t)std::max(dv1 ? 0 : m, dv2 ? 0 : p) * 2 * n * es);
+  const size_t outs = al(4 * (size_t)k * sizeof(double));
+  const size_t need = r1 + r2 + stage + outs;
+  if (need > h->cplx_bytes) {
+    CU(cudaStreamSynchronize(h->stream));
+    if (h->cplx) cudaFree(h->cplx);
+    h->cplx = nullptr;
+    h->cplx_bytes = 0;
+    if (cudaMalloc(&h->cplx, need) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, GSVD_RAND_ERR_OOM, "workspace of the realified complex pair (%zu bytes) failed", need);
+    }
+    h->cplx_bytes = need;
+  }
+  char* R1 = h->cplx;
+  char* R2 = R1 + r1;
+  char* stg = R2 + r2;
+  double* ah = reinterpret_cast<double*>(stg + stage);
+  double* bh = ah + 2 * k;
+  const void* src[2] = {G1, G2};
+  const int64_t Ms[2] = {m, p}, lds[2] = {ld1, ld2};
+  char* Rs[2] = {R1, R2};
+  for (int s = 0; s < 2; ++s) {
+    const void* g = src[s];
+    int64_t ldg = lds[s];
+    if (!(s ? dv2 : dv1)) {  // host: land the rows (n complex entries each) contiguously first
+      CU(copy_rows(stg, (size_t)2 * n * es, g, (size_t)2 * ldg * es, (size_t)2 * n * es, (size_t)Ms[s],
+                   cudaMemcpyHostToDevice, h->stream));
+      g = stg;
+      ldg = n;
+    }
+    if (f64)
+      CU(launch_realify<double>(static_cast<const double*>(g), ldg, Ms[s], n, reinterpret_cast<double*>(Rs[s]), ldr,
+                                h->stream));
+    else
+      CU(launch_realify<float>(static_cast<const float*>(g), ldg, Ms[s], n, reinterpret_cast<float*>(Rs[s]), ldr,
+                               h->stream));
+  }
+  h->cplx_sketch = true;
+  const int rc = solve_dispatch(h, false, R1, 2 * m, ldr, R2, 2 * p, ldr, 2 * n, 2 * k, 2 * os, q, seed, ah, bh,
+                                nullptr, resid_out);
+  h->cplx_sketch = false;
+  h->fact.valid = false;  // the factors of the realified pair are not the complex pair's
+  if (rc) return rc;
+  // every complex GSV appears twice (alpha_hat non-increasing): one of each two
+  const bool ad = is_device_ptr(alpha), bd = is_device_ptr(beta);
+  CU(cudaMemcpy2DAsync(alpha, sizeof(double), ah, 2 * sizeof(double), sizeof(double), (size_t)k,
+                       ad ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaMemcpy2DAsync(beta, sizeof(double), bh, 2 * sizeof(double), sizeof(double), (size_t)k,
+                       bd ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  if (r_out) {
+    if (is_device_ptr(r_out))
+      CU(cudaMemcpy(r_out, &k, sizeof(int), cudaMemcpyHostToDevice));
+    else
+      *r_out = k;
+  }
+  return GSVD_RAND_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -2434,6 +2541,7 @@ int gsvd_rand_destroy(gsvd_rand_t h) {
   if (h->tab_host) cudaFreeHost(h->tab_host);
   if (h->gstage) cudaFree(h->gstage);
   if (h->gbounce) cudaFree(h->gbounce);
+  if (h->cplx) cudaFree(h->cplx);
   delete h;
   return GSVD_RAND_OK;
 }
@@ -2507,6 +2615,21 @@ int gsvd_rand_solve(gsvd_rand_t h, const void* G1, int64_t m, int64_t ld1, const
   // adaptive: Algorithm 1 bases (k = output capacity; oversample and q are not used)
   return solve_dispatch(h, h->cfg.adaptive != 0, G1, m, ld1, G2, p, ld2, n, k, oversample, q, seed, alpha, beta,
                         r_out, resid_out);
+}
+
+int gsvd_rand_solve_complex(gsvd_rand_t h, const void* G1, int64_t m, int64_t ld1, const void* G2, int64_t p,
+                            int64_t ld2, int64_t n, int k, int oversample, int q, uint64_t seed, double* alpha,
+                            double* beta, int* r_out, double* resid_out) {
+  if (!h) return GSVD_RAND_ERR_ARG;
+  if (!G1 || !G2 || !alpha || !beta) return fail(h, GSVD_RAND_ERR_ARG, "null pointer argument");
+  if (m < 1 || p < 1 || n < 1) return fail(h, GSVD_RAND_ERR_ARG, "empty matrix (m=%lld p=%lld n=%lld)",
+                                           (long long)m, (long long)p, (long long)n);
+  if (ld1 < n || ld2 < n) return fail(h, GSVD_RAND_ERR_ARG, "leading dimension smaller than n");
+  if (k < 1 || oversample < 0 || q < 0 || q > 16)
+    return fail(h, GSVD_RAND_ERR_ARG, "need k >= 1, oversample >= 0, 0 <= q <= 16");
+  if (n > (int64_t)1 << 29 || m > (int64_t)1 << 39 || p > (int64_t)1 << 39)
+    return fail(h, GSVD_RAND_ERR_ARG, "dimension too large");
+  return solve_complex(h, G1, m, ld1, G2, p, ld2, n, k, oversample, q, seed, alpha, beta, r_out, resid_out);
 }
 
 int gsvd_rand_solve_batched(gsvd_rand_t h, int npairs, gsvd_rand_pair* pairs, int workers) {

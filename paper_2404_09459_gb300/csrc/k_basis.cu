@@ -83,6 +83,73 @@ __global__ void gaussian_kmajor_kernel(T* Xt, int64_t ldx, int64_t n, int l, int
   Xt[(int64_t)j * ldx + i] = v;
 }
 
+// The real 2n x 2l test matrix of a complex pair (K-major, as gaussian_kmajor_kernel writes
+// it): rho(Omega), Omega (n x l) complex with Omega[j][c] = g(e) + i g(e + 1), e = 2 (j l + c),
+// g the real Philox/Box-Muller stream of an n x 2l matrix; each complex entry a + ib becomes the
+// 2 x 2 block [[a, -b], [b, a]] (rows 2j, 2j + 1 and columns 2c, 2c + 1 of rho(Omega)).
+template <typename T>
+__global__ void gaussian_kmajor_cplx_kernel(T* Xt, int64_t ldx, int64_t n2, int l2, int lrows, uint32_t k0,
+                                            uint32_t k1, uint32_t pair, uint32_t side, uint32_t stream) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // column of Xt (row of rho(Omega))
+  int j = blockIdx.y;                                          // row of Xt (column of rho(Omega))
+  if (i >= ldx || j >= lrows) return;
+  T v = T(0);
+  if (i < n2 && j < l2) {
+    const int64_t e = (i >> 1) * (int64_t)l2 + (j & ~1);  // complex entry (i / 2, j / 2): real part
+    const int a = (int)(i & 1), b = j & 1;
+    v = a == b ? gaussian_at<T>(e, k0, k1, pair, side, stream) : gaussian_at<T>(e + 1, k0, k1, pair, side, stream);
+    if (a == 0 && b == 1) v = -v;
+  }
+  Xt[(int64_t)j * ldx + i] = v;
+}
+
+template <typename T>
+cudaError_t launch_gaussian_kmajor_cplx(T* Xt, int64_t ldx, int64_t n2, int l2, int lrows, uint64_t seed,
+                                        uint32_t pair, uint32_t side, uint32_t stream, cudaStream_t st) {
+  if ((n2 & 1) || (l2 & 1)) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)cdiv(ldx, 256), (unsigned)lrows);
+  gaussian_kmajor_cplx_kernel<T><<<grid, 256, 0, st>>>(Xt, ldx, n2, l2, lrows, (uint32_t)seed,
+                                                       (uint32_t)(seed >> 32), pair, side, stream);
+  return launched();
+}
+template cudaError_t launch_gaussian_kmajor_cplx<double>(double*, int64_t, int64_t, int, int, uint64_t,
+                                                         uint32_t, uint32_t, uint32_t, cudaStream_t);
+template cudaError_t launch_gaussian_kmajor_cplx<float>(float*, int64_t, int64_t, int, int, uint64_t,
+                                                        uint32_t, uint32_t, uint32_t, cudaStream_t);
+
+// R = rho(G): G (M x n complex, interleaved (re, im) pairs of T, row stride ldg complex entries)
+// into the real 2M x 2n matrix R (row stride ldr), entry a + ib as the block [[a, -b], [b, a]].
+// A thread per complex entry; rows 2i and 2i + 1 of R are written as pairs.
+template <typename T>
+__global__ void realify_kernel(const T* __restrict__ G, int64_t ldg, int64_t M, int64_t n, T* __restrict__ R,
+                               int64_t ldr) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = blockIdx.y;
+  if (j >= n || i >= M) return;
+  const T a = G[2 * (i * ldg + j)], b = G[2 * (i * ldg + j) + 1];
+  T* r0 = R + (2 * i) * ldr + 2 * j;
+  T* r1 = r0 + ldr;
+  r0[0] = a;
+  r0[1] = -b;
+  r1[0] = b;
+  r1[1] = a;
+}
+
+template <typename T>
+cudaError_t launch_realify(const T* G, int64_t ldg, int64_t M, int64_t n, T* R, int64_t ldr, cudaStream_t st) {
+  if (M < 1 || n < 1) return cudaSuccess;
+  for (int64_t r0 = 0; r0 < M; r0 += 65535) {
+    const int64_t rows = std::min<int64_t>(65535, M - r0);
+    dim3 grid((unsigned)cdiv(n, 256), (unsigned)rows);
+    realify_kernel<T><<<grid, 256, 0, st>>>(G + 2 * r0 * ldg, ldg, rows, n, R + 2 * r0 * ldr, ldr);
+    cudaError_t e = launched();
+    if (e) return e;
+  }
+  return cudaSuccess;
+}
+template cudaError_t launch_realify<double>(const double*, int64_t, int64_t, int64_t, double*, int64_t, cudaStream_t);
+template cudaError_t launch_realify<float>(const float*, int64_t, int64_t, int64_t, float*, int64_t, cudaStream_t);
+
 template <typename T>
 cudaError_t launch_gaussian_kmajor(T* Xt, int64_t ldx, int64_t n, int l, int lrows, uint64_t seed,
                                    uint32_t pair, uint32_t side, uint32_t stream, cudaStream_t st) {

@@ -11,6 +11,7 @@
 //     Indust. Appl. Math. 35, 2018), whose work is FP64 GEMMs again.
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 
 #include "kernels.h"
 
@@ -24,7 +25,121 @@ constexpr int SG_T = 32, SG_BK = 32;
 static_assert(SG_T == 32 && SG_BK == 32, "dgemm_small_kernel's loader assumes 32 x 32 tiles");
 constexpr int SG_KGRAIN = 8;  // split-K chunks are multiples of 8 (partial tiles are zero-filled)
 
-template <typename TA, typename TB>
+// ----------------------------------------------------------------------------
+// Double-float arithmetic (the mixed-precision paths).  GB300 runs FP32 at 64x its FP64 rate,
+// so the refinement products of the mixed paths (1e-4 target) keep each operand as an
+// unevaluated sum hi + lo of two FP32 numbers (Dekker, Numer. Math. 18, 1971) and accumulate
+// with error-free transformations: the FP32 product of the high parts with its exact rounding
+// error from an FMA, the cross terms hi*lo, and Knuth's TwoSum for the running sum (Knuth,
+// TAOCP vol. 2, 4.2.2).  Relative precision about 2^-48 per product, against 2^-53 in FP64; the
+// plain FP64 path keeps FP64.  The _rn intrinsics keep the compiler from contracting the
+// TwoSum steps into FMAs, which would break their exactness.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ void df_fma(const float2 a, const float2 b, float& sh, float& sl) {
+  const float ph = __fmul_rn(a.x, b.x);
+  const float pe = fmaf(a.x, b.x, -ph);                 // exact rounding error of a.x b.x
+  const float pl = fmaf(a.x, b.y, fmaf(a.y, b.x, pe));  // plus the cross terms
+  const float s = __fadd_rn(sh, ph);
+  const float bb = __fsub_rn(s, sh);
+  const float e = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(ph, bb));  // sh + ph - s exactly
+  sh = s;
+  sl = __fadd_rn(sl, __fadd_rn(e, pl));
+}
+// (sh, sl) back to |sl| <= ulp(sh) / 2 (Dekker's fast two-sum; |sh| >= |sl| by construction).
+__device__ __forceinline__ void df_renorm(float& sh, float& sl) {
+  const float s = __fadd_rn(sh, sl);
+  sl = __fsub_rn(sl, __fsub_rn(s, sh));
+  sh = s;
+}
+// One operand element into a tile slot: FP64 as is, or (DF) as its hi + lo FP32 pair stored in
+// the same 8 bytes (hi = nearest FP32, lo = nearest FP32 to the remainder).
+template <bool DF, typename T>
+__device__ __forceinline__ void sg_put(double* slot, T v) {
+  if constexpr (DF) {
+    float h, l;
+    if constexpr (std::is_same<T, float>::value) {
+      h = v;
+      l = 0.f;
+    } else {
+      h = __double2float_rn(v);
+      l = __double2float_rn(v - (double)h);
+    }
+    *reinterpret_cast<float2*>(slot) = make_float2(h, l);
+  } else {
+    *slot = (double)v;
+  }
+}
+// The 2 x 2 outputs of a thread over one k-tile (kk < kk_end): FP64 FMAs, or double-float.
+template <bool DF>
+__device__ __forceinline__ void sg_tile(const double (*As)[SG_T + 1], const double (*Bs)[SG_T + 1], int kk_end,
+                                        int ty, int tx, double (&acc)[2][2], float (&dh)[2][2], float (&dl)[2][2]) {
+  if constexpr (DF) {
+#pragma unroll 4
+    for (int kk = 0; kk < kk_end; ++kk) {
+      const float2 a0 = *reinterpret_cast<const float2*>(&As[kk][ty * 2]);
+      const float2 a1 = *reinterpret_cast<const float2*>(&As[kk][ty * 2 + 1]);
+      const float2 b0 = *reinterpret_cast<const float2*>(&Bs[kk][tx * 2]);
+      const float2 b1 = *reinterpret_cast<const float2*>(&Bs[kk][tx * 2 + 1]);
+      df_fma(a0, b0, dh[0][0], dl[0][0]);
+      df_fma(a0, b1, dh[0][1], dl[0][1]);
+      df_fma(a1, b0, dh[1][0], dl[1][0]);
+      df_fma(a1, b1, dh[1][1], dl[1][1]);
+    }
+#pragma unroll
+    for (int m = 0; m < 2; ++m)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) df_renorm(dh[m][q], dl[m][q]);
+  } else {
+#pragma unroll 8
+    for (int kk = 0; kk < kk_end; ++kk) {
+      const double a0 = As[kk][ty * 2], a1 = As[kk][ty * 2 + 1];
+      const double b0 = Bs[kk][tx * 2], b1 = Bs[kk][tx * 2 + 1];
+      acc[0][0] = fma(a0, b0, acc[0][0]);
+      acc[0][1] = fma(a0, b1, acc[0][1]);
+      acc[1][0] = fma(a1, b0, acc[1][0]);
+      acc[1][1] = fma(a1, b1, acc[1][1]);
+    }
+  }
+}
+template <bool DF>
+__device__ __forceinline__ double sg_out(const double (&acc)[2][2], const float (&dh)[2][2], const float (&dl)[2][2],
+                                         int m, int q) {
+  return DF ? (double)dh[m][q] + (double)dl[m][q] : acc[m][q];
+}
+
+// A (N x N, ld N) scaled by the power of two that brings its largest |diagonal entry| into
+// [1, 2): exact, and it keeps a Gram of any scale inside FP32's exponent range for the
+// double-float products (the eigenvectors do not depend on the scale).  One CTA per problem.
+__device__ __forceinline__ void pow2_scale_body(double* A, int N) {
+  __shared__ double s_m[8];
+  double m = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) m = fmax(m, fabs(A[(int64_t)i * N + i]));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) s_m[threadIdx.x >> 5] = m;
+  __syncthreads();
+  double mx = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, s_m[w]);
+  if (!(mx > 0.0) || !isfinite(mx)) return;
+  const double f = ldexp(1.0, -ilogb(mx));
+  for (int64_t e = threadIdx.x; e < (int64_t)N * N; e += blockDim.x) A[e] *= f;
+}
+__global__ __launch_bounds__(256) void pow2_scale_kernel(double* A, int N) { pow2_scale_body(A, N); }
+__global__ __launch_bounds__(256) void pow2_scale_b_kernel(const EigB* __restrict__ tab) {
+  const EigB& e = tab[blockIdx.x];
+  pow2_scale_body(const_cast<double*>(e.A), e.N);
+}
+cudaError_t launch_pow2_scale(double* A, int N, cudaStream_t st) {
+  if (N < 1) return cudaSuccess;
+  pow2_scale_kernel<<<1, 256, 0, st>>>(A, N);
+  return launched();
+}
+cudaError_t launch_pow2_scale_b(const EigB* tab, int nprob, cudaStream_t st) {
+  if (nprob < 1) return cudaSuccess;
+  pow2_scale_b_kernel<<<nprob, 256, 0, st>>>(tab);
+  return launched();
+}
+
+template <typename TA, typename TB, bool DF>
 __global__ __launch_bounds__(256) void dgemm_small_kernel(int Mr, int Nc, int K, const TA* __restrict__ A,
                                                           int64_t lda, int ta, const TB* __restrict__ B,
                                                           int64_t ldb, int tb, double* __restrict__ part,
@@ -35,6 +150,7 @@ __global__ __launch_bounds__(256) void dgemm_small_kernel(int Mr, int Nc, int K,
   const int i0 = blockIdx.x * SG_T, j0 = blockIdx.y * SG_T, z = blockIdx.z;
   const int kb = z * kchunk, ke = min(K, kb + kchunk);
   double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  float dh[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, dl[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
   for (int k0 = kb; k0 < ke; k0 += SG_BK) {
     for (int e = tid; e < SG_T * SG_BK; e += 256) {
       int a = e / 32, b = e % 32;
@@ -42,36 +158,27 @@ __global__ __launch_bounds__(256) void dgemm_small_kernel(int Mr, int Nc, int K,
       int i, kk;
       if (!ta) { i = a; kk = b; } else { kk = a; i = b; }
       int gi = i0 + i, gk = k0 + kk;
-      double va = 0.0;
-      if (gi < Mr && gk < ke) va = (double)(ta ? A[(int64_t)gk * lda + gi] : A[(int64_t)gi * lda + gk]);
-      As[kk][i] = va;
+      TA va = TA(0);
+      if (gi < Mr && gk < ke) va = ta ? A[(int64_t)gk * lda + gi] : A[(int64_t)gi * lda + gk];
+      sg_put<DF>(&As[kk][i], va);
       // B element (k, j)
       int j;
       if (!tb) { kk = a; j = b; } else { j = a; kk = b; }
       int gj = j0 + j;
       gk = k0 + kk;
-      double vb = 0.0;
-      if (gj < Nc && gk < ke) vb = (double)(tb ? B[(int64_t)gj * ldb + gk] : B[(int64_t)gk * ldb + gj]);
-      Bs[kk][j] = vb;
+      TB vb = TB(0);
+      if (gj < Nc && gk < ke) vb = tb ? B[(int64_t)gj * ldb + gk] : B[(int64_t)gk * ldb + gj];
+      sg_put<DF>(&Bs[kk][j], vb);
     }
     __syncthreads();
-    const int kk_end = min(SG_BK, ke - k0);
-#pragma unroll 8
-    for (int kk = 0; kk < kk_end; ++kk) {
-      double a0 = As[kk][ty * 2], a1 = As[kk][ty * 2 + 1];
-      double b0 = Bs[kk][tx * 2], b1 = Bs[kk][tx * 2 + 1];
-      acc[0][0] = fma(a0, b0, acc[0][0]);
-      acc[0][1] = fma(a0, b1, acc[0][1]);
-      acc[1][0] = fma(a1, b0, acc[1][0]);
-      acc[1][1] = fma(a1, b1, acc[1][1]);
-    }
+    sg_tile<DF>(As, Bs, min(SG_BK, ke - k0), ty, tx, acc, dh, dl);
     __syncthreads();
   }
   double* P = part + (int64_t)z * Mr * Nc;
   for (int m = 0; m < 2; ++m)
     for (int q = 0; q < 2; ++q) {
       int i = i0 + ty * 2 + m, j = j0 + tx * 2 + q;
-      if (i < Mr && j < Nc) P[(int64_t)i * Nc + j] = acc[m][q];
+      if (i < Mr && j < Nc) P[(int64_t)i * Nc + j] = sg_out<DF>(acc, dh, dl, m, q);
     }
 }
 
@@ -89,7 +196,7 @@ __global__ void dgemm_reduce_kernel(const double* __restrict__ part, int splits,
 template <typename TA, typename TB>
 cudaError_t launch_dgemm_small(int Mr, int Nc, int K, const TA* A, int64_t lda, int ta, const TB* B,
                                int64_t ldb, int tb, double* C, int64_t ldc, double alpha, double beta,
-                               double* work, int64_t work_elems, cudaStream_t st) {
+                               double* work, int64_t work_elems, cudaStream_t st, bool df) {
   if (Mr <= 0 || Nc <= 0) return cudaSuccess;
   int tiles = (int)(cdiv(Mr, SG_T) * cdiv(Nc, SG_T));
   int kslices = (int)cdiv(std::max(K, 1), SG_KGRAIN);
@@ -99,7 +206,10 @@ cudaError_t launch_dgemm_small(int Mr, int Nc, int K, const TA* A, int64_t lda, 
   int kchunk = (int)round_up(cdiv(std::max(K, 1), splits), SG_KGRAIN);
   splits = (int)cdiv(std::max(K, 1), kchunk);
   dim3 grid((unsigned)cdiv(Mr, SG_T), (unsigned)cdiv(Nc, SG_T), (unsigned)splits);
-  dgemm_small_kernel<TA, TB><<<grid, 256, 0, st>>>(Mr, Nc, K, A, lda, ta, B, ldb, tb, work, kchunk);
+  if (df)
+    dgemm_small_kernel<TA, TB, true><<<grid, 256, 0, st>>>(Mr, Nc, K, A, lda, ta, B, ldb, tb, work, kchunk);
+  else
+    dgemm_small_kernel<TA, TB, false><<<grid, 256, 0, st>>>(Mr, Nc, K, A, lda, ta, B, ldb, tb, work, kchunk);
   cudaError_t e = launched();
   if (e != cudaSuccess) return e;
   dgemm_reduce_kernel<<<(unsigned)cdiv((int64_t)Mr * Nc, 256), 256, 0, st>>>(work, splits, Mr, Nc, C, ldc,
@@ -108,10 +218,10 @@ cudaError_t launch_dgemm_small(int Mr, int Nc, int K, const TA* A, int64_t lda, 
 }
 template cudaError_t launch_dgemm_small<double, double>(int, int, int, const double*, int64_t, int,
                                                         const double*, int64_t, int, double*, int64_t,
-                                                        double, double, double*, int64_t, cudaStream_t);
+                                                        double, double, double*, int64_t, cudaStream_t, bool);
 template cudaError_t launch_dgemm_small<float, float>(int, int, int, const float*, int64_t, int,
                                                       const float*, int64_t, int, double*, int64_t,
-                                                      double, double, double*, int64_t, cudaStream_t);
+                                                      double, double, double*, int64_t, cudaStream_t, bool);
 
 // ============================================================================
 // One-CTA cyclic Jacobi in FP32 with the round-robin (circle) ordering: every
@@ -327,7 +437,7 @@ __global__ void oa_form_kernel(int N, const double* __restrict__ XtX, const doub
 }
 
 cudaError_t launch_oa_refine(const double* A, int N, double* X, double* lam, double* work,
-                             int64_t work_elems, cudaStream_t st) {
+                             int64_t work_elems, cudaStream_t st, bool df) {
   const int64_t nn = (int64_t)N * N;
   const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(128, cdiv(nn, 1024)));
   if (work_elems < 4 * nn + 3 * nb + nn) return cudaErrorInvalidValue;
@@ -339,18 +449,18 @@ cudaError_t launch_oa_refine(const double* A, int N, double* X, double* lam, dou
   double* sk = part + 3 * nb;
   const int64_t skn = work_elems - 4 * nn - 3 * nb;
   cudaError_t e;
-  if ((e = launch_dgemm_small<double, double>(N, N, N, X, N, 1, X, N, 0, XtX, N, 1.0, 0.0, sk, skn, st)))
+  if ((e = launch_dgemm_small<double, double>(N, N, N, X, N, 1, X, N, 0, XtX, N, 1.0, 0.0, sk, skn, st, df)))
     return e;
-  if ((e = launch_dgemm_small<double, double>(N, N, N, A, N, 0, X, N, 0, P, N, 1.0, 0.0, sk, skn, st)))
+  if ((e = launch_dgemm_small<double, double>(N, N, N, A, N, 0, X, N, 0, P, N, 1.0, 0.0, sk, skn, st, df)))
     return e;
-  if ((e = launch_dgemm_small<double, double>(N, N, N, X, N, 1, P, N, 0, S, N, 1.0, 0.0, sk, skn, st)))
+  if ((e = launch_dgemm_small<double, double>(N, N, N, X, N, 1, P, N, 0, S, N, 1.0, 0.0, sk, skn, st, df)))
     return e;
   oa_norms_kernel<<<nb, 256, 0, st>>>(A, N, XtX, S, part, lam);
   if ((e = launched())) return e;
   oa_form_kernel<<<nb, 256, 0, st>>>(N, XtX, S, part, nb, lam, F);
   if ((e = launched())) return e;
   // X <- X + X F   (the reduce of the split-K product reads and writes X elementwise)
-  return launch_dgemm_small<double, double>(N, N, N, X, N, 0, F, N, 0, X, N, 1.0, 1.0, sk, skn, st);
+  return launch_dgemm_small<double, double>(N, N, N, X, N, 0, F, N, 0, X, N, 1.0, 1.0, sk, skn, st, df);
 }
 
 // ============================================================================
@@ -915,7 +1025,7 @@ cudaError_t launch_residual(const double* gpart, int ng, const double* bpart, in
 // Batched forms for the compressed-pair GSVDs of a grouped solve: one launch
 // per step for all pairs (tables in device memory, see kernels.h).
 // ============================================================================
-template <typename TA, typename TB>
+template <typename TA, typename TB, bool DF>
 __global__ __launch_bounds__(256) void dgemm_b_kernel(const DgemmB* __restrict__ tab) {
   const DgemmB& g = tab[blockIdx.z];
   const int i0 = blockIdx.x * SG_T, j0 = blockIdx.y * SG_T;
@@ -929,34 +1039,26 @@ __global__ __launch_bounds__(256) void dgemm_b_kernel(const DgemmB* __restrict__
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int K = g.K, ta = g.ta, tb = g.tb;
   double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  float dh[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, dl[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
   for (int k0 = 0; k0 < K; k0 += SG_BK) {
     for (int e = tid; e < SG_T * SG_BK; e += 256) {
       const int a = e / 32, b = e % 32;
       int i, kk;
       if (!ta) { i = a; kk = b; } else { kk = a; i = b; }
       int gi = i0 + i, gk = k0 + kk;
-      As[kk][i] = (gi < g.Mr && gk < K) ? (double)(ta ? A[(int64_t)gk * g.lda + gi] : A[(int64_t)gi * g.lda + gk]) : 0.0;
+      sg_put<DF>(&As[kk][i], (gi < g.Mr && gk < K) ? (ta ? A[(int64_t)gk * g.lda + gi] : A[(int64_t)gi * g.lda + gk])
+                                                  : TA(0));
       int j;
       if (!tb) { kk = a; j = b; } else { j = a; kk = b; }
       const int gj = j0 + j;
       gk = k0 + kk;
-      Bs[kk][j] = (gj < g.Nc && gk < K) ? (double)(tb ? B[(int64_t)gj * g.ldb + gk] : B[(int64_t)gk * g.ldb + gj]) : 0.0;
+      sg_put<DF>(&Bs[kk][j], (gj < g.Nc && gk < K) ? (tb ? B[(int64_t)gj * g.ldb + gk] : B[(int64_t)gk * g.ldb + gj])
+                                                  : TB(0));
     }
     __syncthreads();
-    // threads whose rows and columns all lie past the edge skip the FP64 work (the SM's
+    // threads whose rows and columns all lie past the edge skip the arithmetic (the SM's
     // FP64 units, ~1/64 of its FP32 rate, then go to the threads with real outputs)
-    if (i0 + ty * 2 < g.Mr && j0 + tx * 2 < g.Nc) {
-      const int kk_end = min(SG_BK, K - k0);
-#pragma unroll 8
-      for (int kk = 0; kk < kk_end; ++kk) {
-        const double a0 = As[kk][ty * 2], a1 = As[kk][ty * 2 + 1];
-        const double b0 = Bs[kk][tx * 2], b1 = Bs[kk][tx * 2 + 1];
-        acc[0][0] = fma(a0, b0, acc[0][0]);
-        acc[0][1] = fma(a0, b1, acc[0][1]);
-        acc[1][0] = fma(a1, b0, acc[1][0]);
-        acc[1][1] = fma(a1, b1, acc[1][1]);
-      }
-    }
+    if (i0 + ty * 2 < g.Mr && j0 + tx * 2 < g.Nc) sg_tile<DF>(As, Bs, min(SG_BK, K - k0), ty, tx, acc, dh, dl);
     __syncthreads();
   }
   for (int m = 0; m < 2; ++m)
@@ -964,7 +1066,8 @@ __global__ __launch_bounds__(256) void dgemm_b_kernel(const DgemmB* __restrict__
       const int i = i0 + ty * 2 + m, j = j0 + tx * 2 + q;
       if (i < g.Mr && j < g.Nc) {
         double* c = g.C + (int64_t)i * g.ldc + j;
-        const double v = g.beta == 0.0 ? g.alpha * acc[m][q] : g.alpha * acc[m][q] + g.beta * (*c);
+        const double r = sg_out<DF>(acc, dh, dl, m, q);
+        const double v = g.beta == 0.0 ? g.alpha * r : g.alpha * r + g.beta * (*c);
         *c = v;
         if (g.sym && blockIdx.x < blockIdx.y) g.C[(int64_t)j * g.ldc + i] = v;
       }
@@ -972,14 +1075,17 @@ __global__ __launch_bounds__(256) void dgemm_b_kernel(const DgemmB* __restrict__
 }
 
 template <typename TA, typename TB>
-cudaError_t launch_dgemm_b(const DgemmB* tab, int nprob, int max_Mr, int max_Nc, cudaStream_t st) {
+cudaError_t launch_dgemm_b(const DgemmB* tab, int nprob, int max_Mr, int max_Nc, cudaStream_t st, bool df) {
   if (nprob <= 0) return cudaSuccess;
   const dim3 grid((unsigned)cdiv(max_Mr, SG_T), (unsigned)cdiv(max_Nc, SG_T), (unsigned)nprob);
-  dgemm_b_kernel<TA, TB><<<grid, 256, 0, st>>>(tab);
+  if (df)
+    dgemm_b_kernel<TA, TB, true><<<grid, 256, 0, st>>>(tab);
+  else
+    dgemm_b_kernel<TA, TB, false><<<grid, 256, 0, st>>>(tab);
   return launched();
 }
-template cudaError_t launch_dgemm_b<float, float>(const DgemmB*, int, int, int, cudaStream_t);
-template cudaError_t launch_dgemm_b<double, double>(const DgemmB*, int, int, int, cudaStream_t);
+template cudaError_t launch_dgemm_b<float, float>(const DgemmB*, int, int, int, cudaStream_t, bool);
+template cudaError_t launch_dgemm_b<double, double>(const DgemmB*, int, int, int, cudaStream_t, bool);
 
 // Frobenius sums of A, R = I - X^T X and S - diag(lam) (part[0..2]) and lam, one CTA per problem.
 __global__ __launch_bounds__(256) void oa_norms_b_kernel(const OaB* __restrict__ tab) {
@@ -1072,17 +1178,17 @@ void oa_b_tables(const OaB* h, int nprob, DgemmB* dg) {
   }
 }
 
-cudaError_t launch_oa_refine_b(const OaB* tab, const DgemmB* dg, int nprob, int max_N, cudaStream_t st) {
+cudaError_t launch_oa_refine_b(const OaB* tab, const DgemmB* dg, int nprob, int max_N, cudaStream_t st, bool df) {
   if (nprob <= 0) return cudaSuccess;
   cudaError_t e;
   for (int k = 0; k < 3; ++k)
-    if ((e = launch_dgemm_b<double, double>(dg + (int64_t)k * nprob, nprob, max_N, max_N, st))) return e;
+    if ((e = launch_dgemm_b<double, double>(dg + (int64_t)k * nprob, nprob, max_N, max_N, st, df))) return e;
   oa_norms_b_kernel<<<nprob, 256, 0, st>>>(tab);
   if ((e = launched())) return e;
   const dim3 g2((unsigned)cdiv((int64_t)max_N * max_N, 256), 1, (unsigned)nprob);
   oa_form_b_kernel<<<g2, 256, 0, st>>>(tab);
   if ((e = launched())) return e;
-  if ((e = launch_dgemm_b<double, double>(dg + 3ll * nprob, nprob, max_N, max_N, st))) return e;
+  if ((e = launch_dgemm_b<double, double>(dg + 3ll * nprob, nprob, max_N, max_N, st, df))) return e;
   oa_update_b_kernel<<<g2, 256, 0, st>>>(tab);
   return launched();
 }

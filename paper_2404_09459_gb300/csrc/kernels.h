@@ -17,6 +17,15 @@ cudaError_t launch_gaussian_rowmajor(double* out, int64_t n, int64_t l, uint64_t
                                      uint32_t side, uint32_t stream, cudaStream_t st);
 // Omega^T stored K-major for the sketch product: Xt[j * ldx + i] = Omega[i][j],
 // j < lrows (rows l..lrows-1 are zero), i < n (columns n..ldx-1 are zero).
+// Complex pairs: rho(Omega) of the complex n x l test matrix Omega[j][c] = g(2 (j l + c)) +
+// i g(2 (j l + c) + 1) (g the real stream of an n x 2l matrix), written K-major like
+// launch_gaussian_kmajor with n2 = 2n, l2 = 2l; and R = rho(G) (2M x 2n, row stride ldr) of a
+// complex M x n matrix stored as interleaved (re, im) pairs with row stride ldg complex entries.
+template <typename T>
+cudaError_t launch_gaussian_kmajor_cplx(T* Xt, int64_t ldx, int64_t n2, int l2, int lrows, uint64_t seed,
+                                        uint32_t pair, uint32_t side, uint32_t stream, cudaStream_t st);
+template <typename T>
+cudaError_t launch_realify(const T* G, int64_t ldg, int64_t M, int64_t n, T* R, int64_t ldr, cudaStream_t st);
 template <typename T>
 cudaError_t launch_gaussian_kmajor(T* Xt, int64_t ldx, int64_t n, int l, int lrows, uint64_t seed,
                                    uint32_t pair, uint32_t side, uint32_t stream, cudaStream_t st);
@@ -92,13 +101,16 @@ int64_t apply_rows_per_cta(int l, int elem_bytes);
 
 // ---- small FP64 dense kernels (compressed-pair GSVD) -----------------------
 // C (Mr x Nc) = op(A) * op(B) in FP64 accumulation; op(X) = X or X^T.
+// df: double-float arithmetic (each operand as an FP32 hi + lo pair, error-free products and
+// TwoSum accumulation, about 2^-48 relative) in place of FP64 FMAs: several times faster on GB300,
+// for the mixed-precision paths; operands must lie inside FP32's exponent range (launch_pow2_scale).
 // A: if !ta, Mr x K with lda; else K x Mr.  B: if !tb, K x Nc with ldb; else Nc x K.
 // Split-K partials go to `work` (splits * Mr * Nc doubles) then a reduce writes
 // C = alpha * sum + beta * C.  Returns cudaErrorInvalidValue if work too small.
 template <typename TA, typename TB>
 cudaError_t launch_dgemm_small(int Mr, int Nc, int K, const TA* A, int64_t lda, int ta, const TB* B,
                                int64_t ldb, int tb, double* C, int64_t ldc, double alpha, double beta,
-                               double* work, int64_t work_elems, cudaStream_t st);
+                               double* work, int64_t work_elems, cudaStream_t st, bool df = false);
 
 // One-CTA cyclic Jacobi eigensolver in FP32 (parallel round-robin order) on the
 // symmetric N x N FP64 matrix A (scaled internally).  Writes the eigenvector
@@ -123,7 +135,7 @@ cudaError_t launch_eig_f32(const double* A, int N, double* X, double* lam, float
 // F_ij = (s_ij + lam_j r_ij)/(lam_j - lam_i) (|lam_i - lam_j| > delta) or r_ij/2,
 // X <- X + X F.  work: 4*N*N + splitK scratch doubles.
 cudaError_t launch_oa_refine(const double* A, int N, double* X, double* lam, double* work,
-                             int64_t work_elems, cudaStream_t st);
+                             int64_t work_elems, cudaStream_t st, bool df = false);
 
 // Gather the r leading eigenvectors (by lam, descending; NaN last) of X (N x N)
 // into Zr (N x r); order receives the permutation.
@@ -300,7 +312,7 @@ struct DgemmB {
   int sym;  // the result is symmetric (Mr == Nc): upper tiles computed and mirrored
 };
 template <typename TA, typename TB>
-cudaError_t launch_dgemm_b(const DgemmB* tab, int nprob, int max_Mr, int max_Nc, cudaStream_t st);
+cudaError_t launch_dgemm_b(const DgemmB* tab, int nprob, int max_Mr, int max_Nc, cudaStream_t st, bool df = false);
 
 // One Ogita-Aishima step per problem (as launch_oa_refine), and the cut cluster after it.
 struct OaB {
@@ -317,7 +329,8 @@ struct OaB {
 };
 // The four products of a step use `dg` (4 * nprob DgemmB entries, filled by oa_b_tables).
 void oa_b_tables(const OaB* hostOa, int nprob, DgemmB* dg);
-cudaError_t launch_oa_refine_b(const OaB* tab, const DgemmB* dg, int nprob, int max_N, cudaStream_t st);
+cudaError_t launch_oa_refine_b(const OaB* tab, const DgemmB* dg, int nprob, int max_N, cudaStream_t st,
+                               bool df = false);
 cudaError_t launch_oa_cut_cluster_b(const OaB* tab, int nprob, int max_N, cudaStream_t st);
 
 struct SelB {
@@ -345,6 +358,10 @@ struct ScatterB {  // dst[0..count) = src[0..count)
 };
 cudaError_t launch_scatter_b(const ScatterB* tab, int n, cudaStream_t st);
 
+// A (N x N) times the power of two that puts its largest |diagonal entry| in [1, 2) (exact).
+cudaError_t launch_pow2_scale(double* A, int N, cudaStream_t st);
+struct EigB;
+cudaError_t launch_pow2_scale_b(const EigB* tab, int nprob, cudaStream_t st);  // each entry's A and N
 struct EigB {
   const double* A;
   double* X;

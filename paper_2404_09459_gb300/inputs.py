@@ -164,6 +164,54 @@ def full_gmp_pair(m: int, p: int, n: int, seed: int = 0, rank_frac: float = 0.6,
     return G1.astype(dtype), G2.astype(dtype), alpha, beta
 
 
+def _haar_columns_complex(rng: np.random.Generator, rows: int, cols: int) -> np.ndarray:
+    a = rng.standard_normal((rows, cols)) + 1j * rng.standard_normal((rows, cols))
+    q, r = np.linalg.qr(a)
+    d = np.diag(r)
+    return q * (d / np.abs(d))[None, :]
+
+
+def planted_pair_complex(spec: PairSpec, dtype=np.complex128):
+    """The planted recipe over C: G1 = U_r diag(alpha) D O_r + sigma N1, G2 = V_r diag(beta) D O_r
+    + sigma N2 with U_r, V_r complex Haar column-orthonormal, O_r complex orthonormal rows and
+    N circularly symmetric complex Gaussian (E |N_ij|^2 = 1).  Returns (G1, G2, alpha, beta)."""
+    rng = np.random.default_rng(np.random.SeedSequence([spec.seed, spec.m, spec.p, spec.n, spec.r, 7001]))
+    alpha = planted_alpha(spec, rng)
+    beta = np.sqrt((1.0 - alpha) * (1.0 + alpha))
+    d = planted_scale(spec)
+    U = _haar_columns_complex(rng, spec.m, spec.r)
+    V = _haar_columns_complex(rng, spec.p, spec.r)
+    O = _haar_columns_complex(rng, spec.n, spec.r).conj().T
+    G1 = (U * (alpha * d)[None, :]) @ O
+    G2 = (V * (beta * d)[None, :]) @ O
+    if spec.sigma:
+        for G in (G1, G2):
+            G += spec.sigma * (rng.standard_normal(G.shape) + 1j * rng.standard_normal(G.shape)) / np.sqrt(2.0)
+    return G1.astype(dtype), G2.astype(dtype), alpha, beta
+
+
+def full_gmp_pair_complex(m: int, p: int, n: int, seed: int = 0, rank_frac: float = 0.6, dtype=np.complex128):
+    """The paper's own synthetic pair of Section 4.1 as the paper states it, over C: as
+    full_gmp_pair with complex orthonormalised Gaussian U, V and a complex Gaussian R."""
+    if m < n or p < n:
+        raise ValueError("the construction needs m >= n and p >= n")
+    rng = np.random.default_rng(np.random.SeedSequence([seed, m, p, n, 4102]))
+    r = int(round(rank_frac * min(m, p, n)))
+    n_one = n_zero = n - r
+    n_mid = n - n_one - n_zero
+    if n_mid < 0:
+        raise ValueError("rank_frac must be at least 0.5")
+    mid = np.sort(rng.uniform(0.0, 1.0, n_mid))[::-1]
+    alpha = np.concatenate([np.ones(n_one), mid, np.zeros(n_zero)])
+    beta = np.sqrt((1.0 - alpha) * (1.0 + alpha))
+    U = _haar_columns_complex(rng, m, n)
+    V = _haar_columns_complex(rng, p, n)
+    R = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(2.0)
+    G1 = (U * alpha[None, :]) @ R
+    G2 = (V * beta[None, :]) @ R
+    return G1.astype(dtype), G2.astype(dtype), alpha, beta
+
+
 def uneven_batch(npairs: int = 256, seed: int = 0, m_range=(2000, 30000), n_range=(100, 1000),
                  r_range=(10, 100), oversample: int = 10, q: int = 1, sigma: float = 1e-9):
     """Specs of a batch of uneven pairs: m, p ~ U[m_range], n ~ U[n_range],

@@ -492,3 +492,108 @@ def test_bf16_omega_sketch_stays_a_range_finder():
     assert np.max(O.gsv_error(plain["alpha"], plain["beta"], rounded["alpha"], rounded["beta"])) < 1e-12
     with pytest.raises(ValueError):
         O.rand_gsvd(G1, G2, r, 4, 0, seed=5, omega_round="fp8")
+
+
+# ---------------------------------------------------------------- complex pairs (Section 1 over C)
+def _full_rank_pair_complex(rng, m, p, n, alpha=None, cond=10.0):
+    """G1 = U diag(alpha) R, G2 = V diag(beta) R over C: U, V with orthonormal columns, R nonsingular."""
+    if alpha is None:
+        alpha = np.sort(rng.uniform(0.02, 0.98, n))[::-1]
+    beta = np.sqrt(1.0 - alpha ** 2)
+
+    def cgauss(r, c):
+        return rng.standard_normal((r, c)) + 1j * rng.standard_normal((r, c))
+
+    U, _ = np.linalg.qr(cgauss(m, n))
+    V, _ = np.linalg.qr(cgauss(p, n))
+    A, _ = np.linalg.qr(cgauss(n, n))
+    Bq, _ = np.linalg.qr(cgauss(n, n))
+    R = A @ np.diag(np.logspace(0, np.log10(cond), n)) @ Bq
+    return U @ np.diag(alpha) @ R, V @ np.diag(beta) @ R, alpha, beta
+
+
+def test_complex_direct_gsvd_matches_planted_and_hermitian_pencil():
+    # the planted GSVs of a complex pair, and brute force by the Hermitian-definite pencil
+    # (a transpose in place of the conjugate transpose makes the pencil non-Hermitian and fails)
+    rng = _rng(40)
+    for n in (1, 3, 6):
+        G1, G2, a, b = _full_rank_pair_complex(rng, 9, 8, n)
+        ad, bd = O.direct_gsvd_complex(G1, G2)
+        np.testing.assert_allclose(ad, a, atol=1e-12)
+        np.testing.assert_allclose(bd, b, atol=1e-12)
+        ap, bp = O.pencil_gsvd_complex(G1, G2)
+        np.testing.assert_allclose(ap, a, atol=1e-10)
+        np.testing.assert_allclose(np.sort(bp), np.sort(b), atol=1e-10)
+        # exchanging the two matrices exchanges alpha and beta
+        a2, b2 = O.direct_gsvd_complex(G2, G1)
+        np.testing.assert_allclose(a2, np.sort(b)[::-1], atol=1e-12)
+
+
+def test_complex_gsvs_appear_twice_in_the_realified_pair():
+    # C as real 2 x 2 blocks is a ring homomorphism: the real oracle on (realify(G1), realify(G2))
+    # returns every complex GSV twice; the block signs are pinned by realify(A) realify(B) = realify(AB)
+    rng = _rng(41)
+    G1, G2, a, b = _full_rank_pair_complex(rng, 12, 10, 5)
+    ar, br = O.direct_gsvd(O.realify(G1), O.realify(G2))
+    np.testing.assert_allclose(ar[0::2], a, atol=1e-12)
+    np.testing.assert_allclose(ar[1::2], a, atol=1e-12)
+    np.testing.assert_allclose(br[0::2], np.sort(b), atol=1e-12)
+    A = rng.standard_normal((4, 3)) + 1j * rng.standard_normal((4, 3))
+    B = rng.standard_normal((3, 2)) + 1j * rng.standard_normal((3, 2))
+    np.testing.assert_allclose(O.realify(A) @ O.realify(B), O.realify(A @ B), atol=1e-14)
+    np.testing.assert_allclose(O.realify(A.conj().T), O.realify(A).T, atol=0)
+
+
+def test_complex_gaussian_test_matrix_is_circular():
+    # independent N(0, 1) real and imaginary parts: E|w|^2 = 2, E w^2 = 0, uncorrelated parts
+    W = O.gaussian_complex(400, 50, seed=12, pair=3, side=1)
+    x, y = W.real.ravel(), W.imag.ravel()
+    assert stats.kstest(x, "norm").pvalue > 1e-3 and stats.kstest(y, "norm").pvalue > 1e-3
+    assert abs(np.mean(np.abs(W) ** 2) - 2.0) < 0.05
+    assert abs(np.mean(W ** 2)) < 0.05
+    assert abs(np.corrcoef(x, y)[0, 1]) < 0.03
+    # the sketch of the realified pair by the realified test matrix is the realified sketch
+    G = _rng(42).standard_normal((7, 400)) + 1j * _rng(43).standard_normal((7, 400))
+    np.testing.assert_allclose(O.realify(G) @ O.realify(W), O.realify(G @ W), atol=1e-10)
+
+
+@pytest.mark.parametrize("q", [0, 1, 2])
+def test_complex_randomized_equals_planted_on_exact_rank(q):
+    # exact rank r with l >= r: the bases capture the ranges, so the randomized GSVs are the
+    # planted ones; q >= 1 runs the power steps with G^H (a plain transpose loses the range)
+    from paper_2404_09459_gb300.inputs import planted_pair_complex
+    spec = PairSpec(m=120, p=90, n=40, r=8, alpha="uniform", decay="exp10", sigma=0.0, k=8, oversample=4,
+                    q=q, seed=44)
+    G1, G2, a, b = planted_pair_complex(spec)
+    out = O.rand_gsvd_complex(G1, G2, 8, 4, q, seed=9)
+    np.testing.assert_allclose(out["alpha"], a, atol=1e-10)
+    np.testing.assert_allclose(out["beta"], b, atol=1e-10)
+    assert out["resid1"] < 1e-12 and out["resid2"] < 1e-12
+
+
+def test_paper_complex_full_pair_recovered():
+    # Section 4.1's synthetic pair as the paper states it (complex U, V, R): 40% of the pairs at
+    # (1, 0), 40% at (0, 1), 20% uniform; all n pairs are resolved with k = n
+    from paper_2404_09459_gb300.inputs import full_gmp_pair_complex
+    G1, G2, a, b = full_gmp_pair_complex(150, 130, 50, seed=2)
+    d_a, d_b = O.direct_gsvd_complex(G1, G2)
+    np.testing.assert_allclose(d_a, a, atol=1e-12)
+    out = O.rand_gsvd_complex(G1, G2, 50, 0, 0, seed=5)
+    np.testing.assert_allclose(out["alpha"], a, atol=1e-10)
+    np.testing.assert_allclose(out["beta"], b, atol=1e-10)
+
+
+@pytest.mark.parametrize("q", [1, 2])
+def test_complex_power_steps_span_the_powered_sketch(q):
+    # subspace iteration (Halko, Martinsson & Tropp 2011, Alg. 4.4) spans range((G G^H)^q G Omega)
+    # in exact arithmetic; on a full-rank, mildly conditioned G the two bases agree to rounding
+    # (a power step taken with G^T instead of G^H spans another subspace)
+    rng = _rng(45)
+    U, _ = np.linalg.qr(rng.standard_normal((60, 40)) + 1j * rng.standard_normal((60, 40)))
+    V, _ = np.linalg.qr(rng.standard_normal((40, 40)) + 1j * rng.standard_normal((40, 40)))
+    G = (U * np.linspace(1.0, 0.1, 40)[None, :]) @ V.conj().T
+    Q = O.basis_fixed_complex(G, 10, q, seed=3, pair=1, side=0)
+    W = O.gaussian_complex(40, 10, seed=3, pair=1, side=0)
+    P, _ = np.linalg.qr(np.linalg.matrix_power(G @ G.conj().T, q) @ G @ W)
+    sines = np.linalg.norm(P - Q @ (Q.conj().T @ P), 2)
+    assert sines < 1e-10, sines
