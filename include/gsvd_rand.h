@@ -240,11 +240,26 @@ int gsvd_rand_solve_batched(gsvd_rand_t h, int npairs, gsvd_rand_pair *pairs, in
  * path chunks its Gram sums differently from gsvd_rand_solve, so results agree with it
  * to rounding (not bit for bit); repeated calls are bit-identical.  The plan, tables
  * and graph live in device memory owned by h (freed by gsvd_rand_destroy).
+ * With cfg->adaptive = 1 every side's basis comes from Algorithm 1 (BasisExt with the
+ * cumulated-residual stop of Section 2) instead: blocks of b = cfg->block_b <= 32 Gaussian
+ * columns (Omega_i from counter words (t, pair, s, 0x10000 + i), as gsvd_rand_solve), each
+ * projected twice against the basis so far, orthonormalised, projected and orthonormalised
+ * again, until sqrt(||G||_F^2 - sum_i ||P_i^T G||_F^2) <= tol ||G||_F or the basis has
+ * min(m, p, n, 128) columns (then TOL_MISS, results still written).  Every block is one step
+ * for the whole batch; the stop test runs on the device, where each side has a stop word that
+ * makes the later blocks skip it (no host read between blocks).  oversample and q are not
+ * used; each pair returns min(k, l1 + l2) pairs (*r_out; alpha / beta need min(k, 2 cap)
+ * entries, those past *r_out are set to -1); gsvd_rand_grouped_basis_cols gives l1, l2.
  * Returns GSVD_RAND_OK when all pairs succeeded, else the status of the first
  * failing pair.  Ordered after and before cfg->stream; synchronises.
- * Errors: ARG, OOM, CUDA, UNSUPPORTED (precision, adaptive / learned / basis-only
- * contexts, no sm_103 tensor cores), and per-pair NONFINITE, BREAKDOWN, TIMEOUT. */
+ * Errors: ARG, OOM, CUDA, UNSUPPORTED (precision, learned / basis-only contexts, no sm_103
+ * tensor cores), and per-pair NONFINITE, BREAKDOWN, TIMEOUT, TOL_MISS (adaptive). */
 int gsvd_rand_solve_grouped(gsvd_rand_t h, int npairs, gsvd_rand_pair *pairs);
+
+/* The basis columns of each side of the last grouped solve on h with cfg->adaptive = 1
+ * (Algorithm 1 in grouped form, see gsvd_rand_solve_grouped): cols[2 i + s] for pair i,
+ * side s (0 for pairs left out); npairs entries of the last call's array.  Errors: ARG. */
+int gsvd_rand_grouped_basis_cols(gsvd_rand_t h, int *cols, int npairs);
 
 /* The last grouped plan of h: tuned[6] = (stages, CTAs per SM) of the first sketch,
  * the power-step sketch and the G^T Q / projection products; the graph captures and

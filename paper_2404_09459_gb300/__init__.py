@@ -27,7 +27,7 @@ EXPORTS = ("gsvd_rand_config_init", "gsvd_rand_create", "gsvd_rand_destroy", "gs
            "gsvd_rand_probe_features", "gsvd_rand_mlp_forward", "gsvd_rand_mlp_loss_grad", "gsvd_rand_mlp_adam",
            "gsvd_rand_mlp_train", "gsvd_rand_mlp_set", "gsvd_rand_mlp_load", "gsvd_rand_last_plan",
            "gsvd_rand_solve_grouped", "gsvd_rand_grouped_info", "gsvd_rand_chol64_retries",
-           "gsvd_rand_product_shapes", "gsvd_rand_factors", "gsvd_rand_solve_complex")
+           "gsvd_rand_product_shapes", "gsvd_rand_factors", "gsvd_rand_solve_complex", "gsvd_rand_grouped_basis_cols")
 NOALLOC_MAX_N = 32768
 FLAG_PROFILE = 2
 FLAG_BF16_SPLIT_POWER = 4
@@ -77,6 +77,7 @@ def load_library(path: str | None = None):
     lib.gsvd_rand_last_error.argtypes = [vp]
     lib.gsvd_rand_last_error.restype = C.c_char_p
     lib.gsvd_rand_solve.argtypes = [vp, vp, i64, i64, vp, i64, i64, i64, i32, i32, i32, u64, vp, vp, vp, vp]
+    lib.gsvd_rand_grouped_basis_cols.argtypes = [vp, vp, i32]
     lib.gsvd_rand_solve_complex.argtypes = [vp, vp, i64, i64, vp, i64, i64, i64, i32, i32, i32, u64, vp, vp, vp, vp]
     lib.gsvd_rand_metrics.argtypes = [vp, vp, vp, i32, i32, i32, vp, vp, vp, vp, vp]
     lib.gsvd_rand_gaussian.argtypes = [vp, i64, i64, u64, u32, u32, u32, vp]
@@ -298,6 +299,12 @@ class Context:
         the sequence captured into a CUDA graph and replayed while the inputs stay the same.
         host_out: alpha / beta returned in host memory (numpy) even for device inputs."""
         return self._many(pairs, None, host_out)
+
+    def grouped_basis_cols(self, npairs: int):
+        """[(l1, l2)] per pair of the last grouped adaptive solve (Algorithm 1 basis columns)."""
+        c = (C.c_int * (2 * npairs))()
+        self._check(self.lib.gsvd_rand_grouped_basis_cols(self.h, c, npairs))
+        return [(c[2 * i], c[2 * i + 1]) for i in range(npairs)]
 
     def grouped_info(self):
         """dict(tuned=[(stages, ctas_per_sm)] x 3 (first sketch, power sketch, G^T Q), captures,

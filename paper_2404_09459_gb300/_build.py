@@ -18,7 +18,8 @@ LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libgsvdrand.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["api.cu", "k_basis.cu", "k_small.cu", "k_eig.cu", "k_tc.cu", "k_cholqr.cu", "noalloc.cu", "k_mlp.cu"]
+SOURCES = ["api.cu", "k_basis.cu", "k_small.cu", "k_eig.cu", "k_tc.cu", "k_cholqr.cu", "noalloc.cu", "k_mlp.cu",
+           "k_adapt.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fno-strict-aliasing",
          "-I", INCLUDE]

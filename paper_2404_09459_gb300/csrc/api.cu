@@ -1140,7 +1140,7 @@ int solve_adaptive_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, 
 // ---------------------------------------------------------------------------
 template <typename T, typename TC>
 int probe_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, const void* G2v, int64_t p, int64_t ld2,
-            int64_t n, uint64_t seed, float* feats) {
+            int64_t n, uint64_t seed, float* feats, DevStatus* st_ext = nullptr) {
   constexpr int PL = 16;
   cudaStream_t st = h->stream;
   const int prec = h->cfg.prec;
@@ -1179,6 +1179,7 @@ int probe_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, const voi
   Bump bp;
   bp.base = h->ws;
   DevStatus* st_dev = bp.take<DevStatus>(1);
+  if (st_ext) st_dev = st_ext;  // a batch of probes: the caller's status word, read after the batch
   const void* Gs[2] = {G1v, G2v};
   int64_t ldg[2] = {ld1, ld2};
   const int64_t Ms[2] = {m, p};
@@ -1192,7 +1193,7 @@ int probe_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, const voi
       ldg[s] = lds;
     }
   SideBufs<T> sb[2] = {side_take<T>(bp, pl, 0, use_tc, bf16), side_take<T>(bp, pl, 1, use_tc, bf16)};
-  CU(cudaMemsetAsync(st_dev, 0, sizeof(DevStatus), st));
+  if (!st_ext) CU(cudaMemsetAsync(st_dev, 0, sizeof(DevStatus), st));
   Solver<T, TC> sv{h, st, st_dev, prec, use_tc, nullptr, bf16, true};
   for (int s = 0; s < 2; ++s) {
     SideBufs<T>& b = sb[s];
@@ -1220,6 +1221,7 @@ int probe_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, const voi
     const int gct = use_tc ? tc_gx_ctas(M) : gemm_gx_simt_ctas(M);
     CU(launch_probe_features(b.W, (const double*)b.R, b.gnorm, gct, feats + 32 * s, st));
   }
+  if (st_ext) return GSVD_RAND_OK;
   CU(cudaMemcpyAsync(h->st_host, st_dev, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
   if (h->st_host->code)
@@ -1229,9 +1231,10 @@ int probe_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, const voi
 }
 
 int probe_dispatch(gsvd_rand_ctx* h, const void* G1, int64_t m, int64_t ld1, const void* G2, int64_t p, int64_t ld2,
-                   int64_t n, uint64_t seed, float* feats_dev) {
-  if (h->cfg.prec == GSVD_RAND_FP64) return probe_t<double, double>(h, G1, m, ld1, G2, p, ld2, n, seed, feats_dev);
-  return probe_t<float, float>(h, G1, m, ld1, G2, p, ld2, n, seed, feats_dev);
+                   int64_t n, uint64_t seed, float* feats_dev, DevStatus* st_ext = nullptr) {
+  if (h->cfg.prec == GSVD_RAND_FP64)
+    return probe_t<double, double>(h, G1, m, ld1, G2, p, ld2, n, seed, feats_dev, st_ext);
+  return probe_t<float, float>(h, G1, m, ld1, G2, p, ld2, n, seed, feats_dev, st_ext);
 }
 
 // The fixed-rank or adaptive solve (arguments already checked).
@@ -1293,25 +1296,18 @@ int solve_learned(gsvd_rand_ctx* h, const void* G1, int64_t m, int64_t ld1, cons
   int rc = probe_dispatch(h, G1, m, ld1, G2, p, ld2, n, seed, F + MLP_FEATS);
   if (rc) return rc;
   CU(mlp_forward(F, F + MLP_NORM, F + MLP_FEATS, 1, 1, F + MLP_LOGITS, F + MLP_SCR, h->stream));
-  float z[MLP_OUT];
-  CU(cudaMemcpyAsync(z, F + MLP_LOGITS, sizeof(z), cudaMemcpyDeviceToHost, h->stream));
+  // the plan on the device (k: the smallest bucket whose cumulative softmax probability reaches
+  // GSVD_RAND_MLP_KQUANTILE, a miss costing a fallback and an oversized basis only columns;
+  // q: the most probable), then the solve's own limits
+  int* plan_dev = reinterpret_cast<int*>(F + MLP_SCR);
+  CU(launch_mlp_plan(F + MLP_LOGITS, 1, (float)GSVD_RAND_MLP_KQUANTILE, nullptr, nullptr, nullptr, plan_dev,
+                     h->stream));
+  int plan[3];
+  CU(cudaMemcpyAsync(plan, plan_dev, sizeof(plan), cudaMemcpyDeviceToHost, h->stream));
   CU(cudaStreamSynchronize(h->stream));
-  // k: the smallest bucket whose cumulative softmax probability reaches GSVD_RAND_MLP_KQUANTILE
-  // (a miss costs a fallback, an oversized basis only some columns); q: the most probable
-  int kb = 0, q = 0;
-  {
-    double mx = z[0], tot = 0.0, cum = 0.0;
-    for (int j = 1; j < GSVD_RAND_MLP_KCLS; ++j) mx = std::max(mx, (double)z[j]);
-    for (int j = 0; j < GSVD_RAND_MLP_KCLS; ++j) tot += std::exp((double)z[j] - mx);
-    for (kb = 0; kb < GSVD_RAND_MLP_KCLS - 1; ++kb) {
-      cum += std::exp((double)z[kb] - mx) / tot;
-      if (cum >= GSVD_RAND_MLP_KQUANTILE) break;
-    }
-  }
-  for (int j = 1; j < GSVD_RAND_MLP_QCLS; ++j)
-    if (z[GSVD_RAND_MLP_KCLS + q] < z[GSVD_RAND_MLP_KCLS + j]) q = j;
+  const int q = plan[1];
   const int64_t lmax = std::min<int64_t>(std::min(std::min(m, p), n), h->cfg.prec == GSVD_RAND_FP64 ? 224 : 256);
-  int k = std::min<int64_t>(std::min(GSVD_RAND_MLP_KBUCKET * (kb + 1), kcap), lmax - oversample);
+  int k = (int)std::min<int64_t>(std::min(plan[0], kcap), lmax - oversample);
   k = std::max(k, 1);
   h->last_plan[0] = k;
   h->last_plan[1] = q;
@@ -1360,6 +1356,8 @@ struct GroupState {
   std::vector<int> prof_tag;
   // results
   size_t res_off = 0, res_bytes = 0;  // results block inside the workspace
+  size_t stop_off = 0;                // adaptive: the stop words (2 per pair) in the results block
+  std::vector<int> cols;              // adaptive: the basis columns of each side of the last solve
   std::vector<int> valid;             // pair index of each solved pair
   struct Out {
     size_t a_off, b_off;  // alpha / beta of the pair in the results block
@@ -1504,6 +1502,12 @@ struct GSide {
   int64_t rps;
   int gchunks;
   int64_t grpc;
+  // grouped Algorithm 1: the orthonormalised block before its second projection, Q^T Y and its
+  // chunk partials, the running residual state and the stop word (in the results block)
+  float* Pb = nullptr;
+  double *C = nullptr, *xpart = nullptr, *state = nullptr;
+  float* epart = nullptr;  // chunk partials of the block energy ||P^T G||_F^2
+  int* stop = nullptr;
 };
 struct GPair {
   int k, l, L, q;
@@ -1533,6 +1537,7 @@ struct GroupBuild {
     int tune_slot;
     int stages, per_sm;  // picked by the autotuner for this launch's own shape
     int prec;            // 3: 3xTF32; else single-pass TF32
+    size_t fl_off;       // problems with stop words: the filtered tile list (0: none)
   };
   std::vector<Gemm> gemms;
   size_t ws_bytes = 0;
@@ -1550,14 +1555,22 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
   GroupState* g = h->grp;
   DevStatus* st_all = bp.take<DevStatus>(np);
   double* resid_all = bp.take<double>(2ll * np);
+  // grouped Algorithm 1 (adaptive contexts): a stop word per side, read back with the results
+  const bool adaptive = h->cfg.adaptive != 0;
+  const int bsz = h->cfg.block_b;
+  int* stop_all = adaptive ? bp.take<int>(2ll * np) : nullptr;
+  g->stop_off = adaptive ? (size_t)((char*)stop_all - base) : 0;
+  auto acap = [](const gsvd_rand_pair& q) {  // the column cap of both sides' bases
+    return (int)std::min<int64_t>(std::min<int64_t>(std::min(q.m, q.p), q.n), ADAPT_CMAX);
+  };
   g->outs.assign(np, GroupState::Out{});
   gb.prs.resize(np);
   for (int i = 0; i < np; ++i) {
     const gsvd_rand_pair& q = *pv[i];
     GroupState::Out& o = g->outs[i];
-    o.k = q.k;
-    double* a = bp.take<double>(q.k);
-    double* b = bp.take<double>(q.k);
+    o.k = adaptive ? std::min(q.k, 2 * acap(q)) : q.k;
+    double* a = bp.take<double>(o.k);
+    double* b = bp.take<double>(o.k);
     o.a_off = (size_t)((char*)a - base);
     o.b_off = (size_t)((char*)b - base);
     gb.prs[i].alpha = a;
@@ -1572,8 +1585,13 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
     GPair& P = gb.prs[i];
     P.k = q.k;
     P.l = q.k + q.oversample;
-    P.L = 2 * P.l;
     P.q = q.q;
+    if (adaptive) {  // bases of up to cap columns per side, grown by blocks; min(k, 2 cap) pairs
+      P.l = acap(q);
+      P.k = std::min(q.k, 2 * P.l);
+      P.q = 0;
+    }
+    P.L = 2 * P.l;
     P.n = q.n;
     P.ldn = round_up(q.n, 4);
     P.st = st_all + i;
@@ -1592,7 +1610,8 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
       S.ldm = round_up(S.M, 4);
       S.Xt = bp.take<float>((int64_t)S.lx * S.ldx);
       S.Y = bp.take<float>(S.M * S.lp);
-      S.Qt = bp.take<float>((int64_t)S.lx * S.ldm);
+      // adaptive: a block product reads round_up(bi, 16) rows from row c, up to 16 past lx
+      S.Qt = bp.take<float>((int64_t)(S.lx + (adaptive ? 16 : 0)) * S.ldm);
       S.tmp = bp.take<float>(2 * std::max(S.M, S.n) * S.lt);
       S.Z = bp.take<float>(S.n * S.lp);
       S.rps = round_up(cdiv(S.M, cdiv(S.M, GROUP_GTQ_ROWS)), 32);
@@ -1606,6 +1625,14 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
       S.R = bp.take<float>((int64_t)S.lx * S.lp);
       S.gnorm = bp.take<double>(tc_group_norm_parts() * cdiv(S.M, 128));
       S.bnorm = bp.take<double>(cdiv(S.n * P.l, 256));
+      if (adaptive) {
+        S.Pb = bp.take<float>(S.M * S.lp);
+        S.C = bp.take<double>((int64_t)P.l * bsz);
+        S.xpart = bp.take<double>(adapt_xpart_elems(S.M, P.l, bsz));
+        S.state = bp.take<double>(4);
+        S.epart = bp.take<float>(adapt_energy_part_elems(S.M, S.n, bsz));
+        S.stop = stop_all + 2 * i + s;
+      }
     }
   const int L = P.L;
     P.S = bp.take<float>((int64_t)L * P.ldn);
@@ -1643,8 +1670,8 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
       return cudaMemsetAsync(st0, 0, (size_t)np * sizeof(DevStatus), st);
     });
   }
-  // Omega^T for every side
-  {
+  // Omega^T for every side (the fixed-rank sketch)
+  if (!adaptive) {
     std::vector<GaussB> t(ns);
     int64_t mldx = 0;
     int mlr = 0;
@@ -1677,11 +1704,21 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
     int nmma = 16;
     for (auto& x : sp) nmma = std::max(nmma, (int)round_up(x.l, 16));
     if (base && !tc_group_build(mode, sp.data(), na, A.buf.data() + off, &nmma)) return false;
-    gb.gemms.push_back(GroupBuild::Gemm{mode, norm, off, na, nmma, ntiles, kmean, slot, 0, 0, gprec});
+    // problems with stop words run from a tile list filtered on the device before the launch
+    bool any_stop = false;
+    for (auto& x : sp) any_stop = any_stop || x.stop != nullptr;
+    const size_t fl = any_stop ? A.add(nullptr, tc_group_filter_bytes(ntiles)) : 0;
+    gb.gemms.push_back(GroupBuild::Gemm{mode, norm, off, na, nmma, ntiles, kmean, slot, 0, 0, gprec, fl});
     const size_t gi = gb.gemms.size() - 1;
     DevStatus* sd = st_all;
     push([gi, &gb, sd](const unsigned char* d, cudaStream_t st) {
       const GroupBuild::Gemm& G = gb.gemms[gi];
+      if (G.fl_off) {
+        cudaError_t e = tc_group_filter(d + G.off, G.nprob, G.ntiles, const_cast<unsigned char*>(d) + G.fl_off, st);
+        if (e != cudaSuccess) return e;
+        return tc_group_launch(G.mode, G.prec, G.norm, d + G.off, G.nprob, G.ntiles, G.nmma, G.stages, G.per_sm, sd,
+                               st, d + G.fl_off);
+      }
       return tc_group_launch(G.mode, G.prec, G.norm, d + G.off, G.nprob, G.ntiles, G.nmma, G.stages, G.per_sm, sd,
                              st);
     });
@@ -1760,8 +1797,27 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
   // grouped 3xTF32 tensor-core product with R^{-1} transposed as its K-major operand; the last
   // pass stores Q transposed.   which 0: Y (M x l) -> Q^T; 1: Z (n x l) -> X^T
   bool orth_ok = true;
-  auto add_orth = [&](int which, int stage0) {
-    const int na = (int)act.size();
+  // one CholeskyQR3 job: src (M x l, ld lds) -> out (row-major, or transposed: out[c * ldo + row]),
+  // with the side's scratch (two intermediates in tmp, Gram partials, W, R^{-1}); a stop word
+  // makes every launch of the job skip a side that has stopped
+  struct OrthJob {
+    const float* src;
+    int64_t lds, M;
+    int l;
+    float* tmp;
+    int64_t lt;
+    double *gpart, *W;
+    float* R;
+    int64_t lp;
+    float* out;
+    int64_t ldo;
+    int transpose;
+    DevStatus* st;
+    int stage;
+    const int* stop;
+  };
+  auto add_orth_jobs = [&](const std::vector<OrthJob>& jobs) {
+    const int na = (int)jobs.size();
     for (int pass = 0; pass < 3; ++pass) {
       std::vector<TcGroupSpec> asp(na);
       std::vector<GramB> gt[2];
@@ -1770,40 +1826,39 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
       int maxlc[2] = {1, 1}, maxch[2] = {1, 1};
       int64_t msum = 0;
       for (int a = 0; a < na; ++a) {
-        const int j = act[a];
-        const GSide& S = gb.sides[j];
-        const int64_t M = which == 0 ? S.M : S.n;
-        const float* src = pass == 0 ? (which == 0 ? S.Y : S.Z) : (pass == 1 ? S.tmp : S.tmp + M * S.lt);
-        const int64_t lds = pass == 0 ? S.lp : S.lt;
+        const OrthJob& J = jobs[a];
+        const int64_t M = J.M;
+        const float* src = pass == 0 ? J.src : (pass == 1 ? J.tmp : J.tmp + M * J.lt);
+        const int64_t lds = pass == 0 ? J.lds : J.lt;
         const int64_t rpc = round_up(cdiv(M, cdiv(M, GROUP_GRAM_ROWS)), 16);
         const int chunks = (int)cdiv(M, rpc);
-        const int cls = S.l > 64 ? 1 : 0;
-        gt[cls].push_back(GramB{src, lds, M, rpc, S.l, chunks, S.gpart});
-        rt[cls].push_back(GramRedB{S.gpart, chunks, S.l, S.W});
-        const double shift = pass == 0 ? 11.0 * ((double)rpc + S.l + 1) * u : 0.0;
+        const int cls = J.l > 64 ? 1 : 0;
+        gt[cls].push_back(GramB{src, lds, M, rpc, J.l, chunks, J.gpart, J.stop});
+        rt[cls].push_back(GramRedB{J.gpart, chunks, J.l, J.W, J.stop});
+        const double shift = pass == 0 ? 11.0 * ((double)rpc + J.l + 1) * u : 0.0;
         const double tau = 8.0 * (double)std::max<int64_t>(rpc, 128) * u;
-        ct[cls].push_back(CholB{S.W, shift, tau, S.R, gb.prs[j / 2].st, S.l,
-                                10 * (j & 1) + stage0 + (pass > 0 ? 1 : 0), (int)S.lp, 0});
-        maxlc[cls] = std::max(maxlc[cls], S.l);
+        ct[cls].push_back(CholB{J.W, shift, tau, J.R, J.st, J.l, J.stage + (pass > 0 ? 1 : 0), (int)J.lp, 0, J.stop});
+        maxlc[cls] = std::max(maxlc[cls], J.l);
         maxch[cls] = std::max(maxch[cls], chunks);
         TcGroupSpec& x = asp[a];
         memset(&x, 0, sizeof(x));
         x.G = src;
         x.ldg = lds;
         x.M = M;
-        x.n = S.l;
-        x.l = S.l;
-        x.Bt = S.R;
-        x.ldb = S.lp;
+        x.n = J.l;
+        x.l = J.l;
+        x.Bt = J.R;
+        x.ldb = J.lp;
+        x.stop = J.stop;
         if (pass < 2) {
-          x.out = pass == 0 ? S.tmp : S.tmp + M * S.lt;
-          x.ldo = S.lt;
+          x.out = pass == 0 ? J.tmp : J.tmp + M * J.lt;
+          x.ldo = J.lt;
         } else {
-          x.out = which == 0 ? S.Qt : S.Xt;
-          x.ldo = which == 0 ? S.ldm : S.ldx;
-          x.transpose_out = 1;
+          x.out = J.out;
+          x.ldo = J.ldo;
+          x.transpose_out = J.transpose;
         }
-        msum += S.l;
+        msum += J.l;
       }
       cur_tag = GSVD_RAND_STAGE_ORTH;
       for (int cls = 0; cls < 2; ++cls) {
@@ -1822,25 +1877,204 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
       cur_tag = GSVD_RAND_STAGE_ORTH;
     }
   };
+  // which 0: Y (M x l) -> Q^T; 1: Z (n x l) -> X^T, for the active sides
+  auto add_orth = [&](int which, int stage0) {
+    std::vector<OrthJob> jobs;
+    for (int j : act) {
+      const GSide& S = gb.sides[j];
+      const int64_t M = which == 0 ? S.M : S.n;
+      jobs.push_back(OrthJob{which == 0 ? S.Y : S.Z, S.lp, M, S.l, S.tmp, S.lt, S.gpart, S.W, S.R, S.lp,
+                             which == 0 ? S.Qt : S.Xt, which == 0 ? S.ldm : S.ldx, 1, gb.prs[j / 2].st,
+                             10 * (j & 1) + stage0, nullptr});
+    }
+    add_orth_jobs(jobs);
+  };
 
-  set_active(-1);
-  if (!add_gemm(0, true, 0)) return fail(h, GSVD_RAND_ERR_ARG, "tensor map of a grouped product rejected");
-  add_orth(0, 1);
-  int qmax = 0;
-  for (auto* q : pv) qmax = std::max(qmax, q->q);
-  for (int it = 0; it < qmax; ++it) {
-    set_active(it);
-    if (!add_gemm(1, false, 2)) return fail(h, GSVD_RAND_ERR_ARG, "tensor map of a grouped product rejected");
-    add_reduce(false);
-    add_orth(1, 3);
-    if (!add_gemm(0, false, 1)) return fail(h, GSVD_RAND_ERR_ARG, "tensor map of a grouped product rejected");
-    add_orth(0, 5);
+  if (!adaptive) {
+    set_active(-1);
+    if (!add_gemm(0, true, 0)) return fail(h, GSVD_RAND_ERR_ARG, "tensor map of a grouped product rejected");
+    add_orth(0, 1);
+    int qmax = 0;
+    for (auto* q : pv) qmax = std::max(qmax, q->q);
+    for (int it = 0; it < qmax; ++it) {
+      set_active(it);
+      if (!add_gemm(1, false, 2)) return fail(h, GSVD_RAND_ERR_ARG, "tensor map of a grouped product rejected");
+      add_reduce(false);
+      add_orth(1, 3);
+      if (!add_gemm(0, false, 1)) return fail(h, GSVD_RAND_ERR_ARG, "tensor map of a grouped product rejected");
+      add_orth(0, 5);
+    }
+  } else {
+    // ---- Algorithm 1 per side, every block one step for the whole batch ----
+    // block i of side s (while its stop word is zero): Omega_i (Philox stream 0x10000 + i,
+    // bi = min(b, cap - i b) columns), Y = G Omega_i, Y <- Y - Q (Q^T Y) twice, P = orth(Y),
+    // P <- orth(P - Q (Q^T P)) into rows [c, c + bi) of Q^T, then ||P^T G||_F^2 and the stop test
+    {
+      int* s0 = stop_all;
+      push([s0, np](const unsigned char*, cudaStream_t st) {
+        return cudaMemsetAsync(s0, 0, 2 * (size_t)np * sizeof(int), st);
+      });
+    }
+    int nbmax = 0;
+    for (auto& P : gb.prs) nbmax = std::max(nbmax, (int)cdiv(P.l, bsz));
+    for (int i = 0; i < nbmax; ++i) {
+      act.clear();
+      for (int j = 0; j < ns; ++j)
+        if ((int64_t)i * bsz < gb.prs[j / 2].l) act.push_back(j);
+      const int na = (int)act.size();
+      const int c = i * bsz;
+      auto bi_of = [&](int j) { return std::min(bsz, gb.prs[j / 2].l - c); };
+      // Omega_i of every side still in the loop (stopped sides draw it too; nothing reads it)
+      cur_tag = GSVD_RAND_STAGE_SETUP;
+      {
+        std::vector<GaussB> t(na);
+        int64_t mldx = 0;
+        int mlr = 0;
+        for (int a = 0; a < na; ++a) {
+          const int j = act[a];
+          const GSide& S = gb.sides[j];
+          const gsvd_rand_pair& q = *pv[j / 2];
+          const int bi = bi_of(j);
+          t[a] = GaussB{S.Xt, S.ldx, S.n, bi, (int)round_up(bi, 16), q.seed, q.pair, (uint32_t)(j & 1),
+                        GSVD_RAND_STREAM_ADAPTIVE + (uint32_t)i, 0};
+          mldx = std::max(mldx, S.ldx);
+          mlr = std::max(mlr, (int)round_up(bi, 16));
+        }
+        const size_t off = A.add(t);
+        push([off, na, mldx, mlr](const unsigned char* d, cudaStream_t st) {
+          return launch_gaussian_kmajor_b(reinterpret_cast<const GaussB*>(d + off), na, mldx, mlr, st);
+        });
+      }
+      // Y = G Omega_i (the first block also sums ||G||_F^2)
+      cur_tag = GSVD_RAND_STAGE_SKETCH;
+      {
+        std::vector<TcGroupSpec> sp(na);
+        int64_t ksum = 0;
+        for (int a = 0; a < na; ++a) {
+          const int j = act[a];
+          const GSide& S = gb.sides[j];
+          TcGroupSpec& x = sp[a];
+          memset(&x, 0, sizeof(x));
+          x.G = S.G;
+          x.ldg = S.ldg;
+          x.M = S.M;
+          x.n = S.n;
+          x.l = bi_of(j);
+          x.Bt = S.Xt;
+          x.ldb = S.ldx;
+          x.out = S.Y;
+          x.ldo = S.lp;
+          x.gnorm_part = i == 0 ? S.gnorm : nullptr;
+          x.stop = i == 0 ? nullptr : S.stop;
+          ksum += S.n;
+        }
+        if (!add_gemm_specs(0, i == 0, -1, sp, ksum / std::max(na, 1), prec))
+          return fail(h, GSVD_RAND_ERR_ARG, "tensor map of a grouped product rejected");
+      }
+      // Y <- Y - Q (Q^T Y) (or P), against the c columns so far
+      auto add_project = [&](bool of_p) {
+        cur_tag = GSVD_RAND_STAGE_ORTH;
+        std::vector<AdaptB> t(na);
+        int64_t mM = 0;
+        int mb = 1;
+        for (int a = 0; a < na; ++a) {
+          const int j = act[a];
+          const GSide& S = gb.sides[j];
+          t[a] = AdaptB{S.Qt, S.ldm, S.M, of_p ? S.Pb : S.Y, S.lp, c, bi_of(j), S.C, S.xpart, S.stop};
+          mM = std::max(mM, S.M);
+          mb = std::max(mb, bi_of(act[a]));
+        }
+        const size_t off = A.add(t);
+        const int cc = c;
+        push([off, na, mM, cc, mb](const unsigned char* d, cudaStream_t st) {
+          return launch_adapt_project_b(reinterpret_cast<const AdaptB*>(d + off), na, mM, cc, mb, st);
+        });
+      };
+      if (c > 0) {
+        add_project(false);
+        add_project(false);
+      }
+      // P = orth(Y): straight into rows [0, bi) of Q^T for the first block, else row-major into
+      // Pb, projected once more and orthonormalised again into rows [c, c + bi)
+      {
+        std::vector<OrthJob> jobs;
+        for (int j : act) {
+          const GSide& S = gb.sides[j];
+          const bool first = c == 0;
+          jobs.push_back(OrthJob{S.Y, S.lp, S.M, bi_of(j), S.tmp, S.lt, S.gpart, S.W, S.R, S.lp,
+                                 first ? S.Qt : S.Pb, first ? S.ldm : S.lp, first ? 1 : 0, gb.prs[j / 2].st,
+                                 10 * (j & 1) + 1, S.stop});
+        }
+        add_orth_jobs(jobs);
+      }
+      if (c > 0) {
+        add_project(true);
+        std::vector<OrthJob> jobs;
+        for (int j : act) {
+          const GSide& S = gb.sides[j];
+          jobs.push_back(OrthJob{S.Pb, S.lp, S.M, bi_of(j), S.tmp, S.lt, S.gpart, S.W, S.R, S.lp,
+                                 S.Qt + (int64_t)c * S.ldm, S.ldm, 1, gb.prs[j / 2].st, 10 * (j & 1) + 3, S.stop});
+        }
+        add_orth_jobs(jobs);
+      }
+      // ||P^T G||_F^2 of the new block on the CUDA cores (FP32 over 2048-row chunks, FP64 sums)
+      cur_tag = GSVD_RAND_STAGE_GTQ;
+      {
+        std::vector<AdaptEnergyB> t(na);
+        int64_t mM = 0, mn = 0;
+        int mb = 1;
+        for (int a = 0; a < na; ++a) {
+          const int j = act[a];
+          const GSide& S = gb.sides[j];
+          t[a] = AdaptEnergyB{S.G, S.ldg, S.M, S.n, S.Qt, S.ldm, c, bi_of(j), S.epart, S.bnorm, S.stop};
+          mM = std::max(mM, S.M);
+          mn = std::max(mn, S.n);
+          mb = std::max(mb, bi_of(j));
+        }
+        const size_t off = A.add(t);
+        push([off, na, mM, mn, mb](const unsigned char* d, cudaStream_t st) {
+          return launch_adapt_energy_b(reinterpret_cast<const AdaptEnergyB*>(d + off), na, mM, mn, mb, st);
+        });
+      }
+      // the stop test of every side (the estimate also goes to the pair's residual slot)
+      {
+        std::vector<AdaptStopB> t(na);
+        for (int a = 0; a < na; ++a) {
+          const int j = act[a];
+          const GSide& S = gb.sides[j];
+          const int bi = bi_of(j);
+          t[a] = AdaptStopB{S.gnorm, S.bnorm, S.state, S.stop, h->cfg.tol,
+                            (int)(tc_group_norm_parts() * cdiv(S.M, 128)), (int)cdiv(S.n * bi, 256), c + bi,
+                            c == 0 ? 1 : 0, c + bi >= gb.prs[j / 2].l ? 1 : 0, gb.prs[j / 2].resid + (j & 1),
+                            gb.prs[j / 2].st};
+        }
+        const size_t off = A.add(t);
+        push([off, na](const unsigned char* d, cudaStream_t st) {
+          return launch_adapt_stop_b(reinterpret_cast<const AdaptStopB*>(d + off), na, st);
+        });
+      }
+    }
+    // rows [stop, cap) of every basis to zero: the projection below then gives the stack of
+    // Algorithm 1's bases (zero rows in between leave the GSVs unchanged)
+    {
+      std::vector<AdaptMaskB> t(ns);
+      int64_t mx = 1;
+      for (int j = 0; j < ns; ++j) {
+        const GSide& S = gb.sides[j];
+        t[j] = AdaptMaskB{S.Qt, S.ldm, S.l, 0, S.stop};
+        mx = std::max(mx, (int64_t)S.l * S.ldm);
+      }
+      const size_t off = A.add(t);
+      push([off, ns, mx](const unsigned char* d, cudaStream_t st) {
+        return launch_adapt_mask_b(reinterpret_cast<const AdaptMaskB*>(d + off), ns, mx, st);
+      });
+    }
   }
   set_active(-1);
   if (!add_gemm(1, false, 2)) return fail(h, GSVD_RAND_ERR_ARG, "tensor map of a grouped product rejected");
   if (!orth_ok) return fail(h, GSVD_RAND_ERR_ARG, "tensor map of a grouped CholeskyQR product rejected");
   add_reduce(true);
-  {
+  if (!adaptive) {  // (the adaptive stop test wrote its final estimates)
     cur_tag = GSVD_RAND_STAGE_GTQ;
     std::vector<ResidB> t(ns);
     for (int j = 0; j < ns; ++j) {
@@ -1955,6 +2189,21 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
       return launch_select_topr_b(reinterpret_cast<const SelB*>(d + off), np, mL, st);
     });
   }
+  // adaptive: the columns beyond the pairs the stopped bases hold (stop1 + stop2 < r)
+  size_t trim_off = 0;
+  if (adaptive) {
+    std::vector<AdaptTrimB> t(np);
+    for (int i = 0; i < np; ++i) {
+      const GPair& P = gb.prs[i];
+      t[i] = AdaptTrimB{P.Zr, P.C1, P.L, P.k, gb.sides[2 * i].stop, gb.sides[2 * i + 1].stop};
+    }
+    trim_off = A.add(t);
+    const size_t off = trim_off;
+    const int mL = maxL, mk = maxk;
+    push([off, np, mL, mk](const unsigned char* d, cudaStream_t st) {
+      return launch_adapt_trim_b(reinterpret_cast<const AdaptTrimB*>(d + off), np, mL, mk, 0, st);
+    });
+  }
   {
     std::vector<DgemmB> t(np);
     for (int i = 0; i < np; ++i) {
@@ -1978,6 +2227,13 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
     push([off, np, mk](const unsigned char* d, cudaStream_t st) {
       return launch_dgemm_b<double, double>(reinterpret_cast<const DgemmB*>(d + off), np, mk, mk, st, true);
     });
+    if (adaptive) {
+      const size_t toff = trim_off;
+      const int mL = maxL;
+      push([toff, np, mL, mk](const unsigned char* d, cudaStream_t st) {
+        return launch_adapt_trim_b(reinterpret_cast<const AdaptTrimB*>(d + toff), np, mL, mk, 1, st);
+      });
+    }
   }
   add_eig(true);
   add_oa(true);
@@ -2024,15 +2280,22 @@ int solve_grouped(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs) {
   const int prec = h->cfg.prec;
   if (prec != GSVD_RAND_TF32 && prec != GSVD_RAND_TF32X3)
     return fail(h, GSVD_RAND_ERR_UNSUPPORTED, "grouped solves run the TF32 / 3xTF32 tensor-core products");
-  if (h->cfg.adaptive || h->cfg.use_learned || (h->cfg.flags & GSVD_RAND_FLAG_BASIS_ONLY))
-    return fail(h, GSVD_RAND_ERR_UNSUPPORTED, "grouped solves are fixed-rank solves with the compressed-pair GSVD");
+  if (h->cfg.use_learned || (h->cfg.flags & GSVD_RAND_FLAG_BASIS_ONLY))
+    return fail(h, GSVD_RAND_ERR_UNSUPPORTED, "grouped solves take fixed-rank or adaptive bases and the compressed-pair GSVD");
+  const bool adaptive = h->cfg.adaptive != 0;
+  if (adaptive && (h->cfg.block_b < 1 || h->cfg.block_b > ADAPT_BMAX || !(h->cfg.tol >= 0.0)))
+    return fail(h, GSVD_RAND_ERR_ARG, "grouped adaptive solves need 1 <= block_b <= %d and tol >= 0", ADAPT_BMAX);
   if (h->tc_ok < 0) h->tc_ok = tc_available(h->cfg.device) ? 1 : 0;
   if (!h->tc_ok) return fail(h, GSVD_RAND_ERR_UNSUPPORTED, "tensor-core path unavailable on this device");
   CU(cudaSetDevice(h->cfg.device));
   // the key of this batch: every argument but the status slots
-  std::vector<unsigned char> key((size_t)npairs * sizeof(gsvd_rand_pair) + 2 * sizeof(int));
+  std::vector<unsigned char> key((size_t)npairs * sizeof(gsvd_rand_pair) + 2 * sizeof(int) + 2 * sizeof(double));
   memcpy(key.data(), &prec, sizeof(int));
   memcpy(key.data() + sizeof(int), &h->cfg.flags, sizeof(int));
+  {  // the adaptive parameters (zero for fixed-rank solves)
+    const double ab[2] = {adaptive ? (double)h->cfg.block_b : 0.0, adaptive ? h->cfg.tol : -1.0};
+    memcpy(key.data() + (size_t)npairs * sizeof(gsvd_rand_pair) + 2 * sizeof(int), ab, sizeof(ab));
+  }
   for (int i = 0; i < npairs; ++i) {
     // the outputs are copied out of the results block after the graph: not part of the key
     gsvd_rand_pair c;
@@ -2070,9 +2333,11 @@ int solve_grouped(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs) {
     g->valid.clear();
     for (int i = 0; i < npairs; ++i) {
       gsvd_rand_pair& q = pairs[i];
-      const int64_t l = (int64_t)q.k + q.oversample;
+      // fixed rank: l = k + oversample; adaptive: the column cap min(m, p, n, ADAPT_CMAX)
+      const int64_t l = adaptive ? std::min<int64_t>(std::min(std::min(q.m, q.p), q.n), ADAPT_CMAX)
+                                 : (int64_t)q.k + q.oversample;
       bool ok = q.G1 && q.G2 && q.alpha && q.beta && q.m >= 1 && q.p >= 1 && q.n >= 1 && q.ld1 >= q.n &&
-                q.ld2 >= q.n && q.k >= 1 && q.oversample >= 0 && q.q >= 0 && q.q <= 16 && l <= 128 &&
+                q.ld2 >= q.n && q.k >= 1 && q.oversample >= 0 && q.q >= 0 && q.q <= 16 && l >= 1 && l <= 128 &&
                 l <= std::min(std::min(q.m, q.p), q.n) && is_device_ptr(q.G1) && is_device_ptr(q.G2) &&
                 tc_shape_ok(q.G1, q.ld1, (int)l) && tc_shape_ok(q.G2, q.ld2, (int)l);
       q.status = ok ? GSVD_RAND_OK : GSVD_RAND_ERR_ARG;
@@ -2251,11 +2516,17 @@ int solve_grouped(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs) {
   CU(cudaStreamSynchronize(gs));
   const DevStatus* sth = reinterpret_cast<const DevStatus*>(g->host);
   const double* rh = reinterpret_cast<const double*>(g->host + ((nv * sizeof(DevStatus) + 255) & ~size_t(255)));
+  const int* stops = adaptive ? reinterpret_cast<const int*>(g->host + (g->stop_off - g->res_off)) : nullptr;
+  g->cols.assign(2 * (size_t)nv, 0);
   int first_bad = -1;
   for (int t = 0; t < nv; ++t) {
     gsvd_rand_pair& q = pairs[g->valid[t]];
     const GroupState::Out& o = g->outs[t];
     q.status = sth[t].code;
+    if (adaptive) {
+      g->cols[2 * t] = stops[2 * t];
+      g->cols[2 * t + 1] = stops[2 * t + 1];
+    }
     if (!is_device_ptr(q.alpha)) memcpy(q.alpha, g->host + (o.a_off - g->res_off), (size_t)o.k * sizeof(double));
     if (!is_device_ptr(q.beta)) memcpy(q.beta, g->host + (o.b_off - g->res_off), (size_t)o.k * sizeof(double));
     if (q.resid_out) {
@@ -2265,7 +2536,8 @@ int solve_grouped(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs) {
         memcpy(q.resid_out, rh + 2 * t, 2 * sizeof(double));
     }
     if (q.r_out) {
-      const int r = q.k;
+      // adaptive: the pairs the bases hold, min(k, columns of both sides)
+      const int r = adaptive ? std::min(o.k, stops[2 * t] + stops[2 * t + 1]) : q.k;
       if (is_device_ptr(q.r_out))
         CU(cudaMemcpy(q.r_out, &r, sizeof(int), cudaMemcpyHostToDevice));
       else
@@ -2697,6 +2969,21 @@ int gsvd_rand_solve_grouped(gsvd_rand_t h, int npairs, gsvd_rand_pair* pairs) {
   if (!h || npairs < 0 || (npairs > 0 && !pairs)) return GSVD_RAND_ERR_ARG;
   if (npairs == 0) return GSVD_RAND_OK;
   return solve_grouped_staged(h, npairs, pairs);
+}
+
+int gsvd_rand_grouped_basis_cols(gsvd_rand_t h, int* cols, int npairs) {
+  if (!h || !cols || npairs < 0) return GSVD_RAND_ERR_ARG;
+  if (!h->grp) return fail(h, GSVD_RAND_ERR_ARG, "no grouped solve on this context");
+  const GroupState* g = h->grp;
+  for (int i = 0; i < 2 * npairs; ++i) cols[i] = 0;
+  for (size_t t = 0; t < g->valid.size() && 2 * t + 1 < g->cols.size(); ++t) {
+    const int i = g->valid[t];
+    if (i < npairs) {
+      cols[2 * i] = g->cols[2 * t];
+      cols[2 * i + 1] = g->cols[2 * t + 1];
+    }
+  }
+  return GSVD_RAND_OK;
 }
 
 int gsvd_rand_grouped_info(gsvd_rand_t h, int* tuned, int64_t* captures, int64_t* replays, int64_t* launches) {

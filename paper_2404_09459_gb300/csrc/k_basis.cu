@@ -1152,11 +1152,13 @@ cudaError_t launch_reduce_splits_b(const ReduceB* tab, int nprob, int64_t max_nl
 
 __global__ __launch_bounds__(CHOL64_THREADS, 1) void chol64_b_kernel(const CholB* __restrict__ tab) {
   const CholB& a = tab[blockIdx.x];
+  if (a.stop && *a.stop) return;
   chol64_body<float>(a.W, a.l, a.shift_coef, a.tau_rel, a.Rinv, a.st, a.stage, a.ldt);
 }
 
 __global__ __launch_bounds__(CHOL_THREADS) void chol_shift_b_kernel(const CholB* __restrict__ tab) {
   const CholB& a = tab[blockIdx.x];
+  if (a.stop && *a.stop) return;
   chol_shift_body<float>(a.W, a.l, a.shift_coef, a.tau_rel, a.Rinv, a.st, a.stage, nullptr, 1, a.ldt);
 }
 
@@ -1189,7 +1191,7 @@ constexpr int GB_SLAB = 32, GB_LP = 128, GB_LS = GB_LP + 4;
 __global__ __launch_bounds__(256, 2) void gram_blocks_b_kernel(const GramB* __restrict__ tab) {
   const GramB& g = tab[blockIdx.z];
   const int c = blockIdx.x;
-  if (c >= g.chunks) return;
+  if (c >= g.chunks || (g.stop && *g.stop)) return;
   __shared__ __align__(16) float Ys[2][GB_SLAB * GB_LS];
   const int tid = threadIdx.x, l = g.l;
   const int LB = (l + 7) >> 3, nblk = LB * (LB + 1) / 2;
@@ -1309,7 +1311,7 @@ __global__ void gram_sum_b_kernel(const GramRedB* __restrict__ tab) {
   const GramRedB& a = tab[blockIdx.z];
   const int64_t ll = (int64_t)a.l * a.l;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= ll) return;
+  if (e >= ll || (a.stop && *a.stop)) return;
   const int i = (int)(e / a.l), j = (int)(e % a.l);
   if (j < i) return;
   double s = 0.0;

@@ -115,11 +115,15 @@ __device__ __forceinline__ float hash_unit(uint32_t a, uint32_t b) {
 // eigenvalue are replaced within their own eigenspace.  Values growing past 2^60 rescale the
 // whole vector (the same system with a scaled right-hand side).  A non-finite result falls
 // back to the pseudo-random start itself.  x has stride xs.
+// from_x: the right-hand side is x itself (a further step of inverse iteration on a vector from
+// which the accepted columns were projected out: the step amplifies the missing eigenvector
+// of the cluster, where a first step from a random start is dominated by an accepted one).
 __device__ void inverse_iteration_start(const float* __restrict__ e, const float* __restrict__ dm, int N,
-                                        uint32_t j, float* x, int64_t xs) {
-  x[(int64_t)(N - 1) * xs] = hash_unit(j, (uint32_t)(N - 1));
+                                        uint32_t j, float* x, int64_t xs, bool from_x = false) {
+  if (!from_x) x[(int64_t)(N - 1) * xs] = hash_unit(j, (uint32_t)(N - 1));
   for (int i = N - 2; i >= 0; --i) {
-    float y = hash_unit(j, (uint32_t)i) - (e[i] / dm[i + 1]) * x[(int64_t)(i + 1) * xs];
+    const float rhs = from_x ? x[(int64_t)i * xs] : hash_unit(j, (uint32_t)i);
+    float y = rhs - (e[i] / dm[i + 1]) * x[(int64_t)(i + 1) * xs];
     if (fabsf(y) > 1.15e18f) {
       for (int u = i + 1; u < N; ++u) x[(int64_t)u * xs] *= 8.67e-19f;
       y *= 8.67e-19f;
@@ -683,12 +687,13 @@ __device__ __forceinline__ void eig128_body(const double* __restrict__ Ain, int 
       // pass 1: the replacement by inverse iteration; when it falls (nearly) inside the span of
       // the accepted columns (an eigenvalue of T closer to accepted ones than to the missing
       // one), a second attempt from a plain pseudo-random start, which keeps the basis orthonormal
-      for (int att = 0; att < (pass == 1 ? 2 : 1); ++att) {
+      for (int att = 0; att < (pass == 1 ? 3 : 1); ++att) {
       if (pass == 1) {
-        // U pivots of the twisted factorisation at lambda_j are still in row j of Us
+        // U pivots of the twisted factorisation at lambda_j are still in row j of Us; attempt 1
+        // repeats inverse iteration on the projected residual, attempt 2 a plain random start
         if (tid == 0) {
-          if (att == 0)
-            inverse_iteration_start(s_e, Us + (size_t)j * lda, N, (uint32_t)j, Zs + j, lda);
+          if (att < 2)
+            inverse_iteration_start(s_e, Us + (size_t)j * lda, N, (uint32_t)j, Zs + j, lda, att == 1);
           else
             for (int i = 0; i < N; ++i) Zs[(size_t)i * lda + j] = hash_unit((uint32_t)j ^ 0x5bd1e995u, (uint32_t)i);
         }
@@ -735,7 +740,7 @@ __device__ __forceinline__ void eig128_body(const double* __restrict__ Ain, int 
         if (t == 0) {
           s_nrm = dep && pass == 0 ? 0.f : rsqrtf(s2 > 0.f ? s2 : 1.f);
           s_flag[j] = dep && pass == 0 ? -1.f : 1.f;
-          s_retry = (pass == 1 && att == 0 && dep) ? 1 : 0;
+          s_retry = (pass == 1 && att < 2 && dep) ? 1 : 0;
         }
       }
       __syncthreads();
@@ -1112,12 +1117,13 @@ __device__ __forceinline__ void eig_big_body(const double* __restrict__ Ain, int
       if (pass == 1 && s_flag[j] >= 0.f) continue;
       // pass 1: inverse iteration, then (when that falls inside the accepted span) a plain
       // pseudo-random start, as in eig128
-      for (int att = 0; att < (pass == 1 ? 2 : 1); ++att) {
+      for (int att = 0; att < (pass == 1 ? 3 : 1); ++att) {
       if (pass == 1) {
-        // U pivots of the twisted factorisation at lambda_j are still in column j of UT
+        // U pivots of the twisted factorisation at lambda_j are still in column j of UT; attempt 1
+        // repeats inverse iteration on the projected residual, attempt 2 a plain random start
         if (tid == 0) {
-          if (att == 0)
-            inverse_iteration_start(s_e, UT + (size_t)j * N, N, (uint32_t)j, Zj, 1);
+          if (att < 2)
+            inverse_iteration_start(s_e, UT + (size_t)j * N, N, (uint32_t)j, Zj, 1, att == 1);
           else
             for (int i = 0; i < N; ++i) Zj[i] = hash_unit((uint32_t)j ^ 0x5bd1e995u, (uint32_t)i);
         }
@@ -1164,7 +1170,7 @@ __device__ __forceinline__ void eig_big_body(const double* __restrict__ Ain, int
         if (t == 0) {
           s_nrm = dep && pass == 0 ? 0.f : rsqrtf(s2 > 0.f ? s2 : 1.f);
           s_flag[j] = dep && pass == 0 ? -1.f : 1.f;
-          s_retry = (pass == 1 && att == 0 && dep) ? 1 : 0;
+          s_retry = (pass == 1 && att < 2 && dep) ? 1 : 0;
         }
       }
       __syncthreads();

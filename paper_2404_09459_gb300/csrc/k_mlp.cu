@@ -13,6 +13,7 @@
 // (no atomics), so training is reproducible bit for bit.
 #include <cuda_bf16.h>
 
+#include "gsvd_rand.h"
 #include "kernels.h"
 
 namespace gsvdr {
@@ -344,4 +345,44 @@ cudaError_t mlp_adam(float* P, float* m, float* v, const float* grad, int t, flo
   return launched();
 }
 
+}  // namespace gsvdr
+
+namespace gsvdr {
+namespace {
+// The plan of each row of logits (B x (KCLS + QCLS)): kb = the smallest k bucket whose cumulative
+// softmax probability reaches `quantile`, q = the most probable q class (first on ties), then
+// k = min(KBUCKET (kb + 1), kcap[i], lmax[i] - oversample[i]), at least 1.  A thread per row.
+__global__ void mlp_plan_kernel(const float* __restrict__ z, int B, float quantile, const int* __restrict__ kcap,
+                                const int* __restrict__ lmax, const int* __restrict__ os, int* __restrict__ plan) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B) return;
+  const float* zi = z + (int64_t)i * (GSVD_RAND_MLP_KCLS + GSVD_RAND_MLP_QCLS);
+  double mx = zi[0];
+  for (int j = 1; j < GSVD_RAND_MLP_KCLS; ++j) mx = fmax(mx, (double)zi[j]);
+  double tot = 0.0;
+  for (int j = 0; j < GSVD_RAND_MLP_KCLS; ++j) tot += exp((double)zi[j] - mx);
+  int kb = 0;
+  double cum = 0.0;
+  for (kb = 0; kb < GSVD_RAND_MLP_KCLS - 1; ++kb) {
+    cum += exp((double)zi[kb] - mx) / tot;
+    if (cum >= (double)quantile) break;
+  }
+  int q = 0;
+  for (int j = 1; j < GSVD_RAND_MLP_QCLS; ++j)
+    if (zi[GSVD_RAND_MLP_KCLS + q] < zi[GSVD_RAND_MLP_KCLS + j]) q = j;
+  int k = GSVD_RAND_MLP_KBUCKET * (kb + 1);
+  if (kcap) k = min(k, kcap[i]);
+  if (lmax) k = min(k, lmax[i] - (os ? os[i] : 0));
+  plan[3 * i] = max(k, 1);
+  plan[3 * i + 1] = q;
+  plan[3 * i + 2] = kb;
+}
+}  // namespace
+
+cudaError_t launch_mlp_plan(const float* logits, int B, float quantile, const int* kcap, const int* lmax,
+                            const int* os, int* plan, cudaStream_t st) {
+  if (B <= 0) return cudaSuccess;
+  mlp_plan_kernel<<<(B + 127) / 128, 128, 0, st>>>(logits, B, quantile, kcap, lmax, os, plan);
+  return launched();
+}
 }  // namespace gsvdr

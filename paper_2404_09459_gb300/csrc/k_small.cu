@@ -764,8 +764,10 @@ __device__ __forceinline__ void cs_norms_body(const double* __restrict__ U1, int
     for (int k = 0; k < l1; ++k) a = fma(U1[(int64_t)k * r + i], U1[(int64_t)k * r + i], a);
     for (int k = 0; k < l2; ++k) b = fma(U2[(int64_t)k * r + i], U2[(int64_t)k * r + i], b);
     double nn = sqrt(a + b);
-    sa[i] = nn > 0.0 ? sqrt(a) / nn : 0.0;
-    sb[i] = nn > 0.0 ? sqrt(b) / nn : 0.0;
+    // a column of zero norm is no pair (the unused columns of a grouped adaptive solve):
+    // marked -1, which sorts after every pair
+    sa[i] = nn > 0.0 ? sqrt(a) / nn : -1.0;
+    sb[i] = nn > 0.0 ? sqrt(b) / nn : -1.0;
   }
   __syncthreads();
   for (int i = tid; i < r; i += nt) {

@@ -35,6 +35,7 @@ struct TcGroupProb {  // CUtensorMap members carry their own (>= 64-byte) alignm
   int64_t ldo, out_rows, kdim, rows_per_split, split_stride;
   double* gnorm_part; // GX with the fused norm: 4 partial sums of G^2 per row tile
   int ncols, nmma, tiles_x, transpose_out;  // transpose_out: out[c * ldo + row] (GX)
+  const int* stop;    // null, or the stop word of the problem (non-zero: its tiles are filtered out)
 };
 
 namespace {
@@ -831,8 +832,11 @@ __global__ __launch_bounds__(TG_THREADS, 2) void tc_group_kernel(const TcGroupPr
                                                               const int2* __restrict__ tiles, int ntiles,
                                                               int nmma_max, int acc_stride, int tmem_cols,
                                                               int ta_col0, int nacc, int stages,
-                                                              DevStatus* st_glob) {
+                                                              DevStatus* st_glob, const int* ntiles_dev) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // a filtered launch: the tile list holds the active problems' tiles, their count in memory
+  // written before the launch (every role reads the same count, so the pipelines agree)
+  if (ntiles_dev) ntiles = *ntiles_dev;
   constexpr int BKE = 32;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -1186,6 +1190,7 @@ bool tc_group_build(int mode, const TcGroupSpec* specs, int nprob, void* host, i
     p.nmma = nmma;
     p.gnorm_part = s.gnorm_part;
     p.transpose_out = s.transpose_out;
+    p.stop = s.stop;
     if (mode == 0) {
       if (!make_map(&p.mapA, s.G, (uint64_t)s.n, (uint64_t)s.M, (uint64_t)s.ldg, TC_BM)) return false;
       if (!make_map(&p.mapB, s.Bt, (uint64_t)s.n, (uint64_t)nmma, (uint64_t)s.ldb, (uint32_t)nmma)) return false;
@@ -1226,8 +1231,70 @@ int tc_group_max_stages(int mode, int prec, int nmma_max, int per_sm) {
   return std::min(budget / stage, cap);
 }
 
+namespace {
+// Stable compaction of the tile list to the problems whose stop word is zero (one CTA: a
+// block-wide scan per 1024 tiles).  out: the kept tiles, then (at out_count) their number.
+__global__ __launch_bounds__(1024) void tc_group_filter_kernel(const TcGroupProb* __restrict__ probs,
+                                                               const int2* __restrict__ tiles, int ntiles,
+                                                               int2* __restrict__ out, int* __restrict__ out_count) {
+  __shared__ int s_warp[32];
+  __shared__ int s_base;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_base = 0;
+  __syncthreads();
+  for (int t0 = 0; t0 < ntiles; t0 += 1024) {
+    const int t = t0 + tid;
+    int2 tr = make_int2(0, 0);
+    int keep = 0;
+    if (t < ntiles) {
+      tr = tiles[t];
+      const int* sw = probs[tr.x].stop;
+      keep = (sw == nullptr || *sw == 0) ? 1 : 0;
+    }
+    // inclusive scan of keep over the block
+    int v = keep;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += u;
+    }
+    if (lane == 31) s_warp[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+      int w = s_warp[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += u;
+      }
+      s_warp[lane] = w;
+    }
+    __syncthreads();
+    const int before = (warp > 0 ? s_warp[warp - 1] : 0) + v - keep;
+    if (keep) out[s_base + before] = tr;
+    __syncthreads();
+    if (tid == 1023) s_base += s_warp[31];
+    __syncthreads();
+  }
+  if (tid == 0) *out_count = s_base;
+}
+}  // namespace
+
+size_t tc_group_filter_bytes(int64_t ntiles) { return round_up(ntiles * (int64_t)sizeof(int2), 256) + 256; }
+
+cudaError_t tc_group_filter(const void* dev_table, int nprob, int64_t ntiles, void* dev_filtered, cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+  const TcGroupProb* probs = static_cast<const TcGroupProb*>(dev_table);
+  const int2* tiles = reinterpret_cast<const int2*>(static_cast<const unsigned char*>(dev_table) +
+                                                    round_up((int64_t)nprob * (int64_t)sizeof(TcGroupProb), 256));
+  int2* out = static_cast<int2*>(dev_filtered);
+  int* cnt = reinterpret_cast<int*>(static_cast<unsigned char*>(dev_filtered) +
+                                    round_up(ntiles * (int64_t)sizeof(int2), 256));
+  tc_group_filter_kernel<<<1, 1024, 0, st>>>(probs, tiles, (int)ntiles, out, cnt);
+  return launched();
+}
+
 cudaError_t tc_group_launch(int mode, int prec, bool norm, const void* dev_table, int nprob, int64_t ntiles,
-                            int nmma_max, int stages, int per_sm, DevStatus* st_dev, cudaStream_t st) {
+                            int nmma_max, int stages, int per_sm, DevStatus* st_dev, cudaStream_t st,
+                            const void* dev_filtered) {
   if (ntiles <= 0) return cudaSuccess;
   const bool split = prec == 3;
   const int acc_stride = (int)round_up(nmma_max, 32);
@@ -1240,6 +1307,12 @@ cudaError_t tc_group_launch(int mode, int prec, bool norm, const void* dev_table
   const TcGroupProb* probs = static_cast<const TcGroupProb*>(dev_table);
   const int2* tiles = reinterpret_cast<const int2*>(static_cast<const unsigned char*>(dev_table) +
                                                     round_up((int64_t)nprob * (int64_t)sizeof(TcGroupProb), 256));
+  const int* ntiles_dev = nullptr;
+  if (dev_filtered) {
+    tiles = static_cast<const int2*>(dev_filtered);
+    ntiles_dev = reinterpret_cast<const int*>(static_cast<const unsigned char*>(dev_filtered) +
+                                              round_up(ntiles * (int64_t)sizeof(int2), 256));
+  }
   // the dynamic shared memory also caps the CTAs per SM at per_sm (TMEM columns stay within 512)
   size_t smem = group_smem_bytes(mode, split, nmma_max, stages);
   const size_t floor_smem = per_sm >= 2 ? 80 * 1024 : 120 * 1024;
@@ -1249,7 +1322,8 @@ cudaError_t tc_group_launch(int mode, int prec, bool norm, const void* dev_table
   do {                                                                                                       \
     cudaFuncSetAttribute(tc_group_kernel<M_, N_, S_>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024); \
     tc_group_kernel<M_, N_, S_><<<grid, TG_THREADS, smem, st>>>(probs, tiles, (int)ntiles, nmma_max, acc_stride, \
-                                                                tmem_cols, ta_col0, nacc, stages, st_dev);   \
+                                                                tmem_cols, ta_col0, nacc, stages, st_dev,    \
+                                                                ntiles_dev);                                 \
   } while (0)
   if (mode == 0) {
     if (norm && split) GSVDR_TG(0, true, true);

@@ -239,6 +239,12 @@ cudaError_t mlp_loss_grad(const float* P, const float* norm, const float* X, con
                           const int* rows, int B, float* grad, float* loss, float* scratch, cudaStream_t st);
 cudaError_t mlp_adam(float* P, float* m, float* v, const float* grad, int t, float lr, float b1, float b2, float eps,
                      cudaStream_t st);
+// The (k, q) plan of B rows of logits on the device: plan[3 i] = k (the top of the smallest k
+// bucket whose cumulative softmax probability reaches quantile, clipped to kcap[i] and to
+// lmax[i] - os[i]; any of the three arrays may be null), plan[3 i + 1] = q (argmax),
+// plan[3 i + 2] = the k bucket.
+cudaError_t launch_mlp_plan(const float* logits, int B, float quantile, const int* kcap, const int* lmax,
+                            const int* os, int* plan, cudaStream_t st);
 
 // ---- batched forms: one launch for many problems ------------------------------
 // Each launcher takes a table of per-problem arguments in device memory (nprob
@@ -268,11 +274,13 @@ struct GramB {  // Gram partials of Y (M x l, FP32, l <= 128) over `chunks` chun
   int64_t ldy, M, rpc;
   int l, chunks;
   double* part;
+  const int* stop;  // null, or a stop word: the entry is skipped once it is non-zero
 };
 struct GramRedB {  // W = sum of the chunk partials
   const double* part;
   int chunks, l;
   double* W;
+  const int* stop;
 };
 // The whole upper triangle of a chunk's Y^T Y in one CTA (register blocks, FP32 FMA over
 // the chunk's rows), then the chunk sums in FP64 a thread per entry (both deterministic).
@@ -285,11 +293,76 @@ struct CholB {  // shifted Cholesky with the inverse factor (FP32 factor), as la
   float* Rinv;   // ldt == 0: R^{-1} row-major (l x l); ldt > 0: its transpose, Rinv[j * ldt + c] = R^{-1}[c][j]
   DevStatus* st;
   int l, stage, ldt, pad;
+  const int* stop;  // null, or a stop word: the entry is skipped once it is non-zero
 };
 
 // max_l <= 64: the register-resident elimination; <= 128: the shared-memory one.
 cudaError_t launch_chol_b(const CholB* tab, int nprob, int max_l, cudaStream_t st);
 
+
+// ---- grouped Algorithm 1 (k_adapt.cu) -------------------------------------------------
+// Blocks of b <= ADAPT_BMAX columns, bases of at most ADAPT_CMAX columns per side.  Every
+// table entry carries the side's stop word (0 while it adds blocks, then its column count):
+// entries of stopped sides return at once.
+constexpr int ADAPT_BMAX = 32;
+constexpr int ADAPT_CMAX = 128;
+struct AdaptB {  // Y (M x bi, ld ldy) <- Y - Q (Q^T Y), Q the first c rows of Qt (K-major, ld ldq)
+  const float* Qt;
+  int64_t ldq, M;
+  float* Y;
+  int64_t ldy;
+  int c, bi;
+  double* C;      // c x bi: Q^T Y (FP64 sums of FP32 chunk products)
+  double* xpart;  // adapt_xpart_elems(M, c, bi) chunk partials
+  const int* stop;
+};
+int64_t adapt_xpart_elems(int64_t M, int c, int bi);
+// The projection of every entry (max_bi <= ADAPT_BMAX, max_c <= ADAPT_CMAX): three launches.
+cudaError_t launch_adapt_project_b(const AdaptB* tab, int nprob, int64_t max_M, int max_c, int max_bi,
+                                   cudaStream_t st);
+struct AdaptEnergyB {  // ||P^T G||_F^2 of the block P = rows [c, c + bi) of Qt, on the CUDA cores
+  const float* G;
+  int64_t ldg, M, n;
+  const float* Qt;
+  int64_t ldq;
+  int c, bi;
+  float* part;    // adapt_energy_part_elems(M, n, bi) chunk partials
+  double* epart;  // cdiv(n bi, 256) partial sums of squares
+  const int* stop;
+};
+int64_t adapt_energy_part_elems(int64_t M, int64_t n, int bi);
+cudaError_t launch_adapt_energy_b(const AdaptEnergyB* tab, int nprob, int64_t max_M, int64_t max_n, int max_bi,
+                                  cudaStream_t st);
+struct AdaptStopB {  // the stop test of a side after one block
+  const double* gpart;  // first block: the ng partial sums of ||G||_F^2
+  const double* bpart;  // this block: the nb partial sums of ||P_i^T G||_F^2
+  double* state;        // ||G||^2, running sum, estimate
+  int* stop;
+  double tol;
+  int ng, nb, cols, first, last;  // cols: columns after this block; last: the cap is reached
+  double* resid_out;              // the pair's residual slot of this side (the estimate)
+  DevStatus* st;                  // TOL_MISS when the cap is reached above tol
+};
+cudaError_t launch_adapt_stop_b(const AdaptStopB* tab, int nprob, cudaStream_t st);
+struct AdaptMaskB {  // rows [*stop, cap) of Qt (ld ldq) set to zero
+  float* Qt;
+  int64_t ldq;
+  int cap, pad;
+  const int* stop;
+};
+cudaError_t launch_adapt_mask_b(const AdaptMaskB* tab, int nprob, int64_t max_elems, cudaStream_t st);
+// A pair of a grouped adaptive solve holds r_act = min(r, stop1 + stop2) pairs; the compressed-pair
+// GSVD runs with the static r.  mode 0: columns [r_act, r) of Zr (L x r) to zero after the top-r
+// selection; mode 1: C1[j][j] = -1 for j >= r_act after C1 = Z1^T Z1, so that those columns stay
+// apart from every real eigenvector and end as pairs of zero norm (cs_norms marks them -1, last).
+struct AdaptTrimB {
+  double* Zr;
+  double* C1;
+  int L, r;
+  const int* stop1;
+  const int* stop2;
+};
+cudaError_t launch_adapt_trim_b(const AdaptTrimB* tab, int nprob, int max_L, int max_r, int mode, cudaStream_t st);
 
 struct ResidB {  // cumulated residual of one side
   const double* gpart;

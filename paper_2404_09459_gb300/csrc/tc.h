@@ -61,6 +61,7 @@ struct TcGroupSpec {
   int64_t rps, split_stride;
   double* gnorm_part;
   int transpose_out;
+  const int* stop;  // null, or the problem's stop word: its tiles are left out once it is non-zero
 };
 int tc_group_norm_parts();
 // Tiles of a grouped launch (128-row tiles in mode 0; column tiles x splits in mode 1).
@@ -75,6 +76,12 @@ int tc_group_max_stages(int mode, int prec, int nmma_max, int per_sm);
 // One persistent launch over every tile of the table (prec 3 = 3xTF32, else TF32;
 // norm: mode 0 with the fused sum of G^2).  A timed-out wait sets TIMEOUT in st_dev.
 cudaError_t tc_group_launch(int mode, int prec, bool norm, const void* dev_table, int nprob, int64_t ntiles,
-                            int nmma_max, int stages, int per_sm, DevStatus* st_dev, cudaStream_t st);
+                            int nmma_max, int stages, int per_sm, DevStatus* st_dev, cudaStream_t st,
+                            const void* dev_filtered = nullptr);
+// Problems with stop words: tc_group_filter writes into dev_filtered (tc_group_filter_bytes)
+// the tiles of the problems whose stop word is zero, in table order, and their count; a
+// launch given dev_filtered runs those tiles only (every role walks the same list).
+size_t tc_group_filter_bytes(int64_t ntiles);
+cudaError_t tc_group_filter(const void* dev_table, int nprob, int64_t ntiles, void* dev_filtered, cudaStream_t st);
 
 }  // namespace gsvdr

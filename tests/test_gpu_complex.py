@@ -49,8 +49,10 @@ def _check(prec, G1, G2, k, os_, q, seed, device=True):
     dth = np.abs(np.arctan2(a, b) - np.arctan2(ref["alpha"], ref["beta"]))
     assert np.max(dth) <= max(1e-4, TOL[prec])
     assert np.all(np.diff(a) <= TOL[prec]) and np.all(np.diff(b) >= -TOL[prec])
-    # the cumulated residual of the realified pair is the complex pair's (||rho(M)||_F^2 = 2 ||M||_F^2)
-    rtol = 1e-8 if prec == "fp64" else 1e-4
+    # the cumulated residual of the realified pair is the complex pair's (||rho(M)||_F^2 = 2 ||M||_F^2);
+    # ||B||^2 carries the products' relative error, so it is held on the squared scale (2^-10 for
+    # single-pass TF32, as for real pairs)
+    rtol = 1e-8 if prec == "fp64" else (4e-3 if prec == "tf32" else 1e-4)
     for s in range(2):
         assert abs(out["resid"][s] ** 2 - ref[f"resid{s + 1}"] ** 2) <= rtol, (s, out["resid"], ref[f"resid{s + 1}"])
     return a, b, ref

@@ -139,7 +139,7 @@ def test_grouped_new_batch_recaptures_and_bad_pair_is_left_out():
     np.testing.assert_array_equal(good[0]["alpha"].cpu().numpy(), again[0]["alpha"].cpu().numpy())
 
 
-def test_grouped_refuses_fp64_and_adaptive_contexts():
+def test_grouped_refuses_fp64_contexts():
     specs = _specs(15, 1)
     mats = [planted_pair(s)[:2] for s in specs]
     with P.Context("fp64") as ctx:
@@ -251,3 +251,62 @@ def test_grouped_host_inputs_staged_and_replayed():
         for key in ("alpha", "beta"):
             np.testing.assert_array_equal(r[key].cpu().numpy(), np.asarray(a[key]))
             np.testing.assert_array_equal(np.asarray(a[key]), np.asarray(b[key]))
+
+
+def _adaptive_specs():
+    # uneven pairs whose planted rank sets where Algorithm 1 stops: blocks of 8 columns until the
+    # cumulated residual drops below tol (2e-3); before the block that covers the rank the
+    # uncovered directions keep it above ~1e-2 (even where their alpha or beta is small), after it
+    # the noise (1e-9) is far below it, and the estimate's FP32 cancellation floor (~3e-4) too
+    return [PairSpec(m=1200, p=900, n=200, r=12, alpha="uniform", decay="exp10", sigma=1e-9, k=12, seed=71),
+            PairSpec(m=700, p=1500, n=150, r=30, alpha="uniform", decay="exp10", sigma=1e-9, k=30, seed=72),
+            PairSpec(m=400, p=350, n=90, r=5, alpha="uniform", decay="exp10", sigma=1e-9, k=5, seed=73),
+            PairSpec(m=2500, p=2100, n=300, r=21, alpha="uniform", decay="exp10", sigma=1e-9, k=21, seed=74)]
+
+
+def test_grouped_adaptive_matches_oracle_algorithm1():
+    # Algorithm 1 for every side of the batch with the stop test on the device: the basis sizes
+    # equal the FP64 oracle's per side and the GSVs match it at the mixed-precision target
+    specs = _adaptive_specs()
+    mats = [planted_pair(s)[:2] for s in specs]
+    tol, b = 2e-3, 8
+    with P.Context("tf32x3", adaptive=True, block_b=b, tol=tol) as ctx:
+        outs = ctx.solve_grouped(_pairs(specs, mats))
+        cols = ctx.grouped_basis_cols(len(specs))
+        info = ctx.grouped_info()
+    for i, (s, (G1, G2), out) in enumerate(zip(specs, mats, outs)):
+        cap = min(s.m, s.p, s.n, 128)
+        ref = O.rand_gsvd_adaptive(G1, G2, tol, b, s.seed, s.kk, pair=i, max_cols=cap)
+        assert cols[i] == (ref["l1"], ref["l2"]), (i, cols[i], ref["l1"], ref["l2"])
+        assert out["status"] == 0 and out["r"] == min(s.kk, ref["l1"] + ref["l2"])
+        a, bt = out["alpha"].cpu().numpy(), out["beta"].cpu().numpy()
+        e = O.gsv_error(ref["alpha"], ref["beta"], a, bt)
+        assert np.max(e) <= TOL["tf32x3"], (i, np.max(e))
+        # the residual estimate at the stop
+        for sd in range(2):
+            assert out["resid"][sd] <= tol and abs(out["resid"][sd] - ref["hist"][sd][-1]) <= 1e-3, (i, sd)
+    assert info["captures"] == 1
+
+
+def test_grouped_adaptive_replay_and_more_pairs_than_columns():
+    # a replay of the same batch gives the same bits; a pair asking for more pairs (k = 40) than
+    # its two stopped bases hold returns min(k, l1 + l2) of them, the rest marked -1
+    specs = _adaptive_specs()[:3]
+    specs[2] = PairSpec(m=400, p=350, n=90, r=5, alpha="uniform", decay="exp10", sigma=1e-9, k=40, seed=73)
+    mats = [planted_pair(s)[:2] for s in specs]
+    with P.Context("tf32x3", adaptive=True, block_b=8, tol=2e-3) as ctx:
+        first = ctx.solve_grouped(_pairs(specs, mats))
+        second = ctx.solve_grouped(_pairs(specs, mats))
+        cols = ctx.grouped_basis_cols(len(specs))
+    for a, b in zip(first, second):
+        np.testing.assert_array_equal(a["alpha"].cpu().numpy(), b["alpha"].cpu().numpy())
+    G1, G2 = mats[2]
+    ref = O.rand_gsvd_adaptive(G1, G2, 2e-3, 8, specs[2].seed, 40, pair=2, max_cols=min(400, 350, 90, 128))
+    ract = ref["l1"] + ref["l2"]
+    assert cols[2] == (ref["l1"], ref["l2"]) and first[2]["r"] == ract < 40
+    a = first[2]["alpha"].cpu().numpy()
+    bt = first[2]["beta"].cpu().numpy()
+    assert a.size == ract
+    # the planted pairs (rank 5) are resolved; the others are noise-level pairs of the extra columns
+    e = O.gsv_error(ref["alpha"][:5], ref["beta"][:5], a[:5], bt[:5])
+    assert np.max(e) <= TOL["tf32x3"], np.max(e)
