@@ -504,13 +504,15 @@ def run_batched(args, rank, world):
 
 
 def run_learned(args, rank, world):
-    """--workload learned: the learned (k, q) proposal on pairs of the uneven-batch laws (sigma
-    1e-9, FP64, residual tolerance 1e-4).  Labels (Algorithm 1 + fixed-rank bases) and training
-    run on the GPU first (not timed); one timed step = solving every held-out pair with the
-    learned proposal (probe, network, fixed-rank solve, Algorithm 1 fallback on a miss).  The
-    same pairs are also solved once by Algorithm 1 alone (b = 16), by the fixed-rank method at
-    the one (k, q) that the training labels need at most, and with the labels as a perfect
-    proposal.  Timing: host clock around each synchronous solve (generation not timed)."""
+    """--workload learned: the learned (k, q) proposal for whole groups of pairs of the uneven-batch
+    laws (sigma 1e-9), mixed precision (3xTF32 products), residual tolerance --learned-tol.  Labels
+    (the FP64 Algorithm 1 and fixed-rank bases at that tolerance) and training run on the GPU
+    first (not timed).  One timed step = one grouped learned solve of every held-out pair (batched
+    probes, one network forward and the device plans, the fixed-rank group with each pair's plan,
+    one Algorithm 1 group for the misses).  The same group is also solved by the grouped Algorithm
+    1 alone (b = 16), by the fixed-rank group at the one (k, q) the training labels need at most,
+    and with the labels as a perfect proposal.  Timing: CUDA events around each grouped call on the
+    library's stream, after one untimed call that captures its graphs."""
     import tempfile
     import torch
     import paper_2404_09459_gb300 as P
@@ -518,18 +520,19 @@ def run_learned(args, rank, world):
     from paper_2404_09459_gb300.inputs import learned_pairs
     local = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
     dist = None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     P._build.build()
-    tol, os_ = 1e-4, 10
+    tol, os_, b = args.learned_tol, 10, 16
     tr = learned_pairs(args.train, seed=1 + 7919 * rank)
     ho = learned_pairs(args.holdout, seed=2 + 7919 * rank)
     t0 = time.perf_counter()
-    X, yk, yq, kad = learn.make_dataset(tr, tol, os_, local)
+    X, yk, yq, kad = learn.make_dataset(tr, tol, os_, local, features_prec="tf32x3")
     t_label = time.perf_counter() - t0
-    Xh, ykh, yqh, _ = learn.make_dataset(ho, tol, os_, local)
+    Xh, ykh, yqh, _ = learn.make_dataset(ho, tol, os_, local, features_prec="tf32x3")
     t0 = time.perf_counter()
     params, norm, hist = learn.train(X, yk, yq, epochs=args.epochs, batch=256, lr=1e-3, device=local)
     torch.cuda.synchronize()
@@ -538,81 +541,93 @@ def run_learned(args, rank, world):
     pk0, _ = learn.predict(params, norm, Xh, device=local)
     path = os.path.join(tempfile.mkdtemp(), "net.bin")
     learn.save(path, params, norm)
-
-    def arm(make, plans=None, reps=1):
-        learn.timed_solves(ho[:2], make, 128, os_, local, plans[:2] if plans else None)  # warm-up
-        rows = []
-        for _ in range(reps):
-            rows += learn.timed_solves(ho, make, 128, os_, local, plans)
-        secs = sum(r["seconds"] for r in rows)
-        cert = float(np.mean([r["status"] == "ok" and max(r["resid"]) <= tol for r in rows]))
-        return rows, {"value": len(rows) / secs, "unit": "pairs/s", "certified": cert}
-
-    def mk_learned():
-        return P.Context("fp64", device=local, use_learned=True, mlp_path=path, tol=tol, block_b=16)
-
-    lmax = [min(s.m, s.p, s.n, 224) - os_ for s in ho]
-    hopeless = yk == 31
-    kfix = learn.k_of_bucket(int(yk.max()))
+    # the held-out group: FP32 pairs with 16-byte rows (read in place by the grouped products)
+    mats = [tuple(aligned_rows(G) for G in planted_pair_torch(s, device=dev, dtype=torch.float32)[:2]) for s in ho]
+    kcap = 128 - os_
+    kfix = min(learn.k_of_bucket(int(yk.max())), kcap)
     qfix = int(yq[yq < 4].max()) if np.any(yq < 4) else 4
-    barrier = (lambda: (dist.barrier(), torch.cuda.synchronize())) if dist else torch.cuda.synchronize
+    st = torch.cuda.current_stream()
+
+    def pairs_with(plans=None, k=None, q=1):
+        out = []
+        for i, (s, (G1, G2)) in enumerate(zip(ho, mats)):
+            lm = min(s.m, s.p, s.n, 128) - os_
+            kk, qq = plans[i] if plans is not None else (k, q)
+            out.append(dict(G1=G1, G2=G2, k=max(1, min(kk, lm)), oversample=os_, q=qq, seed=s.seed, pair=i))
+        return out
+
+    def arm(make, pl, reps):
+        with make() as ctx:
+            ctx.solve_grouped(pl)  # capture and tuning
+            ms = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                outs = ctx.solve_grouped(pl)
+                e1.record(st)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            plans = ctx.grouped_plans(len(pl)) if getattr(ctx, "_learned", False) else None
+        cert = float(np.mean([o["status"] == 0 and max(o["resid"]) <= tol for o in outs]))
+        msm = statistics.median(ms)
+        return {"value": len(pl) / (msm / 1e3), "unit": "pairs/s", "ms_per_call": msm, "certified": cert}, plans
+
+    reps = max(1, args.steps)
     with ClockSampler(local) as clk:
-        barrier()
-        t0 = time.perf_counter()
-        rows, learned = arm(mk_learned, reps=args.steps)
-        barrier()
-        wall = time.perf_counter() - t0
-    fallback = float(np.mean([r["plan"][2] for r in rows]))
-    _, adaptive = arm(lambda: P.Context("fp64", device=local, adaptive=True, tol=tol, block_b=16))
-    _, plain = arm(lambda: P.Context("fp64", device=local),
-                   plans=[(max(1, min(kfix, lm)), qfix) for lm in lmax])
-    _, perfect = arm(lambda: P.Context("fp64", device=local),
-                     plans=[(max(1, min(learn.k_of_bucket(b), lm)), int(q)) for b, q, lm in zip(ykh, yqh, lmax)])
+        learned, plans = arm(lambda: P.Context("tf32x3", device=local, use_learned=True, mlp_path=path, tol=tol,
+                                               block_b=b), pairs_with(k=kcap), reps)
+    adaptive, _ = arm(lambda: P.Context("tf32x3", device=local, adaptive=True, tol=tol, block_b=b),
+                      pairs_with(k=kcap), reps)
+    plain, _ = arm(lambda: P.Context("tf32x3", device=local), pairs_with(k=kfix, q=qfix), reps)
+    perfect, _ = arm(lambda: P.Context("tf32x3", device=local),
+                     pairs_with(plans=[(learn.k_of_bucket(bb), int(qq)) for bb, qq in zip(ykh, yqh)]), reps)
     value = learned["value"]
     if dist is not None:
-        value = world * len(rows) / max_over_ranks(len(rows) / value, dist, f"cuda:{local}")
+        value = world * len(ho) / max_over_ranks(len(ho) / value, dist, dev)
+    fallback = float(np.mean([p_[2] for p_ in plans])) if plans else None
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = oracle_learned_sample(ho)
+        cpu = oracle_learned_sample(ho, tol=tol)
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
-                "warmup": 2, "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": (f"learned k/q proposal: {args.train} training + {args.holdout} held-out pairs "
-                                        "of the uneven-batch laws (m, p ~ U[2000, 30000], n ~ U[100, 1000], "
-                                        "r ~ U[10, 100], exp(-i/10) scale, sigma 1e-9), FP64, residual tol 1e-4, "
-                                        "oversample 10; one step solves every held-out pair"),
-                           "timing": "host clock around each synchronous solve, device synchronised",
-                           "parallelism": f"independent pairs, {world} rank(s)"},
-                "arms": {"learned": learned, "adaptive_alg1_b16": adaptive,
-                         "plain_fixed_rank": dict(plain, k=kfix, q=qfix), "perfect_proposal": perfect},
+        line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": reps,
+                "warmup": 1, "ms_per_step": learned["ms_per_call"], "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "tf32x3", "data": "synthetic",
+                "config": {"workload": (f"learned k/q proposal, grouped: {args.train} training + {args.holdout} "
+                                        "held-out pairs of the uneven-batch laws (m, p ~ U[2000, 30000], n ~ "
+                                        "U[100, 1000], r ~ U[10, 100], exp(-i/10) scale, sigma 1e-9), 3xTF32 "
+                                        f"products, residual tol {tol:g}, oversample {os_}; one step = one grouped "
+                                        "learned solve of every held-out pair"),
+                           "timing": "CUDA events around each grouped call (median), after one capturing call",
+                           "parallelism": f"independent groups, {world} rank(s)"},
+                "arms": {"learned_grouped": learned, "adaptive_alg1_grouped_b16": adaptive,
+                         "plain_fixed_rank_grouped": dict(plain, k=kfix, q=qfix), "perfect_proposal_grouped": perfect},
                 "gain": {"vs_adaptive": value / adaptive["value"], "vs_plain_fixed_rank": value / plain["value"]},
                 "learned": {"fallback_rate": fallback, "label_seconds": t_label, "train_seconds": t_train,
+                            "train_pairs": args.train, "holdout_pairs": args.holdout,
                             "final_loss": float(hist[-1]), "holdout_k_bucket_acc": float(np.mean(pk0 == ykh)),
                             "holdout_q_acc": float(np.mean(pq == yqh)),
                             "holdout_under_k_at_q90": float(np.mean(pk < ykh)),
-                            "label_q_counts": np.bincount(yq, minlength=5).tolist(),
-                            "hopeless_labels": int(hopeless.sum())},
+                            "label_q_counts": np.bincount(yq, minlength=5).tolist()},
                 "cpu_baseline": cpu, "gpu_launches": None, "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 
 
-def oracle_learned_sample(specs, seconds=20.0, max_pairs=4):
-    """The FP64 oracle's Algorithm 1 (b = 16, tol 1e-4) on a few held-out pairs (host cores)."""
+def oracle_learned_sample(specs, seconds=20.0, max_pairs=4, tol=1e-4):
+    """The FP64 oracle's Algorithm 1 (b = 16) on a few held-out pairs (host cores)."""
     from oracle import gsvd as O
     done, t_total = 0, 0.0
     for s in specs[:max_pairs]:
         G1, G2, _, _ = planted_pair(s)
         t0 = time.perf_counter()
-        O.rand_gsvd_adaptive(G1, G2, 1e-4, 16, s.seed, 128)
+        O.rand_gsvd_adaptive(G1, G2, tol, 16, s.seed, 128)
         t_total += time.perf_counter() - t0
         done += 1
         if t_total > seconds:
             break
     return {"value": done / t_total, "unit": "pairs/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{done} held-out pairs solved by the oracle's Algorithm 1 (b = 16, tol 1e-4)"}
+            "sample": f"{done} held-out pairs solved by the oracle's Algorithm 1 (b = 16, tol {tol:g})"}
 
 
 def measure_rates(device=0):
@@ -669,6 +684,8 @@ def main():
     ap.add_argument("--train", type=int, default=1024, help="learned workload: training pairs")
     ap.add_argument("--holdout", type=int, default=128, help="learned workload: held-out pairs")
     ap.add_argument("--epochs", type=int, default=60, help="learned workload: training epochs")
+    ap.add_argument("--learned-tol", type=float, default=2e-3,
+                    help="learned workload: residual tolerance (mixed precision: above the ~4e-4 floor)")
     ap.add_argument("--measure-rates", action="store_true",
                     help="print the cuBLAS TF32 / FP32 / FP64 GEMM rates of this GPU and exit")
     args = ap.parse_args()

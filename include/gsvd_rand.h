@@ -112,6 +112,10 @@ typedef struct {
 #define GSVD_RAND_FLAG_BF16_SPLIT_POWER 4 /* BF16: power-step operands as hi + lo (two products) */
 #define GSVD_RAND_FLAG_BASIS_ONLY 8 /* bases and residuals only: no compressed-pair GSVD, alpha and
                                        beta may be NULL and are not written, *r_out = 0 */
+#define GSVD_RAND_FLAG_ACC_RESID 16 /* grouped fixed-rank solves: the residual's ||Q^T G||_F^2 summed
+                                       on the CUDA cores (one more pass over G) instead of taken from
+                                       the tensor-core projection, whose long accumulation chains
+                                       lose ~1e-4 of it (an estimate floor near 1e-2) */
 
 /* Stages timed under GSVD_RAND_FLAG_PROFILE. */
 #define GSVD_RAND_STAGE_SKETCH 0 /* Y = G X products (sketch and power steps) */
@@ -250,11 +254,28 @@ int gsvd_rand_solve_batched(gsvd_rand_t h, int npairs, gsvd_rand_pair *pairs, in
  * makes the later blocks skip it (no host read between blocks).  oversample and q are not
  * used; each pair returns min(k, l1 + l2) pairs (*r_out; alpha / beta need min(k, 2 cap)
  * entries, those past *r_out are set to -1); gsvd_rand_grouped_basis_cols gives l1, l2.
+ * With cfg->use_learned = 1 (and a network loaded) the learned proposal runs for the whole
+ * group: the 16-column probe sketch of every pair on the device (no host read between pairs),
+ * one network forward over the batch (BF16 weights) and every pair's (k, q) plan on the device
+ * (as gsvd_rand_solve's learned form; k capped by the pair's k, which is the capacity of alpha
+ * and beta), read back once; the pairs then run as one fixed-rank group with their own k and q,
+ * the residual summed on the CUDA cores (the tensor-core products' estimate has a floor near
+ * 1e-2), and the pairs whose residual misses tol on either side run again as one Algorithm 1
+ * group (cfg->block_b <= 32).  gsvd_rand_grouped_plans gives each pair's (k, q, fallback).
+ * A pair whose FP32 Cholesky factors overflow (NONFINITE) or vanish (BREAKDOWN), as they can
+ * when the sketch's rank is well below l and the noise is under FP32 resolution, is solved again
+ * on its own with FP64 Cholesky factors and its own Philox words (gsvd_rand_solve's form; counted
+ * by gsvd_rand_chol64_retries); its status is that solve's.
  * Returns GSVD_RAND_OK when all pairs succeeded, else the status of the first
  * failing pair.  Ordered after and before cfg->stream; synchronises.
- * Errors: ARG, OOM, CUDA, UNSUPPORTED (precision, learned / basis-only contexts, no sm_103
- * tensor cores), and per-pair NONFINITE, BREAKDOWN, TIMEOUT, TOL_MISS (adaptive). */
+ * Errors: ARG, OOM, CUDA, UNSUPPORTED (precision, basis-only contexts, no sm_103 tensor
+ * cores), and per-pair NONFINITE, BREAKDOWN, TIMEOUT, TOL_MISS (adaptive). */
 int gsvd_rand_solve_grouped(gsvd_rand_t h, int npairs, gsvd_rand_pair *pairs);
+
+/* The plans of the last learned grouped solve on h: plans[3 i] = k, plans[3 i + 1] = q,
+ * plans[3 i + 2] = 1 when pair i fell back to Algorithm 1.  Errors: ARG (no learned grouped
+ * solve of npairs pairs). */
+int gsvd_rand_grouped_plans(gsvd_rand_t h, int *plans, int npairs);
 
 /* The basis columns of each side of the last grouped solve on h with cfg->adaptive = 1
  * (Algorithm 1 in grouped form, see gsvd_rand_solve_grouped): cols[2 i + s] for pair i,
@@ -436,6 +457,14 @@ int gsvd_rand_mlp_set(gsvd_rand_t h, const float *params, const float *norm);
 /* The network from a file: "GSVDMLP1", int32 {64, 128, 32, 5}, then norm (128
  * floats) and params, little-endian.  Errors: ARG (missing or malformed file). */
 int gsvd_rand_mlp_load(gsvd_rand_t h, const char *path);
+
+/* The learned solve's (k, q) plan of B rows of network outputs (logits: device, B x 37 row-major,
+ * as gsvd_rand_mlp_forward writes them), on the device: plan[3 i] = the top k of the smallest k
+ * bucket whose cumulative softmax probability reaches `quantile` (GSVD_RAND_MLP_KQUANTILE in the
+ * learned solves), plan[3 i + 1] = the most probable q (first on ties), plan[3 i + 2] = that k
+ * bucket.  plan: 3 B ints, device or host.  The learned solves apply the same rule and then clip
+ * k to their limits.  Synchronises cfg->stream.  Errors: ARG, CUDA. */
+int gsvd_rand_mlp_plan(gsvd_rand_t h, const float *logits, int B, double quantile, int *plan);
 
 /* k and q of the last learned solve, and fallback = 1 when Algorithm 1 solved it. */
 int gsvd_rand_last_plan(gsvd_rand_t h, int *k, int *q, int *fallback);

@@ -158,6 +158,27 @@ def predict(theta, norm, X, bf16_weights: bool = True):
     return z[:, :KCLS].argmax(axis=1), z[:, KCLS:].argmax(axis=1)
 
 
+def plan(z, quantile: float = 0.9):
+    """The learned solve's decision from network outputs z (B x (KCLS + QCLS)): the k bucket is
+    the smallest one whose cumulative softmax probability reaches `quantile` (an undersized basis
+    costs an Algorithm 1 fallback, an oversized one only columns), q the most probable class
+    (the first on ties).  Returns (k bucket, q) arrays."""
+    z = np.atleast_2d(np.asarray(z, dtype=np.float64))
+    zk = z[:, :KCLS]
+    p = np.exp(zk - zk.max(axis=1, keepdims=True))
+    p /= p.sum(axis=1, keepdims=True)
+    kb = np.empty(z.shape[0], dtype=np.int64)
+    for i in range(z.shape[0]):
+        c = 0.0
+        b = 0
+        for b in range(KCLS):
+            c += p[i, b]
+            if c >= quantile:
+                break
+        kb[i] = b
+    return kb, z[:, KCLS:].argmax(axis=1)
+
+
 # ------------------------------------------------------------------ labels
 
 def k_of_bucket(b: int) -> int:

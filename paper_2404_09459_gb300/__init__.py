@@ -27,11 +27,13 @@ EXPORTS = ("gsvd_rand_config_init", "gsvd_rand_create", "gsvd_rand_destroy", "gs
            "gsvd_rand_probe_features", "gsvd_rand_mlp_forward", "gsvd_rand_mlp_loss_grad", "gsvd_rand_mlp_adam",
            "gsvd_rand_mlp_train", "gsvd_rand_mlp_set", "gsvd_rand_mlp_load", "gsvd_rand_last_plan",
            "gsvd_rand_solve_grouped", "gsvd_rand_grouped_info", "gsvd_rand_chol64_retries",
-           "gsvd_rand_product_shapes", "gsvd_rand_factors", "gsvd_rand_solve_complex", "gsvd_rand_grouped_basis_cols")
+           "gsvd_rand_product_shapes", "gsvd_rand_factors", "gsvd_rand_solve_complex", "gsvd_rand_grouped_basis_cols",
+           "gsvd_rand_grouped_plans", "gsvd_rand_mlp_plan")
 NOALLOC_MAX_N = 32768
 FLAG_PROFILE = 2
 FLAG_BF16_SPLIT_POWER = 4
 FLAG_BASIS_ONLY = 8
+FLAG_ACC_RESID = 16
 MLP_IN, MLP_HID, MLP_KCLS, MLP_QCLS, MLP_KBUCKET = 64, 128, 32, 5, 4
 MLP_PARAMS = 64 * 128 + 128 + 128 * 128 + 128 + 128 * 37 + 37
 STAGES = ("sketch", "gtq", "orth", "small", "small_gram", "small_jacobi", "small_refine", "small_cs", "setup")
@@ -78,6 +80,8 @@ def load_library(path: str | None = None):
     lib.gsvd_rand_last_error.restype = C.c_char_p
     lib.gsvd_rand_solve.argtypes = [vp, vp, i64, i64, vp, i64, i64, i64, i32, i32, i32, u64, vp, vp, vp, vp]
     lib.gsvd_rand_grouped_basis_cols.argtypes = [vp, vp, i32]
+    lib.gsvd_rand_grouped_plans.argtypes = [vp, vp, i32]
+    lib.gsvd_rand_mlp_plan.argtypes = [vp, vp, i32, C.c_double, vp]
     lib.gsvd_rand_solve_complex.argtypes = [vp, vp, i64, i64, vp, i64, i64, i64, i32, i32, i32, u64, vp, vp, vp, vp]
     lib.gsvd_rand_metrics.argtypes = [vp, vp, vp, i32, i32, i32, vp, vp, vp, vp, vp]
     lib.gsvd_rand_gaussian.argtypes = [vp, i64, i64, u64, u32, u32, u32, vp]
@@ -300,6 +304,12 @@ class Context:
         host_out: alpha / beta returned in host memory (numpy) even for device inputs."""
         return self._many(pairs, None, host_out)
 
+    def grouped_plans(self, npairs: int):
+        """[(k, q, fallback)] per pair of the last learned grouped solve."""
+        c = (C.c_int * (3 * npairs))()
+        self._check(self.lib.gsvd_rand_grouped_plans(self.h, c, npairs))
+        return [(c[3 * i], c[3 * i + 1], c[3 * i + 2]) for i in range(npairs)]
+
     def grouped_basis_cols(self, npairs: int):
         """[(l1, l2)] per pair of the last grouped adaptive solve (Algorithm 1 basis columns)."""
         c = (C.c_int * (2 * npairs))()
@@ -419,6 +429,14 @@ class Context:
             self._dev_ptr(yk, i, N), self._dev_ptr(yq, i, N), self._dev_ptr(order, i, steps * B), steps, B, t0,
             lr, hist.data_ptr()))
         return hist[:steps]
+
+    def mlp_plan(self, logits, quantile: float = 0.9):
+        """(k, q, k bucket) per row of device logits (B x 37), the learned solve's rule on the device."""
+        import numpy as np
+        B = int(logits.shape[0])
+        out = np.zeros(3 * B, np.int32)
+        self._check(self.lib.gsvd_rand_mlp_plan(self.h, logits.data_ptr(), B, float(quantile), out.ctypes.data))
+        return out.reshape(B, 3)
 
     def mlp_set(self, params, norm):
         """The network of the learned solve (float32, CUDA tensors or numpy)."""

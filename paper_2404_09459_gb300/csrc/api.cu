@@ -46,6 +46,10 @@ struct gsvd_rand_ctx {
   bool owns_stream = false;      // stream created by the library (batched workers)
   std::vector<gsvd_rand_ctx*> workers;  // sub-contexts of gsvd_rand_solve_batched
   struct GroupState* grp = nullptr;     // gsvd_rand_solve_grouped: plan, tables and captured graph
+  struct GroupState* grp2 = nullptr;    // learned grouped solves: the Algorithm 1 pass of the misses
+  char* lbuf = nullptr;                 // learned grouped solves: features, logits, plans (device)
+  size_t lbuf_bytes = 0;
+  std::vector<int> grp_plans;           // learned grouped solves: (k, q, fallback) per pair
   unsigned char* tab_host = nullptr;    // pinned staging of the two-side product tables of a solve
   size_t tab_host_bytes = 0;
   int64_t chol64_retries = 0;  // solves repeated with FP64 Cholesky factors
@@ -1240,9 +1244,9 @@ int probe_dispatch(gsvd_rand_ctx* h, const void* G1, int64_t m, int64_t ld1, con
 // The fixed-rank or adaptive solve (arguments already checked).
 int solve_dispatch(gsvd_rand_ctx* h, bool adaptive, const void* G1, int64_t m, int64_t ld1, const void* G2, int64_t p,
                    int64_t ld2, int64_t n, int k, int oversample, int q, uint64_t seed, double* alpha, double* beta,
-                   int* r_out, double* resid_out) {
+                   int* r_out, double* resid_out, bool chol64 = false) {
   const bool f64 = h->cfg.prec == GSVD_RAND_FP64;
-  const bool c64 = (h->cfg.flags & GSVD_RAND_FLAG_CHOL_FP64) != 0;
+  const bool c64 = chol64 || (h->cfg.flags & GSVD_RAND_FLAG_CHOL_FP64) != 0;
   // FP32 data with FP32 Cholesky factors: the first (shifted) CholeskyQR pass leaves
   // kappa(Q1) ~ sqrt(s) kappa(Y), s ~ 11 (rpc + l + 1) u tr(Y^T Y).  For sketches with
   // kappa(Y) above ~1e6 (a rank well below l with the noise under FP32 resolution) that is
@@ -1547,16 +1551,18 @@ constexpr int64_t GROUP_GRAM_ROWS = 1024;  // rows per Gram chunk
 constexpr int64_t GROUP_GTQ_ROWS = 4096;   // rows per split of G^T Q
 
 // Lays out the workspace (base == nullptr: sizes only) and records the launch sequence.
-int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int prec, char* base, GroupBuild& gb) {
+// acc_resid: the fixed-rank residual from ||B||_F^2 summed on the CUDA cores (the energy kernels of
+// the adaptive blocks over 32-column slabs of Q) instead of the tensor-core projection's, whose
+// long accumulation chains set a floor near 1e-2 under the estimate (the learned solve's check).
+int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int prec, char* base, GroupBuild& gb,
+                GroupState* g, bool adaptive, bool acc_resid) {
   Bump bp;
   bp.base = base;
   const int np = (int)pv.size();
   // results block (one transfer back): statuses, residuals, alpha / beta of host destinations
-  GroupState* g = h->grp;
   DevStatus* st_all = bp.take<DevStatus>(np);
   double* resid_all = bp.take<double>(2ll * np);
   // grouped Algorithm 1 (adaptive contexts): a stop word per side, read back with the results
-  const bool adaptive = h->cfg.adaptive != 0;
   const int bsz = h->cfg.block_b;
   int* stop_all = adaptive ? bp.take<int>(2ll * np) : nullptr;
   g->stop_off = adaptive ? (size_t)((char*)stop_all - base) : 0;
@@ -1625,6 +1631,10 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
       S.R = bp.take<float>((int64_t)S.lx * S.lp);
       S.gnorm = bp.take<double>(tc_group_norm_parts() * cdiv(S.M, 128));
       S.bnorm = bp.take<double>(cdiv(S.n * P.l, 256));
+      if (acc_resid && !adaptive) {  // the slab energies of ||B||_F^2
+        S.epart = bp.take<float>(adapt_energy_part_elems(S.M, S.n, ADAPT_BMAX));
+        S.C = bp.take<double>(cdiv(P.l, ADAPT_BMAX) * cdiv(S.n * ADAPT_BMAX, 256));  // slab partial sums
+      }
       if (adaptive) {
         S.Pb = bp.take<float>(S.M * S.lp);
         S.C = bp.take<double>((int64_t)P.l * bsz);
@@ -2026,7 +2036,7 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
         for (int a = 0; a < na; ++a) {
           const int j = act[a];
           const GSide& S = gb.sides[j];
-          t[a] = AdaptEnergyB{S.G, S.ldg, S.M, S.n, S.Qt, S.ldm, c, bi_of(j), S.epart, S.bnorm, S.stop};
+          t[a] = AdaptEnergyB{S.G, S.ldg, S.M, S.n, S.Qt, S.ldm, c, bi_of(j), S.epart, S.bnorm, S.stop, 0};
           mM = std::max(mM, S.M);
           mn = std::max(mn, S.n);
           mb = std::max(mb, bi_of(j));
@@ -2074,13 +2084,45 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
   if (!add_gemm(1, false, 2)) return fail(h, GSVD_RAND_ERR_ARG, "tensor map of a grouped product rejected");
   if (!orth_ok) return fail(h, GSVD_RAND_ERR_ARG, "tensor map of a grouped CholeskyQR product rejected");
   add_reduce(true);
+  if (acc_resid && !adaptive) {  // ||B||_F^2 = sum over 32-column slabs of ||P_s^T G||_F^2, CUDA cores
+    cur_tag = GSVD_RAND_STAGE_GTQ;
+    int lmax = 0;
+    for (auto& P : gb.prs) lmax = std::max(lmax, P.l);
+    for (int c0 = 0; c0 < lmax; c0 += ADAPT_BMAX) {
+      std::vector<AdaptEnergyB> t;
+      int64_t mM = 0, mn = 0;
+      int mb = 1;
+      for (int j = 0; j < ns; ++j) {
+        const GSide& S = gb.sides[j];
+        if (c0 >= S.l) continue;
+        const int bi = std::min(ADAPT_BMAX, S.l - c0);
+        double* out = S.C + (int64_t)(c0 / ADAPT_BMAX) * cdiv(S.n * ADAPT_BMAX, 256);
+        t.push_back(AdaptEnergyB{S.G, S.ldg, S.M, S.n, S.Qt, S.ldm, c0, bi, S.epart, out, nullptr,
+                                 (int)cdiv(S.n * ADAPT_BMAX, 256)});
+        mM = std::max(mM, S.M);
+        mn = std::max(mn, S.n);
+        mb = ADAPT_BMAX;  // the sum grid covers every slab's full slot count
+      }
+      const size_t off = A.add(t);
+      const int cnt = (int)t.size();
+      push([off, cnt, mM, mn, mb](const unsigned char* d, cudaStream_t st) {
+        return launch_adapt_energy_b(reinterpret_cast<const AdaptEnergyB*>(d + off), cnt, mM, mn, mb, st);
+      });
+    }
+  }
   if (!adaptive) {  // (the adaptive stop test wrote its final estimates)
     cur_tag = GSVD_RAND_STAGE_GTQ;
     std::vector<ResidB> t(ns);
     for (int j = 0; j < ns; ++j) {
       const GSide& S = gb.sides[j];
-      t[j] = ResidB{S.gnorm, S.bnorm, gb.prs[j / 2].resid + (j & 1), (int)(tc_group_norm_parts() * cdiv(S.M, 128)),
-                    (int)cdiv(S.n * S.l, 256)};
+      // the slab partial sums lie one after another: cdiv(n 32, 256) per slab (the last slab's
+      // tail entries hold zeros from its narrower width)
+      const int nsl = (int)cdiv(S.l, ADAPT_BMAX);
+      t[j] = acc_resid ? ResidB{S.gnorm, S.C, gb.prs[j / 2].resid + (j & 1),
+                                (int)(tc_group_norm_parts() * cdiv(S.M, 128)),
+                                (int)(nsl * cdiv(S.n * ADAPT_BMAX, 256))}
+                       : ResidB{S.gnorm, S.bnorm, gb.prs[j / 2].resid + (j & 1),
+                                (int)(tc_group_norm_parts() * cdiv(S.M, 128)), (int)cdiv(S.n * S.l, 256)};
     }
     const size_t off = A.add(t);
     push([off, ns](const unsigned char* d, cudaStream_t st) {
@@ -2276,13 +2318,15 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
   return GSVD_RAND_OK;
 }
 
-int solve_grouped(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs) {
+// One grouped solve of `pairs` with the state (plan, tables, graph) in *slot: fixed-rank bases,
+// or Algorithm 1's (adaptive); acc_resid as in group_build.
+int solve_grouped_as(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs, GroupState** slot, bool adaptive,
+                     bool acc_resid) {
   const int prec = h->cfg.prec;
   if (prec != GSVD_RAND_TF32 && prec != GSVD_RAND_TF32X3)
     return fail(h, GSVD_RAND_ERR_UNSUPPORTED, "grouped solves run the TF32 / 3xTF32 tensor-core products");
-  if (h->cfg.use_learned || (h->cfg.flags & GSVD_RAND_FLAG_BASIS_ONLY))
+  if (h->cfg.flags & GSVD_RAND_FLAG_BASIS_ONLY)
     return fail(h, GSVD_RAND_ERR_UNSUPPORTED, "grouped solves take fixed-rank or adaptive bases and the compressed-pair GSVD");
-  const bool adaptive = h->cfg.adaptive != 0;
   if (adaptive && (h->cfg.block_b < 1 || h->cfg.block_b > ADAPT_BMAX || !(h->cfg.tol >= 0.0)))
     return fail(h, GSVD_RAND_ERR_ARG, "grouped adaptive solves need 1 <= block_b <= %d and tol >= 0", ADAPT_BMAX);
   if (h->tc_ok < 0) h->tc_ok = tc_available(h->cfg.device) ? 1 : 0;
@@ -2295,6 +2339,7 @@ int solve_grouped(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs) {
   {  // the adaptive parameters (zero for fixed-rank solves)
     const double ab[2] = {adaptive ? (double)h->cfg.block_b : 0.0, adaptive ? h->cfg.tol : -1.0};
     memcpy(key.data() + (size_t)npairs * sizeof(gsvd_rand_pair) + 2 * sizeof(int), ab, sizeof(ab));
+    if (acc_resid) key.push_back(1);
   }
   for (int i = 0; i < npairs; ++i) {
     // the outputs are copied out of the results block after the graph: not part of the key
@@ -2316,13 +2361,13 @@ int solve_grouped(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs) {
     c.beta = reinterpret_cast<double*>((uintptr_t)(pairs[i].beta != nullptr));
     memcpy(key.data() + 2 * sizeof(int) + (size_t)i * sizeof(gsvd_rand_pair), &c, sizeof(c));
   }
-  if (!h->grp) {
-    h->grp = new GroupState();
-    CU(cudaStreamCreateWithFlags(&h->grp->stream, cudaStreamNonBlocking));
-    CU(cudaEventCreateWithFlags(&h->grp->ev_in, cudaEventDisableTiming));
-    CU(cudaEventCreateWithFlags(&h->grp->ev_out, cudaEventDisableTiming));
+  if (!*slot) {
+    *slot = new GroupState();
+    CU(cudaStreamCreateWithFlags(&(*slot)->stream, cudaStreamNonBlocking));
+    CU(cudaEventCreateWithFlags(&(*slot)->ev_in, cudaEventDisableTiming));
+    CU(cudaEventCreateWithFlags(&(*slot)->ev_out, cudaEventDisableTiming));
   }
-  GroupState* g = h->grp;
+  GroupState* g = *slot;
   cudaStream_t gs = g->stream;
   // order after the caller's stream
   CU(cudaEventRecord(g->ev_in, h->stream));
@@ -2362,7 +2407,7 @@ int solve_grouped(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs) {
     }
     // pass 1: sizes; pass 2: the real layout and tables
     GroupBuild sizer;
-    int rc = group_build(h, pv, prec, nullptr, sizer);
+    int rc = group_build(h, pv, prec, nullptr, sizer, g, adaptive, acc_resid);
     if (rc) return rc;
     const size_t tab_bytes = (sizer.arena.buf.size() + 255) & ~size_t(255);
     const size_t need = sizer.ws_bytes + tab_bytes + 4096;
@@ -2380,7 +2425,7 @@ int solve_grouped(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs) {
     GroupBuild* gbp = new GroupBuild();
     std::unique_ptr<GroupBuild> gb_own(gbp);
     GroupBuild& gb = *gbp;
-    if ((rc = group_build(h, pv, prec, g->ws, gb))) return rc;
+    if ((rc = group_build(h, pv, prec, g->ws, gb, g, adaptive, acc_resid))) return rc;
     unsigned char* dtab = reinterpret_cast<unsigned char*>(g->ws) + ((gb.ws_bytes + 255) & ~size_t(255));
     if (gb.arena.buf.size() > tab_bytes) return fail(h, GSVD_RAND_ERR_CUDA, "table layout changed between passes");
     // pinned staging of the tables (and later the results)
@@ -2559,6 +2604,161 @@ int solve_grouped(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs) {
   if (first_bad >= 0)
     return fail(h, pairs[first_bad].status, "pair %d (first failing pair): status %d at stage %d (index %d)",
                 first_bad, pairs[first_bad].status, where, index);
+  h->err.clear();
+  return GSVD_RAND_OK;
+}
+
+int solve_grouped_learned(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs);
+
+// The pairs of a finished group whose FP32 Cholesky factors overflowed (NONFINITE) or vanished
+// (BREAKDOWN) are solved again one by one on h's stream with the factors in FP64, as a single
+// solve repeats itself (a sketch whose rank is well below l, with the noise under FP32
+// resolution: the first shifted pass leaves Q1 too ill-conditioned for the FP32 Gram of the next
+// one).  Each keeps its Philox counter word, so its test matrices are the group's.  rc is the
+// group's return code; the result is the first failing pair's status after the retries.
+int retry_breakdowns(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs, bool adaptive, int rc) {
+  if (rc != GSVD_RAND_ERR_NONFINITE && rc != GSVD_RAND_ERR_BREAKDOWN && rc != GSVD_RAND_ERR_TOL_MISS) return rc;
+  bool any = false;
+  for (int i = 0; i < npairs; ++i) {
+    gsvd_rand_pair& q = pairs[i];
+    if (q.status != GSVD_RAND_ERR_NONFINITE && q.status != GSVD_RAND_ERR_BREAKDOWN) continue;
+    any = true;
+    ++h->chol64_retries;
+    h->pair_word = q.pair;
+    q.status = solve_dispatch(h, adaptive, q.G1, q.m, q.ld1, q.G2, q.p, q.ld2, q.n, q.k, q.oversample, q.q, q.seed,
+                              q.alpha, q.beta, q.r_out, q.resid_out, true);
+    h->pair_word = 0;
+  }
+  if (!any) return rc;
+  for (int i = 0; i < npairs; ++i)
+    if (pairs[i].status)
+      return fail(h, pairs[i].status, "pair %d (first failing pair): status %d after the FP64-Cholesky retries", i,
+                  pairs[i].status);
+  h->err.clear();
+  return GSVD_RAND_OK;
+}
+
+int solve_grouped(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs) {
+  if (h->cfg.use_learned) return solve_grouped_learned(h, npairs, pairs);
+  const bool adaptive = h->cfg.adaptive != 0;
+  if (adaptive && (h->cfg.block_b < 1 || h->cfg.block_b > ADAPT_BMAX || !(h->cfg.tol >= 0.0)))
+    return fail(h, GSVD_RAND_ERR_ARG, "grouped adaptive solves need 1 <= block_b <= %d and tol >= 0", ADAPT_BMAX);
+  const bool acc = !adaptive && (h->cfg.flags & GSVD_RAND_FLAG_ACC_RESID) != 0;
+  return retry_breakdowns(h, npairs, pairs, adaptive, solve_grouped_as(h, npairs, pairs, &h->grp, adaptive, acc));
+}
+
+// The learned proposal for a whole group; Algorithm 1 stays the fallback and the judge of the
+// proposal.  The probe sketch of every pair runs on the device with no host read between pairs,
+// then one network forward over the batch (BF16 weights) and the (k, q) plans on the device,
+// read back once; the pairs run as one fixed-rank group, each with its own k and q and the
+// residual summed on the CUDA cores; the pairs whose residual estimate misses tol on either side
+// (or whose Cholesky factor broke down) run again as one Algorithm 1 group.
+int solve_grouped_learned(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs) {
+  if (!h->mlp_ready) return fail(h, GSVD_RAND_ERR_ARG, "use_learned without a network (mlp_path or gsvd_rand_mlp_set)");
+  const int prec = h->cfg.prec;
+  if (prec != GSVD_RAND_TF32 && prec != GSVD_RAND_TF32X3)
+    return fail(h, GSVD_RAND_ERR_UNSUPPORTED, "grouped solves run the TF32 / 3xTF32 tensor-core products");
+  if (h->cfg.block_b < 1 || h->cfg.block_b > ADAPT_BMAX || !(h->cfg.tol >= 0.0))
+    return fail(h, GSVD_RAND_ERR_ARG, "the Algorithm 1 fallback of a grouped solve needs 1 <= block_b <= %d", ADAPT_BMAX);
+  CU(cudaSetDevice(h->cfg.device));
+  cudaStream_t st = h->stream;
+  const int np = npairs;
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t b_f = al((size_t)np * MLP_IN * sizeof(float)), b_l = al((size_t)np * MLP_OUT * sizeof(float));
+  const size_t b_s = al((size_t)mlp_scratch_floats(np) * sizeof(float)), b_p = al(6 * (size_t)np * sizeof(int));
+  const size_t b_st = al((size_t)np * sizeof(DevStatus));
+  const size_t need = b_f + b_l + b_s + b_p + b_st;
+  if (need > h->lbuf_bytes) {
+    CU(cudaStreamSynchronize(st));
+    if (h->lbuf) cudaFree(h->lbuf);
+    h->lbuf = nullptr;
+    h->lbuf_bytes = 0;
+    if (cudaMalloc(&h->lbuf, need) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, GSVD_RAND_ERR_OOM, "learned-proposal buffers (%zu bytes) failed", need);
+    }
+    h->lbuf_bytes = need;
+  }
+  float* feats = reinterpret_cast<float*>(h->lbuf);
+  float* logits = reinterpret_cast<float*>(h->lbuf + b_f);
+  float* scratch = reinterpret_cast<float*>(h->lbuf + b_f + b_l);
+  int* plan_dev = reinterpret_cast<int*>(h->lbuf + b_f + b_l + b_s);  // 3 np plan, then 3 np limits
+  int* lim_dev = plan_dev + 3 * np;
+  DevStatus* pst = reinterpret_cast<DevStatus*>(h->lbuf + b_f + b_l + b_s + b_p);
+  // per pair: the caller's k (capacity), the widest grouped basis and the oversample
+  std::vector<int> lim(3 * (size_t)np);
+  for (int i = 0; i < np; ++i) {
+    const gsvd_rand_pair& q = pairs[i];
+    lim[i] = std::max(q.k, 1);
+    lim[np + i] = (int)std::min<int64_t>(std::min<int64_t>(std::min(q.m, q.p), q.n), 128);
+    lim[2 * np + i] = q.oversample;
+  }
+  CU(cudaMemcpyAsync(lim_dev, lim.data(), lim.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  CU(cudaMemsetAsync(pst, 0, (size_t)np * sizeof(DevStatus), st));
+  CU(cudaMemsetAsync(feats, 0, (size_t)np * MLP_IN * sizeof(float), st));
+  // the probe of every pair that can run (the grouped solve refuses the others with ARG)
+  for (int i = 0; i < np; ++i) {
+    const gsvd_rand_pair& q = pairs[i];
+    const bool ok = q.G1 && q.G2 && q.m >= 16 && q.p >= 16 && q.n >= 16 && q.ld1 >= q.n && q.ld2 >= q.n &&
+                    is_device_ptr(q.G1) && is_device_ptr(q.G2);
+    if (!ok) continue;
+    h->pair_word = q.pair;
+    const int rc = probe_dispatch(h, q.G1, q.m, q.ld1, q.G2, q.p, q.ld2, q.n, q.seed, feats + (int64_t)i * MLP_IN,
+                                  pst + i);
+    h->pair_word = 0;
+    if (rc) return rc;
+  }
+  float* F = h->mlp_dev;
+  CU(mlp_forward(F, F + MLP_NORM, feats, np, 1, logits, scratch, st));
+  CU(launch_mlp_plan(logits, np, (float)GSVD_RAND_MLP_KQUANTILE, lim_dev, lim_dev + np, lim_dev + 2 * np, plan_dev,
+                     st));
+  std::vector<int> plan(3 * (size_t)np);
+  std::vector<DevStatus> pstat(np);
+  CU(cudaMemcpyAsync(plan.data(), plan_dev, plan.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(pstat.data(), pst, (size_t)np * sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  // the fixed-rank group with each pair's plan
+  std::vector<gsvd_rand_pair> fx(pairs, pairs + np);
+  std::vector<double> res(2 * (size_t)np, 0.0);
+  for (int i = 0; i < np; ++i) {
+    fx[i].k = plan[3 * i];
+    fx[i].q = plan[3 * i + 1];
+    fx[i].resid_out = res.data() + 2 * i;
+  }
+  int rc = solve_grouped_as(h, np, fx.data(), &h->grp, false, true);
+  if (rc && rc != GSVD_RAND_ERR_BREAKDOWN && rc != GSVD_RAND_ERR_NONFINITE && rc != GSVD_RAND_ERR_ARG) return rc;
+  h->grp_plans.assign(3 * (size_t)np, 0);
+  std::vector<int> miss;
+  for (int i = 0; i < np; ++i) {
+    h->grp_plans[3 * i] = plan[3 * i];
+    h->grp_plans[3 * i + 1] = plan[3 * i + 1];
+    const int c = pstat[i].code ? pstat[i].code : fx[i].status;
+    const bool redo = c == GSVD_RAND_ERR_BREAKDOWN || c == GSVD_RAND_ERR_NONFINITE ||
+                      (c == GSVD_RAND_OK && std::max(res[2 * i], res[2 * i + 1]) > h->cfg.tol);
+    if (redo) {
+      miss.push_back(i);
+      h->grp_plans[3 * i + 2] = 1;
+      continue;
+    }
+    pairs[i].status = c;
+    if (c == GSVD_RAND_OK && pairs[i].resid_out) {
+      if (is_device_ptr(pairs[i].resid_out))
+        CU(cudaMemcpy(pairs[i].resid_out, res.data() + 2 * i, 2 * sizeof(double), cudaMemcpyHostToDevice));
+      else
+        memcpy(pairs[i].resid_out, res.data() + 2 * i, 2 * sizeof(double));
+    }
+  }
+  if (!miss.empty()) {
+    std::vector<gsvd_rand_pair> ad;
+    for (int i : miss) ad.push_back(pairs[i]);
+    rc = retry_breakdowns(h, (int)ad.size(), ad.data(), true, solve_grouped_as(h, (int)ad.size(), ad.data(), &h->grp2, true, false));
+    if (rc && rc != GSVD_RAND_ERR_BREAKDOWN && rc != GSVD_RAND_ERR_NONFINITE && rc != GSVD_RAND_ERR_TOL_MISS &&
+        rc != GSVD_RAND_ERR_ARG)
+      return rc;
+    for (size_t t = 0; t < miss.size(); ++t) pairs[miss[t]].status = ad[t].status;
+  }
+  for (int i = 0; i < np; ++i)
+    if (pairs[i].status) return fail(h, pairs[i].status, "pair %d (first failing pair): status %d", i, pairs[i].status);
   h->err.clear();
   return GSVD_RAND_OK;
 }
@@ -2797,11 +2997,13 @@ int gsvd_rand_destroy(gsvd_rand_t h) {
   for (auto wk : h->workers) gsvd_rand_destroy(wk);
   h->workers.clear();
   cudaSetDevice(h->cfg.device);
-  if (h->grp) {
-    cudaStreamSynchronize(h->grp->stream);
-    group_free(h->grp);
-    h->grp = nullptr;
-  }
+  for (GroupState** sl : {&h->grp, &h->grp2})
+    if (*sl) {
+      cudaStreamSynchronize((*sl)->stream);
+      group_free(*sl);
+      *sl = nullptr;
+    }
+  if (h->lbuf) cudaFree(h->lbuf);
   if (h->stream) cudaStreamSynchronize(h->stream); else cudaDeviceSynchronize();
   if (h->owns_stream && h->stream) cudaStreamDestroy(h->stream);
   for (auto e : h->evpool) cudaEventDestroy(e);
@@ -2969,6 +3171,13 @@ int gsvd_rand_solve_grouped(gsvd_rand_t h, int npairs, gsvd_rand_pair* pairs) {
   if (!h || npairs < 0 || (npairs > 0 && !pairs)) return GSVD_RAND_ERR_ARG;
   if (npairs == 0) return GSVD_RAND_OK;
   return solve_grouped_staged(h, npairs, pairs);
+}
+
+int gsvd_rand_grouped_plans(gsvd_rand_t h, int* plans, int npairs) {
+  if (!h || !plans || npairs < 0) return GSVD_RAND_ERR_ARG;
+  if ((int)h->grp_plans.size() < 3 * npairs) return fail(h, GSVD_RAND_ERR_ARG, "no learned grouped solve of that size");
+  for (int i = 0; i < 3 * npairs; ++i) plans[i] = h->grp_plans[i];
+  return GSVD_RAND_OK;
 }
 
 int gsvd_rand_grouped_basis_cols(gsvd_rand_t h, int* cols, int npairs) {
@@ -3202,6 +3411,22 @@ int gsvd_rand_mlp_train(gsvd_rand_t h, float* params, float* m, float* v, const 
     CU(mlp_loss_grad(params, norm, X, yk, yq, order + (int64_t)i * B, B, grad, loss_hist + i, s, h->stream));
     CU(mlp_adam(params, m, v, grad, t0 + i + 1, lr, 0.9f, 0.999f, 1e-8f, h->stream));
   }
+  CU(cudaStreamSynchronize(h->stream));
+  return GSVD_RAND_OK;
+}
+
+int gsvd_rand_mlp_plan(gsvd_rand_t h, const float* logits, int B, double quantile, int* plan) {
+  if (!h || !logits || !plan || B < 1 || !(quantile > 0.0 && quantile <= 1.0)) return GSVD_RAND_ERR_ARG;
+  if (!is_device_ptr(logits)) return fail(h, GSVD_RAND_ERR_ARG, "logits must be device memory");
+  CU(cudaSetDevice(h->cfg.device));
+  const bool dev = is_device_ptr(plan);
+  int* out = plan;
+  if (!dev) {
+    if (int rc = ensure_ws(h, (size_t)3 * B * sizeof(int) + 256)) return rc;
+    out = reinterpret_cast<int*>(h->ws);
+  }
+  CU(launch_mlp_plan(logits, B, (float)quantile, nullptr, nullptr, nullptr, out, h->stream));
+  if (!dev) CU(cudaMemcpyAsync(plan, out, (size_t)3 * B * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CU(cudaStreamSynchronize(h->stream));
   return GSVD_RAND_OK;
 }

@@ -190,7 +190,10 @@ __global__ __launch_bounds__(256) void energy_sum_b_kernel(const AdaptEnergyB* _
   const AdaptEnergyB& a = tab[blockIdx.y];
   if (side_done(a.stop)) return;
   const int64_t nb = a.n * a.bi;
-  if ((int64_t)blockIdx.x * 256 >= nb) return;
+  if ((int64_t)blockIdx.x * 256 >= nb) {  // past the entries: a slot to clear, or nothing
+    if (threadIdx.x == 0 && (int64_t)blockIdx.x < a.nb_out) a.epart[blockIdx.x] = 0.0;
+    return;
+  }
   const int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x;
   double v = 0.0;
   if (e < nb) {
@@ -219,6 +222,8 @@ cudaError_t launch_adapt_energy_b(const AdaptEnergyB* tab, int nprob, int64_t ma
                                   cudaStream_t st) {
   if (nprob <= 0) return cudaSuccess;
   if (max_bi > ADAPT_BMAX) return cudaErrorInvalidValue;
+  // (nb_out never exceeds cdiv(max_n ADAPT_BMAX, 256): the grid below covers it when callers
+  // pass max_bi = ADAPT_BMAX for tables that clear slots)
   const dim3 g1((unsigned)((max_n + EN_COLS - 1) / EN_COLS), (unsigned)((max_M + EN_ROWS - 1) / EN_ROWS),
                 (unsigned)nprob);
   energy_part_b_kernel<<<g1, EN_COLS, 0, st>>>(tab);

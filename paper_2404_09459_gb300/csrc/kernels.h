@@ -327,8 +327,9 @@ struct AdaptEnergyB {  // ||P^T G||_F^2 of the block P = rows [c, c + bi) of Qt,
   int64_t ldq;
   int c, bi;
   float* part;    // adapt_energy_part_elems(M, n, bi) chunk partials
-  double* epart;  // cdiv(n bi, 256) partial sums of squares
+  double* epart;  // cdiv(n bi, 256) partial sums of squares (then zeros up to nb_out)
   const int* stop;
+  int nb_out;     // slots of epart to fill (0: cdiv(n bi, 256))
 };
 int64_t adapt_energy_part_elems(int64_t M, int64_t n, int bi);
 cudaError_t launch_adapt_energy_b(const AdaptEnergyB* tab, int nprob, int64_t max_M, int64_t max_n, int max_bi,

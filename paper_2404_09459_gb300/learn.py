@@ -139,13 +139,16 @@ def predict(params, norm, X, bf16: bool = True, device: int = 0, ctx: Context | 
     finally:
         if own:
             ctx.close()
-    z = z.cpu().numpy().astype(np.float64)
-    q = z[:, MLP_KCLS:].argmax(axis=1)
-    if quantile is None:
-        return z[:, :MLP_KCLS].argmax(axis=1), q
-    zk = z[:, :MLP_KCLS] - z[:, :MLP_KCLS].max(axis=1, keepdims=True)
-    cum = np.cumsum(np.exp(zk) / np.exp(zk).sum(axis=1, keepdims=True), axis=1)
-    return np.minimum(np.argmax(cum >= quantile, axis=1), MLP_KCLS - 1), q
+    if quantile is not None:  # the learned solve's own rule, run by the library on the device
+        ctx2 = ctx if not own else Context("fp32", device=device)
+        try:
+            plan = ctx2.mlp_plan(z.contiguous(), quantile)
+        finally:
+            if own:
+                ctx2.close()
+        return plan[:, 2], plan[:, 1]
+    z = z.cpu().numpy()
+    return z[:, :MLP_KCLS].argmax(axis=1), z[:, MLP_KCLS:].argmax(axis=1)
 
 
 def save(path: str, params, norm):

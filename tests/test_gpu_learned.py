@@ -204,3 +204,108 @@ def test_labels_match_oracle(spec):
     finally:
         lab.close()
     assert tuple(int(x) for x in got) == tuple(int(x) for x in ref)
+
+
+def test_grouped_learned_plans_and_fallback():
+    # the learned proposal for a whole group: every pair proposes k = 16, q = 1 (a fixed network),
+    # capped by each pair's k (its rank here, so that every returned pair is a planted one): the
+    # pairs of rank 16 and 12 are solved by the fixed-rank group, the rank-30 pair misses tol with
+    # k = 16 and is solved again by the grouped Algorithm 1 (mixed precision: tol above the ~4e-4
+    # floor of the residual estimate)
+    from paper_2404_09459_gb300.inputs import aligned_rows
+    specs = [PairSpec(m=900, p=700, n=160, r=16, alpha="uniform", decay="exp10", sigma=1e-10, k=16, oversample=8,
+                      seed=31),
+             PairSpec(m=1300, p=800, n=200, r=30, alpha="uniform", decay="exp10", sigma=1e-10, k=30, oversample=8,
+                      seed=32),
+             PairSpec(m=600, p=640, n=120, r=12, alpha="uniform", decay="exp10", sigma=1e-10, k=12, oversample=8,
+                      seed=33)]
+    mats = [planted_pair(s)[:2] for s in specs]
+    pairs = [dict(G1=aligned_rows(_t(G1)), G2=aligned_rows(_t(G2)), k=s.k, oversample=8, q=0, seed=s.seed, pair=i)
+             for i, (s, (G1, G2)) in enumerate(zip(specs, mats))]
+    tol, b = 2e-3, 8
+    th, norm = _fixed_net(3, 1)
+    with P.Context("tf32x3", use_learned=True, tol=tol, block_b=b) as ctx:
+        ctx.mlp_set(th, norm)
+        outs = ctx.solve_grouped(pairs)
+        plans = ctx.grouped_plans(len(pairs))
+    assert plans == [(16, 1, 0), (16, 1, 1), (12, 1, 0)]
+    for i, (s, (G1, G2), out) in enumerate(zip(specs, mats, outs)):
+        assert out["status"] == 0 and max(out["resid"]) <= tol
+        if plans[i][2]:
+            ref = O.rand_gsvd_adaptive(G1, G2, tol, b, s.seed, s.k, pair=i, max_cols=min(s.m, s.p, s.n, 128))
+        else:
+            ref = O.rand_gsvd(G1, G2, plans[i][0], 8, 1, s.seed, pair=i)
+        assert out["r"] == s.k
+        e = O.gsv_error(ref["alpha"], ref["beta"], out["alpha"].cpu().numpy(), out["beta"].cpu().numpy())
+        assert np.max(e) <= 1e-4, (i, np.max(e))
+
+
+def test_plan_on_device_matches_oracle_rule():
+    # the learned solves' (k, q) decision runs on the device (gsvd_rand_mlp_plan); both sides take
+    # it in FP64 from the same FP32 logits
+    rng = np.random.default_rng(5)
+    z = (rng.standard_normal((300, 37)) * 3.0).astype(np.float32)
+    z[:20, :32] = 0.0  # flat k heads
+    z[20:40, 32:] = 1.0  # q ties: the first class
+    with P.Context("fp32") as ctx:
+        for qt in (0.9, 0.5, 0.99):
+            plan = ctx.mlp_plan(_t(z), qt)
+            kb, q = L.plan(z.astype(np.float64), qt)
+            np.testing.assert_array_equal(plan[:, 2], kb)
+            np.testing.assert_array_equal(plan[:, 1], q)
+            np.testing.assert_array_equal(plan[:, 0], 4 * (kb + 1))
+
+
+def test_grouped_learned_gain_over_algorithm1_and_fixed_rank():
+    # what the trained network gains: labels from the FP64 Algorithm 1 at tol, the network trained on
+    # the GPU by the library's kernels, then one held-out group solved three ways at an equal certified
+    # residual (every pair within tol on both sides): the learned group (probes, network, plans,
+    # fixed-rank group, Algorithm 1 for misses), the grouped Algorithm 1 alone (b = 16), and the
+    # fixed-rank group at the one (k, q) the held-out labels need at most (the choice most favourable
+    # to it), its residual summed on the CUDA cores as the learned group's is (FLAG_ACC_RESID: the
+    # tensor-core projection's estimate cannot certify 2e-3); the learned group runs more pairs per
+    # second than both
+    from paper_2404_09459_gb300.inputs import aligned_rows, learned_pairs, planted_pair_torch
+    tol, os_, b = 2e-3, 10, 16
+    law = dict(m_range=(4000, 12000), n_range=(300, 600))
+    tr = learned_pairs(160, seed=11, **law)
+    ho = learned_pairs(48, seed=12, **law)
+    X, yk, yq, _ = learn.make_dataset(tr, tol, os_, 0, features_prec="tf32x3")
+    params, norm, hist = learn.train(X, yk, yq, epochs=120, batch=64, lr=2e-3)
+    assert hist[-1] < hist[0]
+    mats = [tuple(aligned_rows(G) for G in planted_pair_torch(s, device=DEV, dtype=torch.float32)[:2]) for s in ho]
+    _, yk_ho, yq_ho, _ = learn.make_dataset(ho, tol, os_, 0, features_prec="tf32x3")
+    kfix = min(learn.k_of_bucket(int(yk_ho.max())), 128 - os_)
+    qfix = int(yq_ho.max())
+
+    def pairs_with(k, q):
+        return [dict(G1=G1, G2=G2, k=max(1, min(k, min(s.m, s.p, s.n, 128) - os_)), oversample=os_, q=q,
+                     seed=s.seed, pair=i) for i, (s, (G1, G2)) in enumerate(zip(ho, mats))]
+
+    def timed(ctx, pl):
+        ctx.solve_grouped(pl)  # graphs captured, products tuned
+        ts = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record()
+            outs = ctx.solve_grouped(pl)
+            t1.record()
+            torch.cuda.synchronize()
+            ts.append(t0.elapsed_time(t1))
+        assert all(o["status"] == 0 and max(o["resid"]) <= tol for o in outs)
+        return float(np.median(ts))
+
+    with P.Context("tf32x3", use_learned=True, tol=tol, block_b=b) as ctx:
+        ctx.mlp_set(params.cpu().numpy(), norm.cpu().numpy())
+        t_learned = timed(ctx, pairs_with(128 - os_, 1))
+        plans = ctx.grouped_plans(len(ho))
+    with P.Context("tf32x3", adaptive=True, tol=tol, block_b=b) as ctx:
+        t_adaptive = timed(ctx, pairs_with(128 - os_, 1))
+    with P.Context("tf32x3", flags=P.FLAG_ACC_RESID) as ctx:
+        t_plain = timed(ctx, pairs_with(kfix, qfix))
+    fb = np.mean([p_[2] for p_ in plans])
+    print(f"learned {t_learned:.2f} ms (fallback {fb:.2f}), Algorithm 1 {t_adaptive:.2f} ms, "
+          f"fixed rank (k {kfix}, q {qfix}) {t_plain:.2f} ms")
+    assert t_learned < t_adaptive and t_learned < t_plain

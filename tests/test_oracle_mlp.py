@@ -148,3 +148,21 @@ def test_labels_need_power_steps_on_flat_tail():
         assert L.fixed_residual(G, k, 4, q, 2, 0, side) <= 3e-2
     with pytest.raises(AssertionError):
         L.unpack(np.zeros(5))
+
+
+def test_plan_rule_on_known_probabilities():
+    # logits log(p): cumulative probabilities 0.5, 0.8, 0.95, ... -> the 0.9 quantile is bucket 2,
+    # the 0.5 quantile bucket 0, the 0.8 quantile bucket 1 (reached exactly), q the argmax (first
+    # of two equal maxima)
+    p = np.zeros(L.KCLS)
+    p[:4] = [0.5, 0.3, 0.15, 0.05]
+    zk = np.log(np.where(p > 0, p, 1e-300))
+    zq = np.array([0.0, 2.0, 2.0, 1.0, -1.0])
+    z = np.concatenate([zk, zq])[None, :]
+    for qt, want in ((0.9, 2), (0.5, 0), (0.8 - 1e-12, 1), (0.999, 3)):
+        kb, q = L.plan(z, qt)
+        assert kb[0] == want and q[0] == 1
+    # a flat k head reaches the quantile at bucket ceil(0.9 KCLS) - 1; the last bucket when never reached
+    z2 = np.zeros((1, L.KCLS + 5))
+    assert L.plan(z2, 0.9)[0][0] == int(np.ceil(0.9 * L.KCLS)) - 1
+    assert L.plan(z2, 1.0 + 1e-9)[0][0] == L.KCLS - 1
