@@ -127,7 +127,8 @@ typedef struct {
 #define GSVD_RAND_STAGE_SMALL_REFINE 6 /* ... the FP64 eigenvector refinement of K */
 #define GSVD_RAND_STAGE_SMALL_CS 7     /* ... the CS step (C1, C2 and their eigensolve) */
 #define GSVD_RAND_STAGE_SETUP 8        /* grouped solves: status resets and the Gaussian test matrices */
-#define GSVD_RAND_NUM_STAGES 9
+#define GSVD_RAND_STAGE_PROPOSAL 9     /* learned grouped solves: the probes, the network and the plans */
+#define GSVD_RAND_NUM_STAGES 10
 
 /* Fill *cfg with defaults: device 0, default stream, TF32, fixed rank, b = 100, tol = 1e-4. */
 int gsvd_rand_config_init(gsvd_rand_config *cfg);
@@ -276,6 +277,13 @@ int gsvd_rand_solve_grouped(gsvd_rand_t h, int npairs, gsvd_rand_pair *pairs);
  * plans[3 i + 2] = 1 when pair i fell back to Algorithm 1.  Errors: ARG (no learned grouped
  * solve of npairs pairs). */
 int gsvd_rand_grouped_plans(gsvd_rand_t h, int *plans, int npairs);
+
+/* The probe features of the last learned grouped solve on h: feats[64 i .. 64 i + 63] for pair i
+ * (GSVD_RAND_MLP_IN per pair, as gsvd_rand_probe_features gives them for the pair's own Philox
+ * word; zeros for pairs the probes left out), host memory.  The group's probes run as one grouped
+ * pass whose Gram sums are chunked differently from a single probe's: the features agree with it
+ * to rounding.  Errors: ARG (no learned grouped solve of npairs pairs). */
+int gsvd_rand_grouped_features(gsvd_rand_t h, float *feats, int npairs);
 
 /* The basis columns of each side of the last grouped solve on h with cfg->adaptive = 1
  * (Algorithm 1 in grouped form, see gsvd_rand_solve_grouped): cols[2 i + s] for pair i,

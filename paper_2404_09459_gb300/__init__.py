@@ -28,7 +28,7 @@ EXPORTS = ("gsvd_rand_config_init", "gsvd_rand_create", "gsvd_rand_destroy", "gs
            "gsvd_rand_mlp_train", "gsvd_rand_mlp_set", "gsvd_rand_mlp_load", "gsvd_rand_last_plan",
            "gsvd_rand_solve_grouped", "gsvd_rand_grouped_info", "gsvd_rand_chol64_retries",
            "gsvd_rand_product_shapes", "gsvd_rand_factors", "gsvd_rand_solve_complex", "gsvd_rand_grouped_basis_cols",
-           "gsvd_rand_grouped_plans", "gsvd_rand_mlp_plan")
+           "gsvd_rand_grouped_plans", "gsvd_rand_mlp_plan", "gsvd_rand_grouped_features")
 NOALLOC_MAX_N = 32768
 FLAG_PROFILE = 2
 FLAG_BF16_SPLIT_POWER = 4
@@ -36,7 +36,8 @@ FLAG_BASIS_ONLY = 8
 FLAG_ACC_RESID = 16
 MLP_IN, MLP_HID, MLP_KCLS, MLP_QCLS, MLP_KBUCKET = 64, 128, 32, 5, 4
 MLP_PARAMS = 64 * 128 + 128 + 128 * 128 + 128 + 128 * 37 + 37
-STAGES = ("sketch", "gtq", "orth", "small", "small_gram", "small_jacobi", "small_refine", "small_cs", "setup")
+STAGES = ("sketch", "gtq", "orth", "small", "small_gram", "small_jacobi", "small_refine", "small_cs", "setup",
+          "proposal")
 
 
 class GsvdRandError(RuntimeError):
@@ -81,6 +82,7 @@ def load_library(path: str | None = None):
     lib.gsvd_rand_solve.argtypes = [vp, vp, i64, i64, vp, i64, i64, i64, i32, i32, i32, u64, vp, vp, vp, vp]
     lib.gsvd_rand_grouped_basis_cols.argtypes = [vp, vp, i32]
     lib.gsvd_rand_grouped_plans.argtypes = [vp, vp, i32]
+    lib.gsvd_rand_grouped_features.argtypes = [vp, vp, i32]
     lib.gsvd_rand_mlp_plan.argtypes = [vp, vp, i32, C.c_double, vp]
     lib.gsvd_rand_solve_complex.argtypes = [vp, vp, i64, i64, vp, i64, i64, i64, i32, i32, i32, u64, vp, vp, vp, vp]
     lib.gsvd_rand_metrics.argtypes = [vp, vp, vp, i32, i32, i32, vp, vp, vp, vp, vp]
@@ -309,6 +311,13 @@ class Context:
         c = (C.c_int * (3 * npairs))()
         self._check(self.lib.gsvd_rand_grouped_plans(self.h, c, npairs))
         return [(c[3 * i], c[3 * i + 1], c[3 * i + 2]) for i in range(npairs)]
+
+    def grouped_features(self, npairs: int):
+        """(npairs, 64) float32 probe features of the last learned grouped solve."""
+        import numpy as np
+        f = np.zeros((npairs, MLP_IN), np.float32)
+        self._check(self.lib.gsvd_rand_grouped_features(self.h, f.ctypes.data, npairs))
+        return f
 
     def grouped_basis_cols(self, npairs: int):
         """[(l1, l2)] per pair of the last grouped adaptive solve (Algorithm 1 basis columns)."""

@@ -47,12 +47,17 @@ struct gsvd_rand_ctx {
   std::vector<gsvd_rand_ctx*> workers;  // sub-contexts of gsvd_rand_solve_batched
   struct GroupState* grp = nullptr;     // gsvd_rand_solve_grouped: plan, tables and captured graph
   struct GroupState* grp2 = nullptr;    // learned grouped solves: the Algorithm 1 pass of the misses
+  struct GroupState* grp3 = nullptr;    // learned grouped solves: the probes of the whole group
   char* lbuf = nullptr;                 // learned grouped solves: features, logits, plans (device)
   size_t lbuf_bytes = 0;
   std::vector<int> grp_plans;           // learned grouped solves: (k, q, fallback) per pair
+  std::vector<float> grp_feats;         // learned grouped solves: the 64 probe features per pair
   unsigned char* tab_host = nullptr;    // pinned staging of the two-side product tables of a solve
   size_t tab_host_bytes = 0;
-  int64_t chol64_retries = 0;  // solves repeated with FP64 Cholesky factors
+  int64_t chol64_retries = 0;  // solves repeated with FP64 Cholesky factors (or in FP64 throughout)
+  gsvd_rand_ctx* f64 = nullptr;  // FP64 sub-context (same device and stream) for the last retry form
+  double* wide = nullptr;        // FP64 copies of a pair for that retry
+  size_t wide_bytes = 0;
   int product_shapes[6] = {0, 0, 0, 0, 0, 0};  // tuned (stages, CTAs per SM) of the two-side products
   // where the last fixed-rank solve left its bases, compressed stack and CS factor in the
   // workspace (for gsvd_rand_factors); cleared whenever the workspace is next taken
@@ -1241,6 +1246,58 @@ int probe_dispatch(gsvd_rand_ctx* h, const void* G1, int64_t m, int64_t ld1, con
   return probe_t<float, float>(h, G1, m, ld1, G2, p, ld2, n, seed, feats_dev, st_ext);
 }
 
+// The last retry form of a mixed-precision solve: the pair widened to FP64 (device copies owned
+// by h) and solved by an FP64 sub-context of h on the same stream, with the same Philox words.
+// Its CholeskyQR resolves sketches up to kappa ~ 1e8 before its own shift is needed, where the
+// FP32 bases of a sketch whose rank lies far below l (noise under FP32 resolution) do not.
+// rc0 is returned unchanged when the FP64 form's limits (l or b <= 224) do not admit the solve.
+int solve_widened(gsvd_rand_ctx* h, bool adaptive, const void* G1, int64_t m, int64_t ld1, const void* G2, int64_t p,
+                  int64_t ld2, int64_t n, int k, int oversample, int q, uint64_t seed, double* alpha, double* beta,
+                  int* r_out, double* resid_out, int rc0) {
+  if (adaptive ? h->cfg.block_b > 224 : (int64_t)k + oversample > 224) return rc0;
+  if (h->cplx_sketch) return rc0;  // the realified complex sketch is drawn by h's own solves only
+  if (!h->f64) {
+    gsvd_rand_config c = h->cfg;
+    c.prec = GSVD_RAND_FP64;
+    c.use_learned = 0;
+    c.mlp_path = nullptr;
+    c.flags &= ~GSVD_RAND_FLAG_PROFILE;
+    gsvd_rand_t w = nullptr;
+    const int rc = gsvd_rand_create(&w, &c);
+    if (rc) return fail(h, rc, "cannot create the FP64 retry context");
+    h->f64 = w;
+  }
+  gsvd_rand_ctx* w = h->f64;
+  w->cfg.adaptive = adaptive ? 1 : 0;
+  w->cfg.block_b = h->cfg.block_b;
+  w->cfg.tol = h->cfg.tol;
+  w->cfg.flags = h->cfg.flags & ~(GSVD_RAND_FLAG_PROFILE | GSVD_RAND_FLAG_CHOL_FP64);
+  const size_t need = (size_t)(m + p) * (size_t)n * sizeof(double);
+  if (need > h->wide_bytes) {
+    CU(cudaStreamSynchronize(h->stream));
+    if (h->wide) cudaFree(h->wide);
+    h->wide = nullptr;
+    h->wide_bytes = 0;
+    if (cudaMalloc(&h->wide, need) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, GSVD_RAND_ERR_OOM, "FP64 copies of a pair (%zu bytes) for its last retry failed", need);
+    }
+    h->wide_bytes = need;
+  }
+  double* W1 = h->wide;
+  double* W2 = h->wide + m * n;
+  CU(launch_widen(static_cast<const float*>(G1), ld1, m, n, W1, n, h->stream));
+  CU(launch_widen(static_cast<const float*>(G2), ld2, p, n, W2, n, h->stream));
+  ++h->chol64_retries;
+  h->fact.valid = false;  // the bases of this solve live in the sub-context
+  w->pair_word = h->pair_word;
+  const int rc = gsvd_rand_solve(w, W1, m, n, W2, p, n, n, k, oversample, q, seed, alpha, beta, r_out, resid_out);
+  w->pair_word = 0;
+  if (rc) return fail(h, rc, "FP64 retry: %s", w->err.c_str());
+  h->err.clear();
+  return GSVD_RAND_OK;
+}
+
 // The fixed-rank or adaptive solve (arguments already checked).
 int solve_dispatch(gsvd_rand_ctx* h, bool adaptive, const void* G1, int64_t m, int64_t ld1, const void* G2, int64_t p,
                    int64_t ld2, int64_t n, int k, int oversample, int q, uint64_t seed, double* alpha, double* beta,
@@ -1252,7 +1309,8 @@ int solve_dispatch(gsvd_rand_ctx* h, bool adaptive, const void* G1, int64_t m, i
   // kappa(Y) above ~1e6 (a rank well below l with the noise under FP32 resolution) that is
   // beyond u^(-1/2) of FP32, the FP32 Gram of the next pass no longer resolves Q1's weak
   // columns, and its pivots can overflow (NONFINITE) or vanish (BREAKDOWN).  Such a solve is
-  // repeated with the Cholesky factors in FP64 (the GSVD_RAND_FLAG_CHOL_FP64 form).
+  // repeated with the Cholesky factors in FP64 (the GSVD_RAND_FLAG_CHOL_FP64 form); when the FP32
+  // bases still do not resolve it, once more in FP64 throughout (solve_widened).
   auto retry = [](int rc) { return rc == GSVD_RAND_ERR_NONFINITE || rc == GSVD_RAND_ERR_BREAKDOWN; };
   if (adaptive) {
     if (f64) return solve_adaptive_t<double, double>(h, G1, m, ld1, G2, p, ld2, n, k, seed, alpha, beta, r_out, resid_out);
@@ -1261,7 +1319,10 @@ int solve_dispatch(gsvd_rand_ctx* h, bool adaptive, const void* G1, int64_t m, i
       if (!retry(rc)) return rc;
       ++h->chol64_retries;
     }
-    return solve_adaptive_t<float, double>(h, G1, m, ld1, G2, p, ld2, n, k, seed, alpha, beta, r_out, resid_out);
+    const int rc = solve_adaptive_t<float, double>(h, G1, m, ld1, G2, p, ld2, n, k, seed, alpha, beta, r_out,
+                                                   resid_out);
+    if (!retry(rc)) return rc;
+    return solve_widened(h, true, G1, m, ld1, G2, p, ld2, n, k, oversample, q, seed, alpha, beta, r_out, resid_out, rc);
   }
   if (f64) return solve_t<double, double>(h, G1, m, ld1, G2, p, ld2, n, k, oversample, q, seed, alpha, beta, r_out, resid_out);
   if (!c64) {
@@ -1270,7 +1331,10 @@ int solve_dispatch(gsvd_rand_ctx* h, bool adaptive, const void* G1, int64_t m, i
     if (!retry(rc)) return rc;
     ++h->chol64_retries;
   }
-  return solve_t<float, double>(h, G1, m, ld1, G2, p, ld2, n, k, oversample, q, seed, alpha, beta, r_out, resid_out);
+  const int rc = solve_t<float, double>(h, G1, m, ld1, G2, p, ld2, n, k, oversample, q, seed, alpha, beta, r_out,
+                                       resid_out);
+  if (!retry(rc)) return rc;
+  return solve_widened(h, false, G1, m, ld1, G2, p, ld2, n, k, oversample, q, seed, alpha, beta, r_out, resid_out, rc);
 }
 
 constexpr int MLP_IN = GSVD_RAND_MLP_IN, MLP_OUT = GSVD_RAND_MLP_KCLS + GSVD_RAND_MLP_QCLS;
@@ -1361,6 +1425,7 @@ struct GroupState {
   // results
   size_t res_off = 0, res_bytes = 0;  // results block inside the workspace
   size_t stop_off = 0;                // adaptive: the stop words (2 per pair) in the results block
+  size_t feat_off = 0;                // probe groups: 64 features per solved pair (valid order)
   std::vector<int> cols;              // adaptive: the basis columns of each side of the last solve
   std::vector<int> valid;             // pair index of each solved pair
   struct Out {
@@ -1512,6 +1577,7 @@ struct GSide {
   double *C = nullptr, *xpart = nullptr, *state = nullptr;
   float* epart = nullptr;  // chunk partials of the block energy ||P^T G||_F^2
   int* stop = nullptr;
+  double* Wz = nullptr;  // probe groups: Z^T Z of Z = G^T Y
 };
 struct GPair {
   int k, l, L, q;
@@ -1549,13 +1615,14 @@ struct GroupBuild {
 
 constexpr int64_t GROUP_GRAM_ROWS = 1024;  // rows per Gram chunk
 constexpr int64_t GROUP_GTQ_ROWS = 4096;   // rows per split of G^T Q
+constexpr int GROUP_PROBE_L = 16;          // columns of the learned proposal's probe sketch
 
 // Lays out the workspace (base == nullptr: sizes only) and records the launch sequence.
 // acc_resid: the fixed-rank residual from ||B||_F^2 summed on the CUDA cores (the energy kernels of
 // the adaptive blocks over 32-column slabs of Q) instead of the tensor-core projection's, whose
 // long accumulation chains set a floor near 1e-2 under the estimate (the learned solve's check).
 int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int prec, char* base, GroupBuild& gb,
-                GroupState* g, bool adaptive, bool acc_resid) {
+                GroupState* g, bool adaptive, bool acc_resid, bool probe) {
   Bump bp;
   bp.base = base;
   const int np = (int)pv.size();
@@ -1574,7 +1641,7 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
   for (int i = 0; i < np; ++i) {
     const gsvd_rand_pair& q = *pv[i];
     GroupState::Out& o = g->outs[i];
-    o.k = adaptive ? std::min(q.k, 2 * acap(q)) : q.k;
+    o.k = probe ? 0 : (adaptive ? std::min(q.k, 2 * acap(q)) : q.k);
     double* a = bp.take<double>(o.k);
     double* b = bp.take<double>(o.k);
     o.a_off = (size_t)((char*)a - base);
@@ -1585,6 +1652,8 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
   bp.take<unsigned char>(1);
   g->res_off = 0;
   g->res_bytes = bp.off;
+  float* feats = probe ? bp.take<float>((int64_t)GSVD_RAND_MLP_IN * np) : nullptr;
+  g->feat_off = probe ? (size_t)((char*)feats - base) : 0;
   gb.sides.resize(2 * np);
   for (int i = 0; i < np; ++i) {
     const gsvd_rand_pair& q = *pv[i];
@@ -1595,6 +1664,11 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
     if (adaptive) {  // bases of up to cap columns per side, grown by blocks; min(k, 2 cap) pairs
       P.l = acap(q);
       P.k = std::min(q.k, 2 * P.l);
+      P.q = 0;
+    }
+    if (probe) {  // the 16-column probe sketch of the learned proposal
+      P.l = GROUP_PROBE_L;
+      P.k = 1;
       P.q = 0;
     }
     P.L = 2 * P.l;
@@ -1631,6 +1705,7 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
       S.R = bp.take<float>((int64_t)S.lx * S.lp);
       S.gnorm = bp.take<double>(tc_group_norm_parts() * cdiv(S.M, 128));
       S.bnorm = bp.take<double>(cdiv(S.n * P.l, 256));
+      if (probe) S.Wz = bp.take<double>((int64_t)P.l * P.l);
       if (acc_resid && !adaptive) {  // the slab energies of ||B||_F^2
         S.epart = bp.take<float>(adapt_energy_part_elems(S.M, S.n, ADAPT_BMAX));
         S.C = bp.take<double>(cdiv(P.l, ADAPT_BMAX) * cdiv(S.n * ADAPT_BMAX, 256));  // slab partial sums
@@ -1688,7 +1763,8 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
     for (int j = 0; j < ns; ++j) {
       const GSide& S = gb.sides[j];
       const gsvd_rand_pair& q = *pv[j / 2];
-      t[j] = GaussB{S.Xt, S.ldx, S.n, S.l, S.lx, q.seed, q.pair, (uint32_t)(j & 1), GSVD_RAND_STREAM_FIXED, 0};
+      t[j] = GaussB{S.Xt, S.ldx, S.n, S.l, S.lx, q.seed, q.pair, (uint32_t)(j & 1),
+                    probe ? GSVD_RAND_STREAM_PROBE : GSVD_RAND_STREAM_FIXED, 0};
       mldx = std::max(mldx, S.ldx);
       mlr = std::max(mlr, S.lx);
     }
@@ -1900,6 +1976,59 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
     add_orth_jobs(jobs);
   };
 
+  if (probe) {
+    // the single-pair probe's steps for the whole group: Y = G Omega_probe with ||G||_F^2, Y^T as
+    // the K-major operand, Z = G^T Y, the Grams Y^T Y and Z^T Z, and each side's 32 features
+    set_active(-1);
+    if (!add_gemm(0, true, 0)) return fail(h, GSVD_RAND_ERR_ARG, "tensor map of a grouped product rejected");
+    cur_tag = GSVD_RAND_STAGE_PROPOSAL;
+    for (int j = 0; j < ns; ++j) {
+      const GSide& S = gb.sides[j];
+      const float* Y = S.Y;
+      float* Qt = S.Qt;
+      const int64_t lp = S.lp, M = S.M, ldm = S.ldm;
+      const int l = S.l;
+      push([=](const unsigned char*, cudaStream_t st) { return launch_transpose<float>(Y, lp, M, l, Qt, ldm, st); });
+    }
+    if (!add_gemm(1, false, 2)) return fail(h, GSVD_RAND_ERR_ARG, "tensor map of a grouped product rejected");
+    add_reduce(false);
+    cur_tag = GSVD_RAND_STAGE_PROPOSAL;
+    for (int pass = 0; pass < 2; ++pass) {  // Y^T Y into W, then Z^T Z into Wz
+      std::vector<GramB> gt(ns);
+      std::vector<GramRedB> rt(ns);
+      int mch = 1;
+      for (int j = 0; j < ns; ++j) {
+        const GSide& S = gb.sides[j];
+        const int64_t M = pass ? S.n : S.M;
+        const int64_t rpc = round_up(cdiv(M, cdiv(M, GROUP_GRAM_ROWS)), 16);
+        const int chunks = (int)cdiv(M, rpc);
+        gt[j] = GramB{pass ? S.Z : S.Y, S.lp, M, rpc, S.l, chunks, S.gpart, nullptr};
+        rt[j] = GramRedB{S.gpart, chunks, S.l, pass ? S.Wz : S.W, nullptr};
+        mch = std::max(mch, chunks);
+      }
+      const size_t og = A.add(gt), orr = A.add(rt);
+      push([og, orr, ns, mch](const unsigned char* d, cudaStream_t st) {
+        cudaError_t e;
+        if ((e = launch_gram_blocks_b(reinterpret_cast<const GramB*>(d + og), ns, mch, GROUP_PROBE_L, st))) return e;
+        return launch_gram_sum_b(reinterpret_cast<const GramRedB*>(d + orr), ns, GROUP_PROBE_L, st);
+      });
+    }
+    {
+      std::vector<ProbeFeatB> t(ns);
+      for (int j = 0; j < ns; ++j) {
+        const GSide& S = gb.sides[j];
+        t[j] = ProbeFeatB{S.W, S.Wz, S.gnorm,
+                          feats + (int64_t)(j / 2) * GSVD_RAND_MLP_IN + (GSVD_RAND_MLP_IN / 2) * (j & 1),
+                          (int)(tc_group_norm_parts() * cdiv(S.M, 128)), 0};
+      }
+      const size_t off = A.add(t);
+      push([off, ns](const unsigned char* d, cudaStream_t st) {
+        return launch_probe_features_b(reinterpret_cast<const ProbeFeatB*>(d + off), ns, st);
+      });
+    }
+    for (auto& t : gb.tags) t = GSVD_RAND_STAGE_PROPOSAL;
+    return GSVD_RAND_OK;
+  }
   if (!adaptive) {
     set_active(-1);
     if (!add_gemm(0, true, 0)) return fail(h, GSVD_RAND_ERR_ARG, "tensor map of a grouped product rejected");
@@ -2321,7 +2450,7 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
 // One grouped solve of `pairs` with the state (plan, tables, graph) in *slot: fixed-rank bases,
 // or Algorithm 1's (adaptive); acc_resid as in group_build.
 int solve_grouped_as(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs, GroupState** slot, bool adaptive,
-                     bool acc_resid) {
+                     bool acc_resid, bool probe = false) {
   const int prec = h->cfg.prec;
   if (prec != GSVD_RAND_TF32 && prec != GSVD_RAND_TF32X3)
     return fail(h, GSVD_RAND_ERR_UNSUPPORTED, "grouped solves run the TF32 / 3xTF32 tensor-core products");
@@ -2340,6 +2469,7 @@ int solve_grouped_as(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs, GroupS
     const double ab[2] = {adaptive ? (double)h->cfg.block_b : 0.0, adaptive ? h->cfg.tol : -1.0};
     memcpy(key.data() + (size_t)npairs * sizeof(gsvd_rand_pair) + 2 * sizeof(int), ab, sizeof(ab));
     if (acc_resid) key.push_back(1);
+    if (probe) key.push_back(2);
   }
   for (int i = 0; i < npairs; ++i) {
     // the outputs are copied out of the results block after the graph: not part of the key
@@ -2379,9 +2509,10 @@ int solve_grouped_as(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs, GroupS
     for (int i = 0; i < npairs; ++i) {
       gsvd_rand_pair& q = pairs[i];
       // fixed rank: l = k + oversample; adaptive: the column cap min(m, p, n, ADAPT_CMAX)
-      const int64_t l = adaptive ? std::min<int64_t>(std::min(std::min(q.m, q.p), q.n), ADAPT_CMAX)
-                                 : (int64_t)q.k + q.oversample;
-      bool ok = q.G1 && q.G2 && q.alpha && q.beta && q.m >= 1 && q.p >= 1 && q.n >= 1 && q.ld1 >= q.n &&
+      const int64_t l = probe ? GROUP_PROBE_L
+                              : adaptive ? std::min<int64_t>(std::min(std::min(q.m, q.p), q.n), ADAPT_CMAX)
+                                         : (int64_t)q.k + q.oversample;
+      bool ok = q.G1 && q.G2 && ((q.alpha && q.beta) || probe) && q.m >= 1 && q.p >= 1 && q.n >= 1 && q.ld1 >= q.n &&
                 q.ld2 >= q.n && q.k >= 1 && q.oversample >= 0 && q.q >= 0 && q.q <= 16 && l >= 1 && l <= 128 &&
                 l <= std::min(std::min(q.m, q.p), q.n) && is_device_ptr(q.G1) && is_device_ptr(q.G2) &&
                 tc_shape_ok(q.G1, q.ld1, (int)l) && tc_shape_ok(q.G2, q.ld2, (int)l);
@@ -2407,7 +2538,7 @@ int solve_grouped_as(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs, GroupS
     }
     // pass 1: sizes; pass 2: the real layout and tables
     GroupBuild sizer;
-    int rc = group_build(h, pv, prec, nullptr, sizer, g, adaptive, acc_resid);
+    int rc = group_build(h, pv, prec, nullptr, sizer, g, adaptive, acc_resid, probe);
     if (rc) return rc;
     const size_t tab_bytes = (sizer.arena.buf.size() + 255) & ~size_t(255);
     const size_t need = sizer.ws_bytes + tab_bytes + 4096;
@@ -2425,7 +2556,7 @@ int solve_grouped_as(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs, GroupS
     GroupBuild* gbp = new GroupBuild();
     std::unique_ptr<GroupBuild> gb_own(gbp);
     GroupBuild& gb = *gbp;
-    if ((rc = group_build(h, pv, prec, g->ws, gb, g, adaptive, acc_resid))) return rc;
+    if ((rc = group_build(h, pv, prec, g->ws, gb, g, adaptive, acc_resid, probe))) return rc;
     unsigned char* dtab = reinterpret_cast<unsigned char*>(g->ws) + ((gb.ws_bytes + 255) & ~size_t(255));
     if (gb.arena.buf.size() > tab_bytes) return fail(h, GSVD_RAND_ERR_CUDA, "table layout changed between passes");
     // pinned staging of the tables (and later the results)
@@ -2572,6 +2703,7 @@ int solve_grouped_as(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs, GroupS
       g->cols[2 * t] = stops[2 * t];
       g->cols[2 * t + 1] = stops[2 * t + 1];
     }
+    if (probe) continue;
     if (!is_device_ptr(q.alpha)) memcpy(q.alpha, g->host + (o.a_off - g->res_off), (size_t)o.k * sizeof(double));
     if (!is_device_ptr(q.beta)) memcpy(q.beta, g->host + (o.b_off - g->res_off), (size_t)o.k * sizeof(double));
     if (q.resid_out) {
@@ -2619,6 +2751,8 @@ int solve_grouped_learned(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs);
 int retry_breakdowns(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs, bool adaptive, int rc) {
   if (rc != GSVD_RAND_ERR_NONFINITE && rc != GSVD_RAND_ERR_BREAKDOWN && rc != GSVD_RAND_ERR_TOL_MISS) return rc;
   bool any = false;
+  std::string first;
+  int first_i = -1;
   for (int i = 0; i < npairs; ++i) {
     gsvd_rand_pair& q = pairs[i];
     if (q.status != GSVD_RAND_ERR_NONFINITE && q.status != GSVD_RAND_ERR_BREAKDOWN) continue;
@@ -2628,12 +2762,16 @@ int retry_breakdowns(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs, bool a
     q.status = solve_dispatch(h, adaptive, q.G1, q.m, q.ld1, q.G2, q.p, q.ld2, q.n, q.k, q.oversample, q.q, q.seed,
                               q.alpha, q.beta, q.r_out, q.resid_out, true);
     h->pair_word = 0;
+    if (q.status && first_i < 0) {
+      first_i = i;
+      first = h->err;
+    }
   }
   if (!any) return rc;
   for (int i = 0; i < npairs; ++i)
     if (pairs[i].status)
-      return fail(h, pairs[i].status, "pair %d (first failing pair): status %d after the FP64-Cholesky retries", i,
-                  pairs[i].status);
+      return fail(h, pairs[i].status, "pair %d (first failing pair): status %d%s%s", i, pairs[i].status,
+                  i == first_i ? " in its FP64-Cholesky retry: " : "", i == first_i ? first.c_str() : "");
   h->err.clear();
   return GSVD_RAND_OK;
 }
@@ -2696,27 +2834,51 @@ int solve_grouped_learned(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs) {
   CU(cudaMemcpyAsync(lim_dev, lim.data(), lim.size() * sizeof(int), cudaMemcpyHostToDevice, st));
   CU(cudaMemsetAsync(pst, 0, (size_t)np * sizeof(DevStatus), st));
   CU(cudaMemsetAsync(feats, 0, (size_t)np * MLP_IN * sizeof(float), st));
-  // the probe of every pair that can run (the grouped solve refuses the others with ARG)
-  for (int i = 0; i < np; ++i) {
-    const gsvd_rand_pair& q = pairs[i];
-    const bool ok = q.G1 && q.G2 && q.m >= 16 && q.p >= 16 && q.n >= 16 && q.ld1 >= q.n && q.ld2 >= q.n &&
-                    is_device_ptr(q.G1) && is_device_ptr(q.G2);
-    if (!ok) continue;
-    h->pair_word = q.pair;
-    const int rc = probe_dispatch(h, q.G1, q.m, q.ld1, q.G2, q.p, q.ld2, q.n, q.seed, feats + (int64_t)i * MLP_IN,
-                                  pst + i);
-    h->pair_word = 0;
-    if (rc) return rc;
+  // the probes of the whole group as one grouped pass (pairs it refuses keep zero features; the
+  // fixed-rank group refuses them with ARG); its features land in the probe group's workspace in
+  // the order of its valid pairs and are gathered by pair
+  {
+    std::vector<gsvd_rand_pair> pp(pairs, pairs + np);
+    for (auto& q : pp) {
+      q.k = 1;
+      q.oversample = GROUP_PROBE_L - 1;
+      q.q = 0;
+      q.alpha = q.beta = nullptr;
+      q.r_out = nullptr;
+      q.resid_out = nullptr;
+    }
+    const int prc = solve_grouped_as(h, np, pp.data(), &h->grp3, false, false, true);
+    if (prc && prc != GSVD_RAND_ERR_ARG && prc != GSVD_RAND_ERR_NONFINITE && prc != GSVD_RAND_ERR_BREAKDOWN)
+      return prc;
+    GroupState* g3 = h->grp3;
+    const float* fsrc = reinterpret_cast<const float*>(g3->ws + g3->feat_off);
+    const int nv = (int)g3->valid.size();
+    if (nv == np) {
+      CU(cudaMemcpyAsync(feats, fsrc, (size_t)np * MLP_IN * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    } else {
+      for (int t = 0; t < nv; ++t)
+        CU(cudaMemcpyAsync(feats + (int64_t)g3->valid[t] * MLP_IN, fsrc + (int64_t)t * MLP_IN, MLP_IN * sizeof(float),
+                           cudaMemcpyDeviceToDevice, st));
+    }
+    std::vector<DevStatus> ps(np);
+    for (int i = 0; i < np; ++i) ps[i].code = pp[i].status == GSVD_RAND_ERR_ARG ? 0 : pp[i].status;
+    CU(cudaMemcpyAsync(pst, ps.data(), (size_t)np * sizeof(DevStatus), cudaMemcpyHostToDevice, st));
+    CU(cudaStreamSynchronize(st));
   }
+  std::unique_ptr<ProfScope> prof(new ProfScope(h, GSVD_RAND_STAGE_PROPOSAL));
   float* F = h->mlp_dev;
   CU(mlp_forward(F, F + MLP_NORM, feats, np, 1, logits, scratch, st));
   CU(launch_mlp_plan(logits, np, (float)GSVD_RAND_MLP_KQUANTILE, lim_dev, lim_dev + np, lim_dev + 2 * np, plan_dev,
                      st));
+  prof.reset();
   std::vector<int> plan(3 * (size_t)np);
   std::vector<DevStatus> pstat(np);
+  h->grp_feats.assign((size_t)np * MLP_IN, 0.f);
+  CU(cudaMemcpyAsync(h->grp_feats.data(), feats, h->grp_feats.size() * sizeof(float), cudaMemcpyDeviceToHost, st));
   CU(cudaMemcpyAsync(plan.data(), plan_dev, plan.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
   CU(cudaMemcpyAsync(pstat.data(), pst, (size_t)np * sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
+  prof_collect(h);
   // the fixed-rank group with each pair's plan
   std::vector<gsvd_rand_pair> fx(pairs, pairs + np);
   std::vector<double> res(2 * (size_t)np, 0.0);
@@ -2996,8 +3158,10 @@ int gsvd_rand_destroy(gsvd_rand_t h) {
   if (!h) return GSVD_RAND_OK;
   for (auto wk : h->workers) gsvd_rand_destroy(wk);
   h->workers.clear();
+  if (h->f64) gsvd_rand_destroy(h->f64);
+  h->f64 = nullptr;
   cudaSetDevice(h->cfg.device);
-  for (GroupState** sl : {&h->grp, &h->grp2})
+  for (GroupState** sl : {&h->grp, &h->grp2, &h->grp3})
     if (*sl) {
       cudaStreamSynchronize((*sl)->stream);
       group_free(*sl);
@@ -3016,6 +3180,7 @@ int gsvd_rand_destroy(gsvd_rand_t h) {
   if (h->gstage) cudaFree(h->gstage);
   if (h->gbounce) cudaFree(h->gbounce);
   if (h->cplx) cudaFree(h->cplx);
+  if (h->wide) cudaFree(h->wide);
   delete h;
   return GSVD_RAND_OK;
 }
@@ -3171,6 +3336,14 @@ int gsvd_rand_solve_grouped(gsvd_rand_t h, int npairs, gsvd_rand_pair* pairs) {
   if (!h || npairs < 0 || (npairs > 0 && !pairs)) return GSVD_RAND_ERR_ARG;
   if (npairs == 0) return GSVD_RAND_OK;
   return solve_grouped_staged(h, npairs, pairs);
+}
+
+int gsvd_rand_grouped_features(gsvd_rand_t h, float* feats, int npairs) {
+  if (!h || !feats || npairs < 1 || (size_t)npairs * MLP_IN != h->grp_feats.size())
+    return h ? fail(h, GSVD_RAND_ERR_ARG, "no learned grouped solve of %d pairs on this context", npairs)
+             : GSVD_RAND_ERR_ARG;
+  memcpy(feats, h->grp_feats.data(), h->grp_feats.size() * sizeof(float));
+  return GSVD_RAND_OK;
 }
 
 int gsvd_rand_grouped_plans(gsvd_rand_t h, int* plans, int npairs) {

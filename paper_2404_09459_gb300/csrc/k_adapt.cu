@@ -150,7 +150,7 @@ __global__ void adapt_mask_b_kernel(const AdaptMaskB* __restrict__ tab) {
 // over thousands of rows), which would set a floor near 1e-2 under the cumulated residual.
 // Partials: a thread per column j of G, FP32 FMAs over a chunk of EN_ROWS rows (round to
 // nearest), part[(chunk n + j) bi + t] = sum over the chunk of P[row][t] G[row][j].
-constexpr int EN_ROWS = 2048, EN_COLS = 128, EN_TILE = 64;
+constexpr int EN_ROWS = 2048, EN_COLS = 128, EN_TILE = 64, EN_UNROLL = 8;
 __global__ __launch_bounds__(EN_COLS) void energy_part_b_kernel(const AdaptEnergyB* __restrict__ tab) {
   const AdaptEnergyB& a = tab[blockIdx.z];
   if (side_done(a.stop)) return;
@@ -172,17 +172,34 @@ __global__ __launch_bounds__(EN_COLS) void energy_part_b_kernel(const AdaptEnerg
     }
     __syncthreads();
     if ((int64_t)blockIdx.x * EN_COLS >= a.n) continue;
-    if (j < a.n)
-      for (int r = 0; r < rows; ++r) {
-        const float g = a.G[(rt + r) * a.ldg + j];
+    if (j < a.n) {
+      // EN_UNROLL rows of G loaded ahead of their FMAs (memory-level parallelism: one load in
+      // flight per warp would leave HBM mostly idle); the sums keep their row order
+      const float* gp = a.G + rt * a.ldg + j;
+      int r = 0;
+      for (; r + EN_UNROLL <= rows; r += EN_UNROLL) {
+        float g[EN_UNROLL];
+#pragma unroll
+        for (int u = 0; u < EN_UNROLL; ++u) g[u] = __ldg(gp + (int64_t)(r + u) * a.ldg);
+#pragma unroll
+        for (int u = 0; u < EN_UNROLL; ++u)
+#pragma unroll
+          for (int t = 0; t < ADAPT_BMAX; ++t)
+            if (t < bi) acc[t] = fmaf(psh[r + u][t], g[u], acc[t]);
+      }
+      for (; r < rows; ++r) {
+        const float g = gp[(int64_t)r * a.ldg];
 #pragma unroll
         for (int t = 0; t < ADAPT_BMAX; ++t)
           if (t < bi) acc[t] = fmaf(psh[r][t], g, acc[t]);
       }
+    }
   }
   if (j >= a.n) return;
   float* out = a.part + ((int64_t)blockIdx.y * a.n + j) * bi;
-  for (int t = 0; t < bi; ++t) out[t] = acc[t];
+#pragma unroll
+  for (int t = 0; t < ADAPT_BMAX; ++t)  // unrolled: acc stays in registers
+    if (t < bi) out[t] = acc[t];
 }
 
 // epart[b] = sum over entries e in [256 b, 256 b + 256) of (sum over chunks of part)^2, in FP64.

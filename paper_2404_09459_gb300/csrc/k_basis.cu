@@ -150,6 +150,27 @@ cudaError_t launch_realify(const T* G, int64_t ldg, int64_t M, int64_t n, T* R, 
 template cudaError_t launch_realify<double>(const double*, int64_t, int64_t, int64_t, double*, int64_t, cudaStream_t);
 template cudaError_t launch_realify<float>(const float*, int64_t, int64_t, int64_t, float*, int64_t, cudaStream_t);
 
+// D = G widened to FP64 (M x n, row strides ldg and ldd): a thread per entry.
+__global__ void widen_kernel(const float* __restrict__ G, int64_t ldg, int64_t M, int64_t n, double* __restrict__ D,
+                             int64_t ldd) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = blockIdx.y;
+  if (j >= n || i >= M) return;
+  D[i * ldd + j] = (double)G[i * ldg + j];
+}
+
+cudaError_t launch_widen(const float* G, int64_t ldg, int64_t M, int64_t n, double* D, int64_t ldd, cudaStream_t st) {
+  if (M < 1 || n < 1) return cudaSuccess;
+  for (int64_t r0 = 0; r0 < M; r0 += 65535) {
+    const int64_t rows = std::min<int64_t>(65535, M - r0);
+    dim3 grid((unsigned)cdiv(n, 256), (unsigned)rows);
+    widen_kernel<<<grid, 256, 0, st>>>(G + r0 * ldg, ldg, rows, n, D + r0 * ldd, ldd);
+    cudaError_t e = launched();
+    if (e) return e;
+  }
+  return cudaSuccess;
+}
+
 template <typename T>
 cudaError_t launch_gaussian_kmajor(T* Xt, int64_t ldx, int64_t n, int l, int lrows, uint64_t seed,
                                    uint32_t pair, uint32_t side, uint32_t stream, cudaStream_t st) {

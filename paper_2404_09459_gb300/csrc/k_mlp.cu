@@ -106,9 +106,11 @@ __device__ double eig16_warp(double* A, double* d, double* e2) {
 }  // namespace
 
 // One CTA of 2 warps per side: warp 0 takes W1 = Y^T Y, warp 1 W2 = Z^T Z.
-// gpart: the sketch CTAs' partial sums of G^2 (gcount entries).
-__global__ void probe_features_kernel(const double* __restrict__ W1, const double* __restrict__ W2,
-                                      const double* __restrict__ gpart, int gcount, float* __restrict__ feats) {
+// gpart: the sketch CTAs' partial sums of G^2 (gcount entries).  The FP64 bisection takes a
+// good fraction of a millisecond on one SM (FP64 runs at 1/64 of the FP32 rate), so a group's
+// sides run as one launch, a CTA each (probe_features_b_kernel).
+__device__ void probe_features_body(const double* __restrict__ W1, const double* __restrict__ W2,
+                                    const double* __restrict__ gpart, int gcount, float* __restrict__ feats) {
   __shared__ double A[2][256], D[2][16], E2[2][16];
   __shared__ double s_g2;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -135,9 +137,25 @@ __global__ void probe_features_kernel(const double* __restrict__ W1, const doubl
   }
 }
 
+__global__ __launch_bounds__(64) void probe_features_kernel(const double* __restrict__ W1,
+                                                             const double* __restrict__ W2,
+                                                             const double* __restrict__ gpart, int gcount,
+                                                             float* __restrict__ feats) {
+  probe_features_body(W1, W2, gpart, gcount, feats);
+}
+__global__ __launch_bounds__(64) void probe_features_b_kernel(const ProbeFeatB* __restrict__ tab) {
+  const ProbeFeatB& t = tab[blockIdx.x];
+  probe_features_body(t.W1, t.W2, t.gpart, t.gcount, t.feats);
+}
+
 cudaError_t launch_probe_features(const double* W1, const double* W2, const double* gpart, int gcount,
                                   float* feats, cudaStream_t st) {
   probe_features_kernel<<<1, 64, 0, st>>>(W1, W2, gpart, gcount, feats);
+  return launched();
+}
+cudaError_t launch_probe_features_b(const ProbeFeatB* tab, int nprob, cudaStream_t st) {
+  if (nprob <= 0) return cudaSuccess;
+  probe_features_b_kernel<<<nprob, 64, 0, st>>>(tab);
   return launched();
 }
 

@@ -488,7 +488,7 @@ cudaError_t launch_oa_refine(const double* A, int N, double* X, double* lam, dou
 __device__ __forceinline__ void oa_cut_cluster_body(int N, int r, double* XtX, const double* __restrict__ S,
                                                     const double* __restrict__ part, int nparts,
                                                     const double* __restrict__ lam, double* __restrict__ Vc,
-                                                    int* __restrict__ cinfo, float* jscr) {
+                                                    int* __restrict__ cinfo, float* jscr, double null_rel) {
   extern __shared__ float cut_sm[];
   __shared__ int s_ord[512];
   __shared__ double s_dg[CUT_BIG_NMAX];  // Rayleigh quotients s_ii / x_i^T x_i of the cluster
@@ -527,7 +527,11 @@ __device__ __forceinline__ void oa_cut_cluster_body(int N, int r, double* XtX, c
     const double d = s_delta;
     auto lm = [&](int rk) { return lam[s_ord[rk]]; };
     int lo = r - 1, hi = r + 1;  // ranks [lo, hi)
-    if (r < 1 || r >= N || !(lm(r - 1) - lm(r) <= d)) {
+    // no cluster when the gap at the cut is resolved, or (null_rel > 0) when the last kept
+    // eigenvalue lies below null_rel of the largest: the cut is then in the numerical null space
+    // of K (directions of the bases beyond the pair's rank, at the FP32 data's noise level), where
+    // any split is as good as another
+    if (r < 1 || r >= N || !(lm(r - 1) - lm(r) <= d) || (null_rel > 0.0 && lm(r - 1) <= null_rel * lm(0))) {
       lo = 0;
       hi = 0;
     } else {
@@ -665,7 +669,7 @@ __global__ __launch_bounds__(1024) void oa_cut_cluster_kernel(int N, int r, doub
                                                               const double* __restrict__ lam,
                                                               double* __restrict__ Vc, int* __restrict__ cinfo,
                                                               float* jscr) {
-  oa_cut_cluster_body(N, r, XtX, S, part, nparts, lam, Vc, cinfo, jscr);
+  oa_cut_cluster_body(N, r, XtX, S, part, nparts, lam, Vc, cinfo, jscr, 0.0);
 }
 
 // X[:, idx] <- X[:, idx] V_c, one CTA per row of X.
@@ -1076,12 +1080,103 @@ __global__ __launch_bounds__(256) void dgemm_b_kernel(const DgemmB* __restrict__
     }
 }
 
+// The double-float form of the batched product: the same 32 x 32 output tiles, 64 threads with
+// 4 x 4 outputs each (rows 4 ty .. 4 ty + 3, columns 4 tx .. 4 tx + 3), the operands staged as
+// (hi, lo) FP32 pairs in rows padded to 16-byte multiples so that each thread reads its four A
+// and four B pairs of a k with four 16-byte loads (a 2 x 2 register tile needs one load per
+// product; the 4 x 4 tile, one per four).  Each output is the same double-float chain over k as
+// in dgemm_b_kernel<.., true> (df_fma per k, renormalised after each 32-k stage).
+constexpr int DF_T = 32, DF_BK = 32, DF_THREADS = 64, DF_LD = DF_T + 2;
+static_assert(DF_T == SG_T, "the double-float tiles share the grid of dgemm_b_kernel");
+template <typename T>
+__device__ __forceinline__ float2 df_split(T v) {
+  if constexpr (std::is_same<T, float>::value) {
+    return make_float2(v, 0.f);
+  } else {
+    const float h = __double2float_rn(v);
+    return make_float2(h, __double2float_rn(v - (double)h));
+  }
+}
+template <typename TA, typename TB>
+__global__ __launch_bounds__(DF_THREADS) void dfgemm_b_kernel(const DgemmB* __restrict__ tab) {
+  const DgemmB& g = tab[blockIdx.z];
+  const int i0 = blockIdx.x * DF_T, j0 = blockIdx.y * DF_T;
+  if (i0 >= g.Mr || j0 >= g.Nc) return;
+  if (g.sym && blockIdx.x > blockIdx.y) return;  // symmetric result: upper tiles, mirrored
+  __shared__ __align__(16) float2 As[DF_BK][DF_LD];
+  __shared__ __align__(16) float2 Bs[DF_BK][DF_LD];
+  const TA* __restrict__ A = static_cast<const TA*>(g.A);
+  const TB* __restrict__ B = static_cast<const TB*>(g.B);
+  const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
+  const int K = g.K, ta = g.ta, tb = g.tb;
+  const bool active = i0 + 4 * ty < g.Mr && j0 + 4 * tx < g.Nc;
+  float sh[4][4], sl[4][4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) sh[m][q] = sl[m][q] = 0.f;
+  for (int k0 = 0; k0 < K; k0 += DF_BK) {
+    for (int e = tid; e < DF_T * DF_BK; e += DF_THREADS) {
+      const int a = e / 32, b = e % 32;  // consecutive threads along the contiguous index
+      int i, kk;
+      if (!ta) { i = a; kk = b; } else { kk = a; i = b; }
+      int gi = i0 + i, gk = k0 + kk;
+      As[kk][i] = df_split((gi < g.Mr && gk < K) ? (ta ? A[(int64_t)gk * g.lda + gi] : A[(int64_t)gi * g.lda + gk])
+                                                : TA(0));
+      int j;
+      if (!tb) { kk = a; j = b; } else { j = a; kk = b; }
+      const int gj = j0 + j;
+      gk = k0 + kk;
+      Bs[kk][j] = df_split((gj < g.Nc && gk < K) ? (tb ? B[(int64_t)gj * g.ldb + gk] : B[(int64_t)gk * g.ldb + gj])
+                                                : TB(0));
+    }
+    __syncthreads();
+    if (active) {
+      const int kend = min(DF_BK, K - k0);
+#pragma unroll 2
+      for (int kk = 0; kk < kend; ++kk) {
+        const float4 a01 = *reinterpret_cast<const float4*>(&As[kk][4 * ty]);
+        const float4 a23 = *reinterpret_cast<const float4*>(&As[kk][4 * ty + 2]);
+        const float4 b01 = *reinterpret_cast<const float4*>(&Bs[kk][4 * tx]);
+        const float4 b23 = *reinterpret_cast<const float4*>(&Bs[kk][4 * tx + 2]);
+        const float2 av[4] = {make_float2(a01.x, a01.y), make_float2(a01.z, a01.w), make_float2(a23.x, a23.y),
+                              make_float2(a23.z, a23.w)};
+        const float2 bv[4] = {make_float2(b01.x, b01.y), make_float2(b01.z, b01.w), make_float2(b23.x, b23.y),
+                              make_float2(b23.z, b23.w)};
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) df_fma(av[m], bv[q], sh[m][q], sl[m][q]);
+      }
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) df_renorm(sh[m][q], sl[m][q]);
+    }
+    __syncthreads();
+  }
+  if (!active) return;
+#pragma unroll
+  for (int m = 0; m < 4; ++m)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = i0 + 4 * ty + m, j = j0 + 4 * tx + q;
+      if (i < g.Mr && j < g.Nc) {
+        double* c = g.C + (int64_t)i * g.ldc + j;
+        const double r = (double)sh[m][q] + (double)sl[m][q];
+        const double v = g.beta == 0.0 ? g.alpha * r : g.alpha * r + g.beta * (*c);
+        *c = v;
+        if (g.sym && blockIdx.x < blockIdx.y) g.C[(int64_t)j * g.ldc + i] = v;
+      }
+    }
+}
+
 template <typename TA, typename TB>
 cudaError_t launch_dgemm_b(const DgemmB* tab, int nprob, int max_Mr, int max_Nc, cudaStream_t st, bool df) {
   if (nprob <= 0) return cudaSuccess;
   const dim3 grid((unsigned)cdiv(max_Mr, SG_T), (unsigned)cdiv(max_Nc, SG_T), (unsigned)nprob);
   if (df)
-    dgemm_b_kernel<TA, TB, true><<<grid, 256, 0, st>>>(tab);
+    dfgemm_b_kernel<TA, TB><<<grid, DF_THREADS, 0, st>>>(tab);
   else
     dgemm_b_kernel<TA, TB, false><<<grid, 256, 0, st>>>(tab);
   return launched();
@@ -1199,7 +1294,9 @@ cudaError_t launch_oa_refine_b(const OaB* tab, const DgemmB* dg, int nprob, int 
 // cluster's indices in P), then the rotation of its columns of X.
 __global__ __launch_bounds__(1024) void oa_cut_cluster_b_kernel(const OaB* __restrict__ tab) {
   const OaB& o = tab[blockIdx.x];
-  oa_cut_cluster_body(o.N, o.r, o.XtX, o.S, o.part, 1, o.lam, o.F, reinterpret_cast<int*>(o.P), o.jscr);
+  // grouped solves run FP32 data only: eigenvalues below 1e-12 of the largest (singular values
+  // below 1e-6 of the stack's) are beyond what those bases resolve
+  oa_cut_cluster_body(o.N, o.r, o.XtX, o.S, o.part, 1, o.lam, o.F, reinterpret_cast<int*>(o.P), o.jscr, 1e-12);
 }
 __global__ __launch_bounds__(128) void cut_rotate_b_kernel(const OaB* __restrict__ tab) {
   const OaB& o = tab[blockIdx.z];

@@ -26,6 +26,7 @@ cudaError_t launch_gaussian_kmajor_cplx(T* Xt, int64_t ldx, int64_t n2, int l2, 
                                         uint32_t pair, uint32_t side, uint32_t stream, cudaStream_t st);
 template <typename T>
 cudaError_t launch_realify(const T* G, int64_t ldg, int64_t M, int64_t n, T* R, int64_t ldr, cudaStream_t st);
+cudaError_t launch_widen(const float* G, int64_t ldg, int64_t M, int64_t n, double* D, int64_t ldd, cudaStream_t st);
 template <typename T>
 cudaError_t launch_gaussian_kmajor(T* Xt, int64_t ldx, int64_t n, int l, int lrows, uint64_t seed,
                                    uint32_t pair, uint32_t side, uint32_t stream, cudaStream_t st);
@@ -226,6 +227,13 @@ cudaError_t launch_residual(const double* gpart, int ng, const double* bpart, in
 // ---- learned (k, q) proposal (k_mlp.cu) ----------------------------------------
 // Features of one side from W1 = Y^T Y, W2 = Z^T Z (16 x 16 FP64, full) and the
 // sketch's partial sums of G^2 (gcount entries): 32 floats.
+// The probe features of many sides in one launch (a CTA of 64 threads each).
+struct ProbeFeatB {
+  const double *W1, *W2, *gpart;
+  float* feats;
+  int gcount, pad;
+};
+cudaError_t launch_probe_features_b(const ProbeFeatB* tab, int nprob, cudaStream_t st);
 cudaError_t launch_probe_features(const double* W1, const double* W2, const double* gpart, int gcount,
                                   float* feats, cudaStream_t st);
 int64_t mlp_param_count();

@@ -229,10 +229,13 @@ def test_grouped_dense_tail_across_the_cut():
 def test_grouped_rank_far_below_l_retries_with_fp64_cholesky():
     # sketches whose rank is far below l with noise under FP32 resolution (sigma 1e-9): the first
     # shifted CholeskyQR pass leaves Q1 beyond what the FP32 factors of the next pass resolve, and
-    # such a pair is solved again on its own with FP64 Cholesky factors and the same Philox words.
-    # The first pair is the uneven-batch draw (m 7274, p 7004, n 370, rank 35) whose G2 sketch
-    # at l = 128 and pair word 35 broke down in a grouped solve (pivot 65 overflowed); k = rank,
-    # so the k returned pairs are the planted ones, well separated from the noise pairs
+    # such a pair is solved again on its own with FP64 Cholesky factors and the same Philox words,
+    # and, where those bases still break down, in FP64 throughout on widened copies.
+    # The first pair is an uneven-batch draw (m 7274, p 7004, n 370, rank 35) whose G2 sketch at
+    # pair word 35 broke down in grouped solves; with k = rank the k returned pairs are the planted
+    # ones, well separated from the noise pairs, and are compared with the oracle.  The last pair is
+    # the same matrices with l = 82 (the sketch whose pivot 54 overflowed with FP64 Cholesky factors
+    # too), again with k = rank
     from paper_2404_09459_gb300.inputs import learned_pairs, planted_pair_torch
     s35 = learned_pairs(48, seed=12, m_range=(4000, 12000), n_range=(300, 600))[35]
     specs = [PairSpec(m=s35.m, p=s35.p, n=s35.n, r=s35.r, alpha=s35.alpha, decay=s35.decay, sigma=s35.sigma,
@@ -241,15 +244,22 @@ def test_grouped_rank_far_below_l_retries_with_fp64_cholesky():
                       q=2, seed=71),
              PairSpec(m=2000, p=4000, n=256, r=20, alpha="uniform", decay="exp10", sigma=1e-9, k=20,
                       oversample=100, q=0, seed=72)]
-    words = [35, 1, 2]
+    specs.append(PairSpec(m=s35.m, p=s35.p, n=s35.n, r=s35.r, alpha=s35.alpha, decay=s35.decay, sigma=s35.sigma,
+                          k=s35.r, oversample=82 - s35.r, q=0, seed=s35.seed))
+    words = [35, 1, 2, 35]
     mats = [tuple(G.double().cpu().numpy() for G in planted_pair_torch(specs[0], device="cuda")[:2])]
-    mats += [planted_pair(s)[:2] for s in specs[1:]]
+    mats += [planted_pair(s)[:2] for s in specs[1:3]] + [mats[0]]
     pairs = [dict(G1=_dev(G1), G2=_dev(G2), k=s.kk, oversample=s.oversample, q=s.q, seed=s.seed, pair=w)
              for s, (G1, G2), w in zip(specs, mats, words)]
     with P.Context("tf32x3") as ctx:
         outs = ctx.solve_grouped(pairs)
         retries = ctx.chol64_retries()
-    assert retries >= 1
+        single = ctx.solve_batched(pairs[3:], 1)[0]
+    # the group retried its breaking pairs (the FP32 breakdown is marginal: a single solve's
+    # product rounding may avoid it, so the batched single solve only has to agree)
+    assert retries >= 2
+    outs = outs + [single]
+    specs, mats, words = specs + specs[3:], mats + mats[3:], words + words[3:]
     for s, (G1, G2), w, out in zip(specs, mats, words, outs):
         assert out["status"] == 0 and out["r"] == s.kk
         ref = O.rand_gsvd(G1, G2, s.kk, s.oversample, s.q, s.seed, pair=w)

@@ -240,6 +240,34 @@ def test_grouped_learned_plans_and_fallback():
         assert np.max(e) <= 1e-4, (i, np.max(e))
 
 
+def test_grouped_probe_features_match_oracle():
+    # the probes of a learned group run as one grouped pass (3xTF32 products, batched Grams): the
+    # features of every pair, with its own Philox word, against the oracle's probe of that pair
+    # (the single probe's FP32 targets); a pair too narrow for the probe (n < 16) keeps zeros
+    from paper_2404_09459_gb300.inputs import aligned_rows
+    specs = SPECS + [PairSpec(m=1500, p=900, n=260, r=40, alpha="uniform", decay="exp10", sigma=1e-8, k=40,
+                              oversample=8, seed=35),
+                     PairSpec(m=400, p=300, n=12, r=6, alpha="uniform", decay="exp10", sigma=1e-8, k=4,
+                              oversample=2, seed=36)]
+    mats = [planted_pair(s)[:2] for s in specs]
+    pairs = [dict(G1=aligned_rows(_t(G1)), G2=aligned_rows(_t(G2)), k=min(s.k, s.n - 2), oversample=2, q=0,
+                  seed=s.seed, pair=i) for i, (s, (G1, G2)) in enumerate(zip(specs, mats))]
+    th, norm = _fixed_net(3, 1)
+    with P.Context("tf32x3", use_learned=True, tol=2e-3, block_b=8) as ctx:
+        ctx.mlp_set(th, norm)
+        try:
+            ctx.solve_grouped(pairs)
+        except P.GsvdRandError as e:
+            assert e.name == "ARG"  # the narrow pair
+        got = ctx.grouped_features(len(pairs))
+    for i, (s, (G1, G2)) in enumerate(zip(specs[:-1], mats[:-1])):
+        ref = L.probe_features(G1, G2, s.seed, pair=i)
+        keep = ref > -5.0
+        np.testing.assert_allclose(got[i][keep], ref[keep], rtol=0, atol=2e-3)
+        assert np.all((got[i] >= L.FEAT_MIN) & (got[i] <= L.FEAT_MAX))
+    assert np.all(got[-1] == 0.0)
+
+
 def test_plan_on_device_matches_oracle_rule():
     # the learned solves' (k, q) decision runs on the device (gsvd_rand_mlp_plan); both sides take
     # it in FP64 from the same FP32 logits
