@@ -79,7 +79,7 @@ typedef enum {
 /* Philox stream ids (fourth counter word) of the Gaussian test matrices. */
 #define GSVD_RAND_STREAM_FIXED 0u          /* the n x (k+p) Omega of the fixed-rank solve */
 #define GSVD_RAND_STREAM_ADAPTIVE 0x10000u /* + block index i: Omega_i of Algorithm 1 */
-#define GSVD_RAND_STREAM_PROBE 0x20000u    /* the 16-column probe sketch */
+#define GSVD_RAND_STREAM_PROBE 0x20000u    /* the 64-column probe sketch */
 
 typedef struct gsvd_rand_ctx *gsvd_rand_t;
 
@@ -256,7 +256,7 @@ int gsvd_rand_solve_batched(gsvd_rand_t h, int npairs, gsvd_rand_pair *pairs, in
  * used; each pair returns min(k, l1 + l2) pairs (*r_out; alpha / beta need min(k, 2 cap)
  * entries, those past *r_out are set to -1); gsvd_rand_grouped_basis_cols gives l1, l2.
  * With cfg->use_learned = 1 (and a network loaded) the learned proposal runs for the whole
- * group: the 16-column probe sketch of every pair on the device (no host read between pairs),
+ * group: the 64-column probe sketch of every pair on the device (no host read between pairs),
  * one network forward over the batch (BF16 weights) and every pair's (k, q) plan on the device
  * (as gsvd_rand_solve's learned form; k capped by the pair's k, which is the capacity of alpha
  * and beta), read back once; the pairs then run as one fixed-rank group with their own k and q,
@@ -407,10 +407,11 @@ uint64_t gsvd_rand_launch_count(void);
  * Algorithm 1 labels its training pairs and takes over whenever the proposed
  * bases miss the tolerance.
  *
- * Features (64 floats, side 1 then side 2): with Omega_p the n x 16 Gaussian
- * of Philox stream GSVD_RAND_STREAM_PROBE, Y = G Omega_p and Z = G^T Y,
- * log10 of the eigenvalues of Y^T Y / (16 ||G||_F^2) and of
- * Z^T Z / (16 ||G||_F^4), each descending, clipped to [-12, 1].
+ * Features (64 floats, side 1 then side 2): with Omega_p the n x 64 Gaussian
+ * of Philox stream GSVD_RAND_STREAM_PROBE and Y = G Omega_p, log10 of the 1st,
+ * 3rd, ..., 63rd largest eigenvalues of Y^T Y / (64 ||G||_F^2), clipped to
+ * [-12, 1] (32 per side).  A 64-column probe shows where the energy of each side
+ * falls off for ranks up to about 64 (a 16-column one, only up to 16).
  * Network: x^ = (x - mean) / std, h1 = relu(x^ W1 + b1), h2 = relu(h1 W2 + b2),
  * z = h2 W3 + b3; W1 64 x 128, W2 128 x 128, W3 128 x 37, row-major; params is
  * W1 | b1 | W2 | b2 | W3 | b3 (GSVD_RAND_MLP_PARAMS floats), norm is mean | std
@@ -424,14 +425,14 @@ uint64_t gsvd_rand_launch_count(void);
 #define GSVD_RAND_MLP_KCLS 32
 #define GSVD_RAND_MLP_QCLS 5
 #define GSVD_RAND_MLP_KBUCKET 4
-#define GSVD_RAND_MLP_PROBE 16
+#define GSVD_RAND_MLP_PROBE 64
 #define GSVD_RAND_MLP_KQUANTILE 0.9 /* the learned solve takes the smallest k bucket whose
                                        cumulative softmax probability reaches this level */
 #define GSVD_RAND_MLP_PARAMS (64 * 128 + 128 + 128 * 128 + 128 + 128 * 37 + 37)
 
 /* The 64 probe features of {G1, G2} (layouts and precision as gsvd_rand_solve;
  * the Philox pair word is 0).  feats: 64 floats, device or host.  Errors: ARG
- * (m, p or n below 16), OOM, CUDA. */
+ * (m, p or n below 64), OOM, CUDA. */
 int gsvd_rand_probe_features(gsvd_rand_t h, const void *G1, int64_t m, int64_t ld1, const void *G2, int64_t p,
                              int64_t ld2, int64_t n, uint64_t seed, float *feats);
 

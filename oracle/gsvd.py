@@ -31,7 +31,7 @@ from .philox import gaussian
 # Philox stream ids (fourth counter word); the same values are fixed in the C header.
 STREAM_FIXED = 0          # the n x (k+p) test matrix of the fixed-rank solve
 STREAM_ADAPTIVE = 0x10000  # + block index i: Omega_i of Algorithm 1
-STREAM_PROBE = 0x20000     # the 16-column probe sketch
+STREAM_PROBE = 0x20000     # the 64-column probe sketch of the learned proposal
 
 
 def orth(Y: np.ndarray) -> np.ndarray:

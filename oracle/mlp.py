@@ -10,17 +10,18 @@ the proposed basis misses the residual tolerance.
 
 Readings taken here (the paper has no learned component; each is also listed in
 the design notes):
-  * Probe features.  Per side s with G_s (M x n): Omega_p is the n x 16
-    Gaussian of Philox stream 0x20000; Y = G Omega_p, Z = G^T Y;
-    mu_i = eigenvalues of Y^T Y and nu_i = eigenvalues of Z^T Z, descending;
-    g2 = ||G||_F^2.  Since E||G w||^2 = ||G||_F^2 and E||G^T G w||^2 =
-    ||G^T G||_F^2 for a Gaussian w, mu_i / (16 g2) ~ sigma_i^2 / sum sigma^2
-    and nu_i / (16 g2^2) ~ sigma_i^4 / (sum sigma^2)^2: dimensionless energy
-    fractions of the leading directions and of their powered form.  The 64
-    features are log10 of these (32 per side, side 1 first), clipped to
+  * Probe features.  Per side s with G_s (M x n): Omega_p is the n x 64
+    Gaussian of Philox stream 0x20000; Y = G Omega_p; mu_i = eigenvalues of
+    Y^T Y, descending; g2 = ||G||_F^2.  Since E||G w||^2 = ||G||_F^2 for a
+    Gaussian w, mu_i / (64 g2) ~ sigma_i^2 / sum sigma^2: dimensionless energy
+    fractions of the leading 64 directions.  The 64 features are log10 of
+    mu_1, mu_3, ..., mu_63 over 64 g2 (32 per side, side 1 first), clipped to
     [-12, 1]: an energy fraction of 1e-12 is far below the 1e-8 that a 1e-4
     relative residual leaves, and the clip keeps rounding-level eigenvalues
-    (about 1e-16 of the largest in FP64) out of the features.
+    (about 1e-16 of the largest in FP64) out of the features.  A 64-column
+    probe shows where a side's energy falls off for ranks up to about 64; with
+    16 columns the leading 16 fractions of a pair are the same for every rank
+    above 16 under a fixed decay law, so the rank could not be read off.
   * Network: 64 -> 128 -> 128 -> 37, ReLU, inputs standardised by a fixed
     mean and standard deviation (from the training set); logits 0..31 are
     the k bucket (bucket b covers k = 4b+1 .. 4b+4), logits 32..36 are
@@ -42,7 +43,7 @@ from .philox import gaussian
 
 IN, HID, KCLS, QCLS = 64, 128, 32, 5
 OUT = KCLS + QCLS
-PROBE_COLS = 16
+PROBE_COLS = 64
 K_BUCKET = 4
 FEAT_MIN, FEAT_MAX = -12.0, 1.0
 STREAM_PROBE = O.STREAM_PROBE
@@ -74,14 +75,11 @@ def side_features(G: np.ndarray, seed: int, pair: int, side: int) -> np.ndarray:
     n = G.shape[1]
     Om = gaussian(n, PROBE_COLS, seed, pair, side, STREAM_PROBE)
     Y = G @ Om
-    Z = G.T @ Y
     g2 = float(np.sum(G * G))
     mu = np.linalg.eigvalsh(Y.T @ Y)[::-1]
-    nu = np.linalg.eigvalsh(Z.T @ Z)[::-1]
     with np.errstate(divide="ignore"):
-        f1 = np.log10(np.maximum(mu, 0.0) / (PROBE_COLS * g2))
-        f2 = np.log10(np.maximum(nu, 0.0) / (PROBE_COLS * g2 * g2))
-    return np.clip(np.concatenate([f1, f2]), FEAT_MIN, FEAT_MAX)
+        f = np.log10(np.maximum(mu[0::2], 0.0) / (PROBE_COLS * g2))
+    return np.clip(f, FEAT_MIN, FEAT_MAX)
 
 
 def probe_features(G1, G2, seed: int, pair: int = 0) -> np.ndarray:

@@ -1142,15 +1142,15 @@ int solve_adaptive_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, 
 }
 
 // ---------------------------------------------------------------------------
-// Probe features of the learned proposal: per side Y = G Omega_p (n x 16,
-// Philox stream GSVD_RAND_STREAM_PROBE), Z = G^T Y, the 16 x 16 Grams of Y and
-// Z, and the features from their eigenvalues (k_mlp.cu).  The products and
-// Grams are the solve's own kernels at l = 16.
+// Probe features of the learned proposal: per side Y = G Omega_p (n x 64,
+// Philox stream GSVD_RAND_STREAM_PROBE) with ||G||_F^2, the 64 x 64 Gram of Y,
+// and the features from its eigenvalues (k_mlp.cu).  The product and Gram are
+// the solve's own kernels at l = 64.
 // ---------------------------------------------------------------------------
 template <typename T, typename TC>
 int probe_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, const void* G2v, int64_t p, int64_t ld2,
             int64_t n, uint64_t seed, float* feats, DevStatus* st_ext = nullptr) {
-  constexpr int PL = 16;
+  constexpr int PL = GSVD_RAND_MLP_PROBE;
   cudaStream_t st = h->stream;
   const int prec = h->cfg.prec;
   const bool bf16 = prec == GSVD_RAND_BF16;
@@ -1214,21 +1214,12 @@ int probe_t(gsvd_rand_ctx* h, const void* G1v, int64_t m, int64_t ld1, const voi
       CU(launch_gaussian_kmajor<T>(b.Xt, pl.ldx, n, PL, PL, seed, h->pair_word, (uint32_t)s, GSVD_RAND_STREAM_PROBE,
                                    st));
     if ((rc = sv.gx(Gs[s], ldg[s], M, pl, b, b.gnorm))) return rc;
-    if (use_tc) {
-      CU(launch_transpose<T>(b.Y, pl.lp, M, PL, b.Q, round_up(M, 4), st));
-      if (bf16 && (rc = sv.split_q(b, M, pl, true))) return rc;
-    } else {
-      b.Q = b.Y;  // the CUDA-core G^T Q reads Q row-major with ld lp
-    }
-    if ((rc = sv.gtq(Gs[s], ldg[s], M, pl, b, b.Z, pl.lp, 0, nullptr, true))) return rc;
-    int64_t rpy, rpz;
-    const int cy = gram_chunks(M, PL, &rpy), cz = gram_chunks(n, PL, &rpz);
+    int64_t rpy;
+    const int cy = gram_chunks(M, PL, &rpy);
     CU(launch_gram_partial<T>(b.Y, pl.lp, M, PL, b.gpart, cy, rpy, st));
     CU(launch_gram_reduce(b.gpart, cy, PL, b.W, st));
-    CU(launch_gram_partial<T>(b.Z, pl.lp, n, PL, b.gpart, cz, rpz, st));
-    CU(launch_gram_reduce(b.gpart, cz, PL, (double*)b.R, st));
     const int gct = use_tc ? tc_gx_ctas(M) : gemm_gx_simt_ctas(M);
-    CU(launch_probe_features(b.W, (const double*)b.R, b.gnorm, gct, feats + 32 * s, st));
+    CU(launch_probe_features(b.W, b.gnorm, gct, feats + GSVD_RAND_MLP_IN / 2 * s, st));
   }
   if (st_ext) return GSVD_RAND_OK;
   CU(cudaMemcpyAsync(h->st_host, st_dev, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
@@ -1360,6 +1351,12 @@ int solve_learned(gsvd_rand_ctx* h, const void* G1, int64_t m, int64_t ld1, cons
                   int64_t n, int kcap, int oversample, uint64_t seed, double* alpha, double* beta, int* r_out,
                   double* resid_out) {
   if (!h->mlp_ready) return fail(h, GSVD_RAND_ERR_ARG, "use_learned without a network (mlp_path or gsvd_rand_mlp_set)");
+  if (std::min(std::min(m, p), n) < GSVD_RAND_MLP_PROBE) {  // too narrow for the probe: Algorithm 1
+    h->last_plan[0] = h->last_plan[1] = 0;
+    h->last_plan[2] = 1;
+    return solve_dispatch(h, true, G1, m, ld1, G2, p, ld2, n, kcap, oversample, 0, seed, alpha, beta, r_out,
+                          resid_out);
+  }
   float* F = h->mlp_dev;
   int rc = probe_dispatch(h, G1, m, ld1, G2, p, ld2, n, seed, F + MLP_FEATS);
   if (rc) return rc;
@@ -1577,7 +1574,6 @@ struct GSide {
   double *C = nullptr, *xpart = nullptr, *state = nullptr;
   float* epart = nullptr;  // chunk partials of the block energy ||P^T G||_F^2
   int* stop = nullptr;
-  double* Wz = nullptr;  // probe groups: Z^T Z of Z = G^T Y
 };
 struct GPair {
   int k, l, L, q;
@@ -1615,7 +1611,7 @@ struct GroupBuild {
 
 constexpr int64_t GROUP_GRAM_ROWS = 1024;  // rows per Gram chunk
 constexpr int64_t GROUP_GTQ_ROWS = 4096;   // rows per split of G^T Q
-constexpr int GROUP_PROBE_L = 16;          // columns of the learned proposal's probe sketch
+constexpr int GROUP_PROBE_L = GSVD_RAND_MLP_PROBE;  // columns of the learned proposal's probe sketch
 
 // Lays out the workspace (base == nullptr: sizes only) and records the launch sequence.
 // acc_resid: the fixed-rank residual from ||B||_F^2 summed on the CUDA cores (the energy kernels of
@@ -1666,7 +1662,7 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
       P.k = std::min(q.k, 2 * P.l);
       P.q = 0;
     }
-    if (probe) {  // the 16-column probe sketch of the learned proposal
+    if (probe) {  // the 64-column probe sketch of the learned proposal
       P.l = GROUP_PROBE_L;
       P.k = 1;
       P.q = 0;
@@ -1705,7 +1701,6 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
       S.R = bp.take<float>((int64_t)S.lx * S.lp);
       S.gnorm = bp.take<double>(tc_group_norm_parts() * cdiv(S.M, 128));
       S.bnorm = bp.take<double>(cdiv(S.n * P.l, 256));
-      if (probe) S.Wz = bp.take<double>((int64_t)P.l * P.l);
       if (acc_resid && !adaptive) {  // the slab energies of ||B||_F^2
         S.epart = bp.take<float>(adapt_energy_part_elems(S.M, S.n, ADAPT_BMAX));
         S.C = bp.take<double>(cdiv(P.l, ADAPT_BMAX) * cdiv(S.n * ADAPT_BMAX, 256));  // slab partial sums
@@ -1901,11 +1896,12 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
     DevStatus* st;
     int stage;
     const int* stop;
+    int passes = 3;  // 2: a well-conditioned basis is enough (the power iteration's intermediate bases)
   };
   auto add_orth_jobs = [&](const std::vector<OrthJob>& jobs) {
     const int na = (int)jobs.size();
     for (int pass = 0; pass < 3; ++pass) {
-      std::vector<TcGroupSpec> asp(na);
+      std::vector<TcGroupSpec> asp;
       std::vector<GramB> gt[2];
       std::vector<GramRedB> rt[2];
       std::vector<CholB> ct[2];
@@ -1913,6 +1909,7 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
       int64_t msum = 0;
       for (int a = 0; a < na; ++a) {
         const OrthJob& J = jobs[a];
+        if (pass >= J.passes) continue;
         const int64_t M = J.M;
         const float* src = pass == 0 ? J.src : (pass == 1 ? J.tmp : J.tmp + M * J.lt);
         const int64_t lds = pass == 0 ? J.lds : J.lt;
@@ -1926,7 +1923,8 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
         ct[cls].push_back(CholB{J.W, shift, tau, J.R, J.st, J.l, J.stage + (pass > 0 ? 1 : 0), (int)J.lp, 0, J.stop});
         maxlc[cls] = std::max(maxlc[cls], J.l);
         maxch[cls] = std::max(maxch[cls], chunks);
-        TcGroupSpec& x = asp[a];
+        asp.emplace_back();
+        TcGroupSpec& x = asp.back();
         memset(&x, 0, sizeof(x));
         x.G = src;
         x.ldg = lds;
@@ -1936,7 +1934,7 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
         x.Bt = J.R;
         x.ldb = J.lp;
         x.stop = J.stop;
-        if (pass < 2) {
+        if (pass < J.passes - 1) {
           x.out = pass == 0 ? J.tmp : J.tmp + M * J.lt;
           x.ldo = J.lt;
         } else {
@@ -1958,52 +1956,45 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
           return launch_chol_b(reinterpret_cast<const CholB*>(d + oc), cnt, ml, st);
         });
       }
+      if (asp.empty()) continue;
       // the re-orthonormalisation wins the accuracy back: its products are 3xTF32 in every mode
-      if (!add_gemm_specs(0, false, -1, asp, msum / std::max(na, 1), GSVD_RAND_TF32X3)) orth_ok = false;
+      if (!add_gemm_specs(0, false, -1, asp, msum / (int64_t)asp.size(), GSVD_RAND_TF32X3)) orth_ok = false;
       cur_tag = GSVD_RAND_STAGE_ORTH;
     }
   };
-  // which 0: Y (M x l) -> Q^T; 1: Z (n x l) -> X^T, for the active sides
-  auto add_orth = [&](int which, int stage0) {
+  // which 0: Y (M x l) -> Q^T; 1: Z (n x l) -> X^T, for the active sides.  it: the power step
+  // that follows (-1: none); a basis that only feeds the next power-step product takes two
+  // passes (shifted, then plain: kappa near 1, the same span), the final basis Q three
+  auto add_orth = [&](int which, int stage0, int it) {
     std::vector<OrthJob> jobs;
     for (int j : act) {
       const GSide& S = gb.sides[j];
       const int64_t M = which == 0 ? S.M : S.n;
-      jobs.push_back(OrthJob{which == 0 ? S.Y : S.Z, S.lp, M, S.l, S.tmp, S.lt, S.gpart, S.W, S.R, S.lp,
-                             which == 0 ? S.Qt : S.Xt, which == 0 ? S.ldm : S.ldx, 1, gb.prs[j / 2].st,
-                             10 * (j & 1) + stage0, nullptr});
+      OrthJob J{which == 0 ? S.Y : S.Z, S.lp, M, S.l, S.tmp, S.lt, S.gpart, S.W, S.R, S.lp,
+                which == 0 ? S.Qt : S.Xt, which == 0 ? S.ldm : S.ldx, 1, gb.prs[j / 2].st,
+                10 * (j & 1) + stage0, nullptr};
+      J.passes = (which == 1 || gb.prs[j / 2].q > it) ? 2 : 3;
+      jobs.push_back(J);
     }
     add_orth_jobs(jobs);
   };
 
   if (probe) {
-    // the single-pair probe's steps for the whole group: Y = G Omega_probe with ||G||_F^2, Y^T as
-    // the K-major operand, Z = G^T Y, the Grams Y^T Y and Z^T Z, and each side's 32 features
+    // the single-pair probe's steps for the whole group: Y = G Omega_probe with ||G||_F^2, the
+    // Gram Y^T Y, and each side's 32 features
     set_active(-1);
     if (!add_gemm(0, true, 0)) return fail(h, GSVD_RAND_ERR_ARG, "tensor map of a grouped product rejected");
     cur_tag = GSVD_RAND_STAGE_PROPOSAL;
-    for (int j = 0; j < ns; ++j) {
-      const GSide& S = gb.sides[j];
-      const float* Y = S.Y;
-      float* Qt = S.Qt;
-      const int64_t lp = S.lp, M = S.M, ldm = S.ldm;
-      const int l = S.l;
-      push([=](const unsigned char*, cudaStream_t st) { return launch_transpose<float>(Y, lp, M, l, Qt, ldm, st); });
-    }
-    if (!add_gemm(1, false, 2)) return fail(h, GSVD_RAND_ERR_ARG, "tensor map of a grouped product rejected");
-    add_reduce(false);
-    cur_tag = GSVD_RAND_STAGE_PROPOSAL;
-    for (int pass = 0; pass < 2; ++pass) {  // Y^T Y into W, then Z^T Z into Wz
+    {
       std::vector<GramB> gt(ns);
       std::vector<GramRedB> rt(ns);
       int mch = 1;
       for (int j = 0; j < ns; ++j) {
         const GSide& S = gb.sides[j];
-        const int64_t M = pass ? S.n : S.M;
-        const int64_t rpc = round_up(cdiv(M, cdiv(M, GROUP_GRAM_ROWS)), 16);
-        const int chunks = (int)cdiv(M, rpc);
-        gt[j] = GramB{pass ? S.Z : S.Y, S.lp, M, rpc, S.l, chunks, S.gpart, nullptr};
-        rt[j] = GramRedB{S.gpart, chunks, S.l, pass ? S.Wz : S.W, nullptr};
+        const int64_t rpc = round_up(cdiv(S.M, cdiv(S.M, GROUP_GRAM_ROWS)), 16);
+        const int chunks = (int)cdiv(S.M, rpc);
+        gt[j] = GramB{S.Y, S.lp, S.M, rpc, S.l, chunks, S.gpart, nullptr};
+        rt[j] = GramRedB{S.gpart, chunks, S.l, S.W, nullptr};
         mch = std::max(mch, chunks);
       }
       const size_t og = A.add(gt), orr = A.add(rt);
@@ -2017,7 +2008,7 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
       std::vector<ProbeFeatB> t(ns);
       for (int j = 0; j < ns; ++j) {
         const GSide& S = gb.sides[j];
-        t[j] = ProbeFeatB{S.W, S.Wz, S.gnorm,
+        t[j] = ProbeFeatB{S.W, S.gnorm,
                           feats + (int64_t)(j / 2) * GSVD_RAND_MLP_IN + (GSVD_RAND_MLP_IN / 2) * (j & 1),
                           (int)(tc_group_norm_parts() * cdiv(S.M, 128)), 0};
       }
@@ -2032,16 +2023,16 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
   if (!adaptive) {
     set_active(-1);
     if (!add_gemm(0, true, 0)) return fail(h, GSVD_RAND_ERR_ARG, "tensor map of a grouped product rejected");
-    add_orth(0, 1);
+    add_orth(0, 1, 0);
     int qmax = 0;
     for (auto* q : pv) qmax = std::max(qmax, q->q);
     for (int it = 0; it < qmax; ++it) {
       set_active(it);
       if (!add_gemm(1, false, 2)) return fail(h, GSVD_RAND_ERR_ARG, "tensor map of a grouped product rejected");
       add_reduce(false);
-      add_orth(1, 3);
+      add_orth(1, 3, it);
       if (!add_gemm(0, false, 1)) return fail(h, GSVD_RAND_ERR_ARG, "tensor map of a grouped product rejected");
-      add_orth(0, 5);
+      add_orth(0, 5, it + 1);
     }
   } else {
     // ---- Algorithm 1 per side, every block one step for the whole batch ----
@@ -2834,9 +2825,10 @@ int solve_grouped_learned(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs) {
   CU(cudaMemcpyAsync(lim_dev, lim.data(), lim.size() * sizeof(int), cudaMemcpyHostToDevice, st));
   CU(cudaMemsetAsync(pst, 0, (size_t)np * sizeof(DevStatus), st));
   CU(cudaMemsetAsync(feats, 0, (size_t)np * MLP_IN * sizeof(float), st));
-  // the probes of the whole group as one grouped pass (pairs it refuses keep zero features; the
-  // fixed-rank group refuses them with ARG); its features land in the probe group's workspace in
-  // the order of its valid pairs and are gathered by pair
+  // the probes of the whole group as one grouped pass (pairs it refuses, those narrower than the
+  // probe among them, keep zero features and go straight to the Algorithm 1 group); its features
+  // land in the probe group's workspace in the order of its valid pairs and are gathered by pair
+  std::vector<char> probed(np, 0);
   {
     std::vector<gsvd_rand_pair> pp(pairs, pairs + np);
     for (auto& q : pp) {
@@ -2851,6 +2843,7 @@ int solve_grouped_learned(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs) {
     if (prc && prc != GSVD_RAND_ERR_ARG && prc != GSVD_RAND_ERR_NONFINITE && prc != GSVD_RAND_ERR_BREAKDOWN)
       return prc;
     GroupState* g3 = h->grp3;
+    for (int t : g3->valid) probed[t] = 1;
     const float* fsrc = reinterpret_cast<const float*>(g3->ws + g3->feat_off);
     const int nv = (int)g3->valid.size();
     if (nv == np) {
@@ -2883,7 +2876,7 @@ int solve_grouped_learned(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs) {
   std::vector<gsvd_rand_pair> fx(pairs, pairs + np);
   std::vector<double> res(2 * (size_t)np, 0.0);
   for (int i = 0; i < np; ++i) {
-    fx[i].k = plan[3 * i];
+    fx[i].k = probed[i] ? plan[3 * i] : 0;  // k = 0: left out of the fixed-rank group
     fx[i].q = plan[3 * i + 1];
     fx[i].resid_out = res.data() + 2 * i;
   }
@@ -2895,7 +2888,7 @@ int solve_grouped_learned(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs) {
     h->grp_plans[3 * i] = plan[3 * i];
     h->grp_plans[3 * i + 1] = plan[3 * i + 1];
     const int c = pstat[i].code ? pstat[i].code : fx[i].status;
-    const bool redo = c == GSVD_RAND_ERR_BREAKDOWN || c == GSVD_RAND_ERR_NONFINITE ||
+    const bool redo = !probed[i] || c == GSVD_RAND_ERR_BREAKDOWN || c == GSVD_RAND_ERR_NONFINITE ||
                       (c == GSVD_RAND_OK && std::max(res[2 * i], res[2 * i + 1]) > h->cfg.tol);
     if (redo) {
       miss.push_back(i);
@@ -3491,7 +3484,7 @@ int gsvd_rand_probe_features(gsvd_rand_t h, const void* G1, int64_t m, int64_t l
   if (!h) return GSVD_RAND_ERR_ARG;
   if (!G1 || !G2 || !feats) return fail(h, GSVD_RAND_ERR_ARG, "null pointer argument");
   if (m < GSVD_RAND_MLP_PROBE || p < GSVD_RAND_MLP_PROBE || n < GSVD_RAND_MLP_PROBE || ld1 < n || ld2 < n)
-    return fail(h, GSVD_RAND_ERR_ARG, "the probe needs m, p, n >= 16 and ld >= n");
+    return fail(h, GSVD_RAND_ERR_ARG, "the probe needs m, p, n >= %d and ld >= n", GSVD_RAND_MLP_PROBE);
   CU(cudaSetDevice(h->cfg.device));
   int rc = mlp_alloc(h);
   if (rc) return rc;

@@ -1312,7 +1312,7 @@ __device__ __forceinline__ void eig_cut_big_body(const double* __restrict__ pblo
   const EigB* e = reinterpret_cast<const EigB*>(pblock + CUT_EIGB_OFF);
   const int c = e->N;
   if (c <= CUT_CMAX || c > EB_NMAX) return;
-  eig_big_body(e->A, c, e->X, e->lam, e->scratch, 0.f, c <= ap_cap);
+  eig_big_body(e->A, c, e->X, e->lam, e->scratch, e->noise_rel, c <= ap_cap);
 }
 
 __global__ __launch_bounds__(1024) void eig_cut_big_kernel(const double* __restrict__ pblock, int ap_cap) {

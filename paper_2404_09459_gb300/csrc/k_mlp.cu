@@ -1,10 +1,10 @@
 // The learned (k, q) proposal: probe features of a pair and the 64-128-128-37
 // classifier that reads them (training and inference kernels).
 //
-// Features (per side, from the 16-column probe Y = G Omega_p and Z = G^T Y):
-// log10 of the eigenvalues of Y^T Y over 16 ||G||_F^2 and of Z^T Z over
-// 16 ||G||_F^4, descending, clipped to [-12, 1].  The 16 x 16 eigenvalues come
-// from a Householder tridiagonalisation and Sturm bisection in FP64, one warp per Gram.
+// Features (per side, from the 64-column probe Y = G Omega_p): log10 of every other
+// eigenvalue of Y^T Y (the 1st, 3rd, ..., 63rd largest) over 64 ||G||_F^2, clipped to
+// [-12, 1]: 32 per side.  The 64 x 64 eigenvalues come from a Householder
+// tridiagonalisation and Sturm bisection in FP64, one CTA per Gram.
 //
 // Network: x^ = (x - mean) / std; h1 = relu(x^ W1 + b1); h2 = relu(h1 W2 + b2);
 // z = h2 W3 + b3 (W row-major in x out).  Loss: softmax cross-entropy of the
@@ -28,134 +28,144 @@ constexpr float FEAT_LO = -12.f, FEAT_HI = 1.f;
 __device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
 // ---------------------------------------------------------------- features
-// Eigenvalues of a symmetric 16 x 16 matrix in shared memory (row-major), by one
-// warp: Householder tridiagonalisation (Golub & Van Loan, Alg. 8.3.1; lane i owns
-// row i), then Sturm-count bisection, lane j < 16 finding the j-th smallest
-// eigenvalue.  Absolute accuracy ~ u ||A||, as Jacobi's.  Returns lambda_j in lane j.
-__device__ double eig16_warp(double* A, double* d, double* e2) {
-  const int lane = threadIdx.x & 31;
-  const bool act = lane < 16;
-  for (int k = 0; k < 14; ++k) {
-    // reflector of column k below the diagonal: v = x - alpha e_1, H = I - v v^T / (sg - x0 alpha)
-    const double x = (act && lane > k) ? A[lane * 16 + k] : 0.0;
-    double sg = x * x;
-    for (int o = 16; o > 0; o >>= 1) sg += __shfl_xor_sync(0xffffffffu, sg, o);
-    const double x0 = A[(k + 1) * 16 + k];
+// Eigenvalues of the symmetric 64 x 64 Gram W = Y^T Y (row-major, FP64) by one CTA of 64
+// threads: Householder tridiagonalisation (Golub & Van Loan, Alg. 8.3.1; thread i owns row i of
+// the trailing block), then Sturm-count bisection, thread j finding the j-th smallest eigenvalue.
+// W is positive semi-definite, so the bisection runs on a geometric scale between a floor of
+// 1e-14 of the Gershgorin bound (below it the feature is clipped anyway) and that bound: 30
+// geometric halvings leave a ratio below 1 + 3e-8 between the bracket's ends.
+constexpr int PN = GSVD_RAND_MLP_PROBE;  // probe columns (the Gram's order)
+static_assert(PN == 64, "one CTA of 64 threads per probe Gram");
+
+__device__ __forceinline__ double block_sum64(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();  // red free (previous readers done)
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  return red[0] + red[1];
+}
+
+// Thread j returns the j-th smallest eigenvalue (or a value at or below `floor` when it lies there).
+__device__ double eig64_block(double* A, double* vs, double* ws, double* d, double* e2, double* red, double* floor_out) {
+  const int i = threadIdx.x;
+  for (int k = 0; k < PN - 2; ++k) {
+    // reflector of column k below the diagonal: v = x - alpha e_{k+1}, H = I - v v^T / (sg - x0 alpha)
+    const double x = i > k ? A[i * PN + k] : 0.0;
+    const double sg = block_sum64(x * x, red);
+    const double x0 = A[(k + 1) * PN + k];
     const double sig = sqrt(sg);
     const double alpha = x0 >= 0.0 ? -sig : sig;
     const double den = sg - x0 * alpha;
     const bool refl = sig > 0.0 && den > 0.0;
-    const double v = (lane == k + 1) ? x0 - alpha : x;  // zero at and above row k
-    // p = A v / den (lane i: row i), then w = p - (p^T v / (2 den)) v
+    const double v = (i == k + 1) ? x0 - alpha : x;  // zero at and above row k
+    vs[i] = v;
+    __syncthreads();
+    // p = A v / den (row i), then w = p - (p^T v / (2 den)) v
     double p = 0.0;
-    if (refl)  // uniform: every lane runs the shuffles, rows 0..15 accumulate
-      for (int j = k + 1; j < 16; ++j) {
-        const double vj = __shfl_sync(0xffffffffu, v, j);
-        if (act) p = fma(A[lane * 16 + j], vj, p);
-      }
+    if (refl && i > k)
+      for (int j = k + 1; j < PN; ++j) p = fma(A[i * PN + j], vs[j], p);
     p = refl ? p / den : 0.0;
-    double pv = p * v;
-    for (int o = 16; o > 0; o >>= 1) pv += __shfl_xor_sync(0xffffffffu, pv, o);
-    const double wv = p - (refl ? 0.5 * pv / den : 0.0) * v;
-    __syncwarp();
-    if (refl)  // A <- A - v w^T - w v^T on the trailing block (rows and columns > k)
-      for (int j = k + 1; j < 16; ++j) {
-        const double wj = __shfl_sync(0xffffffffu, wv, j), vj = __shfl_sync(0xffffffffu, v, j);
-        if (act && lane > k) A[lane * 16 + j] -= v * wj + wv * vj;
-      }
-    __syncwarp();
-    if (lane == 0) {
-      d[k] = A[k * 16 + k];
+    const double pv = block_sum64(p * v, red);
+    const double w = p - (refl ? 0.5 * pv / den : 0.0) * v;
+    ws[i] = w;
+    __syncthreads();
+    if (refl && i > k)  // A <- A - v w^T - w v^T on the trailing block
+      for (int j = k + 1; j < PN; ++j) A[i * PN + j] -= v * ws[j] + w * vs[j];
+    if (i == 0) {
+      d[k] = A[k * PN + k];
       e2[k] = refl ? alpha * alpha : x0 * x0;
     }
-    __syncwarp();
+    __syncthreads();
   }
-  if (lane == 0) {
-    d[14] = A[14 * 16 + 14];
-    d[15] = A[15 * 16 + 15];
-    e2[14] = A[15 * 16 + 14] * A[15 * 16 + 14];
+  if (i == 0) {
+    d[PN - 2] = A[(PN - 2) * PN + PN - 2];
+    d[PN - 1] = A[(PN - 1) * PN + PN - 1];
+    e2[PN - 2] = A[(PN - 1) * PN + PN - 2] * A[(PN - 1) * PN + PN - 2];
   }
-  __syncwarp();
-  // Gershgorin bounds, then bisection on the Sturm count of T - x I
-  double lo = 0.0, hi = 0.0;
-  for (int i = 0; i < 16; ++i) {
-    const double r = (i > 0 ? sqrt(e2[i - 1]) : 0.0) + (i < 15 ? sqrt(e2[i]) : 0.0);
-    lo = fmin(lo, d[i] - r);
-    hi = fmax(hi, d[i] + r);
+  __syncthreads();
+  double hi = 0.0;
+  for (int r = 0; r < PN; ++r) {
+    const double rad = (r > 0 ? sqrt(e2[r - 1]) : 0.0) + (r < PN - 1 ? sqrt(e2[r]) : 0.0);
+    hi = fmax(hi, d[r] + rad);
   }
-  const double nrm = fmax(fabs(lo), fabs(hi));
-  const double pivmin = fmax(1e-300, 1e-30 * nrm);
-  const int j = lane & 15;
-  for (int it = 0; it < 64 && hi - lo > 1e-17 * nrm; ++it) {
-    const double mid = 0.5 * (lo + hi);
+  const double fl = 1e-14 * hi;
+  *floor_out = fl;
+  const double pivmin = fmax(1e-300, 1e-30 * hi);
+  auto count_below = [&](double xv) {  // eigenvalues of T below xv (Sturm sequence of T - xv I)
     int cnt = 0;
     double q = 1.0;
-    for (int i = 0; i < 16; ++i) {
-      q = (d[i] - mid) - (i > 0 ? e2[i - 1] / q : 0.0);
+    for (int r = 0; r < PN; ++r) {
+      q = (d[r] - xv) - (r > 0 ? e2[r - 1] / q : 0.0);
       if (fabs(q) < pivmin) q = -pivmin;
       cnt += q < 0.0;
     }
-    if (cnt > j)
-      hi = mid;
+    return cnt;
+  };
+  if (!(hi > 0.0) || count_below(fl) > i) return 0.0;  // at or below the floor
+  double lo = fl, up = hi;
+  for (int it = 0; it < 30; ++it) {
+    const double mid = sqrt(lo * up);
+    if (count_below(mid) > i)
+      up = mid;
     else
       lo = mid;
   }
-  return 0.5 * (lo + hi);
+  return sqrt(lo * up);
 }
 
 }  // namespace
 
-// One CTA of 2 warps per side: warp 0 takes W1 = Y^T Y, warp 1 W2 = Z^T Z.
-// gpart: the sketch CTAs' partial sums of G^2 (gcount entries).  The FP64 bisection takes a
-// good fraction of a millisecond on one SM (FP64 runs at 1/64 of the FP32 rate), so a group's
-// sides run as one launch, a CTA each (probe_features_b_kernel).
-__device__ void probe_features_body(const double* __restrict__ W1, const double* __restrict__ W2,
-                                    const double* __restrict__ gpart, int gcount, float* __restrict__ feats) {
-  __shared__ double A[2][256], D[2][16], E2[2][16];
+// One CTA of 64 threads per side: W = Y^T Y (PN x PN, upper triangle valid) and gpart, the
+// sketch CTAs' partial sums of G^2 (gcount entries); feats[t] (t = 0 .. 31) = log10 of the
+// (2t + 1)-th largest eigenvalue over PN ||G||_F^2, clipped.  The FP64 arithmetic takes a good
+// fraction of a millisecond on one SM (FP64 runs at 1/64 of the FP32 rate), so a group's sides
+// run as one launch, a CTA each (probe_features_b_kernel).
+__device__ void probe_features_body(const double* __restrict__ W, const double* __restrict__ gpart, int gcount,
+                                    float* __restrict__ feats) {
+  __shared__ double A[PN * PN];
+  __shared__ double vs[PN], ws[PN], D[PN], E2[PN], red[2];
   __shared__ double s_g2;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (warp == 0) {
+  const int tid = threadIdx.x;
+  if (tid < 32) {
     double g = 0.0;
-    for (int i = lane; i < gcount; i += 32) g += gpart[i];
+    for (int i = tid; i < gcount; i += 32) g += gpart[i];
     for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
-    if (lane == 0) s_g2 = g;
+    if (tid == 0) s_g2 = g;
   }
-  const double* W = warp == 0 ? W1 : W2;
-  for (int e = lane; e < 256; e += 32) {
-    const int i = e >> 4, j = e & 15;
-    A[warp][e] = W[(i <= j ? i : j) * 16 + (i <= j ? j : i)];  // the Gram partials hold the upper triangle
+  for (int e = tid; e < PN * PN; e += PN) {
+    const int i = e / PN, j = e % PN;
+    A[e] = W[(i <= j ? i : j) * PN + (i <= j ? j : i)];  // the Gram sums hold the upper triangle
   }
   __syncthreads();
-  const double lam = eig16_warp(A[warp], D[warp], E2[warp]);
-  const int rank = 15 - lane;  // lane j holds the j-th smallest: descending position 15 - j
-  if (lane < 16) {
-    const double den = 16.0 * (warp == 0 ? s_g2 : s_g2 * s_g2);
-    const double r = lam > 0.0 && den > 0.0 ? lam / den : 0.0;
+  double fl;
+  const double lam = eig64_block(A, vs, ws, D, E2, red, &fl);
+  const int pos = PN - 1 - tid;  // thread j holds the j-th smallest: descending position PN - 1 - j
+  if ((pos & 1) == 0) {
+    const double den = (double)PN * s_g2;
+    const double r = lam > fl && den > 0.0 ? lam / den : 0.0;
     float f = r > 0.0 ? (float)log10(r) : FEAT_LO;
     f = fminf(fmaxf(f, FEAT_LO), FEAT_HI);
-    feats[warp * 16 + rank] = f;
+    feats[pos >> 1] = f;
   }
 }
 
-__global__ __launch_bounds__(64) void probe_features_kernel(const double* __restrict__ W1,
-                                                             const double* __restrict__ W2,
+__global__ __launch_bounds__(PN) void probe_features_kernel(const double* __restrict__ W,
                                                              const double* __restrict__ gpart, int gcount,
                                                              float* __restrict__ feats) {
-  probe_features_body(W1, W2, gpart, gcount, feats);
+  probe_features_body(W, gpart, gcount, feats);
 }
-__global__ __launch_bounds__(64) void probe_features_b_kernel(const ProbeFeatB* __restrict__ tab) {
+__global__ __launch_bounds__(PN) void probe_features_b_kernel(const ProbeFeatB* __restrict__ tab) {
   const ProbeFeatB& t = tab[blockIdx.x];
-  probe_features_body(t.W1, t.W2, t.gpart, t.gcount, t.feats);
+  probe_features_body(t.W, t.gpart, t.gcount, t.feats);
 }
 
-cudaError_t launch_probe_features(const double* W1, const double* W2, const double* gpart, int gcount,
-                                  float* feats, cudaStream_t st) {
-  probe_features_kernel<<<1, 64, 0, st>>>(W1, W2, gpart, gcount, feats);
+cudaError_t launch_probe_features(const double* W, const double* gpart, int gcount, float* feats, cudaStream_t st) {
+  probe_features_kernel<<<1, PN, 0, st>>>(W, gpart, gcount, feats);
   return launched();
 }
 cudaError_t launch_probe_features_b(const ProbeFeatB* tab, int nprob, cudaStream_t st) {
   if (nprob <= 0) return cudaSuccess;
-  probe_features_b_kernel<<<nprob, 64, 0, st>>>(tab);
+  probe_features_b_kernel<<<nprob, PN, 0, st>>>(tab);
   return launched();
 }
 

@@ -498,6 +498,7 @@ __device__ __forceinline__ void oa_cut_cluster_body(int N, int r, double* XtX, c
   __shared__ int s_p[CUT_CMAX / 2], s_q[CUT_CMAX / 2];
   __shared__ float s_cs[CUT_CMAX / 2], s_sn[CUT_CMAX / 2];
   __shared__ unsigned s_off;
+  __shared__ int s_null;
   const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nwarp = nt >> 5;
   // clusters beyond CUT_CMAX columns go to the second launch when its scratch is given
   const bool big_ok = jscr != nullptr && N > CUT_CMAX;
@@ -540,6 +541,11 @@ __device__ __forceinline__ void oa_cut_cluster_body(int N, int r, double* XtX, c
     }
     s_lo = lo;
     s_c = hi - lo;
+    // the cluster reaches into the numerical null space of K (null_rel > 0): its block is then
+    // taken unshifted, so that the null eigenvalues sit at zero, where the big eigensolver takes
+    // them as noise (an orthonormal complement of the other columns: their orientation inside
+    // the null space is arbitrary) instead of separating a many-fold eigenvalue column by column
+    s_null = null_rel > 0.0 && hi > lo && lm(hi - 1) <= null_rel * lm(0);
     cinfo[0] = hi - lo;
     if (eb) eb->N = 0;  // no second eigensolve unless the cluster is large (below)
   }
@@ -555,7 +561,7 @@ __device__ __forceinline__ void oa_cut_cluster_body(int N, int r, double* XtX, c
   if (tid == 0) {
     double mu = 0.0;
     for (int a = 0; a < c; ++a) mu += s_dg[a];
-    s_mu = mu / c;
+    s_mu = s_null ? 0.0 : mu / c;
   }
   __syncthreads();
   {  // scale: the largest |entry| of the shifted block (parallel max)
@@ -587,7 +593,7 @@ __device__ __forceinline__ void oa_cut_cluster_body(int N, int r, double* XtX, c
       eb->X = Vc;
       eb->lam = reinterpret_cast<double*>(cinfo) + CUT_LAM_OFF;
       eb->scratch = jscr;
-      eb->noise_rel = 0.f;
+      eb->noise_rel = s_null ? 1e-6f : 0.f;  // FP32 resolution of the unit-scaled block
       eb->N = c;
     }
     return;

@@ -229,13 +229,12 @@ cudaError_t launch_residual(const double* gpart, int ng, const double* bpart, in
 // sketch's partial sums of G^2 (gcount entries): 32 floats.
 // The probe features of many sides in one launch (a CTA of 64 threads each).
 struct ProbeFeatB {
-  const double *W1, *W2, *gpart;
+  const double *W, *gpart;
   float* feats;
   int gcount, pad;
 };
 cudaError_t launch_probe_features_b(const ProbeFeatB* tab, int nprob, cudaStream_t st);
-cudaError_t launch_probe_features(const double* W1, const double* W2, const double* gpart, int gcount,
-                                  float* feats, cudaStream_t st);
+cudaError_t launch_probe_features(const double* W, const double* gpart, int gcount, float* feats, cudaStream_t st);
 int64_t mlp_param_count();
 int64_t mlp_scratch_floats(int B);
 // Logits (B x 37) of X (B x 64); bf16: weight matrices rounded to BF16.

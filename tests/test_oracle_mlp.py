@@ -114,12 +114,32 @@ def test_features_rank_one_closed_form_and_rank_floor():
     u, v = rng.standard_normal(200), rng.standard_normal(70)
     G = 3.0 * np.outer(u, v)
     f = L.side_features(G, 5, 1, 0)
-    Om = gaussian(70, 16, 5, 1, 0, L.STREAM_PROBE)
-    w = Om.T @ v / np.linalg.norm(v)  # Y = 3 |u| |v| u^ w^T
-    np.testing.assert_allclose(f[0], np.log10(w @ w / 16), atol=1e-10)
-    # G^T G Omega = 9 |u|^2 |v|^2 v^ w^T:  nu_1 / (16 g2^2) = |w|^2 / 16 as well
-    np.testing.assert_allclose(f[16], np.log10(w @ w / 16), atol=1e-10)
-    assert np.all(f[1:16] == L.FEAT_MIN) and np.all(f[17:] == L.FEAT_MIN)  # nothing beyond rank one
+    assert f.shape == (32,)
+    Om = gaussian(70, 64, 5, 1, 0, L.STREAM_PROBE)
+    w = Om.T @ v / np.linalg.norm(v)  # Y = 3 |u| |v| u^ w^T, Y^T Y = g2 w w^T
+    np.testing.assert_allclose(f[0], np.log10(w @ w / 64), atol=1e-10)
+    assert np.all(f[1:] == L.FEAT_MIN)  # nothing beyond rank one
+
+
+def test_features_show_ranks_up_to_the_probe_width():
+    # orthonormal U, V and equal singular values: Y^T Y = Omega^T V V^T Omega, whose nonzero
+    # eigenvalues are those of the r x r Wishart matrix W = (V^T Omega)(V^T Omega)^T, so the
+    # features are exactly log10 of W's eigenvalues over 64 r (g2 = r), every other one, and the
+    # rank shows as the first clipped feature: feature t is clipped exactly when 2 t >= r
+    rng = np.random.default_rng(11)
+    n = 150
+    for r in (6, 23, 40, 63):
+        U, _ = np.linalg.qr(rng.standard_normal((300, r)))
+        V, _ = np.linalg.qr(rng.standard_normal((n, r)))
+        G = U @ V.T
+        f = L.side_features(G, 4, 0, 1)
+        Om = gaussian(n, 64, 4, 0, 1, L.STREAM_PROBE)
+        B = V.T @ Om
+        lam = np.sort(np.linalg.eigvalsh(B @ B.T))[::-1]
+        want = np.log10(lam[0::2] / (64 * r))
+        t = np.arange(32)
+        np.testing.assert_allclose(f[2 * t < r], want, atol=1e-9)
+        assert np.all(f[2 * t >= r] == L.FEAT_MIN)
 
 
 def test_labels_on_exact_rank_pair():
