@@ -1896,7 +1896,6 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
     DevStatus* st;
     int stage;
     const int* stop;
-    int passes = 3;  // 2: a well-conditioned basis is enough (the power iteration's intermediate bases)
   };
   auto add_orth_jobs = [&](const std::vector<OrthJob>& jobs) {
     const int na = (int)jobs.size();
@@ -1909,7 +1908,6 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
       int64_t msum = 0;
       for (int a = 0; a < na; ++a) {
         const OrthJob& J = jobs[a];
-        if (pass >= J.passes) continue;
         const int64_t M = J.M;
         const float* src = pass == 0 ? J.src : (pass == 1 ? J.tmp : J.tmp + M * J.lt);
         const int64_t lds = pass == 0 ? J.lds : J.lt;
@@ -1934,7 +1932,7 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
         x.Bt = J.R;
         x.ldb = J.lp;
         x.stop = J.stop;
-        if (pass < J.passes - 1) {
+        if (pass < 2) {
           x.out = pass == 0 ? J.tmp : J.tmp + M * J.lt;
           x.ldo = J.lt;
         } else {
@@ -1962,19 +1960,17 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
       cur_tag = GSVD_RAND_STAGE_ORTH;
     }
   };
-  // which 0: Y (M x l) -> Q^T; 1: Z (n x l) -> X^T, for the active sides.  it: the power step
-  // that follows (-1: none); a basis that only feeds the next power-step product takes two
-  // passes (shifted, then plain: kappa near 1, the same span), the final basis Q three
-  auto add_orth = [&](int which, int stage0, int it) {
+  // which 0: Y (M x l) -> Q^T; 1: Z (n x l) -> X^T, for the active sides (three passes each: a
+  // two-pass basis between power steps, kappa(Q2) up to ~1.1 on the batch law, broke FP32
+  // factors downstream and left 1e-2 GSV errors)
+  auto add_orth = [&](int which, int stage0) {
     std::vector<OrthJob> jobs;
     for (int j : act) {
       const GSide& S = gb.sides[j];
       const int64_t M = which == 0 ? S.M : S.n;
-      OrthJob J{which == 0 ? S.Y : S.Z, S.lp, M, S.l, S.tmp, S.lt, S.gpart, S.W, S.R, S.lp,
-                which == 0 ? S.Qt : S.Xt, which == 0 ? S.ldm : S.ldx, 1, gb.prs[j / 2].st,
-                10 * (j & 1) + stage0, nullptr};
-      J.passes = (which == 1 || gb.prs[j / 2].q > it) ? 2 : 3;
-      jobs.push_back(J);
+      jobs.push_back(OrthJob{which == 0 ? S.Y : S.Z, S.lp, M, S.l, S.tmp, S.lt, S.gpart, S.W, S.R, S.lp,
+                             which == 0 ? S.Qt : S.Xt, which == 0 ? S.ldm : S.ldx, 1, gb.prs[j / 2].st,
+                             10 * (j & 1) + stage0, nullptr});
     }
     add_orth_jobs(jobs);
   };
@@ -2023,16 +2019,16 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
   if (!adaptive) {
     set_active(-1);
     if (!add_gemm(0, true, 0)) return fail(h, GSVD_RAND_ERR_ARG, "tensor map of a grouped product rejected");
-    add_orth(0, 1, 0);
+    add_orth(0, 1);
     int qmax = 0;
     for (auto* q : pv) qmax = std::max(qmax, q->q);
     for (int it = 0; it < qmax; ++it) {
       set_active(it);
       if (!add_gemm(1, false, 2)) return fail(h, GSVD_RAND_ERR_ARG, "tensor map of a grouped product rejected");
       add_reduce(false);
-      add_orth(1, 3, it);
+      add_orth(1, 3);
       if (!add_gemm(0, false, 1)) return fail(h, GSVD_RAND_ERR_ARG, "tensor map of a grouped product rejected");
-      add_orth(0, 5, it + 1);
+      add_orth(0, 5);
     }
   } else {
     // ---- Algorithm 1 per side, every block one step for the whole batch ----

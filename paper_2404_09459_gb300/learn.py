@@ -151,6 +151,18 @@ def predict(params, norm, X, bf16: bool = True, device: int = 0, ctx: Context | 
     return z[:, :MLP_KCLS].argmax(axis=1), z[:, MLP_KCLS:].argmax(axis=1)
 
 
+def constant_net(kb: int, q: int):
+    """Parameters and normalisation of a network that proposes bucket kb and q for every pair
+    (zero weights, biases that put more than 0.999 of each head's softmax mass there): the plain
+    fixed-rank method run through the learned pipeline (same probes, fixed-rank group, residual
+    sums and Algorithm 1 fallback), so that a comparison isolates what the trained network adds."""
+    th = np.zeros(MLP_PARAMS, np.float32)
+    b3 = MLP_PARAMS - (MLP_KCLS + MLP_QCLS)
+    th[b3 + int(kb)] = 12.0
+    th[b3 + MLP_KCLS + int(q)] = 12.0
+    return th, np.concatenate([np.zeros(MLP_IN), np.ones(MLP_IN)]).astype(np.float32)
+
+
 def save(path: str, params, norm):
     """The network file gsvd_rand_mlp_load reads."""
     p = np.asarray(params.cpu().numpy() if hasattr(params, "cpu") else params, np.float32)
