@@ -846,7 +846,7 @@ def main():
     gsv = None
     if rank == 0 and not args.no_error:
         from oracle import gsvd as O
-        got = [(out["alpha"].cpu().numpy(), out["beta"].cpu().numpy())]
+        got = [tuple(np.asarray(x.cpu() if hasattr(x, "cpu") else x) for x in (out["alpha"], out["beta"]))]
         h1, h2 = G1.double().cpu().numpy(), G2.double().cpu().numpy()
         ref = O.rand_gsvd(h1, h2, spec.kk, spec.oversample, spec.q, rspec.seed,
                           omega_round="bf16" if prec == "bf16" else None)

@@ -1103,7 +1103,10 @@ __device__ __forceinline__ float2 df_split(T v) {
     return make_float2(h, __double2float_rn(v - (double)h));
   }
 }
-template <typename TA, typename TB>
+// LOW: plain FP32 products of the operands' high parts (the Ogita-Aishima increment X F, whose
+// entries are of the size of the current error: FP32's relative 6e-8 of an increment of 1e-7 is
+// far below what the next step corrects).
+template <typename TA, typename TB, bool LOW>
 __global__ __launch_bounds__(DF_THREADS) void dfgemm_b_kernel(const DgemmB* __restrict__ tab) {
   const DgemmB& g = tab[blockIdx.z];
   const int i0 = blockIdx.x * DF_T, j0 = blockIdx.y * DF_T;
@@ -1152,12 +1155,19 @@ __global__ __launch_bounds__(DF_THREADS) void dfgemm_b_kernel(const DgemmB* __re
 #pragma unroll
         for (int m = 0; m < 4; ++m)
 #pragma unroll
-          for (int q = 0; q < 4; ++q) df_fma(av[m], bv[q], sh[m][q], sl[m][q]);
+          for (int q = 0; q < 4; ++q) {
+            if (LOW)
+              sh[m][q] = fmaf(av[m].x, bv[q].x, sh[m][q]);
+            else
+              df_fma(av[m], bv[q], sh[m][q], sl[m][q]);
+          }
       }
+      if (!LOW) {
 #pragma unroll
-      for (int m = 0; m < 4; ++m)
+        for (int m = 0; m < 4; ++m)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) df_renorm(sh[m][q], sl[m][q]);
+          for (int q = 0; q < 4; ++q) df_renorm(sh[m][q], sl[m][q]);
+      }
     }
     __syncthreads();
   }
@@ -1178,17 +1188,19 @@ __global__ __launch_bounds__(DF_THREADS) void dfgemm_b_kernel(const DgemmB* __re
 }
 
 template <typename TA, typename TB>
-cudaError_t launch_dgemm_b(const DgemmB* tab, int nprob, int max_Mr, int max_Nc, cudaStream_t st, bool df) {
+cudaError_t launch_dgemm_b(const DgemmB* tab, int nprob, int max_Mr, int max_Nc, cudaStream_t st, int df) {
   if (nprob <= 0) return cudaSuccess;
   const dim3 grid((unsigned)cdiv(max_Mr, SG_T), (unsigned)cdiv(max_Nc, SG_T), (unsigned)nprob);
-  if (df)
-    dfgemm_b_kernel<TA, TB><<<grid, DF_THREADS, 0, st>>>(tab);
+  if (df == 2)
+    dfgemm_b_kernel<TA, TB, true><<<grid, DF_THREADS, 0, st>>>(tab);
+  else if (df)
+    dfgemm_b_kernel<TA, TB, false><<<grid, DF_THREADS, 0, st>>>(tab);
   else
     dgemm_b_kernel<TA, TB, false><<<grid, 256, 0, st>>>(tab);
   return launched();
 }
-template cudaError_t launch_dgemm_b<float, float>(const DgemmB*, int, int, int, cudaStream_t, bool);
-template cudaError_t launch_dgemm_b<double, double>(const DgemmB*, int, int, int, cudaStream_t, bool);
+template cudaError_t launch_dgemm_b<float, float>(const DgemmB*, int, int, int, cudaStream_t, int);
+template cudaError_t launch_dgemm_b<double, double>(const DgemmB*, int, int, int, cudaStream_t, int);
 
 // Frobenius sums of A, R = I - X^T X and S - diag(lam) (part[0..2]) and lam, one CTA per problem.
 __global__ __launch_bounds__(256) void oa_norms_b_kernel(const OaB* __restrict__ tab) {
@@ -1291,7 +1303,8 @@ cudaError_t launch_oa_refine_b(const OaB* tab, const DgemmB* dg, int nprob, int 
   const dim3 g2((unsigned)cdiv((int64_t)max_N * max_N, 256), 1, (unsigned)nprob);
   oa_form_b_kernel<<<g2, 256, 0, st>>>(tab);
   if ((e = launched())) return e;
-  if ((e = launch_dgemm_b<double, double>(dg + 3ll * nprob, nprob, max_N, max_N, st, df))) return e;
+  // the increment X F: FP32 products on the mixed paths (its entries are of the error's size)
+  if ((e = launch_dgemm_b<double, double>(dg + 3ll * nprob, nprob, max_N, max_N, st, df ? 2 : 0))) return e;
   oa_update_b_kernel<<<g2, 256, 0, st>>>(tab);
   return launched();
 }

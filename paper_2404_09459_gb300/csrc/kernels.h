@@ -392,8 +392,9 @@ struct DgemmB {
   int Mr, Nc, K, ta, tb;
   int sym;  // the result is symmetric (Mr == Nc): upper tiles computed and mirrored
 };
+// df: 0 FP64, 1 double-float, 2 FP32 products of the high parts (the refinement's increment)
 template <typename TA, typename TB>
-cudaError_t launch_dgemm_b(const DgemmB* tab, int nprob, int max_Mr, int max_Nc, cudaStream_t st, bool df = false);
+cudaError_t launch_dgemm_b(const DgemmB* tab, int nprob, int max_Mr, int max_Nc, cudaStream_t st, int df = 0);
 
 // One Ogita-Aishima step per problem (as launch_oa_refine), and the cut cluster after it.
 struct OaB {
