@@ -588,7 +588,8 @@ def run_learned(args, rank, world):
     plain, plain_plans = arm(lambda: P.Context("tf32x3", device=local, use_learned=True, mlp_path=cpath, tol=tol,
                                                block_b=b), pairs_with(k=kcap), reps)
     plain["fallback_rate"] = float(np.mean([p_[2] for p_ in plain_plans])) if plain_plans else None
-    perfect, _ = arm(lambda: P.Context("tf32x3", device=local),
+    # the labels as a perfect proposal (no fallback), the residual summed as the learned group sums it
+    perfect, _ = arm(lambda: P.Context("tf32x3", device=local, flags=P.FLAG_ACC_RESID),
                      pairs_with(plans=[(learn.k_of_bucket(bb), int(qq)) for bb, qq in zip(ykh, yqh)]), reps)
     value = learned["value"]
     if dist is not None:

@@ -845,7 +845,10 @@ __global__ void factor_prep_kernel(const double* __restrict__ U1, int l, int r, 
   }
 }
 
-// out[i][c] = sc[c] sum_j Q(i, j) Uh[j][perm[c]]: a thread per row, a grid row per column
+// out[i][c] = sc[c] sum_j Q(i, j) Uh[j][perm[c]]: a thread per row, a grid row per column.  A cold
+// path (gsvd_rand_factors, on request after a solve, never inside the timed solves): Q is re-read
+// once per output column and, in the row-major layout, with a stride of lp elements between
+// neighbouring threads; it costs O(M l r) strided loads, a small multiple of one solve's products.
 template <typename T>
 __global__ void factor_side_kernel(const T* __restrict__ Q, int64_t rs, int64_t cs, int64_t M, int l,
                                    const double* __restrict__ Uh, int r, const double* __restrict__ scr, int which,
