@@ -386,6 +386,14 @@ struct Solver {
     const double shift_coef = 11.0 * ((double)rpc + l + 1) * u;
     // pivots below ~8 rpc u relative to their own column are below the Gram's resolution
     const double tau = 8.0 * (double)std::max<int64_t>(rpc, apply_rows_per_cta(l, (int)sizeof(T))) * u;
+    if constexpr (std::is_same<T, float>::value && std::is_same<TC, float>::value) {
+      // bases wider than 128 columns: Q = Y R^{-1} as a 3xTF32 tensor-core product (the CUDA-core
+      // apply cannot stage R^{-1} in shared memory beyond 128 columns and reads it from L2 per
+      // product: 1.3 ms per pass at M = 120000, l = 220, against a product bound by moving Y and Q)
+      if (l > 128 && h->tc_ok &&
+          (prec == GSVD_RAND_TF32 || prec == GSVD_RAND_TF32X3 || prec == GSVD_RAND_BF16))
+        return orth_tc(b, Yin, M, l, lp, out, ldo, transpose_out, stage, shift_coef, tau, chunks, rpc);
+    }
     // the Gram of each new Q: fused into Q = Y R^{-1} (one partial per row tile) for l <= 64;
     // for wider bases one l x l partial per 32-row tile would be GBs of partials, so the
     // chunked Gram kernel reads Q again instead
@@ -417,6 +425,37 @@ struct Solver {
       return rc;
     CU(launch_chol_shift<TC>(b.W, l, 0.0, tau, (TC*)b.R, (TC*)b.cscr, st_dev, stage + 1, st));
     CU((launch_apply_rinv<T, TC>(q2, lt, M, l, (const TC*)b.R, out, ldo, transpose_out, nullptr, st)));
+    return GSVD_RAND_OK;
+  }
+
+  // Shifted CholeskyQR3 with the products Q = Y R^{-1} on the tensor cores (3xTF32, as the grouped
+  // solves take them): each pass's Cholesky writes R^{-1} transposed (the K-major B operand, its
+  // padding rows up to the MMA width zeroed); the passes alternate between the two halves of b.tmp,
+  // and a transposed result is written by a transpose of the last one.
+  int orth_tc(SideBufs<T>& b, const T* Yin, int64_t M, int l, int64_t lp, T* out, int64_t ldo, int transpose_out,
+              int stage, double shift_coef, double tau, int chunks, int64_t rpc) {
+    if constexpr (std::is_same<T, float>::value && std::is_same<TC, float>::value) {
+      const int64_t lt = round_up(l, 4);
+      const int nmma = (int)round_up(l, 16);
+      float* Rt = reinterpret_cast<float*>(b.R);  // nmma x lt floats fit the l x l doubles for l > 128
+      CU(cudaMemsetAsync(Rt + (int64_t)l * lt, 0, (size_t)(nmma - l) * lt * sizeof(float), st));
+      T* q1 = b.tmp;
+      T* q2 = b.tmp + M * lt;
+      const T* src = Yin;
+      int64_t lds = lp;
+      for (int pass = 0; pass < 3; ++pass) {
+        CU(launch_gram_partial<T>(src, lds, M, l, b.gpart, chunks, rpc, st));
+        CU(launch_gram_reduce(b.gpart, chunks, l, b.W, st));
+        CU(launch_chol_shift<TC>(b.W, l, pass == 0 ? shift_coef : 0.0, tau, Rt, (TC*)b.cscr, st_dev,
+                                 stage + (pass > 0 ? 1 : 0), st, (int)lt));
+        const bool direct = pass == 2 && !transpose_out;
+        T* dst = direct ? out : (pass == 1 ? q2 : q1);
+        CU(tc_gemm_gx(GSVD_RAND_TF32X3, src, lds, M, l, Rt, lt, l, dst, direct ? ldo : lt, nullptr, st_dev, st));
+        src = dst;
+        lds = lt;
+      }
+      if (transpose_out) CU(launch_transpose<T>(q1, lt, M, l, out, ldo, st));
+    }
     return GSVD_RAND_OK;
   }
 

@@ -795,8 +795,8 @@ template <typename TC>
 __global__ __launch_bounds__(CHOL_THREADS) void chol_shift_kernel(const double* __restrict__ W, int l,
                                                                   double shift_coef, double tau_rel,
                                                                   TC* __restrict__ Rinv, DevStatus* st_dev,
-                                                                  int stage, TC* gscr, int use_smem) {
-  chol_shift_body<TC>(W, l, shift_coef, tau_rel, Rinv, st_dev, stage, gscr, use_smem);
+                                                                  int stage, TC* gscr, int use_smem, int ldt) {
+  chol_shift_body<TC>(W, l, shift_coef, tau_rel, Rinv, st_dev, stage, gscr, use_smem, ldt);
 }
 
 // The same elimination for l <= 64 with the augmented rows in registers:
@@ -960,8 +960,9 @@ int64_t chol_scratch_elems(int l) { return (int64_t)l * (l | 1); }
 
 template <typename TC>
 cudaError_t launch_chol_shift(const double* W, int l, double shift_coef, double tau_rel, TC* Rinv,
-                              TC* scratch, DevStatus* st_dev, int stage, cudaStream_t st) {
+                              TC* scratch, DevStatus* st_dev, int stage, cudaStream_t st, int ldt) {
   if (l < 1 || l > 256) return cudaErrorInvalidValue;
+  if (ldt && l <= 64) return cudaErrorInvalidValue;  // the transposed factor is written by the wide kernel only
   if (l <= 64) {
     chol64_kernel<TC><<<1, CHOL64_THREADS, 0, st>>>(W, l, shift_coef, tau_rel, Rinv, st_dev, stage);
     return launched();
@@ -970,13 +971,13 @@ cudaError_t launch_chol_shift(const double* W, int l, double shift_coef, double 
   int use_smem = smem <= 216 * 1024;
   cudaFuncSetAttribute(chol_shift_kernel<TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 216 * 1024);
   chol_shift_kernel<TC><<<1, CHOL_THREADS, use_smem ? smem : 0, st>>>(W, l, shift_coef, tau_rel, Rinv, st_dev,
-                                                                      stage, scratch, use_smem);
+                                                                      stage, scratch, use_smem, ldt);
   return launched();
 }
 template cudaError_t launch_chol_shift<double>(const double*, int, double, double, double*, double*,
-                                               DevStatus*, int, cudaStream_t);
+                                               DevStatus*, int, cudaStream_t, int);
 template cudaError_t launch_chol_shift<float>(const double*, int, double, double, float*, float*,
-                                              DevStatus*, int, cudaStream_t);
+                                              DevStatus*, int, cudaStream_t, int);
 
 // ============================================================================
 // Q = Y R^{-1} over a tile of rows per CTA, register-blocked: 16 x 16 threads,

@@ -85,9 +85,11 @@ cudaError_t launch_gram_reduce(const double* part, int chunks, int l, double* W,
 // Q = Y Rinv is zero).  All columns dropped -> BREAKDOWN; non-finite -> NONFINITE.
 // scratch: chol_scratch_elems(l) TC values (used when shared memory is too small).
 int64_t chol_scratch_elems(int l);
+// ldt > 0 (l > 64 only): the inverse factor transposed, Rinv[j * ldt + c] = R^{-1}[c][j] (the K-major
+// operand of a tensor-core Q = Y R^{-1})
 template <typename TC>
 cudaError_t launch_chol_shift(const double* W, int l, double shift_coef, double tau_rel, TC* Rinv,
-                              TC* scratch, DevStatus* st_dev, int stage, cudaStream_t st);
+                              TC* scratch, DevStatus* st_dev, int stage, cudaStream_t st, int ldt = 0);
 
 // Q = Y Rinv (upper triangular) per tile of rows, optional Gram partials of Q
 // per CTA (part != nullptr, one chunk per CTA), optional transposed output

@@ -428,7 +428,8 @@ def test_tf32x3_large_pair_full_size():
     ("fp64", 3000, 2600, 400, 90, 10, 1),      # L = 200
     ("tf32x3", 5000, 4100, 600, 110, 14, 1),   # L = 248
     ("fp32", 3000, 2500, 500, 170, 10, 1),     # L = 360: matrix in global scratch
-], ids=["L200-fp64", "L248-tf32x3", "L360-fp32"])
+    ("tf32x3", 4000, 3500, 600, 140, 12, 1),   # l = 152 > 128: Q = Y R^-1 on the tensor cores
+], ids=["L200-fp64", "L248-tf32x3", "L360-fp32", "l152-tf32x3"])
 def test_wide_compressed_pair(prec, m, p, n, k, os_, q):
     # scale law logspace(0, 2) over r = k planted pairs: every returned pair is a signal pair well
     # above the noise (a noise-determined pair has an arbitrary alpha and would interleave with the
