@@ -1603,6 +1603,7 @@ struct GSide {
   float *Xt, *Y, *Qt, *tmp, *Z, *part;
   double *gpart, *W, *gnorm, *bnorm;
   float* R;  // R^{-1} transposed (lx x lp, padding rows zero): the K-major operand of Q = Y R^{-1}
+  float* Xtlo = nullptr;  // Xt - tf32(Xt) for the fixed-rank sketches (lx x ldx)
   int splits;
   int64_t rps;
   int gchunks;
@@ -1738,6 +1739,7 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
       S.gpart = bp.take<double>((int64_t)S.gchunks * P.l * P.l);
       S.W = bp.take<double>((int64_t)P.l * P.l);
       S.R = bp.take<float>((int64_t)S.lx * S.lp);
+      S.Xtlo = bp.take<float>((int64_t)S.lx * S.ldx);
       S.gnorm = bp.take<double>(tc_group_norm_parts() * cdiv(S.M, 128));
       S.bnorm = bp.take<double>(cdiv(S.n * P.l, 256));
       if (acc_resid && !adaptive) {  // the slab energies of ||B||_F^2
@@ -1798,7 +1800,7 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
       const GSide& S = gb.sides[j];
       const gsvd_rand_pair& q = *pv[j / 2];
       t[j] = GaussB{S.Xt, S.ldx, S.n, S.l, S.lx, q.seed, q.pair, (uint32_t)(j & 1),
-                    probe ? GSVD_RAND_STREAM_PROBE : GSVD_RAND_STREAM_FIXED, 0};
+                    probe ? GSVD_RAND_STREAM_PROBE : GSVD_RAND_STREAM_FIXED, 0, S.Xtlo};
       mldx = std::max(mldx, S.ldx);
       mlr = std::max(mlr, S.lx);
     }
@@ -1861,6 +1863,7 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
       x.ldo = S.lp;
       if (mode == 0) {
         x.Bt = S.Xt;
+        x.Bt_lo = S.Xtlo;  // written with Xt (the Gaussian, then each power step's basis)
         x.ldb = S.ldx;
         x.out = S.Y;
         x.gnorm_part = norm ? S.gnorm : nullptr;
@@ -2066,6 +2069,22 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
       if (!add_gemm(1, false, 2)) return fail(h, GSVD_RAND_ERR_ARG, "tensor map of a grouped product rejected");
       add_reduce(false);
       add_orth(1, 3);
+      {  // the low half of each new basis X^T, the B operand of the next sketch (timed with the
+         // re-orthonormalisation that produced the basis: the sketch stage holds the products alone)
+        cur_tag = GSVD_RAND_STAGE_ORTH;
+        std::vector<LoHalfB> t;
+        int64_t mx = 0;
+        for (int j : act) {
+          const GSide& S = gb.sides[j];
+          t.push_back(LoHalfB{S.Xt, S.Xtlo, (int64_t)S.lx, S.ldx, S.ldx, nullptr});
+          mx = std::max(mx, (int64_t)S.lx * S.ldx);
+        }
+        const size_t off = A.add(t);
+        const int cnt = (int)t.size();
+        push([off, cnt, mx](const unsigned char* d, cudaStream_t st) {
+          return launch_low_half_b(reinterpret_cast<const LoHalfB*>(d + off), cnt, mx, st);
+        });
+      }
       if (!add_gemm(0, false, 1)) return fail(h, GSVD_RAND_ERR_ARG, "tensor map of a grouped product rejected");
       add_orth(0, 5);
     }

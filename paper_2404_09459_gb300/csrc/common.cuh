@@ -101,6 +101,12 @@ __device__ __forceinline__ bool finite_val(T v) {
 }
 
 __host__ __device__ __forceinline__ int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// x - tf32(x) with tf32(x) the truncation the tensor core applies to an FP32 operand of a
+// kind::tf32 MMA (the low 13 mantissa bits cleared): exact, the low half of a 3xTF32 operand.
+__device__ __forceinline__ float tf32_low_half(float x) {
+  return x - __uint_as_float(__float_as_uint(x) & 0xffffe000u);
+}
 __host__ __device__ __forceinline__ int64_t round_up(int64_t a, int64_t b) { return cdiv(a, b) * b; }
 
 }  // namespace gsvdr

@@ -1149,6 +1149,22 @@ __global__ void gaussian_kmajor_b_kernel(const GaussB* __restrict__ tab) {
     v = gaussian_at<float>(i * (int64_t)a.l + j, (uint32_t)a.seed, (uint32_t)(a.seed >> 32), a.pair, a.side,
                            a.stream);
   a.Xt[(int64_t)j * a.ldx + i] = v;
+  if (a.lo) a.lo[(int64_t)j * a.ldx + i] = tf32_low_half(v);
+}
+
+__global__ void low_half_b_kernel(const LoHalfB* __restrict__ tab) {
+  const LoHalfB& a = tab[blockIdx.y];
+  if (a.stop && *a.stop) return;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.rows * a.cols) return;
+  const int64_t r = e / a.cols, c = e - r * a.cols;
+  a.dst[r * a.ld + c] = tf32_low_half(a.src[r * a.ld + c]);
+}
+
+cudaError_t launch_low_half_b(const LoHalfB* tab, int nprob, int64_t max_elems, cudaStream_t st) {
+  if (nprob <= 0 || max_elems <= 0) return cudaSuccess;
+  low_half_b_kernel<<<dim3((unsigned)cdiv(max_elems, 256), (unsigned)nprob), 256, 0, st>>>(tab);
+  return launched();
 }
 
 cudaError_t launch_gaussian_kmajor_b(const GaussB* tab, int nprob, int64_t max_ldx, int max_lrows, cudaStream_t st) {

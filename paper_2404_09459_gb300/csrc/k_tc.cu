@@ -31,11 +31,13 @@ namespace gsvdr {
 struct TcGroupProb {  // CUtensorMap members carry their own (>= 64-byte) alignment
   CUtensorMap mapA;   // G: row tiles (GX) or unswizzled 32 x 32 boxes (GTQ)
   CUtensorMap mapB;   // K-major B operand: X^T (GX) or Q^T (GTQ)
+  CUtensorMap mapBlo; // GX, 3xTF32, has_blo: B - tf32(B), the same geometry as mapB
   float* out;         // Y (GX) or the split partials (GTQ)
   int64_t ldo, out_rows, kdim, rows_per_split, split_stride;
   double* gnorm_part; // GX with the fused norm: 4 partial sums of G^2 per row tile
   int ncols, nmma, tiles_x, transpose_out;  // transpose_out: out[c * ldo + row] (GX)
   const int* stop;    // null, or the stop word of the problem (non-zero: its tiles are filtered out)
+  int has_blo, pad_;
 };
 
 namespace {
@@ -193,6 +195,14 @@ struct SqAccF {
     float t = hi + p;
     float z = t - hi;
     lo += ((hi - (t - z)) + (p - z)) + e;
+    hi = t;
+  }
+  // a short partial sum (of at most 16 squares, summed with plain FMAs: relative error a few
+  // units of FP32 rounding, of either sign) added with the same compensation
+  __device__ __forceinline__ void add_sum(float p) {
+    float t = hi + p;
+    float z = t - hi;
+    lo += (hi - (t - z)) + (p - z);
     hi = t;
   }
 };
@@ -910,7 +920,8 @@ __global__ __launch_bounds__(TG_THREADS, 2) void tc_group_kernel(const TcGroupPr
           if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) break;
           ++issued;
           uint8_t* st = base + (size_t)s * L.bytes;
-          mbar_expect_tx(&full[s], (uint32_t)TC_A_BYTES + b_bytes);
+          const bool blo = SPLIT && MODE == 0 && P.has_blo;
+          mbar_expect_tx(&full[s], (uint32_t)TC_A_BYTES + b_bytes * (blo ? 2u : 1u));
           const int k0 = (int)(kb + (int64_t)kt * BKE);
           if (MODE == 0) {
             tma_load_2d(st + L.a, &P.mapA, &full[s], k0, t0);
@@ -919,6 +930,7 @@ __global__ __launch_bounds__(TG_THREADS, 2) void tc_group_kernel(const TcGroupPr
             for (int q = 0; q < 128 / BKE; ++q) tma_load_2d(st + L.a + q * (BKE * 128), &P.mapA, &full[s], t0 + BKE * q, k0);
           }
           tma_load_2d(st + L.b, &P.mapB, &full[s], k0, 0);
+          if (blo) tma_load_2d(st + L.blo, &P.mapBlo, &full[s], k0, 0);
         }
       }
       if (*abort_flag) {
@@ -1033,21 +1045,26 @@ __global__ __launch_bounds__(TG_THREADS, 2) void tc_group_kernel(const TcGroupPr
 #pragma unroll
               for (int k = 0; k < 16; ++k) v[k] = stg[(16 * half + k) * 32];
             }
+            if (NORM) {  // the 16 squares of this thread's row slice, then one compensated add
+              float s16 = 0.f;
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-              if (NORM) sq.add(v[k]);
-              lo[k] = tf32_lo(v[k]);
+              for (int k = 0; k < 16; ++k) s16 = fmaf(v[k], v[k], s16);
+              sq.add_sum(s16);
             }
+#pragma unroll
+            for (int k = 0; k < 16; ++k) lo[k] = tf32_lo(v[k]);
             const uint32_t ta =
                 tmem + ((uint32_t)(32 * sub) << 16) + (uint32_t)(ta_col0 + TG_TA_STAGE_COLS * s + 16 * half);
             tmem_st16(ta, v);
             tmem_st16(ta + 32u, lo);
-            // B_lo in shared memory
-            const float4* b4 = reinterpret_cast<const float4*>(st + L.b);
-            float4* blo4 = reinterpret_cast<float4*>(st + L.blo);
-            for (int i = et; i < (int)(b_bytes / 16); i += PT) {
-              float4 x = b4[i];
-              blo4[i] = make_float4(tf32_lo(x.x), tf32_lo(x.y), tf32_lo(x.z), tf32_lo(x.w));
+            // B_lo in shared memory (unless the TMA brought it with B)
+            if (!(MODE == 0 && P.has_blo)) {
+              const float4* b4 = reinterpret_cast<const float4*>(st + L.b);
+              float4* blo4 = reinterpret_cast<float4*>(st + L.blo);
+              for (int i = et; i < (int)(b_bytes / 16); i += PT) {
+                float4 x = b4[i];
+                blo4[i] = make_float4(tf32_lo(x.x), tf32_lo(x.y), tf32_lo(x.z), tf32_lo(x.w));
+              }
             }
             tmem_wait_st();
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -1070,10 +1087,7 @@ __global__ __launch_bounds__(TG_THREADS, 2) void tc_group_kernel(const TcGroupPr
             const float4* a4 = reinterpret_cast<const float4*>(st + L.a);
             for (int i = et; i < TC_A_BYTES / 16; i += PT) {
               float4 x = a4[i];
-              sq.add(x.x);
-              sq.add(x.y);
-              sq.add(x.z);
-              sq.add(x.w);
+              sq.add_sum(fmaf(x.w, x.w, fmaf(x.z, x.z, fmaf(x.y, x.y, x.x * x.x))));
             }
           }
           __syncwarp();
@@ -1194,6 +1208,10 @@ bool tc_group_build(int mode, const TcGroupSpec* specs, int nprob, void* host, i
     if (mode == 0) {
       if (!make_map(&p.mapA, s.G, (uint64_t)s.n, (uint64_t)s.M, (uint64_t)s.ldg, TC_BM)) return false;
       if (!make_map(&p.mapB, s.Bt, (uint64_t)s.n, (uint64_t)nmma, (uint64_t)s.ldb, (uint32_t)nmma)) return false;
+      if (s.Bt_lo) {
+        if (!make_map(&p.mapBlo, s.Bt_lo, (uint64_t)s.n, (uint64_t)nmma, (uint64_t)s.ldb, (uint32_t)nmma)) return false;
+        p.has_blo = 1;
+      }
       p.out_rows = s.M;
       p.kdim = s.n;
       p.tiles_x = (int)cdiv(s.M, TC_BM);

@@ -264,6 +264,7 @@ struct GaussB {  // Omega^T of one side, K-major FP32 (as launch_gaussian_kmajor
   int l, lrows;
   uint64_t seed;
   uint32_t pair, side, stream, pad;
+  float* lo;  // null, or Xt - tf32(Xt) in the same layout (the low half of a 3xTF32 B operand)
 };
 cudaError_t launch_gaussian_kmajor_b(const GaussB* tab, int nprob, int64_t max_ldx, int max_lrows, cudaStream_t st);
 
@@ -304,6 +305,14 @@ struct CholB {  // shifted Cholesky with the inverse factor (FP32 factor), as la
   int l, stage, ldt, pad;
   const int* stop;  // null, or a stop word: the entry is skipped once it is non-zero
 };
+// dst = src - tf32(src) over rows x cols (row strides lds, ldd), one entry per problem.
+struct LoHalfB {
+  const float* src;
+  float* dst;
+  int64_t rows, cols, ld;
+  const int* stop;
+};
+cudaError_t launch_low_half_b(const LoHalfB* tab, int nprob, int64_t max_elems, cudaStream_t st);
 
 // max_l <= 64: the register-resident elimination; <= 128: the shared-memory one.
 cudaError_t launch_chol_b(const CholB* tab, int nprob, int max_l, cudaStream_t st);

@@ -62,6 +62,9 @@ struct TcGroupSpec {
   double* gnorm_part;
   int transpose_out;
   const int* stop;  // null, or the problem's stop word: its tiles are left out once it is non-zero
+  // mode 0, 3xTF32: null, or Bt - tf32(Bt) in Bt's layout, loaded by TMA beside Bt (the preparation
+  // warps then form only A's low half)
+  const float* Bt_lo;
 };
 int tc_group_norm_parts();
 // Tiles of a grouped launch (128-row tiles in mode 0; column tiles x splits in mode 1).
