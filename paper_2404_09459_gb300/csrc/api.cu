@@ -1620,6 +1620,7 @@ struct GPair {
   int64_t n, ldn;
   float* S;
   double *K, *X, *lam, *Zr, *C1, *Wv, *mu, *U1, *XtX, *P, *S2, *F, *opart;
+  float2 *Adf, *Xdf, *Pdf, *Fdf;  // (hi, lo) copies of the refinement's operands (L x L, reused at N = k)
   int* order;
   float* jscr;
   DevStatus* st;
@@ -1770,6 +1771,10 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
     P.P = bp.take<double>((int64_t)L * L);
     P.S2 = bp.take<double>((int64_t)L * L);
     P.F = bp.take<double>((int64_t)L * L);
+    P.Adf = bp.take<float2>((int64_t)L * L);
+    P.Xdf = bp.take<float2>((int64_t)L * L);
+    P.Pdf = bp.take<float2>((int64_t)L * L);
+    P.Fdf = bp.take<float2>((int64_t)L * L);
     P.opart = bp.take<double>(4);
     P.jscr = bp.take<float>(eig_scratch_floats(L));
   }
@@ -2374,6 +2379,10 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
       const int N = c1 ? P.k : P.L;
       t[i] = OaB{c1 ? P.C1 : P.K, c1 ? P.Wv : P.X, c1 ? P.mu : P.lam, P.XtX, P.P, P.S2, P.F, P.opart, N, P.k,
                  c1 ? nullptr : P.jscr};
+      t[i].Adf = P.Adf;  // the double-float products read (hi, lo) copies of their operands
+      t[i].Xdf = P.Xdf;
+      t[i].Pdf = P.Pdf;
+      t[i].Fdf = P.Fdf;
       mN = std::max(mN, N);
     }
     std::vector<DgemmB> dg(4 * (size_t)np);

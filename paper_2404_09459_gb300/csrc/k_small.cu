@@ -1101,10 +1101,19 @@ template <typename T>
 __device__ __forceinline__ float2 df_split(T v) {
   if constexpr (std::is_same<T, float>::value) {
     return make_float2(v, 0.f);
+  } else if constexpr (std::is_same<T, float2>::value) {
+    return v;  // already a (hi, lo) pair
   } else {
     const float h = __double2float_rn(v);
     return make_float2(h, __double2float_rn(v - (double)h));
   }
+}
+template <typename T>
+__device__ __forceinline__ T df_zero() {
+  if constexpr (std::is_same<T, float2>::value)
+    return make_float2(0.f, 0.f);
+  else
+    return T(0);
 }
 // LOW: plain FP32 products of the operands' high parts (the Ogita-Aishima increment X F, whose
 // entries are of the size of the current error: FP32's relative 6e-8 of an increment of 1e-7 is
@@ -1134,13 +1143,13 @@ __global__ __launch_bounds__(DF_THREADS) void dfgemm_b_kernel(const DgemmB* __re
       if (!ta) { i = a; kk = b; } else { kk = a; i = b; }
       int gi = i0 + i, gk = k0 + kk;
       As[kk][i] = df_split((gi < g.Mr && gk < K) ? (ta ? A[(int64_t)gk * g.lda + gi] : A[(int64_t)gi * g.lda + gk])
-                                                : TA(0));
+                                                : df_zero<TA>());
       int j;
       if (!tb) { kk = a; j = b; } else { j = a; kk = b; }
       const int gj = j0 + j;
       gk = k0 + kk;
       Bs[kk][j] = df_split((gj < g.Nc && gk < K) ? (tb ? B[(int64_t)gj * g.ldb + gk] : B[(int64_t)gk * g.ldb + gj])
-                                                : TB(0));
+                                                : df_zero<TB>());
     }
     __syncthreads();
     if (active) {
@@ -1204,6 +1213,20 @@ cudaError_t launch_dgemm_b(const DgemmB* tab, int nprob, int max_Mr, int max_Nc,
 }
 template cudaError_t launch_dgemm_b<float, float>(const DgemmB*, int, int, int, cudaStream_t, int);
 template cudaError_t launch_dgemm_b<double, double>(const DgemmB*, int, int, int, cudaStream_t, int);
+
+// The refinement's operands as (hi, lo) FP32 pairs, converted once per product instead of in
+// every tile that loads them (FP64 conversions run at the FP64 rate: each N x N operand is loaded
+// by N / 32 tiles).  which: 0 A, 1 X, 2 P, 3 F.
+__global__ void oa_to_df_b_kernel(const OaB* __restrict__ tab, int which) {
+  const OaB& o = tab[blockIdx.y];
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)o.N * o.N) return;
+  const double* src = which == 0 ? o.A : which == 1 ? o.X : which == 2 ? o.P : o.F;
+  float2* dst = which == 0 ? o.Adf : which == 1 ? o.Xdf : which == 2 ? o.Pdf : o.Fdf;
+  const double v = src[e];
+  const float h = __double2float_rn(v);
+  dst[e] = make_float2(h, __double2float_rn(v - (double)h));
+}
 
 // Frobenius sums of A, R = I - X^T X and S - diag(lam) (part[0..2]) and lam, one CTA per problem.
 __global__ __launch_bounds__(256) void oa_norms_b_kernel(const OaB* __restrict__ tab) {
@@ -1273,7 +1296,7 @@ void oa_b_tables(const OaB* h, int nprob, DgemmB* dg) {
   for (int i = 0; i < nprob; ++i) {
     const OaB& o = h[i];
     const int N = o.N;
-    auto mk = [&](const double* A, int ta, const double* B, int tb, double* C) {
+    auto mk = [&](const void* A, int ta, const void* B, int tb, double* C) {
       DgemmB g;
       memset(&g, 0, sizeof(g));
       g.A = A;
@@ -1287,27 +1310,55 @@ void oa_b_tables(const OaB* h, int nprob, DgemmB* dg) {
       g.tb = tb;
       return g;
     };
-    dg[i] = mk(o.X, 1, o.X, 0, o.XtX);               // X^T X (symmetric)
+    // double-float form (o.Xdf set): the operands are the (hi, lo) pair copies
+    const bool d2 = o.Xdf != nullptr;
+    const void* X = d2 ? (const void*)o.Xdf : (const void*)o.X;
+    dg[i] = mk(X, 1, X, 0, o.XtX);                   // X^T X (symmetric)
     dg[i].sym = 1;
-    dg[nprob + i] = mk(o.A, 0, o.X, 0, o.P);         // A X
-    dg[2 * nprob + i] = mk(o.X, 1, o.P, 0, o.S);     // X^T (A X) (symmetric: A is)
+    dg[nprob + i] = mk(d2 ? (const void*)o.Adf : (const void*)o.A, 0, X, 0, o.P);  // A X
+    dg[2 * nprob + i] = mk(X, 1, d2 ? (const void*)o.Pdf : (const void*)o.P, 0, o.S);  // X^T (A X) (symmetric: A is)
     dg[2 * nprob + i].sym = 1;
-    dg[3 * nprob + i] = mk(o.X, 0, o.F, 0, o.P);     // X F
+    dg[3 * nprob + i] = mk(X, 0, d2 ? (const void*)o.Fdf : (const void*)o.F, 0, o.P);  // X F
   }
 }
 
 cudaError_t launch_oa_refine_b(const OaB* tab, const DgemmB* dg, int nprob, int max_N, cudaStream_t st, bool df) {
   if (nprob <= 0) return cudaSuccess;
   cudaError_t e;
-  for (int k = 0; k < 3; ++k)
-    if ((e = launch_dgemm_b<double, double>(dg + (int64_t)k * nprob, nprob, max_N, max_N, st, df))) return e;
+  const dim3 g2((unsigned)cdiv((int64_t)max_N * max_N, 256), 1, (unsigned)nprob);
+  const dim3 gc((unsigned)cdiv((int64_t)max_N * max_N, 256), (unsigned)nprob);
+  const dim3 gd((unsigned)cdiv(max_N, SG_T), (unsigned)cdiv(max_N, SG_T), (unsigned)nprob);
+  if (df) {
+    // operands converted once to (hi, lo) pairs (oa_b_tables points the products at them)
+    for (int w = 0; w < 2; ++w) {
+      oa_to_df_b_kernel<<<gc, 256, 0, st>>>(tab, w);
+      if ((e = launched())) return e;
+    }
+    for (int k = 0; k < 2; ++k) {
+      dfgemm_b_kernel<float2, float2, false><<<gd, DF_THREADS, 0, st>>>(dg + (int64_t)k * nprob);
+      if ((e = launched())) return e;
+    }
+    oa_to_df_b_kernel<<<gc, 256, 0, st>>>(tab, 2);
+    if ((e = launched())) return e;
+    dfgemm_b_kernel<float2, float2, false><<<gd, DF_THREADS, 0, st>>>(dg + 2ll * nprob);
+    if ((e = launched())) return e;
+  } else {
+    for (int k = 0; k < 3; ++k)
+      if ((e = launch_dgemm_b<double, double>(dg + (int64_t)k * nprob, nprob, max_N, max_N, st, 0))) return e;
+  }
   oa_norms_b_kernel<<<nprob, 256, 0, st>>>(tab);
   if ((e = launched())) return e;
-  const dim3 g2((unsigned)cdiv((int64_t)max_N * max_N, 256), 1, (unsigned)nprob);
   oa_form_b_kernel<<<g2, 256, 0, st>>>(tab);
   if ((e = launched())) return e;
   // the increment X F: FP32 products on the mixed paths (its entries are of the error's size)
-  if ((e = launch_dgemm_b<double, double>(dg + 3ll * nprob, nprob, max_N, max_N, st, df ? 2 : 0))) return e;
+  if (df) {
+    oa_to_df_b_kernel<<<gc, 256, 0, st>>>(tab, 3);
+    if ((e = launched())) return e;
+    dfgemm_b_kernel<float2, float2, true><<<gd, DF_THREADS, 0, st>>>(dg + 3ll * nprob);
+    if ((e = launched())) return e;
+  } else if ((e = launch_dgemm_b<double, double>(dg + 3ll * nprob, nprob, max_N, max_N, st, 0))) {
+    return e;
+  }
   oa_update_b_kernel<<<g2, 256, 0, st>>>(tab);
   return launched();
 }

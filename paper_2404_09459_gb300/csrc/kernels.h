@@ -419,6 +419,9 @@ struct OaB {
   double* part;  // 3 sums
   int N, r;
   float* jscr;   // FP32 eigensolver scratch for a large cut cluster (eig_scratch_floats(N)), or null
+  // double-float refinement (launch_oa_refine_b with df): N x N (hi, lo) copies of A, X, P and F
+  // that the products read; null for the FP64 form
+  float2 *Adf = nullptr, *Xdf = nullptr, *Pdf = nullptr, *Fdf = nullptr;
 };
 // The four products of a step use `dg` (4 * nprob DgemmB entries, filled by oa_b_tables).
 void oa_b_tables(const OaB* hostOa, int nprob, DgemmB* dg);
