@@ -86,7 +86,8 @@ def sketch_traffic(prec, workload):
     does not cover this workload/precision or the kernel source changed since it was taken."""
     import hashlib
     files = {("tf32_large", "tf32x3"): "sketch_traffic_tf32x3_large_pair.json",
-             ("bf16_stress", "bf16"): "sketch_traffic_bf16_stress_pair.json"}
+             ("bf16_stress", "bf16"): "sketch_traffic_bf16_stress_pair.json",
+             ("batched", "tf32x3"): "sketch_traffic_grouped_batch.json"}
     if (workload, prec) not in files:
         return None
     try:
