@@ -74,8 +74,10 @@ struct gsvd_rand_ctx {
   double* fact_scr = nullptr;  // device scratch of gsvd_rand_factors (4 x 512 doubles)
   char* gstage = nullptr;      // device copies of a grouped solve's host inputs
   size_t gstage_bytes = 0;
-  char* gbounce = nullptr;     // contiguous landing area of one host matrix before its rows are padded
-  size_t gbounce_bytes = 0;
+  char* gbounce = nullptr;     // two contiguous landing areas of host matrices before their rows are padded
+  size_t gbounce_bytes = 0;    // (of each of the two)
+  cudaStream_t gstage_st = nullptr;            // re-pitch stream of the staging (owned)
+  cudaEvent_t gstage_ev[4] = {nullptr, nullptr, nullptr, nullptr};  // landed / re-pitched, per buffer
   // complex pairs: the realified matrices, staged host inputs and the doubled GSVs
   char* cplx = nullptr;
   size_t cplx_bytes = 0;
@@ -3013,7 +3015,13 @@ int solve_grouped_staged(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs) {
   if (need == 0) return solve_grouped(h, npairs, pairs);
   if (need > h->gstage_bytes) {
     // nothing of an earlier call is in flight: every grouped solve synchronises before it returns
-    if (h->gstage) cudaFree(h->gstage);
+    if (h->gstage_st) {
+    cudaStreamSynchronize(h->gstage_st);
+    cudaStreamDestroy(h->gstage_st);
+    for (auto e : h->gstage_ev)
+      if (e) cudaEventDestroy(e);
+  }
+  if (h->gstage) cudaFree(h->gstage);
     h->gstage = nullptr;
     h->gstage_bytes = 0;
     if (cudaMalloc(&h->gstage, need) != cudaSuccess) {
@@ -3027,18 +3035,33 @@ int solve_grouped_staged(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs) {
     for (int s = 0; s < 2; ++s)
       if ((host[i] & (1 << s)) && pairs[i].n % 4)
         bounce = std::max(bounce, (size_t)(s ? pairs[i].p : pairs[i].m) * pairs[i].n * sizeof(float));
+  bounce = (bounce + 255) & ~size_t(255);
   if (bounce > h->gbounce_bytes) {
     CU(cudaStreamSynchronize(h->stream));
+    if (h->gstage_st) CU(cudaStreamSynchronize(h->gstage_st));
     if (h->gbounce) cudaFree(h->gbounce);
     h->gbounce = nullptr;
     h->gbounce_bytes = 0;
-    if (cudaMalloc(&h->gbounce, bounce) != cudaSuccess) {
+    if (cudaMalloc(&h->gbounce, 2 * bounce) != cudaSuccess) {
       cudaGetLastError();
-      return fail(h, GSVD_RAND_ERR_OOM, "bounce buffer of the grouped solve's host inputs (%zu bytes) failed",
+      return fail(h, GSVD_RAND_ERR_OOM, "bounce buffers of the grouped solve's host inputs (2 x %zu bytes) failed",
                   bounce);
     }
     h->gbounce_bytes = bounce;
   }
+  if (!h->gstage_st) {
+    CU(cudaStreamCreateWithFlags(&h->gstage_st, cudaStreamNonBlocking));
+    for (auto& e : h->gstage_ev) CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  // The host matrices land on h's stream at the link's rate; a matrix with unaligned rows lands
+  // contiguously in one of two bounce buffers and is re-pitched by a kernel on the staging stream
+  // while the next one lands in the other buffer.
+  cudaStream_t rs = h->gstage_st;
+  cudaEvent_t* landed = h->gstage_ev;      // [b]: buffer b's matrix has landed
+  cudaEvent_t* repitched = h->gstage_ev + 2;  // [b]: buffer b's matrix has been re-pitched (buffer free)
+  CU(cudaEventRecord(repitched[0], h->stream));  // both buffers free, in order after earlier work
+  CU(cudaEventRecord(repitched[1], h->stream));
+  int nb = 0;  // matrices through the bounce buffers so far
   std::vector<gsvd_rand_pair> sp(pairs, pairs + npairs);
   size_t off = 0;
   for (int i = 0; i < npairs; ++i) {
@@ -3053,10 +3076,14 @@ int solve_grouped_staged(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs) {
       if (ldn == q.n) {
         CU(copy_rows(dst, row, src, (size_t)ld * sizeof(float), row, (size_t)M, cudaMemcpyHostToDevice, h->stream));
       } else {
-        CU(copy_rows(h->gbounce, row, src, (size_t)ld * sizeof(float), row, (size_t)M, cudaMemcpyHostToDevice,
-                     h->stream));
-        CU(cudaMemcpy2DAsync(dst, (size_t)ldn * sizeof(float), h->gbounce, row, row, (size_t)M,
-                             cudaMemcpyDeviceToDevice, h->stream));
+        const int b = nb++ & 1;
+        char* bb = h->gbounce + (size_t)b * h->gbounce_bytes;
+        CU(cudaStreamWaitEvent(h->stream, repitched[b], 0));
+        CU(copy_rows(bb, row, src, (size_t)ld * sizeof(float), row, (size_t)M, cudaMemcpyHostToDevice, h->stream));
+        CU(cudaEventRecord(landed[b], h->stream));
+        CU(cudaStreamWaitEvent(rs, landed[b], 0));
+        CU(launch_repitch(reinterpret_cast<const float*>(bb), M, q.n, reinterpret_cast<float*>(dst), ldn, rs));
+        CU(cudaEventRecord(repitched[b], rs));
       }
       if (s) {
         q.G2 = dst;
@@ -3068,6 +3095,9 @@ int solve_grouped_staged(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs) {
       off += ((size_t)M * ldn * sizeof(float) + 255) & ~size_t(255);
     }
   }
+  // the grouped solve (ordered after h's stream) waits for the last re-pitches
+  CU(cudaStreamWaitEvent(h->stream, repitched[0], 0));
+  CU(cudaStreamWaitEvent(h->stream, repitched[1], 0));
   const int rc = solve_grouped(h, npairs, sp.data());
   for (int i = 0; i < npairs; ++i) pairs[i].status = sp[i].status;
   return rc;

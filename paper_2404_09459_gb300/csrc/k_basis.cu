@@ -1167,6 +1167,24 @@ cudaError_t launch_low_half_b(const LoHalfB* tab, int nprob, int64_t max_elems, 
   return launched();
 }
 
+// dst (rows x n, row stride ldd) = src (rows x n, contiguous): the re-pitch of a host matrix landed
+// in one contiguous copy (a thread per element, reads and writes coalesced along the rows).
+__global__ void repitch_kernel(const float* __restrict__ src, int64_t rows, int64_t n, float* __restrict__ dst,
+                               int64_t ldd) {
+  const int64_t total = rows * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / n, c = e - r * n;
+    dst[r * ldd + c] = src[e];
+  }
+}
+
+cudaError_t launch_repitch(const float* src, int64_t rows, int64_t n, float* dst, int64_t ldd, cudaStream_t st) {
+  if (rows < 1 || n < 1) return cudaSuccess;
+  const int64_t blocks = std::min<int64_t>(cdiv(rows * n, 256), 152 * 16);
+  repitch_kernel<<<(unsigned)blocks, 256, 0, st>>>(src, rows, n, dst, ldd);
+  return launched();
+}
+
 cudaError_t launch_gaussian_kmajor_b(const GaussB* tab, int nprob, int64_t max_ldx, int max_lrows, cudaStream_t st) {
   if (nprob <= 0) return cudaSuccess;
   gaussian_kmajor_b_kernel<<<dim3((unsigned)cdiv(max_ldx, 256), (unsigned)max_lrows, (unsigned)nprob), 256, 0, st>>>(tab);

@@ -27,6 +27,8 @@ cudaError_t launch_gaussian_kmajor_cplx(T* Xt, int64_t ldx, int64_t n2, int l2, 
 template <typename T>
 cudaError_t launch_realify(const T* G, int64_t ldg, int64_t M, int64_t n, T* R, int64_t ldr, cudaStream_t st);
 cudaError_t launch_widen(const float* G, int64_t ldg, int64_t M, int64_t n, double* D, int64_t ldd, cudaStream_t st);
+// dst (rows x n, row stride ldd) = src (rows x n, contiguous)
+cudaError_t launch_repitch(const float* src, int64_t rows, int64_t n, float* dst, int64_t ldd, cudaStream_t st);
 template <typename T>
 cudaError_t launch_gaussian_kmajor(T* Xt, int64_t ldx, int64_t n, int l, int lrows, uint64_t seed,
                                    uint32_t pair, uint32_t side, uint32_t stream, cudaStream_t st);
