@@ -48,6 +48,7 @@ struct gsvd_rand_ctx {
   struct GroupState* grp = nullptr;     // gsvd_rand_solve_grouped: plan, tables and captured graph
   struct GroupState* grp2 = nullptr;    // learned grouped solves: the Algorithm 1 pass of the misses
   struct GroupState* grp3 = nullptr;    // learned grouped solves: the probes of the whole group
+  struct GroupState* grp4 = nullptr;    // fixed-rank grouped solves from host buffers: the second half
   char* lbuf = nullptr;                 // learned grouped solves: features, logits, plans (device)
   size_t lbuf_bytes = 0;
   std::vector<int> grp_plans;           // learned grouped solves: (k, q, fallback) per pair
@@ -77,7 +78,9 @@ struct gsvd_rand_ctx {
   char* gbounce = nullptr;     // two contiguous landing areas of host matrices before their rows are padded
   size_t gbounce_bytes = 0;    // (of each of the two)
   cudaStream_t gstage_st = nullptr;            // re-pitch stream of the staging (owned)
+  cudaStream_t gcopy_st = nullptr;             // host-to-device copy stream of the staging (owned)
   cudaEvent_t gstage_ev[4] = {nullptr, nullptr, nullptr, nullptr};  // landed / re-pitched, per buffer
+  cudaEvent_t gcopy_ev[3] = {nullptr, nullptr, nullptr};  // copy stream start, first half landed / re-pitched
   // complex pairs: the realified matrices, staged host inputs and the doubled GSVs
   char* cplx = nullptr;
   size_t cplx_bytes = 0;
@@ -3017,8 +3020,12 @@ int solve_grouped_staged(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs) {
     // nothing of an earlier call is in flight: every grouped solve synchronises before it returns
     if (h->gstage_st) {
     cudaStreamSynchronize(h->gstage_st);
+    cudaStreamSynchronize(h->gcopy_st);
     cudaStreamDestroy(h->gstage_st);
+    cudaStreamDestroy(h->gcopy_st);
     for (auto e : h->gstage_ev)
+      if (e) cudaEventDestroy(e);
+    for (auto e : h->gcopy_ev)
       if (e) cudaEventDestroy(e);
   }
   if (h->gstage) cudaFree(h->gstage);
@@ -3051,20 +3058,34 @@ int solve_grouped_staged(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs) {
   }
   if (!h->gstage_st) {
     CU(cudaStreamCreateWithFlags(&h->gstage_st, cudaStreamNonBlocking));
+    CU(cudaStreamCreateWithFlags(&h->gcopy_st, cudaStreamNonBlocking));
     for (auto& e : h->gstage_ev) CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    for (auto& e : h->gcopy_ev) CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   }
-  // The host matrices land on h's stream at the link's rate; a matrix with unaligned rows lands
-  // contiguously in one of two bounce buffers and is re-pitched by a kernel on the staging stream
-  // while the next one lands in the other buffer.
-  cudaStream_t rs = h->gstage_st;
+  // A fixed-rank group of at least 16 pairs runs as two halves: the second half's inputs land
+  // while the first half is solved (each half its own captured group; every pair's arithmetic is
+  // the same in any group, so the results are those of one group).
+  const bool halves = !h->cfg.adaptive && !h->cfg.use_learned && npairs >= 16;
+  const int split = halves ? npairs / 2 : npairs;
+  // The host matrices land on the copy stream at the link's rate; a matrix with unaligned rows
+  // lands contiguously in one of two bounce buffers and is re-pitched by a kernel on the staging
+  // stream while the next one lands in the other buffer.
+  cudaStream_t cs = h->gcopy_st, rs = h->gstage_st;
   cudaEvent_t* landed = h->gstage_ev;      // [b]: buffer b's matrix has landed
   cudaEvent_t* repitched = h->gstage_ev + 2;  // [b]: buffer b's matrix has been re-pitched (buffer free)
-  CU(cudaEventRecord(repitched[0], h->stream));  // both buffers free, in order after earlier work
-  CU(cudaEventRecord(repitched[1], h->stream));
+  CU(cudaEventRecord(h->gcopy_ev[0], h->stream));  // in order after earlier work on h's stream
+  CU(cudaStreamWaitEvent(cs, h->gcopy_ev[0], 0));
+  CU(cudaStreamWaitEvent(rs, h->gcopy_ev[0], 0));
+  CU(cudaEventRecord(repitched[0], cs));  // both buffers free
+  CU(cudaEventRecord(repitched[1], cs));
   int nb = 0;  // matrices through the bounce buffers so far
   std::vector<gsvd_rand_pair> sp(pairs, pairs + npairs);
   size_t off = 0;
   for (int i = 0; i < npairs; ++i) {
+    if (i == split) {  // the first half has landed (copies) and been re-pitched
+      CU(cudaEventRecord(h->gcopy_ev[1], cs));
+      CU(cudaEventRecord(h->gcopy_ev[2], rs));
+    }
     gsvd_rand_pair& q = sp[i];
     const int64_t ldn = round_up(q.n, 4);
     for (int s = 0; s < 2; ++s) {
@@ -3074,13 +3095,13 @@ int solve_grouped_staged(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs) {
       char* dst = h->gstage + off;
       const size_t row = (size_t)q.n * sizeof(float);
       if (ldn == q.n) {
-        CU(copy_rows(dst, row, src, (size_t)ld * sizeof(float), row, (size_t)M, cudaMemcpyHostToDevice, h->stream));
+        CU(copy_rows(dst, row, src, (size_t)ld * sizeof(float), row, (size_t)M, cudaMemcpyHostToDevice, cs));
       } else {
         const int b = nb++ & 1;
         char* bb = h->gbounce + (size_t)b * h->gbounce_bytes;
-        CU(cudaStreamWaitEvent(h->stream, repitched[b], 0));
-        CU(copy_rows(bb, row, src, (size_t)ld * sizeof(float), row, (size_t)M, cudaMemcpyHostToDevice, h->stream));
-        CU(cudaEventRecord(landed[b], h->stream));
+        CU(cudaStreamWaitEvent(cs, repitched[b], 0));
+        CU(copy_rows(bb, row, src, (size_t)ld * sizeof(float), row, (size_t)M, cudaMemcpyHostToDevice, cs));
+        CU(cudaEventRecord(landed[b], cs));
         CU(cudaStreamWaitEvent(rs, landed[b], 0));
         CU(launch_repitch(reinterpret_cast<const float*>(bb), M, q.n, reinterpret_cast<float*>(dst), ldn, rs));
         CU(cudaEventRecord(repitched[b], rs));
@@ -3095,12 +3116,35 @@ int solve_grouped_staged(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs) {
       off += ((size_t)M * ldn * sizeof(float) + 255) & ~size_t(255);
     }
   }
-  // the grouped solve (ordered after h's stream) waits for the last re-pitches
-  CU(cudaStreamWaitEvent(h->stream, repitched[0], 0));
-  CU(cudaStreamWaitEvent(h->stream, repitched[1], 0));
-  const int rc = solve_grouped(h, npairs, sp.data());
+  if (!halves) {
+    // the grouped solve (ordered after h's stream) waits for the copies and the last re-pitches
+    CU(cudaEventRecord(h->gcopy_ev[1], cs));
+    CU(cudaEventRecord(h->gcopy_ev[2], rs));
+    CU(cudaStreamWaitEvent(h->stream, h->gcopy_ev[1], 0));
+    CU(cudaStreamWaitEvent(h->stream, h->gcopy_ev[2], 0));
+    const int rc = solve_grouped(h, npairs, sp.data());
+    for (int i = 0; i < npairs; ++i) pairs[i].status = sp[i].status;
+    return rc;
+  }
+  // first half: after its inputs only (the second half's copies continue meanwhile)
+  CU(cudaStreamWaitEvent(h->stream, h->gcopy_ev[1], 0));
+  CU(cudaStreamWaitEvent(h->stream, h->gcopy_ev[2], 0));
+  const bool acc = (h->cfg.flags & GSVD_RAND_FLAG_ACC_RESID) != 0;
+  const int rc1 = retry_breakdowns(h, split, sp.data(), false, solve_grouped_as(h, split, sp.data(), &h->grp, false, acc));
+  const std::string err1 = h->err;
+  // second half: after every copy and re-pitch
+  CU(cudaEventRecord(h->gcopy_ev[1], cs));
+  CU(cudaEventRecord(h->gcopy_ev[2], rs));
+  CU(cudaStreamWaitEvent(h->stream, h->gcopy_ev[1], 0));
+  CU(cudaStreamWaitEvent(h->stream, h->gcopy_ev[2], 0));
+  const int rc2 = retry_breakdowns(h, npairs - split, sp.data() + split, false,
+                                   solve_grouped_as(h, npairs - split, sp.data() + split, &h->grp4, false, acc));
   for (int i = 0; i < npairs; ++i) pairs[i].status = sp[i].status;
-  return rc;
+  if (rc1) {  // the first failing pair is in the first half
+    h->err = err1;
+    return rc1;
+  }
+  return rc2;
 }
 
 // A complex pair {G1, G2} through its realified form: rho maps each entry a + ib to the real
@@ -3247,7 +3291,7 @@ int gsvd_rand_destroy(gsvd_rand_t h) {
   if (h->f64) gsvd_rand_destroy(h->f64);
   h->f64 = nullptr;
   cudaSetDevice(h->cfg.device);
-  for (GroupState** sl : {&h->grp, &h->grp2, &h->grp3})
+  for (GroupState** sl : {&h->grp, &h->grp2, &h->grp3, &h->grp4})
     if (*sl) {
       cudaStreamSynchronize((*sl)->stream);
       group_free(*sl);

@@ -295,6 +295,31 @@ def test_grouped_host_inputs_staged_and_replayed():
             np.testing.assert_array_equal(np.asarray(a[key]), np.asarray(b[key]))
 
 
+def test_grouped_host_inputs_in_two_overlapped_halves():
+    # 20 pairs from host buffers: the group runs as two halves, the second half's inputs landing
+    # while the first is solved; every pair's result is bit-identical to one group of device inputs
+    # (a pair's arithmetic does not depend on the group it runs in), and a repeated call replays
+    specs = _specs(23, 20)
+    mats = [planted_pair(s)[:2] for s in specs]
+    dev_pairs = _pairs(specs, mats)
+    host_pairs = [dict(d, G1=torch.from_numpy(np.ascontiguousarray(G1, dtype=np.float32)).pin_memory(),
+                       G2=torch.from_numpy(np.ascontiguousarray(G2, dtype=np.float32)).pin_memory())
+                  for d, (G1, G2) in zip(dev_pairs, mats)]
+    with P.Context("tf32x3") as ctx:
+        ref = ctx.solve_grouped(dev_pairs)
+    with P.Context("tf32x3") as ctx:
+        first = ctx.solve_grouped(host_pairs)
+        second = ctx.solve_grouped(host_pairs)
+        info = ctx.grouped_info()
+    assert info["captures"] == 1 and info["replays"] == 2
+    for r, a, b in zip(ref, first, second):
+        assert a["status"] == 0 and b["status"] == 0
+        for key in ("alpha", "beta"):
+            np.testing.assert_array_equal(r[key].cpu().numpy(), np.asarray(a[key]))
+            np.testing.assert_array_equal(np.asarray(a[key]), np.asarray(b[key]))
+    _check_vs_oracle("tf32x3", specs[:3], mats[:3], first[:3])
+
+
 def _adaptive_specs():
     # uneven pairs whose planted rank sets where Algorithm 1 stops: blocks of 8 columns until the
     # cumulated residual drops below tol (2e-3); before the block that covers the rank the
