@@ -240,9 +240,9 @@ int gsvd_rand_solve_batched(gsvd_rand_t h, int npairs, gsvd_rand_pair *pairs, in
  * with 16-byte aligned rows are read in place; host matrices (any ld >= n) are copied on
  * cfg->stream, every call, into device memory owned by h (rows padded to 16 bytes, kept
  * for later calls, freed by gsvd_rand_destroy) and solved from there; a fixed-rank group of at
- * least 16 pairs from host buffers then runs as two halves, the second half's inputs copied
- * while the first half is solved (the results are those of one group); pairs may differ in
- * every size and in q.  A pair that breaks
+ * least 16 pairs from host buffers then runs as chunks (two, or one per 64 pairs up to four),
+ * each chunk's inputs copied while the chunk before it is solved (the results are those of one
+ * group); pairs may differ in every size and in q.  A pair that breaks
  * these rules gets status ARG and is left out; the others are solved.  The grouped
  * path chunks its Gram sums differently from gsvd_rand_solve, so results agree with it
  * to rounding (not bit for bit); repeated calls are bit-identical.  The plan, tables

@@ -48,7 +48,7 @@ struct gsvd_rand_ctx {
   struct GroupState* grp = nullptr;     // gsvd_rand_solve_grouped: plan, tables and captured graph
   struct GroupState* grp2 = nullptr;    // learned grouped solves: the Algorithm 1 pass of the misses
   struct GroupState* grp3 = nullptr;    // learned grouped solves: the probes of the whole group
-  struct GroupState* grp4 = nullptr;    // fixed-rank grouped solves from host buffers: the second half
+  struct GroupState* grpc[3] = {nullptr, nullptr, nullptr};  // fixed-rank groups from host buffers: chunks 1-3
   char* lbuf = nullptr;                 // learned grouped solves: features, logits, plans (device)
   size_t lbuf_bytes = 0;
   std::vector<int> grp_plans;           // learned grouped solves: (k, q, fallback) per pair
@@ -80,7 +80,7 @@ struct gsvd_rand_ctx {
   cudaStream_t gstage_st = nullptr;            // re-pitch stream of the staging (owned)
   cudaStream_t gcopy_st = nullptr;             // host-to-device copy stream of the staging (owned)
   cudaEvent_t gstage_ev[4] = {nullptr, nullptr, nullptr, nullptr};  // landed / re-pitched, per buffer
-  cudaEvent_t gcopy_ev[3] = {nullptr, nullptr, nullptr};  // copy stream start, first half landed / re-pitched
+  cudaEvent_t gcopy_ev[9] = {};  // copy stream start, then per chunk: landed (copy stream), re-pitched
   // complex pairs: the realified matrices, staged host inputs and the doubled GSVs
   char* cplx = nullptr;
   size_t cplx_bytes = 0;
@@ -3062,11 +3062,12 @@ int solve_grouped_staged(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs) {
     for (auto& e : h->gstage_ev) CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     for (auto& e : h->gcopy_ev) CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   }
-  // A fixed-rank group of at least 16 pairs runs as two halves: the second half's inputs land
-  // while the first half is solved (each half its own captured group; every pair's arithmetic is
-  // the same in any group, so the results are those of one group).
-  const bool halves = !h->cfg.adaptive && !h->cfg.use_learned && npairs >= 16;
-  const int split = halves ? npairs / 2 : npairs;
+  // A fixed-rank group of at least 16 pairs runs as chunks (two, or one per 64 pairs up to four):
+  // each chunk's inputs land while the chunk before it is solved (each chunk its own captured
+  // group; every pair's arithmetic is the same in any group, so the results are those of one).
+  const int nch = (!h->cfg.adaptive && !h->cfg.use_learned && npairs >= 16) ? std::max(2, std::min(4, npairs / 64)) : 1;
+  std::vector<int> bound(nch + 1);
+  for (int c = 0; c <= nch; ++c) bound[c] = (int)((int64_t)npairs * c / nch);
   // The host matrices land on the copy stream at the link's rate; a matrix with unaligned rows
   // lands contiguously in one of two bounce buffers and is re-pitched by a kernel on the staging
   // stream while the next one lands in the other buffer.
@@ -3081,10 +3082,12 @@ int solve_grouped_staged(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs) {
   int nb = 0;  // matrices through the bounce buffers so far
   std::vector<gsvd_rand_pair> sp(pairs, pairs + npairs);
   size_t off = 0;
+  int chunk = 0;
   for (int i = 0; i < npairs; ++i) {
-    if (i == split) {  // the first half has landed (copies) and been re-pitched
-      CU(cudaEventRecord(h->gcopy_ev[1], cs));
-      CU(cudaEventRecord(h->gcopy_ev[2], rs));
+    while (i == bound[chunk + 1]) {  // chunk `chunk` has landed (copies) and been re-pitched
+      CU(cudaEventRecord(h->gcopy_ev[1 + 2 * chunk], cs));
+      CU(cudaEventRecord(h->gcopy_ev[2 + 2 * chunk], rs));
+      ++chunk;
     }
     gsvd_rand_pair& q = sp[i];
     const int64_t ldn = round_up(q.n, 4);
@@ -3116,35 +3119,39 @@ int solve_grouped_staged(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs) {
       off += ((size_t)M * ldn * sizeof(float) + 255) & ~size_t(255);
     }
   }
-  if (!halves) {
-    // the grouped solve (ordered after h's stream) waits for the copies and the last re-pitches
-    CU(cudaEventRecord(h->gcopy_ev[1], cs));
-    CU(cudaEventRecord(h->gcopy_ev[2], rs));
+  CU(cudaEventRecord(h->gcopy_ev[1 + 2 * (nch - 1)], cs));  // the last chunk
+  CU(cudaEventRecord(h->gcopy_ev[2 + 2 * (nch - 1)], rs));
+  if (nch == 1) {
     CU(cudaStreamWaitEvent(h->stream, h->gcopy_ev[1], 0));
     CU(cudaStreamWaitEvent(h->stream, h->gcopy_ev[2], 0));
     const int rc = solve_grouped(h, npairs, sp.data());
     for (int i = 0; i < npairs; ++i) pairs[i].status = sp[i].status;
     return rc;
   }
-  // first half: after its inputs only (the second half's copies continue meanwhile)
-  CU(cudaStreamWaitEvent(h->stream, h->gcopy_ev[1], 0));
-  CU(cudaStreamWaitEvent(h->stream, h->gcopy_ev[2], 0));
+  // chunk by chunk, each after its own inputs (the later chunks' copies continue meanwhile); the
+  // first failing pair (by index) decides the return code and the message
   const bool acc = (h->cfg.flags & GSVD_RAND_FLAG_ACC_RESID) != 0;
-  const int rc1 = retry_breakdowns(h, split, sp.data(), false, solve_grouped_as(h, split, sp.data(), &h->grp, false, acc));
-  const std::string err1 = h->err;
-  // second half: after every copy and re-pitch
-  CU(cudaEventRecord(h->gcopy_ev[1], cs));
-  CU(cudaEventRecord(h->gcopy_ev[2], rs));
-  CU(cudaStreamWaitEvent(h->stream, h->gcopy_ev[1], 0));
-  CU(cudaStreamWaitEvent(h->stream, h->gcopy_ev[2], 0));
-  const int rc2 = retry_breakdowns(h, npairs - split, sp.data() + split, false,
-                                   solve_grouped_as(h, npairs - split, sp.data() + split, &h->grp4, false, acc));
-  for (int i = 0; i < npairs; ++i) pairs[i].status = sp[i].status;
-  if (rc1) {  // the first failing pair is in the first half
-    h->err = err1;
-    return rc1;
+  int rc = GSVD_RAND_OK;
+  std::string err;
+  for (int c = 0; c < nch; ++c) {
+    CU(cudaStreamWaitEvent(h->stream, h->gcopy_ev[1 + 2 * c], 0));
+    CU(cudaStreamWaitEvent(h->stream, h->gcopy_ev[2 + 2 * c], 0));
+    const int n = bound[c + 1] - bound[c];
+    gsvd_rand_pair* pc = sp.data() + bound[c];
+    const int r = retry_breakdowns(h, n, pc, false,
+                                   solve_grouped_as(h, n, pc, c == 0 ? &h->grp : &h->grpc[c - 1], false, acc));
+    if (r && !rc) {
+      rc = r;
+      err = h->err;
+    }
   }
-  return rc2;
+  for (int i = 0; i < npairs; ++i) pairs[i].status = sp[i].status;
+  if (rc) {
+    h->err = err;
+    return rc;
+  }
+  h->err.clear();
+  return GSVD_RAND_OK;
 }
 
 // A complex pair {G1, G2} through its realified form: rho maps each entry a + ib to the real
@@ -3291,7 +3298,7 @@ int gsvd_rand_destroy(gsvd_rand_t h) {
   if (h->f64) gsvd_rand_destroy(h->f64);
   h->f64 = nullptr;
   cudaSetDevice(h->cfg.device);
-  for (GroupState** sl : {&h->grp, &h->grp2, &h->grp3, &h->grp4})
+  for (GroupState** sl : {&h->grp, &h->grp2, &h->grp3, &h->grpc[0], &h->grpc[1], &h->grpc[2]})
     if (*sl) {
       cudaStreamSynchronize((*sl)->stream);
       group_free(*sl);
