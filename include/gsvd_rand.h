@@ -382,7 +382,10 @@ int gsvd_rand_philox(gsvd_rand_t h, uint64_t count, uint64_t seed, uint32_t pair
 
 /* Accumulated device time (ms, from CUDA events on the solve stream) and call
  * count of one stage since creation or the last reset; only filled while the
- * context has GSVD_RAND_FLAG_PROFILE.  Errors: ARG (bad stage). */
+ * context has GSVD_RAND_FLAG_PROFILE.  In grouped solves the compressed-pair
+ * GSVDs of pairs with L = 2l > 128 run as a branch concurrent with the others',
+ * each step timed on its own branch: there the stage totals overlap and can sum
+ * to more than the solve's elapsed time.  Errors: ARG (bad stage). */
 int gsvd_rand_profile_get(gsvd_rand_t h, int stage, double *total_ms, int64_t *calls);
 int gsvd_rand_profile_reset(gsvd_rand_t h);
 

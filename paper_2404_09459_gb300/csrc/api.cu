@@ -1451,7 +1451,9 @@ int solve_learned(gsvd_rand_ctx* h, const void* G1, int64_t m, int64_t ld1, cons
 struct GroupState {
   std::vector<unsigned char> key;    // the batch the graph was captured for
   cudaStream_t stream = nullptr;     // capture stream (non-blocking, owned)
+  cudaStream_t side = nullptr;       // the graph's concurrent branch is captured from here (owned)
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;  // capture-time edges between the two streams
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   unsigned char* host = nullptr;     // pinned: table staging, then the results block
@@ -1487,6 +1489,9 @@ void group_free(GroupState* g) {
   if (g->exec) cudaGraphExecDestroy(g->exec);
   if (g->graph) cudaGraphDestroy(g->graph);
   if (g->stream) cudaStreamDestroy(g->stream);
+  if (g->side) cudaStreamDestroy(g->side);
+  if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+  if (g->ev_join) cudaEventDestroy(g->ev_join);
   if (g->ev_in) cudaEventDestroy(g->ev_in);
   if (g->ev_out) cudaEventDestroy(g->ev_out);
   for (auto e : g->prof_ev) cudaEventDestroy(e);
@@ -1640,6 +1645,10 @@ struct GroupBuild {
   // launches, replayed in order; each receives the device address of the table arena
   std::vector<std::function<cudaError_t(const unsigned char*, cudaStream_t)>> ops;
   std::vector<int> tags;  // GSVD_RAND_STAGE_* of each op (timed under GSVD_RAND_FLAG_PROFILE)
+  // the stream of each op: LANE_MAIN, LANE_SIDE (a concurrent branch of the graph), or the
+  // markers LANE_FORK (the side stream starts after what came before) and LANE_JOIN (what
+  // follows waits for the side stream)
+  std::vector<signed char> lanes;
   struct Gemm {
     int mode;
     bool norm;
@@ -1655,6 +1664,7 @@ struct GroupBuild {
   size_t ws_bytes = 0;
 };
 
+constexpr signed char LANE_MAIN = 0, LANE_SIDE = 1, LANE_FORK = 2, LANE_JOIN = 3;
 constexpr int64_t GROUP_GRAM_ROWS = 1024;  // rows per Gram chunk
 constexpr int64_t GROUP_GTQ_ROWS = 4096;   // rows per split of G^T Q
 constexpr int GROUP_PROBE_L = GSVD_RAND_MLP_PROBE;  // columns of the learned proposal's probe sketch
@@ -1789,9 +1799,16 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
   const int ns = 2 * np;
   Arena& A = gb.arena;
   int cur_tag = GSVD_RAND_STAGE_SETUP;
+  signed char cur_lane = LANE_MAIN;
   auto push = [&](std::function<cudaError_t(const unsigned char*, cudaStream_t)> f) {
     gb.ops.push_back(std::move(f));
     gb.tags.push_back(cur_tag);
+    gb.lanes.push_back(cur_lane);
+  };
+  auto push_marker = [&](signed char m) {
+    gb.ops.push_back(nullptr);
+    gb.tags.push_back(cur_tag);
+    gb.lanes.push_back(m);
   };
   const double u = 5.9604644775390625e-08;  // FP32 unit roundoff
   // statuses to zero on every replay
@@ -2315,193 +2332,214 @@ int group_build(gsvd_rand_ctx* h, const std::vector<gsvd_rand_pair*>& pv, int pr
   }
 
   // ---- compressed-pair GSVDs ----
-  cur_tag = GSVD_RAND_STAGE_SMALL_GRAM;
-  int maxL = 0, maxk = 0, maxl1 = 0;
-  for (auto& P : gb.prs) {
-    maxL = std::max(maxL, P.L);
-    maxk = std::max(maxk, P.k);
-    maxl1 = std::max(maxl1, P.l);
-  }
-  {
-    std::vector<DgemmB> t(np);
-    for (int i = 0; i < np; ++i) {
-      const GPair& P = gb.prs[i];
-      DgemmB& x = t[i];
-      memset(&x, 0, sizeof(x));
-      x.A = P.S;
-      x.B = P.S;
-      x.C = P.K;
-      x.lda = x.ldb = P.ldn;
-      x.ldc = P.L;
-      x.alpha = 1.0;
-      x.Mr = x.Nc = P.L;
-      x.K = (int)P.n;
-      x.ta = 0;
-      x.tb = 1;
-      x.sym = 1;  // K = S S^T
+  // One chain of batched launches over the pairs ix (tables of their own).
+  auto small_gsvd = [&](const std::vector<int>& ix) {
+    const int np = (int)ix.size();
+    cur_tag = GSVD_RAND_STAGE_SMALL_GRAM;
+    int maxL = 0, maxk = 0, maxl1 = 0;
+    for (int i : ix) {
+      maxL = std::max(maxL, gb.prs[i].L);
+      maxk = std::max(maxk, gb.prs[i].k);
+      maxl1 = std::max(maxl1, gb.prs[i].l);
     }
-    const size_t off = A.add(t);
-    const int mL = maxL;
-    push([off, np, mL](const unsigned char* d, cudaStream_t st) {
-      return launch_dgemm_b<float, float>(reinterpret_cast<const DgemmB*>(d + off), np, mL, mL, st, true);
-    });
-    // each K by a power of two into FP32's exponent range (the double-float refinement)
-    std::vector<EigB> ks(np);
-    for (int i = 0; i < np; ++i) ks[i] = EigB{gb.prs[i].K, nullptr, nullptr, nullptr, 0.f, gb.prs[i].L};
-    const size_t koff = A.add(ks);
-    push([koff, np](const unsigned char* d, cudaStream_t st) {
-      return launch_pow2_scale_b(reinterpret_cast<const EigB*>(d + koff), np, st);
-    });
-  }
-  // FP32 eigensolver starts, split by size class
-  auto add_eig = [&](bool c1) {
-    cur_tag = c1 ? GSVD_RAND_STAGE_SMALL_CS : GSVD_RAND_STAGE_SMALL_JACOBI;
-    for (int cls = 0; cls < 2; ++cls) {
-      std::vector<EigB> t;
+    {
+      std::vector<DgemmB> t(np);
+      for (int i = 0; i < np; ++i) {
+        const GPair& P = gb.prs[ix[i]];
+        DgemmB& x = t[i];
+        memset(&x, 0, sizeof(x));
+        x.A = P.S;
+        x.B = P.S;
+        x.C = P.K;
+        x.lda = x.ldb = P.ldn;
+        x.ldc = P.L;
+        x.alpha = 1.0;
+        x.Mr = x.Nc = P.L;
+        x.K = (int)P.n;
+        x.ta = 0;
+        x.tb = 1;
+        x.sym = 1;  // K = S S^T
+      }
+      const size_t off = A.add(t);
+      const int mL = maxL;
+      push([off, np, mL](const unsigned char* d, cudaStream_t st) {
+        return launch_dgemm_b<float, float>(reinterpret_cast<const DgemmB*>(d + off), np, mL, mL, st, true);
+      });
+      // each K by a power of two into FP32's exponent range (the double-float refinement)
+      std::vector<EigB> ks(np);
+      for (int i = 0; i < np; ++i) ks[i] = EigB{gb.prs[ix[i]].K, nullptr, nullptr, nullptr, 0.f, gb.prs[ix[i]].L};
+      const size_t koff = A.add(ks);
+      push([koff, np](const unsigned char* d, cudaStream_t st) {
+        return launch_pow2_scale_b(reinterpret_cast<const EigB*>(d + koff), np, st);
+      });
+    }
+    // FP32 eigensolver starts, split by size class
+    auto add_eig = [&](bool c1) {
+      cur_tag = c1 ? GSVD_RAND_STAGE_SMALL_CS : GSVD_RAND_STAGE_SMALL_JACOBI;
+      for (int cls = 0; cls < 2; ++cls) {
+        std::vector<EigB> t;
+        int mN = 0;
+        for (int i = 0; i < np; ++i) {
+          const GPair& P = gb.prs[ix[i]];
+          const int N = c1 ? P.k : P.L;
+          if ((N > 128) != (cls == 1)) continue;
+          t.push_back(c1 ? EigB{P.C1, P.Wv, P.mu, P.jscr, 0.f, N} : EigB{P.K, P.X, P.lam, P.jscr, 1e-6f, N});
+          mN = std::max(mN, N);
+        }
+        if (t.empty()) continue;
+        const size_t off = A.add(t);
+        const int cnt = (int)t.size();
+        push([off, cnt, mN](const unsigned char* d, cudaStream_t st) {
+          return launch_eig_f32_b(reinterpret_cast<const EigB*>(d + off), cnt, mN, st);
+        });
+      }
+    };
+    // Ogita-Aishima steps (three: the mixed-precision count), the cut cluster after the first
+    auto add_oa = [&](bool c1) {
+      cur_tag = c1 ? GSVD_RAND_STAGE_SMALL_CS : GSVD_RAND_STAGE_SMALL_REFINE;
+      std::vector<OaB> t(np);
       int mN = 0;
       for (int i = 0; i < np; ++i) {
-        const GPair& P = gb.prs[i];
+        const GPair& P = gb.prs[ix[i]];
         const int N = c1 ? P.k : P.L;
-        if ((N > 128) != (cls == 1)) continue;
-        t.push_back(c1 ? EigB{P.C1, P.Wv, P.mu, P.jscr, 0.f, N} : EigB{P.K, P.X, P.lam, P.jscr, 1e-6f, N});
+        t[i] = OaB{c1 ? P.C1 : P.K, c1 ? P.Wv : P.X, c1 ? P.mu : P.lam, P.XtX, P.P, P.S2, P.F, P.opart, N, P.k,
+                   c1 ? nullptr : P.jscr};
+        t[i].Adf = P.Adf;  // the double-float products read (hi, lo) copies of their operands
+        t[i].Xdf = P.Xdf;
+        t[i].Pdf = P.Pdf;
+        t[i].Fdf = P.Fdf;
         mN = std::max(mN, N);
       }
-      if (t.empty()) continue;
-      const size_t off = A.add(t);
-      const int cnt = (int)t.size();
-      push([off, cnt, mN](const unsigned char* d, cudaStream_t st) {
-        return launch_eig_f32_b(reinterpret_cast<const EigB*>(d + off), cnt, mN, st);
-      });
-    }
-  };
-  // Ogita-Aishima steps (three: the mixed-precision count), the cut cluster after the first
-  auto add_oa = [&](bool c1) {
-    cur_tag = c1 ? GSVD_RAND_STAGE_SMALL_CS : GSVD_RAND_STAGE_SMALL_REFINE;
-    std::vector<OaB> t(np);
-    int mN = 0;
-    for (int i = 0; i < np; ++i) {
-      const GPair& P = gb.prs[i];
-      const int N = c1 ? P.k : P.L;
-      t[i] = OaB{c1 ? P.C1 : P.K, c1 ? P.Wv : P.X, c1 ? P.mu : P.lam, P.XtX, P.P, P.S2, P.F, P.opart, N, P.k,
-                 c1 ? nullptr : P.jscr};
-      t[i].Adf = P.Adf;  // the double-float products read (hi, lo) copies of their operands
-      t[i].Xdf = P.Xdf;
-      t[i].Pdf = P.Pdf;
-      t[i].Fdf = P.Fdf;
-      mN = std::max(mN, N);
-    }
-    std::vector<DgemmB> dg(4 * (size_t)np);
-    oa_b_tables(t.data(), np, dg.data());
-    const size_t ot = A.add(t), od = A.add(dg);
-    for (int it = 0; it < 3; ++it) {
-      push([ot, od, np, mN](const unsigned char* d, cudaStream_t st) {
-        return launch_oa_refine_b(reinterpret_cast<const OaB*>(d + ot), reinterpret_cast<const DgemmB*>(d + od), np,
-                                  mN, st, true);
-      });
-      if (!c1 && it == 0)  // the cut cluster split after the first step, as in the single solve
-        push([ot, np, mN](const unsigned char* d, cudaStream_t st) {
-          return launch_oa_cut_cluster_b(reinterpret_cast<const OaB*>(d + ot), np, mN, st);
+      std::vector<DgemmB> dg(4 * (size_t)np);
+      oa_b_tables(t.data(), np, dg.data());
+      const size_t ot = A.add(t), od = A.add(dg);
+      for (int it = 0; it < 3; ++it) {
+        push([ot, od, np, mN](const unsigned char* d, cudaStream_t st) {
+          return launch_oa_refine_b(reinterpret_cast<const OaB*>(d + ot), reinterpret_cast<const DgemmB*>(d + od), np,
+                                    mN, st, true);
         });
-    }
-  };
-  add_eig(false);
-  add_oa(false);
-  cur_tag = GSVD_RAND_STAGE_SMALL_CS;
-  {
-    std::vector<SelB> t(np);
-    for (int i = 0; i < np; ++i) {
-      const GPair& P = gb.prs[i];
-      t[i] = SelB{P.X, P.lam, P.Zr, P.order, P.L, P.k};
-    }
-    const size_t off = A.add(t);
-    const int mL = maxL;
-    push([off, np, mL](const unsigned char* d, cudaStream_t st) {
-      return launch_select_topr_b(reinterpret_cast<const SelB*>(d + off), np, mL, st);
-    });
-  }
-  // adaptive: the columns beyond the pairs the stopped bases hold (stop1 + stop2 < r)
-  size_t trim_off = 0;
-  if (adaptive) {
-    std::vector<AdaptTrimB> t(np);
-    for (int i = 0; i < np; ++i) {
-      const GPair& P = gb.prs[i];
-      t[i] = AdaptTrimB{P.Zr, P.C1, P.L, P.k, gb.sides[2 * i].stop, gb.sides[2 * i + 1].stop};
-    }
-    trim_off = A.add(t);
-    const size_t off = trim_off;
-    const int mL = maxL, mk = maxk;
-    push([off, np, mL, mk](const unsigned char* d, cudaStream_t st) {
-      return launch_adapt_trim_b(reinterpret_cast<const AdaptTrimB*>(d + off), np, mL, mk, 0, st);
-    });
-  }
-  {
-    std::vector<DgemmB> t(np);
-    for (int i = 0; i < np; ++i) {
-      const GPair& P = gb.prs[i];
-      DgemmB& x = t[i];
-      memset(&x, 0, sizeof(x));
-      x.A = P.Zr;
-      x.B = P.Zr;
-      x.C = P.C1;
-      x.lda = x.ldb = P.k;
-      x.ldc = P.k;
-      x.alpha = 1.0;
-      x.Mr = x.Nc = P.k;
-      x.K = P.l;
-      x.ta = 1;
-      x.tb = 0;
-      x.sym = 1;  // C1 = Z1^T Z1
-    }
-    const size_t off = A.add(t);
-    const int mk = maxk;
-    push([off, np, mk](const unsigned char* d, cudaStream_t st) {
-      return launch_dgemm_b<double, double>(reinterpret_cast<const DgemmB*>(d + off), np, mk, mk, st, true);
-    });
-    if (adaptive) {
-      const size_t toff = trim_off;
+        if (!c1 && it == 0)  // the cut cluster split after the first step, as in the single solve
+          push([ot, np, mN](const unsigned char* d, cudaStream_t st) {
+            return launch_oa_cut_cluster_b(reinterpret_cast<const OaB*>(d + ot), np, mN, st);
+          });
+      }
+    };
+    add_eig(false);
+    add_oa(false);
+    cur_tag = GSVD_RAND_STAGE_SMALL_CS;
+    {
+      std::vector<SelB> t(np);
+      for (int i = 0; i < np; ++i) {
+        const GPair& P = gb.prs[ix[i]];
+        t[i] = SelB{P.X, P.lam, P.Zr, P.order, P.L, P.k};
+      }
+      const size_t off = A.add(t);
       const int mL = maxL;
-      push([toff, np, mL, mk](const unsigned char* d, cudaStream_t st) {
-        return launch_adapt_trim_b(reinterpret_cast<const AdaptTrimB*>(d + toff), np, mL, mk, 1, st);
+      push([off, np, mL](const unsigned char* d, cudaStream_t st) {
+        return launch_select_topr_b(reinterpret_cast<const SelB*>(d + off), np, mL, st);
       });
     }
-  }
-  add_eig(true);
-  add_oa(true);
-  cur_tag = GSVD_RAND_STAGE_SMALL_CS;
-  {
-    std::vector<DgemmB> t(2 * (size_t)np);
-    for (int i = 0; i < np; ++i) {
-      const GPair& P = gb.prs[i];
-      for (int s = 0; s < 2; ++s) {
-        DgemmB& x = t[2 * i + s];
+    // adaptive: the columns beyond the pairs the stopped bases hold (stop1 + stop2 < r)
+    size_t trim_off = 0;
+    if (adaptive) {
+      std::vector<AdaptTrimB> t(np);
+      for (int i = 0; i < np; ++i) {
+        const GPair& P = gb.prs[ix[i]];
+        t[i] = AdaptTrimB{P.Zr, P.C1, P.L, P.k, gb.sides[2 * ix[i]].stop, gb.sides[2 * ix[i] + 1].stop};
+      }
+      trim_off = A.add(t);
+      const size_t off = trim_off;
+      const int mL = maxL, mk = maxk;
+      push([off, np, mL, mk](const unsigned char* d, cudaStream_t st) {
+        return launch_adapt_trim_b(reinterpret_cast<const AdaptTrimB*>(d + off), np, mL, mk, 0, st);
+      });
+    }
+    {
+      std::vector<DgemmB> t(np);
+      for (int i = 0; i < np; ++i) {
+        const GPair& P = gb.prs[ix[i]];
+        DgemmB& x = t[i];
         memset(&x, 0, sizeof(x));
-        x.A = P.Zr + (int64_t)s * P.l * P.k;
-        x.B = P.Wv;
-        x.C = P.U1 + (int64_t)s * P.l * P.k;
-        x.lda = x.ldb = x.ldc = P.k;
+        x.A = P.Zr;
+        x.B = P.Zr;
+        x.C = P.C1;
+        x.lda = x.ldb = P.k;
+        x.ldc = P.k;
         x.alpha = 1.0;
-        x.Mr = P.l;
-        x.Nc = P.k;
-        x.K = P.k;
+        x.Mr = x.Nc = P.k;
+        x.K = P.l;
+        x.ta = 1;
+        x.tb = 0;
+        x.sym = 1;  // C1 = Z1^T Z1
+      }
+      const size_t off = A.add(t);
+      const int mk = maxk;
+      push([off, np, mk](const unsigned char* d, cudaStream_t st) {
+        return launch_dgemm_b<double, double>(reinterpret_cast<const DgemmB*>(d + off), np, mk, mk, st, true);
+      });
+      if (adaptive) {
+        const size_t toff = trim_off;
+        const int mL = maxL;
+        push([toff, np, mL, mk](const unsigned char* d, cudaStream_t st) {
+          return launch_adapt_trim_b(reinterpret_cast<const AdaptTrimB*>(d + toff), np, mL, mk, 1, st);
+        });
       }
     }
-    const size_t off = A.add(t);
-    const int ml = maxl1, mk = maxk, n2 = 2 * np;
-    push([off, n2, ml, mk](const unsigned char* d, cudaStream_t st) {
-      return launch_dgemm_b<double, double>(reinterpret_cast<const DgemmB*>(d + off), n2, ml, mk, st, true);
-    });
-  }
-  {
-    std::vector<CsB> t(np);
-    for (int i = 0; i < np; ++i) {
-      const GPair& P = gb.prs[i];
-      t[i] = CsB{P.U1, P.U1 + (int64_t)P.l * P.k, P.alpha, P.beta, P.l, P.l, P.k, 0};
+    add_eig(true);
+    add_oa(true);
+    cur_tag = GSVD_RAND_STAGE_SMALL_CS;
+    {
+      std::vector<DgemmB> t(2 * (size_t)np);
+      for (int i = 0; i < np; ++i) {
+        const GPair& P = gb.prs[ix[i]];
+        for (int s = 0; s < 2; ++s) {
+          DgemmB& x = t[2 * i + s];
+          memset(&x, 0, sizeof(x));
+          x.A = P.Zr + (int64_t)s * P.l * P.k;
+          x.B = P.Wv;
+          x.C = P.U1 + (int64_t)s * P.l * P.k;
+          x.lda = x.ldb = x.ldc = P.k;
+          x.alpha = 1.0;
+          x.Mr = P.l;
+          x.Nc = P.k;
+          x.K = P.k;
+        }
+      }
+      const size_t off = A.add(t);
+      const int ml = maxl1, mk = maxk, n2 = 2 * np;
+      push([off, n2, ml, mk](const unsigned char* d, cudaStream_t st) {
+        return launch_dgemm_b<double, double>(reinterpret_cast<const DgemmB*>(d + off), n2, ml, mk, st, true);
+      });
     }
-    const size_t off = A.add(t);
-    const int mk = maxk;
-    push([off, np, mk](const unsigned char* d, cudaStream_t st) {
-      return launch_cs_norms_b(reinterpret_cast<const CsB*>(d + off), np, mk, st);
-    });
+    {
+      std::vector<CsB> t(np);
+      for (int i = 0; i < np; ++i) {
+        const GPair& P = gb.prs[ix[i]];
+        t[i] = CsB{P.U1, P.U1 + (int64_t)P.l * P.k, P.alpha, P.beta, P.l, P.l, P.k, 0};
+      }
+      const size_t off = A.add(t);
+      const int mk = maxk;
+      push([off, np, mk](const unsigned char* d, cudaStream_t st) {
+        return launch_cs_norms_b(reinterpret_cast<const CsB*>(d + off), np, mk, st);
+      });
+    }
+  };
+  // Pairs with L > 128 (FP32 starts and cut clusters in the long one-CTA-per-pair kernels) run
+  // as a concurrent branch of the graph beside the others, whose launches then fill the SMs
+  // those stragglers leave idle; the arithmetic of each pair is the same either way.
+  {
+    std::vector<int> lo, hi;
+    for (int i = 0; i < np; ++i) (gb.prs[i].L > CUT_CMAX ? hi : lo).push_back(i);
+    if (lo.empty() || hi.empty()) {
+      small_gsvd(lo.empty() ? hi : lo);
+    } else {
+      push_marker(LANE_FORK);
+      cur_lane = LANE_SIDE;
+      small_gsvd(hi);
+      cur_lane = LANE_MAIN;
+      small_gsvd(lo);
+      push_marker(LANE_JOIN);
+    }
   }
   return GSVD_RAND_OK;
 }
@@ -2555,6 +2593,9 @@ int solve_grouped_as(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs, GroupS
     CU(cudaStreamCreateWithFlags(&(*slot)->stream, cudaStreamNonBlocking));
     CU(cudaEventCreateWithFlags(&(*slot)->ev_in, cudaEventDisableTiming));
     CU(cudaEventCreateWithFlags(&(*slot)->ev_out, cudaEventDisableTiming));
+    CU(cudaStreamCreateWithFlags(&(*slot)->side, cudaStreamNonBlocking));
+    CU(cudaEventCreateWithFlags(&(*slot)->ev_fork, cudaEventDisableTiming));
+    CU(cudaEventCreateWithFlags(&(*slot)->ev_join, cudaEventDisableTiming));
   }
   GroupState* g = *slot;
   cudaStream_t gs = g->stream;
@@ -2664,18 +2705,34 @@ int solve_grouped_as(gsvd_rand_ctx* h, int npairs, gsvd_rand_pair* pairs, GroupS
         g->prof_ev.push_back(e);
       }
     cudaError_t ce = cudaSuccess;
-    size_t bad_op = 0;
+    size_t bad_op = 0, j = 0;
+    bool forked = false;
     for (size_t i = 0; i < gb.ops.size(); ++i) {
+      const signed char ln = gb.lanes[i];
+      if (ln == LANE_FORK || ln == LANE_JOIN) {
+        // a plain record under capture is an edge between the streams
+        cudaStream_t from = ln == LANE_FORK ? gs : g->side, to = ln == LANE_FORK ? g->side : gs;
+        cudaEvent_t ev = ln == LANE_FORK ? g->ev_fork : g->ev_join;
+        if ((ce = cudaEventRecord(ev, from)) != cudaSuccess || (ce = cudaStreamWaitEvent(to, ev, 0)) != cudaSuccess)
+          break;
+        forked = ln == LANE_FORK;
+        ++bad_op;
+        continue;
+      }
+      cudaStream_t os = ln == LANE_SIDE ? g->side : gs;
       // external records: event nodes of the graph (a plain record under capture is only an edge)
-      if (prof && (ce = cudaEventRecordWithFlags(g->prof_ev[2 * i], gs, cudaEventRecordExternal)) != cudaSuccess)
+      if (prof && (ce = cudaEventRecordWithFlags(g->prof_ev[2 * j], os, cudaEventRecordExternal)) != cudaSuccess)
         break;
-      if ((ce = gb.ops[i](dtab, gs)) != cudaSuccess) break;
+      if ((ce = gb.ops[i](dtab, os)) != cudaSuccess) break;
       if (prof) {
-        if ((ce = cudaEventRecordWithFlags(g->prof_ev[2 * i + 1], gs, cudaEventRecordExternal)) != cudaSuccess) break;
+        if ((ce = cudaEventRecordWithFlags(g->prof_ev[2 * j + 1], os, cudaEventRecordExternal)) != cudaSuccess) break;
         g->prof_tag.push_back(gb.tags[i]);
       }
+      ++j;
       ++bad_op;
     }
+    if (forked && cudaEventRecord(g->ev_join, g->side) == cudaSuccess)  // a failed capture ends joined
+      cudaStreamWaitEvent(gs, g->ev_join, 0);
     cudaGraph_t graph = nullptr;
     cudaError_t ee = cudaStreamEndCapture(gs, &graph);
     if (ce != cudaSuccess || ee != cudaSuccess) {
