@@ -733,6 +733,16 @@ template <typename T>
 constexpr int oa_iters() {
   return std::is_same<T, double>::value ? 6 : 3;
 }
+// The single solve's refinement of K splits the cut cluster after its second step, not its
+// first: the first step's delta still carries the FP32 start's mixing of close eigenvectors
+// (Gram-Schmidt within the start's 1e-3 clusters), so a cut gap that the next step resolves
+// by itself (the default pair: 6.4e-5 of ||K||) still joined a cluster there, and its FP32
+// Jacobi took 0.71 ms of a 3.4 ms solve.  Two steps follow the split on the mixed paths as
+// before, hence one more in all; the FP64 path keeps four after it.
+template <typename T>
+constexpr int oa_iters_k() {
+  return oa_iters<T>() + (std::is_same<T, double>::value ? 0 : 1);
+}
 
 // Compressed-pair GSVD (Algorithm 2 with the rank-revealing reading): the r
 // leading left singular vectors Zr of S = [B1; B2] are the leading eigenvectors
@@ -760,12 +770,12 @@ int small_gsvd(gsvd_rand_ctx* h, cudaStream_t st, DevStatus* st_dev, const T* S,
   }
   {
     ProfScope ps(h, GSVD_RAND_STAGE_SMALL_REFINE);
-    for (int it = 0; it < oa_iters<T>(); ++it) {
+    for (int it = 0; it < oa_iters_k<T>(); ++it) {
       CU(launch_oa_refine(sb.K, L, sb.X, sb.lam, sb.work, sb.work_elems, st, df));
-      // after the first step every eigenvector outside the clusters has squared its start
-      // error, so the cluster that straddles the cut (of any size up to L) is split then,
-      // and the remaining steps (two on the mixed paths) refine the split columns
-      if (it == 0) CU(launch_oa_cut_cluster(L, r, sb.X, sb.lam, sb.work, sb.work_elems, sb.jscratch, st));
+      // after the second step the clusters are the ones the FP32 start cannot resolve, so the
+      // cluster that straddles the cut (of any size up to L) is split then, and the remaining
+      // steps (two on the mixed paths) refine the split columns
+      if (it == 1) CU(launch_oa_cut_cluster(L, r, sb.X, sb.lam, sb.work, sb.work_elems, sb.jscratch, st));
     }
   }
   ProfScope ps_cs(h, GSVD_RAND_STAGE_SMALL_CS);
