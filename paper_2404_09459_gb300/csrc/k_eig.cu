@@ -869,15 +869,22 @@ __device__ __forceinline__ void eig128_body(const double* __restrict__ Ain, int 
 }
 
 // ============================================================================
-// The same method for 128 < N <= 512, one CTA of 1024 threads.  The matrix is
-// kept as its packed lower triangle, Ap[i (i + 1) / 2 + j] = A_ij (j <= i), in
-// shared memory while it fits (N <= 318), else in global scratch; the
-// reflector of step k overwrites column k below the diagonal.  The
-// eigenvectors of T, their factorisation pivots and the complement's
-// reflectors live column-major in global scratch (each column contiguous).
+// The same method for 128 < N <= 512, one CTA of 1024 threads.  The launch
+// gives the CTA dyn_floats floats of dynamic shared memory; the matrix is kept
+//   - full (row-major, both triangles) in shared memory when N^2 floats fit
+//     (N <= 227), else
+//   - as its packed lower triangle, Ap[i (i + 1) / 2 + j] = A_ij (j <= i), in
+//     shared memory when that fits (N <= 318), else
+//   - full in global scratch (rows read and written whole, coalesced).
+// The full forms apply the rank-2 update to (i, j) and (j, i) as the same
+// correctly rounded value, so the stored matrix stays exactly symmetric and the
+// row i right of the diagonal serves as column i.  The reflector of step k is
+// stored contiguously (row k of RT) for the back-transformation.  From step 2
+// on the eigenvectors of T live column-major in shared memory when N^2 floats
+// fit (the matrix is no longer needed), else in global scratch; their
+// factorisation pivots and the complement's reflectors stay in global scratch.
 //   1. Householder tridiagonalisation, three barriers per step: the reflector
-//      (one warp), p = beta A v (a warp per row, reading the row part and the
-//      column part of the packed triangle), then the rank-2 update;
+//      (one warp), p = beta A v (a warp per row), then the rank-2 update;
 //   2.-3c. as in eig128 (multisection, twisted factorisation, cluster CGS2,
 //      orthonormal complement of the noise columns);
 //   4. X = H_0 ... H_{N-3} Z, a warp per column of Z held in registers.
@@ -885,14 +892,21 @@ __device__ __forceinline__ void eig128_body(const double* __restrict__ Ain, int 
 namespace {
 constexpr int EB_NMAX = 512;
 constexpr int EB_SMEM_NMAX = 318;  // N (N + 1) / 2 floats = 202,884 bytes: with ~24 KB static, within 227 KB
+constexpr int EB_DYN_FLOATS = 202 * 1024 / 4;  // the dynamic shared memory cap of the eig_big launches
 __device__ __forceinline__ int pk(int i, int j) { return ((i * (i + 1)) >> 1) + j; }  // j <= i
+// Dynamic shared memory (floats) for problems up to N: the full matrix when it fits, else the
+// packed triangle when that fits, else none.
+int eb_dyn_floats(int N) {
+  const int64_t full = (int64_t)N * N, packed = (int64_t)N * (N + 1) / 2;
+  return full <= EB_DYN_FLOATS ? (int)full : (packed <= EB_DYN_FLOATS ? (int)packed : 0);
+}
 }  // namespace
 
-int64_t eig_big_scratch_floats(int N) { return 4ll * N * N + (int64_t)N * (N + 1) / 2 + 64; }
+int64_t eig_big_scratch_floats(int N) { return 6ll * N * N + 64; }
 
 __device__ __forceinline__ void eig_big_body(const double* __restrict__ Ain, int N, double* __restrict__ Xout,
                                              double* __restrict__ lam, float* __restrict__ gscr, float noise_rel,
-                                             int ap_smem) {
+                                             int dyn_floats) {
   extern __shared__ float ebsm[];
   __shared__ float s_d[EB_NMAX], s_e[EB_NMAX], s_beta[EB_NMAX], s_v[EB_NMAX], s_p[EB_NMAX], s_lam[EB_NMAX];
   __shared__ float s_cf[EB_NMAX], s_flag[EB_NMAX];
@@ -902,11 +916,15 @@ __device__ __forceinline__ void eig_big_body(const double* __restrict__ Ain, int
   __shared__ int s_retry;
   const int tid = threadIdx.x, w = tid >> 5, t = tid & 31;
   const size_t NN = (size_t)N * N;
-  float* ZT = gscr;        // N x N column-major: eigenvectors of T, then of A
-  float* LT = ZT + NN;     // N x N column-major: L pivots of eigenvalue j in column j
-  float* UT = LT + NN;     // N x N column-major: U pivots
-  float* VT = UT + NN;     // N x N column-major: the complement's Householder columns
-  float* Ap = ap_smem ? ebsm : VT + NN;
+  const bool z_smem = (int64_t)NN <= dyn_floats;  // full matrix, then Z, in shared memory
+  const bool packed = !z_smem && (int64_t)N * (N + 1) / 2 <= dyn_floats;
+  float* LT = gscr + NN;      // N x N column-major: L pivots of eigenvalue j in column j
+  float* UT = gscr + 2 * NN;  // N x N column-major: U pivots
+  float* VT = gscr + 3 * NN;  // N x N column-major: the complement's Householder columns
+  float* RT = gscr + 4 * NN;  // N x N: reflector k in row k (entries k + 1 .. N - 1)
+  float* Af = z_smem ? ebsm : gscr + 5 * NN;  // the full forms' matrix (row-major)
+  float* Ap = ebsm;                           // the packed form's triangle
+  float* ZT = z_smem ? ebsm : gscr;  // from step 2 on: eigenvectors of T, then of A (column-major)
 
   if (w == 0) {
     double mx = 0.0;
@@ -916,12 +934,19 @@ __device__ __forceinline__ void eig_big_body(const double* __restrict__ Ain, int
   }
   __syncthreads();
   const float inv = 1.0f / s_scale;
-  for (int i = w; i < N; i += 32)
-    for (int j = t; j <= i; j += 32) Ap[pk(i, j)] = (float)(Ain[(int64_t)i * N + j] * (double)inv);
+  if (packed) {
+    for (int i = w; i < N; i += 32)
+      for (int j = t; j <= i; j += 32) Ap[pk(i, j)] = (float)(Ain[(int64_t)i * N + j] * (double)inv);
+  } else {  // both triangles from the lower one: exactly symmetric
+    for (int i = w; i < N; i += 32)
+      for (int j = t; j < N; j += 32)
+        Af[(size_t)i * N + j] = (float)(Ain[(int64_t)max(i, j) * N + min(i, j)] * (double)inv);
+  }
   for (int i = tid; i < N; i += 1024) s_v[i] = 0.f;
   __syncthreads();
 
   // ---- 1. tridiagonalisation ------------------------------------------------
+  if (packed) {
   for (int k = 0; k + 2 < N; ++k) {
     if (w == 0) {
       const float x0 = Ap[pk(k + 1, k)];
@@ -934,7 +959,7 @@ __device__ __forceinline__ void eig_big_body(const double* __restrict__ Ain, int
         for (int i = k + 1 + t; i < N; i += 32) {
           const float v = i == k + 1 ? 1.f : Ap[pk(i, k)] * vs;
           s_v[i] = v;
-          Ap[pk(i, k)] = v;  // kept for the back-transformation
+          RT[(size_t)k * N + i] = v;  // kept for the back-transformation
         }
       if (t == 0) {
         s_beta[k] = bk;
@@ -981,7 +1006,71 @@ __device__ __forceinline__ void eig_big_body(const double* __restrict__ Ain, int
     s_d[N - 1] = Ap[pk(N - 1, N - 1)];
     s_beta[N - 1] = 0.f;
   }
-  __syncthreads();
+  } else {
+  for (int k = 0; k + 2 < N; ++k) {
+    const float* Ak = Af + (size_t)k * N;  // row k right of the diagonal = column k below it
+    if (w == 0) {
+      const float x0 = Ak[k + 1];
+      const float sig = warp_nrm2(k + 1, N, t, [&](int i) { return Ak[i]; });
+      const float alpha = x0 >= 0.f ? -sig : sig;
+      const bool refl = sig > 0.f && isfinite(sig);
+      const float bk = refl ? (alpha - x0) / alpha : 0.f;  // normalised reflector, v_0 = 1, bk in [1, 2]
+      const float vs = refl ? 1.f / (x0 - alpha) : 0.f;
+      if (refl)
+        for (int i = k + 1 + t; i < N; i += 32) {
+          const float v = i == k + 1 ? 1.f : Ak[i] * vs;
+          s_v[i] = v;
+          RT[(size_t)k * N + i] = v;  // kept for the back-transformation
+        }
+      if (t == 0) {
+        s_beta[k] = bk;
+        s_e[k] = bk > 0.f ? alpha : x0;
+        s_d[k] = Ak[k];
+        s_v[k] = 0.f;
+      }
+    }
+    __syncthreads();
+    const float bk = s_beta[k];
+    if (bk == 0.f) continue;  // uniform: nothing to annihilate
+    // p = bk A22 v (rows k+1 .. N-1, each read whole), per-warp share of p^T v
+    float pvw = 0.f;
+    for (int i = k + 1 + w; i < N; i += 32) {
+      const float* row = Af + (size_t)i * N;
+      float s = 0.f;
+      for (int j = k + 1 + t; j < N; j += 32) s = fmaf(row[j], s_v[j], s);
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      s *= bk;
+      pvw = fmaf(s, s_v[i], pvw);
+      if (t == 0) s_p[i] = s;
+    }
+    if (t == 0) s_red[w] = pvw;
+    __syncthreads();
+    float pv = s_red[t];
+    for (int o = 16; o > 0; o >>= 1) pv += __shfl_xor_sync(0xffffffffu, pv, o);
+    const float kk = 0.5f * bk * pv;
+    // A22 <- A22 - v w^T - w v^T with w = p - kk v: (i, j) and (j, i) get the same value
+    // (two correctly rounded products and their correctly rounded sum, in either order)
+    for (int i = k + 1 + w; i < N; i += 32) {
+      const float vi = s_v[i], wi = s_p[i] - kk * vi;
+      float* row = Af + (size_t)i * N;
+      for (int j = k + 1 + t; j < N; j += 32) {
+        const float vj = s_v[j], wj = s_p[j] - kk * vj;
+        row[j] -= __fadd_rn(__fmul_rn(vi, wj), __fmul_rn(wi, vj));
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (N >= 2) {
+      s_d[N - 2] = Af[(size_t)(N - 2) * N + N - 2];
+      s_e[N - 2] = Af[(size_t)(N - 1) * N + N - 2];
+      s_beta[N - 2] = 0.f;
+    }
+    s_d[N - 1] = Af[(size_t)(N - 1) * N + N - 1];
+    s_beta[N - 1] = 0.f;
+  }
+  }
+  __syncthreads();  // the matrix is dead from here on (Z may take its shared memory)
 
   // ---- 2. eigenvalues (multisection) and eigenvectors of T ------------------
   if (w == 0) {
@@ -1267,7 +1356,7 @@ __device__ __forceinline__ void eig_big_body(const double* __restrict__ Ain, int
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
         const int i = t + 32 * r;
-        v[r] = (i > k && i < N) ? Ap[pk(i, k)] : 0.f;
+        v[r] = (i > k && i < N) ? RT[(size_t)k * N + i] : 0.f;
         s = fmaf(v[r], z[r], s);
       }
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -1291,8 +1380,8 @@ __global__ __launch_bounds__(1024) void eig128_kernel(const double* __restrict__
 
 __global__ __launch_bounds__(1024) void eig_big_kernel(const double* __restrict__ Ain, int N,
                                                        double* __restrict__ Xout, double* __restrict__ lam,
-                                                       float* __restrict__ gscr, float noise_rel, int ap_smem) {
-  eig_big_body(Ain, N, Xout, lam, gscr, noise_rel, ap_smem);
+                                                       float* __restrict__ gscr, float noise_rel, int dyn_floats) {
+  eig_big_body(Ain, N, Xout, lam, gscr, noise_rel, dyn_floats);
 }
 
 // Batched: one CTA per problem (the grouped solve's compressed pairs).
@@ -1300,46 +1389,44 @@ __global__ __launch_bounds__(1024) void eig128_b_kernel(const EigB* __restrict__
   const EigB& a = tab[blockIdx.x];
   eig128_body(a.A, a.N, a.X, a.lam, a.scratch, a.noise_rel);
 }
-__global__ __launch_bounds__(1024) void eig_big_b_kernel(const EigB* __restrict__ tab) {
+__global__ __launch_bounds__(1024) void eig_big_b_kernel(const EigB* __restrict__ tab, int dyn_floats) {
   const EigB& a = tab[blockIdx.x];
-  eig_big_body(a.A, a.N, a.X, a.lam, a.scratch, a.noise_rel, 1);
+  eig_big_body(a.A, a.N, a.X, a.lam, a.scratch, a.noise_rel, dyn_floats);
 }
 
 // A cut cluster of more than CUT_CMAX columns (the descriptor written by the cut-cluster
 // detection kernel into the P block of the refinement work; N = 0: nothing to solve).  The
-// packed triangle stays in shared memory when N <= ap_cap (the launch's allocation).
-__device__ __forceinline__ void eig_cut_big_body(const double* __restrict__ pblock, int ap_cap) {
+// launch gives dyn_floats floats of dynamic shared memory.
+__device__ __forceinline__ void eig_cut_big_body(const double* __restrict__ pblock, int dyn_floats) {
   const EigB* e = reinterpret_cast<const EigB*>(pblock + CUT_EIGB_OFF);
   const int c = e->N;
   if (c <= CUT_CMAX || c > EB_NMAX) return;
-  eig_big_body(e->A, c, e->X, e->lam, e->scratch, e->noise_rel, c <= ap_cap);
+  eig_big_body(e->A, c, e->X, e->lam, e->scratch, e->noise_rel, dyn_floats);
 }
 
-__global__ __launch_bounds__(1024) void eig_cut_big_kernel(const double* __restrict__ pblock, int ap_cap) {
-  eig_cut_big_body(pblock, ap_cap);
+__global__ __launch_bounds__(1024) void eig_cut_big_kernel(const double* __restrict__ pblock, int dyn_floats) {
+  eig_cut_big_body(pblock, dyn_floats);
 }
 
-__global__ __launch_bounds__(1024) void eig_cut_big_b_kernel(const OaB* __restrict__ tab, int ap_cap) {
+__global__ __launch_bounds__(1024) void eig_cut_big_b_kernel(const OaB* __restrict__ tab, int dyn_floats) {
   const OaB& o = tab[blockIdx.x];
   if (o.N <= CUT_CMAX || !o.jscr) return;  // no room for a descriptor, or no scratch: clipped clusters only
-  eig_cut_big_body(o.P, ap_cap);
+  eig_cut_big_body(o.P, dyn_floats);
 }
 
 cudaError_t launch_eig_cut_big(const double* pblock, int max_N, cudaStream_t st) {
   if (max_N <= CUT_CMAX) return cudaSuccess;
-  const int cap = std::min(max_N, EB_SMEM_NMAX);
-  const size_t smem = (size_t)cap * (cap + 1) / 2 * sizeof(float);
-  cudaFuncSetAttribute(eig_cut_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 202 * 1024);
-  eig_cut_big_kernel<<<1, 1024, smem, st>>>(pblock, cap);
+  const int dyn = eb_dyn_floats(std::min(max_N, EB_SMEM_NMAX));
+  cudaFuncSetAttribute(eig_cut_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, EB_DYN_FLOATS * 4);
+  eig_cut_big_kernel<<<1, 1024, (size_t)dyn * sizeof(float), st>>>(pblock, dyn);
   return launched();
 }
 
 cudaError_t launch_eig_cut_big_b(const OaB* tab, int nprob, int max_N, cudaStream_t st) {
   if (nprob <= 0 || max_N <= CUT_CMAX) return cudaSuccess;
-  const int cap = std::min(max_N, EB_SMEM_NMAX);
-  const size_t smem = (size_t)cap * (cap + 1) / 2 * sizeof(float);
-  cudaFuncSetAttribute(eig_cut_big_b_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 202 * 1024);
-  eig_cut_big_b_kernel<<<nprob, 1024, smem, st>>>(tab, cap);
+  const int dyn = eb_dyn_floats(std::min(max_N, EB_SMEM_NMAX));
+  cudaFuncSetAttribute(eig_cut_big_b_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, EB_DYN_FLOATS * 4);
+  eig_cut_big_b_kernel<<<nprob, 1024, (size_t)dyn * sizeof(float), st>>>(tab, dyn);
   return launched();
 }
 
@@ -1352,9 +1439,9 @@ cudaError_t launch_eig_f32_b(const EigB* tab, int nprob, int max_N, cudaStream_t
     eig128_b_kernel<<<nprob, 1024, smem, st>>>(tab);
     return launched();
   }
-  const size_t smem = (size_t)max_N * (max_N + 1) / 2 * sizeof(float);
-  cudaFuncSetAttribute(eig_big_b_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 202 * 1024);
-  eig_big_b_kernel<<<nprob, 1024, smem, st>>>(tab);
+  const int dyn = eb_dyn_floats(max_N);
+  cudaFuncSetAttribute(eig_big_b_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, EB_DYN_FLOATS * 4);
+  eig_big_b_kernel<<<nprob, 1024, (size_t)dyn * sizeof(float), st>>>(tab, dyn);
   return launched();
 }
 
@@ -1370,11 +1457,10 @@ cudaError_t launch_eig_f32(const double* A, int N, double* X, double* lam, float
     return launched();
   }
   if (N <= EB_NMAX) {
-    const int ap_smem = N <= EB_SMEM_NMAX;
-    const size_t smem = ap_smem ? (size_t)N * (N + 1) / 2 * sizeof(float) : 0;
+    const int dyn = eb_dyn_floats(N);
     // a fixed cap: concurrent launches must not lower it
-    cudaFuncSetAttribute(eig_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 202 * 1024);
-    eig_big_kernel<<<1, 1024, smem, st>>>(A, N, X, lam, scratch, (float)noise_rel, ap_smem);
+    cudaFuncSetAttribute(eig_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, EB_DYN_FLOATS * 4);
+    eig_big_kernel<<<1, 1024, (size_t)dyn * sizeof(float), st>>>(A, N, X, lam, scratch, (float)noise_rel, dyn);
     return launched();
   }
   const size_t smem = (2ull * N * lda + 8ull * N) * sizeof(float);
