@@ -621,7 +621,10 @@ __global__ __launch_bounds__(256) void gram_partial_kernel(const T* __restrict__
 int gram_chunks(int64_t M, int l, int64_t* rows_per_chunk) {
   int64_t t = cdiv(l, GR_T);
   int64_t upper = t * (t + 1) / 2;
-  int64_t chunks = std::max<int64_t>(1, (2 * 152) / upper);
+  // two CTAs per SM; eight for bases wider than 128 columns, whose CTAs each stream thousands
+  // of rows with unhidden load latency at two per SM (0.63 ms, 26% of the FP32 rate, for
+  // M = 120000, l = 220)
+  int64_t chunks = std::max<int64_t>(1, ((l > 128 ? 8 : 2) * 152) / upper);
   chunks = std::min<int64_t>(chunks, std::max<int64_t>(1, cdiv(M, 64)));
   // keep the partial buffer <= 8M doubles
   while (chunks > 1 && chunks * (int64_t)l * l > (8ll << 20)) --chunks;
