@@ -464,6 +464,60 @@ struct Solver {
     return GSVD_RAND_OK;
   }
 
+  // orth_tc for both sides in lockstep: per pass the two Grams, then one launch factoring both
+  // (two CTAs side by side: each factorisation is one CTA's chain of l pivots, 0.5 ms at l = 220),
+  // then the two products.  Each side's arithmetic is orth_tc's.
+  int orth_tc2(SideBufs<T>* b, const T* const* Yin, const int64_t* M, int l, int64_t lp, T* const* out,
+               const int64_t* ldo, int transpose_out, const int* stage) {
+    if constexpr (std::is_same<T, float>::value && std::is_same<TC, float>::value) {
+      const double u = 5.9604644775390625e-08;
+      const int64_t lt = round_up(l, 4);
+      const int nmma = (int)round_up(l, 16);
+      int chunks[2];
+      int64_t rpc[2], lds[2];
+      double shift[2], tau[2];
+      float* Rt[2];
+      T *q1[2], *q2[2];
+      const T* src[2];
+      for (int s = 0; s < 2; ++s) {
+        chunks[s] = gram_chunks(M[s], l, &rpc[s]);
+        shift[s] = 11.0 * ((double)rpc[s] + l + 1) * u;
+        tau[s] = 8.0 * (double)std::max<int64_t>(rpc[s], apply_rows_per_cta(l, (int)sizeof(T))) * u;
+        Rt[s] = reinterpret_cast<float*>(b[s].R);
+        CU(cudaMemsetAsync(Rt[s] + (int64_t)l * lt, 0, (size_t)(nmma - l) * lt * sizeof(float), st));
+        q1[s] = b[s].tmp;
+        q2[s] = b[s].tmp + M[s] * lt;
+        src[s] = Yin[s];
+        lds[s] = lp;
+      }
+      for (int pass = 0; pass < 3; ++pass) {
+        CholPairArgs a;
+        for (int s = 0; s < 2; ++s) {
+          CU(launch_gram_partial<T>(src[s], lds[s], M[s], l, b[s].gpart, chunks[s], rpc[s], st));
+          CU(launch_gram_reduce(b[s].gpart, chunks[s], l, b[s].W, st));
+          a.W[s] = b[s].W;
+          a.Rinv[s] = Rt[s];
+          a.scratch[s] = reinterpret_cast<float*>(b[s].cscr);
+          a.shift_coef[s] = pass == 0 ? shift[s] : 0.0;
+          a.tau_rel[s] = tau[s];
+          a.stage[s] = stage[s] + (pass > 0 ? 1 : 0);
+        }
+        CU(launch_chol_shift_pair(a, l, st_dev, st, (int)lt));
+        const bool direct = pass == 2 && !transpose_out;
+        for (int s = 0; s < 2; ++s) {
+          T* dst = direct ? out[s] : (pass == 1 ? q2[s] : q1[s]);
+          CU(tc_gemm_gx(GSVD_RAND_TF32X3, src[s], lds[s], M[s], l, Rt[s], lt, l, dst, direct ? ldo[s] : lt, nullptr,
+                        st_dev, st));
+          src[s] = dst;
+          lds[s] = lt;
+        }
+      }
+      if (transpose_out)
+        for (int s = 0; s < 2; ++s) CU(launch_transpose<T>(q1[s], lt, M[s], l, out[s], ldo[s], st));
+    }
+    return GSVD_RAND_OK;
+  }
+
   // The same re-orthonormalisation for both sides at once: when both bases fit the fused
   // kernel together (two CTAs per SM), one cooperative launch runs both sides' passes, so
   // the latency of the Cholesky chains and grid barriers is paid once; otherwise side by side.
@@ -487,6 +541,16 @@ struct Solver {
                          stage[s]};
       CU((launch_cholqr2_fused_n<T, TC>(fb, st_dev, st)));
       return GSVD_RAND_OK;
+    }
+    if constexpr (std::is_same<T, float>::value && std::is_same<TC, float>::value) {
+      // bases wider than 128 columns on the tensor-core path (neither side in the fused kernel)
+      const bool fused0 = ctas[0] > 0 && ctas[0] <= cholqr2_fused_max_ctas();
+      const bool fused1 = ctas[1] > 0 && ctas[1] <= cholqr2_fused_max_ctas();
+      if (!fused0 && !fused1 && l > 128 && l <= 256 && h->tc_ok &&
+          (prec == GSVD_RAND_TF32 || prec == GSVD_RAND_TF32X3 || prec == GSVD_RAND_BF16)) {
+        ProfScope ps(h, GSVD_RAND_STAGE_ORTH);
+        return orth_tc2(b, Yin, M, l, lp, out, ldo, transpose_out, stage);
+      }
     }
     int rc;
     for (int s = 0; s < 2; ++s)

@@ -977,6 +977,22 @@ cudaError_t launch_chol_shift(const double* W, int l, double shift_coef, double 
                                                                       stage, scratch, use_smem, ldt);
   return launched();
 }
+__global__ __launch_bounds__(CHOL_THREADS) void chol_shift_pair_kernel(CholPairArgs a, int l, DevStatus* st_dev,
+                                                                       int use_smem, int ldt) {
+  const int s = blockIdx.x;
+  chol_shift_body<float>(a.W[s], l, a.shift_coef[s], a.tau_rel[s], a.Rinv[s], st_dev, a.stage[s], a.scratch[s],
+                         use_smem, ldt);
+}
+
+cudaError_t launch_chol_shift_pair(const CholPairArgs& a, int l, DevStatus* st_dev, cudaStream_t st, int ldt) {
+  if (l <= 64 || l > 256) return cudaErrorInvalidValue;
+  size_t smem = (size_t)chol_scratch_elems(l) * sizeof(float);
+  int use_smem = smem <= 216 * 1024;
+  cudaFuncSetAttribute(chol_shift_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 216 * 1024);
+  chol_shift_pair_kernel<<<2, CHOL_THREADS, use_smem ? smem : 0, st>>>(a, l, st_dev, use_smem, ldt);
+  return launched();
+}
+
 template cudaError_t launch_chol_shift<double>(const double*, int, double, double, double*, double*,
                                                DevStatus*, int, cudaStream_t, int);
 template cudaError_t launch_chol_shift<float>(const double*, int, double, double, float*, float*,

@@ -92,6 +92,16 @@ int64_t chol_scratch_elems(int l);
 template <typename TC>
 cudaError_t launch_chol_shift(const double* W, int l, double shift_coef, double tau_rel, TC* Rinv,
                               TC* scratch, DevStatus* st_dev, int stage, cudaStream_t st, int ldt = 0);
+// The same factorisation of two Grams of equal width at once (two CTAs: the two sides of a
+// pair), each with its own shift, floor, destination, scratch and status stage; 64 < l <= 256.
+struct CholPairArgs {
+  const double* W[2];
+  float* Rinv[2];
+  float* scratch[2];
+  double shift_coef[2], tau_rel[2];
+  int stage[2];
+};
+cudaError_t launch_chol_shift_pair(const CholPairArgs& a, int l, DevStatus* st_dev, cudaStream_t st, int ldt);
 
 // Q = Y Rinv (upper triangular) per tile of rows, optional Gram partials of Q
 // per CTA (part != nullptr, one chunk per CTA), optional transposed output
