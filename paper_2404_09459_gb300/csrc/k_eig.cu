@@ -902,11 +902,46 @@ int eb_dyn_floats(int N) {
 }
 }  // namespace
 
-int64_t eig_big_scratch_floats(int N) { return 6ll * N * N + 64; }
+int64_t eig_big_scratch_floats(int N) { return 6ll * N * N + N + 64; }
+
+// Column j of X = H_0 ... H_{N-3} Z (Z column-major in ZT, reflector k in row k of RT, its scalar
+// in beta[k]; zero: no reflector), by one warp (lane t), written to Xout in FP64.
+__device__ __forceinline__ void eig_big_back_col(int j, int N, const float* ZT, const float* __restrict__ RT,
+                                                 const float* beta, double* __restrict__ Xout, int t) {
+  constexpr int NR = EB_NMAX / 32;
+  const float* Zc = ZT + (size_t)j * N;
+  float z[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    const int i = t + 32 * r;
+    z[r] = i < N ? Zc[i] : 0.f;
+  }
+  for (int k = N - 3; k >= 0; --k) {
+    const float bk = beta[k];
+    if (bk == 0.f) continue;
+    float v[NR];
+    float s = 0.f;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const int i = t + 32 * r;
+      v[r] = (i > k && i < N) ? RT[(size_t)k * N + i] : 0.f;
+      s = fmaf(v[r], z[r], s);
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    s *= bk;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) z[r] -= s * v[r];
+  }
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    const int i = t + 32 * r;
+    if (i < N) Xout[(int64_t)i * N + j] = (double)z[r];
+  }
+}
 
 __device__ __forceinline__ void eig_big_body(const double* __restrict__ Ain, int N, double* __restrict__ Xout,
                                              double* __restrict__ lam, float* __restrict__ gscr, float noise_rel,
-                                             int dyn_floats) {
+                                             int dyn_floats, int back = 1) {
   extern __shared__ float ebsm[];
   __shared__ float s_d[EB_NMAX], s_e[EB_NMAX], s_beta[EB_NMAX], s_v[EB_NMAX], s_p[EB_NMAX], s_lam[EB_NMAX];
   __shared__ float s_cf[EB_NMAX], s_flag[EB_NMAX];
@@ -1339,37 +1374,23 @@ __device__ __forceinline__ void eig_big_body(const double* __restrict__ Ain, int
   }
 
   // ---- 4. back-transformation, a warp per column of Z in registers -----------
-  constexpr int NR = EB_NMAX / 32;
-  for (int j = w; j < N; j += 32) {
-    const float* Zc = ZT + (size_t)j * N;
-    float z[NR];
-#pragma unroll
-    for (int r = 0; r < NR; ++r) {
-      const int i = t + 32 * r;
-      z[r] = i < N ? Zc[i] : 0.f;
-    }
-    for (int k = N - 3; k >= 0; --k) {
-      const float bk = s_beta[k];
-      if (bk == 0.f) continue;
-      float v[NR];
-      float s = 0.f;
-#pragma unroll
-      for (int r = 0; r < NR; ++r) {
-        const int i = t + 32 * r;
-        v[r] = (i > k && i < N) ? RT[(size_t)k * N + i] : 0.f;
-        s = fmaf(v[r], z[r], s);
-      }
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      s *= bk;
-#pragma unroll
-      for (int r = 0; r < NR; ++r) z[r] -= s * v[r];
-    }
-#pragma unroll
-    for (int r = 0; r < NR; ++r) {
-      const int i = t + 32 * r;
-      if (i < N) Xout[(int64_t)i * N + j] = (double)z[r];
-    }
+  if (!back) {  // a separate launch spreads the columns over CTAs (eig_big_back_kernel)
+    for (int k = tid; k < N; k += 1024) gscr[6 * NN + k] = s_beta[k];
+    return;
   }
+  for (int j = w; j < N; j += 32) eig_big_back_col(j, N, ZT, RT, s_beta, Xout, t);
+}
+
+// X = H_0 ... H_{N-3} Z for columns spread over CTAs, a warp per column: the last step of
+// eig_big_body when that ran with back = 0 (Z, the reflectors and their scalars in scratch).
+__global__ __launch_bounds__(256) void eig_big_back_kernel(int N, const float* __restrict__ gscr,
+                                                           double* __restrict__ Xout) {
+  __shared__ float s_beta[EB_NMAX];
+  const size_t NN = (size_t)N * N;
+  for (int k = threadIdx.x; k < N; k += 256) s_beta[k] = gscr[6 * NN + k];
+  __syncthreads();
+  const int j = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (j < N) eig_big_back_col(j, N, gscr, gscr + 4 * NN, s_beta, Xout, threadIdx.x & 31);
 }
 
 __global__ __launch_bounds__(1024) void eig128_kernel(const double* __restrict__ Ain, int N,
@@ -1380,8 +1401,9 @@ __global__ __launch_bounds__(1024) void eig128_kernel(const double* __restrict__
 
 __global__ __launch_bounds__(1024) void eig_big_kernel(const double* __restrict__ Ain, int N,
                                                        double* __restrict__ Xout, double* __restrict__ lam,
-                                                       float* __restrict__ gscr, float noise_rel, int dyn_floats) {
-  eig_big_body(Ain, N, Xout, lam, gscr, noise_rel, dyn_floats);
+                                                       float* __restrict__ gscr, float noise_rel, int dyn_floats,
+                                                       int back) {
+  eig_big_body(Ain, N, Xout, lam, gscr, noise_rel, dyn_floats, back);
 }
 
 // Batched: one CTA per problem (the grouped solve's compressed pairs).
@@ -1460,7 +1482,14 @@ cudaError_t launch_eig_f32(const double* A, int N, double* X, double* lam, float
     const int dyn = eb_dyn_floats(N);
     // a fixed cap: concurrent launches must not lower it
     cudaFuncSetAttribute(eig_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, EB_DYN_FLOATS * 4);
-    eig_big_kernel<<<1, 1024, (size_t)dyn * sizeof(float), st>>>(A, N, X, lam, scratch, (float)noise_rel, dyn);
+    // Z in global scratch (N^2 floats beyond the shared memory): its back-transformation runs as
+    // a second launch over ceil(N / 8) CTAs of 8 warps instead of on this CTA's 32 warps
+    const int back = (int64_t)N * N <= dyn ? 1 : 0;
+    eig_big_kernel<<<1, 1024, (size_t)dyn * sizeof(float), st>>>(A, N, X, lam, scratch, (float)noise_rel, dyn,
+                                                                 back);
+    cudaError_t e = launched();
+    if (e || back) return e;
+    eig_big_back_kernel<<<(unsigned)((N + 7) / 8), 256, 0, st>>>(N, scratch, X);
     return launched();
   }
   const size_t smem = (2ull * N * lda + 8ull * N) * sizeof(float);
